@@ -1,0 +1,336 @@
+"""FP64 CPU oracle: cPINN / XPINN losses, gradients, Adam and stitched eval.
+
+TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU baseline).
+
+Jet component order used throughout (K = number of components kept):
+    0: u,  1: d u / d z0,  2: d u / d z1,  3: d2 u / d z0^2,  4: d2 u / d z1^2
+where z = (x, y) for steady problems and z = (x, t) for Burgers.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from paper_2104_10013_gb300 import problems as P
+
+DT = torch.float64
+
+
+def _t(a) -> torch.Tensor:
+    return torch.as_tensor(np.asarray(a, dtype=np.float64), dtype=DT)
+
+
+# --------------------------------------------------------------------------
+# Network (Sec. 3)
+# --------------------------------------------------------------------------
+
+def softplus(z: torch.Tensor) -> torch.Tensor:
+    """log(1 + e^z), written in a form without overflow for large z."""
+    return torch.clamp(z, min=0.0) + torch.log1p(torch.exp(-torch.abs(z)))
+
+
+def network(layers, z: torch.Tensor, out_act: int) -> torch.Tensor:
+    """N^1 = W^1 z + b^1, N^k = W^k tanh(N^{k-1}) + b^k (2 <= k <= L), with
+    the slope n*a^k fixed at its initial value 1 (Sec. 3).  The last layer is
+    the identity, or a softplus for a strictly positive field."""
+    h = z
+    for k, (W, b) in enumerate(layers):
+        if k > 0:
+            h = torch.tanh(h)
+        h = h @ W.T + b
+    if out_act == P.ACT_SOFTPLUS:
+        h = softplus(h)
+    return h
+
+
+def _grad(y: torch.Tensor, z: torch.Tensor) -> torch.Tensor:
+    g = torch.autograd.grad(y.sum(), z, create_graph=True, allow_unused=True)[0]
+    return torch.zeros_like(z) if g is None else g
+
+
+def jets(layers, z: torch.Tensor, out_act: int, K: int) -> torch.Tensor:
+    """Network output and its input derivatives at every point, by reverse-mode
+    AD (Sec. 4.1): returns [n, D_out, K] in the component order above.  The
+    result stays differentiable with respect to the weights."""
+    z = z.detach().clone().requires_grad_(True)
+    u = network(layers, z, out_act)
+    comps = [u]
+    if K > 1:
+        g = [_grad(u[:, o], z) for o in range(u.shape[1])]
+        comps.append(torch.stack([gi[:, 0] for gi in g], 1))
+        if K > 2:
+            comps.append(torch.stack([gi[:, 1] for gi in g], 1))
+        if K > 3:
+            comps.append(torch.stack([_grad(gi[:, 0], z)[:, 0] for gi in g], 1))
+        if K > 4:
+            comps.append(torch.stack([_grad(gi[:, 1], z)[:, 1] for gi in g], 1))
+    return torch.stack(comps, dim=2)
+
+
+# --------------------------------------------------------------------------
+# PDE residuals and interface fluxes (Sec. 2, Sec. 7)
+# --------------------------------------------------------------------------
+
+# jet components needed at residual points, per PDE and per net
+K_RES = {P.PDE_BURGERS: (4,), P.PDE_POISSON: (5,), P.PDE_NS: (5,), P.PDE_DIFFUSION: (5, 3)}
+
+
+def K_IFACE(pde: int, method: int) -> tuple:
+    """Jet components needed at interface points: first derivatives for the
+    cPINN flux, the residual's components for XPINN residual continuity."""
+    if method == P.XPINN:
+        return K_RES[pde]
+    if pde == P.PDE_BURGERS:
+        return (2,)
+    return (3, 3) if pde == P.PDE_DIFFUSION else (3,)
+
+
+def n_eq(pde: int) -> int:
+    return 3 if pde == P.PDE_NS else 1
+
+
+def n_out_total(problem) -> int:
+    return sum(n.widths[-1] for n in problem.subs[0].nets)
+
+
+def residual(pde: int, J: list, f: torch.Tensor, nu: float, re: float) -> torch.Tensor:
+    """F(u) = L_x(u) - f (Sec. 2) from the jets J (one [n, D_out, K] tensor per
+    net); returns [n, n_eq].
+      Burgers (Eq. BE, z = (x, t)):   u_t + u u_x - nu u_xx
+      Poisson:                        -(u_xx + u_yy) - f
+      Navier-Stokes (Eq. NSEq):       u.grad u + grad p - lap u / Re, div u
+                                      (no forcing term; f is ignored)
+      inverse diffusion (Eq. heq):    K lap u + grad K . grad u - f
+    """
+    Ju = J[0]
+    if pde == P.PDE_BURGERS:
+        u, ux, ut, uxx = Ju[:, 0, 0], Ju[:, 0, 1], Ju[:, 0, 2], Ju[:, 0, 3]
+        return (ut + u * ux - nu * uxx - f)[:, None]
+    if pde == P.PDE_POISSON:
+        return (-(Ju[:, 0, 3] + Ju[:, 0, 4]) - f)[:, None]
+    if pde == P.PDE_NS:
+        u, v, p = Ju[:, 0], Ju[:, 1], Ju[:, 2]
+        r1 = u[:, 0] * u[:, 1] + v[:, 0] * u[:, 2] + p[:, 1] - (u[:, 3] + u[:, 4]) / re
+        r2 = u[:, 0] * v[:, 1] + v[:, 0] * v[:, 2] + p[:, 2] - (v[:, 3] + v[:, 4]) / re
+        r3 = u[:, 1] + v[:, 2]
+        return torch.stack([r1, r2, r3], 1)
+    if pde == P.PDE_DIFFUSION:
+        Jk = J[1]
+        u, k = Ju[:, 0], Jk[:, 0]
+        r = k[:, 0] * (u[:, 3] + u[:, 4]) + k[:, 1] * u[:, 1] + k[:, 2] * u[:, 2] - f
+        return r[:, None]
+    raise ValueError(pde)
+
+
+def flux_normal(pde: int, J: list, normal, nu: float, re: float, flux_mode: int) -> torch.Tensor:
+    """Normal flux f . n at interface points (cPINN, Eq. cPINNLoss), one
+    column per conservation law; returns [n, n_eq].
+      Burgers, conservative form u_t + (u^2/2 - nu u_x)_x = 0 in (x, t):
+          f = (u^2/2 - nu u_x, u); the literal mode uses u u_x - nu u_x.
+      Poisson -div(grad u) = f:   f = -grad u.
+      Navier-Stokes: Table flux-table (x-momentum, y-momentum, mass).
+      Diffusion div(K grad u) = f: f = K grad u.
+    """
+    n0, n1 = float(normal[0]), float(normal[1])
+    Ju = J[0]
+    if pde == P.PDE_BURGERS:
+        u, ux = Ju[:, 0, 0], Ju[:, 0, 1]
+        fx = u * u / 2 - nu * ux if flux_mode == P.FLUX_CONSERVATIVE else u * ux - nu * ux
+        return (n0 * fx + n1 * u)[:, None]
+    if pde == P.PDE_POISSON:
+        return (-(n0 * Ju[:, 0, 1] + n1 * Ju[:, 0, 2]))[:, None]
+    if pde == P.PDE_NS:
+        u, v, p = Ju[:, 0], Ju[:, 1], Ju[:, 2]
+        fxm = (u[:, 0] ** 2 + p[:, 0] - u[:, 1] / re, u[:, 0] * v[:, 0] - u[:, 2] / re)
+        fym = (u[:, 0] * v[:, 0] - v[:, 1] / re, v[:, 0] ** 2 + p[:, 0] - v[:, 2] / re)
+        fma = (u[:, 0], v[:, 0])
+        return torch.stack([n0 * a + n1 * b for a, b in (fxm, fym, fma)], 1)
+    if pde == P.PDE_DIFFUSION:
+        k = J[1][:, 0, 0]
+        return (k * (n0 * Ju[:, 0, 1] + n1 * Ju[:, 0, 2]))[:, None]
+    raise ValueError(pde)
+
+
+# --------------------------------------------------------------------------
+# Adam (Sec. 6) and routing (Eq. FSol)
+# --------------------------------------------------------------------------
+
+def adam_update(theta, g, m, v, t: int, lr, b1: float, b2: float, eps: float):
+    """One bias-corrected Adam step (Kingma & Ba), per subdomain learning rate
+    `lr` (scalar or per-parameter array).  Returns (theta, m, v)."""
+    theta, g, m, v, lr = (np.asarray(a, dtype=np.float64) for a in (theta, g, m, v, lr))
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mhat = m / (1 - b1 ** t)
+    vhat = v / (1 - b2 ** t)
+    return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def route_rect(rects, xy) -> list:
+    """For each point, the subdomains whose closed rectangle contains it; a
+    point on a common interface of S subdomains belongs to all S of them."""
+    xy = np.asarray(xy, dtype=np.float64)
+    out = []
+    for x, y in xy:
+        out.append([q for q, (x0, x1, y0, y1) in enumerate(rects)
+                    if x0 <= x <= x1 and y0 <= y <= y1])
+    return out
+
+
+# --------------------------------------------------------------------------
+# The training step (Algorithm 1)
+# --------------------------------------------------------------------------
+
+class Oracle:
+    """Loss terms, gradients and Adam steps of a cPINN/XPINN problem."""
+
+    def __init__(self, problem: P.Problem):
+        self.pb = problem
+        self.offsets = []
+        off = 0
+        for s in problem.subs:
+            self.offsets.append(off)
+            off += s.n_params
+        self.n_params = off
+
+    # -- parameters --------------------------------------------------------
+    def _layers(self, flat: torch.Tensor, q: int) -> list:
+        """Views of the packed parameter vector: per net, [(W^k, b^k), ...]."""
+        off = self.offsets[q]
+        nets = []
+        for net in self.pb.subs[q].nets:
+            layers = []
+            for k in range(1, len(net.widths)):
+                no, ni = net.widths[k], net.widths[k - 1]
+                W = flat[off:off + no * ni].view(no, ni); off += no * ni
+                b = flat[off:off + no]; off += no
+                layers.append((W, b))
+            nets.append(layers)
+        return nets
+
+    def _jets(self, flat, q, xy, Ks) -> list:
+        s = self.pb.subs[q]
+        z = _t(xy)
+        return [jets(L, z, net.out_act, K)
+                for L, net, K in zip(self._layers(flat, q), s.nets, Ks)]
+
+    def net_jets(self, flat, q: int, net: int, xy, K: int) -> np.ndarray:
+        """Jets [n, D_out, K] of network `net` of subdomain q at points xy."""
+        flat = _t(flat)
+        s = self.pb.subs[q]
+        L = self._layers(flat, q)[net]
+        return jets(L, _t(xy), s.nets[net].out_act, K).detach().numpy()
+
+    # -- interface quantities (Algorithm 1, computation stage) -------------
+    def iface_quantities(self, flat, e: int, side: int):
+        """Side `side` (0: q, 1: q+) of interface e: the solution vector u
+        (all outputs of all nets) and the exchanged quantity, the normal flux
+        f . n (cPINN) or the residual F (XPINN), at the interface points."""
+        pb = self.pb
+        it = pb.ifaces[e]
+        q = it.q if side == 0 else it.qp
+        J = self._jets(flat, q, it.xy, K_IFACE(pb.pde, it.method))
+        uvec = torch.cat([j[:, :, 0] for j in J], 1)
+        if it.method == P.CPINN:
+            qty = flux_normal(pb.pde, J, it.normal, pb.nu, pb.re, pb.flux_mode)
+        else:
+            zero_f = torch.zeros(it.xy.shape[0], dtype=DT)
+            qty = residual(pb.pde, J, zero_f, pb.nu, pb.re)
+        return uvec, qty
+
+    # -- loss (Eqs. cPINNLoss / XPINNLoss) ---------------------------------
+    def loss_terms(self, flat: torch.Tensor) -> torch.Tensor:
+        """[n_sub, 5] tensor of MSE terms (data net 0, data net 1, residual,
+        average solution, flux or residual continuity), differentiable with
+        respect to `flat` through each subdomain's own parameters only."""
+        pb = self.pb
+        rows = []
+        # values exchanged across every interface, held constant (stop-gradient)
+        recv = {}
+        for e in range(len(pb.ifaces)):
+            for side in (0, 1):
+                u, qty = self.iface_quantities(flat, e, side)
+                recv[(e, side)] = (u.detach(), qty.detach())
+        for q, s in enumerate(pb.subs):
+            terms = [torch.zeros((), dtype=DT) for _ in range(P.N_TERMS)]
+            # data mismatch MSE_u per net
+            for ni, ds in enumerate(s.data):
+                if ds is None or ds.xy.shape[0] == 0:
+                    continue
+                L = self._layers(flat, q)[ni]
+                u = network(L, _t(ds.xy), s.nets[ni].out_act)
+                terms[ni] = ((u - _t(ds.val)) ** 2).sum(1).mean()
+            # residual MSE_F
+            if s.res_xy.shape[0] > 0:
+                J = self._jets(flat, q, s.res_xy, K_RES[pb.pde])
+                r = residual(pb.pde, J, _t(s.res_f), pb.nu, pb.re)
+                terms[2] = (r ** 2).sum(1).mean()
+            # interface terms: sum over neighbours of per-interface means
+            for e, it in enumerate(pb.ifaces):
+                if q not in (it.q, it.qp):
+                    continue
+                side = 0 if it.q == q else 1
+                u, qty = self.iface_quantities(flat, e, side)
+                u_o, qty_o = recv[(e, 1 - side)]
+                uavg = (u + u_o) / 2
+                terms[3] = terms[3] + ((u - uavg) ** 2).sum(1).mean()
+                terms[4] = terms[4] + ((qty - qty_o) ** 2).sum(1).mean()
+            rows.append(torch.stack(terms))
+        return torch.stack(rows)
+
+    def weights(self) -> np.ndarray:
+        """[n_sub, 5] loss weights W_u(net 0), W_u(net 1), W_F, W_I, W_flux|W_IF."""
+        W = np.zeros((self.pb.n_sub, P.N_TERMS))
+        for q, s in enumerate(self.pb.subs):
+            for ni, w in enumerate(s.w_data):
+                W[q, ni] = w
+            W[q, 2:] = (s.w_res, s.w_avg, s.w_iface)
+        return W
+
+    def grad(self, flat_np):
+        """Loss terms [n_sub, 5] and the packed gradient of every J(Theta_q)
+        with respect to its own Theta_q."""
+        flat = _t(flat_np).requires_grad_(True)
+        terms = self.loss_terms(flat)
+        J = (terms * _t(self.weights())).sum()
+        (g,) = torch.autograd.grad(J, flat, allow_unused=True)
+        g = torch.zeros_like(flat) if g is None else g
+        return terms.detach().numpy(), g.detach().numpy()
+
+    def lr_vector(self) -> np.ndarray:
+        return np.concatenate([np.full(s.n_params, s.lr) for s in self.pb.subs])
+
+    def step(self, flat, m, v, t: int):
+        """One training step of Algorithm 1: losses, gradients, then an
+        independent Adam update of every subdomain.  t is the 1-based step
+        number after the update.  Returns (terms, theta, m, v)."""
+        terms, g = self.grad(flat)
+        pb = self.pb
+        theta, m, v = adam_update(flat, g, m, v, t, self.lr_vector(), pb.beta1, pb.beta2, pb.eps)
+        return terms, theta, m, v
+
+    # -- stitched prediction (Eq. FSol) --------------------------------------
+    def eval_stitched(self, flat, model: int, xy, K: int) -> np.ndarray:
+        """u(z) = sum_q u_q(z) 1_{Omega_q}(z), the indicator being 1/S on a
+        common interface of S subdomains; jets [n, D_out_total, K].  Points
+        outside every subdomain give NaN."""
+        pb = self.pb
+        spm = pb.subs_per_model or pb.n_sub
+        qs = list(range(model * spm, (model + 1) * spm))
+        rects = [pb.subs[q].rect for q in qs]
+        memb = route_rect(rects, xy)
+        flat = _t(flat)
+        dout = n_out_total(pb)
+        out = np.zeros((len(xy), dout, K))
+        for li, q in enumerate(qs):
+            idx = [i for i, m in enumerate(memb) if li in m]
+            if not idx:
+                continue
+            pts = np.asarray(xy)[idx]
+            J = np.concatenate([
+                jets(L, _t(pts), net.out_act, K).detach().numpy()
+                for L, net in zip(self._layers(flat, q), pb.subs[q].nets)], axis=1)
+            S = np.array([len(memb[i]) for i in idx], dtype=np.float64)
+            out[idx] += J / S[:, None, None]
+        out[[i for i, m in enumerate(memb) if not m]] = np.nan
+        return out

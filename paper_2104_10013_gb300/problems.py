@@ -1,0 +1,383 @@
+"""Seeded synthetic problem generators for domain-decomposed PINNs.
+
+This module builds the *inputs* of a cPINN / XPINN training problem: the
+decomposition of the domain into subdomains, the residual, data and interface
+point sets sampled in each of them, the forcing term and the boundary data of
+the PDE, and the initial network weights.  It holds none of the method's
+arithmetic (no network evaluation, no residual, no loss, no optimiser): it is
+shared, unchanged, by the FP64 oracle and by the CUDA path, which both read
+the float32 arrays it produces.
+
+Pre-processing follows Sec. 5.1 / Algorithm 1 (pre-processing stage): the
+domain is split into non-overlapping subdomains, and training, residual and
+interface points are sampled i.i.d. per subdomain.  Points are drawn uniformly
+in each subdomain (the paper's "N(0, sigma^2)" is not meaningful on a bounded
+subdomain).  Every float array is rounded to float32 here, so that both sides
+consume bit-identical inputs.
+
+PDE ids: 0 Burgers (Sec. 7.3 / 7.5), 1 Poisson, 2 steady incompressible
+Navier-Stokes (Eq. NSEq, Sec. 7.4), 3 inverse diffusion (Eq. heq, Sec. 7.6).
+Interface methods: 0 cPINN (Eq. cPINNLoss), 1 XPINN (Eq. XPINNLoss).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PDE_BURGERS, PDE_POISSON, PDE_NS, PDE_DIFFUSION = 0, 1, 2, 3
+CPINN, XPINN = 0, 1
+ACT_IDENTITY, ACT_SOFTPLUS = 0, 1
+FLUX_CONSERVATIVE, FLUX_LITERAL = 0, 1
+
+# number of loss terms reported per subdomain:
+#   0 MSE_u of data set of net 0, 1 MSE_u of data set of net 1, 2 MSE_F,
+#   3 MSE_uavg, 4 MSE_flux (cPINN) or MSE_R (XPINN)
+N_TERMS = 5
+
+
+@dataclass
+class NetSpec:
+    """One fully connected tanh network (Sec. 3): widths = [N_0, ..., N_L]."""
+    widths: list
+    out_act: int = ACT_IDENTITY
+
+    @property
+    def n_params(self) -> int:
+        return sum(self.widths[k] * self.widths[k - 1] + self.widths[k]
+                   for k in range(1, len(self.widths)))
+
+
+@dataclass
+class DataSet:
+    """Training data of one network: points [n, 2] and targets [n, D_out]."""
+    xy: np.ndarray
+    val: np.ndarray
+
+
+@dataclass
+class Subdomain:
+    nets: list                      # [NetSpec], one or two networks
+    res_xy: np.ndarray              # float32 [n_F, 2] residual points
+    res_f: np.ndarray               # float32 [n_F] forcing f at residual points
+    data: list                      # per net: DataSet or None
+    w_data: list                    # per net: W_u
+    w_res: float = 1.0              # W_F
+    w_avg: float = 1.0              # W_I
+    w_iface: float = 1.0            # W_I,flux (cPINN) or W_I,F (XPINN)
+    lr: float = 1e-3
+    rect: tuple | None = None       # (x0, x1, y0, y1) closed rectangle, for routing
+    params: list = field(default_factory=list)  # per net: [(W[N_k,N_k-1], b[N_k]) ...]
+
+    @property
+    def n_params(self) -> int:
+        return sum(n.n_params for n in self.nets)
+
+
+@dataclass
+class Interface:
+    """A common interface between subdomains q and qp, with its own points."""
+    q: int
+    qp: int
+    method: int
+    normal: tuple
+    xy: np.ndarray                  # float32 [n_I, 2]
+
+
+@dataclass
+class Problem:
+    name: str
+    pde: int
+    subs: list
+    ifaces: list
+    nu: float = 0.0
+    re: float = 1.0
+    flux_mode: int = FLUX_CONSERVATIVE
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    subs_per_model: int = 0         # subdomains per independent copy (0: all)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_sub(self) -> int:
+        return len(self.subs)
+
+    @property
+    def n_models(self) -> int:
+        spm = self.subs_per_model or self.n_sub
+        return self.n_sub // spm
+
+    def packed_params(self) -> np.ndarray:
+        """All parameters in the packed layout: per subdomain, per net, per
+        layer k = 1..L: W^k row-major [N_k][N_{k-1}] followed by b^k."""
+        out = []
+        for s in self.subs:
+            for net_params in s.params:
+                for W, b in net_params:
+                    out.append(W.reshape(-1))
+                    out.append(b.reshape(-1))
+        return np.concatenate(out).astype(np.float32)
+
+    def unpack_params(self, flat: np.ndarray) -> list:
+        """Inverse of packed_params: per subdomain, per net, [(W, b), ...]."""
+        flat = np.asarray(flat)
+        res, off = [], 0
+        for s in self.subs:
+            sp = []
+            for net in s.nets:
+                layers = []
+                for k in range(1, len(net.widths)):
+                    no, ni = net.widths[k], net.widths[k - 1]
+                    W = flat[off:off + no * ni].reshape(no, ni); off += no * ni
+                    b = flat[off:off + no]; off += no
+                    layers.append((W, b))
+                sp.append(layers)
+            res.append(sp)
+        assert off == flat.size
+        return res
+
+    @property
+    def n_params(self) -> int:
+        return sum(s.n_params for s in self.subs)
+
+    @property
+    def n_res(self) -> int:
+        return sum(s.res_xy.shape[0] for s in self.subs)
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).astype(np.float32))
+
+
+def _rng(seed: int, *key: int) -> np.random.Generator:
+    return np.random.default_rng([int(seed)] + [int(k) for k in key])
+
+
+def xavier_params(net: NetSpec, rng: np.random.Generator) -> list:
+    """Xavier-normal weights (std = sqrt(2 / (fan_in + fan_out))), zero biases."""
+    layers = []
+    for k in range(1, len(net.widths)):
+        no, ni = net.widths[k], net.widths[k - 1]
+        W = rng.normal(0.0, math.sqrt(2.0 / (ni + no)), size=(no, ni))
+        layers.append((_f32(W), np.zeros(no, np.float32)))
+    return layers
+
+
+def _uniform_rect(rng, n, x0, x1, y0, y1) -> np.ndarray:
+    u = rng.random((n, 2))
+    return np.stack([x0 + (x1 - x0) * u[:, 0], y0 + (y1 - y0) * u[:, 1]], axis=1)
+
+
+def _segment_points(rng, n, a, b) -> np.ndarray:
+    """n uniform points on the segment from a to b."""
+    s = rng.random(n)
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return a[None, :] + s[:, None] * (b - a)[None, :]
+
+
+def _split_counts(n, lengths) -> list:
+    """Split n points over pieces proportionally to their lengths."""
+    lengths = np.asarray(lengths, float)
+    if lengths.sum() <= 0:
+        return [0] * len(lengths)
+    raw = n * lengths / lengths.sum()
+    cnt = np.floor(raw).astype(int)
+    for i in np.argsort(-(raw - cnt))[: n - cnt.sum()]:
+        cnt[i] += 1
+    return cnt.tolist()
+
+
+def _rect_boundary_pieces(rect, domain) -> list:
+    """Edges of a rectangle that lie on the boundary of the rectangular domain."""
+    x0, x1, y0, y1 = rect
+    X0, X1, Y0, Y1 = domain
+    pieces = []
+    if abs(x0 - X0) < 1e-12:
+        pieces.append(((x0, y0), (x0, y1)))
+    if abs(x1 - X1) < 1e-12:
+        pieces.append(((x1, y0), (x1, y1)))
+    if abs(y0 - Y0) < 1e-12:
+        pieces.append(((x0, y0), (x1, y0)))
+    if abs(y1 - Y1) < 1e-12:
+        pieces.append(((x0, y1), (x1, y1)))
+    return pieces
+
+
+def _grid_interfaces(xc, yc, rng_for, n_iface, method) -> list:
+    """Interfaces of a tensor grid with cell (i, j) -> subdomain i + nx*j."""
+    nx, ny = len(xc) - 1, len(yc) - 1
+    out = []
+    e = 0
+    for j in range(ny):            # vertical cuts x = xc[i], i = 1..nx-1
+        for i in range(1, nx):
+            q, qp = (i - 1) + nx * j, i + nx * j
+            xy = _segment_points(rng_for(e), n_iface, (xc[i], yc[j]), (xc[i], yc[j + 1]))
+            out.append(Interface(q, qp, method, (1.0, 0.0), _f32(xy)))
+            e += 1
+    for j in range(1, ny):         # horizontal cuts y = yc[j]
+        for i in range(nx):
+            q, qp = i + nx * (j - 1), i + nx * j
+            xy = _segment_points(rng_for(e), n_iface, (xc[i], yc[j]), (xc[i + 1], yc[j]))
+            out.append(Interface(q, qp, method, (0.0, 1.0), _f32(xy)))
+            e += 1
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Exact solutions / forcing terms (problem data, not method arithmetic)
+# ---------------------------------------------------------------------------
+
+def poisson_exact(x, y):
+    """Manufactured u* = sin(2 pi x) sin(3 pi y) + 0.1 sin(20 pi x y)."""
+    return np.sin(2 * np.pi * x) * np.sin(3 * np.pi * y) + 0.1 * np.sin(20 * np.pi * x * y)
+
+
+def poisson_forcing(x, y):
+    """f = -lap u* for poisson_exact (derived by hand)."""
+    return (13 * np.pi ** 2 * np.sin(2 * np.pi * x) * np.sin(3 * np.pi * y)
+            + 40 * np.pi ** 2 * (x ** 2 + y ** 2) * np.sin(20 * np.pi * x * y))
+
+
+def kovasznay_lambda(re):
+    return re / 2 - math.sqrt(re * re / 4 + 4 * math.pi ** 2)
+
+
+def kovasznay_exact(x, y, re):
+    """Kovasznay flow (u, v, p), a closed-form solution of steady NS."""
+    lam = kovasznay_lambda(re)
+    e = np.exp(lam * x)
+    u = 1 - e * np.cos(2 * np.pi * y)
+    v = lam / (2 * np.pi) * e * np.sin(2 * np.pi * y)
+    p = 0.5 * (1 - np.exp(2 * lam * x))
+    return np.stack([u, v, p], axis=-1)
+
+
+def diffusion_exact_u(x, y):
+    """Temperature field of Sec. 7.6: T = 20 exp(-0.1 y)."""
+    return 20.0 * np.exp(-0.1 * y)
+
+
+def diffusion_exact_k(x, y):
+    """Synthetic conductivity K* = 1 + 0.5 sin(pi x) cos(pi y)."""
+    return 1.0 + 0.5 * np.sin(np.pi * x) * np.cos(np.pi * y)
+
+
+def diffusion_forcing(x, y):
+    """f = div(K* grad u*) for the two fields above (derived by hand)."""
+    return np.exp(-0.1 * y) * (0.2 + 0.1 * np.sin(np.pi * x) * np.cos(np.pi * y)
+                               + np.pi * np.sin(np.pi * x) * np.sin(np.pi * y))
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+
+def burgers_cpinn(n_sub=4, n_res=1000, n_iface=100, n_bc=50, hidden=(20, 20, 20),
+                  lr=1e-3, seed=0, flux_mode=FLUX_CONSERVATIVE, nu=0.01 / math.pi) -> Problem:
+    """1D viscous Burgers u_t + u u_x = nu u_xx on x in [-1,1], t in [0,1]
+    (Sec. 7.3, Eq. BE), u(x,0) = -sin(pi x), u(+-1,t) = 0; n_sub equal x-slabs
+    coupled by cPINN (flux + average continuity).  Inputs are (x, t)."""
+    xc = np.linspace(-1.0, 1.0, n_sub + 1)
+    net = NetSpec([2, *hidden, 1])
+    subs = []
+    for q in range(n_sub):
+        x0, x1 = xc[q], xc[q + 1]
+        rng = _rng(seed, 1, q)
+        res = _uniform_rect(rng, n_res, x0, x1, 0.0, 1.0)
+        # initial / boundary data spread over the subdomain's boundary pieces
+        pieces = [((x0, 0.0), (x1, 0.0))]
+        if q == 0:
+            pieces.append(((-1.0, 0.0), (-1.0, 1.0)))
+        if q == n_sub - 1:
+            pieces.append(((1.0, 0.0), (1.0, 1.0)))
+        lens = [math.dist(a, b) for a, b in pieces]
+        cnt = _split_counts(n_bc, lens)
+        rb = _rng(seed, 2, q)
+        bxy = np.concatenate([_segment_points(rb, c, a, b) for (a, b), c in zip(pieces, cnt)])
+        bval = np.where(np.abs(bxy[:, 1]) < 1e-12, -np.sin(np.pi * bxy[:, 0]), 0.0)
+        sub = Subdomain(nets=[net], res_xy=_f32(res), res_f=np.zeros(n_res, np.float32),
+                        data=[DataSet(_f32(bxy), _f32(bval[:, None]))], w_data=[1.0],
+                        lr=lr, rect=(x0, x1, 0.0, 1.0))
+        sub.params = [xavier_params(net, _rng(seed, 3, q))]
+        subs.append(sub)
+    ifaces = _grid_interfaces(xc, np.array([0.0, 1.0]), lambda e: _rng(seed, 4, e), n_iface, CPINN)
+    return Problem("burgers_cpinn", PDE_BURGERS, subs, ifaces, nu=nu, flux_mode=flux_mode,
+                   meta=dict(xcuts=xc.tolist(), ycuts=[0.0, 1.0]))
+
+
+def poisson_xpinn(nx=4, ny=4, n_res_range=(2000, 20000), depth_range=(4, 6), width_range=(20, 80),
+                  n_iface=200, n_bc=100, lr=1e-3, seed=0, min_cell=0.1) -> Problem:
+    """2D Poisson -lap u = f on the unit square, manufactured solution
+    poisson_exact, XPINN on an uneven nx x ny tensor grid.  Each subdomain draws
+    its residual-point count, depth (hidden layers) and width from the seed."""
+    g = _rng(seed, 10)
+
+    def cuts(n):
+        while True:
+            c = np.sort(g.random(n - 1))
+            full = np.concatenate([[0.0], c, [1.0]])
+            if np.all(np.diff(full) >= min_cell):
+                return full
+    xc, yc = cuts(nx), cuts(ny)
+    subs = []
+    for j in range(ny):
+        for i in range(nx):
+            q = i + nx * j
+            hp = _rng(seed, 11, q)
+            n_res = int(hp.integers(n_res_range[0], n_res_range[1] + 1))
+            depth = int(hp.integers(depth_range[0], depth_range[1] + 1))
+            width = int(hp.integers(width_range[0], width_range[1] + 1))
+            net = NetSpec([2] + [width] * depth + [1])
+            rect = (xc[i], xc[i + 1], yc[j], yc[j + 1])
+            rng = _rng(seed, 12, q)
+            res = _f32(_uniform_rect(rng, n_res, *rect))
+            pieces = _rect_boundary_pieces(rect, (0.0, 1.0, 0.0, 1.0))
+            rb = _rng(seed, 13, q)
+            data = None
+            if pieces:
+                bxy = _f32(np.concatenate([_segment_points(rb, n_bc, a, b) for a, b in pieces]))
+                data = DataSet(bxy, _f32(poisson_exact(bxy[:, 0].astype(np.float64),
+                                                       bxy[:, 1].astype(np.float64))[:, None]))
+            f = poisson_forcing(res[:, 0].astype(np.float64), res[:, 1].astype(np.float64))
+            sub = Subdomain(nets=[net], res_xy=res, res_f=_f32(f), data=[data], w_data=[1.0],
+                            lr=lr, rect=rect)
+            sub.params = [xavier_params(net, _rng(seed, 14, q))]
+            subs.append(sub)
+    ifaces = _grid_interfaces(xc, yc, lambda e: _rng(seed, 15, e), n_iface, XPINN)
+    return Problem("poisson_xpinn", PDE_POISSON, subs, ifaces,
+                   meta=dict(xcuts=xc.tolist(), ycuts=yc.tolist()))
+
+
+def kovasznay_cpinn(nx=8, ny=8, n_res=50000, n_iface=256, n_bc=80, width=64, depth=6, re=40.0,
+                    lr=6e-4, seed=0) -> Problem:
+    """2D steady incompressible NS (Eq. NSEq), Kovasznay flow at Re on
+    [-0.5,1] x [-0.5,1.5], cPINN on an equal nx x ny grid; each boundary
+    subdomain gets n_bc Dirichlet points for (u, v, p)."""
+    dom = (-0.5, 1.0, -0.5, 1.5)
+    xc = np.linspace(dom[0], dom[1], nx + 1)
+    yc = np.linspace(dom[2], dom[3], ny + 1)
+    net = NetSpec([2] + [width] * depth + [3])
+    subs = []
+    for j in range(ny):
+        for i in range(nx):
+            q = i + nx * j
+            rect = (xc[i], xc[i + 1], yc[j], yc[j + 1])
+            res = _f32(_uniform_rect(_rng(seed, 21, q), n_res, *rect))
+            pieces = _rect_boundary_pieces(rect, dom)
+            data = None
+            if pieces:
+                cnt = _split_counts(n_bc, [math.dist(a, b) for a, b in pieces])
+                rb = _rng(seed, 22, q)
+                bxy = _f32(np.concatenate([_segment_points(rb, c, a, b)
+                                           for (a, b), c in zip(pieces, cnt)]))
+                data = DataSet(bxy, _f32(kovasznay_exact(bxy[:, 0].astype(np.float64),
+                                                         bxy[:, 1].astype(np.float64), re)))
+            sub = Subdomain(nets=[net], res_xy=res, res_f=np.zeros(n_res, np.float32),
+                            data=[data], w_data=[1.0], lr=lr, rect=rect)
+            sub.params = [xavier_params(net, _rng(seed, 23, q))]
+            subs.append(sub)
+    ifaces = _grid_interfaces(xc, yc, lambda e: _rng(seed, 24, e), n_iface, CPINN)
+    return Problem("kovasznay_cpinn", PDE_NS, subs, ifaces, re=re,
+                   meta=dict(xcuts=xc.tolist(), ycuts=yc.tolist()))
