@@ -1,0 +1,219 @@
+/*
+ * xpinn.h — C ABI of the GB300 library for domain-decomposed physics-informed
+ * neural networks (cPINN / XPINN), after "Parallel Physics-Informed Neural
+ * Networks via Domain Decomposition" (Shukla, Jagtap, Karniadakis, 2021).
+ *
+ * One handle holds one problem: every subdomain Omega_q of a decomposed domain
+ * (Sec. 4.2, Sec. 5.1), its network(s) (Sec. 3), its residual, data and
+ * interface point sets, its loss weights (Eqs. cPINNLoss and XPINNLoss) and
+ * its Adam state (Sec. 6).  Independent copies of a decomposition (for
+ * hyper-parameter sweeps) are simply more subdomains in the same handle.
+ *
+ * Conventions, for every function below:
+ *  - The return value is an xpinn_status; XPINN_OK (0) on success.  On error a
+ *    message is available from xpinn_last_error() (thread-local).  No call
+ *    aborts, throws across the ABI or traps on the device.
+ *  - Pointers named "host" must be host memory.  Pointers documented as
+ *    "host or device" may be either; the library asks the CUDA runtime which
+ *    (cudaPointerGetAttributes).  With a device pointer the call is
+ *    asynchronous in `stream`; with a host pointer it returns after the data
+ *    has been copied, which synchronises `stream`.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Calls on one handle are stream-ordered and not thread-safe.
+ *  - Jet components are ordered (u, d0 u, d1 u, d00 u, d11 u): value, first
+ *    derivatives and diagonal second derivatives with respect to the two
+ *    inputs z = (z0, z1), which are (x, t) for Burgers and (x, y) otherwise.
+ *    A request of derivative order 0, 1 or 2 returns the first 1, 3 or 5.
+ *  - The caller owns every buffer it passes; xpinn_create copies what it needs.
+ */
+#ifndef XPINN_H
+#define XPINN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XPINN_MAX_NETS 2      /* networks per subdomain (inverse problems use 2) */
+#define XPINN_MAX_LAYERS 12   /* weight layers L per network */
+#define XPINN_MAX_WIDTH 112   /* neurons per hidden layer */
+#define XPINN_MAX_OUT 3       /* outputs per network */
+#define XPINN_N_TERMS 5       /* loss terms reported per subdomain, see below */
+
+typedef enum {
+  XPINN_OK = 0,
+  XPINN_ERR_INVALID = -1,     /* bad argument or inconsistent description */
+  XPINN_ERR_OOM = -2,         /* device allocation failed */
+  XPINN_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  XPINN_ERR_TIMEOUT = -4,     /* a bounded device wait gave up */
+  XPINN_ERR_NONFINITE = -5,   /* a loss became NaN or infinite */
+  XPINN_ERR_UNSUPPORTED = -6  /* valid, but outside what this build implements */
+} xpinn_status;
+
+/* PDEs (residual F(u) = L_x(u) - f, Sec. 2):
+ *  BURGERS   u_t + u u_x - nu u_xx                     (Eq. BE), z = (x, t)
+ *  POISSON   -(u_xx + u_yy) - f
+ *  NS        steady incompressible Navier-Stokes, outputs (u, v, p),
+ *            u.grad u + grad p - lap u / Re and div u  (Eq. NSEq)
+ *  DIFFUSION div(K grad u) - f with two networks per subdomain, u and K
+ *            (the inverse problem of Eq. heq)                                 */
+enum { XPINN_PDE_BURGERS = 0, XPINN_PDE_POISSON = 1, XPINN_PDE_NS = 2, XPINN_PDE_DIFFUSION = 3 };
+/* Interface conditions: cPINN (Eq. cPINNLoss: average solution + normal flux
+ * continuity) or XPINN (Eq. XPINNLoss: average solution + residual continuity). */
+enum { XPINN_CPINN = 0, XPINN_XPINN = 1 };
+/* Output layer activation: identity (Sec. 3) or softplus (a positive field). */
+enum { XPINN_ACT_IDENTITY = 0, XPINN_ACT_SOFTPLUS = 1 };
+/* Burgers flux for cPINN: conservative f = u^2/2 - nu u_x, or u u_x - nu u_x. */
+enum { XPINN_FLUX_CONSERVATIVE = 0, XPINN_FLUX_LITERAL = 1 };
+
+/* Loss terms, per subdomain, in this order (each is the MSE before weighting):
+ *  0 MSE_u of the data set of network 0      1 MSE_u of the data set of network 1
+ *  2 MSE_F (residual)                         3 MSE_uavg (sum over neighbours)
+ *  4 MSE_flux (cPINN) or MSE_R (XPINN), summed over neighbours.
+ * J(Theta_q) = w_data[0] T0 + w_data[1] T1 + w_res T2 + w_avg T3 + w_iface T4. */
+
+/* A fully connected network (Sec. 3): N^1 = W^1 z + b^1,
+ * N^k = W^k tanh(N^{k-1}) + b^k for 2 <= k <= L; widths[0] = 2 (inputs),
+ * widths[L] = outputs.  The layer-wise slope n*a^k is fixed at 1. */
+typedef struct {
+  int32_t n_layers;                        /* L >= 2 */
+  int32_t widths[XPINN_MAX_LAYERS + 1];
+  int32_t out_act;                         /* XPINN_ACT_* */
+} xpinn_net_desc;
+
+/* One subdomain Omega_q.  All arrays are host memory, float32, row-major. */
+typedef struct {
+  int32_t n_nets;                          /* 1, or 2 for XPINN_PDE_DIFFUSION (u, K) */
+  xpinn_net_desc nets[XPINN_MAX_NETS];
+  int64_t n_res;                           /* residual points x_F */
+  const float* res_xy;                     /* [n_res][2] */
+  const float* res_f;                      /* [n_res] forcing f, or NULL for f = 0 */
+  int64_t n_data[XPINN_MAX_NETS];          /* data / boundary points of each net */
+  const float* data_xy[XPINN_MAX_NETS];    /* [n_data][2] */
+  const float* data_val[XPINN_MAX_NETS];   /* [n_data][D_out of that net] targets */
+  float w_data[XPINN_MAX_NETS];            /* W_u */
+  float w_res;                             /* W_F */
+  float w_avg;                             /* W_I */
+  float w_iface;                           /* W_I,flux (cPINN) or W_I,F (XPINN) */
+  float lr;                                /* Adam learning rate of this subdomain */
+  float rect[4];                           /* closed box x0, x1, y0, y1 used by xpinn_eval */
+} xpinn_subdomain_desc;
+
+/* A common interface between subdomains q and q_plus with its own points
+ * (one point set, evaluated by both networks).  Each side's loss treats the
+ * other side's values as constants, as Algorithm 1 receives them. */
+typedef struct {
+  int32_t q, q_plus;
+  int32_t method;                          /* XPINN_CPINN or XPINN_XPINN */
+  float normal[2];                         /* n for the cPINN flux f . n */
+  int64_t n_pts;
+  const float* xy;                         /* [n_pts][2] */
+} xpinn_interface_desc;
+
+typedef struct {
+  int32_t pde;                             /* XPINN_PDE_* */
+  float nu;                                /* Burgers viscosity */
+  float re;                                /* Navier-Stokes Reynolds number */
+  int32_t flux_mode;                       /* XPINN_FLUX_* (Burgers cPINN only) */
+  int32_t n_sub;
+  const xpinn_subdomain_desc* subs;        /* [n_sub] */
+  int32_t n_iface;
+  const xpinn_interface_desc* ifaces;      /* [n_iface] */
+  float beta1, beta2, eps;                 /* Adam constants shared by all subdomains */
+  int32_t subs_per_model;                  /* subdomains per independent copy; 0 = n_sub */
+  const float* init_params;                /* packed parameters (see xpinn_get_params) */
+} xpinn_problem_desc;
+
+typedef struct xpinn_ctx* xpinn_handle;
+
+/* Create a handle: validates `desc`, copies every array to the device and
+ * plans the grouped step.  Device memory is allocated here and freed by
+ * xpinn_destroy.  Errors: INVALID (inconsistent description), UNSUPPORTED
+ * (a width, depth or output count beyond the limits above), OOM, CUDA. */
+int xpinn_create(const xpinn_problem_desc* desc, xpinn_handle* out);
+
+/* Free all device and host memory of the handle.  NULL is accepted. */
+int xpinn_destroy(xpinn_handle h);
+
+/* Message of the last error on this thread ("" if none). */
+const char* xpinn_last_error(void);
+
+/* Number of floats in the packed parameter vector: subdomain by subdomain,
+ * network by network, layer k = 1..L: W^k row-major [N_k][N_{k-1}], then b^k. */
+int64_t xpinn_num_params(xpinn_handle h);
+
+/* Copy the packed parameters out of / into the handle (host or device
+ * pointer, n = xpinn_num_params).  set_params leaves Adam's moments and step
+ * count unchanged. */
+int xpinn_get_params(xpinn_handle h, float* dst, int64_t n, void* stream);
+int xpinn_set_params(xpinn_handle h, const float* src, int64_t n, void* stream);
+
+/* Loss terms and gradients at the current parameters, with no update:
+ * losses [n_sub][XPINN_N_TERMS] (or NULL), grads packed like the parameters
+ * (or NULL), dJ(Theta_q)/dTheta_q for every q with the neighbours' interface
+ * values held constant (Algorithm 1).  Host or device pointers. */
+int xpinn_grad(xpinn_handle h, float* losses, float* grads, void* stream);
+
+/* n_steps training steps of Algorithm 1, all subdomains in one grouped
+ * launch per phase: interface values, jets + residual + interface terms +
+ * reverse pass, then reduction and Adam (Sec. 6).  losses, if not NULL,
+ * receives [n_steps][n_sub][XPINN_N_TERMS], each row measured before that
+ * step's update.  Returns XPINN_ERR_NONFINITE (after completing the steps) if
+ * a loss is NaN or infinite and `losses` was given. */
+int xpinn_step(xpinn_handle h, int32_t n_steps, float* losses, void* stream);
+
+/* Jets of network `net` of subdomain q at n points xy [n][2]:
+ * out [n][D_out][1 + 2*(order>0) + 2*(order>1)], order 0..2.  Host or device
+ * pointers (both on the same side). */
+int xpinn_net_jets(xpinn_handle h, int32_t q, int32_t net, const float* xy, int64_t n,
+                   int32_t order, float* out, void* stream);
+
+/* The stitched solution of Eq. FSol for copy `model`: u(z) = sum_q u_q(z)
+ * 1_{Omega_q}(z), with 1/S on an interface shared by S subdomains; points are
+ * routed to subdomains on the device by their closed boxes (`rect`).  out
+ * [n][D_out_total][1 + 2*(order>0) + 2*(order>1)], where D_out_total counts
+ * the outputs of all networks of a subdomain.  Points outside every box give
+ * NaN.  Host or device pointers (both on the same side). */
+int xpinn_eval(xpinn_handle h, int32_t model, const float* xy, int64_t n, int32_t order,
+               float* out, void* stream);
+
+/* Replace the residual points (and forcing) of every subdomain, keeping the
+ * per-subdomain counts: xy [n_res_total][2], f [n_res_total] or NULL (f = 0),
+ * subdomain by subdomain in order.  Host or device pointers.  Used to
+ * resample residual points between steps. */
+int xpinn_set_residual_points(xpinn_handle h, const float* xy, const float* f, int64_t n,
+                              void* stream);
+
+/* Checkpoint: the parameters, Adam moments m and v and the step count as one
+ * versioned blob in host memory.  get_state with blob == NULL stores the
+ * required size in *n.  set_state rejects a blob of another problem shape. */
+int xpinn_get_state(xpinn_handle h, void* blob, size_t* n);
+int xpinn_set_state(xpinn_handle h, const void* blob, size_t n);
+
+/* Execution options (see xpinn_options). */
+typedef struct {
+  int32_t schedule;        /* 0 grouped (one launch per phase for all subdomains),
+                              1 per-subdomain loop (the same kernels launched once
+                              per subdomain per phase: the baseline) */
+  int32_t use_graph;       /* 1: replay steps from a captured CUDA graph */
+  int32_t items_per_cta;   /* work items per CTA the scheduler aims for (>= 1) */
+  int32_t points_per_thread; /* 1 or 2 points in a thread's register tile */
+} xpinn_options;
+
+int xpinn_get_options(xpinn_handle h, xpinn_options* opt);
+int xpinn_set_options(xpinn_handle h, const xpinn_options* opt);
+
+/* Interface exchange buffer after the last grad/step: for every interface
+ * (in order), every point, side 0 (q) then side 1 (q_plus): the solution
+ * vector u (all outputs of all networks) followed by the exchanged quantity
+ * (normal fluxes f . n for cPINN, residuals F for XPINN).  n_floats receives
+ * the size when out is NULL.  Host or device pointer. */
+int xpinn_iface_values(xpinn_handle h, float* out, int64_t* n_floats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XPINN_H */

@@ -20,6 +20,11 @@ def _t(a) -> torch.Tensor:
     return torch.as_tensor(np.asarray(a, dtype=np.float64), dtype=DT)
 
 
+def _r32(x) -> float:
+    """A scalar as the float32 value the problem description carries."""
+    return float(np.float32(x))
+
+
 # --------------------------------------------------------------------------
 # Network (Sec. 3)
 # --------------------------------------------------------------------------
@@ -192,6 +197,9 @@ class Oracle:
             self.offsets.append(off)
             off += s.n_params
         self.n_params = off
+        # scalars exactly as the float32 problem description carries them
+        self.nu, self.re = _r32(problem.nu), _r32(problem.re)
+        self.beta1, self.beta2, self.eps = _r32(problem.beta1), _r32(problem.beta2), _r32(problem.eps)
 
     # -- parameters --------------------------------------------------------
     def _layers(self, flat: torch.Tensor, q: int) -> list:
@@ -232,10 +240,13 @@ class Oracle:
         J = self._jets(flat, q, it.xy, K_IFACE(pb.pde, it.method))
         uvec = torch.cat([j[:, :, 0] for j in J], 1)
         if it.method == P.CPINN:
-            qty = flux_normal(pb.pde, J, it.normal, pb.nu, pb.re, pb.flux_mode)
+            normal = (_r32(it.normal[0]), _r32(it.normal[1]))
+            qty = flux_normal(pb.pde, J, normal, self.nu, self.re, pb.flux_mode)
         else:
+            # the forcing is the same on both sides of a common point, so it
+            # cancels in F_q - F_q+; it is left out of the exchanged residual
             zero_f = torch.zeros(it.xy.shape[0], dtype=DT)
-            qty = residual(pb.pde, J, zero_f, pb.nu, pb.re)
+            qty = residual(pb.pde, J, zero_f, self.nu, self.re)
         return uvec, qty
 
     # -- loss (Eqs. cPINNLoss / XPINNLoss) ---------------------------------
@@ -263,7 +274,7 @@ class Oracle:
             # residual MSE_F
             if s.res_xy.shape[0] > 0:
                 J = self._jets(flat, q, s.res_xy, K_RES[pb.pde])
-                r = residual(pb.pde, J, _t(s.res_f), pb.nu, pb.re)
+                r = residual(pb.pde, J, _t(s.res_f), self.nu, self.re)
                 terms[2] = (r ** 2).sum(1).mean()
             # interface terms: sum over neighbours of per-interface means
             for e, it in enumerate(pb.ifaces):
@@ -285,7 +296,7 @@ class Oracle:
             for ni, w in enumerate(s.w_data):
                 W[q, ni] = w
             W[q, 2:] = (s.w_res, s.w_avg, s.w_iface)
-        return W
+        return W.astype(np.float32).astype(np.float64)
 
     def grad(self, flat_np):
         """Loss terms [n_sub, 5] and the packed gradient of every J(Theta_q)
@@ -298,7 +309,7 @@ class Oracle:
         return terms.detach().numpy(), g.detach().numpy()
 
     def lr_vector(self) -> np.ndarray:
-        return np.concatenate([np.full(s.n_params, s.lr) for s in self.pb.subs])
+        return np.concatenate([np.full(s.n_params, _r32(s.lr)) for s in self.pb.subs])
 
     def step(self, flat, m, v, t: int):
         """One training step of Algorithm 1: losses, gradients, then an
@@ -306,7 +317,7 @@ class Oracle:
         number after the update.  Returns (terms, theta, m, v)."""
         terms, g = self.grad(flat)
         pb = self.pb
-        theta, m, v = adam_update(flat, g, m, v, t, self.lr_vector(), pb.beta1, pb.beta2, pb.eps)
+        theta, m, v = adam_update(flat, g, m, v, t, self.lr_vector(), self.beta1, self.beta2, self.eps)
         return terms, theta, m, v
 
     # -- stitched prediction (Eq. FSol) --------------------------------------

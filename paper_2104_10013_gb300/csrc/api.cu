@@ -1,0 +1,1082 @@
+// C ABI of the cPINN / XPINN library (declared in include/xpinn.h).
+//
+// xpinn_create copies the problem to the device and plans the step: it cuts
+// every subdomain's point sets into work items of similar cost, sizes shared
+// memory and per-CTA scratch, and lays out the gradient slices.  A training
+// step (Algorithm 1) is then four launches on one stream, replayed from a
+// CUDA graph:
+//   step_begin   reset work counters, advance the Adam step and loss slot
+//   jet kernel   interface sides, forward only: fills the exchange buffer
+//   jet kernel   all residual / data / interface items: jets, loss, reverse
+//   reduce_adam  fixed-order sum of the gradient slices, Adam per subdomain
+// The per-subdomain loop schedule launches the same kernels once per
+// subdomain and phase instead (the baseline the grouped launch replaces).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "xpinn_dev.cuh"
+
+namespace xp {
+void launch_route(const float2* pts, int64_t n, const SubDev* subs, int q0, int nq, int* S, int* memb,
+                  int* counts, int* err, cudaStream_t st);
+void launch_bucket(const float2* pts, int64_t n, const int* S, const int* memb, int* cursor, int* pos,
+                   float2* epts, float* escale, cudaStream_t st);
+void launch_gather(int64_t n, int row, const int* S, const int* pos, const float* eout, float* out,
+                   cudaStream_t st);
+}  // namespace xp
+
+using namespace xp;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct Error {
+  int code;
+};
+
+[[noreturn]] void fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  throw Error{code};
+}
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? XPINN_ERR_OOM : XPINN_ERR_CUDA, "%s: %s", what,
+         cudaGetErrorString(e));
+  }
+}
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) count = 1;
+    ck(cudaMalloc(&p, count * sizeof(T)), "cudaMalloc");
+    n = count;
+  }
+  void ensure(size_t count) {
+    if (count > n) alloc(count);
+  }
+  void upload(const T* src, size_t count, cudaStream_t s = 0) {
+    alloc(count);
+    if (count) ck(cudaMemcpyAsync(p, src, count * sizeof(T), cudaMemcpyHostToDevice, s), "upload");
+  }
+};
+
+bool is_device_ptr(const void* ptr) {
+  if (!ptr) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int k_res(int pde, int net) {
+  if (pde == XPINN_PDE_BURGERS) return net == 0 ? 4 : 0;
+  if (pde == XPINN_PDE_DIFFUSION) return net == 0 ? 5 : 3;
+  return net == 0 ? 5 : 0;
+}
+int k_iface(int pde, int method, int net) {
+  if (method == XPINN_XPINN) return k_res(pde, net);
+  if (pde == XPINN_PDE_BURGERS) return net == 0 ? 2 : 0;
+  if (pde == XPINN_PDE_DIFFUSION) return 3;
+  return net == 0 ? 3 : 0;
+}
+
+}  // namespace
+
+struct Plan {
+  std::vector<Item> items;       // [0, n_fwd): exchange items; then the main items
+  int n_fwd = 0;
+  std::vector<int> q_items, q_item_begin;
+  std::vector<int64_t> q_part_off;
+  std::vector<int2> red_blocks;
+  // per-subdomain ranges (loop schedule)
+  std::vector<int> fwd_begin, main_begin;   // [n_sub + 1], relative to n_fwd for main
+  int64_t partial_floats = 0;
+};
+
+struct xpinn_ctx {
+  // problem
+  int pde = 0, flux_mode = 0;
+  float nu = 0, re = 1, beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
+  int n_sub = 0, n_iface = 0, spm = 0;
+  std::vector<SubDev> subs;
+  std::vector<IfaceDev> ifaces;
+  int64_t n_params = 0, n_res_total = 0, n_pts_total = 0, n_if_pts = 0;
+  int n_out_total = 0, n_eq = 1, d4_nv = 0;
+  // device problem
+  DevBuf<float> params, m, v, grads, res_f, tgt, d4, partials, scratch, loss_ring;
+  DevBuf<float2> pts;
+  DevBuf<SubDev> subs_d;
+  DevBuf<IfaceDev> ifaces_d;
+  DevBuf<double> loss_part;
+  DevBuf<Item> items_d;
+  DevBuf<int> q_items_d, q_item_begin_d, counters, state_i, err_d;
+  DevBuf<int64_t> q_part_off_d;
+  DevBuf<int2> red_blocks_d;
+  // eval
+  DevBuf<float2> e_pts, e_epts;
+  DevBuf<float> e_out, e_escale, e_eout;
+  DevBuf<int> e_S, e_memb, e_pos, e_counts;
+  DevBuf<Item> e_items;
+  // plan
+  Plan plan;
+  StepArgs base{};
+  size_t smem = 0;
+  int n_sm = 0, grid = 0;
+  int ring_cap = 256;
+  int host_t = 0, host_slot = 0;
+  xpinn_options opt{0, 1, 4, 2};
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int n_counters = 0;
+  int p_cap = 256;
+  DevBuf<int> e_counter;
+
+  ~xpinn_ctx() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
+
+  int* step_t() { return state_i.p; }
+  int* loss_slot() { return state_i.p + 1; }
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Validation and packing
+// ---------------------------------------------------------------------------
+void validate_net(const xpinn_net_desc& n, int pde, int net_idx, int q) {
+  if (n.n_layers < 2 || n.n_layers > XPINN_MAX_LAYERS)
+    fail(n.n_layers < 2 ? XPINN_ERR_INVALID : XPINN_ERR_UNSUPPORTED,
+         "subdomain %d net %d: n_layers %d outside [2, %d]", q, net_idx, n.n_layers, XPINN_MAX_LAYERS);
+  if (n.widths[0] != 2) fail(XPINN_ERR_INVALID, "subdomain %d net %d: widths[0] must be 2", q, net_idx);
+  for (int k = 1; k < n.n_layers; ++k)
+    if (n.widths[k] < 1 || n.widths[k] > XPINN_MAX_WIDTH)
+      fail(n.widths[k] < 1 ? XPINN_ERR_INVALID : XPINN_ERR_UNSUPPORTED,
+           "subdomain %d net %d: hidden width %d outside [1, %d]", q, net_idx, n.widths[k], XPINN_MAX_WIDTH);
+  const int D = n.widths[n.n_layers];
+  int want = 1;
+  if (pde == XPINN_PDE_NS) want = 3;
+  if (D != want) fail(XPINN_ERR_INVALID, "subdomain %d net %d: %d outputs, this PDE needs %d", q, net_idx, D, want);
+  if (n.out_act != XPINN_ACT_IDENTITY && n.out_act != XPINN_ACT_SOFTPLUS)
+    fail(XPINN_ERR_INVALID, "subdomain %d net %d: bad out_act %d", q, net_idx, n.out_act);
+}
+
+int64_t net_params(const xpinn_net_desc& n) {
+  int64_t t = 0;
+  for (int k = 1; k <= n.n_layers; ++k) t += (int64_t)n.widths[k] * n.widths[k - 1] + n.widths[k];
+  return t;
+}
+
+double net_macs(const NetDev& n) {
+  double t = 0;
+  for (int k = 1; k <= n.L; ++k) t += (double)n.wp[k] * n.wp[k - 1];
+  return t;
+}
+
+void check_finite(const float* a, int64_t n, const char* what) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) fail(XPINN_ERR_INVALID, "%s[%lld] is not finite", what, (long long)i);
+}
+
+// ---------------------------------------------------------------------------
+// Planning
+// ---------------------------------------------------------------------------
+struct Limits {
+  int szA = 4, szW = 4, szU = 4, pmax = 4;
+  int64_t scratch = 4;
+};
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+int max_hidden_wp(const NetDev& n) {
+  int w = MT;
+  for (int k = 1; k < n.L; ++k) w = std::max(w, n.wp[k]);
+  return w;
+}
+
+// Points per sub-tile for an item evaluating the nets with K[n] > 0.
+int choose_P(const SubDev& sd, const int K[2], int cap) {
+  int ng = 1, dk = 0;
+  for (int n = 0; n < sd.n_nets; ++n)
+    if (K[n]) {
+      ng = std::max(ng, max_hidden_wp(sd.net[n]) / MT);
+      dk += sd.net[n].w[sd.net[n].L] * K[n];
+    }
+  int P = (NT / ng) * 2;
+  P = std::min(P, 256);
+  P = std::min(P, std::max(4, 2048 / std::max(1, dk)));
+  P = std::min(P, cap);
+  return std::max(4, P / 4 * 4);
+}
+
+void item_needs(const SubDev& sd, const Item& it, Limits& l) {
+  int u = 0;
+  int64_t sc = 0;
+  for (int n = 0; n < sd.n_nets; ++n) {
+    const int K = it.K[n];
+    if (!K) continue;
+    const NetDev& nd = sd.net[n];
+    int rows = 0;
+    for (int k = 1; k < nd.L; ++k) {
+      rows += nd.wp[k];
+      l.szA = std::max(l.szA, nd.wp[k] * K * it.P);
+    }
+    for (int k = 2; k < nd.L; ++k) l.szW = std::max(l.szW, nd.wp[k] * nd.wp[k - 1]);
+    u += nd.w[nd.L] * K * it.P;
+    sc += (int64_t)(rows + nd.w[nd.L]) * K * it.P;
+  }
+  l.szU = std::max(l.szU, u);
+  l.scratch = std::max(l.scratch, sc);
+  l.pmax = std::max(l.pmax, it.P);
+}
+
+size_t smem_of(const Limits& l) {
+  StepArgs a{};
+  a.szA = round_up(l.szA, 4);
+  a.szW = round_up(l.szW, 4);
+  a.szU = round_up(l.szU, 4);
+  a.pmax = round_up(l.pmax, 4);
+  return jet_step_smem_bytes(a);
+}
+
+double item_cost(const SubDev& sd, const Item& it) {
+  double c = 0;
+  for (int n = 0; n < sd.n_nets; ++n)
+    if (it.K[n]) c += it.K[n] * net_macs(sd.net[n]) * (it.kind == IT_IFACE_FWD || it.kind == IT_EVAL ? 1 : 3);
+  return c * it.n_pts + 2e4;
+}
+
+// Build items for the training step.  `schedule` 0 orders them by cost
+// (largest first) for the grouped launch, 1 groups them by subdomain.
+void build_plan(xpinn_ctx* h, int p_cap) {
+  Plan pl;
+  std::vector<Item> fwd, main_;
+  auto mk = [&](int kind, int q, int edge, int side, int64_t off, int n, int K0, int K1) {
+    Item it{};
+    it.kind = kind;
+    it.q = q;
+    it.edge = edge;
+    it.side = side;
+    it.pt_off = off;
+    it.n_pts = n;
+    it.K[0] = K0;
+    it.K[1] = K1;
+    it.P = choose_P(h->subs[q], it.K, p_cap);
+    it.part_off = -1;
+    return it;
+  };
+  // first pass: one item per point set, to estimate the total cost
+  double total = 0;
+  for (int q = 0; q < h->n_sub; ++q) {
+    const SubDev& sd = h->subs[q];
+    if (sd.n_res) {
+      Item it = mk(IT_RES, q, -1, 0, sd.res_off, sd.n_res, k_res(h->pde, 0), sd.n_nets > 1 ? k_res(h->pde, 1) : 0);
+      total += item_cost(sd, it);
+    }
+  }
+  const double target = std::max(1.0, total / (double)(h->grid * std::max(1, h->opt.items_per_cta)));
+  auto split = [&](Item proto, std::vector<Item>& out) {
+    const SubDev& sd = h->subs[proto.q];
+    const double c = item_cost(sd, proto);
+    int chunks = std::max(1, (int)std::lround(c / target));
+    int per = (proto.n_pts + chunks - 1) / chunks;
+    per = std::max(proto.P, (per + proto.P - 1) / proto.P * proto.P);
+    for (int s = 0; s < proto.n_pts; s += per) {
+      Item it = proto;
+      it.pt_off = proto.pt_off + s;
+      it.n_pts = std::min(per, proto.n_pts - s);
+      out.push_back(it);
+    }
+  };
+  for (int q = 0; q < h->n_sub; ++q) {
+    const SubDev& sd = h->subs[q];
+    const int K1 = sd.n_nets > 1 ? k_res(h->pde, 1) : 0;
+    if (sd.n_res) split(mk(IT_RES, q, -1, 0, sd.res_off, sd.n_res, k_res(h->pde, 0), K1), main_);
+    for (int n = 0; n < sd.n_nets; ++n)
+      if (sd.n_data[n])
+        split(mk(n == 0 ? IT_DATA0 : IT_DATA1, q, -1, 0, sd.data_off[n], sd.n_data[n], n == 0 ? 1 : 0,
+                 n == 1 ? 1 : 0),
+              main_);
+  }
+  for (int e = 0; e < h->n_iface; ++e) {
+    const IfaceDev& f = h->ifaces[e];
+    if (!f.n_pts) continue;
+    for (int side = 0; side < 2; ++side) {
+      const int q = side ? f.qp : f.q;
+      const int K0 = k_iface(h->pde, f.method, 0);
+      const int K1 = h->subs[q].n_nets > 1 ? k_iface(h->pde, f.method, 1) : 0;
+      split(mk(IT_IFACE_FWD, q, e, side, f.pt_off, f.n_pts, K0, K1), fwd);
+      split(mk(IT_IFACE, q, e, side, f.pt_off, f.n_pts, K0, K1), main_);
+    }
+  }
+  auto order = [&](std::vector<Item>& v) {
+    if (h->opt.schedule == 0) {
+      std::stable_sort(v.begin(), v.end(), [&](const Item& a, const Item& b) {
+        return item_cost(h->subs[a.q], a) > item_cost(h->subs[b.q], b);
+      });
+    } else {
+      std::stable_sort(v.begin(), v.end(), [&](const Item& a, const Item& b) {
+        if (a.q != b.q) return a.q < b.q;
+        return item_cost(h->subs[a.q], a) > item_cost(h->subs[b.q], b);
+      });
+    }
+  };
+  order(fwd);
+  order(main_);
+  pl.n_fwd = (int)fwd.size();
+  pl.items = fwd;
+  pl.items.insert(pl.items.end(), main_.begin(), main_.end());
+  // gradient slices and per-subdomain item lists (in item order: deterministic)
+  std::vector<std::vector<int>> per_q(h->n_sub);
+  for (size_t i = pl.n_fwd; i < pl.items.size(); ++i) {
+    Item& it = pl.items[i];
+    it.part_off = pl.partial_floats;
+    pl.partial_floats += h->subs[it.q].n_params;
+    per_q[it.q].push_back((int)i);
+  }
+  pl.q_item_begin.push_back(0);
+  for (int q = 0; q < h->n_sub; ++q) {
+    for (int i : per_q[q]) {
+      pl.q_items.push_back(i);
+      pl.q_part_off.push_back(pl.items[i].part_off);
+    }
+    pl.q_item_begin.push_back((int)pl.q_items.size());
+    for (int e0 = 0; e0 < h->subs[q].n_params; e0 += 256) pl.red_blocks.push_back(make_int2(q, e0));
+  }
+  // per-subdomain ranges for the loop schedule
+  pl.fwd_begin.assign(h->n_sub + 1, 0);
+  pl.main_begin.assign(h->n_sub + 1, 0);
+  if (h->opt.schedule == 1) {
+    for (int i = 0; i < pl.n_fwd; ++i) pl.fwd_begin[pl.items[i].q + 1]++;
+    for (size_t i = pl.n_fwd; i < pl.items.size(); ++i) pl.main_begin[pl.items[i].q + 1]++;
+    for (int q = 0; q < h->n_sub; ++q) {
+      pl.fwd_begin[q + 1] += pl.fwd_begin[q];
+      pl.main_begin[q + 1] += pl.main_begin[q];
+    }
+  }
+  h->plan = std::move(pl);
+}
+
+// Shared memory and scratch needs of the plan's items and of evaluation
+// items (every network, order 2) under the same sub-tile cap.
+Limits limits_of(xpinn_ctx* h, int cap) {
+  Limits l;
+  for (const Item& it : h->plan.items) item_needs(h->subs[it.q], it, l);
+  for (int q = 0; q < h->n_sub; ++q) {
+    const SubDev& sd = h->subs[q];
+    for (int net = -1; net < sd.n_nets; ++net) {
+      Item it{};
+      it.kind = IT_EVAL;
+      it.q = q;
+      it.K[0] = (net <= 0) ? 5 : 0;
+      it.K[1] = (net == 1 || (net < 0 && sd.n_nets > 1)) ? 5 : 0;
+      it.P = choose_P(sd, it.K, cap);
+      item_needs(sd, it, l);
+    }
+  }
+  return l;
+}
+
+void size_and_upload_plan(xpinn_ctx* h) {
+  const Plan& pl = h->plan;
+  const Limits l = limits_of(h, h->p_cap);
+  StepArgs& a = h->base;
+  a.szA = round_up(l.szA, 4);
+  a.szW = round_up(l.szW, 4);
+  a.szU = round_up(l.szU, 4);
+  a.pmax = round_up(l.pmax, 4);
+  a.scratch_per_cta = round_up((int)std::min<int64_t>(l.scratch, 1 << 30), 4);
+  h->smem = jet_step_smem_bytes(a);
+  h->items_d.upload(pl.items.data(), pl.items.size());
+  h->q_items_d.upload(pl.q_items.data(), pl.q_items.size());
+  h->q_item_begin_d.upload(pl.q_item_begin.data(), pl.q_item_begin.size());
+  h->q_part_off_d.upload(pl.q_part_off.data(), pl.q_part_off.size());
+  h->red_blocks_d.upload(pl.red_blocks.data(), pl.red_blocks.size());
+  h->partials.alloc((size_t)pl.partial_floats);
+  h->loss_part.alloc(2 * pl.items.size());
+  h->scratch.alloc((size_t)h->grid * a.scratch_per_cta);
+  h->n_counters = 2 + 2 * h->n_sub;
+  h->counters.alloc(h->n_counters);
+  ck(cudaMemset(h->counters.p, 0, sizeof(int) * h->n_counters), "memset");
+  ck(jet_step_configure(h->smem), "cudaFuncSetAttribute(smem)");
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+}
+
+void plan(xpinn_ctx* h) {
+  int optin = 0;
+  ck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0), "attr");
+  int cap = 256;
+  for (;;) {
+    build_plan(h, cap);
+    if (smem_of(limits_of(h, cap)) + 1024 <= (size_t)optin || cap <= 8) break;
+    cap -= 8;
+  }
+  h->p_cap = cap;
+  size_and_upload_plan(h);
+  if (h->smem + 1024 > (size_t)optin)
+    fail(XPINN_ERR_UNSUPPORTED, "networks too wide for shared memory (%zu bytes)", h->smem);
+}
+
+// ---------------------------------------------------------------------------
+// Step launches
+// ---------------------------------------------------------------------------
+StepArgs args_for(xpinn_ctx* h, int begin, int count, int counter_idx) {
+  StepArgs a = h->base;
+  a.items = h->items_d.p + begin;
+  a.n_items = count;
+  a.item_base = begin;
+  a.counter = h->counters.p + counter_idx;
+  return a;
+}
+
+void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads) {
+  const Plan& pl = h->plan;
+  launch_step_begin(h->counters.p, h->n_counters, h->step_t(), h->loss_slot(), adam ? 1 : 0, s);
+  const int n_main = (int)pl.items.size() - pl.n_fwd;
+  ReduceArgs r{};
+  r.blocks = h->red_blocks_d.p;
+  r.n_blocks = (int)pl.red_blocks.size();
+  r.subs = h->subs_d.p;
+  r.q_items = h->q_items_d.p;
+  r.q_item_begin = h->q_item_begin_d.p;
+  r.q_part_off = h->q_part_off_d.p;
+  r.items = h->items_d.p;
+  r.partials = h->partials.p;
+  r.loss_part = h->loss_part.p;
+  r.params = h->params.p;
+  r.m = h->m.p;
+  r.v = h->v.p;
+  r.grads = grads;
+  r.loss_ring = h->loss_ring.p;
+  r.ring_cap = h->ring_cap;
+  r.loss_slot = h->loss_slot();
+  r.step_t = h->step_t();
+  r.do_adam = adam ? 1 : 0;
+  r.beta1 = h->beta1;
+  r.beta2 = h->beta2;
+  r.eps = h->eps;
+  r.n_sub = h->n_sub;
+  if (h->opt.schedule == 0) {
+    if (pl.n_fwd) launch_jet_step(args_for(h, 0, pl.n_fwd, 0), std::min(h->grid, pl.n_fwd), h->smem, s);
+    if (n_main) launch_jet_step(args_for(h, pl.n_fwd, n_main, 1), std::min(h->grid, n_main), h->smem, s);
+    launch_reduce_adam(r, s);
+  } else {
+    for (int q = 0; q < h->n_sub; ++q) {
+      const int b = pl.fwd_begin[q], c = pl.fwd_begin[q + 1] - b;
+      if (c) launch_jet_step(args_for(h, b, c, 2 + q), std::min(h->grid, c), h->smem, s);
+    }
+    for (int q = 0; q < h->n_sub; ++q) {
+      const int b = pl.n_fwd + pl.main_begin[q], c = pl.main_begin[q + 1] - pl.main_begin[q];
+      if (c) launch_jet_step(args_for(h, b, c, 2 + h->n_sub + q), std::min(h->grid, c), h->smem, s);
+    }
+    // one reduce/Adam launch per subdomain
+    int bi = 0;
+    for (int q = 0; q < h->n_sub; ++q) {
+      int nb = 0;
+      while (bi + nb < (int)pl.red_blocks.size() && pl.red_blocks[bi + nb].x == q) ++nb;
+      ReduceArgs rq = r;
+      rq.blocks = h->red_blocks_d.p + bi;
+      rq.n_blocks = nb;
+      launch_reduce_adam(rq, s);
+      bi += nb;
+    }
+  }
+  ck(cudaGetLastError(), "kernel launch");
+}
+
+void copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (!bytes) return;
+  if (is_device_ptr(dst)) {
+    ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s), "copy out");
+  } else {
+    ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s), "copy out");
+    ck(cudaStreamSynchronize(s), "sync");
+  }
+}
+
+void copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (!bytes) return;
+  if (is_device_ptr(src)) {
+    ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s), "copy in");
+  } else {
+    ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s), "copy in");
+    ck(cudaStreamSynchronize(s), "sync");
+  }
+}
+
+void check_device_error(xpinn_ctx* h, cudaStream_t s) {
+  int e = 0;
+  ck(cudaMemcpyAsync(&e, h->err_d.p, sizeof(int), cudaMemcpyDeviceToHost, s), "read error flag");
+  ck(cudaStreamSynchronize(s), "sync");
+  if (e) {
+    ck(cudaMemsetAsync(h->err_d.p, 0, sizeof(int), s), "reset error flag");
+    fail(XPINN_ERR_INVALID, "device check failed (code %d)", e);
+  }
+}
+
+// Jets of items over an evaluation buffer of points (already on the device).
+void run_eval_items(xpinn_ctx* h, std::vector<Item>& items, const float2* pts, float* out, int dout,
+                    const float* scale, cudaStream_t s) {
+  if (items.empty()) return;
+  h->e_items.ensure(items.size());
+  ck(cudaMemcpyAsync(h->e_items.p, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice, s),
+     "items");
+  StepArgs a = h->base;
+  a.items = h->e_items.p;
+  a.n_items = (int)items.size();
+  a.item_base = 0;
+  h->e_counter.ensure(1);
+  a.counter = h->e_counter.p;
+  a.eval_pts = pts;
+  a.eval_out = out;
+  a.eval_dout = dout;
+  a.eval_scale = scale;
+  ck(cudaMemsetAsync(a.counter, 0, sizeof(int), s), "memset");
+  launch_jet_step(a, std::min<int>(h->grid, (int)items.size()), h->smem, s);
+  ck(cudaGetLastError(), "eval launch");
+  // keep the host copy alive until the copy has been consumed
+  ck(cudaStreamSynchronize(s), "sync");
+}
+
+void eval_items_for(xpinn_ctx* h, int q, int net, int K, int64_t first, int64_t n, int64_t out_off,
+                    int dout, std::vector<Item>& items) {
+  const SubDev& sd = h->subs[q];
+  Item proto{};
+  proto.kind = IT_EVAL;
+  proto.q = q;
+  proto.K[0] = (net == 0 || net < 0) ? K : 0;
+  proto.K[1] = (net == 1 || (net < 0 && sd.n_nets > 1)) ? K : 0;
+  proto.P = choose_P(sd, proto.K, h->p_cap);
+  proto.part_off = -1;
+  const int64_t per = (int64_t)proto.P * 16;
+  for (int64_t s = 0; s < n; s += per) {
+    Item it = proto;
+    it.pt_off = first + s;
+    it.n_pts = (int)std::min<int64_t>(per, n - s);
+    it.out_off = out_off + s * dout;
+    items.push_back(it);
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+#define API_BEGIN try {
+#define API_END                                  \
+  }                                              \
+  catch (const Error& e) {                       \
+    return e.code;                               \
+  }                                              \
+  catch (const std::bad_alloc&) {                \
+    g_err = "host allocation failed";            \
+    return XPINN_ERR_OOM;                        \
+  }                                              \
+  catch (...) {                                  \
+    g_err = "unexpected host exception";         \
+    return XPINN_ERR_INVALID;                    \
+  }                                              \
+  g_err.clear();                                 \
+  return XPINN_OK;
+
+extern "C" {
+
+const char* xpinn_last_error(void) { return g_err.c_str(); }
+
+int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
+  API_BEGIN
+  if (!d || !out) fail(XPINN_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  if (d->pde < 0 || d->pde > 3) fail(XPINN_ERR_INVALID, "unknown pde %d", d->pde);
+  if (d->n_sub < 1 || !d->subs) fail(XPINN_ERR_INVALID, "need at least one subdomain");
+  if (d->n_iface < 0 || (d->n_iface > 0 && !d->ifaces)) fail(XPINN_ERR_INVALID, "bad interface list");
+  if (!d->init_params) fail(XPINN_ERR_INVALID, "init_params is required");
+  if (d->flux_mode != XPINN_FLUX_CONSERVATIVE && d->flux_mode != XPINN_FLUX_LITERAL)
+    fail(XPINN_ERR_INVALID, "bad flux_mode");
+  if (!(d->beta1 >= 0 && d->beta1 < 1 && d->beta2 >= 0 && d->beta2 < 1 && d->eps > 0))
+    fail(XPINN_ERR_INVALID, "bad Adam constants");
+  if (d->pde == XPINN_PDE_NS && !(d->re > 0)) fail(XPINN_ERR_INVALID, "Reynolds number must be > 0");
+  const int spm = d->subs_per_model ? d->subs_per_model : d->n_sub;
+  if (spm < 1 || d->n_sub % spm) fail(XPINN_ERR_INVALID, "subs_per_model must divide n_sub");
+  auto h = std::make_unique<xpinn_ctx>();
+  h->pde = d->pde;
+  h->nu = d->nu;
+  h->re = d->re;
+  h->flux_mode = d->flux_mode;
+  h->beta1 = d->beta1;
+  h->beta2 = d->beta2;
+  h->eps = d->eps;
+  h->n_sub = d->n_sub;
+  h->n_iface = d->n_iface;
+  h->spm = spm;
+  h->n_eq = d->pde == XPINN_PDE_NS ? 3 : 1;
+  const int want_nets = d->pde == XPINN_PDE_DIFFUSION ? 2 : 1;
+  // ---- subdomains
+  std::vector<float2> pts_res, pts_data;
+  std::vector<float> res_f, tgt;
+  int64_t poff = 0;
+  for (int q = 0; q < d->n_sub; ++q) {
+    const xpinn_subdomain_desc& s = d->subs[q];
+    if (s.n_nets != want_nets)
+      fail(XPINN_ERR_INVALID, "subdomain %d: %d networks, this PDE needs %d", q, s.n_nets, want_nets);
+    SubDev sd{};
+    sd.n_nets = s.n_nets;
+    sd.poff = poff;
+    int off = 0;
+    for (int n = 0; n < s.n_nets; ++n) {
+      validate_net(s.nets[n], d->pde, n, q);
+      NetDev& nd = sd.net[n];
+      nd.L = s.nets[n].n_layers;
+      nd.out_act = s.nets[n].out_act;
+      for (int k = 0; k <= nd.L; ++k) {
+        nd.w[k] = s.nets[n].widths[k];
+        nd.wp[k] = round_up(nd.w[k], MT);
+      }
+      for (int k = 1; k <= nd.L; ++k) {
+        nd.off[k] = off;
+        off += nd.w[k] * nd.w[k - 1] + nd.w[k];
+      }
+    }
+    sd.n_params = off;
+    poff += off;
+    if (s.n_res < 0 || (s.n_res > 0 && !s.res_xy)) fail(XPINN_ERR_INVALID, "subdomain %d: bad residual points", q);
+    if (s.n_res > (1 << 30)) fail(XPINN_ERR_UNSUPPORTED, "subdomain %d: too many residual points", q);
+    sd.res_off = (int64_t)pts_res.size();
+    sd.n_res = (int)s.n_res;
+    sd.inv_n_res = s.n_res ? 1.f / (float)s.n_res : 0.f;
+    check_finite(s.res_xy, 2 * s.n_res, "res_xy");
+    for (int64_t i = 0; i < s.n_res; ++i) {
+      pts_res.push_back(make_float2(s.res_xy[2 * i], s.res_xy[2 * i + 1]));
+      res_f.push_back(s.res_f ? s.res_f[i] : 0.f);
+    }
+    if (s.res_f) check_finite(s.res_f, s.n_res, "res_f");
+    for (int n = 0; n < s.n_nets; ++n) {
+      const int D = sd.net[n].w[sd.net[n].L];
+      if (s.n_data[n] < 0 || (s.n_data[n] > 0 && (!s.data_xy[n] || !s.data_val[n])))
+        fail(XPINN_ERR_INVALID, "subdomain %d: bad data set %d", q, n);
+      check_finite(s.data_xy[n], 2 * s.n_data[n], "data_xy");
+      check_finite(s.data_val[n], D * s.n_data[n], "data_val");
+      sd.data_off[n] = (int64_t)pts_data.size();   // rebased below
+      sd.tgt_off[n] = (int64_t)tgt.size();
+      sd.n_data[n] = (int)s.n_data[n];
+      sd.inv_n_data[n] = s.n_data[n] ? 1.f / (float)s.n_data[n] : 0.f;
+      sd.w_data[n] = s.w_data[n];
+      for (int64_t i = 0; i < s.n_data[n]; ++i) {
+        pts_data.push_back(make_float2(s.data_xy[n][2 * i], s.data_xy[n][2 * i + 1]));
+        for (int o = 0; o < D; ++o) tgt.push_back(s.data_val[n][i * D + o]);
+      }
+    }
+    sd.w_res = s.w_res;
+    sd.w_avg = s.w_avg;
+    sd.w_iface = s.w_iface;
+    sd.lr = s.lr;
+    if (!std::isfinite(s.lr) || !std::isfinite(s.w_res) || !std::isfinite(s.w_avg) || !std::isfinite(s.w_iface))
+      fail(XPINN_ERR_INVALID, "subdomain %d: non-finite weight or learning rate", q);
+    for (int i = 0; i < 4; ++i) sd.rect[i] = s.rect[i];
+    h->subs.push_back(sd);
+  }
+  h->n_params = poff;
+  h->n_res_total = (int64_t)pts_res.size();
+  h->n_out_total = 0;
+  for (int n = 0; n < h->subs[0].n_nets; ++n) h->n_out_total += h->subs[0].net[n].w[h->subs[0].net[n].L];
+  h->d4_nv = h->n_out_total + h->n_eq;
+  for (auto& sd : h->subs)
+    for (int n = 0; n < sd.n_nets; ++n) sd.data_off[n] += h->n_res_total;
+  // ---- interfaces
+  std::vector<float2> pts_if;
+  for (int e = 0; e < d->n_iface; ++e) {
+    const xpinn_interface_desc& f = d->ifaces[e];
+    if (f.q < 0 || f.q >= d->n_sub || f.q_plus < 0 || f.q_plus >= d->n_sub || f.q == f.q_plus)
+      fail(XPINN_ERR_INVALID, "interface %d: bad subdomains (%d, %d)", e, f.q, f.q_plus);
+    if (f.method != XPINN_CPINN && f.method != XPINN_XPINN) fail(XPINN_ERR_INVALID, "interface %d: bad method", e);
+    if (f.n_pts < 0 || (f.n_pts > 0 && !f.xy)) fail(XPINN_ERR_INVALID, "interface %d: bad points", e);
+    check_finite(f.xy, 2 * f.n_pts, "iface xy");
+    IfaceDev fd{};
+    fd.q = f.q;
+    fd.qp = f.q_plus;
+    fd.method = f.method;
+    fd.n_pts = (int)f.n_pts;
+    fd.nx = f.normal[0];
+    fd.ny = f.normal[1];
+    fd.inv_n = f.n_pts ? 1.f / (float)f.n_pts : 0.f;
+    fd.d4_pt = (int64_t)pts_if.size();
+    for (int64_t i = 0; i < f.n_pts; ++i) pts_if.push_back(make_float2(f.xy[2 * i], f.xy[2 * i + 1]));
+    h->ifaces.push_back(fd);
+  }
+  h->n_if_pts = (int64_t)pts_if.size();
+  const int64_t if_base = h->n_res_total + (int64_t)pts_data.size();
+  for (auto& f : h->ifaces) f.pt_off = if_base + f.d4_pt;
+  check_finite(d->init_params, h->n_params, "init_params");
+  // ---- device
+  ck(cudaFree(0), "CUDA init");
+  ck(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, 0), "attr");
+  h->grid = h->n_sm;
+  std::vector<float2> all = pts_res;
+  all.insert(all.end(), pts_data.begin(), pts_data.end());
+  all.insert(all.end(), pts_if.begin(), pts_if.end());
+  h->n_pts_total = (int64_t)all.size();
+  h->pts.upload(all.data(), all.size());
+  h->res_f.upload(res_f.data(), res_f.size());
+  h->tgt.upload(tgt.data(), tgt.size());
+  h->params.upload(d->init_params, (size_t)h->n_params);
+  h->m.alloc((size_t)h->n_params);
+  h->v.alloc((size_t)h->n_params);
+  h->grads.alloc((size_t)h->n_params);
+  ck(cudaMemset(h->m.p, 0, h->n_params * sizeof(float)), "memset");
+  ck(cudaMemset(h->v.p, 0, h->n_params * sizeof(float)), "memset");
+  h->subs_d.upload(h->subs.data(), h->subs.size());
+  h->ifaces_d.upload(h->ifaces.data(), h->ifaces.size());
+  h->d4.alloc((size_t)std::max<int64_t>(1, h->n_if_pts * 2 * h->d4_nv));
+  ck(cudaMemset(h->d4.p, 0, h->d4.n * sizeof(float)), "memset");
+  h->state_i.alloc(2);
+  ck(cudaMemset(h->state_i.p, 0, 2 * sizeof(int)), "memset");
+  h->err_d.alloc(1);
+  ck(cudaMemset(h->err_d.p, 0, sizeof(int)), "memset");
+  h->loss_ring.alloc((size_t)h->ring_cap * h->n_sub * XPINN_N_TERMS);
+  StepArgs& a = h->base;
+  a.subs = h->subs_d.p;
+  a.ifaces = h->ifaces_d.p;
+  a.params = h->params.p;
+  a.pts = h->pts.p;
+  a.res_f = h->res_f.p;
+  a.tgt = h->tgt.p;
+  a.d4 = h->d4.p;
+  a.d4_nv = h->d4_nv;
+  a.pde = h->pde;
+  a.nu = h->nu;
+  a.re = h->re;
+  a.flux_mode = h->flux_mode;
+  a.n_out_total = h->n_out_total;
+  a.n_eq = h->n_eq;
+  a.err = h->err_d.p;
+  plan(h.get());
+  a.partials = h->partials.p;
+  a.loss_part = h->loss_part.p;
+  a.scratch = h->scratch.p;
+  ck(cudaDeviceSynchronize(), "create");
+  *out = h.release();
+  API_END
+}
+
+int xpinn_destroy(xpinn_handle h) {
+  API_BEGIN
+  if (h) {
+    cudaDeviceSynchronize();
+    delete h;
+  }
+  API_END
+}
+
+int64_t xpinn_num_params(xpinn_handle h) { return h ? h->n_params : -1; }
+
+int xpinn_get_params(xpinn_handle h, float* dst, int64_t n, void* stream) {
+  API_BEGIN
+  if (!h || !dst || n != h->n_params) fail(XPINN_ERR_INVALID, "bad arguments");
+  copy_out(dst, h->params.p, n * sizeof(float), (cudaStream_t)stream);
+  API_END
+}
+
+int xpinn_set_params(xpinn_handle h, const float* src, int64_t n, void* stream) {
+  API_BEGIN
+  if (!h || !src || n != h->n_params) fail(XPINN_ERR_INVALID, "bad arguments");
+  copy_in(h->params.p, src, n * sizeof(float), (cudaStream_t)stream);
+  API_END
+}
+
+int xpinn_grad(xpinn_handle h, float* losses, float* grads, void* stream) {
+  API_BEGIN
+  if (!h) fail(XPINN_ERR_INVALID, "NULL handle");
+  cudaStream_t s = (cudaStream_t)stream;
+  enqueue_step(h, s, false, h->grads.p);
+  h->host_slot += 1;
+  const int slot = h->host_slot % h->ring_cap;
+  if (losses)
+    copy_out(losses, h->loss_ring.p + (size_t)slot * h->n_sub * XPINN_N_TERMS,
+             sizeof(float) * h->n_sub * XPINN_N_TERMS, s);
+  if (grads) copy_out(grads, h->grads.p, sizeof(float) * h->n_params, s);
+  API_END
+}
+
+int xpinn_step(xpinn_handle h, int32_t n_steps, float* losses, void* stream) {
+  API_BEGIN
+  if (!h || n_steps < 0) fail(XPINN_ERR_INVALID, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t row = (size_t)h->n_sub * XPINN_N_TERMS;
+  const bool dev_out = losses && is_device_ptr(losses);
+  std::vector<float> host_rows;
+  int done = 0;
+  while (done < n_steps) {
+    const int chunk = std::min(n_steps - done, h->ring_cap);
+    const int first_slot = h->host_slot + 1;
+    for (int i = 0; i < chunk; ++i) {
+      if (h->opt.use_graph) {
+        if (!h->graph) {
+          if (!h->cap_stream) ck(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "stream");
+          cudaGraph_t g;
+          ck(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+          try {
+            enqueue_step(h, h->cap_stream, true, nullptr);
+          } catch (...) {
+            cudaStreamEndCapture(h->cap_stream, &g);
+            throw;
+          }
+          ck(cudaStreamEndCapture(h->cap_stream, &g), "end capture");
+          ck(cudaGraphInstantiate(&h->graph, g, 0), "instantiate");
+          cudaGraphDestroy(g);
+        }
+        ck(cudaGraphLaunch(h->graph, s), "graph launch");
+      } else {
+        enqueue_step(h, s, true, nullptr);
+      }
+      h->host_slot += 1;
+      h->host_t += 1;
+    }
+    if (losses) {
+      for (int i = 0; i < chunk; ++i) {
+        const int slot = (first_slot + i) % h->ring_cap;
+        float* dst = losses + (size_t)(done + i) * row;
+        if (dev_out)
+          ck(cudaMemcpyAsync(dst, h->loss_ring.p + slot * row, row * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy");
+        else
+          ck(cudaMemcpyAsync(dst, h->loss_ring.p + slot * row, row * sizeof(float), cudaMemcpyDeviceToHost, s), "copy");
+      }
+      if (!dev_out) ck(cudaStreamSynchronize(s), "sync");
+    }
+    done += chunk;
+  }
+  ck(cudaGetLastError(), "step");
+  if (losses && !dev_out) {
+    for (size_t i = 0; i < (size_t)n_steps * row; ++i)
+      if (!std::isfinite(losses[i])) fail(XPINN_ERR_NONFINITE, "loss became non-finite");
+  }
+  API_END
+}
+
+int xpinn_net_jets(xpinn_handle h, int32_t q, int32_t net, const float* xy, int64_t n, int32_t order,
+                   float* out, void* stream) {
+  API_BEGIN
+  if (!h || q < 0 || q >= h->n_sub || net < 0 || net >= h->subs[q].n_nets || order < 0 || order > 2 ||
+      n < 0 || (n > 0 && (!xy || !out)))
+    fail(XPINN_ERR_INVALID, "bad arguments");
+  if (n == 0) { g_err.clear(); return XPINN_OK; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = order == 0 ? 1 : (order == 1 ? 3 : 5);
+  const NetDev& nd = h->subs[q].net[net];
+  const int dout = nd.w[nd.L] * K;
+  const bool dev = is_device_ptr(xy);
+  const float2* pts;
+  if (dev) {
+    pts = reinterpret_cast<const float2*>(xy);
+  } else {
+    h->e_pts.ensure(n);
+    copy_in(h->e_pts.p, xy, n * sizeof(float2), s);
+    pts = h->e_pts.p;
+  }
+  float* o = out;
+  if (!is_device_ptr(out)) {
+    h->e_out.ensure((size_t)n * dout);
+    o = h->e_out.p;
+  }
+  std::vector<Item> items;
+  eval_items_for(h, q, net, K, 0, n, 0, dout, items);
+  run_eval_items(h, items, pts, o, dout, nullptr, s);
+  if (o != out) copy_out(out, o, sizeof(float) * n * dout, s);
+  API_END
+}
+
+int xpinn_eval(xpinn_handle h, int32_t model, const float* xy, int64_t n, int32_t order, float* out,
+               void* stream) {
+  API_BEGIN
+  if (!h || model < 0 || model >= h->n_sub / h->spm || order < 0 || order > 2 || n < 0 ||
+      (n > 0 && (!xy || !out)))
+    fail(XPINN_ERR_INVALID, "bad arguments");
+  if (n == 0) { g_err.clear(); return XPINN_OK; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = order == 0 ? 1 : (order == 1 ? 3 : 5);
+  const int row = h->n_out_total * K;
+  const int q0 = model * h->spm, nq = h->spm;
+  const float2* pts;
+  if (is_device_ptr(xy)) {
+    pts = reinterpret_cast<const float2*>(xy);
+  } else {
+    h->e_pts.ensure(n);
+    copy_in(h->e_pts.p, xy, n * sizeof(float2), s);
+    pts = h->e_pts.p;
+  }
+  h->e_S.ensure(n);
+  h->e_memb.ensure(n * 4);
+  h->e_pos.ensure(n * 4);
+  h->e_counts.ensure(2 * nq);
+  ck(cudaMemsetAsync(h->e_counts.p, 0, sizeof(int) * 2 * nq, s), "memset");
+  launch_route(pts, n, h->subs_d.p, q0, nq, h->e_S.p, h->e_memb.p, h->e_counts.p, h->err_d.p, s);
+  std::vector<int> counts(nq);
+  ck(cudaMemcpyAsync(counts.data(), h->e_counts.p, sizeof(int) * nq, cudaMemcpyDeviceToHost, s), "counts");
+  ck(cudaStreamSynchronize(s), "sync");
+  check_device_error(h, s);
+  std::vector<int> start(nq + 1, 0);
+  for (int l = 0; l < nq; ++l) start[l + 1] = start[l] + counts[l];
+  const int64_t n_ent = start[nq];
+  ck(cudaMemcpyAsync(h->e_counts.p + nq, start.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, s), "cursor");
+  h->e_epts.ensure(std::max<int64_t>(1, n_ent));
+  h->e_escale.ensure(std::max<int64_t>(1, n_ent));
+  h->e_eout.ensure(std::max<int64_t>(1, n_ent * row));
+  launch_bucket(pts, n, h->e_S.p, h->e_memb.p, h->e_counts.p + nq, h->e_pos.p, h->e_epts.p, h->e_escale.p, s);
+  std::vector<Item> items;
+  for (int l = 0; l < nq; ++l)
+    if (counts[l]) eval_items_for(h, q0 + l, -1, K, start[l], counts[l], (int64_t)start[l] * row, row, items);
+  run_eval_items(h, items, h->e_epts.p, h->e_eout.p, row, h->e_escale.p, s);
+  float* o = out;
+  if (!is_device_ptr(out)) {
+    h->e_out.ensure((size_t)n * row);
+    o = h->e_out.p;
+  }
+  launch_gather(n, row, h->e_S.p, h->e_pos.p, h->e_eout.p, o, s);
+  ck(cudaGetLastError(), "gather");
+  if (o != out) copy_out(out, o, sizeof(float) * n * row, s);
+  API_END
+}
+
+int xpinn_set_residual_points(xpinn_handle h, const float* xy, const float* f, int64_t n, void* stream) {
+  API_BEGIN
+  if (!h || !xy || n != h->n_res_total) fail(XPINN_ERR_INVALID, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  copy_in(h->pts.p, xy, n * sizeof(float2), s);
+  if (f)
+    copy_in(h->res_f.p, f, n * sizeof(float), s);
+  else
+    ck(cudaMemsetAsync(h->res_f.p, 0, n * sizeof(float), s), "memset");
+  API_END
+}
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t version;
+  int32_t step_t;
+  int64_t n_params;
+  int64_t n_sub;
+};
+}  // namespace
+
+int xpinn_get_state(xpinn_handle h, void* blob, size_t* n) {
+  API_BEGIN
+  if (!h || !n) fail(XPINN_ERR_INVALID, "bad arguments");
+  const size_t need = sizeof(StateHeader) + 3 * sizeof(float) * h->n_params;
+  if (!blob) {
+    *n = need;
+    g_err.clear();
+    return XPINN_OK;
+  }
+  if (*n < need) fail(XPINN_ERR_INVALID, "state buffer too small (%zu < %zu)", *n, need);
+  StateHeader hd{};
+  memcpy(hd.magic, "XPINNST1", 8);
+  hd.version = 1;
+  int t = 0;
+  ck(cudaMemcpy(&t, h->step_t(), sizeof(int), cudaMemcpyDeviceToHost), "state");
+  hd.step_t = t;
+  hd.n_params = h->n_params;
+  hd.n_sub = h->n_sub;
+  char* b = static_cast<char*>(blob);
+  memcpy(b, &hd, sizeof hd);
+  float* p = reinterpret_cast<float*>(b + sizeof hd);
+  ck(cudaMemcpy(p, h->params.p, sizeof(float) * h->n_params, cudaMemcpyDeviceToHost), "state");
+  ck(cudaMemcpy(p + h->n_params, h->m.p, sizeof(float) * h->n_params, cudaMemcpyDeviceToHost), "state");
+  ck(cudaMemcpy(p + 2 * h->n_params, h->v.p, sizeof(float) * h->n_params, cudaMemcpyDeviceToHost), "state");
+  *n = need;
+  API_END
+}
+
+int xpinn_set_state(xpinn_handle h, const void* blob, size_t n) {
+  API_BEGIN
+  if (!h || !blob) fail(XPINN_ERR_INVALID, "bad arguments");
+  const size_t need = sizeof(StateHeader) + 3 * sizeof(float) * h->n_params;
+  StateHeader hd;
+  if (n < sizeof hd) fail(XPINN_ERR_INVALID, "state blob too small");
+  memcpy(&hd, blob, sizeof hd);
+  if (memcmp(hd.magic, "XPINNST1", 8) || hd.version != 1) fail(XPINN_ERR_INVALID, "not a state blob");
+  if (hd.n_params != h->n_params || hd.n_sub != h->n_sub || n != need)
+    fail(XPINN_ERR_INVALID, "state blob of another problem shape");
+  const float* p = reinterpret_cast<const float*>(static_cast<const char*>(blob) + sizeof hd);
+  ck(cudaDeviceSynchronize(), "sync");
+  ck(cudaMemcpy(h->params.p, p, sizeof(float) * h->n_params, cudaMemcpyHostToDevice), "state");
+  ck(cudaMemcpy(h->m.p, p + h->n_params, sizeof(float) * h->n_params, cudaMemcpyHostToDevice), "state");
+  ck(cudaMemcpy(h->v.p, p + 2 * h->n_params, sizeof(float) * h->n_params, cudaMemcpyHostToDevice), "state");
+  ck(cudaMemcpy(h->step_t(), &hd.step_t, sizeof(int), cudaMemcpyHostToDevice), "state");
+  h->host_t = hd.step_t;
+  API_END
+}
+
+int xpinn_get_options(xpinn_handle h, xpinn_options* opt) {
+  API_BEGIN
+  if (!h || !opt) fail(XPINN_ERR_INVALID, "bad arguments");
+  *opt = h->opt;
+  API_END
+}
+
+int xpinn_set_options(xpinn_handle h, const xpinn_options* opt) {
+  API_BEGIN
+  if (!h || !opt) fail(XPINN_ERR_INVALID, "bad arguments");
+  if (opt->schedule < 0 || opt->schedule > 1 || opt->items_per_cta < 1 || opt->items_per_cta > 64 ||
+      opt->points_per_thread != 2)
+    fail(XPINN_ERR_INVALID, "bad options");
+  ck(cudaDeviceSynchronize(), "sync");
+  h->opt = *opt;
+  plan(h);
+  h->base.partials = h->partials.p;
+  h->base.loss_part = h->loss_part.p;
+  h->base.scratch = h->scratch.p;
+  API_END
+}
+
+int xpinn_iface_values(xpinn_handle h, float* out, int64_t* n_floats, void* stream) {
+  API_BEGIN
+  if (!h || !n_floats) fail(XPINN_ERR_INVALID, "bad arguments");
+  const int64_t need = h->n_if_pts * 2 * h->d4_nv;
+  if (!out) {
+    *n_floats = need;
+    g_err.clear();
+    return XPINN_OK;
+  }
+  if (*n_floats < need) fail(XPINN_ERR_INVALID, "buffer too small");
+  copy_out(out, h->d4.p, sizeof(float) * need, (cudaStream_t)stream);
+  *n_floats = need;
+  API_END
+}
+
+}  // extern "C"

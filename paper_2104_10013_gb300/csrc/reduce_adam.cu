@@ -1,0 +1,85 @@
+// Deterministic gradient reduction and per-subdomain Adam (Sec. 6).
+//
+// Every work item of the jet kernel left its gradient contribution in a
+// private slice.  Here one thread per parameter sums the slices of its
+// subdomain in a fixed order (so the result is bitwise reproducible), then
+// applies one bias-corrected Adam step with the subdomain's own learning
+// rate: the subdomains are optimised independently, as in Algorithm 1.
+#include <cuda_runtime.h>
+
+#include "xpinn_dev.cuh"
+
+namespace xp {
+
+constexpr int RT = 256;
+
+// Start of a step: reset the work counters of both jet launches, advance the
+// Adam step count and the loss-ring slot.  One thread.
+__global__ void step_begin_kernel(int* counters, int n_counters, int* step_t, int* loss_slot,
+                                  int do_adam) {
+  for (int i = 0; i < n_counters; ++i) counters[i] = 0;
+  if (do_adam) *step_t += 1;
+  *loss_slot += 1;
+}
+
+void launch_step_begin(int* counters, int n_counters, int* step_t, int* loss_slot, int do_adam,
+                       cudaStream_t s) {
+  step_begin_kernel<<<1, 1, 0, s>>>(counters, n_counters, step_t, loss_slot, do_adam);
+}
+
+__global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
+  const int2 blk = a.blocks[blockIdx.x];
+  const int q = blk.x;
+  const SubDev& sd = a.subs[q];
+  const int ib = a.q_item_begin[q], ie = a.q_item_begin[q + 1];
+  __shared__ float s_bc[2];
+  if (threadIdx.x == 0 && a.do_adam) {
+    const int t = *a.step_t;
+    s_bc[0] = (float)(1.0 - pow((double)a.beta1, (double)t));
+    s_bc[1] = (float)(1.0 - pow((double)a.beta2, (double)t));
+  }
+  // loss terms of this subdomain (first block of the subdomain only)
+  if (blk.y == 0 && threadIdx.x < XPINN_N_TERMS) {
+    const int term = threadIdx.x;
+    double acc = 0.0;
+    for (int k = ib; k < ie; ++k) {
+      const Item& it = a.items[a.q_items[k]];
+      const double* lp = a.loss_part + 2 * a.q_items[k];
+      switch (it.kind) {
+        case IT_DATA0: if (term == 0) acc += lp[0]; break;
+        case IT_DATA1: if (term == 1) acc += lp[0]; break;
+        case IT_RES: if (term == 2) acc += lp[0]; break;
+        case IT_IFACE:
+          if (term == 3) acc += lp[0];
+          if (term == 4) acc += lp[1];
+          break;
+        default: break;
+      }
+    }
+    const int slot = (*a.loss_slot) % a.ring_cap;
+    a.loss_ring[((int64_t)slot * a.n_sub + q) * XPINN_N_TERMS + term] = (float)acc;
+  }
+  __syncthreads();
+  const int e = blk.y + threadIdx.x;
+  if (e >= sd.n_params) return;
+  float g = 0.f;
+  for (int k = ib; k < ie; ++k) g += a.partials[a.q_part_off[k] + e];
+  const int64_t gi = sd.poff + e;
+  if (a.grads) a.grads[gi] = g;
+  if (a.do_adam) {
+    const float b1 = a.beta1, b2 = a.beta2;
+    const float m = b1 * a.m[gi] + (1.f - b1) * g;
+    const float v = b2 * a.v[gi] + (1.f - b2) * g * g;
+    a.m[gi] = m;
+    a.v[gi] = v;
+    const float mhat = m / s_bc[0];
+    const float vhat = v / s_bc[1];
+    a.params[gi] -= sd.lr * mhat / (sqrtf(vhat) + a.eps);
+  }
+}
+
+void launch_reduce_adam(const ReduceArgs& a, cudaStream_t s) {
+  if (a.n_blocks > 0) reduce_adam_kernel<<<a.n_blocks, RT, 0, s>>>(a);
+}
+
+}  // namespace xp

@@ -1,0 +1,155 @@
+// Device-side data layout shared by the kernels and the host planner.
+//
+// The whole problem lives in a handful of flat device arrays:
+//   params / m / v / grads : the packed parameter vector (layout of xpinn.h)
+//   pts                    : every training point as float2, grouped as
+//                            [residual points of all subdomains]
+//                            [data points of all subdomains and nets]
+//                            [interface points of all interfaces]
+//   res_f                  : forcing at residual points (indexed like pts)
+//   tgt                    : data targets [point][D_out]
+//   d4                     : interface exchange buffer
+//                            [interface point][side][u..., exchanged qty...]
+// A step is a list of work items (one subdomain, one point kind, one range of
+// points).  Each item writes its gradient contribution to a private slice of
+// `partials` and its loss sums to `loss_part`; a second kernel sums the slices
+// of each subdomain in a fixed order, so results do not depend on which CTA
+// ran which item.
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "xpinn.h"
+
+namespace xp {
+
+constexpr int NT = 256;          // threads per CTA of the jet kernel
+constexpr int MT = 8;            // neurons in a thread's register tile
+constexpr int KMAX = 5;          // jet components (u, d0, d1, d00, d11)
+constexpr int MAXL = XPINN_MAX_LAYERS;
+constexpr int MAXNETS = XPINN_MAX_NETS;
+constexpr int MAXW = XPINN_MAX_WIDTH;
+
+enum ItemKind : int {
+  IT_RES = 0,        // residual points: MSE_F
+  IT_DATA0 = 1,      // data points of net 0: MSE_u
+  IT_DATA1 = 2,      // data points of net 1: MSE_u
+  IT_IFACE = 3,      // one side of an interface: MSE_uavg + MSE_flux / MSE_R
+  IT_IFACE_FWD = 4,  // one side of an interface, forward only: writes d4
+  IT_EVAL = 5,       // jets at caller points (xpinn_net_jets / xpinn_eval)
+};
+
+struct NetDev {
+  int L;                 // weight layers
+  int out_act;           // XPINN_ACT_*
+  int w[MAXL + 1];       // widths N_0..N_L
+  int wp[MAXL + 1];      // widths padded to a multiple of MT
+  int off[MAXL + 1];     // offset of W^k inside the subdomain's parameters (k >= 1);
+                         // b^k follows W^k
+};
+
+struct SubDev {
+  int n_nets;
+  int n_params;
+  int64_t poff;          // offset of the subdomain's parameters in the packed vector
+  NetDev net[MAXNETS];
+  float w_data[MAXNETS], w_res, w_avg, w_iface;
+  float inv_n_res;
+  float inv_n_data[MAXNETS];
+  int64_t res_off;       // first residual point in pts
+  int64_t data_off[MAXNETS];
+  int64_t tgt_off[MAXNETS];   // first target float in tgt
+  int n_res;
+  int n_data[MAXNETS];
+  float lr;
+  float rect[4];
+};
+
+struct IfaceDev {
+  int q, qp, method;
+  int n_pts;
+  float nx, ny;
+  float inv_n;
+  int64_t pt_off;        // first point in pts
+  int64_t d4_pt;         // first interface point index in d4
+};
+
+struct Item {
+  int kind;
+  int q;                 // subdomain
+  int edge, side;        // interface items
+  int n_pts;
+  int P;                 // points per sub-tile
+  int K[MAXNETS];        // jet components per net, 0 if the net is not evaluated
+  int64_t pt_off;        // first point (pts, or the eval point buffer)
+  int64_t part_off;      // first float of this item's gradient slice (-1: none)
+  int64_t out_off;       // eval: first output float; others unused
+};
+
+struct StepArgs {
+  const Item* items;
+  int n_items;
+  int item_base;         // index of items[0] in the plan (loss_part slots)
+  int* counter;          // work counter of this launch (reset before it)
+  const SubDev* subs;
+  const IfaceDev* ifaces;
+  const float* params;
+  const float2* pts;
+  const float* res_f;
+  const float* tgt;
+  float* d4;
+  int d4_nv;             // floats per (interface point, side)
+  float* partials;
+  double* loss_part;     // [n_items][2]
+  float* scratch;        // per-CTA scratch for saved jets
+  int64_t scratch_per_cta;
+  int pde;
+  float nu, re;
+  int flux_mode;
+  int n_out_total;       // outputs of all nets of a subdomain
+  int n_eq;              // residual components
+  // smem plan (floats)
+  int szA, szW, szU;
+  int pmax;              // largest sub-tile of any item
+  // eval
+  const float2* eval_pts;
+  float* eval_out;
+  const float* eval_scale;   // per point weight (1/S) or NULL
+  int eval_dout;             // output row stride in floats per point
+  int* err;                  // device error flag (bounds checks)
+};
+
+// Kernel entry points (defined in jet_step.cu / reduce_adam.cu / route.cu).
+void launch_jet_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
+size_t jet_step_smem_bytes(const StepArgs& a);
+cudaError_t jet_step_configure(size_t smem);
+
+struct ReduceArgs {
+  const int2* blocks;        // (subdomain, first param) of each CTA
+  int n_blocks;
+  const SubDev* subs;
+  const int* q_items;        // CSR: items contributing to each subdomain
+  const int* q_item_begin;   // [n_sub + 1]
+  const Item* items;
+  const float* partials;
+  const double* loss_part;
+  float* params;
+  float* m;
+  float* v;
+  float* grads;              // NULL: not written
+  float* loss_ring;          // [ring_cap][n_sub][5] loss rows, one slot per step
+  int ring_cap;
+  const int* loss_slot;      // device slot counter (already incremented)
+  const int64_t* q_part_off; // CSR (like q_items): gradient slice offset of each item
+  const int* step_t;         // device Adam step count (already incremented)
+  int do_adam;
+  float beta1, beta2, eps;
+  int n_sub;
+};
+
+void launch_reduce_adam(const ReduceArgs& a, cudaStream_t s);
+void launch_step_begin(int* counters, int n_counters, int* step_t, int* loss_slot, int do_adam,
+                       cudaStream_t s);
+
+}  // namespace xp

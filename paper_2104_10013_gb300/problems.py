@@ -151,6 +151,12 @@ def _f32(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64).astype(np.float32))
 
 
+def _cuts32(c) -> np.ndarray:
+    """Cut coordinates rounded to float32 values, so that subdomain boxes,
+    interface points and query points on a cut agree on both sides."""
+    return np.asarray(c, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
 def _rng(seed: int, *key: int) -> np.random.Generator:
     return np.random.default_rng([int(seed)] + [int(k) for k in key])
 
@@ -279,7 +285,7 @@ def burgers_cpinn(n_sub=4, n_res=1000, n_iface=100, n_bc=50, hidden=(20, 20, 20)
     """1D viscous Burgers u_t + u u_x = nu u_xx on x in [-1,1], t in [0,1]
     (Sec. 7.3, Eq. BE), u(x,0) = -sin(pi x), u(+-1,t) = 0; n_sub equal x-slabs
     coupled by cPINN (flux + average continuity).  Inputs are (x, t)."""
-    xc = np.linspace(-1.0, 1.0, n_sub + 1)
+    xc = _cuts32(np.linspace(-1.0, 1.0, n_sub + 1))
     net = NetSpec([2, *hidden, 1])
     subs = []
     for q in range(n_sub):
@@ -319,7 +325,7 @@ def poisson_xpinn(nx=4, ny=4, n_res_range=(2000, 20000), depth_range=(4, 6), wid
             c = np.sort(g.random(n - 1))
             full = np.concatenate([[0.0], c, [1.0]])
             if np.all(np.diff(full) >= min_cell):
-                return full
+                return _cuts32(full)
     xc, yc = cuts(nx), cuts(ny)
     subs = []
     for j in range(ny):
@@ -356,8 +362,8 @@ def kovasznay_cpinn(nx=8, ny=8, n_res=50000, n_iface=256, n_bc=80, width=64, dep
     [-0.5,1] x [-0.5,1.5], cPINN on an equal nx x ny grid; each boundary
     subdomain gets n_bc Dirichlet points for (u, v, p)."""
     dom = (-0.5, 1.0, -0.5, 1.5)
-    xc = np.linspace(dom[0], dom[1], nx + 1)
-    yc = np.linspace(dom[2], dom[3], ny + 1)
+    xc = _cuts32(np.linspace(dom[0], dom[1], nx + 1))
+    yc = _cuts32(np.linspace(dom[2], dom[3], ny + 1))
     net = NetSpec([2] + [width] * depth + [3])
     subs = []
     for j in range(ny):

@@ -1,0 +1,294 @@
+"""Python binding of the C ABI in include/xpinn.h (ctypes, marshalling only).
+
+Every computation runs in the CUDA library; this module only builds the
+problem description, passes pointers and reshapes results.  Arrays may be
+numpy arrays (host) or CUDA torch tensors (device); with device tensors the
+calls are asynchronous on torch's current stream.
+
+The library must have been built (paper_2104_10013_gb300.build.build()); if
+it is missing, load() raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import problems as P
+
+MAX_NETS, MAX_LAYERS, N_TERMS = 2, 12, 5
+
+_STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "NONFINITE",
+           -6: "UNSUPPORTED"}
+
+
+class XpinnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"xpinn {_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class NetDesc(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("widths", C.c_int32 * (MAX_LAYERS + 1)), ("out_act", C.c_int32)]
+
+
+class SubDesc(C.Structure):
+    _fields_ = [("n_nets", C.c_int32), ("nets", NetDesc * MAX_NETS),
+                ("n_res", C.c_int64), ("res_xy", C.c_void_p), ("res_f", C.c_void_p),
+                ("n_data", C.c_int64 * MAX_NETS), ("data_xy", C.c_void_p * MAX_NETS),
+                ("data_val", C.c_void_p * MAX_NETS), ("w_data", C.c_float * MAX_NETS),
+                ("w_res", C.c_float), ("w_avg", C.c_float), ("w_iface", C.c_float),
+                ("lr", C.c_float), ("rect", C.c_float * 4)]
+
+
+class IfaceDesc(C.Structure):
+    _fields_ = [("q", C.c_int32), ("q_plus", C.c_int32), ("method", C.c_int32),
+                ("normal", C.c_float * 2), ("n_pts", C.c_int64), ("xy", C.c_void_p)]
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("pde", C.c_int32), ("nu", C.c_float), ("re", C.c_float), ("flux_mode", C.c_int32),
+                ("n_sub", C.c_int32), ("subs", C.POINTER(SubDesc)),
+                ("n_iface", C.c_int32), ("ifaces", C.POINTER(IfaceDesc)),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("subs_per_model", C.c_int32), ("init_params", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("schedule", C.c_int32), ("use_graph", C.c_int32), ("items_per_cta", C.c_int32),
+                ("points_per_thread", C.c_int32)]
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libxpinn.so")
+
+
+def load() -> C.CDLL:
+    """Load lib/libxpinn.so (built in-tree).  Raises if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run paper_2104_10013_gb300.build.build())")
+    L = C.CDLL(path)
+    vp, i32, i64, fp = C.c_void_p, C.c_int32, C.c_int64, C.c_void_p
+    sig = {
+        "xpinn_create": (C.c_int, [C.POINTER(ProblemDesc), C.POINTER(vp)]),
+        "xpinn_destroy": (C.c_int, [vp]),
+        "xpinn_last_error": (C.c_char_p, []),
+        "xpinn_num_params": (i64, [vp]),
+        "xpinn_get_params": (C.c_int, [vp, fp, i64, vp]),
+        "xpinn_set_params": (C.c_int, [vp, fp, i64, vp]),
+        "xpinn_grad": (C.c_int, [vp, fp, fp, vp]),
+        "xpinn_step": (C.c_int, [vp, i32, fp, vp]),
+        "xpinn_net_jets": (C.c_int, [vp, i32, i32, fp, i64, i32, fp, vp]),
+        "xpinn_eval": (C.c_int, [vp, i32, fp, i64, i32, fp, vp]),
+        "xpinn_set_residual_points": (C.c_int, [vp, fp, fp, i64, vp]),
+        "xpinn_get_state": (C.c_int, [vp, vp, C.POINTER(C.c_size_t)]),
+        "xpinn_set_state": (C.c_int, [vp, vp, C.c_size_t]),
+        "xpinn_get_options": (C.c_int, [vp, C.POINTER(Options)]),
+        "xpinn_set_options": (C.c_int, [vp, C.POINTER(Options)]),
+        "xpinn_iface_values": (C.c_int, [vp, fp, C.POINTER(i64), vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    _LIB = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise XpinnError(rc, load().xpinn_last_error().decode())
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _ptr(x):
+    """(pointer, keepalive) of a numpy array or a CUDA torch tensor."""
+    if x is None:
+        return None, None
+    if hasattr(x, "data_ptr"):          # torch tensor
+        return x.data_ptr(), x
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data, a
+
+
+def _stream(x=None):
+    if x is not None and hasattr(x, "is_cuda") and x.is_cuda:
+        import torch
+        return torch.cuda.current_stream(x.device).cuda_stream
+    return None
+
+
+class Solver:
+    """One problem on the GPU: the grouped cPINN/XPINN training step, jets,
+    stitched evaluation and checkpointing, through the C ABI."""
+
+    def __init__(self, problem: P.Problem, init_params=None):
+        self.lib = load()
+        self.pb = problem
+        keep = []
+
+        def arr(a, dt=np.float32):
+            a = np.ascontiguousarray(np.asarray(a, dtype=dt))
+            keep.append(a)
+            return a.ctypes.data
+
+        subs = (SubDesc * problem.n_sub)()
+        for q, s in enumerate(problem.subs):
+            d = subs[q]
+            d.n_nets = len(s.nets)
+            for n, net in enumerate(s.nets):
+                d.nets[n].n_layers = len(net.widths) - 1
+                for k, w in enumerate(net.widths):
+                    d.nets[n].widths[k] = w
+                d.nets[n].out_act = net.out_act
+            d.n_res = s.res_xy.shape[0]
+            d.res_xy = arr(s.res_xy) if d.n_res else None
+            d.res_f = arr(s.res_f) if d.n_res else None
+            for n in range(len(s.nets)):
+                ds = s.data[n] if n < len(s.data) else None
+                if ds is not None and ds.xy.shape[0]:
+                    d.n_data[n] = ds.xy.shape[0]
+                    d.data_xy[n] = arr(ds.xy)
+                    d.data_val[n] = arr(ds.val)
+                d.w_data[n] = s.w_data[n] if n < len(s.w_data) else 0.0
+            d.w_res, d.w_avg, d.w_iface, d.lr = s.w_res, s.w_avg, s.w_iface, s.lr
+            for i, v in enumerate(s.rect if s.rect is not None else (0, 0, 0, 0)):
+                d.rect[i] = v
+        ifs = (IfaceDesc * max(1, len(problem.ifaces)))()
+        for e, it in enumerate(problem.ifaces):
+            f = ifs[e]
+            f.q, f.q_plus, f.method = it.q, it.qp, it.method
+            f.normal[0], f.normal[1] = it.normal
+            f.n_pts = it.xy.shape[0]
+            f.xy = arr(it.xy) if f.n_pts else None
+        desc = ProblemDesc()
+        desc.pde, desc.nu, desc.re, desc.flux_mode = problem.pde, problem.nu, problem.re, problem.flux_mode
+        desc.n_sub, desc.subs = problem.n_sub, subs
+        desc.n_iface, desc.ifaces = len(problem.ifaces), ifs
+        desc.beta1, desc.beta2, desc.eps = problem.beta1, problem.beta2, problem.eps
+        desc.subs_per_model = problem.subs_per_model
+        theta = problem.packed_params() if init_params is None else _f32(init_params)
+        desc.init_params = arr(theta)
+        h = C.c_void_p()
+        _check(self.lib.xpinn_create(C.byref(desc), C.byref(h)))
+        self.h = h
+        self.n_params = int(self.lib.xpinn_num_params(h))
+        self.n_sub = problem.n_sub
+
+    # ---------------------------------------------------------------- lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.xpinn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- params
+    def get_params(self, out=None):
+        out = np.empty(self.n_params, np.float32) if out is None else out
+        p, k = _ptr(out)
+        _check(self.lib.xpinn_get_params(self.h, p, self.n_params, _stream(out)))
+        return out
+
+    def set_params(self, theta):
+        p, k = _ptr(theta if hasattr(theta, "data_ptr") else _f32(theta))
+        _check(self.lib.xpinn_set_params(self.h, p, self.n_params, _stream(theta)))
+
+    # ---------------------------------------------------------------- step
+    def grad(self, losses=None, grads=None):
+        """(losses [n_sub, 5], grads [n_params]) at the current parameters."""
+        losses = np.empty((self.n_sub, N_TERMS), np.float32) if losses is None else losses
+        grads = np.empty(self.n_params, np.float32) if grads is None else grads
+        lp, _ = _ptr(losses)
+        gp, _ = _ptr(grads)
+        _check(self.lib.xpinn_grad(self.h, lp, gp, _stream(grads)))
+        return losses, grads
+
+    def step(self, n_steps=1, losses=True, stream=None):
+        """Run n_steps training steps; returns losses [n_steps, n_sub, 5] (or None)."""
+        if losses is True:
+            losses = np.empty((n_steps, self.n_sub, N_TERMS), np.float32)
+        lp, _ = _ptr(losses) if losses is not None and losses is not False else (None, None)
+        st = stream if stream is not None else _stream(losses if hasattr(losses, "is_cuda") else None)
+        _check(self.lib.xpinn_step(self.h, n_steps, lp, st))
+        return losses if lp is not None else None
+
+    def set_residual_points(self, xy, f=None):
+        xp_, k1 = _ptr(xy if hasattr(xy, "data_ptr") else _f32(xy))
+        fp_, k2 = _ptr(f if (f is None or hasattr(f, "data_ptr")) else _f32(f))
+        _check(self.lib.xpinn_set_residual_points(self.h, xp_, fp_, self.pb.n_res, _stream(xy)))
+
+    # ---------------------------------------------------------------- jets / eval
+    @staticmethod
+    def n_comp(order):
+        return (1, 3, 5)[order]
+
+    def net_jets(self, q, net, xy, order=2, out=None):
+        """Jets [n, D_out, K] of network `net` of subdomain q at xy [n, 2]."""
+        n = int(xy.shape[0])
+        D = self.pb.subs[q].nets[net].widths[-1]
+        K = self.n_comp(order)
+        if out is None:
+            out = np.empty((n, D, K), np.float32)
+        src = xy if hasattr(xy, "data_ptr") else _f32(xy)
+        xp_, _ = _ptr(src)
+        op, _ = _ptr(out)
+        _check(self.lib.xpinn_net_jets(self.h, q, net, xp_, n, order, op, _stream(xy)))
+        return out
+
+    def eval(self, model, xy, order=0, out=None):
+        """Stitched solution of Eq. FSol: [n, D_out_total, K]."""
+        n = int(xy.shape[0])
+        D = sum(net.widths[-1] for net in self.pb.subs[0].nets)
+        K = self.n_comp(order)
+        if out is None:
+            out = np.empty((n, D, K), np.float32)
+        src = xy if hasattr(xy, "data_ptr") else _f32(xy)
+        xp_, _ = _ptr(src)
+        op, _ = _ptr(out)
+        _check(self.lib.xpinn_eval(self.h, model, xp_, n, order, op, _stream(xy)))
+        return out
+
+    def iface_values(self):
+        n = C.c_int64(0)
+        _check(self.lib.xpinn_iface_values(self.h, None, C.byref(n), None))
+        out = np.empty(n.value, np.float32)
+        _check(self.lib.xpinn_iface_values(self.h, out.ctypes.data, C.byref(n), None))
+        return out
+
+    # ---------------------------------------------------------------- state / options
+    def get_state(self) -> bytes:
+        n = C.c_size_t(0)
+        _check(self.lib.xpinn_get_state(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(self.lib.xpinn_get_state(self.h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def set_state(self, blob: bytes):
+        _check(self.lib.xpinn_set_state(self.h, blob, len(blob)))
+
+    def options(self) -> dict:
+        o = Options()
+        _check(self.lib.xpinn_get_options(self.h, C.byref(o)))
+        return {f: getattr(o, f) for f, _ in Options._fields_}
+
+    def set_options(self, **kw):
+        cur = self.options()
+        cur.update(kw)
+        o = Options(**cur)
+        _check(self.lib.xpinn_set_options(self.h, C.byref(o)))

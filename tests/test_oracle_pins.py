@@ -17,6 +17,7 @@ import torch
 
 from oracle import Oracle, jets, residual, flux_normal, adam_update, route_rect, network
 from paper_2104_10013_gb300 import problems as P
+from tests.cases import tiny_problem as _tiny_problem, CASES
 
 DT = torch.float64
 NU = 0.01 / math.pi
@@ -218,38 +219,6 @@ def test_jets_match_central_differences(out_act):
 
 
 # ---------------------------------------------------------------- losses
-
-def _tiny_problem(pde, method, n_sub=2, widths=None, n_res=7, n_data=5, n_if=4, seed=0):
-    """Two (or more) subdomains side by side on [0, n_sub] x [0, 1] with tiny
-    networks, random targets and forcing; every loss term is active."""
-    rng = np.random.default_rng(seed)
-    nets = {P.PDE_BURGERS: [P.NetSpec(widths or [2, 3, 3, 1])],
-            P.PDE_POISSON: [P.NetSpec(widths or [2, 3, 3, 1])],
-            P.PDE_NS: [P.NetSpec(widths or [2, 3, 3, 3])],
-            P.PDE_DIFFUSION: [P.NetSpec(widths or [2, 3, 3, 1]),
-                              P.NetSpec([2, 3, 1], P.ACT_SOFTPLUS)]}[pde]
-    subs = []
-    for q in range(n_sub):
-        res = rng.uniform((q, 0), (q + 1, 1), size=(n_res, 2))
-        data = []
-        for n in nets:
-            dxy = rng.uniform((q, 0), (q + 1, 1), size=(n_data, 2))
-            data.append(P.DataSet(P._f32(dxy), P._f32(rng.normal(size=(n_data, n.widths[-1])))))
-        s = P.Subdomain(nets=nets, res_xy=P._f32(res), res_f=P._f32(rng.normal(size=n_res)),
-                        data=data, w_data=[1.3, 0.7][:len(nets)], w_res=0.9, w_avg=1.1,
-                        w_iface=0.8, lr=1e-3 * (q + 1), rect=(q, q + 1, 0.0, 1.0))
-        s.params = [[(P._f32(rng.normal(size=W.shape)), P._f32(rng.normal(size=b.shape) * 0.3))
-                     for W, b in P.xavier_params(n, rng)] for n in nets]
-        subs.append(s)
-    ifaces = [P.Interface(q, q + 1, method, (1.0, 0.0),
-                          P._f32(np.stack([np.full(n_if, q + 1.0), rng.random(n_if)], 1)))
-              for q in range(n_sub - 1)]
-    return P.Problem("tiny", pde, subs, ifaces, nu=NU, re=7.0)
-
-
-CASES = [(P.PDE_BURGERS, P.CPINN), (P.PDE_BURGERS, P.XPINN), (P.PDE_POISSON, P.XPINN),
-         (P.PDE_POISSON, P.CPINN), (P.PDE_NS, P.CPINN), (P.PDE_NS, P.XPINN),
-         (P.PDE_DIFFUSION, P.XPINN), (P.PDE_DIFFUSION, P.CPINN)]
 
 
 @pytest.mark.parametrize("pde,method", CASES)
