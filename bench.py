@@ -1,0 +1,314 @@
+#!/usr/bin/env python3
+"""Benchmark of the grouped cPINN / XPINN training step on GB300.
+
+One step = one pass of the whole hot path over all subdomains: interface
+exchange, jets (value, first and second input derivatives) through every
+subdomain's network at its residual, data and interface points, PDE residual
+and interface terms, reverse pass, fixed-order gradient reduction and Adam.
+
+Default workload: 16-subdomain XPINN Poisson on the unit square (uneven 4x4
+grid, per-subdomain depth 4-6 and width 20-80, 2k-20k residual points each,
+seed 0).  Inputs are ~2 MB, far below L2, so L2 is flushed (a 256 MB write)
+before every timed step and each step is timed alone with CUDA events on the
+launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+With N > 1 (torchrun) every rank trains its own replica (replicas only: the
+path has no cross-GPU exchange); value = all ranks' residual points / the
+slowest rank's time.  --impl reference times the FP64 CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "residual pts/s (jet fwd+bwd) grouped vs per-subdomain loop; query p50/p99 ms"
+FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 partitions x 32)
+
+
+def workload(name):
+    from paper_2104_10013_gb300 import problems as P
+    if name == "c2":
+        return P.poisson_xpinn(), ("XPINN Poisson -lap u = f on the unit square, 16 subdomains of an uneven "
+                                   "4x4 grid, depth 4-6 x width 20-80 tanh MLPs and 2k-20k residual points "
+                                   "per subdomain (seed 0), 200 points per interface")
+    if name == "c1":
+        return P.burgers_cpinn(), "cPINN Burgers, 4 x-slabs, 2->20x3->1, 1000 residual pts each"
+    if name == "c3":
+        return P.kovasznay_cpinn(), "cPINN Kovasznay NS Re=40, 8x8 grid, 2->64x6->3, 50k residual pts each"
+    raise SystemExit(f"unknown workload {name}")
+
+
+# jet components propagated at residual points, per PDE and network:
+# Burgers (u, u_x, u_t, u_xx); Poisson and NS (u, u_x, u_y, u_xx, u_yy);
+# inverse diffusion: u-net 5, K-net (K, K_x, K_y)
+K_RES = {0: (4,), 1: (5,), 2: (5,), 3: (5, 3)}
+
+
+def algorithmic_flops(pb):
+    """6 K M FLOP per residual point (forward W h, reverse W^T z-bar and
+    z-bar h^T, FMA = 2 FLOP), M = sum over layers k >= 2 of N_k N_{k-1}."""
+    tot = 0.0
+    for s in pb.subs:
+        for net, K in zip(s.nets, K_RES[pb.pde]):
+            w = net.widths
+            M = sum(w[k] * w[k - 1] for k in range(2, len(w)))
+            tot += 6.0 * K * M * s.res_xy.shape[0]
+    return tot
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_id}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if "Active" in v and "Not" not in v})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].strip().replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def time_steps(torch, s, stream, flush, steps):
+    """Time `steps` single steps, each alone: flush L2, then events around
+    the step on its stream.  Returns (step ms list, jet-kernel ms list)."""
+    step_ms, jet_ms = [], []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0.record(stream)
+        s.step(1, losses=None, stream=stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        jet_ms.append(float(s.phase_times()[2]))
+    return step_ms, jet_ms
+
+
+def cpu_baseline(pb, seconds):
+    """The FP64 oracle, as it stands, on this host's cores: gradients of whole
+    subdomains of the same workload in turn until `seconds` have passed."""
+    import torch
+    from oracle import Oracle
+    orc = Oracle(pb)
+    theta = pb.packed_params()
+    pts, t_tot, qs = 0, 0.0, []
+    q = 0
+    while t_tot < seconds and len(qs) < 4 * pb.n_sub:
+        t0 = time.perf_counter()
+        orc.grad(theta, subset=[q])
+        t_tot += time.perf_counter() - t0
+        pts += pb.subs[q].res_xy.shape[0]
+        qs.append(q)
+        q = (q + 1) % pb.n_sub
+    return {"value": pts / t_tot, "unit": "pts/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle gradient of {len(qs)} whole subdomains (q = {qs[0]}..{qs[-1]} in turn) "
+                      f"of the same workload, {pts} residual points in {t_tot:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    pb, desc = workload(args.workload)
+    from oracle import Oracle
+    orc = Oracle(pb)
+    theta = pb.packed_params()
+    q = 0
+    for _ in range(args.warmup):
+        orc.grad(theta, subset=[q]); q = (q + 1) % pb.n_sub
+    pts, t_tot = 0, 0.0
+    t_start = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.grad(theta, subset=[q])
+        t_tot += time.perf_counter() - t0
+        pts += pb.subs[q].res_xy.shape[0]
+        q = (q + 1) % pb.n_sub
+    v = pts / t_tot
+    sample = (f"each step: FP64 oracle gradient of one whole subdomain of the workload (subdomains in turn), "
+              f"{pts} residual points over {args.steps} steps")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "pts/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc},
+        "cpu_baseline": {"value": v, "unit": "pts/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t_start}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-loop", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2104_10013_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_2104_10013_gb300 import xpinn as X
+    X.load()
+
+    pb, desc = workload(args.workload)
+    n_res = pb.n_res
+    s = X.Solver(pb)
+    s.set_options(profile_phases=1)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        s.step(1, losses=None, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K grouped steps
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = str(local)
+    clocks = Clocks(gpu_id)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, jet_ms = time_steps(torch, s, stream, flush, args.steps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = float(np.sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n_res * args.steps / (total_ms / 1e3)
+    ms_step = total_ms / args.steps
+    launches_per_step = 4 if any(it.xy.shape[0] for it in pb.ifaces) else 3
+
+    # ---- roofline of the dominant kernel (the jet kernel over all items)
+    flops = algorithmic_flops(pb)
+    jet_avg = float(np.mean(jet_ms))
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (jet_avg / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "xp::jet_step_kernel (residual, data and interface items)",
+            "kernel_ms": jet_avg, "kernel_share_of_step": jet_avg / ms_step,
+            "flop_per_launch": flops,
+            "peak_note": f"FP32 FFMA peak derived: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x "
+                         f"{sm_max:.0f} MHz (max SM clock)"}
+
+    out = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": desc, "n_sub": pb.n_sub, "residual_pts_per_step": n_res,
+                      "params": pb.n_params, "l2": "flushed (256 MB write) before every timed step",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "adam_steps_per_s": 1e3 / ms_step, "roofline": roof, "gpu_launches": launches_per_step * args.steps,
+           "clocks": clk}
+
+    # ---- per-subdomain launch loop, same kernels, same GPU
+    if not args.no_loop:
+        s.set_options(schedule=1, profile_phases=1)
+        for _ in range(3):
+            s.step(1, losses=None, stream=stream.cuda_stream)
+        lms, ljet = time_steps(torch, s, stream, flush, args.steps)
+        lval = n_res * args.steps / (np.sum(lms) / 1e3)
+        out["loop"] = {"value": lval, "unit": "pts/s", "ms_per_step": float(np.mean(lms)),
+                       "grouped_speedup": (n_res * args.steps / (np.sum(step_ms) / 1e3)) / lval}
+        s.set_options(schedule=0, profile_phases=1)
+
+    # ---- end to end through the public API with host buffers
+    if not args.no_e2e:
+        xy = torch.from_numpy(np.concatenate([sd.res_xy for sd in pb.subs])).pin_memory()
+        f = torch.from_numpy(np.concatenate([sd.res_f for sd in pb.subs])).pin_memory()
+        losses = torch.empty((1, pb.n_sub, 5), dtype=torch.float32).pin_memory()
+        for _ in range(3):
+            s.set_residual_points(xy, f)
+            s.step(1, losses=losses)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.set_residual_points(xy, f)
+            s.step(1, losses=losses)
+        e2e_s = time.perf_counter() - t0
+        out["e2e"] = {"value": n_res * args.steps / e2e_s * world, "unit": "pts/s",
+                      "h2d_bytes_per_step": int(xy.numel() * 4 + f.numel() * 4),
+                      "d2h_bytes_per_step": int(losses.numel() * 4),
+                      "ms_per_step": 1e3 * e2e_s / args.steps}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(pb, args.cpu_seconds)
+    s.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -20,6 +20,8 @@
  *    has been copied, which synchronises `stream`.
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *    stream.  Calls on one handle are stream-ordered and not thread-safe.
+ *  - A handle belongs to the CUDA device that was current when it was
+ *    created; every call makes that device current for its duration.
  *  - Jet components are ordered (u, d0 u, d1 u, d00 u, d11 u): value, first
  *    derivatives and diagonal second derivatives with respect to the two
  *    inputs z = (z0, z1), which are (x, t) for Burgers and (x, y) otherwise.
@@ -199,11 +201,20 @@ typedef struct {
                               per subdomain per phase: the baseline) */
   int32_t use_graph;       /* 1: replay steps from a captured CUDA graph */
   int32_t items_per_cta;   /* work items per CTA the scheduler aims for (>= 1) */
-  int32_t points_per_thread; /* 1 or 2 points in a thread's register tile */
+  int32_t points_per_thread; /* points in a thread's register tile (2) */
+  int32_t profile_phases;  /* 1: record CUDA events between the phases of every
+                              step (also inside the graph), see xpinn_phase_times */
 } xpinn_options;
 
 int xpinn_get_options(xpinn_handle h, xpinn_options* opt);
 int xpinn_set_options(xpinn_handle h, const xpinn_options* opt);
+
+/* Device time in milliseconds of the four phases of the most recent step or
+ * grad call, measured by CUDA events recorded on the call's stream:
+ * ms[0] step start, ms[1] interface exchange launch(es), ms[2] jet kernel
+ * launch(es) over residual, data and interface points, ms[3] reduction and
+ * Adam.  Requires profile_phases = 1; waits for that step to finish. */
+int xpinn_phase_times(xpinn_handle h, float* ms);
 
 /* Interface exchange buffer after the last grad/step: for every interface
  * (in order), every point, side 0 (q) then side 1 (q_plus): the solution

@@ -250,19 +250,24 @@ class Oracle:
         return uvec, qty
 
     # -- loss (Eqs. cPINNLoss / XPINNLoss) ---------------------------------
-    def loss_terms(self, flat: torch.Tensor) -> torch.Tensor:
+    def loss_terms(self, flat: torch.Tensor, subset=None) -> torch.Tensor:
         """[n_sub, 5] tensor of MSE terms (data net 0, data net 1, residual,
         average solution, flux or residual continuity), differentiable with
-        respect to `flat` through each subdomain's own parameters only."""
+        respect to `flat` through each subdomain's own parameters only.
+        With `subset`, only the rows of those subdomains (in that order)."""
         pb = self.pb
+        qs = list(range(pb.n_sub)) if subset is None else list(subset)
         rows = []
         # values exchanged across every interface, held constant (stop-gradient)
         recv = {}
-        for e in range(len(pb.ifaces)):
+        for e, it in enumerate(pb.ifaces):
+            if it.q not in qs and it.qp not in qs:
+                continue
             for side in (0, 1):
                 u, qty = self.iface_quantities(flat, e, side)
                 recv[(e, side)] = (u.detach(), qty.detach())
-        for q, s in enumerate(pb.subs):
+        for q in qs:
+            s = pb.subs[q]
             terms = [torch.zeros((), dtype=DT) for _ in range(P.N_TERMS)]
             # data mismatch MSE_u per net
             for ni, ds in enumerate(s.data):
@@ -298,12 +303,14 @@ class Oracle:
             W[q, 2:] = (s.w_res, s.w_avg, s.w_iface)
         return W.astype(np.float32).astype(np.float64)
 
-    def grad(self, flat_np):
+    def grad(self, flat_np, subset=None):
         """Loss terms [n_sub, 5] and the packed gradient of every J(Theta_q)
-        with respect to its own Theta_q."""
+        with respect to its own Theta_q (with `subset`: those subdomains'
+        rows, and a gradient that is zero elsewhere)."""
         flat = _t(flat_np).requires_grad_(True)
-        terms = self.loss_terms(flat)
-        J = (terms * _t(self.weights())).sum()
+        terms = self.loss_terms(flat, subset)
+        W = self.weights() if subset is None else self.weights()[list(subset)]
+        J = (terms * _t(W)).sum()
         (g,) = torch.autograd.grad(J, flat, allow_unused=True)
         g = torch.zeros_like(flat) if g is None else g
         return terms.detach().numpy(), g.detach().numpy()

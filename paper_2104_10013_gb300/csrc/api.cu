@@ -155,7 +155,9 @@ struct xpinn_ctx {
   int n_sm = 0, grid = 0;
   int ring_cap = 256;
   int host_t = 0, host_slot = 0;
-  xpinn_options opt{0, 1, 4, 2};
+  xpinn_options opt{0, 1, 4, 2, 0};
+  int device = 0;
+  cudaEvent_t ev[5] = {};
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   int n_counters = 0;
@@ -165,6 +167,8 @@ struct xpinn_ctx {
   ~xpinn_ctx() {
     if (graph) cudaGraphExecDestroy(graph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
   }
 
   int* step_t() { return state_i.p; }
@@ -464,8 +468,13 @@ StepArgs args_for(xpinn_ctx* h, int begin, int count, int counter_idx) {
   return a;
 }
 
+void mark(xpinn_ctx* h, int i, cudaStream_t s) {
+  if (h->opt.profile_phases) ck(cudaEventRecordWithFlags(h->ev[i], s, cudaEventRecordExternal), "event");
+}
+
 void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads) {
   const Plan& pl = h->plan;
+  mark(h, 0, s);
   launch_step_begin(h->counters.p, h->n_counters, h->step_t(), h->loss_slot(), adam ? 1 : 0, s);
   const int n_main = (int)pl.items.size() - pl.n_fwd;
   ReduceArgs r{};
@@ -492,18 +501,24 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads) {
   r.eps = h->eps;
   r.n_sub = h->n_sub;
   if (h->opt.schedule == 0) {
+    mark(h, 1, s);
     if (pl.n_fwd) launch_jet_step(args_for(h, 0, pl.n_fwd, 0), std::min(h->grid, pl.n_fwd), h->smem, s);
+    mark(h, 2, s);
     if (n_main) launch_jet_step(args_for(h, pl.n_fwd, n_main, 1), std::min(h->grid, n_main), h->smem, s);
+    mark(h, 3, s);
     launch_reduce_adam(r, s);
   } else {
+    mark(h, 1, s);
     for (int q = 0; q < h->n_sub; ++q) {
       const int b = pl.fwd_begin[q], c = pl.fwd_begin[q + 1] - b;
       if (c) launch_jet_step(args_for(h, b, c, 2 + q), std::min(h->grid, c), h->smem, s);
     }
+    mark(h, 2, s);
     for (int q = 0; q < h->n_sub; ++q) {
       const int b = pl.n_fwd + pl.main_begin[q], c = pl.main_begin[q + 1] - pl.main_begin[q];
       if (c) launch_jet_step(args_for(h, b, c, 2 + h->n_sub + q), std::min(h->grid, c), h->smem, s);
     }
+    mark(h, 3, s);
     // one reduce/Adam launch per subdomain
     int bi = 0;
     for (int q = 0; q < h->n_sub; ++q) {
@@ -516,6 +531,7 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads) {
       bi += nb;
     }
   }
+  mark(h, 4, s);
   ck(cudaGetLastError(), "kernel launch");
 }
 
@@ -594,6 +610,21 @@ void eval_items_for(xpinn_ctx* h, int q, int net, int K, int64_t first, int64_t 
 }
 
 }  // namespace
+
+// Makes the handle's device current for the duration of an API call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(const xpinn_ctx* h) {
+    if (h && cudaGetDevice(&prev) == cudaSuccess && prev != h->device) {
+      ck(cudaSetDevice(h->device), "cudaSetDevice");
+    } else {
+      prev = -1;
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 // ===========================================================================
 // C ABI
@@ -745,6 +776,7 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
   check_finite(d->init_params, h->n_params, "init_params");
   // ---- device
   ck(cudaFree(0), "CUDA init");
+  ck(cudaGetDevice(&h->device), "cudaGetDevice");
   ck(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, 0), "attr");
   h->grid = h->n_sm;
   std::vector<float2> all = pts_res;
@@ -808,6 +840,7 @@ int64_t xpinn_num_params(xpinn_handle h) { return h ? h->n_params : -1; }
 int xpinn_get_params(xpinn_handle h, float* dst, int64_t n, void* stream) {
   API_BEGIN
   if (!h || !dst || n != h->n_params) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
   copy_out(dst, h->params.p, n * sizeof(float), (cudaStream_t)stream);
   API_END
 }
@@ -815,6 +848,7 @@ int xpinn_get_params(xpinn_handle h, float* dst, int64_t n, void* stream) {
 int xpinn_set_params(xpinn_handle h, const float* src, int64_t n, void* stream) {
   API_BEGIN
   if (!h || !src || n != h->n_params) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
   copy_in(h->params.p, src, n * sizeof(float), (cudaStream_t)stream);
   API_END
 }
@@ -822,6 +856,7 @@ int xpinn_set_params(xpinn_handle h, const float* src, int64_t n, void* stream) 
 int xpinn_grad(xpinn_handle h, float* losses, float* grads, void* stream) {
   API_BEGIN
   if (!h) fail(XPINN_ERR_INVALID, "NULL handle");
+  DeviceGuard dg(h);
   cudaStream_t s = (cudaStream_t)stream;
   enqueue_step(h, s, false, h->grads.p);
   h->host_slot += 1;
@@ -836,6 +871,7 @@ int xpinn_grad(xpinn_handle h, float* losses, float* grads, void* stream) {
 int xpinn_step(xpinn_handle h, int32_t n_steps, float* losses, void* stream) {
   API_BEGIN
   if (!h || n_steps < 0) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t row = (size_t)h->n_sub * XPINN_N_TERMS;
   const bool dev_out = losses && is_device_ptr(losses);
@@ -894,6 +930,7 @@ int xpinn_net_jets(xpinn_handle h, int32_t q, int32_t net, const float* xy, int6
   if (!h || q < 0 || q >= h->n_sub || net < 0 || net >= h->subs[q].n_nets || order < 0 || order > 2 ||
       n < 0 || (n > 0 && (!xy || !out)))
     fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
   if (n == 0) { g_err.clear(); return XPINN_OK; }
   cudaStream_t s = (cudaStream_t)stream;
   const int K = order == 0 ? 1 : (order == 1 ? 3 : 5);
@@ -926,6 +963,7 @@ int xpinn_eval(xpinn_handle h, int32_t model, const float* xy, int64_t n, int32_
   if (!h || model < 0 || model >= h->n_sub / h->spm || order < 0 || order > 2 || n < 0 ||
       (n > 0 && (!xy || !out)))
     fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
   if (n == 0) { g_err.clear(); return XPINN_OK; }
   cudaStream_t s = (cudaStream_t)stream;
   const int K = order == 0 ? 1 : (order == 1 ? 3 : 5);
@@ -975,6 +1013,7 @@ int xpinn_eval(xpinn_handle h, int32_t model, const float* xy, int64_t n, int32_
 int xpinn_set_residual_points(xpinn_handle h, const float* xy, const float* f, int64_t n, void* stream) {
   API_BEGIN
   if (!h || !xy || n != h->n_res_total) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
   cudaStream_t s = (cudaStream_t)stream;
   copy_in(h->pts.p, xy, n * sizeof(float2), s);
   if (f)
@@ -997,6 +1036,7 @@ struct StateHeader {
 int xpinn_get_state(xpinn_handle h, void* blob, size_t* n) {
   API_BEGIN
   if (!h || !n) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
   const size_t need = sizeof(StateHeader) + 3 * sizeof(float) * h->n_params;
   if (!blob) {
     *n = need;
@@ -1025,6 +1065,7 @@ int xpinn_get_state(xpinn_handle h, void* blob, size_t* n) {
 int xpinn_set_state(xpinn_handle h, const void* blob, size_t n) {
   API_BEGIN
   if (!h || !blob) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
   const size_t need = sizeof(StateHeader) + 3 * sizeof(float) * h->n_params;
   StateHeader hd;
   if (n < sizeof hd) fail(XPINN_ERR_INVALID, "state blob too small");
@@ -1052,11 +1093,15 @@ int xpinn_get_options(xpinn_handle h, xpinn_options* opt) {
 int xpinn_set_options(xpinn_handle h, const xpinn_options* opt) {
   API_BEGIN
   if (!h || !opt) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
   if (opt->schedule < 0 || opt->schedule > 1 || opt->items_per_cta < 1 || opt->items_per_cta > 64 ||
-      opt->points_per_thread != 2)
+      opt->points_per_thread != 2 || opt->profile_phases < 0 || opt->profile_phases > 1)
     fail(XPINN_ERR_INVALID, "bad options");
   ck(cudaDeviceSynchronize(), "sync");
   h->opt = *opt;
+  if (h->opt.profile_phases)
+    for (auto& e : h->ev)
+      if (!e) ck(cudaEventCreate(&e), "cudaEventCreate");
   plan(h);
   h->base.partials = h->partials.p;
   h->base.loss_part = h->loss_part.p;
@@ -1064,9 +1109,20 @@ int xpinn_set_options(xpinn_handle h, const xpinn_options* opt) {
   API_END
 }
 
+int xpinn_phase_times(xpinn_handle h, float* ms) {
+  API_BEGIN
+  if (!h || !ms) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  if (!h->opt.profile_phases || !h->ev[0]) fail(XPINN_ERR_INVALID, "profile_phases is off");
+  ck(cudaEventSynchronize(h->ev[4]), "event sync");
+  for (int i = 0; i < 4; ++i) ck(cudaEventElapsedTime(ms + i, h->ev[i], h->ev[i + 1]), "elapsed");
+  API_END
+}
+
 int xpinn_iface_values(xpinn_handle h, float* out, int64_t* n_floats, void* stream) {
   API_BEGIN
   if (!h || !n_floats) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
   const int64_t need = h->n_if_pts * 2 * h->d4_nv;
   if (!out) {
     *n_floats = need;

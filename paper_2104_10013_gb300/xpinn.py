@@ -57,7 +57,7 @@ class ProblemDesc(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("schedule", C.c_int32), ("use_graph", C.c_int32), ("items_per_cta", C.c_int32),
-                ("points_per_thread", C.c_int32)]
+                ("points_per_thread", C.c_int32), ("profile_phases", C.c_int32)]
 
 
 _LIB = None
@@ -95,6 +95,7 @@ def load() -> C.CDLL:
         "xpinn_get_options": (C.c_int, [vp, C.POINTER(Options)]),
         "xpinn_set_options": (C.c_int, [vp, C.POINTER(Options)]),
         "xpinn_iface_values": (C.c_int, [vp, fp, C.POINTER(i64), vp]),
+        "xpinn_phase_times": (C.c_int, [vp, fp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -286,6 +287,12 @@ class Solver:
         o = Options()
         _check(self.lib.xpinn_get_options(self.h, C.byref(o)))
         return {f: getattr(o, f) for f, _ in Options._fields_}
+
+    def phase_times(self):
+        """Device ms of (start, exchange, jet kernel, reduce+Adam) of the last step."""
+        ms = np.zeros(4, np.float32)
+        _check(self.lib.xpinn_phase_times(self.h, ms.ctypes.data))
+        return ms
 
     def set_options(self, **kw):
         cur = self.options()
