@@ -43,6 +43,7 @@ extern "C" {
 #define XPINN_MAX_WIDTH 112   /* neurons per hidden layer */
 #define XPINN_MAX_OUT 3       /* outputs per network */
 #define XPINN_N_TERMS 5       /* loss terms reported per subdomain, see below */
+#define XPINN_NOALLOC_SCRATCH_BYTES (32 << 20)  /* see xpinn_residual_grad_noalloc */
 
 typedef enum {
   XPINN_OK = 0,
@@ -222,6 +223,39 @@ int xpinn_phase_times(xpinn_handle h, float* ms);
  * (normal fluxes f . n for cPINN, residuals F for XPINN).  n_floats receives
  * the size when out is NULL.  Host or device pointer. */
 int xpinn_iface_values(xpinn_handle h, float* out, int64_t* n_floats, void* stream);
+
+/* Residual loss and its gradient for ONE network, allocating no device
+ * memory.  (The paper has no counterpart: this is a deployment convenience.)
+ *
+ * For callers that cannot call cudaMalloc themselves or through this library
+ * -- code that runs inside a host framework whose allocator owns the device,
+ * a runtime with a fixed memory budget, or a region that must not allocate
+ * while it is timed or replayed.  The caller passes device buffers it already
+ * owns; the library's working memory comes from one built-in device array of
+ * XPINN_NOALLOC_SCRATCH_BYTES (32 MiB), which every GPU that loads the
+ * library holds until the library is unloaded.  When the working set of a
+ * request does not fit, the call uses fewer CTAs; if it does not fit even
+ * with one, it is rejected with XPINN_ERR_UNSUPPORTED and a message naming
+ * the size.
+ *
+ * Computes, for pde BURGERS, POISSON or NS (single-network PDEs):
+ *   loss[0]  = MSE_F = (1/n) sum_i |F(u)(xy_i)|^2              (device, 1 float)
+ *   grads    = d (w_res * MSE_F) / d theta, packed like one net (device)
+ * with the network `net` (host struct) and parameters `params` (device,
+ * layer by layer W^k row-major then b^k), points xy [n][2] and forcing f [n]
+ * (device; pass zeros when f = 0: it is required).  It is the residual part
+ * of xpinn_grad for one subdomain.  Asynchronous in `stream`.
+ *
+ * The first call on each device looks up the array's device address (and
+ * raises the jet kernel's shared-memory limit); make that first call before
+ * any stream capture.  Every call reuses the same array and leaves its
+ * contents behind; each call clears what must start at zero itself.  Calls
+ * that overlap on the GPU (other streams, other threads) race on the array:
+ * order them on one stream.  Errors: INVALID, UNSUPPORTED, CUDA; the message
+ * is available from xpinn_last_error(). */
+int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, const xpinn_net_desc* net,
+                                const float* params, const float* xy, const float* f, int64_t n,
+                                float w_res, float* loss, float* grads, void* stream);
 
 #ifdef __cplusplus
 }

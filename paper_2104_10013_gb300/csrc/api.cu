@@ -39,6 +39,14 @@ namespace {
 
 thread_local std::string g_err;
 
+}  // namespace
+
+namespace xp {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace xp
+
+namespace {
+
 struct Error {
   int code;
 };

@@ -96,6 +96,8 @@ def load() -> C.CDLL:
         "xpinn_set_options": (C.c_int, [vp, C.POINTER(Options)]),
         "xpinn_iface_values": (C.c_int, [vp, fp, C.POINTER(i64), vp]),
         "xpinn_phase_times": (C.c_int, [vp, fp]),
+        "xpinn_residual_grad_noalloc": (C.c_int, [i32, C.c_float, C.c_float, C.POINTER(NetDesc), fp, fp, fp,
+                                                  i64, C.c_float, fp, fp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
