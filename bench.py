@@ -192,6 +192,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-loop", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pt", type=int, default=0, help="points per thread in the register tile (0: library default)")
+    ap.add_argument("--items-per-cta", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -217,7 +219,12 @@ def main():
     pb, desc = workload(args.workload)
     n_res = pb.n_res
     s = X.Solver(pb)
-    s.set_options(profile_phases=1)
+    opts = {"profile_phases": 1}
+    if args.pt:
+        opts["points_per_thread"] = args.pt
+    if args.items_per_cta:
+        opts["items_per_cta"] = args.items_per_cta
+    s.set_options(**opts)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
@@ -267,20 +274,21 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": desc, "n_sub": pb.n_sub, "residual_pts_per_step": n_res,
                       "params": pb.n_params, "l2": "flushed (256 MB write) before every timed step",
-                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                      "options": s.options()},
            "adam_steps_per_s": 1e3 / ms_step, "roofline": roof, "gpu_launches": launches_per_step * args.steps,
            "clocks": clk}
 
     # ---- per-subdomain launch loop, same kernels, same GPU
     if not args.no_loop:
-        s.set_options(schedule=1, profile_phases=1)
+        s.set_options(schedule=1)
         for _ in range(3):
             s.step(1, losses=None, stream=stream.cuda_stream)
         lms, ljet = time_steps(torch, s, stream, flush, args.steps)
         lval = n_res * args.steps / (np.sum(lms) / 1e3)
         out["loop"] = {"value": lval, "unit": "pts/s", "ms_per_step": float(np.mean(lms)),
                        "grouped_speedup": (n_res * args.steps / (np.sum(step_ms) / 1e3)) / lval}
-        s.set_options(schedule=0, profile_phases=1)
+        s.set_options(schedule=0)
 
     # ---- end to end through the public API with host buffers
     if not args.no_e2e:

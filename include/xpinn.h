@@ -202,7 +202,8 @@ typedef struct {
                               per subdomain per phase: the baseline) */
   int32_t use_graph;       /* 1: replay steps from a captured CUDA graph */
   int32_t items_per_cta;   /* work items per CTA the scheduler aims for (>= 1) */
-  int32_t points_per_thread; /* points in a thread's register tile (2) */
+  int32_t points_per_thread; /* points in a thread's register tile: 2 (default,
+                              one CTA per SM) or 1 (two CTAs per SM) */
   int32_t profile_phases;  /* 1: record CUDA events between the phases of every
                               step (also inside the graph), see xpinn_phase_times */
 } xpinn_options;
@@ -212,9 +213,10 @@ int xpinn_set_options(xpinn_handle h, const xpinn_options* opt);
 
 /* Device time in milliseconds of the four phases of the most recent step or
  * grad call, measured by CUDA events recorded on the call's stream:
- * ms[0] step start, ms[1] interface exchange launch(es), ms[2] jet kernel
- * launch(es) over residual, data and interface points, ms[3] reduction and
- * Adam.  Requires profile_phases = 1; waits for that step to finish. */
+ * ms[0] step start, ms[1] interface exchange launches (per-subdomain loop
+ * schedule; 0 in the grouped schedule, whose single jet launch does the
+ * exchange too), ms[2] jet kernel launch(es), ms[3] reduction and Adam.
+ * Requires profile_phases = 1; waits for that step to finish. */
 int xpinn_phase_times(xpinn_handle h, float* ms);
 
 /* Interface exchange buffer after the last grad/step: for every interface

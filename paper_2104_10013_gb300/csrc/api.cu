@@ -124,6 +124,7 @@ int k_iface(int pde, int method, int net) {
 struct Plan {
   std::vector<Item> items;       // [0, n_fwd): exchange items; then the main items
   int n_fwd = 0;
+  int first_iface = 0;           // first item that reads the exchange buffer
   std::vector<int> q_items, q_item_begin;
   std::vector<int64_t> q_part_off;
   std::vector<int2> red_blocks;
@@ -238,15 +239,16 @@ int max_hidden_wp(const NetDev& n) {
   return w;
 }
 
-// Points per sub-tile for an item evaluating the nets with K[n] > 0.
-int choose_P(const SubDev& sd, const int K[2], int cap) {
+// Points per sub-tile for an item evaluating the nets with K[n] > 0: enough
+// (neuron group, point group) register tiles to occupy the CTA's threads.
+int choose_P(const SubDev& sd, const int K[2], int cap, int pt) {
   int ng = 1, dk = 0;
   for (int n = 0; n < sd.n_nets; ++n)
     if (K[n]) {
       ng = std::max(ng, max_hidden_wp(sd.net[n]) / MT);
       dk += sd.net[n].w[sd.net[n].L] * K[n];
     }
-  int P = (NT / ng) * 2;
+  int P = (NT / ng) * pt;
   P = std::min(P, 256);
   P = std::min(P, std::max(4, 2048 / std::max(1, dk)));
   P = std::min(P, cap);
@@ -276,7 +278,7 @@ void item_needs(const SubDev& sd, const Item& it, Limits& l) {
 
 size_t smem_of(const Limits& l) {
   StepArgs a{};
-  a.szA = round_up(l.szA, 4);
+  a.szA = round_up(std::max(l.szA, NT * 16), 4);
   a.szW = round_up(l.szW, 4);
   a.szU = round_up(l.szU, 4);
   a.pmax = round_up(l.pmax, 4);
@@ -305,7 +307,7 @@ void build_plan(xpinn_ctx* h, int p_cap) {
     it.n_pts = n;
     it.K[0] = K0;
     it.K[1] = K1;
-    it.P = choose_P(h->subs[q], it.K, p_cap);
+    it.P = choose_P(h->subs[q], it.K, p_cap, h->opt.points_per_thread);
     it.part_off = -1;
     return it;
   };
@@ -353,21 +355,34 @@ void build_plan(xpinn_ctx* h, int p_cap) {
       split(mk(IT_IFACE, q, e, side, f.pt_off, f.n_pts, K0, K1), main_);
     }
   }
+  // Grouped: largest first, but items that read the exchange buffer last (in
+  // one launch they wait for the exchange items, which come first).  Loop:
+  // by subdomain, then the same order.  Within a subdomain both orders agree,
+  // so both schedules sum the gradient slices identically.
   auto order = [&](std::vector<Item>& v) {
+    auto key = [&](const Item& a, const Item& b) {
+      const bool ia = a.kind == IT_IFACE, ib = b.kind == IT_IFACE;
+      if (ia != ib) return ib;
+      return item_cost(h->subs[a.q], a) > item_cost(h->subs[b.q], b);
+    };
     if (h->opt.schedule == 0) {
-      std::stable_sort(v.begin(), v.end(), [&](const Item& a, const Item& b) {
-        return item_cost(h->subs[a.q], a) > item_cost(h->subs[b.q], b);
-      });
+      std::stable_sort(v.begin(), v.end(), key);
     } else {
       std::stable_sort(v.begin(), v.end(), [&](const Item& a, const Item& b) {
         if (a.q != b.q) return a.q < b.q;
-        return item_cost(h->subs[a.q], a) > item_cost(h->subs[b.q], b);
+        return key(a, b);
       });
     }
   };
   order(fwd);
   order(main_);
   pl.n_fwd = (int)fwd.size();
+  pl.first_iface = pl.n_fwd + (int)main_.size();
+  for (size_t i = 0; i < main_.size(); ++i)
+    if (main_[i].kind == IT_IFACE) {
+      pl.first_iface = pl.n_fwd + (int)i;
+      break;
+    }
   pl.items = fwd;
   pl.items.insert(pl.items.end(), main_.begin(), main_.end());
   // gradient slices and per-subdomain item lists (in item order: deterministic)
@@ -414,7 +429,7 @@ Limits limits_of(xpinn_ctx* h, int cap) {
       it.q = q;
       it.K[0] = (net <= 0) ? 5 : 0;
       it.K[1] = (net == 1 || (net < 0 && sd.n_nets > 1)) ? 5 : 0;
-      it.P = choose_P(sd, it.K, cap);
+      it.P = choose_P(sd, it.K, cap, h->opt.points_per_thread);
       item_needs(sd, it, l);
     }
   }
@@ -425,11 +440,12 @@ void size_and_upload_plan(xpinn_ctx* h) {
   const Plan& pl = h->plan;
   const Limits l = limits_of(h, h->p_cap);
   StepArgs& a = h->base;
-  a.szA = round_up(l.szA, 4);
+  a.szA = round_up(std::max(l.szA, NT * 16), 4);   // also the dW split-reduction buffer
   a.szW = round_up(l.szW, 4);
   a.szU = round_up(l.szU, 4);
   a.pmax = round_up(l.pmax, 4);
   a.scratch_per_cta = round_up((int)std::min<int64_t>(l.scratch, 1 << 30), 4);
+  a.pt = h->opt.points_per_thread;
   h->smem = jet_step_smem_bytes(a);
   h->items_d.upload(pl.items.data(), pl.items.size());
   h->q_items_d.upload(pl.q_items.data(), pl.q_items.size());
@@ -439,7 +455,7 @@ void size_and_upload_plan(xpinn_ctx* h) {
   h->partials.alloc((size_t)pl.partial_floats);
   h->loss_part.alloc(2 * pl.items.size());
   h->scratch.alloc((size_t)h->grid * a.scratch_per_cta);
-  h->n_counters = 2 + 2 * h->n_sub;
+  h->n_counters = 3 + 2 * h->n_sub;   // [0] main, [1] spare, [2] exchange done, then loop counters
   h->counters.alloc(h->n_counters);
   ck(cudaMemset(h->counters.p, 0, sizeof(int) * h->n_counters), "memset");
   ck(jet_step_configure(h->smem), "cudaFuncSetAttribute(smem)");
@@ -450,18 +466,31 @@ void size_and_upload_plan(xpinn_ctx* h) {
 }
 
 void plan(xpinn_ctx* h) {
-  int optin = 0;
-  ck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0), "attr");
+  int optin = 0, per_sm = 0;
+  ck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device), "attr");
+  ck(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device), "attr");
+  // one point per thread keeps registers <= 128: aim for two CTAs per SM
+  const int pt = h->opt.points_per_thread;
+  const size_t budget = pt == 1 ? (size_t)per_sm / 2 - 2048 : (size_t)optin - 1024;
   int cap = 256;
   for (;;) {
+    h->grid = h->n_sm * (pt == 1 ? 2 : 1);   // provisional, for item sizes
     build_plan(h, cap);
-    if (smem_of(limits_of(h, cap)) + 1024 <= (size_t)optin || cap <= 8) break;
-    cap -= 8;
+    if (smem_of(limits_of(h, cap)) <= budget || cap <= 8) break;
+    cap -= 4;
   }
   h->p_cap = cap;
   size_and_upload_plan(h);
   if (h->smem + 1024 > (size_t)optin)
     fail(XPINN_ERR_UNSUPPORTED, "networks too wide for shared memory (%zu bytes)", h->smem);
+  const int bps = jet_step_blocks_per_sm(pt, h->smem);
+  if (bps < 1) fail(XPINN_ERR_UNSUPPORTED, "jet kernel does not fit an SM (%zu bytes smem)", h->smem);
+  if (h->n_sm * bps != h->grid) {
+    // re-plan item sizes and scratch for the grid the occupancy allows
+    h->grid = h->n_sm * bps;
+    build_plan(h, cap);
+    size_and_upload_plan(h);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -473,6 +502,9 @@ StepArgs args_for(xpinn_ctx* h, int begin, int count, int counter_idx) {
   a.n_items = count;
   a.item_base = begin;
   a.counter = h->counters.p + counter_idx;
+  a.fwd_done = h->counters.p + 2;
+  a.wait_from = 0;
+  a.n_fwd_wait = 0;
   return a;
 }
 
@@ -509,10 +541,16 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads) {
   r.eps = h->eps;
   r.n_sub = h->n_sub;
   if (h->opt.schedule == 0) {
+    // one launch: exchange items first, interface items last (they wait)
     mark(h, 1, s);
-    if (pl.n_fwd) launch_jet_step(args_for(h, 0, pl.n_fwd, 0), std::min(h->grid, pl.n_fwd), h->smem, s);
     mark(h, 2, s);
-    if (n_main) launch_jet_step(args_for(h, pl.n_fwd, n_main, 1), std::min(h->grid, n_main), h->smem, s);
+    const int n_all = (int)pl.items.size();
+    if (n_all) {
+      StepArgs a = args_for(h, 0, n_all, 0);
+      a.wait_from = pl.first_iface;
+      a.n_fwd_wait = pl.n_fwd;
+      launch_jet_step(a, std::min(h->grid, n_all), h->smem, s);
+    }
     mark(h, 3, s);
     launch_reduce_adam(r, s);
   } else {
@@ -569,6 +607,7 @@ void check_device_error(xpinn_ctx* h, cudaStream_t s) {
   ck(cudaStreamSynchronize(s), "sync");
   if (e) {
     ck(cudaMemsetAsync(h->err_d.p, 0, sizeof(int), s), "reset error flag");
+    if (e == XPINN_ERR_TIMEOUT) fail(XPINN_ERR_TIMEOUT, "a bounded device wait gave up");
     fail(XPINN_ERR_INVALID, "device check failed (code %d)", e);
   }
 }
@@ -605,7 +644,7 @@ void eval_items_for(xpinn_ctx* h, int q, int net, int K, int64_t first, int64_t 
   proto.q = q;
   proto.K[0] = (net == 0 || net < 0) ? K : 0;
   proto.K[1] = (net == 1 || (net < 0 && sd.n_nets > 1)) ? K : 0;
-  proto.P = choose_P(sd, proto.K, h->p_cap);
+  proto.P = choose_P(sd, proto.K, h->p_cap, h->opt.points_per_thread);
   proto.part_off = -1;
   const int64_t per = (int64_t)proto.P * 16;
   for (int64_t s = 0; s < n; s += per) {
@@ -786,7 +825,7 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
   ck(cudaFree(0), "CUDA init");
   ck(cudaGetDevice(&h->device), "cudaGetDevice");
   ck(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, 0), "attr");
-  h->grid = h->n_sm;
+  h->grid = h->n_sm;   // set by plan()
   std::vector<float2> all = pts_res;
   all.insert(all.end(), pts_data.begin(), pts_data.end());
   all.insert(all.end(), pts_if.begin(), pts_if.end());
@@ -873,6 +912,7 @@ int xpinn_grad(xpinn_handle h, float* losses, float* grads, void* stream) {
     copy_out(losses, h->loss_ring.p + (size_t)slot * h->n_sub * XPINN_N_TERMS,
              sizeof(float) * h->n_sub * XPINN_N_TERMS, s);
   if (grads) copy_out(grads, h->grads.p, sizeof(float) * h->n_params, s);
+  check_device_error(h, s);
   API_END
 }
 
@@ -925,6 +965,7 @@ int xpinn_step(xpinn_handle h, int32_t n_steps, float* losses, void* stream) {
     done += chunk;
   }
   ck(cudaGetLastError(), "step");
+  if (losses && !dev_out) check_device_error(h, s);
   if (losses && !dev_out) {
     for (size_t i = 0; i < (size_t)n_steps * row; ++i)
       if (!std::isfinite(losses[i])) fail(XPINN_ERR_NONFINITE, "loss became non-finite");
@@ -1103,7 +1144,8 @@ int xpinn_set_options(xpinn_handle h, const xpinn_options* opt) {
   if (!h || !opt) fail(XPINN_ERR_INVALID, "bad arguments");
   DeviceGuard dg(h);
   if (opt->schedule < 0 || opt->schedule > 1 || opt->items_per_cta < 1 || opt->items_per_cta > 64 ||
-      opt->points_per_thread != 2 || opt->profile_phases < 0 || opt->profile_phases > 1)
+      opt->points_per_thread < 1 || opt->points_per_thread > 2 || opt->profile_phases < 0 ||
+      opt->profile_phases > 1)
     fail(XPINN_ERR_INVALID, "bad options");
   ck(cudaDeviceSynchronize(), "sync");
   h->opt = *opt;

@@ -21,15 +21,34 @@
 //             into the item's private gradient slice.
 //
 // Layer contractions are register-tiled FP32 FFMA loops: a thread owns MT=8
-// neurons x PT=2 points x K jet components; activations live in shared
-// memory laid out [neuron][component][point].
+// neurons x PT points x K jet components (PT = 1 or 2, a template parameter:
+// PT = 1 keeps a thread under 128 registers so that two CTAs share an SM);
+// activations live in shared memory laid out [neuron][component][point].
 #include <cuda_runtime.h>
 
 #include "xpinn_dev.cuh"
 
 namespace xp {
 
-constexpr int PT = 2;
+// loads / stores of PT consecutive points
+template <int PT>
+__device__ __forceinline__ void ldp(const float* p, float (&v)[PT]) {
+  if constexpr (PT == 1) {
+    v[0] = *p;
+  } else {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+  }
+}
+template <int PT>
+__device__ __forceinline__ void stp(float* p, const float (&v)[PT]) {
+  if constexpr (PT == 1) {
+    *p = v[0];
+  } else {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  }
+}
 
 struct Smem {
   float* A;      // activations H^{k} / H^{k-1}      [wp][K][P]
@@ -43,18 +62,26 @@ struct Smem {
   double* red;   // 32 doubles for block reductions
 };
 
-__device__ __forceinline__ Smem carve(const StepArgs& a, int pmax) {
+// Sizes of the shared-memory regions (floats).  Functions that are not
+// inlined receive this by value and rebuild their pointers from the
+// extern __shared__ array, so that the compiler knows they address shared
+// memory (32-bit shared loads and stores, not generic ones).
+struct SmemLayout {
+  int szA, szW, szU, pmax;
+};
+
+__device__ __forceinline__ Smem carve(SmemLayout l) {
   extern __shared__ __align__(16) float sm[];
   Smem s;
   s.A = sm;
-  s.B = s.A + a.szA;
-  s.W = s.B + a.szA;
-  s.U = s.W + a.szW;
-  s.Ub = s.U + a.szU;
-  s.bias = s.Ub + a.szU;
+  s.B = s.A + l.szA;
+  s.W = s.B + l.szA;
+  s.U = s.W + l.szW;
+  s.Ub = s.U + l.szU;
+  s.bias = s.Ub + l.szU;
   s.sx = s.bias + (MAXW + 16);
-  s.sy = s.sx + pmax;
-  s.red = reinterpret_cast<double*>(s.sy + pmax);
+  s.sy = s.sx + l.pmax;
+  s.red = reinterpret_cast<double*>(s.sy + l.pmax);
   return s;
 }
 
@@ -121,8 +148,8 @@ __device__ __forceinline__ float sigmoid_f(float z) {
 // Register-tiled contractions
 // ---------------------------------------------------------------------------
 
-// Z[n][c][p] = sum_j Wt[j][n] A[j][c][p] + (c == 0) b[n], tile n0..n0+7 x p0..p0+1
-template <int K>
+// Z[n][c][p] = sum_j Wt[j][n] A[j][c][p] + (c == 0) b[n], tile n0..n0+7 x p0..p0+PT-1
+template <int K, int PT>
 __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const float* __restrict__ Wt,
                                          const float* __restrict__ bias, int in_p, int out_p, int P,
                                          int n0, int p0, float (&acc)[MT][K][PT]) {
@@ -143,22 +170,20 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const floa
     const float4 wa = *reinterpret_cast<const float4*>(wp + j * out_p);
     const float4 wb = *reinterpret_cast<const float4*>(wp + j * out_p + 4);
     const float w[MT] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-    float2 h[K];
+    float h[K][PT];
 #pragma unroll
-    for (int c = 0; c < K; ++c) h[c] = *reinterpret_cast<const float2*>(ap + (j * K + c) * P);
+    for (int c = 0; c < K; ++c) ldp<PT>(ap + (j * K + c) * P, h[c]);
 #pragma unroll
-    for (int i = 0; i < MT; ++i) {
+    for (int i = 0; i < MT; ++i)
 #pragma unroll
-      for (int c = 0; c < K; ++c) {
-        acc[i][c][0] = fmaf(w[i], h[c].x, acc[i][c][0]);
-        acc[i][c][1] = fmaf(w[i], h[c].y, acc[i][c][1]);
-      }
-    }
+      for (int c = 0; c < K; ++c)
+#pragma unroll
+        for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], h[c][pp], acc[i][c][pp]);
   }
 }
 
-// Hb[j][c][p] = sum_n Wn[n][j] Zb[n][c][p], tile j0..j0+7 x p0..p0+1
-template <int K>
+// Hb[j][c][p] = sum_n Wn[n][j] Zb[n][c][p], tile j0..j0+7 x p0..p0+PT-1
+template <int K, int PT>
 __device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, const float* __restrict__ Wn,
                                          int out_p, int in_p, int P, int j0, int p0,
                                          float (&acc)[MT][K][PT]) {
@@ -175,82 +200,103 @@ __device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, const flo
     const float4 wa = *reinterpret_cast<const float4*>(wp + n * in_p);
     const float4 wb = *reinterpret_cast<const float4*>(wp + n * in_p + 4);
     const float w[MT] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-    float2 zb[K];
+    float zb[K][PT];
 #pragma unroll
-    for (int c = 0; c < K; ++c) zb[c] = *reinterpret_cast<const float2*>(zp + (n * K + c) * P);
+    for (int c = 0; c < K; ++c) ldp<PT>(zp + (n * K + c) * P, zb[c]);
 #pragma unroll
-    for (int i = 0; i < MT; ++i) {
+    for (int i = 0; i < MT; ++i)
 #pragma unroll
-      for (int c = 0; c < K; ++c) {
-        acc[i][c][0] = fmaf(w[i], zb[c].x, acc[i][c][0]);
-        acc[i][c][1] = fmaf(w[i], zb[c].y, acc[i][c][1]);
-      }
-    }
+      for (int c = 0; c < K; ++c)
+#pragma unroll
+        for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], zb[c][pp], acc[i][c][pp]);
   }
 }
 
+// Gradient slices are private to an item: its first sub-tile stores, later
+// sub-tiles add with a reduction that does not wait for the old value.  The
+// same thread owns the same element in every sub-tile, so the additions of
+// one element happen in program order and the result is deterministic.
 __device__ __forceinline__ void accum(float* p, float v, bool first) {
-  *p = first ? v : (*p + v);
+  if (first)
+    *p = v;
+  else
+    atomicAdd(p, v);
 }
 
-// dW[n][j] += sum_{c,p} Zb[n][c][p] H[j][c][p] for n < out_w, j < in_w.
-// Groups of 8 lanes own an 8 x 4 tile and split the (c, p) range between
-// them (interleaved float4 chunks), then reduce with shuffles: a fixed order.
-__device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, const float* __restrict__ H,
-                                         int out_w, int in_w, int KP, float* __restrict__ pW,
-                                         bool first) {
-  const int lane8 = threadIdx.x & 7;
-  const int warp = threadIdx.x >> 5;
-  const int n_tn = (out_w + 7) >> 3, n_tj = (in_w + 3) >> 2;
-  const int n_tiles = n_tn * n_tj;
+// dW[n][j] += sum_{c,p} Zb[n][c][p] H[j][c][p] for n < out_w, j < in_w, with
+// H given transposed, HT[(c*P + p)][j] (row stride RS).  Each thread owns a
+// 4 x 4 tile of dW; narrow layers split the (c, p) range over S threads per
+// tile and reduce the S partial tiles in a fixed order through shared memory
+// (R, at least NT * 16 floats; it may alias HT, which is dead once the
+// contraction is done).  Float4 loads: Zb rows
+// are read as 4 consecutive (c, p), broadcast to the lanes of a tile row;
+// HT rows as 4 consecutive j, contiguous across lanes.
+__device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, const float* __restrict__ HT,
+                                         int RS, int out_p, int in_p, int out_w, int in_w, int KP,
+                                         float* __restrict__ R, float* __restrict__ pW, bool first) {
+  const int tid = threadIdx.x;
+  const int tj_n = in_p >> 2, tn_n = out_p >> 2;
+  const int T = tj_n * tn_n;
+  int S = NT / T;
+  S = S < 1 ? 1 : (S > 16 ? 16 : S);
   const int KP4 = KP >> 2;
-  for (int base = warp * 4; base < n_tiles; base += (NT / 32) * 4) {
-    const int tile = base + ((threadIdx.x >> 3) & 3);
-    const bool valid = tile < n_tiles;
-    const int tn = valid ? tile / n_tj : 0;
-    const int tj = valid ? tile - tn * n_tj : 0;
-    const int n0 = tn * 8, j0 = tj * 4;
-    float acc[8][4];
+  const bool split = S > 1;
+  for (int base = 0; base < T * S; base += NT) {
+    const int u = base + tid;
+    const bool valid = u < T * S;
+    const int tile = valid ? u % T : 0;
+    const int sp = valid ? u / T : 0;
+    const int tn = tile / tj_n, tj = tile - tn * tj_n;
+    const int n0 = tn * 4, j0 = tj * 4;
+    float acc[4][4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.f;
     if (valid) {
       const float4* z4 = reinterpret_cast<const float4*>(Zb + n0 * KP);
-      const float4* h4 = reinterpret_cast<const float4*>(H + j0 * KP);
-      for (int g = lane8; g < KP4; g += 8) {
-        float4 h[4];
+      for (int g = sp; g < KP4; g += S) {
+        float4 z[4];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) h[jj] = h4[jj * KP4 + g];
+        for (int i = 0; i < 4; ++i) z[i] = z4[i * KP4 + g];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float4 z = z4[i * KP4 + g];
+        for (int t = 0; t < 4; ++t) {
+          const float4 h = *reinterpret_cast<const float4*>(HT + (4 * g + t) * RS + j0);
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            acc[i][jj] = fmaf(z.x, h[jj].x, acc[i][jj]);
-            acc[i][jj] = fmaf(z.y, h[jj].y, acc[i][jj]);
-            acc[i][jj] = fmaf(z.z, h[jj].z, acc[i][jj]);
-            acc[i][jj] = fmaf(z.w, h[jj].w, acc[i][jj]);
+          for (int i = 0; i < 4; ++i) {
+            const float zv = t == 0 ? z[i].x : (t == 1 ? z[i].y : (t == 2 ? z[i].z : z[i].w));
+            acc[i][0] = fmaf(zv, h.x, acc[i][0]);
+            acc[i][1] = fmaf(zv, h.y, acc[i][1]);
+            acc[i][2] = fmaf(zv, h.z, acc[i][2]);
+            acc[i][3] = fmaf(zv, h.w, acc[i][3]);
           }
         }
       }
     }
+    if (!split) {
+      if (valid) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        float v = acc[i][jj];
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
-        acc[i][jj] = v;
+          for (int jj = 0; jj < 4; ++jj)
+            if (n0 + i < out_w && j0 + jj < in_w) accum(pW + (n0 + i) * in_w + j0 + jj, acc[i][jj], first);
       }
-    if (valid && lane8 == 0) {
+    } else {
+      __syncthreads();                       // HT / Zb reads of all threads done
+      if (valid) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-          if (n0 + i < out_w && j0 + jj < in_w) accum(pW + (n0 + i) * in_w + j0 + jj, acc[i][jj], first);
+          for (int jj = 0; jj < 4; ++jj) R[(sp * T + tile) * 16 + i * 4 + jj] = acc[i][jj];
+      }
+      __syncthreads();
+      for (int e = tid; e < T * 16; e += NT) {
+        const int tl = e >> 4, q = e & 15, i = q >> 2, jj = q & 3;
+        float v = 0.f;
+        for (int k = 0; k < S; ++k) v += R[(k * T + tl) * 16 + q];
+        const int n = (tl / tj_n) * 4 + i, j = (tl % tj_n) * 4 + jj;
+        if (n < out_w && j < in_w) accum(pW + n * in_w + j, v, first);
+      }
     }
   }
 }
@@ -296,9 +342,11 @@ __device__ __forceinline__ void group_dots(int rows, int len4, const float* __re
 // saved pre-activation jets of every layer in S.
 // S layout: layer 1..L-1: [wp_k][K][P] each, then layer L: [D][K][P].
 // ---------------------------------------------------------------------------
-template <int K>
-__device__ void net_forward(const Smem& s, const NetDev& nd, const float* __restrict__ prm, int P,
-                            float* __restrict__ S, float* __restrict__ Uo) {
+template <int K, int PT>
+__device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm, int P,
+                            float* __restrict__ S, int uoff) {
+  const Smem s = carve(sl);
+  float* __restrict__ Uo = s.U + uoff;
   const int tid = threadIdx.x;
   const int n_pg = P / PT;
   const int L = nd.L;
@@ -347,7 +395,7 @@ __device__ void net_forward(const Smem& s, const NetDev& nd, const float* __rest
     const int n0 = ng * MT, p0 = pg * PT;
     float acc[MT][K][PT];
     if (act) {
-      gemm_fwd<K>(s.A, s.W, s.bias, in_p, out_p, P, n0, p0, acc);
+      gemm_fwd<K, PT>(s.A, s.W, s.bias, in_p, out_p, P, n0, p0, acc);
 #pragma unroll
       for (int i = 0; i < MT; ++i) {
         float sv[K][PT];
@@ -364,8 +412,7 @@ __device__ void net_forward(const Smem& s, const NetDev& nd, const float* __rest
           }
         }
 #pragma unroll
-        for (int c = 0; c < K; ++c)
-          *reinterpret_cast<float2*>(Sk + ((n0 + i) * K + c) * P + p0) = make_float2(sv[c][0], sv[c][1]);
+        for (int c = 0; c < K; ++c) stp<PT>(Sk + ((n0 + i) * K + c) * P + p0, sv[c]);
       }
     }
     __syncthreads();
@@ -373,9 +420,7 @@ __device__ void net_forward(const Smem& s, const NetDev& nd, const float* __rest
 #pragma unroll
       for (int i = 0; i < MT; ++i)
 #pragma unroll
-        for (int c = 0; c < K; ++c)
-          *reinterpret_cast<float2*>(s.A + ((n0 + i) * K + c) * P + p0) =
-              make_float2(acc[i][c][0], acc[i][c][1]);
+        for (int c = 0; c < K; ++c) stp<PT>(s.A + ((n0 + i) * K + c) * P + p0, acc[i][c]);
     }
     __syncthreads();
     Sk += out_p * K * P;
@@ -434,21 +479,47 @@ __device__ __forceinline__ void act_from_saved(float* __restrict__ dst, const fl
   }
 }
 
+// The same, transposed: HT[(c*P + p) * wp + n] (row stride wp), for the
+// weight-gradient contraction.  A thread takes one neuron and 4 points.
+template <int K>
+__device__ __forceinline__ void act_from_saved_T(float* __restrict__ HT, const float* __restrict__ Sk,
+                                                 int wp, int P) {
+  const int P4 = P >> 2;
+  for (int idx = threadIdx.x; idx < wp * P4; idx += NT) {
+    const int n = idx % wp, pq = idx / wp;
+    float4 sv4[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) sv4[c] = *reinterpret_cast<const float4*>(Sk + (n * K + c) * P + 4 * pq);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float sv[K], h[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c)
+        sv[c] = t == 0 ? sv4[c].x : (t == 1 ? sv4[c].y : (t == 2 ? sv4[c].z : sv4[c].w));
+      tanh_jet_from_saved<K>(sv, h);
+#pragma unroll
+      for (int c = 0; c < K; ++c) HT[(c * P + 4 * pq + t) * wp + n] = h[c];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Network reverse pass.  Ub holds the seeds [D][K][P] (overwritten).  The
-// gradient slice pg receives dW^k, db^k at the network's offsets.
+// gradient slice gslice receives dW^k, db^k at the network's offsets.
 // ---------------------------------------------------------------------------
-template <int K>
-__device__ void net_backward(const Smem& s, const NetDev& nd, const float* __restrict__ prm, int P,
-                             const float* __restrict__ S, float* __restrict__ Ub,
+template <int K, int PT>
+__device__ __noinline__ void net_backward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm, int P,
+                             const float* __restrict__ S, int uoff,
                              float* __restrict__ gslice, bool first) {
+  const Smem s = carve(sl);
+  float* __restrict__ Ub = s.Ub + uoff;
   const int tid = threadIdx.x;
   const int n_pg = P / PT;
   const int L = nd.L;
   const int KP = K * P;
-  int soff[MAXL + 1];
-  soff[1] = 0;
-  for (int k = 2; k <= L; ++k) soff[k] = soff[k - 1] + nd.wp[k - 1] * KP;
+  // saved jets of layer L (top), then walk down layer by layer
+  const float* SL = S;
+  for (int k = 1; k < L; ++k) SL += nd.wp[k] * KP;
 
   // ---- output layer
   const int D = nd.w[L], in_w = nd.w[L - 1], in_p = nd.wp[L - 1];
@@ -458,7 +529,7 @@ __device__ void net_backward(const Smem& s, const NetDev& nd, const float* __res
       float z[K], yb[K], zb[K];
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        z[c] = S[soff[L] + (o * K + c) * P + p];
+        z[c] = SL[(o * K + c) * P + p];
         yb[c] = Ub[(o * K + c) * P + p];
       }
       const float g = sigmoid_f(z[0]);
@@ -474,10 +545,10 @@ __device__ void net_backward(const Smem& s, const NetDev& nd, const float* __res
       for (int c = 0; c < K; ++c) Ub[(o * K + c) * P + p] = zb[c];
     }
   }
-  act_from_saved<K>(s.A, S + soff[L - 1], in_p, P);
+  const float* Sk = SL - in_p * KP;   // saved jets of layer L-1
+  act_from_saved<K>(s.A, Sk, in_p, P);
   __syncthreads();
   {
-    const float* WL = prm + nd.off[L];
     float* gW = gslice + nd.off[L];
     float* gb = gW + D * in_w;
     // dW^L[o][j] = sum_{c,p} zb^L[o][c][p] H^{L-1}[j][c][p]
@@ -486,7 +557,6 @@ __device__ void net_backward(const Smem& s, const NetDev& nd, const float* __res
     // db^L[o] = sum_p zb^L[o][0][p]
     group_dots(D, P / 4, Ub, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
                [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
-    (void)WL;
   }
   // h-bar^{L-1} = (W^L)^T zb^L into registers
   float acc[MT][K][PT];
@@ -507,34 +577,29 @@ __device__ void net_backward(const Smem& s, const NetDev& nd, const float* __res
         for (int i = 0; i < MT; ++i) w[i] = (j0 + i < in_w) ? __ldg(WL + o * in_w + j0 + i) : 0.f;
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-          const float2 zb = *reinterpret_cast<const float2*>(Ub + (o * K + c) * P + p0);
+          float zb[PT];
+          ldp<PT>(Ub + (o * K + c) * P + p0, zb);
 #pragma unroll
-          for (int i = 0; i < MT; ++i) {
-            acc[i][c][0] = fmaf(w[i], zb.x, acc[i][c][0]);
-            acc[i][c][1] = fmaf(w[i], zb.y, acc[i][c][1]);
-          }
+          for (int i = 0; i < MT; ++i)
+#pragma unroll
+            for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], zb[pp], acc[i][c][pp]);
         }
       }
     }
   }
   __syncthreads();
 
-  // ---- hidden layers L-1 .. 1
+  // ---- hidden layers L-1 .. 1 (Sk points at the saved jets of layer k)
   for (int k = L - 1; k >= 1; --k) {
     const int out_p = nd.wp[k], out_w = nd.w[k];
     const int ng = tid / n_pg, pg = tid - ng * n_pg;
     const int n0 = ng * MT, p0 = pg * PT;
     if (ng < out_p / MT) {
-      const float* Sk = S + soff[k];
 #pragma unroll
       for (int i = 0; i < MT; ++i) {
         float sv2[K][PT];
 #pragma unroll
-        for (int c = 0; c < K; ++c) {
-          const float2 v = *reinterpret_cast<const float2*>(Sk + ((n0 + i) * K + c) * P + p0);
-          sv2[c][0] = v.x;
-          sv2[c][1] = v.y;
-        }
+        for (int c = 0; c < K; ++c) ldp<PT>(Sk + ((n0 + i) * K + c) * P + p0, sv2[c]);
 #pragma unroll
         for (int pp = 0; pp < PT; ++pp) {
           float sv[K], hb[K], zb[K];
@@ -548,29 +613,27 @@ __device__ void net_backward(const Smem& s, const NetDev& nd, const float* __res
           for (int c = 0; c < K; ++c) acc[i][c][pp] = zb[c];
         }
 #pragma unroll
-        for (int c = 0; c < K; ++c)
-          *reinterpret_cast<float2*>(s.B + ((n0 + i) * K + c) * P + p0) =
-              make_float2(acc[i][c][0], acc[i][c][1]);
+        for (int c = 0; c < K; ++c) stp<PT>(s.B + ((n0 + i) * K + c) * P + p0, acc[i][c]);
       }
     }
     float* gW = gslice + nd.off[k];
     if (k >= 2) {
       const int in_pk = nd.wp[k - 1], in_wk = nd.w[k - 1];
-      act_from_saved<K>(s.A, S + soff[k - 1], in_pk, P);
+      const float* Skm1 = Sk - in_pk * KP;
+      act_from_saved_T<K>(s.A, Skm1, in_pk, P);
       const float* Wk = prm + nd.off[k];
       for (int idx = tid; idx < out_p * in_pk; idx += NT) {
         const int n = idx / in_pk, j = idx - n * in_pk;
         s.W[idx] = (n < out_w && j < in_wk) ? __ldg(Wk + n * in_wk + j) : 0.f;
       }
       __syncthreads();
-      // h-bar^{k-1} = (W^k)^T zb^k
-      const bool act2 = ng < in_pk / MT;
-      if (act2) gemm_bwd<K>(s.B, s.W, out_p, in_pk, P, n0, p0, acc);
-      // dW^k and db^k
-      dW_tiles(s.B, s.A, out_w, in_wk, KP, gW, first);
+      // h-bar^{k-1} = (W^k)^T zb^k into registers, then dW^k and db^k
+      if (ng < in_pk / MT) gemm_bwd<K, PT>(s.B, s.W, out_p, in_pk, P, n0, p0, acc);
       float* gb = gW + out_w * in_wk;
       group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
                  [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
+      dW_tiles(s.B, s.A, in_pk, out_p, in_pk, out_w, in_wk, KP, s.A, gW, first);
+      Sk = Skm1;
     } else {
       __syncthreads();
       // layer 1: dW^1[n][i] = sum_p zb0[n][p] z_i[p] + sum_p zb_{1+i}[n][p]
@@ -582,10 +645,10 @@ __device__ void net_backward(const Smem& s, const NetDev& nd, const float* __res
       __syncthreads();
       if (K > 1)
         group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K + 1; },
-                   [=](int r) { return 0; }, [=](int r, float v) { gW[2 * r] += v; });
+                   [=](int r) { return 0; }, [=](int r, float v) { atomicAdd(gW + 2 * r, v); });
       if (K > 2)
         group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K + 2; },
-                   [=](int r) { return 0; }, [=](int r, float v) { gW[2 * r + 1] += v; });
+                   [=](int r) { return 0; }, [=](int r, float v) { atomicAdd(gW + 2 * r + 1, v); });
       group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
                  [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
     }
@@ -753,25 +816,27 @@ __device__ __forceinline__ void flux_seed(int pde, const PtJets& J, float n0, fl
 // ---------------------------------------------------------------------------
 // Item processing
 // ---------------------------------------------------------------------------
-__device__ void forward_any(int K, const Smem& s, const NetDev& nd, const float* prm, int P, float* S,
-                            float* Uo) {
+template <int PT>
+__device__ void forward_any(int K, SmemLayout sl, const NetDev& nd, const float* prm, int P, float* S,
+                            int uoff) {
   switch (K) {
-    case 1: net_forward<1>(s, nd, prm, P, S, Uo); break;
-    case 2: net_forward<2>(s, nd, prm, P, S, Uo); break;
-    case 3: net_forward<3>(s, nd, prm, P, S, Uo); break;
-    case 4: net_forward<4>(s, nd, prm, P, S, Uo); break;
-    default: net_forward<5>(s, nd, prm, P, S, Uo); break;
+    case 1: net_forward<1, PT>(sl, nd, prm, P, S, uoff); break;
+    case 2: net_forward<2, PT>(sl, nd, prm, P, S, uoff); break;
+    case 3: net_forward<3, PT>(sl, nd, prm, P, S, uoff); break;
+    case 4: net_forward<4, PT>(sl, nd, prm, P, S, uoff); break;
+    default: net_forward<5, PT>(sl, nd, prm, P, S, uoff); break;
   }
 }
 
-__device__ void backward_any(int K, const Smem& s, const NetDev& nd, const float* prm, int P,
-                             const float* S, float* Ub, float* g, bool first) {
+template <int PT>
+__device__ void backward_any(int K, SmemLayout sl, const NetDev& nd, const float* prm, int P,
+                             const float* S, int uoff, float* g, bool first) {
   switch (K) {
-    case 1: net_backward<1>(s, nd, prm, P, S, Ub, g, first); break;
-    case 2: net_backward<2>(s, nd, prm, P, S, Ub, g, first); break;
-    case 3: net_backward<3>(s, nd, prm, P, S, Ub, g, first); break;
-    case 4: net_backward<4>(s, nd, prm, P, S, Ub, g, first); break;
-    default: net_backward<5>(s, nd, prm, P, S, Ub, g, first); break;
+    case 1: net_backward<1, PT>(sl, nd, prm, P, S, uoff, g, first); break;
+    case 2: net_backward<2, PT>(sl, nd, prm, P, S, uoff, g, first); break;
+    case 3: net_backward<3, PT>(sl, nd, prm, P, S, uoff, g, first); break;
+    case 4: net_backward<4, PT>(sl, nd, prm, P, S, uoff, g, first); break;
+    default: net_backward<5, PT>(sl, nd, prm, P, S, uoff, g, first); break;
   }
 }
 
@@ -788,31 +853,180 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
-__device__ void process_item(const StepArgs& a, const Smem& s, const Item& it, int item_idx,
+// Jets of point p from U into J (components beyond a net's K stay 0).
+__device__ __forceinline__ void load_point_jets(const SubDev& sd, const Item& it, const float* U,
+                                                int u1, int P, int p, PtJets& J) {
+#pragma unroll
+  for (int o = 0; o < XPINN_MAX_OUT; ++o)
+#pragma unroll
+    for (int c = 0; c < KMAX; ++c) J.u[o][c] = 0.f;
+#pragma unroll
+  for (int c = 0; c < KMAX; ++c) J.k[c] = 0.f;
+  const int K0 = it.K[0], K1 = it.K[1];
+  const int D0 = sd.net[0].w[sd.net[0].L];
+  if (K0) {
+#pragma unroll
+    for (int o = 0; o < XPINN_MAX_OUT; ++o)
+#pragma unroll
+      for (int c = 0; c < KMAX; ++c)
+        if (o < D0 && c < K0) J.u[o][c] = U[(o * K0 + c) * P + p];
+  }
+  if (K1) {
+#pragma unroll
+    for (int c = 0; c < KMAX; ++c)
+      if (c < K1) J.k[c] = U[u1 + c * P + p];
+  }
+}
+
+__device__ __forceinline__ void store_point_seeds(const SubDev& sd, const Item& it, float* Ub, int u1,
+                                                  int P, int p, const PtJets& G) {
+  const int K0 = it.K[0], K1 = it.K[1];
+  const int D0 = sd.net[0].w[sd.net[0].L];
+  if (K0) {
+#pragma unroll
+    for (int o = 0; o < XPINN_MAX_OUT; ++o)
+#pragma unroll
+      for (int c = 0; c < KMAX; ++c)
+        if (o < D0 && c < K0) Ub[(o * K0 + c) * P + p] = G.u[o][c];
+  }
+  if (K1) {
+#pragma unroll
+    for (int c = 0; c < KMAX; ++c)
+      if (c < K1) Ub[u1 + c * P + p] = G.k[c];
+  }
+}
+
+// Loss terms and seeds of one point (see the kind of item).  Returns the
+// point's contributions to the item's two loss sums in l0, l1.
+__device__ __forceinline__ void point_stage(const StepArgs& a, const SubDev& sd, const Item& it,
+                                            const IfaceDev* ifc, const PtJets& J, PtJets& G, bool valid,
+                                            int64_t gp, int64_t ip, double& l0, double& l1) {
+  const int D0 = sd.net[0].w[sd.net[0].L];
+  switch (it.kind) {
+    case IT_RES: {
+      float r[3] = {0.f, 0.f, 0.f};
+      const float f = valid ? a.res_f[gp] : 0.f;
+      const int ne = residual_fwd(a.pde, J, f, a.nu, a.re, r);
+      float sq = 0.f, e[3] = {0.f, 0.f, 0.f};
+      const float coef = 2.f * sd.w_res * sd.inv_n_res;
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (q < ne) {
+          sq += r[q] * r[q];
+          e[q] = valid ? coef * r[q] : 0.f;
+        }
+      if (valid) l0 += (double)sq * sd.inv_n_res;
+      residual_seed(a.pde, J, e, a.nu, a.re, G);
+      break;
+    }
+    case IT_DATA0: {
+      const float* tg = a.tgt + sd.tgt_off[0] + (gp - sd.data_off[0]) * D0;
+      const float coef = 2.f * sd.w_data[0] * sd.inv_n_data[0];
+      float sq = 0.f;
+#pragma unroll
+      for (int o = 0; o < XPINN_MAX_OUT; ++o)
+        if (o < D0) {
+          const float d = valid ? J.u[o][0] - tg[o] : 0.f;
+          sq += d * d;
+          G.u[o][0] = coef * d;
+        }
+      if (valid) l0 += (double)sq * sd.inv_n_data[0];
+      break;
+    }
+    case IT_DATA1: {
+      const float* tg = a.tgt + sd.tgt_off[1] + (gp - sd.data_off[1]);
+      const float coef = 2.f * sd.w_data[1] * sd.inv_n_data[1];
+      const float d = valid ? J.k[0] - tg[0] : 0.f;
+      G.k[0] = coef * d;
+      if (valid) l0 += (double)(d * d) * sd.inv_n_data[1];
+      break;
+    }
+    case IT_IFACE:
+    case IT_IFACE_FWD: {
+      // solution vector (all outputs of all nets) and exchanged quantity
+      float uv[XPINN_MAX_OUT + 1] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int o = 0; o < XPINN_MAX_OUT; ++o)
+        if (o < D0) uv[o] = J.u[o][0];
+      const int nu_ = D0 + (sd.n_nets > 1 ? 1 : 0);
+      if (sd.n_nets > 1) uv[D0] = J.k[0];
+      float qv[3] = {0.f, 0.f, 0.f};
+      const int nq = ifc->method == XPINN_CPINN
+                         ? flux_fwd(a.pde, J, ifc->nx, ifc->ny, a.nu, a.re, a.flux_mode, qv)
+                         : residual_fwd(a.pde, J, 0.f, a.nu, a.re, qv);
+      if (it.kind == IT_IFACE_FWD) {
+        if (valid) {
+          float* d = a.d4 + (ip * 2 + it.side) * a.d4_nv;
+#pragma unroll
+          for (int v = 0; v < XPINN_MAX_OUT + 1; ++v)
+            if (v < nu_) d[v] = uv[v];
+#pragma unroll
+          for (int v = 0; v < 3; ++v)
+            if (v < nq) d[nu_ + v] = qv[v];
+        }
+        break;
+      }
+      const float* dsrc = a.d4 + (ip * 2 + (1 - it.side)) * a.d4_nv;
+      float d[XPINN_MAX_OUT + 1 + 3];
+#pragma unroll
+      for (int v = 0; v < XPINN_MAX_OUT + 1 + 3; ++v)
+        d[v] = v < a.d4_nv ? __ldcg(dsrc + v) : 0.f;   // written by other CTAs in this launch
+      float sa = 0.f, sf = 0.f;
+      const float ca = sd.w_avg * ifc->inv_n;          // d/du of W_I/N ((u-u')/2)^2
+      const float cf = 2.f * sd.w_iface * ifc->inv_n;
+#pragma unroll
+      for (int o = 0; o < XPINN_MAX_OUT; ++o)
+        if (o < D0) {
+          const float dd = valid ? 0.5f * (uv[o] - d[o]) : 0.f;
+          sa += dd * dd;
+          G.u[o][0] += ca * dd;
+        }
+      if (sd.n_nets > 1) {
+        const float dd = valid ? 0.5f * (uv[D0] - d[D0]) : 0.f;
+        sa += dd * dd;
+        G.k[0] += ca * dd;
+      }
+      float e[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (q < nq) {
+          const float dd = valid ? qv[q] - d[nu_ + q] : 0.f;
+          sf += dd * dd;
+          e[q] = cf * dd;
+        }
+      if (ifc->method == XPINN_CPINN)
+        flux_seed(a.pde, J, ifc->nx, ifc->ny, a.nu, a.re, a.flux_mode, e, G);
+      else
+        residual_seed(a.pde, J, e, a.nu, a.re, G);
+      if (valid) {
+        l0 += (double)sa * ifc->inv_n;
+        l1 += (double)sf * ifc->inv_n;
+      }
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+template <int PT>
+__device__ void process_item(const StepArgs& a, SmemLayout sl, const Item& it, int item_idx,
                              float* __restrict__ scratch) {
+  const Smem s = carve(sl);
   const SubDev& sd = a.subs[it.q];
   const int P = it.P;
   const float* prm = a.params + sd.poff;
   const int tid = threadIdx.x;
   const bool has_bwd = it.kind <= IT_IFACE;
-  // per-net offsets in U / scratch
-  int uoff[MAXNETS];
-  int64_t soff[MAXNETS];
-  {
-    int u = 0;
-    int64_t so = 0;
-    for (int n = 0; n < sd.n_nets; ++n) {
-      uoff[n] = u;
-      soff[n] = so;
-      const NetDev& nd = sd.net[n];
-      const int K = it.K[n];
-      if (K) {
-        u += nd.w[nd.L] * K * P;
-        int64_t rows = 0;
-        for (int k = 1; k < nd.L; ++k) rows += nd.wp[k];
-        so += (rows + nd.w[nd.L]) * K * P;
-      }
-    }
+  // offsets of net 1 in U and in the scratch (net 0 starts at 0)
+  int u1 = 0;
+  int64_t s1 = 0;
+  if (it.K[0]) {
+    const NetDev& nd = sd.net[0];
+    u1 = nd.w[nd.L] * it.K[0] * P;
+    int64_t rows = 0;
+    for (int k = 1; k < nd.L; ++k) rows += nd.wp[k];
+    s1 = (rows + nd.w[nd.L]) * it.K[0] * P;
   }
   const IfaceDev* ifc = (it.kind == IT_IFACE || it.kind == IT_IFACE_FWD) ? &a.ifaces[it.edge] : nullptr;
   double l0 = 0.0, l1 = 0.0;
@@ -827,145 +1041,51 @@ __device__ void process_item(const StepArgs& a, const Smem& s, const Item& it, i
       s.sy[p] = z.y;
     }
     __syncthreads();
-    for (int n = 0; n < sd.n_nets; ++n)
-      if (it.K[n]) forward_any(it.K[n], s, sd.net[n], prm, P, scratch + soff[n], s.U + uoff[n]);
-    // ---- per point: loss terms and seeds
+    if (it.K[0]) forward_any<PT>(it.K[0], sl, sd.net[0], prm, P, scratch, 0);
+    if (it.K[1]) forward_any<PT>(it.K[1], sl, sd.net[1], prm, P, scratch + s1, u1);
+    // ---- per point: loss terms and seeds (or exchange / evaluation output)
     for (int p = tid; p < P; p += NT) {
       const bool valid = p < nv;
       PtJets J, G;
+      load_point_jets(sd, it, s.U, u1, P, p, J);
+      if (it.kind == IT_EVAL) {
+        if (valid) {
+          float* out = a.eval_out + it.out_off + (int64_t)(t0 + p) * a.eval_dout;
+          const float sc = a.eval_scale ? a.eval_scale[it.pt_off + t0 + p] : 1.f;
+          const int K0 = it.K[0], K1 = it.K[1];
+          const int D0 = sd.net[0].w[sd.net[0].L];
+          int col = 0;
+          if (K0) {
+#pragma unroll
+            for (int o = 0; o < XPINN_MAX_OUT; ++o)
+#pragma unroll
+              for (int c = 0; c < KMAX; ++c)
+                if (o < D0 && c < K0) out[col++] = sc * J.u[o][c];
+          }
+          if (K1) {
+#pragma unroll
+            for (int c = 0; c < KMAX; ++c)
+              if (c < K1) out[col++] = sc * J.k[c];
+          }
+        }
+        continue;
+      }
 #pragma unroll
       for (int o = 0; o < XPINN_MAX_OUT; ++o)
 #pragma unroll
-        for (int c = 0; c < KMAX; ++c) { J.u[o][c] = 0.f; G.u[o][c] = 0.f; }
+        for (int c = 0; c < KMAX; ++c) G.u[o][c] = 0.f;
 #pragma unroll
-      for (int c = 0; c < KMAX; ++c) { J.k[c] = 0.f; G.k[c] = 0.f; }
-      for (int n = 0; n < sd.n_nets; ++n) {
-        const int K = it.K[n];
-        if (!K) continue;
-        const int D = sd.net[n].w[sd.net[n].L];
-        const float* Un = s.U + uoff[n];
-        for (int o = 0; o < D; ++o)
-          for (int c = 0; c < K; ++c) {
-            const float v = Un[(o * K + c) * P + p];
-            if (n == 0) J.u[o][c] = v; else J.k[c] = v;
-          }
-      }
+      for (int c = 0; c < KMAX; ++c) G.k[c] = 0.f;
       const int64_t gp = it.pt_off + t0 + p;   // global point index
-      switch (it.kind) {
-        case IT_RES: {
-          float r[3];
-          const float f = valid ? a.res_f[gp] : 0.f;
-          const int ne = residual_fwd(a.pde, J, f, a.nu, a.re, r);
-          float sq = 0.f, e[3] = {0.f, 0.f, 0.f};
-          const float coef = 2.f * sd.w_res * sd.inv_n_res;
-          for (int q = 0; q < ne; ++q) { sq += r[q] * r[q]; e[q] = valid ? coef * r[q] : 0.f; }
-          if (valid) l0 += (double)sq * sd.inv_n_res;
-          residual_seed(a.pde, J, e, a.nu, a.re, G);
-          break;
-        }
-        case IT_DATA0:
-        case IT_DATA1: {
-          const int n = it.kind - IT_DATA0;
-          const int D = sd.net[n].w[sd.net[n].L];
-          const float* tg = a.tgt + sd.tgt_off[n] + (gp - sd.data_off[n]) * D;
-          const float coef = 2.f * sd.w_data[n] * sd.inv_n_data[n];
-          float sq = 0.f;
-          for (int o = 0; o < D; ++o) {
-            const float u = n == 0 ? J.u[o][0] : J.k[0];
-            const float d = valid ? u - tg[o] : 0.f;
-            sq += d * d;
-            if (n == 0) G.u[o][0] = coef * d; else G.k[0] = coef * d;
-          }
-          if (valid) l0 += (double)sq * sd.inv_n_data[n];
-          break;
-        }
-        case IT_IFACE:
-        case IT_IFACE_FWD: {
-          // solution vector and exchanged quantity of this side
-          float uv[4];
-          int nu_ = 0;
-          const int D0 = sd.net[0].w[sd.net[0].L];
-          for (int o = 0; o < D0; ++o) uv[nu_++] = J.u[o][0];
-          if (sd.n_nets > 1) uv[nu_++] = J.k[0];
-          float qv[3];
-          int nq;
-          if (ifc->method == XPINN_CPINN)
-            nq = flux_fwd(a.pde, J, ifc->nx, ifc->ny, a.nu, a.re, a.flux_mode, qv);
-          else
-            nq = residual_fwd(a.pde, J, 0.f, a.nu, a.re, qv);
-          const int64_t ip = ifc->d4_pt + (it.pt_off - ifc->pt_off) + t0 + p;
-          if (it.kind == IT_IFACE_FWD) {
-            if (valid) {
-              float* d = a.d4 + (ip * 2 + it.side) * a.d4_nv;
-              for (int v = 0; v < nu_; ++v) d[v] = uv[v];
-              for (int v = 0; v < nq; ++v) d[nu_ + v] = qv[v];
-            }
-            break;
-          }
-          const float* d = a.d4 + (ip * 2 + (1 - it.side)) * a.d4_nv;
-          float sa = 0.f, sf = 0.f;
-          const float ca = sd.w_avg * ifc->inv_n;          // d/du of W_I/N ((u-u')/2)^2
-          const float cf = 2.f * sd.w_iface * ifc->inv_n;
-          int v = 0;
-          for (int o = 0; o < D0; ++o, ++v) {
-            const float dd = valid ? 0.5f * (uv[v] - d[v]) : 0.f;
-            sa += dd * dd;
-            G.u[o][0] += ca * dd;
-          }
-          if (sd.n_nets > 1) {
-            const float dd = valid ? 0.5f * (uv[v] - d[v]) : 0.f;
-            sa += dd * dd;
-            G.k[0] += ca * dd;
-          }
-          float e[3] = {0.f, 0.f, 0.f};
-          for (int q = 0; q < nq; ++q) {
-            const float dd = valid ? qv[q] - d[nu_ + q] : 0.f;
-            sf += dd * dd;
-            e[q] = cf * dd;
-          }
-          if (ifc->method == XPINN_CPINN)
-            flux_seed(a.pde, J, ifc->nx, ifc->ny, a.nu, a.re, a.flux_mode, e, G);
-          else
-            residual_seed(a.pde, J, e, a.nu, a.re, G);
-          if (valid) {
-            l0 += (double)sa * ifc->inv_n;
-            l1 += (double)sf * ifc->inv_n;
-          }
-          break;
-        }
-        default: {   // IT_EVAL
-          if (valid) {
-            float* out = a.eval_out + it.out_off + (int64_t)(t0 + p) * a.eval_dout;
-            const float sc = a.eval_scale ? a.eval_scale[it.pt_off + t0 + p] : 1.f;
-            int col = 0;
-            for (int n = 0; n < sd.n_nets; ++n) {
-              const int K = it.K[n];
-              if (!K) continue;
-              const int D = sd.net[n].w[sd.net[n].L];
-              for (int o = 0; o < D; ++o)
-                for (int c = 0; c < K; ++c) out[col++] = sc * (n == 0 ? J.u[o][c] : J.k[c]);
-            }
-          }
-          break;
-        }
-      }
-      if (has_bwd) {
-        for (int n = 0; n < sd.n_nets; ++n) {
-          const int K = it.K[n];
-          if (!K) continue;
-          const int D = sd.net[n].w[sd.net[n].L];
-          float* Ubn = s.Ub + uoff[n];
-          for (int o = 0; o < D; ++o)
-            for (int c = 0; c < K; ++c) Ubn[(o * K + c) * P + p] = n == 0 ? G.u[o][c] : G.k[c];
-        }
-      }
+      const int64_t ip = ifc ? ifc->d4_pt + (it.pt_off - ifc->pt_off) + t0 + p : 0;
+      point_stage(a, sd, it, ifc, J, G, valid, gp, ip, l0, l1);
+      if (has_bwd) store_point_seeds(sd, it, s.Ub, u1, P, p, G);
     }
     __syncthreads();
     if (has_bwd) {
       float* gs = a.partials + it.part_off;
-      for (int n = 0; n < sd.n_nets; ++n)
-        if (it.K[n])
-          backward_any(it.K[n], s, sd.net[n], prm, P, scratch + soff[n], s.Ub + uoff[n], gs, first);
+      if (it.K[0]) backward_any<PT>(it.K[0], sl, sd.net[0], prm, P, scratch, 0, gs, first);
+      if (it.K[1]) backward_any<PT>(it.K[1], sl, sd.net[1], prm, P, scratch + s1, u1, gs, first);
       // a net that is not evaluated by this item contributes zero gradient
       if (first)
         for (int n = 0; n < sd.n_nets; ++n)
@@ -988,8 +1108,36 @@ __device__ void process_item(const StepArgs& a, const Smem& s, const Item& it, i
   }
 }
 
-__global__ void __launch_bounds__(NT, 1) jet_step_kernel(StepArgs a) {
-  const Smem s = carve(a, a.pmax);
+// PT = 1 keeps registers <= 128 so that two CTAs fit on an SM; PT = 2 uses
+// a larger register tile at one CTA per SM.
+// Wait (thread 0) until `need` exchange items have completed.  Every exchange
+// item is claimed before any item that waits, and exchange items never wait,
+// so the wait ends; it is still bounded: after about 4 s it sets the error
+// flag and returns false, and the item is skipped.
+__device__ bool wait_exchange(const StepArgs& a) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned ns = 32;
+    for (long it = 0; atomicAdd(a.fwd_done, 0) < a.n_fwd_wait; ++it) {
+      if (it > (1l << 22)) {
+        atomicCAS(a.err, 0, XPINN_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 1024) ns <<= 1;
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int PT>
+__global__ void __launch_bounds__(NT, PT == 1 ? 2 : 1) jet_step_kernel(StepArgs a) {
+  const SmemLayout sl{a.szA, a.szW, a.szU, a.pmax};
   __shared__ int s_item;
   float* scratch = a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
   for (;;) {
@@ -998,7 +1146,16 @@ __global__ void __launch_bounds__(NT, 1) jet_step_kernel(StepArgs a) {
     const int it = s_item;
     __syncthreads();
     if (it >= a.n_items) break;
-    process_item(a, s, a.items[it], a.item_base + it, scratch);
+    if (a.n_fwd_wait > 0 && it >= a.wait_from && !wait_exchange(a)) continue;
+    const Item& item = a.items[it];
+    process_item<PT>(a, sl, item, a.item_base + it, scratch);
+    if (item.kind == IT_IFACE_FWD && a.n_fwd_wait > 0) {
+      __syncthreads();                      // every thread's exchange stores issued
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(a.fwd_done, 1);
+      }
+    }
   }
 }
 
@@ -1008,11 +1165,28 @@ size_t jet_step_smem_bytes(const StepArgs& a) {
 }
 
 cudaError_t jet_step_configure(size_t smem) {
-  return cudaFuncSetAttribute(jet_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(jet_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(jet_step_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int jet_step_blocks_per_sm(int pt, size_t smem) {
+  int n = 0;
+  const cudaError_t e = pt == 1
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<1>, NT, smem)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<2>, NT, smem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 void launch_jet_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
-  jet_step_kernel<<<grid, NT, smem, s>>>(a);
+  if (a.pt == 1)
+    jet_step_kernel<1><<<grid, NT, smem, s>>>(a);
+  else
+    jet_step_kernel<2><<<grid, NT, smem, s>>>(a);
 }
 
 }  // namespace xp

@@ -92,6 +92,9 @@ struct StepArgs {
   int n_items;
   int item_base;         // index of items[0] in the plan (loss_part slots)
   int* counter;          // work counter of this launch (reset before it)
+  int* fwd_done;         // exchange items completed in this launch
+  int wait_from;         // items from this index on read the exchange buffer:
+  int n_fwd_wait;        // they wait until n_fwd_wait exchange items are done (0: no wait)
   const SubDev* subs;
   const IfaceDev* ifaces;
   const float* params;
@@ -112,6 +115,7 @@ struct StepArgs {
   // smem plan (floats)
   int szA, szW, szU;
   int pmax;              // largest sub-tile of any item
+  int pt;                // points per thread in the register tile (1 or 2)
   // eval
   const float2* eval_pts;
   float* eval_out;
@@ -124,6 +128,7 @@ struct StepArgs {
 void launch_jet_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
 size_t jet_step_smem_bytes(const StepArgs& a);
 cudaError_t jet_step_configure(size_t smem);
+int jet_step_blocks_per_sm(int pt, size_t smem);
 
 struct ReduceArgs {
   const int2* blocks;        // (subdomain, first param) of each CTA
