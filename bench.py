@@ -45,6 +45,9 @@ def workload(name):
         return P.burgers_cpinn(), "cPINN Burgers, 4 x-slabs, 2->20x3->1, 1000 residual pts each"
     if name == "c3":
         return P.kovasznay_cpinn(), "cPINN Kovasznay NS Re=40, 8x8 grid, 2->64x6->3, 50k residual pts each"
+    if name == "c4":
+        return P.diffusion_xpinn(), ("XPINN inverse diffusion on a star polygon, 10 Voronoi regions x 256 copies, "
+                                     "u: 2->40x5->1, K: 2->20x4->1 softplus, 30k residual pts per region")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -126,6 +129,76 @@ def time_steps(torch, s, stream, flush, steps):
     return step_ms, jet_ms
 
 
+def serving(X, solver_c2, n_req, max_query, seed=0):
+    """Continuous-batching server over three trained models (Burgers cPINN,
+    the benchmark's Poisson XPINN, Kovasznay cPINN with 2k points per
+    subdomain): Poisson arrivals at 70% of the closed-loop capacity, a mix of
+    evaluation queries (log-uniform 1..max_query points, derivative order
+    0-2) and training-step requests (one step of a whole model)."""
+    from paper_2104_10013_gb300 import problems as P
+    rng = np.random.default_rng(seed)
+    pbs = [P.burgers_cpinn(), None, P.kovasznay_cpinn(n_res=2000)]
+    models = [X.Solver(pbs[0]), solver_c2, X.Solver(pbs[2])]
+    pbs[1] = solver_c2.pb
+    for m in (models[0], models[2]):
+        m.step(20, losses=None)                       # "trained" models
+    boxes = [(pb.meta["xcuts"][0], pb.meta["xcuts"][-1], pb.meta["ycuts"][0], pb.meta["ycuts"][-1])
+             for pb in pbs]
+
+    def make():
+        m = int(rng.integers(0, 3))
+        if rng.random() < 0.2:
+            return ("step", m, None, None, pbs[m].n_res)
+        n = int(10 ** rng.uniform(0, np.log10(max_query)))
+        x0, x1, y0, y1 = boxes[m]
+        xy = np.stack([rng.uniform(x0, x1, n), rng.uniform(y0, y1, n)], 1).astype(np.float32)
+        return ("eval", m, xy, int(rng.integers(0, 3)), n)
+
+    def submit(srv, r):
+        return srv.submit_step(r[1], 1) if r[0] == "step" else srv.submit_eval(r[1], r[2], r[3])
+
+    srv = X.Server(models, hbm_budget=4 << 30)
+    # closed-loop capacity: keep 8 requests in flight
+    cap_reqs = [make() for _ in range(max(40, n_req // 5))]
+    t0 = time.perf_counter()
+    inflight, k = [], 0
+    while k < len(cap_reqs) or inflight:
+        while k < len(cap_reqs) and len(inflight) < 8:
+            inflight.append(submit(srv, cap_reqs[k])); k += 1
+        srv.wait(inflight.pop(0))
+    cap = len(cap_reqs) / (time.perf_counter() - t0)
+    lam = 0.7 * cap
+    reqs = [make() for _ in range(n_req)]
+    gaps = rng.exponential(1.0 / lam, n_req)
+    tickets = []
+    t_start = time.perf_counter()
+    t_next = t_start
+    for r, g in zip(reqs, gaps):
+        t_next += g
+        while time.perf_counter() < t_next:
+            time.sleep(min(1e-4, max(0.0, t_next - time.perf_counter())))
+        tickets.append((r, submit(srv, r)))
+    res = [(r, srv.wait(t)) for r, t in tickets]
+    wall = time.perf_counter() - t_start
+    srv.close()
+    for m in (models[0], models[2]):
+        m.close()
+    lat = np.array([x["latency_ms"] for _, x in res])
+    ev = np.array([x["latency_ms"] for r, x in res if r[0] == "eval"])
+    stp = np.array([x["latency_ms"] for r, x in res if r[0] == "step"])
+    pts = sum(r[4] for r, _ in res)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "eval_p50_ms": float(np.percentile(ev, 50)), "eval_p99_ms": float(np.percentile(ev, 99)),
+            "step_p50_ms": float(np.percentile(stp, 50)) if len(stp) else None,
+            "step_p99_ms": float(np.percentile(stp, 99)) if len(stp) else None,
+            "sustained_pts_per_s": pts / wall, "requests": n_req,
+            "arrival_rate_per_s": lam, "capacity_req_per_s": cap,
+            "max_batch": int(max(x["batch"] for _, x in res)),
+            "mix": f"80% evaluation queries (log-uniform 1..{max_query} pts, order 0-2), 20% one-step "
+                   "training requests, over Burgers cPINN / Poisson XPINN / Kovasznay cPINN models; "
+                   "Poisson arrivals at 70% of closed-loop capacity"}
+
+
 def cpu_baseline(pb, seconds):
     """The FP64 oracle, as it stands, on this host's cores: gradients of whole
     subdomains of the same workload in turn until `seconds` have passed."""
@@ -194,6 +267,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pt", type=int, default=0, help="points per thread in the register tile (0: library default)")
     ap.add_argument("--items-per-cta", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=400)
+    ap.add_argument("--serving-max-query", type=int, default=100000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -225,6 +302,12 @@ def main():
     if args.items_per_cta:
         opts["items_per_cta"] = args.items_per_cta
     s.set_options(**opts)
+    tune = None
+    if not args.no_autotune and not args.pt and not args.items_per_cta:
+        t0 = time.perf_counter()
+        tune = s.autotune(steps=5)
+        tune["seconds"] = time.perf_counter() - t0
+        s.set_options(profile_phases=1)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
@@ -275,7 +358,7 @@ def main():
            "config": {"workload": desc, "n_sub": pb.n_sub, "residual_pts_per_step": n_res,
                       "params": pb.n_params, "l2": "flushed (256 MB write) before every timed step",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                      "options": s.options()},
+                      "options": s.options(), "autotune": tune},
            "adam_steps_per_s": 1e3 / ms_step, "roofline": roof, "gpu_launches": launches_per_step * args.steps,
            "clocks": clk}
 
@@ -308,6 +391,9 @@ def main():
                       "h2d_bytes_per_step": int(xy.numel() * 4 + f.numel() * 4),
                       "d2h_bytes_per_step": int(losses.numel() * 4),
                       "ms_per_step": 1e3 * e2e_s / args.steps}
+
+    if not args.no_serving and args.workload == "c2":
+        out["serving"] = serving(X, s, args.serving_requests, args.serving_max_query)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(pb, args.cpu_seconds)

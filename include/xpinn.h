@@ -206,10 +206,20 @@ typedef struct {
                               one CTA per SM) or 1 (two CTAs per SM) */
   int32_t profile_phases;  /* 1: record CUDA events between the phases of every
                               step (also inside the graph), see xpinn_phase_times */
+  int32_t max_points_per_tile; /* cap on the points a CTA processes at once
+                                  (0: as many as the register tiles allow) */
 } xpinn_options;
 
 int xpinn_get_options(xpinn_handle h, xpinn_options* opt);
 int xpinn_set_options(xpinn_handle h, const xpinn_options* opt);
+
+/* Autotuner: times `steps` gradient passes (no parameter update) for each
+ * candidate of points_per_thread {2, 1} x items_per_cta {2, 4, 8, 16} x
+ * max_points_per_tile {0, 128, 64, 32} with the grouped schedule, keeps the
+ * fastest, applies it and returns it in *best (and its median ms per pass
+ * in *best_ms).  Candidates that do not fit shared memory are skipped.
+ * Parameters, Adam state and step count are unchanged.  Synchronises. */
+int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* best_ms);
 
 /* Device time in milliseconds of the four phases of the most recent step or
  * grad call, measured by CUDA events recorded on the call's stream:
@@ -225,6 +235,57 @@ int xpinn_phase_times(xpinn_handle h, float* ms);
  * (normal fluxes f . n for cPINN, residuals F for XPINN).  n_floats receives
  * the size when out is NULL.  Host or device pointer. */
 int xpinn_iface_values(xpinn_handle h, float* out, int64_t* n_floats, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of evaluation and training-step requests over
+ * several models (handles).  A dispatcher admits requests in arrival order
+ * while the device memory of the admitted requests fits `hbm_budget` bytes;
+ * each model has a worker thread and a CUDA stream, so the work of different
+ * models overlaps on the GPU.  A worker takes every admitted request of its
+ * model that is waiting: consecutive evaluation requests with the same copy
+ * and derivative order are stitched (Eq. FSol) in one routed launch, step
+ * requests run xpinn_step on the model in arrival order.  Each point's value
+ * does not depend on the other points of a batch, so a request's result is
+ * the same alone and in a mix (bitwise).  All request buffers are host
+ * memory, owned by the caller until the request completes.
+ * ------------------------------------------------------------------------- */
+enum { XPINN_REQ_EVAL = 0, XPINN_REQ_STEP = 1 };
+enum { XPINN_PENDING = 1 };   /* xpinn_server_poll: not finished yet */
+
+typedef struct {
+  int32_t kind;       /* XPINN_REQ_EVAL or XPINN_REQ_STEP */
+  int32_t model;      /* index into the server's models */
+  int32_t copy;       /* EVAL: copy (model) inside the handle, as xpinn_eval */
+  int32_t order;      /* EVAL: derivative order 0..2 */
+  int64_t n;          /* EVAL: points */
+  const float* xy;    /* EVAL: [n][2] host */
+  float* out;         /* EVAL: [n][D_out_total][K] host, as xpinn_eval */
+  int32_t n_steps;    /* STEP: training steps */
+  float* losses;      /* STEP: [n_steps][n_sub][5] host, or NULL */
+} xpinn_request;
+
+typedef struct {
+  int32_t status;     /* xpinn_status of the request */
+  double queue_ms;    /* submit -> admitted */
+  double latency_ms;  /* submit -> completed */
+  int32_t batch;      /* number of requests served in the same launch */
+  char error[160];    /* message when status != XPINN_OK */
+} xpinn_result;
+
+typedef struct xpinn_server xpinn_server;
+
+/* models: handles that outlive the server (not owned).  hbm_budget: bytes of
+ * request buffers (points, routing entries, outputs) allowed in flight. */
+int xpinn_server_create(const xpinn_handle* models, int32_t n_models, size_t hbm_budget,
+                        xpinn_server** out);
+/* Non-blocking.  *ticket identifies the request.  XPINN_ERR_OOM if the
+ * request alone exceeds hbm_budget (it could never be admitted). */
+int xpinn_server_submit(xpinn_server* s, const xpinn_request* req, uint64_t* ticket);
+/* XPINN_OK with *res filled once the request is finished (the ticket is then
+ * released), XPINN_PENDING before, XPINN_ERR_INVALID for an unknown ticket. */
+int xpinn_server_poll(xpinn_server* s, uint64_t ticket, xpinn_result* res);
+/* Waits for every submitted request, stops the workers, frees the server. */
+int xpinn_server_destroy(xpinn_server* s);
 
 /* Residual loss and its gradient for ONE network, allocating no device
  * memory.  (The paper has no counterpart: this is a deployment convenience.)

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libxpinn.so")
-SOURCES = ["jet_step.cu", "reduce_adam.cu", "route.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["jet_step.cu", "reduce_adam.cu", "route.cu", "api.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

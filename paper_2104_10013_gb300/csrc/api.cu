@@ -164,7 +164,7 @@ struct xpinn_ctx {
   int n_sm = 0, grid = 0;
   int ring_cap = 256;
   int host_t = 0, host_slot = 0;
-  xpinn_options opt{0, 1, 4, 2, 0};
+  xpinn_options opt{0, 1, 4, 2, 0, 0};
   int device = 0;
   cudaEvent_t ev[5] = {};
   cudaStream_t cap_stream = nullptr;
@@ -183,6 +183,14 @@ struct xpinn_ctx {
   int* step_t() { return state_i.p; }
   int* loss_slot() { return state_i.p + 1; }
 };
+
+// Read-only facts of a handle for the request server.
+namespace xp {
+int ctx_out_total(xpinn_handle h) { return h->n_out_total; }
+int ctx_n_sub(xpinn_handle h) { return h->n_sub; }
+int ctx_n_copies(xpinn_handle h) { return h->n_sub / h->spm; }
+int ctx_device(xpinn_handle h) { return h->device; }
+}  // namespace xp
 
 namespace {
 
@@ -458,7 +466,14 @@ void size_and_upload_plan(xpinn_ctx* h) {
   h->n_counters = 3 + 2 * h->n_sub;   // [0] main, [1] spare, [2] exchange done, then loop counters
   h->counters.alloc(h->n_counters);
   ck(cudaMemset(h->counters.p, 0, sizeof(int) * h->n_counters), "memset");
-  ck(jet_step_configure(h->smem), "cudaFuncSetAttribute(smem)");
+  // The limit is a property of the kernel, shared by every handle: raise it to
+  // the device maximum (never to this handle's own need, which could lower it
+  // below what another handle launches with).
+  {
+    int optin = 0;
+    ck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device), "attr");
+    ck(jet_step_configure((size_t)optin - 1024), "cudaFuncSetAttribute(smem)");
+  }
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -472,7 +487,7 @@ void plan(xpinn_ctx* h) {
   // one point per thread keeps registers <= 128: aim for two CTAs per SM
   const int pt = h->opt.points_per_thread;
   const size_t budget = pt == 1 ? (size_t)per_sm / 2 - 2048 : (size_t)optin - 1024;
-  int cap = 256;
+  int cap = h->opt.max_points_per_tile > 0 ? std::min(256, std::max(8, h->opt.max_points_per_tile)) : 256;
   for (;;) {
     h->grid = h->n_sm * (pt == 1 ? 2 : 1);   // provisional, for item sizes
     build_plan(h, cap);
@@ -672,6 +687,18 @@ struct DeviceGuard {
     if (prev >= 0) cudaSetDevice(prev);
   }
 };
+
+// Re-plan the step for new options (items, shared memory, scratch).
+void apply_options(xpinn_ctx* h, const xpinn_options& o) {
+  h->opt = o;
+  if (h->opt.profile_phases)
+    for (auto& e : h->ev)
+      if (!e) ck(cudaEventCreate(&e), "cudaEventCreate");
+  plan(h);
+  h->base.partials = h->partials.p;
+  h->base.loss_part = h->loss_part.p;
+  h->base.scratch = h->scratch.p;
+}
 
 // ===========================================================================
 // C ABI
@@ -1145,17 +1172,79 @@ int xpinn_set_options(xpinn_handle h, const xpinn_options* opt) {
   DeviceGuard dg(h);
   if (opt->schedule < 0 || opt->schedule > 1 || opt->items_per_cta < 1 || opt->items_per_cta > 64 ||
       opt->points_per_thread < 1 || opt->points_per_thread > 2 || opt->profile_phases < 0 ||
-      opt->profile_phases > 1)
+      opt->profile_phases > 1 || opt->max_points_per_tile < 0)
     fail(XPINN_ERR_INVALID, "bad options");
   ck(cudaDeviceSynchronize(), "sync");
-  h->opt = *opt;
-  if (h->opt.profile_phases)
-    for (auto& e : h->ev)
-      if (!e) ck(cudaEventCreate(&e), "cudaEventCreate");
-  plan(h);
-  h->base.partials = h->partials.p;
-  h->base.loss_part = h->loss_part.p;
-  h->base.scratch = h->scratch.p;
+  apply_options(h, *opt);
+  API_END
+}
+
+int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* best_ms) {
+  API_BEGIN
+  if (!h || steps < 1 || !best) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  ck(cudaDeviceSynchronize(), "sync");
+  const xpinn_options orig = h->opt;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ck(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
+  ck(cudaEventCreate(&e0), "event");
+  ck(cudaEventCreate(&e1), "event");
+  xpinn_options win = orig;
+  float win_ms = 3.4e38f;
+  try {
+    for (int pt : {2, 1})
+      for (int ipc : {2, 4, 8, 16})
+        for (int cap : {0, 128, 64, 32}) {
+          xpinn_options c = orig;
+          c.schedule = 0;
+          c.points_per_thread = pt;
+          c.items_per_cta = ipc;
+          c.max_points_per_tile = cap;
+          c.profile_phases = 0;
+          try {
+            apply_options(h, c);
+          } catch (const Error&) {
+            continue;   // does not fit: skip
+          }
+          for (int w = 0; w < 2; ++w) {
+            enqueue_step(h, s, false, h->grads.p);
+            h->host_slot += 1;
+          }
+          std::vector<float> t;
+          for (int i = 0; i < steps; ++i) {
+            ck(cudaEventRecord(e0, s), "event");
+            enqueue_step(h, s, false, h->grads.p);
+            h->host_slot += 1;
+            ck(cudaEventRecord(e1, s), "event");
+            ck(cudaEventSynchronize(e1), "event sync");
+            float ms = 0;
+            ck(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+            t.push_back(ms);
+          }
+          std::sort(t.begin(), t.end());
+          const float med = t[t.size() / 2];
+          if (med < win_ms) {
+            win_ms = med;
+            win = c;
+          }
+        }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    apply_options(h, orig);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  win.schedule = orig.schedule;
+  win.use_graph = orig.use_graph;
+  win.profile_phases = orig.profile_phases;
+  apply_options(h, win);
+  *best = h->opt;
+  if (best_ms) *best_ms = win_ms;
   API_END
 }
 

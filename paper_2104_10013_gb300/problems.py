@@ -387,3 +387,161 @@ def kovasznay_cpinn(nx=8, ny=8, n_res=50000, n_iface=256, n_bc=80, width=64, dep
     ifaces = _grid_interfaces(xc, yc, lambda e: _rng(seed, 24, e), n_iface, CPINN)
     return Problem("kovasznay_cpinn", PDE_NS, subs, ifaces, re=re,
                    meta=dict(xcuts=xc.tolist(), ycuts=yc.tolist()))
+
+
+# ---------------------------------------------------------------------------
+# Irregular geometry: a star polygon split into clipped Voronoi regions
+# ---------------------------------------------------------------------------
+
+def star_polygon(rng, n_vert=14, r_min=0.55, r_max=1.0, center=(1.0, 1.0)):
+    """Vertices (counter-clockwise) of a seeded star-shaped, usually
+    non-convex polygon."""
+    ang = np.sort(rng.uniform(0, 2 * np.pi, n_vert))
+    rad = rng.uniform(r_min, r_max, n_vert)
+    return np.stack([center[0] + rad * np.cos(ang), center[1] + rad * np.sin(ang)], 1)
+
+
+def in_polygon(xy, poly) -> np.ndarray:
+    """Even-odd rule point-in-polygon test for points xy [n, 2]."""
+    x, y = xy[:, 0][:, None], xy[:, 1][:, None]
+    x0, y0 = poly[:, 0][None, :], poly[:, 1][None, :]
+    x1, y1 = np.roll(poly[:, 0], -1)[None, :], np.roll(poly[:, 1], -1)[None, :]
+    cond = (y0 > y) != (y1 > y)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        xc = x0 + (y - y0) * (x1 - x0) / (y1 - y0)
+    return (np.sum(cond & (x < xc), axis=1) % 2) == 1
+
+
+def nearest_site(xy, sites) -> np.ndarray:
+    d = ((xy[:, None, :] - sites[None, :, :]) ** 2).sum(-1)
+    return np.argmin(d, axis=1)
+
+
+def _bisector_pieces(poly, sites, i, j):
+    """Pieces (a, b) of the common Voronoi edge of sites i and j inside the polygon."""
+    si, sj = sites[i], sites[j]
+    m = 0.5 * (si + sj)
+    nrm = sj - si
+    d = np.array([-nrm[1], nrm[0]]) / np.linalg.norm(nrm)
+    lo, hi = -1e3, 1e3
+    for k in range(len(sites)):
+        if k in (i, j):
+            continue
+        # |x - s_i|^2 <= |x - s_k|^2  <=>  2 x.(s_k - s_i) <= |s_k|^2 - |s_i|^2, x = m + t d
+        g = 2 * (sites[k] - si)
+        c = sites[k] @ sites[k] - si @ si - g @ m
+        a = g @ d
+        if abs(a) < 1e-14:
+            if c < 0:
+                return []
+            continue
+        if a > 0:
+            hi = min(hi, c / a)
+        else:
+            lo = max(lo, c / a)
+    if hi <= lo:
+        return []
+    # crossings with the polygon boundary
+    ts = [lo, hi]
+    n = len(poly)
+    for e in range(n):
+        p, q = poly[e], poly[(e + 1) % n]
+        M = np.array([d, p - q]).T
+        if abs(np.linalg.det(M)) < 1e-14:
+            continue
+        t, s = np.linalg.solve(M, p - m)
+        if 0 <= s <= 1 and lo < t < hi:
+            ts.append(t)
+    ts = np.sort(np.array(ts))
+    pieces = []
+    for a, b in zip(ts[:-1], ts[1:]):
+        mid = m + 0.5 * (a + b) * d
+        if b - a > 1e-9 and in_polygon(mid[None, :], poly)[0]:
+            pieces.append((m + a * d, m + b * d))
+    return pieces
+
+
+def _sample_region(rng, poly, sites, q, n, batch=200000):
+    lo, hi = poly.min(0), poly.max(0)
+    out, have = [], 0
+    while have < n:
+        z = lo + (hi - lo) * rng.random((batch, 2))
+        z = z[in_polygon(z, poly)]
+        z = z[nearest_site(z, sites) == q]
+        out.append(z)
+        have += len(z)
+    return np.concatenate(out)[:n]
+
+
+def diffusion_xpinn(n_regions=10, n_res=30000, n_obs=500, n_iface=100, n_kbc=50, n_copies=256,
+                    u_hidden=(40,) * 5, k_hidden=(20,) * 4, noise=0.01, seed=0) -> Problem:
+    """Inverse diffusion div(K grad u) = f (Eq. heq) with unknown K, on a seeded
+    non-convex star polygon split into the clipped Voronoi regions of
+    n_regions seeded sites; two networks per region, u and K (softplus
+    output).  Data: n_obs noisy observations of u* = 20 exp(-0.1 y) per region
+    (noise sigma = `noise` x rms of the observed values), n_kbc values of
+    K* = 1 + 0.5 sin(pi x) cos(pi y) on the polygon boundary per boundary
+    region, n_iface points on every common Voronoi edge (XPINN).  n_copies
+    independent copies share the points and differ in initial weights,
+    learning rate (log-uniform in [1e-4, 1e-2]) and the weights W_I, W_F
+    (log-uniform in [0.1, 10])."""
+    g = _rng(seed, 40)
+    poly = star_polygon(g)
+    sites = []
+    while len(sites) < n_regions:
+        z = poly.min(0) + (poly.max(0) - poly.min(0)) * g.random((64, 2))
+        sites.extend(z[in_polygon(z, poly)].tolist())
+    sites = np.array(sites[:n_regions])
+    # boundary points for K data: uniform in arc length, assigned to the nearest site
+    edges = [(poly[e], poly[(e + 1) % len(poly)]) for e in range(len(poly))]
+    lens = np.array([math.dist(a, b) for a, b in edges])
+    gb = _rng(seed, 41)
+    cnt = _split_counts(20 * n_kbc * n_regions, lens)
+    bpts = np.concatenate([_segment_points(gb, c, a, b) for (a, b), c in zip(edges, cnt)])
+    bown = nearest_site(bpts, sites)
+    u_net = NetSpec([2, *u_hidden, 1])
+    k_net = NetSpec([2, *k_hidden, 1], ACT_SOFTPLUS)
+    region_pts = []
+    for q in range(n_regions):
+        rng = _rng(seed, 42, q)
+        res = _f32(_sample_region(rng, poly, sites, q, n_res))
+        f = _f32(diffusion_forcing(res[:, 0].astype(np.float64), res[:, 1].astype(np.float64)))
+        obs = _sample_region(rng, poly, sites, q, n_obs)
+        uo = diffusion_exact_u(obs[:, 0], obs[:, 1])
+        uo = uo + noise * np.sqrt(np.mean(uo ** 2)) * rng.normal(size=uo.shape)
+        kb = bpts[bown == q][:n_kbc]
+        kd = DataSet(_f32(kb), _f32(diffusion_exact_k(kb[:, 0], kb[:, 1])[:, None])) if len(kb) else None
+        region_pts.append((res, f, DataSet(_f32(obs), _f32(uo[:, None])), kd))
+    iface_geo = []
+    for i in range(n_regions):
+        for j in range(i + 1, n_regions):
+            pieces = _bisector_pieces(poly, sites, i, j)
+            if not pieces:
+                continue
+            plen = np.array([math.dist(a, b) for a, b in pieces])
+            if plen.sum() < 1e-6:
+                continue
+            ge = _rng(seed, 43, i, j)
+            c = _split_counts(n_iface, plen)
+            xy = np.concatenate([_segment_points(ge, cc, a, b) for (a, b), cc in zip(pieces, c)])
+            nrm = (sites[j] - sites[i]) / np.linalg.norm(sites[j] - sites[i])
+            iface_geo.append((i, j, (float(nrm[0]), float(nrm[1])), _f32(xy)))
+    subs, ifaces = [], []
+    for cp in range(n_copies):
+        hp = _rng(seed, 44, cp)
+        lr = float(10 ** hp.uniform(-4, -2))
+        w_i = float(10 ** hp.uniform(-1, 1))
+        w_f = float(10 ** hp.uniform(-1, 1))
+        for q in range(n_regions):
+            res, f, du, dk = region_pts[q]
+            sub = Subdomain(nets=[u_net, k_net], res_xy=res, res_f=f, data=[du, dk], w_data=[1.0, 1.0],
+                            w_res=w_f, w_avg=w_i, w_iface=w_i, lr=lr)
+            lo, hi = poly.min(0), poly.max(0)
+            sub.rect = (float(lo[0]), float(hi[0]), float(lo[1]), float(hi[1]))
+            sub.params = [xavier_params(u_net, _rng(seed, 45, cp, q, 0)),
+                          xavier_params(k_net, _rng(seed, 45, cp, q, 1))]
+            subs.append(sub)
+        for (i, j, nrm, xy) in iface_geo:
+            ifaces.append(Interface(cp * n_regions + i, cp * n_regions + j, XPINN, nrm, xy))
+    return Problem("diffusion_xpinn", PDE_DIFFUSION, subs, ifaces, subs_per_model=n_regions,
+                   meta=dict(polygon=poly.tolist(), sites=sites.tolist(), n_copies=n_copies))

@@ -57,7 +57,19 @@ class ProblemDesc(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("schedule", C.c_int32), ("use_graph", C.c_int32), ("items_per_cta", C.c_int32),
-                ("points_per_thread", C.c_int32), ("profile_phases", C.c_int32)]
+                ("points_per_thread", C.c_int32), ("profile_phases", C.c_int32),
+                ("max_points_per_tile", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("model", C.c_int32), ("copy", C.c_int32), ("order", C.c_int32),
+                ("n", C.c_int64), ("xy", C.c_void_p), ("out", C.c_void_p), ("n_steps", C.c_int32),
+                ("losses", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("queue_ms", C.c_double), ("latency_ms", C.c_double),
+                ("batch", C.c_int32), ("error", C.c_char * 160)]
 
 
 _LIB = None
@@ -96,6 +108,11 @@ def load() -> C.CDLL:
         "xpinn_set_options": (C.c_int, [vp, C.POINTER(Options)]),
         "xpinn_iface_values": (C.c_int, [vp, fp, C.POINTER(i64), vp]),
         "xpinn_phase_times": (C.c_int, [vp, fp]),
+        "xpinn_autotune": (C.c_int, [vp, i32, C.POINTER(Options), C.POINTER(C.c_float)]),
+        "xpinn_server_create": (C.c_int, [C.POINTER(vp), i32, C.c_size_t, C.POINTER(vp)]),
+        "xpinn_server_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+        "xpinn_server_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(Result)]),
+        "xpinn_server_destroy": (C.c_int, [vp]),
         "xpinn_residual_grad_noalloc": (C.c_int, [i32, C.c_float, C.c_float, C.POINTER(NetDesc), fp, fp, fp,
                                                   i64, C.c_float, fp, fp, vp]),
     }
@@ -290,6 +307,43 @@ class Solver:
         _check(self.lib.xpinn_get_options(self.h, C.byref(o)))
         return {f: getattr(o, f) for f, _ in Options._fields_}
 
+    def signature(self) -> str:
+        """Key of the problem's shape for the autotuning cache: PDE, per
+        subdomain the network widths and point counts, interface sizes."""
+        import hashlib
+        pb = self.pb
+        parts = [str(pb.pde)]
+        for sd in pb.subs:
+            parts.append(";".join(",".join(map(str, n.widths)) for n in sd.nets))
+            parts.append(str(sd.res_xy.shape[0]))
+            parts.append(",".join(str(d.xy.shape[0]) if d is not None else "0" for d in sd.data))
+        parts.append(",".join(f"{it.method}:{it.xy.shape[0]}" for it in pb.ifaces))
+        return hashlib.sha256("|".join(parts).encode()).hexdigest()[:24]
+
+    def autotune(self, steps=5, cache=None) -> dict:
+        """Pick tile shapes by timing (xpinn_autotune); with `cache` (a JSON
+        file path) reuse and record the choice for this problem shape."""
+        import json
+        key = self.signature()
+        db = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                db = json.load(f)
+        if key in db:
+            keep = {k: v for k, v in db[key]["options"].items()
+                    if k in ("points_per_thread", "items_per_cta", "max_points_per_tile")}
+            self.set_options(**keep)
+            return db[key]
+        o = Options()
+        ms = C.c_float(0)
+        _check(self.lib.xpinn_autotune(self.h, steps, C.byref(o), C.byref(ms)))
+        rec = {"options": {f: getattr(o, f) for f, _ in Options._fields_}, "ms": ms.value}
+        if cache:
+            db[key] = rec
+            with open(cache, "w") as f:
+                json.dump(db, f, indent=1)
+        return rec
+
     def phase_times(self):
         """Device ms of (start, exchange, jet kernel, reduce+Adam) of the last step."""
         ms = np.zeros(4, np.float32)
@@ -301,3 +355,71 @@ class Solver:
         cur.update(kw)
         o = Options(**cur)
         _check(self.lib.xpinn_set_options(self.h, C.byref(o)))
+
+
+class Server:
+    """Continuous-batching request server over several Solvers (xpinn_server_*).
+
+    submit_eval / submit_step return a ticket; poll(ticket) returns None while
+    the request is pending, else a dict with the status, queue and latency
+    times (ms), the batch size it was served in and its output."""
+
+    def __init__(self, solvers, hbm_budget=1 << 30):
+        self.lib = load()
+        self.solvers = list(solvers)
+        hs = (C.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        out = C.c_void_p()
+        _check(self.lib.xpinn_server_create(hs, len(self.solvers), hbm_budget, C.byref(out)))
+        self.s = out
+        self._keep = {}
+
+    def submit_eval(self, model, xy, order=0, copy=0):
+        xy = _f32(xy)
+        pb = self.solvers[model].pb
+        D = sum(n.widths[-1] for n in pb.subs[0].nets)
+        out = np.empty((xy.shape[0], D, Solver.n_comp(order)), np.float32)
+        r = Request(kind=0, model=model, copy=copy, order=order, n=xy.shape[0], xy=xy.ctypes.data,
+                    out=out.ctypes.data, n_steps=0, losses=None)
+        t = C.c_uint64()
+        _check(self.lib.xpinn_server_submit(self.s, C.byref(r), C.byref(t)))
+        self._keep[t.value] = (xy, out)
+        return t.value
+
+    def submit_step(self, model, n_steps=1):
+        sv = self.solvers[model]
+        losses = np.empty((n_steps, sv.n_sub, N_TERMS), np.float32)
+        r = Request(kind=1, model=model, copy=0, order=0, n=0, xy=None, out=None, n_steps=n_steps,
+                    losses=losses.ctypes.data)
+        t = C.c_uint64()
+        _check(self.lib.xpinn_server_submit(self.s, C.byref(r), C.byref(t)))
+        self._keep[t.value] = (None, losses)
+        return t.value
+
+    def poll(self, ticket):
+        res = Result()
+        rc = self.lib.xpinn_server_poll(self.s, ticket, C.byref(res))
+        if rc == 1:
+            return None
+        _check(rc)
+        _, out = self._keep.pop(ticket)
+        return {"status": res.status, "queue_ms": res.queue_ms, "latency_ms": res.latency_ms,
+                "batch": res.batch, "error": res.error.decode(), "out": out}
+
+    def wait(self, ticket, sleep=1e-4):
+        import time
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            time.sleep(sleep)
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.xpinn_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

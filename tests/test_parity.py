@@ -87,10 +87,15 @@ def small_c3():
     return P.kovasznay_cpinn(nx=3, ny=3, n_res=1500, n_iface=96, n_bc=80)
 
 
+def small_c4():
+    return P.diffusion_xpinn(n_res=1200, n_obs=100, n_iface=40, n_kbc=20, n_copies=2)
+
+
 WORKLOADS = {
     "c1_burgers_cpinn_full": lambda: P.burgers_cpinn(),
     "c2_poisson_xpinn_small": small_c2,
     "c3_kovasznay_cpinn_small": small_c3,
+    "c4_diffusion_xpinn_small": small_c4,
 }
 TINY = {f"tiny_pde{p}_m{m}": (lambda p=p, m=m: tiny_problem(p, m, n_sub=3, n_res=37, n_data=11, n_if=9))
         for p, m in CASES}
@@ -285,3 +290,21 @@ def test_full_size_bench_workload_parity(X):
     assert_losses(losses, terms)
     assert_grads(g, g_ref, pb)
     s.close()
+
+
+def test_autotune_keeps_parity_and_state(X, tmp_path):
+    pb = small_c2()
+    s = X.Solver(pb)
+    theta0 = s.get_params()
+    cache = str(tmp_path / "tune.json")
+    rec = s.autotune(steps=2, cache=cache)
+    assert rec["options"]["points_per_thread"] in (1, 2) and rec["ms"] > 0
+    assert np.array_equal(s.get_params(), theta0)          # tuning does not train
+    losses, g = s.grad()
+    terms, g_ref = Oracle(pb).grad(pb.packed_params())
+    assert_losses(losses, terms)
+    assert_grads(g, g_ref, pb)
+    s2 = X.Solver(pb)
+    rec2 = s2.autotune(cache=cache)                         # served from the cache
+    assert rec2 == rec and s2.options()["items_per_cta"] == rec["options"]["items_per_cta"]
+    s.close(); s2.close()
