@@ -45,6 +45,9 @@ def workload(name):
         return P.burgers_cpinn(), "cPINN Burgers, 4 x-slabs, 2->20x3->1, 1000 residual pts each"
     if name == "c3":
         return P.kovasznay_cpinn(), "cPINN Kovasznay NS Re=40, 8x8 grid, 2->64x6->3, 50k residual pts each"
+    if name == "tablevb":
+        return P.burgers_spacetime(4, 2), ("XPINN space-time Burgers, 4 x 2 subdomains, 2->20x5->1, 80k residual pts "
+                                           "in total, 20 pts per interface (Table TableVB)")
     if name == "c4":
         return P.diffusion_xpinn(), ("XPINN inverse diffusion on a star polygon, 10 Voronoi regions x 256 copies, "
                                      "u: 2->40x5->1, K: 2->20x4->1 softplus, 30k residual pts per region")

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1192,10 +1193,15 @@ int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* be
   ck(cudaEventCreate(&e1), "event");
   xpinn_options win = orig;
   float win_ms = 3.4e38f;
+  const auto t_start = std::chrono::steady_clock::now();
+  auto elapsed_s = [&] {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  };
   try {
     for (int pt : {2, 1})
-      for (int ipc : {2, 4, 8, 16})
-        for (int cap : {0, 128, 64, 32}) {
+      for (int ipc : {4, 8, 16, 2})
+        for (int cap : {0, 64, 128, 32}) {
+          if (elapsed_s() > 20.0) continue;   // time budget: keep the best so far
           xpinn_options c = orig;
           c.schedule = 0;
           c.points_per_thread = pt;

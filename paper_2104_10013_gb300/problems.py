@@ -545,3 +545,48 @@ def diffusion_xpinn(n_regions=10, n_res=30000, n_obs=500, n_iface=100, n_kbc=50,
             ifaces.append(Interface(cp * n_regions + i, cp * n_regions + j, XPINN, nrm, xy))
     return Problem("diffusion_xpinn", PDE_DIFFUSION, subs, ifaces, subs_per_model=n_regions,
                    meta=dict(polygon=poly.tolist(), sites=sites.tolist(), n_copies=n_copies))
+
+
+def burgers_spacetime(nx=4, nt=2, n_res_total=80000, n_iface=20, n_bc=50, hidden=(20,) * 5, lr=8e-4,
+                      method_x=XPINN, method_t=XPINN, seed=0, nu=0.01 / math.pi) -> Problem:
+    """Viscous Burgers (Eq. BE1, Sec. 7.5) on x in [-1,1], t in [0,1] split
+    into nx x nt space-time subdomains (Table TableVB): residual points spread
+    uniformly over the subdomains, n_iface points on every interface, initial
+    data on t = 0 and boundary data on x = +-1.  Interfaces across x-cuts use
+    method_x, across t-cuts method_t (XPINN by default; cPINN in space with
+    XPINN in time is the combination suggested in Sec. 7.7)."""
+    xc = _cuts32(np.linspace(-1.0, 1.0, nx + 1))
+    tc = _cuts32(np.linspace(0.0, 1.0, nt + 1))
+    net = NetSpec([2, *hidden, 1])
+    n_sub = nx * nt
+    per = n_res_total // n_sub
+    subs = []
+    for j in range(nt):
+        for i in range(nx):
+            q = i + nx * j
+            rect = (xc[i], xc[i + 1], tc[j], tc[j + 1])
+            res = _f32(_uniform_rect(_rng(seed, 51, q), per, *rect))
+            pieces = []
+            if j == 0:
+                pieces.append(((xc[i], 0.0), (xc[i + 1], 0.0)))
+            if i == 0:
+                pieces.append(((-1.0, tc[j]), (-1.0, tc[j + 1])))
+            if i == nx - 1:
+                pieces.append(((1.0, tc[j]), (1.0, tc[j + 1])))
+            data = None
+            if pieces:
+                cnt = _split_counts(n_bc, [math.dist(a, b) for a, b in pieces])
+                rb = _rng(seed, 52, q)
+                bxy = np.concatenate([_segment_points(rb, c, a, b) for (a, b), c in zip(pieces, cnt)])
+                bval = np.where(np.abs(bxy[:, 1]) < 1e-12, -np.sin(np.pi * bxy[:, 0]), 0.0)
+                data = DataSet(_f32(bxy), _f32(bval[:, None]))
+            sub = Subdomain(nets=[net], res_xy=res, res_f=np.zeros(per, np.float32), data=[data],
+                            w_data=[1.0], lr=lr, rect=rect)
+            sub.params = [xavier_params(net, _rng(seed, 53, q))]
+            subs.append(sub)
+    ifaces = _grid_interfaces(xc, tc, lambda e: _rng(seed, 54, e), n_iface, method_x)
+    n_xcuts = (nx - 1) * nt
+    for it in ifaces[n_xcuts:]:
+        it.method = method_t
+    return Problem("burgers_spacetime", PDE_BURGERS, subs, ifaces, nu=nu,
+                   meta=dict(xcuts=xc.tolist(), ycuts=tc.tolist()))

@@ -96,6 +96,8 @@ WORKLOADS = {
     "c2_poisson_xpinn_small": small_c2,
     "c3_kovasznay_cpinn_small": small_c3,
     "c4_diffusion_xpinn_small": small_c4,
+    "burgers_spacetime_xpinn_4x2": lambda: P.burgers_spacetime(4, 2, n_res_total=6000),
+    "burgers_cpinn_x_xpinn_t_4x4": lambda: P.burgers_spacetime(4, 4, n_res_total=6000, method_x=P.CPINN),
 }
 TINY = {f"tiny_pde{p}_m{m}": (lambda p=p, m=m: tiny_problem(p, m, n_sub=3, n_res=37, n_data=11, n_if=9))
         for p, m in CASES}

@@ -51,3 +51,15 @@ def test_voronoi_regions_and_edges():
     assert pb.subs[0].res_xy is pb.subs[n].res_xy
     assert pb.subs[0].lr != pb.subs[n].lr
     assert not np.array_equal(pb.subs[0].params[0][0][0], pb.subs[n].params[0][0][0])
+
+
+def test_spacetime_burgers_interfaces():
+    pb = P.burgers_spacetime(4, 2, n_res_total=800, method_x=P.CPINN)
+    assert pb.n_sub == 8 and len(pb.ifaces) == 3 * 2 + 4 * 1
+    for it in pb.ifaces:
+        if it.normal == (1.0, 0.0):
+            assert it.method == P.CPINN and np.allclose(it.xy[:, 0], it.xy[0, 0])
+        else:
+            assert it.method == P.XPINN and np.allclose(it.xy[:, 1], it.xy[0, 1])
+    ic = [s for s in pb.subs if s.rect[2] == 0.0]
+    assert len(ic) == 4 and all(s.data[0] is not None for s in ic)
