@@ -270,6 +270,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pt", type=int, default=0, help="points per thread in the register tile (0: library default)")
     ap.add_argument("--items-per-cta", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: library default)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=400)
@@ -304,9 +305,11 @@ def main():
         opts["points_per_thread"] = args.pt
     if args.items_per_cta:
         opts["items_per_cta"] = args.items_per_cta
+    if args.threads:
+        opts["threads_per_cta"] = args.threads
     s.set_options(**opts)
     tune = None
-    if not args.no_autotune and not args.pt and not args.items_per_cta:
+    if not args.no_autotune and not args.pt and not args.items_per_cta and not args.threads:
         t0 = time.perf_counter()
         tune = s.autotune(steps=5)
         tune["seconds"] = time.perf_counter() - t0

@@ -208,6 +208,12 @@ typedef struct {
                               step (also inside the graph), see xpinn_phase_times */
   int32_t max_points_per_tile; /* cap on the points a CTA processes at once
                                   (0: as many as the register tiles allow) */
+  int32_t threads_per_cta;  /* 256 (default); 128: smaller CTAs, more per SM;
+                               512 (with points_per_thread = 1): more warps */
+  int32_t inject_fault;     /* testing only: 1 makes the in-kernel wait for the
+                               interface exchange wait for one item more than
+                               exists, so it gives up after about 1 s and the
+                               call returns XPINN_ERR_TIMEOUT; 0 (default) off */
 } xpinn_options;
 
 int xpinn_get_options(xpinn_handle h, xpinn_options* opt);

@@ -165,7 +165,7 @@ struct xpinn_ctx {
   int n_sm = 0, grid = 0;
   int ring_cap = 256;
   int host_t = 0, host_slot = 0;
-  xpinn_options opt{0, 1, 4, 2, 0, 0};
+  xpinn_options opt{0, 1, 4, 2, 0, 0, 256, 0};
   int device = 0;
   cudaEvent_t ev[5] = {};
   cudaStream_t cap_stream = nullptr;
@@ -242,6 +242,11 @@ struct Limits {
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+int cta_threads(const xpinn_ctx* h) {
+  const int t = h->opt.threads_per_cta;
+  return (t == 128 || t == 512) ? t : 256;
+}
+
 int max_hidden_wp(const NetDev& n) {
   int w = MT;
   for (int k = 1; k < n.L; ++k) w = std::max(w, n.wp[k]);
@@ -250,14 +255,14 @@ int max_hidden_wp(const NetDev& n) {
 
 // Points per sub-tile for an item evaluating the nets with K[n] > 0: enough
 // (neuron group, point group) register tiles to occupy the CTA's threads.
-int choose_P(const SubDev& sd, const int K[2], int cap, int pt) {
+int choose_P(const SubDev& sd, const int K[2], int cap, int pt, int nt) {
   int ng = 1, dk = 0;
   for (int n = 0; n < sd.n_nets; ++n)
     if (K[n]) {
       ng = std::max(ng, max_hidden_wp(sd.net[n]) / MT);
       dk += sd.net[n].w[sd.net[n].L] * K[n];
     }
-  int P = (NT / ng) * pt;
+  int P = (nt / ng) * pt;
   P = std::min(P, 256);
   P = std::min(P, std::max(4, 2048 / std::max(1, dk)));
   P = std::min(P, cap);
@@ -285,9 +290,9 @@ void item_needs(const SubDev& sd, const Item& it, Limits& l) {
   l.pmax = std::max(l.pmax, it.P);
 }
 
-size_t smem_of(const Limits& l) {
+size_t smem_of(const Limits& l, int nt) {
   StepArgs a{};
-  a.szA = round_up(std::max(l.szA, NT * 16), 4);
+  a.szA = round_up(std::max(l.szA, nt * 32), 4);
   a.szW = round_up(l.szW, 4);
   a.szU = round_up(l.szU, 4);
   a.pmax = round_up(l.pmax, 4);
@@ -316,7 +321,7 @@ void build_plan(xpinn_ctx* h, int p_cap) {
     it.n_pts = n;
     it.K[0] = K0;
     it.K[1] = K1;
-    it.P = choose_P(h->subs[q], it.K, p_cap, h->opt.points_per_thread);
+    it.P = choose_P(h->subs[q], it.K, p_cap, h->opt.points_per_thread, cta_threads(h));
     it.part_off = -1;
     return it;
   };
@@ -438,7 +443,7 @@ Limits limits_of(xpinn_ctx* h, int cap) {
       it.q = q;
       it.K[0] = (net <= 0) ? 5 : 0;
       it.K[1] = (net == 1 || (net < 0 && sd.n_nets > 1)) ? 5 : 0;
-      it.P = choose_P(sd, it.K, cap, h->opt.points_per_thread);
+      it.P = choose_P(sd, it.K, cap, h->opt.points_per_thread, cta_threads(h));
       item_needs(sd, it, l);
     }
   }
@@ -449,12 +454,13 @@ void size_and_upload_plan(xpinn_ctx* h) {
   const Plan& pl = h->plan;
   const Limits l = limits_of(h, h->p_cap);
   StepArgs& a = h->base;
-  a.szA = round_up(std::max(l.szA, NT * 16), 4);   // also the dW split-reduction buffer
+  a.szA = round_up(std::max(l.szA, cta_threads(h) * 32), 4);   // also the dW split-reduction buffer
   a.szW = round_up(l.szW, 4);
   a.szU = round_up(l.szU, 4);
   a.pmax = round_up(l.pmax, 4);
   a.scratch_per_cta = round_up((int)std::min<int64_t>(l.scratch, 1 << 30), 4);
   a.pt = h->opt.points_per_thread;
+  a.nt = cta_threads(h);
   h->smem = jet_step_smem_bytes(a);
   h->items_d.upload(pl.items.data(), pl.items.size());
   h->q_items_d.upload(pl.q_items.data(), pl.q_items.size());
@@ -485,21 +491,25 @@ void plan(xpinn_ctx* h) {
   int optin = 0, per_sm = 0;
   ck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device), "attr");
   ck(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device), "attr");
-  // one point per thread keeps registers <= 128: aim for two CTAs per SM
+  // one point per thread keeps registers <= 128: two 256-thread CTAs per SM;
+  // 128-thread CTAs: twice as many
   const int pt = h->opt.points_per_thread;
-  const size_t budget = pt == 1 ? (size_t)per_sm / 2 - 2048 : (size_t)optin - 1024;
+  const int nt = cta_threads(h);
+  const int per_sm_ctas = nt == 512 ? 1 : (pt == 1 ? 2 : 1) * (256 / nt);
+  const size_t budget =
+      per_sm_ctas == 1 ? (size_t)optin - 1024 : (size_t)per_sm / per_sm_ctas - 2048;
   int cap = h->opt.max_points_per_tile > 0 ? std::min(256, std::max(8, h->opt.max_points_per_tile)) : 256;
   for (;;) {
-    h->grid = h->n_sm * (pt == 1 ? 2 : 1);   // provisional, for item sizes
+    h->grid = h->n_sm * per_sm_ctas;   // provisional, for item sizes
     build_plan(h, cap);
-    if (smem_of(limits_of(h, cap)) <= budget || cap <= 8) break;
+    if (smem_of(limits_of(h, cap), nt) <= budget || cap <= 8) break;
     cap -= 4;
   }
   h->p_cap = cap;
   size_and_upload_plan(h);
   if (h->smem + 1024 > (size_t)optin)
     fail(XPINN_ERR_UNSUPPORTED, "networks too wide for shared memory (%zu bytes)", h->smem);
-  const int bps = jet_step_blocks_per_sm(pt, h->smem);
+  const int bps = jet_step_blocks_per_sm(pt, nt, h->smem);
   if (bps < 1) fail(XPINN_ERR_UNSUPPORTED, "jet kernel does not fit an SM (%zu bytes smem)", h->smem);
   if (h->n_sm * bps != h->grid) {
     // re-plan item sizes and scratch for the grid the occupancy allows
@@ -564,7 +574,7 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads) {
     if (n_all) {
       StepArgs a = args_for(h, 0, n_all, 0);
       a.wait_from = pl.first_iface;
-      a.n_fwd_wait = pl.n_fwd;
+      a.n_fwd_wait = pl.n_fwd + (h->opt.inject_fault == 1 && pl.n_fwd ? 1 : 0);
       launch_jet_step(a, std::min(h->grid, n_all), h->smem, s);
     }
     mark(h, 3, s);
@@ -660,7 +670,7 @@ void eval_items_for(xpinn_ctx* h, int q, int net, int K, int64_t first, int64_t 
   proto.q = q;
   proto.K[0] = (net == 0 || net < 0) ? K : 0;
   proto.K[1] = (net == 1 || (net < 0 && sd.n_nets > 1)) ? K : 0;
-  proto.P = choose_P(sd, proto.K, h->p_cap, h->opt.points_per_thread);
+  proto.P = choose_P(sd, proto.K, h->p_cap, h->opt.points_per_thread, cta_threads(h));
   proto.part_off = -1;
   const int64_t per = (int64_t)proto.P * 16;
   for (int64_t s = 0; s < n; s += per) {
@@ -1173,7 +1183,10 @@ int xpinn_set_options(xpinn_handle h, const xpinn_options* opt) {
   DeviceGuard dg(h);
   if (opt->schedule < 0 || opt->schedule > 1 || opt->items_per_cta < 1 || opt->items_per_cta > 64 ||
       opt->points_per_thread < 1 || opt->points_per_thread > 2 || opt->profile_phases < 0 ||
-      opt->profile_phases > 1 || opt->max_points_per_tile < 0)
+      opt->profile_phases > 1 || opt->max_points_per_tile < 0 ||
+      (opt->threads_per_cta != 0 && opt->threads_per_cta != 128 && opt->threads_per_cta != 256 &&
+       opt->threads_per_cta != 512) || opt->inject_fault < 0 || opt->inject_fault > 1 ||
+      (opt->threads_per_cta == 512 && opt->points_per_thread != 1))
     fail(XPINN_ERR_INVALID, "bad options");
   ck(cudaDeviceSynchronize(), "sync");
   apply_options(h, *opt);
@@ -1198,15 +1211,18 @@ int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* be
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   };
   try {
+    for (int nt : {256, 512, 128})
     for (int pt : {2, 1})
       for (int ipc : {4, 8, 16, 2})
         for (int cap : {0, 64, 128, 32}) {
           if (elapsed_s() > 20.0) continue;   // time budget: keep the best so far
+          if (nt == 512 && pt != 1) continue;
           xpinn_options c = orig;
           c.schedule = 0;
           c.points_per_thread = pt;
           c.items_per_cta = ipc;
           c.max_points_per_tile = cap;
+          c.threads_per_cta = nt;
           c.profile_phases = 0;
           try {
             apply_options(h, c);

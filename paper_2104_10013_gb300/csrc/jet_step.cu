@@ -165,7 +165,7 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const floa
   }
   const float* wp = Wt + n0;
   const float* ap = A + p0;
-#pragma unroll 2
+#pragma unroll 4
   for (int j = 0; j < in_p; ++j) {
     const float4 wa = *reinterpret_cast<const float4*>(wp + j * out_p);
     const float4 wb = *reinterpret_cast<const float4*>(wp + j * out_p + 4);
@@ -195,7 +195,7 @@ __device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, const flo
       for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = 0.f;
   const float* wp = Wn + j0;
   const float* zp = Zb + p0;
-#pragma unroll 2
+#pragma unroll 4
   for (int n = 0; n < out_p; ++n) {
     const float4 wa = *reinterpret_cast<const float4*>(wp + n * in_p);
     const float4 wb = *reinterpret_cast<const float4*>(wp + n * in_p + 4);
@@ -225,50 +225,53 @@ __device__ __forceinline__ void accum(float* p, float v, bool first) {
 
 // dW[n][j] += sum_{c,p} Zb[n][c][p] H[j][c][p] for n < out_w, j < in_w, with
 // H given transposed, HT[(c*P + p)][j] (row stride RS).  Each thread owns a
-// 4 x 4 tile of dW; narrow layers split the (c, p) range over S threads per
-// tile and reduce the S partial tiles in a fixed order through shared memory
-// (R, at least NT * 16 floats; it may alias HT, which is dead once the
-// contraction is done).  Float4 loads: Zb rows
-// are read as 4 consecutive (c, p), broadcast to the lanes of a tile row;
-// HT rows as 4 consecutive j, contiguous across lanes.
+// TA x 4 tile of dW (TA = 8: eight Zb rows share each HT load, which halves
+// the shared-memory wavefronts per FFMA against a 4 x 4 tile); narrow layers
+// split the (c, p) range over S threads per tile and reduce the S partial
+// tiles in a fixed order through shared memory (R, at least blockDim.x * TA * 4
+// floats; it may alias HT, which is dead once the contraction is done).
+// Float4 loads: Zb rows are read as 4 consecutive (c, p), broadcast to the
+// lanes of a tile row; HT rows as 4 consecutive j, contiguous across lanes.
+template <int TA>
 __device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, const float* __restrict__ HT,
                                          int RS, int out_p, int in_p, int out_w, int in_w, int KP,
                                          float* __restrict__ R, float* __restrict__ pW, bool first) {
+  constexpr int TE = TA * 4;   // tile elements
   const int tid = threadIdx.x;
-  const int tj_n = in_p >> 2, tn_n = out_p >> 2;
+  const int tj_n = in_p >> 2, tn_n = out_p / TA;
   const int T = tj_n * tn_n;
-  int S = NT / T;
+  int S = (int)blockDim.x / T;
   S = S < 1 ? 1 : (S > 16 ? 16 : S);
   const int KP4 = KP >> 2;
   const bool split = S > 1;
-  for (int base = 0; base < T * S; base += NT) {
+  for (int base = 0; base < T * S; base += blockDim.x) {
     const int u = base + tid;
     const bool valid = u < T * S;
     const int tile = valid ? u % T : 0;
     const int sp = valid ? u / T : 0;
     const int tn = tile / tj_n, tj = tile - tn * tj_n;
-    const int n0 = tn * 4, j0 = tj * 4;
-    float acc[4][4];
+    const int n0 = tn * TA, j0 = tj * 4;
+    float acc[TA][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TA; ++i)
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.f;
     if (valid) {
       const float4* z4 = reinterpret_cast<const float4*>(Zb + n0 * KP);
       for (int g = sp; g < KP4; g += S) {
-        float4 z[4];
+        float4 h[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) z[i] = z4[i * KP4 + g];
+        for (int t = 0; t < 4; ++t) h[t] = *reinterpret_cast<const float4*>(HT + (4 * g + t) * RS + j0);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const float4 h = *reinterpret_cast<const float4*>(HT + (4 * g + t) * RS + j0);
+        for (int i = 0; i < TA; ++i) {
+          const float4 z = z4[i * KP4 + g];
+          const float zv[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float zv = t == 0 ? z[i].x : (t == 1 ? z[i].y : (t == 2 ? z[i].z : z[i].w));
-            acc[i][0] = fmaf(zv, h.x, acc[i][0]);
-            acc[i][1] = fmaf(zv, h.y, acc[i][1]);
-            acc[i][2] = fmaf(zv, h.z, acc[i][2]);
-            acc[i][3] = fmaf(zv, h.w, acc[i][3]);
+          for (int t = 0; t < 4; ++t) {
+            acc[i][0] = fmaf(zv[t], h[t].x, acc[i][0]);
+            acc[i][1] = fmaf(zv[t], h[t].y, acc[i][1]);
+            acc[i][2] = fmaf(zv[t], h[t].z, acc[i][2]);
+            acc[i][3] = fmaf(zv[t], h[t].w, acc[i][3]);
           }
         }
       }
@@ -276,7 +279,7 @@ __device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, const flo
     if (!split) {
       if (valid) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TA; ++i)
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj)
             if (n0 + i < out_w && j0 + jj < in_w) accum(pW + (n0 + i) * in_w + j0 + jj, acc[i][jj], first);
@@ -285,16 +288,16 @@ __device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, const flo
       __syncthreads();                       // HT / Zb reads of all threads done
       if (valid) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TA; ++i)
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) R[(sp * T + tile) * 16 + i * 4 + jj] = acc[i][jj];
+          for (int jj = 0; jj < 4; ++jj) R[(sp * T + tile) * TE + i * 4 + jj] = acc[i][jj];
       }
       __syncthreads();
-      for (int e = tid; e < T * 16; e += NT) {
-        const int tl = e >> 4, q = e & 15, i = q >> 2, jj = q & 3;
+      for (int e = tid; e < T * TE; e += blockDim.x) {
+        const int tl = e / TE, q = e - tl * TE, i = q >> 2, jj = q & 3;
         float v = 0.f;
-        for (int k = 0; k < S; ++k) v += R[(k * T + tl) * 16 + q];
-        const int n = (tl / tj_n) * 4 + i, j = (tl % tj_n) * 4 + jj;
+        for (int k = 0; k < S; ++k) v += R[(k * T + tl) * TE + q];
+        const int n = (tl / tj_n) * TA + i, j = (tl % tj_n) * 4 + jj;
         if (n < out_w && j < in_w) accum(pW + n * in_w + j, v, first);
       }
     }
@@ -308,7 +311,7 @@ __device__ __forceinline__ void group_dots(int rows, int len4, const float* __re
                                            const float* __restrict__ Y, XR xr, YR yr, OUT out) {
   const int lane8 = threadIdx.x & 7;
   const int warp = threadIdx.x >> 5;
-  for (int base = warp * 4; base < rows; base += (NT / 32) * 4) {
+  for (int base = warp * 4; base < rows; base += (int)(blockDim.x >> 5) * 4) {
     const int r = base + ((threadIdx.x >> 3) & 3);
     const bool valid = r < rows;
     float acc = 0.f;
@@ -355,7 +358,7 @@ __device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const 
     const int w1 = nd.w[1], wp1 = nd.wp[1];
     const float* W1 = prm + nd.off[1];
     const float* b1 = W1 + 2 * w1;
-    for (int idx = tid; idx < wp1 * P; idx += NT) {
+    for (int idx = tid; idx < wp1 * P; idx += blockDim.x) {
       const int n = idx / P, p = idx - n * P;
       float w0 = 0.f, wv = 0.f, b = 0.f;
       if (n < w1) {
@@ -384,11 +387,11 @@ __device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const 
     const int in_p = nd.wp[k - 1], out_p = nd.wp[k], in_w = nd.w[k - 1], out_w = nd.w[k];
     const float* Wk = prm + nd.off[k];
     const float* bk = Wk + out_w * in_w;
-    for (int idx = tid; idx < in_p * out_p; idx += NT) {
+    for (int idx = tid; idx < in_p * out_p; idx += blockDim.x) {
       const int n = idx / in_p, j = idx - n * in_p;
       s.W[j * out_p + n] = (n < out_w && j < in_w) ? __ldg(Wk + n * in_w + j) : 0.f;
     }
-    for (int n = tid; n < out_p; n += NT) s.bias[n] = n < out_w ? __ldg(bk + n) : 0.f;
+    for (int n = tid; n < out_p; n += blockDim.x) s.bias[n] = n < out_w ? __ldg(bk + n) : 0.f;
     __syncthreads();
     const int ng = tid / n_pg, pg = tid - ng * n_pg;
     const bool act = ng < out_p / MT;
@@ -430,7 +433,7 @@ __device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const 
     const int in_w = nd.w[L - 1], D = nd.w[L];
     const float* WL = prm + nd.off[L];
     const float* bL = WL + D * in_w;
-    for (int idx = tid; idx < D * P; idx += NT) {
+    for (int idx = tid; idx < D * P; idx += blockDim.x) {
       const int o = idx / P, p = idx - o * P;
       float z[K];
       z[0] = __ldg(bL + o);
@@ -468,7 +471,7 @@ __device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const 
 template <int K>
 __device__ __forceinline__ void act_from_saved(float* __restrict__ dst, const float* __restrict__ Sk,
                                                int wp, int P) {
-  for (int idx = threadIdx.x; idx < wp * P; idx += NT) {
+  for (int idx = threadIdx.x; idx < wp * P; idx += blockDim.x) {
     const int n = idx / P, p = idx - n * P;
     float sv[K], h[K];
 #pragma unroll
@@ -485,7 +488,7 @@ template <int K>
 __device__ __forceinline__ void act_from_saved_T(float* __restrict__ HT, const float* __restrict__ Sk,
                                                  int wp, int P) {
   const int P4 = P >> 2;
-  for (int idx = threadIdx.x; idx < wp * P4; idx += NT) {
+  for (int idx = threadIdx.x; idx < wp * P4; idx += blockDim.x) {
     const int n = idx % wp, pq = idx / wp;
     float4 sv4[K];
 #pragma unroll
@@ -524,7 +527,7 @@ __device__ __noinline__ void net_backward(SmemLayout sl, const NetDev& nd, const
   // ---- output layer
   const int D = nd.w[L], in_w = nd.w[L - 1], in_p = nd.wp[L - 1];
   if (nd.out_act == XPINN_ACT_SOFTPLUS) {
-    for (int idx = tid; idx < D * P; idx += NT) {
+    for (int idx = tid; idx < D * P; idx += blockDim.x) {
       const int o = idx / P, p = idx - o * P;
       float z[K], yb[K], zb[K];
 #pragma unroll
@@ -622,7 +625,7 @@ __device__ __noinline__ void net_backward(SmemLayout sl, const NetDev& nd, const
       const float* Skm1 = Sk - in_pk * KP;
       act_from_saved_T<K>(s.A, Skm1, in_pk, P);
       const float* Wk = prm + nd.off[k];
-      for (int idx = tid; idx < out_p * in_pk; idx += NT) {
+      for (int idx = tid; idx < out_p * in_pk; idx += blockDim.x) {
         const int n = idx / in_pk, j = idx - n * in_pk;
         s.W[idx] = (n < out_w && j < in_wk) ? __ldg(Wk + n * in_wk + j) : 0.f;
       }
@@ -632,7 +635,7 @@ __device__ __noinline__ void net_backward(SmemLayout sl, const NetDev& nd, const
       float* gb = gW + out_w * in_wk;
       group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
                  [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
-      dW_tiles(s.B, s.A, in_pk, out_p, in_pk, out_w, in_wk, KP, s.A, gW, first);
+      dW_tiles<8>(s.B, s.A, in_pk, out_p, in_pk, out_w, in_wk, KP, s.A, gW, first);
       Sk = Skm1;
     } else {
       __syncthreads();
@@ -849,7 +852,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   __syncthreads();
   double t = 0.0;
   if (threadIdx.x == 0)
-    for (int w = 0; w < NT / 32; ++w) t += red[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
   return t;
 }
 
@@ -1034,7 +1037,7 @@ __device__ void process_item(const StepArgs& a, SmemLayout sl, const Item& it, i
     const int nv = min(P, it.n_pts - t0);
     const bool first = t0 == 0;
     const float2* src = (it.kind == IT_EVAL) ? a.eval_pts : a.pts;
-    for (int p = tid; p < P; p += NT) {
+    for (int p = tid; p < P; p += blockDim.x) {
       float2 z = make_float2(0.f, 0.f);
       if (p < nv) z = src[it.pt_off + t0 + p];
       s.sx[p] = z.x;
@@ -1044,7 +1047,7 @@ __device__ void process_item(const StepArgs& a, SmemLayout sl, const Item& it, i
     if (it.K[0]) forward_any<PT>(it.K[0], sl, sd.net[0], prm, P, scratch, 0);
     if (it.K[1]) forward_any<PT>(it.K[1], sl, sd.net[1], prm, P, scratch + s1, u1);
     // ---- per point: loss terms and seeds (or exchange / evaluation output)
-    for (int p = tid; p < P; p += NT) {
+    for (int p = tid; p < P; p += blockDim.x) {
       const bool valid = p < nv;
       PtJets J, G;
       load_point_jets(sd, it, s.U, u1, P, p, J);
@@ -1093,7 +1096,7 @@ __device__ void process_item(const StepArgs& a, SmemLayout sl, const Item& it, i
             const NetDev& nd = sd.net[n];
             const int beg = nd.off[1];
             const int end = nd.off[nd.L] + nd.w[nd.L] * (nd.w[nd.L - 1] + 1);
-            for (int e = beg + tid; e < end; e += NT) gs[e] = 0.f;
+            for (int e = beg + tid; e < end; e += blockDim.x) gs[e] = 0.f;
           }
     }
     __syncthreads();
@@ -1112,7 +1115,7 @@ __device__ void process_item(const StepArgs& a, SmemLayout sl, const Item& it, i
 // a larger register tile at one CTA per SM.
 // Wait (thread 0) until `need` exchange items have completed.  Every exchange
 // item is claimed before any item that waits, and exchange items never wait,
-// so the wait ends; it is still bounded: after about 4 s it sets the error
+// so the wait ends; it is still bounded: after about 1 s it sets the error
 // flag and returns false, and the item is skipped.
 __device__ bool wait_exchange(const StepArgs& a) {
   __shared__ int s_ok;
@@ -1120,7 +1123,7 @@ __device__ bool wait_exchange(const StepArgs& a) {
     int ok = 1;
     unsigned ns = 32;
     for (long it = 0; atomicAdd(a.fwd_done, 0) < a.n_fwd_wait; ++it) {
-      if (it > (1l << 22)) {
+      if (it > (1l << 20) || atomicAdd(a.err, 0) != 0) {   // gave up here or elsewhere
         atomicCAS(a.err, 0, XPINN_ERR_TIMEOUT);
         ok = 0;
         break;
@@ -1135,8 +1138,13 @@ __device__ bool wait_exchange(const StepArgs& a) {
   return s_ok != 0;
 }
 
-template <int PT>
-__global__ void __launch_bounds__(NT, PT == 1 ? 2 : 1) jet_step_kernel(StepArgs a) {
+// PT = 1 keeps registers <= 128 so that two 256-thread CTAs fit on an SM;
+// PT = 2 uses a larger register tile.  NTH = 128 halves the CTA so that two
+// (or four) independent CTAs share an SM and one CTA's narrow phases (first
+// and output layers, loss, small reductions) overlap another's contractions.
+// NTH = 512 with PT = 1 keeps the sub-tile of 256 x PT=2 with twice the warps.
+template <int PT, int NTH>
+__global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : (PT == 1 ? 2 : 1) * (256 / NTH)) jet_step_kernel(StepArgs a) {
   const SmemLayout sl{a.szA, a.szW, a.szU, a.pmax};
   __shared__ int s_item;
   float* scratch = a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
@@ -1165,16 +1173,26 @@ size_t jet_step_smem_bytes(const StepArgs& a) {
 }
 
 cudaError_t jet_step_configure(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(jet_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(jet_step_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int v = (int)smem;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(jet_step_kernel<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, v))) return e;
+  if ((e = cudaFuncSetAttribute(jet_step_kernel<2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, v))) return e;
+  if ((e = cudaFuncSetAttribute(jet_step_kernel<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, v))) return e;
+  if ((e = cudaFuncSetAttribute(jet_step_kernel<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, v))) return e;
+  return cudaFuncSetAttribute(jet_step_kernel<1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
 }
 
-int jet_step_blocks_per_sm(int pt, size_t smem) {
+int jet_step_blocks_per_sm(int pt, int nt, size_t smem) {
   int n = 0;
-  const cudaError_t e = pt == 1
-      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<1>, NT, smem)
-      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<2>, NT, smem);
+  cudaError_t e;
+  if (nt == 512)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<1, 512>, 512, smem);
+  else if (nt == 128)
+    e = pt == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<1, 128>, 128, smem)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<2, 128>, 128, smem);
+  else
+    e = pt == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<1, 256>, 256, smem)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<2, 256>, 256, smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -1183,10 +1201,19 @@ int jet_step_blocks_per_sm(int pt, size_t smem) {
 }
 
 void launch_jet_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
-  if (a.pt == 1)
-    jet_step_kernel<1><<<grid, NT, smem, s>>>(a);
-  else
-    jet_step_kernel<2><<<grid, NT, smem, s>>>(a);
+  if (a.nt == 512) {
+    jet_step_kernel<1, 512><<<grid, 512, smem, s>>>(a);
+  } else if (a.nt == 128) {
+    if (a.pt == 1)
+      jet_step_kernel<1, 128><<<grid, 128, smem, s>>>(a);
+    else
+      jet_step_kernel<2, 128><<<grid, 128, smem, s>>>(a);
+  } else {
+    if (a.pt == 1)
+      jet_step_kernel<1, 256><<<grid, 256, smem, s>>>(a);
+    else
+      jet_step_kernel<2, 256><<<grid, 256, smem, s>>>(a);
+  }
 }
 
 }  // namespace xp

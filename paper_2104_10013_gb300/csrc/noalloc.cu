@@ -242,12 +242,13 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   a.re = re;
   a.n_out_total = D;
   a.n_eq = pde == XPINN_PDE_NS ? 3 : 1;
-  a.szA = (int)std::max(wmax * K * P, NT * 16);
+  a.szA = (int)std::max(wmax * K * P, NT * 32);
   a.szW = 4;
   for (int k = 2; k < L; ++k) a.szW = std::max(a.szW, nd.wp[k] * nd.wp[k - 1]);
   a.szU = (D * K * P + 3) / 4 * 4;
   a.pmax = P;
   a.pt = 2;
+  a.nt = NT;
   a.err = reinterpret_cast<int*>(base + lay.err);
   const size_t smem = jet_step_smem_bytes(a);
   int optin = 0;

@@ -24,7 +24,7 @@
 
 namespace xp {
 
-constexpr int NT = 256;          // threads per CTA of the jet kernel
+constexpr int NT = 256;          // threads per CTA of the jet kernel (the largest; 128 also exists)
 constexpr int MT = 8;            // neurons in a thread's register tile
 constexpr int KMAX = 5;          // jet components (u, d0, d1, d00, d11)
 constexpr int MAXL = XPINN_MAX_LAYERS;
@@ -116,6 +116,7 @@ struct StepArgs {
   int szA, szW, szU;
   int pmax;              // largest sub-tile of any item
   int pt;                // points per thread in the register tile (1 or 2)
+  int nt;                // threads per CTA (256 or 128)
   // eval
   const float2* eval_pts;
   float* eval_out;
@@ -128,7 +129,7 @@ struct StepArgs {
 void launch_jet_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
 size_t jet_step_smem_bytes(const StepArgs& a);
 cudaError_t jet_step_configure(size_t smem);
-int jet_step_blocks_per_sm(int pt, size_t smem);
+int jet_step_blocks_per_sm(int pt, int nt, size_t smem);
 
 struct ReduceArgs {
   const int2* blocks;        // (subdomain, first param) of each CTA

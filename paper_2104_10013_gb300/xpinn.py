@@ -58,7 +58,8 @@ class ProblemDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("schedule", C.c_int32), ("use_graph", C.c_int32), ("items_per_cta", C.c_int32),
                 ("points_per_thread", C.c_int32), ("profile_phases", C.c_int32),
-                ("max_points_per_tile", C.c_int32)]
+                ("max_points_per_tile", C.c_int32), ("threads_per_cta", C.c_int32),
+                ("inject_fault", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -331,7 +332,8 @@ class Solver:
                 db = json.load(f)
         if key in db:
             keep = {k: v for k, v in db[key]["options"].items()
-                    if k in ("points_per_thread", "items_per_cta", "max_points_per_tile")}
+                    if k in ("points_per_thread", "items_per_cta", "max_points_per_tile",
+                             "threads_per_cta")}
             self.set_options(**keep)
             return db[key]
         o = Options()
