@@ -32,6 +32,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "residual pts/s (jet fwd+bwd) grouped vs per-subdomain loop; query p50/p99 ms"
+
+# DRAM traffic of the jet kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, one launch of the default workload; see profiles/).
+# Reported only while the kernel source is the one that was measured.
+TRAFFIC = {"jet_step.cu sha256[:16]": "ceb4fc8c77d104c2", "workload": "c2",
+           "bytes_per_launch": 70456576 + 944904448}
 FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 partitions x 32)
 
 
@@ -351,8 +357,13 @@ def main():
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (jet_avg / 1e3) / 1e12
+    import hashlib
+    src = os.path.join(ROOT, "paper_2104_10013_gb300", "csrc", "jet_step.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    traffic = (TRAFFIC["bytes_per_launch"]
+               if sha == TRAFFIC["jet_step.cu sha256[:16]"] and args.workload == TRAFFIC["workload"] else None)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "xp::jet_step_kernel (residual, data and interface items)",
+            "traffic": traffic, "kernel": "xp::jet_step_kernel (residual, data and interface items)",
             "kernel_ms": jet_avg, "kernel_share_of_step": jet_avg / ms_step,
             "flop_per_launch": flops,
             "peak_note": f"FP32 FFMA peak derived: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x "
