@@ -68,6 +68,9 @@ enum { XPINN_PDE_BURGERS = 0, XPINN_PDE_POISSON = 1, XPINN_PDE_NS = 2, XPINN_PDE
 enum { XPINN_CPINN = 0, XPINN_XPINN = 1 };
 /* Output layer activation: identity (Sec. 3) or softplus (a positive field). */
 enum { XPINN_ACT_IDENTITY = 0, XPINN_ACT_SOFTPLUS = 1 };
+/* Routing of evaluation points (xpinn_eval): boxes, or Voronoi cells of sites
+ * clipped to a polygon (irregular decompositions, Sec. 7.6). */
+enum { XPINN_REGION_BOX = 0, XPINN_REGION_VORONOI = 1 };
 /* Burgers flux for cPINN: conservative f = u^2/2 - nu u_x, or u u_x - nu u_x. */
 enum { XPINN_FLUX_CONSERVATIVE = 0, XPINN_FLUX_LITERAL = 1 };
 
@@ -102,6 +105,11 @@ typedef struct {
   float w_iface;                           /* W_I,flux (cPINN) or W_I,F (XPINN) */
   float lr;                                /* Adam learning rate of this subdomain */
   float rect[4];                           /* closed box x0, x1, y0, y1 used by xpinn_eval */
+  int32_t region_kind;                     /* how xpinn_eval routes points to it:
+                                              XPINN_REGION_BOX: the closed box `rect`;
+                                              XPINN_REGION_VORONOI: the points of the
+                                              problem's polygon nearest to `site` */
+  float site[2];
 } xpinn_subdomain_desc;
 
 /* A common interface between subdomains q and q_plus with its own points
@@ -127,6 +135,8 @@ typedef struct {
   float beta1, beta2, eps;                 /* Adam constants shared by all subdomains */
   int32_t subs_per_model;                  /* subdomains per independent copy; 0 = n_sub */
   const float* init_params;                /* packed parameters (see xpinn_get_params) */
+  int32_t n_poly;                          /* polygon (domain) for Voronoi regions, or 0 */
+  const float* poly;                       /* [n_poly][2] vertices, host */
 } xpinn_problem_desc;
 
 typedef struct xpinn_ctx* xpinn_handle;
@@ -175,7 +185,10 @@ int xpinn_net_jets(xpinn_handle h, int32_t q, int32_t net, const float* xy, int6
 
 /* The stitched solution of Eq. FSol for copy `model`: u(z) = sum_q u_q(z)
  * 1_{Omega_q}(z), with 1/S on an interface shared by S subdomains; points are
- * routed to subdomains on the device by their closed boxes (`rect`).  out
+ * routed to subdomains on the device by their closed boxes (`rect`), or for
+ * Voronoi regions by the even-odd polygon test and the nearest site (S sites
+ * at exactly the same float32 distance (dx*dx + dy*dy, no fused multiply-add)
+ * share the point).  out
  * [n][D_out_total][1 + 2*(order>0) + 2*(order>1)], where D_out_total counts
  * the outputs of all networks of a subdomain.  Points outside every box give
  * NaN.  Host or device pointers (both on the same side). */

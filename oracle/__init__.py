@@ -19,6 +19,6 @@ Every function is pinned by tests that do not reuse it (closed forms, finite
 differences, invariants and special cases); see tests/test_oracle_pins.py.
 """
 from .xpinn_oracle import (  # noqa: F401
-    Oracle, network, jets, residual, flux_normal, adam_update, route_rect,
+    Oracle, network, jets, residual, flux_normal, adam_update, route_rect, route_voronoi,
     K_RES, K_IFACE, n_eq, n_out_total,
 )

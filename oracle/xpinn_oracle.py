@@ -182,6 +182,33 @@ def route_rect(rects, xy) -> list:
     return out
 
 
+def route_voronoi(sites, polygon, xy) -> list:
+    """Irregular regions (Sec. 7.6): a point inside the polygon (even-odd
+    rule) belongs to the Voronoi cell of its nearest site; the sites at exactly
+    the same float32 distance ((dx*dx) + (dy*dy), each operation rounded to
+    float32) share it.  Points outside the polygon belong to no region."""
+    poly = np.asarray(polygon, dtype=np.float64)
+    xy = np.asarray(xy)
+    out = []
+    s32 = np.asarray(sites, dtype=np.float32)
+    for z in xy:
+        x, y = float(z[0]), float(z[1])
+        inside = False
+        for e in range(len(poly)):
+            (ax, ay), (bx, by) = poly[e], poly[(e + 1) % len(poly)]
+            if (ay > y) != (by > y) and x < ax + (y - ay) * (bx - ax) / (by - ay):
+                inside = not inside
+        if not inside:
+            out.append([])
+            continue
+        z32 = np.asarray(z, dtype=np.float32)
+        dx = z32[0] - s32[:, 0]
+        dy = z32[1] - s32[:, 1]
+        d = (dx * dx) + (dy * dy)          # float32 arithmetic, no fused multiply-add
+        out.append([int(q) for q in np.nonzero(d == d.min())[0]])
+    return out
+
+
 # --------------------------------------------------------------------------
 # The training step (Algorithm 1)
 # --------------------------------------------------------------------------
@@ -335,8 +362,10 @@ class Oracle:
         pb = self.pb
         spm = pb.subs_per_model or pb.n_sub
         qs = list(range(model * spm, (model + 1) * spm))
-        rects = [pb.subs[q].rect for q in qs]
-        memb = route_rect(rects, xy)
+        if pb.subs[qs[0]].region_kind == P.REGION_VORONOI:
+            memb = route_voronoi([pb.subs[q].site for q in qs], pb.polygon, xy)
+        else:
+            memb = route_rect([pb.subs[q].rect for q in qs], xy)
         flat = _t(flat)
         dout = n_out_total(pb)
         out = np.zeros((len(xy), dout, K))

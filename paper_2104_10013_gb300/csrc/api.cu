@@ -27,7 +27,7 @@
 
 namespace xp {
 void launch_route(const float2* pts, int64_t n, const SubDev* subs, int q0, int nq, int* S, int* memb,
-                  int* counts, int* err, cudaStream_t st);
+                  int* counts, int* err, const float2* poly, int n_poly, cudaStream_t st);
 void launch_bucket(const float2* pts, int64_t n, const int* S, const int* memb, int* cursor, int* pos,
                    float2* epts, float* escale, cudaStream_t st);
 void launch_gather(int64_t n, int row, const int* S, const int* pos, const float* eout, float* out,
@@ -145,7 +145,8 @@ struct xpinn_ctx {
   int n_out_total = 0, n_eq = 1, d4_nv = 0;
   // device problem
   DevBuf<float> params, m, v, grads, res_f, tgt, d4, partials, scratch, loss_ring;
-  DevBuf<float2> pts;
+  DevBuf<float2> pts, poly;
+  int n_poly = 0;
   DevBuf<SubDev> subs_d;
   DevBuf<IfaceDev> ifaces_d;
   DevBuf<double> loss_part;
@@ -825,6 +826,11 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
     if (!std::isfinite(s.lr) || !std::isfinite(s.w_res) || !std::isfinite(s.w_avg) || !std::isfinite(s.w_iface))
       fail(XPINN_ERR_INVALID, "subdomain %d: non-finite weight or learning rate", q);
     for (int i = 0; i < 4; ++i) sd.rect[i] = s.rect[i];
+    if (s.region_kind != XPINN_REGION_BOX && s.region_kind != XPINN_REGION_VORONOI)
+      fail(XPINN_ERR_INVALID, "subdomain %d: bad region_kind", q);
+    sd.region_kind = s.region_kind;
+    sd.site[0] = s.site[0];
+    sd.site[1] = s.site[1];
     h->subs.push_back(sd);
   }
   h->n_params = poff;
@@ -859,6 +865,17 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
   const int64_t if_base = h->n_res_total + (int64_t)pts_data.size();
   for (auto& f : h->ifaces) f.pt_off = if_base + f.d4_pt;
   check_finite(d->init_params, h->n_params, "init_params");
+  if (d->n_poly < 0 || d->n_poly == 1 || d->n_poly == 2 || (d->n_poly > 0 && !d->poly))
+    fail(XPINN_ERR_INVALID, "bad polygon");
+  for (int q = 0; q < d->n_sub; q += spm)
+    for (int l = 1; l < spm; ++l)
+      if (d->subs[q + l].region_kind != d->subs[q].region_kind)
+        fail(XPINN_ERR_INVALID, "copy %d mixes box and Voronoi regions", q / spm);
+  if (d->subs[0].region_kind == XPINN_REGION_VORONOI && d->n_poly < 3)
+    fail(XPINN_ERR_INVALID, "Voronoi regions need the polygon");
+  std::vector<float2> poly_h;
+  for (int v = 0; v < d->n_poly; ++v) poly_h.push_back(make_float2(d->poly[2 * v], d->poly[2 * v + 1]));
+  check_finite(d->poly, 2 * (int64_t)d->n_poly, "poly");
   // ---- device
   ck(cudaFree(0), "CUDA init");
   ck(cudaGetDevice(&h->device), "cudaGetDevice");
@@ -870,6 +887,8 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
   h->n_pts_total = (int64_t)all.size();
   h->pts.upload(all.data(), all.size());
   h->res_f.upload(res_f.data(), res_f.size());
+  h->n_poly = (int)poly_h.size();
+  h->poly.upload(poly_h.data(), poly_h.size());
   h->tgt.upload(tgt.data(), tgt.size());
   h->params.upload(d->init_params, (size_t)h->n_params);
   h->m.alloc((size_t)h->n_params);
@@ -1069,7 +1088,8 @@ int xpinn_eval(xpinn_handle h, int32_t model, const float* xy, int64_t n, int32_
   h->e_pos.ensure(n * 4);
   h->e_counts.ensure(2 * nq);
   ck(cudaMemsetAsync(h->e_counts.p, 0, sizeof(int) * 2 * nq, s), "memset");
-  launch_route(pts, n, h->subs_d.p, q0, nq, h->e_S.p, h->e_memb.p, h->e_counts.p, h->err_d.p, s);
+  launch_route(pts, n, h->subs_d.p, q0, nq, h->e_S.p, h->e_memb.p, h->e_counts.p, h->err_d.p, h->poly.p,
+               h->n_poly, s);
   std::vector<int> counts(nq);
   ck(cudaMemcpyAsync(counts.data(), h->e_counts.p, sizeof(int) * nq, cudaMemcpyDeviceToHost, s), "counts");
   ck(cudaStreamSynchronize(s), "sync");

@@ -151,7 +151,7 @@ __device__ __forceinline__ float sigmoid_f(float z) {
 // Z[n][c][p] = sum_j Wt[j][n] A[j][c][p] + (c == 0) b[n], tile n0..n0+7 x p0..p0+PT-1
 template <int K, int PT>
 __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const float* __restrict__ Wt,
-                                         const float* __restrict__ bias, int in_p, int out_p, int P,
+                                         const float* __restrict__ bias, int in_w, int out_p, int P,
                                          int n0, int p0, float (&acc)[MT][K][PT]) {
 #pragma unroll
   for (int i = 0; i < MT; ++i) {
@@ -166,7 +166,7 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const floa
   const float* wp = Wt + n0;
   const float* ap = A + p0;
 #pragma unroll 4
-  for (int j = 0; j < in_p; ++j) {
+  for (int j = 0; j < in_w; ++j) {          // padded inputs are zero: stop at the true width
     const float4 wa = *reinterpret_cast<const float4*>(wp + j * out_p);
     const float4 wb = *reinterpret_cast<const float4*>(wp + j * out_p + 4);
     const float w[MT] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
@@ -185,7 +185,7 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const floa
 // Hb[j][c][p] = sum_n Wn[n][j] Zb[n][c][p], tile j0..j0+7 x p0..p0+PT-1
 template <int K, int PT>
 __device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, const float* __restrict__ Wn,
-                                         int out_p, int in_p, int P, int j0, int p0,
+                                         int out_w, int in_p, int P, int j0, int p0,
                                          float (&acc)[MT][K][PT]) {
 #pragma unroll
   for (int i = 0; i < MT; ++i)
@@ -196,7 +196,7 @@ __device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, const flo
   const float* wp = Wn + j0;
   const float* zp = Zb + p0;
 #pragma unroll 4
-  for (int n = 0; n < out_p; ++n) {
+  for (int n = 0; n < out_w; ++n) {         // padded neurons carry zero adjoints
     const float4 wa = *reinterpret_cast<const float4*>(wp + n * in_p);
     const float4 wb = *reinterpret_cast<const float4*>(wp + n * in_p + 4);
     const float w[MT] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
@@ -398,7 +398,7 @@ __device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const 
     const int n0 = ng * MT, p0 = pg * PT;
     float acc[MT][K][PT];
     if (act) {
-      gemm_fwd<K, PT>(s.A, s.W, s.bias, in_p, out_p, P, n0, p0, acc);
+      gemm_fwd<K, PT>(s.A, s.W, s.bias, in_w, out_p, P, n0, p0, acc);
 #pragma unroll
       for (int i = 0; i < MT; ++i) {
         float sv[K][PT];
@@ -631,7 +631,7 @@ __device__ __noinline__ void net_backward(SmemLayout sl, const NetDev& nd, const
       }
       __syncthreads();
       // h-bar^{k-1} = (W^k)^T zb^k into registers, then dW^k and db^k
-      if (ng < in_pk / MT) gemm_bwd<K, PT>(s.B, s.W, out_p, in_pk, P, n0, p0, acc);
+      if (ng < in_pk / MT) gemm_bwd<K, PT>(s.B, s.W, out_w, in_pk, P, n0, p0, acc);
       float* gb = gW + out_w * in_wk;
       group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
                  [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });

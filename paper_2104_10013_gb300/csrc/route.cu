@@ -11,15 +11,56 @@ namespace xp {
 constexpr int RTT = 256;
 constexpr int MAXS = 4;   // a point of a box decomposition lies in at most 4 boxes
 
+// Even-odd rule: is z inside the polygon poly[0..m)?
+__device__ __forceinline__ bool in_polygon(float2 z, const float2* __restrict__ poly, int m) {
+  bool in = false;
+  for (int e = 0; e < m; ++e) {
+    const float2 a = poly[e], b = poly[e + 1 == m ? 0 : e + 1];
+    if ((a.y > z.y) != (b.y > z.y)) {
+      const float xc = a.x + (z.y - a.y) * (b.x - a.x) / (b.y - a.y);
+      if (z.x < xc) in = !in;
+    }
+  }
+  return in;
+}
+
+// Squared distance rounded as (dx*dx) + (dy*dy) with no fused multiply-add,
+// so that exact ties are the same on every implementation.
+__device__ __forceinline__ float dist2(float2 z, const float* s) {
+  const float dx = __fsub_rn(z.x, s[0]), dy = __fsub_rn(z.y, s[1]);
+  return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+}
+
 // Per point: membership count S and the (ascending) subdomain ids.  Counts
-// entries per subdomain.  Points in more than MAXS boxes raise err = 1.
+// entries per subdomain.  Points in more than MAXS regions raise err = 1.
+// Box regions: closed boxes.  Voronoi regions: inside the polygon, nearest
+// site (all sites at the minimum distance).
 __global__ void route_kernel(const float2* __restrict__ pts, int64_t n, const SubDev* __restrict__ subs,
                              int q0, int nq, int* __restrict__ S, int* __restrict__ memb,
-                             int* __restrict__ counts, int* __restrict__ err) {
+                             int* __restrict__ counts, int* __restrict__ err,
+                             const float2* __restrict__ poly, int n_poly) {
   const int64_t i = (int64_t)blockIdx.x * RTT + threadIdx.x;
   if (i >= n) return;
   const float2 z = pts[i];
   int s = 0;
+  if (subs[q0].region_kind == XPINN_REGION_VORONOI) {
+    if (n_poly >= 3 && in_polygon(z, poly, n_poly)) {
+      float dmin = 3.4e38f;
+      for (int l = 0; l < nq; ++l) dmin = fminf(dmin, dist2(z, subs[q0 + l].site));
+      for (int l = 0; l < nq; ++l)
+        if (dist2(z, subs[q0 + l].site) == dmin) {
+          if (s < MAXS) {
+            memb[i * MAXS + s] = l;
+            atomicAdd(counts + l, 1);
+          } else {
+            atomicCAS(err, 0, 1);
+          }
+          ++s;
+        }
+    }
+    S[i] = s < MAXS ? s : MAXS;
+    return;
+  }
   for (int l = 0; l < nq; ++l) {
     const float* r = subs[q0 + l].rect;
     if (z.x >= r[0] && z.x <= r[1] && z.y >= r[2] && z.y <= r[3]) {
@@ -67,8 +108,10 @@ __global__ void gather_kernel(int64_t n, int row, const int* __restrict__ S, con
 }
 
 void launch_route(const float2* pts, int64_t n, const SubDev* subs, int q0, int nq, int* S, int* memb,
-                  int* counts, int* err, cudaStream_t st) {
-  if (n > 0) route_kernel<<<(unsigned)((n + RTT - 1) / RTT), RTT, 0, st>>>(pts, n, subs, q0, nq, S, memb, counts, err);
+                  int* counts, int* err, const float2* poly, int n_poly, cudaStream_t st) {
+  if (n > 0)
+    route_kernel<<<(unsigned)((n + RTT - 1) / RTT), RTT, 0, st>>>(pts, n, subs, q0, nq, S, memb, counts, err,
+                                                                  poly, n_poly);
 }
 void launch_bucket(const float2* pts, int64_t n, const int* S, const int* memb, int* cursor, int* pos,
                    float2* epts, float* escale, cudaStream_t st) {

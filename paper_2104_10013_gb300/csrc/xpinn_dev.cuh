@@ -64,6 +64,8 @@ struct SubDev {
   int n_data[MAXNETS];
   float lr;
   float rect[4];
+  int region_kind;       // XPINN_REGION_*
+  float site[2];
 };
 
 struct IfaceDev {

@@ -29,6 +29,7 @@ import numpy as np
 PDE_BURGERS, PDE_POISSON, PDE_NS, PDE_DIFFUSION = 0, 1, 2, 3
 CPINN, XPINN = 0, 1
 ACT_IDENTITY, ACT_SOFTPLUS = 0, 1
+REGION_BOX, REGION_VORONOI = 0, 1
 FLUX_CONSERVATIVE, FLUX_LITERAL = 0, 1
 
 # number of loss terms reported per subdomain:
@@ -69,6 +70,8 @@ class Subdomain:
     lr: float = 1e-3
     rect: tuple | None = None       # (x0, x1, y0, y1) closed rectangle, for routing
     params: list = field(default_factory=list)  # per net: [(W[N_k,N_k-1], b[N_k]) ...]
+    region_kind: int = 0            # REGION_BOX, or REGION_VORONOI: polygon cell of `site`
+    site: tuple | None = None
 
     @property
     def n_params(self) -> int:
@@ -99,6 +102,7 @@ class Problem:
     eps: float = 1e-8
     subs_per_model: int = 0         # subdomains per independent copy (0: all)
     meta: dict = field(default_factory=dict)
+    polygon: np.ndarray | None = None   # domain polygon [n, 2] for Voronoi regions
 
     @property
     def n_sub(self) -> int:
@@ -491,7 +495,9 @@ def diffusion_xpinn(n_regions=10, n_res=30000, n_obs=500, n_iface=100, n_kbc=50,
     while len(sites) < n_regions:
         z = poly.min(0) + (poly.max(0) - poly.min(0)) * g.random((64, 2))
         sites.extend(z[in_polygon(z, poly)].tolist())
-    sites = np.array(sites[:n_regions])
+    sites = np.array(sites[:n_regions]).astype(np.float32).astype(np.float64)
+    poly = poly.astype(np.float32).astype(np.float64)
+    sites32 = sites
     # boundary points for K data: uniform in arc length, assigned to the nearest site
     edges = [(poly[e], poly[(e + 1) % len(poly)]) for e in range(len(poly))]
     lens = np.array([math.dist(a, b) for a, b in edges])
@@ -538,13 +544,16 @@ def diffusion_xpinn(n_regions=10, n_res=30000, n_obs=500, n_iface=100, n_kbc=50,
                             w_res=w_f, w_avg=w_i, w_iface=w_i, lr=lr)
             lo, hi = poly.min(0), poly.max(0)
             sub.rect = (float(lo[0]), float(hi[0]), float(lo[1]), float(hi[1]))
+            sub.region_kind = REGION_VORONOI
+            sub.site = (float(sites32[q, 0]), float(sites32[q, 1]))
             sub.params = [xavier_params(u_net, _rng(seed, 45, cp, q, 0)),
                           xavier_params(k_net, _rng(seed, 45, cp, q, 1))]
             subs.append(sub)
         for (i, j, nrm, xy) in iface_geo:
             ifaces.append(Interface(cp * n_regions + i, cp * n_regions + j, XPINN, nrm, xy))
     return Problem("diffusion_xpinn", PDE_DIFFUSION, subs, ifaces, subs_per_model=n_regions,
-                   meta=dict(polygon=poly.tolist(), sites=sites.tolist(), n_copies=n_copies))
+                   meta=dict(polygon=poly.tolist(), sites=sites.tolist(), n_copies=n_copies),
+                   polygon=_f32(poly))
 
 
 def burgers_spacetime(nx=4, nt=2, n_res_total=80000, n_iface=20, n_bc=50, hidden=(20,) * 5, lr=8e-4,

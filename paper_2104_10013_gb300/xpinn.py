@@ -39,7 +39,8 @@ class SubDesc(C.Structure):
                 ("n_data", C.c_int64 * MAX_NETS), ("data_xy", C.c_void_p * MAX_NETS),
                 ("data_val", C.c_void_p * MAX_NETS), ("w_data", C.c_float * MAX_NETS),
                 ("w_res", C.c_float), ("w_avg", C.c_float), ("w_iface", C.c_float),
-                ("lr", C.c_float), ("rect", C.c_float * 4)]
+                ("lr", C.c_float), ("rect", C.c_float * 4), ("region_kind", C.c_int32),
+                ("site", C.c_float * 2)]
 
 
 class IfaceDesc(C.Structure):
@@ -52,7 +53,8 @@ class ProblemDesc(C.Structure):
                 ("n_sub", C.c_int32), ("subs", C.POINTER(SubDesc)),
                 ("n_iface", C.c_int32), ("ifaces", C.POINTER(IfaceDesc)),
                 ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
-                ("subs_per_model", C.c_int32), ("init_params", C.c_void_p)]
+                ("subs_per_model", C.c_int32), ("init_params", C.c_void_p),
+                ("n_poly", C.c_int32), ("poly", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -186,6 +188,9 @@ class Solver:
             d.w_res, d.w_avg, d.w_iface, d.lr = s.w_res, s.w_avg, s.w_iface, s.lr
             for i, v in enumerate(s.rect if s.rect is not None else (0, 0, 0, 0)):
                 d.rect[i] = v
+            d.region_kind = s.region_kind
+            if s.site is not None:
+                d.site[0], d.site[1] = s.site
         ifs = (IfaceDesc * max(1, len(problem.ifaces)))()
         for e, it in enumerate(problem.ifaces):
             f = ifs[e]
@@ -199,6 +204,9 @@ class Solver:
         desc.n_iface, desc.ifaces = len(problem.ifaces), ifs
         desc.beta1, desc.beta2, desc.eps = problem.beta1, problem.beta2, problem.eps
         desc.subs_per_model = problem.subs_per_model
+        if problem.polygon is not None:
+            desc.n_poly = int(problem.polygon.shape[0])
+            desc.poly = arr(problem.polygon)
         theta = problem.packed_params() if init_params is None else _f32(init_params)
         desc.init_params = arr(theta)
         h = C.c_void_p()

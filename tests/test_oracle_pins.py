@@ -338,3 +338,16 @@ def test_stitched_solution_averages_on_interfaces():
     assert np.allclose(out, want, equal_nan=True)
     memb = route_rect([s.rect for s in pb.subs], pts)
     assert [len(m) for m in memb] == [1, 2, 1, 2, 4, 2, 1, 2, 1, 0]
+
+
+def test_voronoi_routing_on_symmetric_sites():
+    """Sites at (-1, 0), (1, 0), (0, 2) in a square: a point on the y axis
+    below the third site's cell is equidistant (exactly, in float32) from the
+    first two and shared by both; points near a site belong to it; points
+    outside the polygon belong to none."""
+    from oracle import route_voronoi
+    sites = [(-1.0, 0.0), (1.0, 0.0), (0.0, 2.0)]
+    square = [(-3, -3), (3, -3), (3, 3), (-3, 3)]
+    pts = [(0.0, -0.5), (-0.9, 0.1), (1.2, -0.3), (0.1, 2.2), (4.0, 0.0), (0.0, 0.25)]
+    memb = route_voronoi(sites, square, pts)
+    assert memb == [[0, 1], [0], [1], [2], [], [0, 1]]

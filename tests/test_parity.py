@@ -310,3 +310,22 @@ def test_autotune_keeps_parity_and_state(X, tmp_path):
     rec2 = s2.autotune(cache=cache)                         # served from the cache
     assert rec2 == rec and s2.options()["items_per_cta"] == rec["options"]["items_per_cta"]
     s.close(); s2.close()
+
+
+@pytest.mark.parametrize("order", [0, 2])
+def test_stitched_eval_on_voronoi_regions(X, order):
+    """Eq. FSol on the irregular decomposition: points inside the polygon go to
+    the region of their nearest site, points outside get NaN."""
+    pb = small_c4()
+    s = X.Solver(pb)
+    rng = np.random.default_rng(4)
+    inside = np.concatenate([sd.res_xy[rng.choice(sd.res_xy.shape[0], 150, replace=False)]
+                             for sd in pb.subs[:10]])
+    outside = np.array([[10.0, 10.0], [-5.0, 0.3]], np.float32)
+    xy = np.concatenate([inside, outside]).astype(np.float32)
+    for model in (0, 1):
+        got = s.eval(model, xy, order)
+        ref = Oracle(pb).eval_stitched(pb.packed_params(), model, xy, (1, 3, 5)[order])
+        assert np.isnan(got[-2:]).all() and np.isnan(ref[-2:]).all()
+        assert_scaled(got[:-2], ref[:-2], RTOL_JET, f"voronoi eval model {model}", axis=(0, 1))
+    s.close()
