@@ -34,14 +34,26 @@ def softplus(z: torch.Tensor) -> torch.Tensor:
     return torch.clamp(z, min=0.0) + torch.log1p(torch.exp(-torch.abs(z)))
 
 
-def network(layers, z: torch.Tensor, out_act: int) -> torch.Tensor:
-    """N^1 = W^1 z + b^1, N^k = W^k tanh(N^{k-1}) + b^k (2 <= k <= L), with
-    the slope n*a^k fixed at its initial value 1 (Sec. 3).  The last layer is
-    the identity, or a softplus for a strictly positive field."""
+def phi(act: int, v: torch.Tensor) -> torch.Tensor:
+    """Hidden activation Phi: tanh, sin or cos (Table Table_USmap)."""
+    if act == P.PHI_SIN:
+        return torch.sin(v)
+    if act == P.PHI_COS:
+        return torch.cos(v)
+    return torch.tanh(v)
+
+
+def network(layers, z: torch.Tensor, out_act: int, act: int = P.PHI_TANH, slopes=None,
+            scale: float = 1.0) -> torch.Tensor:
+    """N^1 = W^1 z + b^1, N^k = W^k Phi(n a^{k-1} N^{k-1}) + b^k (2 <= k <= L),
+    Sec. 3: with `slopes` the layer-wise slopes a^1..a^{L-1} and scale n,
+    otherwise n a^k fixed at its initial value 1.  The last layer is the
+    identity, or a softplus for a strictly positive field."""
     h = z
     for k, (W, b) in enumerate(layers):
         if k > 0:
-            h = torch.tanh(h)
+            s = 1.0 if slopes is None else scale * slopes[k - 1]
+            h = phi(act, s * h)
         h = h @ W.T + b
     if out_act == P.ACT_SOFTPLUS:
         h = softplus(h)
@@ -53,12 +65,13 @@ def _grad(y: torch.Tensor, z: torch.Tensor) -> torch.Tensor:
     return torch.zeros_like(z) if g is None else g
 
 
-def jets(layers, z: torch.Tensor, out_act: int, K: int) -> torch.Tensor:
+def jets(layers, z: torch.Tensor, out_act: int, K: int, act: int = P.PHI_TANH, slopes=None,
+         scale: float = 1.0) -> torch.Tensor:
     """Network output and its input derivatives at every point, by reverse-mode
     AD (Sec. 4.1): returns [n, D_out, K] in the component order above.  The
-    result stays differentiable with respect to the weights."""
+    result stays differentiable with respect to the weights and slopes."""
     z = z.detach().clone().requires_grad_(True)
-    u = network(layers, z, out_act)
+    u = network(layers, z, out_act, act, slopes, scale)
     comps = [u]
     if K > 1:
         g = [_grad(u[:, o], z) for o in range(u.shape[1])]
@@ -231,6 +244,10 @@ class Oracle:
     # -- parameters --------------------------------------------------------
     def _layers(self, flat: torch.Tensor, q: int) -> list:
         """Views of the packed parameter vector: per net, [(W^k, b^k), ...]."""
+        return [layers for layers, _ in self._nets(flat, q)]
+
+    def _nets(self, flat: torch.Tensor, q: int) -> list:
+        """Per net: ([(W^k, b^k), ...], slopes a^1..a^{L-1} or None)."""
         off = self.offsets[q]
         nets = []
         for net in self.pb.subs[q].nets:
@@ -240,21 +257,32 @@ class Oracle:
                 W = flat[off:off + no * ni].view(no, ni); off += no * ni
                 b = flat[off:off + no]; off += no
                 layers.append((W, b))
-            nets.append(layers)
+            a = None
+            if net.adaptive:
+                a = flat[off:off + net.n_slopes]; off += net.n_slopes
+            nets.append((layers, a))
         return nets
+
+    def _net_fn(self, flat, q, n):
+        """The network n of subdomain q as a function of the points."""
+        net = self.pb.subs[q].nets[n]
+        layers, a = self._nets(flat, q)[n]
+        scale = _r32(net.slope_scale)
+        return layers, a, scale, net
 
     def _jets(self, flat, q, xy, Ks) -> list:
         s = self.pb.subs[q]
         z = _t(xy)
-        return [jets(L, z, net.out_act, K)
-                for L, net, K in zip(self._layers(flat, q), s.nets, Ks)]
+        out = []
+        for n, K in enumerate(Ks):
+            layers, a, scale, net = self._net_fn(flat, q, n)
+            out.append(jets(layers, z, net.out_act, K, net.act, a, scale))
+        return out
 
     def net_jets(self, flat, q: int, net: int, xy, K: int) -> np.ndarray:
         """Jets [n, D_out, K] of network `net` of subdomain q at points xy."""
-        flat = _t(flat)
-        s = self.pb.subs[q]
-        L = self._layers(flat, q)[net]
-        return jets(L, _t(xy), s.nets[net].out_act, K).detach().numpy()
+        layers, a, scale, nd = self._net_fn(_t(flat), q, net)
+        return jets(layers, _t(xy), nd.out_act, K, nd.act, a, scale).detach().numpy()
 
     # -- interface quantities (Algorithm 1, computation stage) -------------
     def iface_quantities(self, flat, e: int, side: int):
@@ -300,8 +328,8 @@ class Oracle:
             for ni, ds in enumerate(s.data):
                 if ds is None or ds.xy.shape[0] == 0:
                     continue
-                L = self._layers(flat, q)[ni]
-                u = network(L, _t(ds.xy), s.nets[ni].out_act)
+                layers, a, scale, nd = self._net_fn(flat, q, ni)
+                u = network(layers, _t(ds.xy), nd.out_act, nd.act, a, scale)
                 terms[ni] = ((u - _t(ds.val)) ** 2).sum(1).mean()
             # residual MSE_F
             if s.res_xy.shape[0] > 0:
@@ -375,8 +403,9 @@ class Oracle:
                 continue
             pts = np.asarray(xy)[idx]
             J = np.concatenate([
-                jets(L, _t(pts), net.out_act, K).detach().numpy()
-                for L, net in zip(self._layers(flat, q), pb.subs[q].nets)], axis=1)
+                jets(layers, _t(pts), nd.out_act, K, nd.act, a, scale).detach().numpy()
+                for layers, a, scale, nd in (self._net_fn(flat, q, n) for n in range(len(pb.subs[q].nets)))],
+                axis=1)
             S = np.array([len(memb[i]) for i in idx], dtype=np.float64)
             out[idx] += J / S[:, None, None]
         out[[i for i, m in enumerate(memb) if not m]] = np.nan

@@ -29,6 +29,7 @@ import numpy as np
 PDE_BURGERS, PDE_POISSON, PDE_NS, PDE_DIFFUSION = 0, 1, 2, 3
 CPINN, XPINN = 0, 1
 ACT_IDENTITY, ACT_SOFTPLUS = 0, 1
+PHI_TANH, PHI_SIN, PHI_COS = 0, 1, 2      # hidden activation Phi (Table Table_USmap)
 REGION_BOX, REGION_VORONOI = 0, 1
 FLUX_CONSERVATIVE, FLUX_LITERAL = 0, 1
 
@@ -40,14 +41,24 @@ N_TERMS = 5
 
 @dataclass
 class NetSpec:
-    """One fully connected tanh network (Sec. 3): widths = [N_0, ..., N_L]."""
+    """One fully connected network (Sec. 3): widths = [N_0, ..., N_L], hidden
+    activation Phi (tanh, sin or cos).  With `adaptive`, hidden layer k uses
+    Phi(n a^k z) with a trainable slope a^k and scale n (= slope_scale), one
+    slope per hidden layer, appended after the network's layers."""
     widths: list
     out_act: int = ACT_IDENTITY
+    act: int = PHI_TANH
+    adaptive: bool = False
+    slope_scale: float = 10.0
+
+    @property
+    def n_slopes(self) -> int:
+        return len(self.widths) - 2 if self.adaptive else 0
 
     @property
     def n_params(self) -> int:
         return sum(self.widths[k] * self.widths[k - 1] + self.widths[k]
-                   for k in range(1, len(self.widths)))
+                   for k in range(1, len(self.widths))) + self.n_slopes
 
 
 @dataclass
@@ -72,6 +83,7 @@ class Subdomain:
     params: list = field(default_factory=list)  # per net: [(W[N_k,N_k-1], b[N_k]) ...]
     region_kind: int = 0            # REGION_BOX, or REGION_VORONOI: polygon cell of `site`
     site: tuple | None = None
+    slopes: list = field(default_factory=list)  # per net: a^1..a^{L-1} (adaptive nets) or None
 
     @property
     def n_params(self) -> int:
@@ -115,17 +127,23 @@ class Problem:
 
     def packed_params(self) -> np.ndarray:
         """All parameters in the packed layout: per subdomain, per net, per
-        layer k = 1..L: W^k row-major [N_k][N_{k-1}] followed by b^k."""
+        layer k = 1..L: W^k row-major [N_k][N_{k-1}] followed by b^k; then,
+        for an adaptive net, its slopes a^1..a^{L-1} (initially 1/n, so that
+        n a^k = 1 as in Sec. 3)."""
         out = []
         for s in self.subs:
-            for net_params in s.params:
+            for n, (net, net_params) in enumerate(zip(s.nets, s.params)):
                 for W, b in net_params:
                     out.append(W.reshape(-1))
                     out.append(b.reshape(-1))
+                if net.adaptive:
+                    a = s.slopes[n] if n < len(s.slopes) and s.slopes[n] is not None else None
+                    out.append(np.full(net.n_slopes, 1.0 / net.slope_scale) if a is None else np.asarray(a))
         return np.concatenate(out).astype(np.float32)
 
     def unpack_params(self, flat: np.ndarray) -> list:
-        """Inverse of packed_params: per subdomain, per net, [(W, b), ...]."""
+        """Inverse of packed_params: per subdomain, per net, ([(W, b), ...],
+        slopes or None)."""
         flat = np.asarray(flat)
         res, off = [], 0
         for s in self.subs:
@@ -137,7 +155,10 @@ class Problem:
                     W = flat[off:off + no * ni].reshape(no, ni); off += no * ni
                     b = flat[off:off + no]; off += no
                     layers.append((W, b))
-                sp.append(layers)
+                a = None
+                if net.adaptive:
+                    a = flat[off:off + net.n_slopes]; off += net.n_slopes
+                sp.append((layers, a))
             res.append(sp)
         assert off == flat.size
         return res

@@ -12,15 +12,17 @@ CASES = [(P.PDE_BURGERS, P.CPINN), (P.PDE_BURGERS, P.XPINN), (P.PDE_POISSON, P.X
          (P.PDE_DIFFUSION, P.XPINN), (P.PDE_DIFFUSION, P.CPINN)]
 
 
-def tiny_problem(pde, method, n_sub=2, widths=None, n_res=7, n_data=5, n_if=4, seed=0):
+def tiny_problem(pde, method, n_sub=2, widths=None, n_res=7, n_data=5, n_if=4, seed=0, act=P.PHI_TANH,
+                 adaptive=False):
     """Two (or more) subdomains side by side on [0, n_sub] x [0, 1] with tiny
     networks, random targets and forcing; every loss term is active."""
     rng = np.random.default_rng(seed)
-    nets = {P.PDE_BURGERS: [P.NetSpec(widths or [2, 3, 3, 1])],
-            P.PDE_POISSON: [P.NetSpec(widths or [2, 3, 3, 1])],
-            P.PDE_NS: [P.NetSpec(widths or [2, 3, 3, 3])],
-            P.PDE_DIFFUSION: [P.NetSpec(widths or [2, 3, 3, 1]),
-                              P.NetSpec([2, 3, 1], P.ACT_SOFTPLUS)]}[pde]
+    kw = dict(act=act, adaptive=adaptive)
+    nets = {P.PDE_BURGERS: [P.NetSpec(widths or [2, 3, 3, 1], **kw)],
+            P.PDE_POISSON: [P.NetSpec(widths or [2, 3, 3, 1], **kw)],
+            P.PDE_NS: [P.NetSpec(widths or [2, 3, 3, 3], **kw)],
+            P.PDE_DIFFUSION: [P.NetSpec(widths or [2, 3, 3, 1], **kw),
+                              P.NetSpec([2, 3, 1], P.ACT_SOFTPLUS, **kw)]}[pde]
     subs = []
     for q in range(n_sub):
         res = rng.uniform((q, 0), (q + 1, 1), size=(n_res, 2))
@@ -33,6 +35,9 @@ def tiny_problem(pde, method, n_sub=2, widths=None, n_res=7, n_data=5, n_if=4, s
                         w_iface=0.8, lr=1e-3 * (q + 1), rect=(q, q + 1, 0.0, 1.0))
         s.params = [[(P._f32(rng.normal(size=W.shape)), P._f32(rng.normal(size=b.shape) * 0.3))
                      for W, b in P.xavier_params(n, rng)] for n in nets]
+        if adaptive:   # slopes away from their initial 1/n, so that their gradients are exercised
+            srng = np.random.default_rng(1000 + seed + q)   # own stream: the other draws stay as without slopes
+            s.slopes = [P._f32(srng.uniform(0.05, 0.2, size=n.n_slopes)) for n in nets]
         subs.append(s)
     ifaces = [P.Interface(q, q + 1, method, (1.0, 0.0),
                           P._f32(np.stack([np.full(n_if, q + 1.0), rng.random(n_if)], 1)))

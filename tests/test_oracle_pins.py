@@ -351,3 +351,64 @@ def test_voronoi_routing_on_symmetric_sites():
     pts = [(0.0, -0.5), (-0.9, 0.1), (1.2, -0.3), (0.1, 2.2), (4.0, 0.0), (0.0, 0.25)]
     memb = route_voronoi(sites, square, pts)
     assert memb == [[0, 1], [0], [1], [2], [], [0, 1]]
+
+
+@pytest.mark.parametrize("act", [P.PHI_TANH, P.PHI_SIN, P.PHI_COS])
+def test_one_neuron_with_slope_closed_form(act):
+    # u = w2 phi(s (w1 . z + b1)) + b2: u_i = w2 s w1_i phi', u_ii = w2 s^2 w1_i^2 phi''
+    w1 = np.array([[0.7, -1.3]]); b1 = np.array([0.2]); w2 = np.array([[1.9]]); b2 = np.array([-0.4])
+    n, a = 10.0, 0.137
+    s = n * a
+    layers = [(torch.tensor(w1), torch.tensor(b1)), (torch.tensor(w2), torch.tensor(b2))]
+    z = np.random.default_rng(9).normal(size=(40, 2))
+    J = jets(layers, torch.tensor(z), P.ACT_IDENTITY, 5, act, torch.tensor([a], dtype=torch.float64), n).detach().numpy()[:, 0, :]
+    v = s * (z @ w1[0] + b1[0])
+    f, d1, d2 = {P.PHI_TANH: (np.tanh(v), 1 - np.tanh(v) ** 2, -2 * np.tanh(v) * (1 - np.tanh(v) ** 2)),
+                 P.PHI_SIN: (np.sin(v), np.cos(v), -np.sin(v)),
+                 P.PHI_COS: (np.cos(v), -np.sin(v), -np.cos(v))}[act]
+    ref = np.stack([w2[0, 0] * f + b2[0],
+                    w2[0, 0] * s * w1[0, 0] * d1, w2[0, 0] * s * w1[0, 1] * d1,
+                    w2[0, 0] * s * s * w1[0, 0] ** 2 * d2, w2[0, 0] * s * s * w1[0, 1] ** 2 * d2], 1)
+    assert np.allclose(J, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_initial_slopes_give_the_fixed_network():
+    """n a^k = 1 at initialisation (Sec. 3): an adaptive network with its
+    initial slopes computes exactly what the fixed-slope network does."""
+    pb = _tiny_problem(P.PDE_NS, P.CPINN, n_sub=2)
+    pa = _tiny_problem(P.PDE_NS, P.CPINN, n_sub=2, adaptive=True)
+    for s in pa.subs:
+        s.slopes = []                        # initial slopes 1/n
+    for sa, sb in zip(pa.subs, pb.subs):
+        sa.params = sb.params
+    ta = Oracle(pa).loss_terms(torch.tensor(pa.packed_params().astype(np.float64))).detach().numpy()
+    tb = Oracle(pb).loss_terms(torch.tensor(pb.packed_params().astype(np.float64))).detach().numpy()
+    assert np.allclose(ta, tb, rtol=1e-6)     # 1/n is rounded to float32 in the packed vector
+
+
+@pytest.mark.parametrize("pde,method,act", [(P.PDE_BURGERS, P.CPINN, P.PHI_TANH),
+                                            (P.PDE_POISSON, P.XPINN, P.PHI_SIN),
+                                            (P.PDE_DIFFUSION, P.XPINN, P.PHI_COS)])
+def test_gradient_with_slopes_matches_central_differences(pde, method, act):
+    pb = _tiny_problem(pde, method, act=act, adaptive=True)
+    orc = Oracle(pb)
+    theta = pb.packed_params().astype(np.float64)
+    W = orc.weights()
+    _, g = orc.grad(theta)
+    owner = np.concatenate([np.full(s.n_params, q) for q, s in enumerate(pb.subs)])
+    # every slope, plus some weights
+    slope_idx, off = [], 0
+    for s in pb.subs:
+        for net in s.nets:
+            off += net.n_params
+            slope_idx += list(range(off - net.n_slopes, off))
+    idx = slope_idx + list(np.random.default_rng(1).choice(theta.size, 10, replace=False))
+    h = 1e-6
+    for i in idx:
+        q = owner[i]
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h; tm[i] -= h
+        Jp = (orc.loss_terms(torch.tensor(tp)).detach().numpy()[q] * W[q]).sum()
+        Jm = (orc.loss_terms(torch.tensor(tm)).detach().numpy()[q] * W[q]).sum()
+        fd = (Jp - Jm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
