@@ -36,8 +36,8 @@ METRIC = "residual pts/s (jet fwd+bwd) grouped vs per-subdomain loop; query p50/
 # DRAM traffic of the jet kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, one launch of the default workload; see profiles/).
 # Reported only while the kernel source is the one that was measured.
-TRAFFIC = {"jet_step.cu sha256[:16]": "ceb4fc8c77d104c2", "workload": "c2",
-           "bytes_per_launch": 70456576 + 944904448}
+TRAFFIC = {"jet_step.cuh sha256[:16]": "d9bef43e84c634cc", "workload": "c2",
+           "bytes_per_launch": 63650432 + 944350080}
 FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 partitions x 32)
 
 
@@ -56,7 +56,15 @@ def workload(name):
                                            "in total, 20 pts per interface (Table TableVB)")
     if name == "c4":
         return P.diffusion_xpinn(), ("XPINN inverse diffusion on a star polygon, 10 Voronoi regions x 256 copies, "
-                                     "u: 2->40x5->1, K: 2->20x4->1 softplus, 30k residual pts per region")
+                                     "u: 2->40x5->1, K: 2->20x4->1 softplus, 30k residual pts per region, "
+                                     "adaptive tanh/sin/cos per region (Table Table_USmap)")
+    if name == "c2a":
+        import dataclasses
+        pb = P.poisson_xpinn()
+        for s in pb.subs:
+            s.nets = [dataclasses.replace(n, adaptive=True) for n in s.nets]
+        return pb, ("the default XPINN Poisson workload with trainable layer-wise slopes n a^k (Sec. 3) "
+                    "in every tanh network")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -358,10 +366,10 @@ def main():
     peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (jet_avg / 1e3) / 1e12
     import hashlib
-    src = os.path.join(ROOT, "paper_2104_10013_gb300", "csrc", "jet_step.cu")
+    src = os.path.join(ROOT, "paper_2104_10013_gb300", "csrc", "jet_step.cuh")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     traffic = (TRAFFIC["bytes_per_launch"]
-               if sha == TRAFFIC["jet_step.cu sha256[:16]"] and args.workload == TRAFFIC["workload"] else None)
+               if sha == TRAFFIC["jet_step.cuh sha256[:16]"] and args.workload == TRAFFIC["workload"] else None)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "xp::jet_step_kernel (residual, data and interface items)",
             "kernel_ms": jet_avg, "kernel_share_of_step": jet_avg / ms_step,

@@ -80,13 +80,29 @@ enum { XPINN_FLUX_CONSERVATIVE = 0, XPINN_FLUX_LITERAL = 1 };
  *  4 MSE_flux (cPINN) or MSE_R (XPINN), summed over neighbours.
  * J(Theta_q) = w_data[0] T0 + w_data[1] T1 + w_res T2 + w_avg T3 + w_iface T4. */
 
+/* Hidden activation Phi of a network (Sec. 3; Table Table_USmap uses tanh
+ * and sin networks side by side). */
+enum { XPINN_PHI_TANH = 0, XPINN_PHI_SIN = 1, XPINN_PHI_COS = 2 };
+
 /* A fully connected network (Sec. 3): N^1 = W^1 z + b^1,
- * N^k = W^k tanh(N^{k-1}) + b^k for 2 <= k <= L; widths[0] = 2 (inputs),
- * widths[L] = outputs.  The layer-wise slope n*a^k is fixed at 1. */
+ * N^k = W^k Phi(n a^{k-1} N^{k-1}) + b^k for 2 <= k <= L; widths[0] = 2
+ * (inputs), widths[L] = outputs.
+ *
+ * Parameter layout of one network inside its subdomain's block: for
+ * k = 1..L, W^k row-major [widths[k]][widths[k-1]] then b^k [widths[k]];
+ * then, if adaptive, the L-1 layer-wise slopes a^1..a^{L-1}.  Without
+ * `adaptive` the slope n a^k is fixed at 1 and the network has no slope
+ * parameters.  With it the slopes are trained like every other parameter
+ * (same Adam, same learning rate); the paper's initialisation is
+ * a^k = 1/n.  A zero-initialised descriptor (apart from n_layers, widths)
+ * is a tanh network with fixed slopes. */
 typedef struct {
   int32_t n_layers;                        /* L >= 2 */
   int32_t widths[XPINN_MAX_LAYERS + 1];
   int32_t out_act;                         /* XPINN_ACT_* */
+  int32_t act;                             /* XPINN_PHI_* */
+  int32_t adaptive;                        /* 0 or 1 */
+  float slope_scale;                       /* n > 0 (read only when adaptive; 10 in Sec. 3) */
 } xpinn_net_desc;
 
 /* One subdomain Omega_q.  All arrays are host memory, float32, row-major. */
@@ -324,8 +340,10 @@ int xpinn_server_destroy(xpinn_server* s);
  * Computes, for pde BURGERS, POISSON or NS (single-network PDEs):
  *   loss[0]  = MSE_F = (1/n) sum_i |F(u)(xy_i)|^2              (device, 1 float)
  *   grads    = d (w_res * MSE_F) / d theta, packed like one net (device)
- * with the network `net` (host struct) and parameters `params` (device,
- * layer by layer W^k row-major then b^k), points xy [n][2] and forcing f [n]
+ * with the network `net` (host struct, any activation, slopes fixed or
+ * adaptive) and parameters `params` (device, in the network's layout above:
+ * layer by layer W^k row-major then b^k, then the slopes if adaptive),
+ * points xy [n][2] and forcing f [n]
  * (device; pass zeros when f = 0: it is required).  It is the residual part
  * of xpinn_grad for one subdomain.  Asynchronous in `stream`.
  *

@@ -214,12 +214,12 @@ void validate_net(const xpinn_net_desc& n, int pde, int net_idx, int q) {
   if (D != want) fail(XPINN_ERR_INVALID, "subdomain %d net %d: %d outputs, this PDE needs %d", q, net_idx, D, want);
   if (n.out_act != XPINN_ACT_IDENTITY && n.out_act != XPINN_ACT_SOFTPLUS)
     fail(XPINN_ERR_INVALID, "subdomain %d net %d: bad out_act %d", q, net_idx, n.out_act);
-}
-
-int64_t net_params(const xpinn_net_desc& n) {
-  int64_t t = 0;
-  for (int k = 1; k <= n.n_layers; ++k) t += (int64_t)n.widths[k] * n.widths[k - 1] + n.widths[k];
-  return t;
+  if (n.act != XPINN_PHI_TANH && n.act != XPINN_PHI_SIN && n.act != XPINN_PHI_COS)
+    fail(XPINN_ERR_INVALID, "subdomain %d net %d: bad act %d", q, net_idx, n.act);
+  if (n.adaptive != 0 && n.adaptive != 1)
+    fail(XPINN_ERR_INVALID, "subdomain %d net %d: adaptive must be 0 or 1", q, net_idx);
+  if (n.adaptive && !(n.slope_scale > 0.f && n.slope_scale < 3.0e38f))
+    fail(XPINN_ERR_INVALID, "subdomain %d net %d: slope_scale must be finite and > 0", q, net_idx);
 }
 
 double net_macs(const NetDev& n) {
@@ -451,6 +451,14 @@ Limits limits_of(xpinn_ctx* h, int cap) {
   return l;
 }
 
+// Does some network need the general activation passes?
+int any_general(const xpinn_ctx* h) {
+  for (const SubDev& sd : h->subs)
+    for (int n = 0; n < sd.n_nets; ++n)
+      if (net_is_general(sd.net[n])) return 1;
+  return 0;
+}
+
 void size_and_upload_plan(xpinn_ctx* h) {
   const Plan& pl = h->plan;
   const Limits l = limits_of(h, h->p_cap);
@@ -462,6 +470,7 @@ void size_and_upload_plan(xpinn_ctx* h) {
   a.scratch_per_cta = round_up((int)std::min<int64_t>(l.scratch, 1 << 30), 4);
   a.pt = h->opt.points_per_thread;
   a.nt = cta_threads(h);
+  a.gen = any_general(h);
   h->smem = jet_step_smem_bytes(a);
   h->items_d.upload(pl.items.data(), pl.items.size());
   h->q_items_d.upload(pl.q_items.data(), pl.q_items.size());
@@ -510,7 +519,7 @@ void plan(xpinn_ctx* h) {
   size_and_upload_plan(h);
   if (h->smem + 1024 > (size_t)optin)
     fail(XPINN_ERR_UNSUPPORTED, "networks too wide for shared memory (%zu bytes)", h->smem);
-  const int bps = jet_step_blocks_per_sm(pt, nt, h->smem);
+  const int bps = jet_step_blocks_per_sm(pt, nt, any_general(h), h->smem);
   if (bps < 1) fail(XPINN_ERR_UNSUPPORTED, "jet kernel does not fit an SM (%zu bytes smem)", h->smem);
   if (h->n_sm * bps != h->grid) {
     // re-plan item sizes and scratch for the grid the occupancy allows
@@ -778,17 +787,7 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
     int off = 0;
     for (int n = 0; n < s.n_nets; ++n) {
       validate_net(s.nets[n], d->pde, n, q);
-      NetDev& nd = sd.net[n];
-      nd.L = s.nets[n].n_layers;
-      nd.out_act = s.nets[n].out_act;
-      for (int k = 0; k <= nd.L; ++k) {
-        nd.w[k] = s.nets[n].widths[k];
-        nd.wp[k] = round_up(nd.w[k], MT);
-      }
-      for (int k = 1; k <= nd.L; ++k) {
-        nd.off[k] = off;
-        off += nd.w[k] * nd.w[k - 1] + nd.w[k];
-      }
+      off = fill_net_dev(sd.net[n], s.nets[n], off);
     }
     sd.n_params = off;
     poff += off;

@@ -1,1171 +1,31 @@
-// Grouped, persistent jet kernel for the cPINN / XPINN training step.
-//
-// One CTA processes work items pulled from an atomic counter.  An item is a
-// range of points of one subdomain and one kind (residual, data, interface
-// side, interface exchange, evaluation).  Its points are processed in
-// sub-tiles of P points:
-//
-//   forward   for every network of the subdomain, the Taylor jet of the
-//             network (Sec. 3) at the P points: value, first derivatives and
-//             diagonal second derivatives, propagated layer by layer as
-//             z^k = W^k h^{k-1} + b^k (all jet components share W^k) and
-//             h = tanh(z) with the chain rule for the derivative components;
-//             the pre-activation jets (t, z_i, z_ii) are saved to per-CTA
-//             scratch for the reverse pass;
-//   loss      per point, the residual of the PDE (Sec. 2, Sec. 7), the data
-//             mismatch, or the interface terms of Eq. cPINNLoss / Eq.
-//             XPINNLoss against the neighbour's values read from the exchange
-//             buffer (held constant, Algorithm 1); the derivative of the
-//             weighted loss with respect to every jet component (the seeds);
-//   reverse   back through the jet, layer by layer, accumulating dW^k, db^k
-//             into the item's private gradient slice.
-//
-// Layer contractions are register-tiled FP32 FFMA loops: a thread owns MT=8
-// neurons x PT points x K jet components (PT = 1 or 2, a template parameter:
-// PT = 1 keeps a thread under 128 registers so that two CTAs share an SM);
-// activations live in shared memory laid out [neuron][component][point].
+// Host side of the jet kernel: shared-memory size and attribute, occupancy
+// and launch.  The kernel instantiations live in jet_step_{tanh,gen}_pt1.cu
+// (PT = 1; 256, 128 and 512 threads) and jet_step_{tanh,gen}_pt2.cu (PT = 2;
+// 256 and 128 threads): the tanh family for problems whose networks are all
+// fixed-slope tanh networks, the general family for the rest.
 #include <cuda_runtime.h>
 
 #include "xpinn_dev.cuh"
 
 namespace xp {
 
-// loads / stores of PT consecutive points
-template <int PT>
-__device__ __forceinline__ void ldp(const float* p, float (&v)[PT]) {
-  if constexpr (PT == 1) {
-    v[0] = *p;
-  } else {
-    const float2 t = *reinterpret_cast<const float2*>(p);
-    v[0] = t.x;
-    v[1] = t.y;
-  }
-}
-template <int PT>
-__device__ __forceinline__ void stp(float* p, const float (&v)[PT]) {
-  if constexpr (PT == 1) {
-    *p = v[0];
-  } else {
-    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
-  }
+const void* jet_step_kernel_tanh_pt1(int nt);
+const void* jet_step_kernel_tanh_pt2(int nt);
+const void* jet_step_kernel_gen_pt1(int nt);
+const void* jet_step_kernel_gen_pt2(int nt);
+
+namespace {
+
+// The kernel for a register tile of pt points and nt threads, or NULL.
+const void* kernel_for(int pt, int nt, bool gen) {
+  if (nt == 512 && pt != 1) return nullptr;
+  if (nt != 128 && nt != 256 && nt != 512) return nullptr;
+  if (pt == 1) return gen ? jet_step_kernel_gen_pt1(nt) : jet_step_kernel_tanh_pt1(nt);
+  if (pt == 2) return gen ? jet_step_kernel_gen_pt2(nt) : jet_step_kernel_tanh_pt2(nt);
+  return nullptr;
 }
 
-struct Smem {
-  float* A;      // activations H^{k} / H^{k-1}      [wp][K][P]
-  float* B;      // adjoints z-bar^k                 [wp][K][P]
-  float* W;      // one layer's weights, padded
-  float* U;      // output jets of every net         [D][K][P] per net
-  float* Ub;     // seeds (adjoints of U)
-  float* bias;   // MAXW + 16
-  float* sx;     // point coordinates, SoA
-  float* sy;
-  double* red;   // 32 doubles for block reductions
-};
-
-// Sizes of the shared-memory regions (floats).  Functions that are not
-// inlined receive this by value and rebuild their pointers from the
-// extern __shared__ array, so that the compiler knows they address shared
-// memory (32-bit shared loads and stores, not generic ones).
-struct SmemLayout {
-  int szA, szW, szU, pmax;
-};
-
-__device__ __forceinline__ Smem carve(SmemLayout l) {
-  extern __shared__ __align__(16) float sm[];
-  Smem s;
-  s.A = sm;
-  s.B = s.A + l.szA;
-  s.W = s.B + l.szA;
-  s.U = s.W + l.szW;
-  s.Ub = s.U + l.szU;
-  s.bias = s.Ub + l.szU;
-  s.sx = s.bias + (MAXW + 16);
-  s.sy = s.sx + l.pmax;
-  s.red = reinterpret_cast<double*>(s.sy + l.pmax);
-  return s;
-}
-
-// ---------------------------------------------------------------------------
-// tanh jet, forward and reverse (Sec. 3 network with Phi = tanh, slope 1).
-// Components: 0 value, 1..2 first derivatives, 3..4 second derivatives
-// (component 3 pairs with 1, 4 with 2).
-//   h = t,  h_i = s z_i,  h_ii = s z_ii - 2 t s z_i^2,  t = tanh(z), s = 1 - t^2
-// ---------------------------------------------------------------------------
-template <int K>
-__device__ __forceinline__ void tanh_jet(const float (&z)[K], float (&h)[K], float& t_out) {
-  const float t = tanhf(z[0]);
-  const float s = 1.f - t * t;
-  h[0] = t;
-  if (K > 1) h[1] = s * z[1];
-  if (K > 2) h[2] = s * z[2];
-  if (K > 3) h[3] = s * z[3] - 2.f * t * s * z[1] * z[1];
-  if (K > 4) h[4] = s * z[4] - 2.f * t * s * z[2] * z[2];
-  t_out = t;
-}
-
-// h from the saved (t, z_1, z_2, z_11, z_22)
-template <int K>
-__device__ __forceinline__ void tanh_jet_from_saved(const float (&sv)[K], float (&h)[K]) {
-  const float t = sv[0];
-  const float s = 1.f - t * t;
-  h[0] = t;
-  if (K > 1) h[1] = s * sv[1];
-  if (K > 2) h[2] = s * sv[2];
-  if (K > 3) h[3] = s * sv[3] - 2.f * t * s * sv[1] * sv[1];
-  if (K > 4) h[4] = s * sv[4] - 2.f * t * s * sv[2] * sv[2];
-}
-
-// Reverse of tanh_jet: adjoints hb of (h, h_i, h_ii) to adjoints of (z, z_i, z_ii).
-template <int K>
-__device__ __forceinline__ void tanh_jet_bwd(const float (&sv)[K], const float (&hb)[K], float (&zb)[K]) {
-  const float t = sv[0];
-  const float s = 1.f - t * t;
-  float tb = hb[0];
-  if (K > 1) { zb[1] = s * hb[1]; tb -= 2.f * t * sv[1] * hb[1]; }
-  if (K > 2) { zb[2] = s * hb[2]; tb -= 2.f * t * sv[2] * hb[2]; }
-  if (K > 3) {
-    zb[3] = s * hb[3];
-    zb[1] -= 4.f * t * s * sv[1] * hb[3];
-    tb += (-2.f * t * sv[3] + (6.f * t * t - 2.f) * sv[1] * sv[1]) * hb[3];
-  }
-  if (K > 4) {
-    zb[4] = s * hb[4];
-    zb[2] -= 4.f * t * s * sv[2] * hb[4];
-    tb += (-2.f * t * sv[4] + (6.f * t * t - 2.f) * sv[2] * sv[2]) * hb[4];
-  }
-  zb[0] = s * tb;
-}
-
-// softplus output activation: y = log(1+e^z), y_i = g z_i, y_ii = g z_ii + g(1-g) z_i^2
-__device__ __forceinline__ float softplus_f(float z) {
-  return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));
-}
-__device__ __forceinline__ float sigmoid_f(float z) {
-  return 1.f / (1.f + expf(-z));
-}
-
-// ---------------------------------------------------------------------------
-// Register-tiled contractions
-// ---------------------------------------------------------------------------
-
-// Z[n][c][p] = sum_j Wt[j][n] A[j][c][p] + (c == 0) b[n], tile n0..n0+7 x p0..p0+PT-1
-template <int K, int PT>
-__device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const float* __restrict__ Wt,
-                                         const float* __restrict__ bias, int in_w, int out_p, int P,
-                                         int n0, int p0, float (&acc)[MT][K][PT]) {
-#pragma unroll
-  for (int i = 0; i < MT; ++i) {
-    const float b = bias[n0 + i];
-#pragma unroll
-    for (int pp = 0; pp < PT; ++pp) {
-      acc[i][0][pp] = b;
-#pragma unroll
-      for (int c = 1; c < K; ++c) acc[i][c][pp] = 0.f;
-    }
-  }
-  const float* wp = Wt + n0;
-  const float* ap = A + p0;
-#pragma unroll 4
-  for (int j = 0; j < in_w; ++j) {          // padded inputs are zero: stop at the true width
-    const float4 wa = *reinterpret_cast<const float4*>(wp + j * out_p);
-    const float4 wb = *reinterpret_cast<const float4*>(wp + j * out_p + 4);
-    const float w[MT] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-    float h[K][PT];
-#pragma unroll
-    for (int c = 0; c < K; ++c) ldp<PT>(ap + (j * K + c) * P, h[c]);
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-      for (int c = 0; c < K; ++c)
-#pragma unroll
-        for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], h[c][pp], acc[i][c][pp]);
-  }
-}
-
-// Hb[j][c][p] = sum_n Wn[n][j] Zb[n][c][p], tile j0..j0+7 x p0..p0+PT-1
-template <int K, int PT>
-__device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, const float* __restrict__ Wn,
-                                         int out_w, int in_p, int P, int j0, int p0,
-                                         float (&acc)[MT][K][PT]) {
-#pragma unroll
-  for (int i = 0; i < MT; ++i)
-#pragma unroll
-    for (int c = 0; c < K; ++c)
-#pragma unroll
-      for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = 0.f;
-  const float* wp = Wn + j0;
-  const float* zp = Zb + p0;
-#pragma unroll 4
-  for (int n = 0; n < out_w; ++n) {         // padded neurons carry zero adjoints
-    const float4 wa = *reinterpret_cast<const float4*>(wp + n * in_p);
-    const float4 wb = *reinterpret_cast<const float4*>(wp + n * in_p + 4);
-    const float w[MT] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-    float zb[K][PT];
-#pragma unroll
-    for (int c = 0; c < K; ++c) ldp<PT>(zp + (n * K + c) * P, zb[c]);
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-      for (int c = 0; c < K; ++c)
-#pragma unroll
-        for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], zb[c][pp], acc[i][c][pp]);
-  }
-}
-
-// Gradient slices are private to an item: its first sub-tile stores, later
-// sub-tiles add with a reduction that does not wait for the old value.  The
-// same thread owns the same element in every sub-tile, so the additions of
-// one element happen in program order and the result is deterministic.
-__device__ __forceinline__ void accum(float* p, float v, bool first) {
-  if (first)
-    *p = v;
-  else
-    atomicAdd(p, v);
-}
-
-// dW[n][j] += sum_{c,p} Zb[n][c][p] H[j][c][p] for n < out_w, j < in_w, with
-// H given transposed, HT[(c*P + p)][j] (row stride RS).  Each thread owns a
-// TA x 4 tile of dW (TA = 8: eight Zb rows share each HT load, which halves
-// the shared-memory wavefronts per FFMA against a 4 x 4 tile); narrow layers
-// split the (c, p) range over S threads per tile and reduce the S partial
-// tiles in a fixed order through shared memory (R, at least blockDim.x * TA * 4
-// floats; it may alias HT, which is dead once the contraction is done).
-// Float4 loads: Zb rows are read as 4 consecutive (c, p), broadcast to the
-// lanes of a tile row; HT rows as 4 consecutive j, contiguous across lanes.
-template <int TA>
-__device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, const float* __restrict__ HT,
-                                         int RS, int out_p, int in_p, int out_w, int in_w, int KP,
-                                         float* __restrict__ R, float* __restrict__ pW, bool first) {
-  constexpr int TE = TA * 4;   // tile elements
-  const int tid = threadIdx.x;
-  const int tj_n = in_p >> 2, tn_n = out_p / TA;
-  const int T = tj_n * tn_n;
-  int S = (int)blockDim.x / T;
-  S = S < 1 ? 1 : (S > 16 ? 16 : S);
-  const int KP4 = KP >> 2;
-  const bool split = S > 1;
-  for (int base = 0; base < T * S; base += blockDim.x) {
-    const int u = base + tid;
-    const bool valid = u < T * S;
-    const int tile = valid ? u % T : 0;
-    const int sp = valid ? u / T : 0;
-    const int tn = tile / tj_n, tj = tile - tn * tj_n;
-    const int n0 = tn * TA, j0 = tj * 4;
-    float acc[TA][4];
-#pragma unroll
-    for (int i = 0; i < TA; ++i)
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.f;
-    if (valid) {
-      const float4* z4 = reinterpret_cast<const float4*>(Zb + n0 * KP);
-      for (int g = sp; g < KP4; g += S) {
-        float4 h[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) h[t] = *reinterpret_cast<const float4*>(HT + (4 * g + t) * RS + j0);
-#pragma unroll
-        for (int i = 0; i < TA; ++i) {
-          const float4 z = z4[i * KP4 + g];
-          const float zv[4] = {z.x, z.y, z.z, z.w};
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            acc[i][0] = fmaf(zv[t], h[t].x, acc[i][0]);
-            acc[i][1] = fmaf(zv[t], h[t].y, acc[i][1]);
-            acc[i][2] = fmaf(zv[t], h[t].z, acc[i][2]);
-            acc[i][3] = fmaf(zv[t], h[t].w, acc[i][3]);
-          }
-        }
-      }
-    }
-    if (!split) {
-      if (valid) {
-#pragma unroll
-        for (int i = 0; i < TA; ++i)
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj)
-            if (n0 + i < out_w && j0 + jj < in_w) accum(pW + (n0 + i) * in_w + j0 + jj, acc[i][jj], first);
-      }
-    } else {
-      __syncthreads();                       // HT / Zb reads of all threads done
-      if (valid) {
-#pragma unroll
-        for (int i = 0; i < TA; ++i)
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) R[(sp * T + tile) * TE + i * 4 + jj] = acc[i][jj];
-      }
-      __syncthreads();
-      for (int e = tid; e < T * TE; e += blockDim.x) {
-        const int tl = e / TE, q = e - tl * TE, i = q >> 2, jj = q & 3;
-        float v = 0.f;
-        for (int k = 0; k < S; ++k) v += R[(k * T + tl) * TE + q];
-        const int n = (tl / tj_n) * TA + i, j = (tl % tj_n) * 4 + jj;
-        if (n < out_w && j < in_w) accum(pW + n * in_w + j, v, first);
-      }
-    }
-  }
-}
-
-// Row dot products with 8 lanes per row pair: out[r] (+)= sum_k X[r][k] Y[r'][k].
-// `rows` pairs; X row r at X + xr(r) * len, Y row at Y + yr(r) * len (Y NULL: plain sum).
-template <typename XR, typename YR, typename OUT>
-__device__ __forceinline__ void group_dots(int rows, int len4, const float* __restrict__ X,
-                                           const float* __restrict__ Y, XR xr, YR yr, OUT out) {
-  const int lane8 = threadIdx.x & 7;
-  const int warp = threadIdx.x >> 5;
-  for (int base = warp * 4; base < rows; base += (int)(blockDim.x >> 5) * 4) {
-    const int r = base + ((threadIdx.x >> 3) & 3);
-    const bool valid = r < rows;
-    float acc = 0.f;
-    if (valid) {
-      const float4* x4 = reinterpret_cast<const float4*>(X) + xr(r) * len4;
-      if (Y) {
-        const float4* y4 = reinterpret_cast<const float4*>(Y) + yr(r) * len4;
-        for (int g = lane8; g < len4; g += 8) {
-          const float4 x = x4[g], y = y4[g];
-          acc = fmaf(x.x, y.x, acc);
-          acc = fmaf(x.y, y.y, acc);
-          acc = fmaf(x.z, y.z, acc);
-          acc = fmaf(x.w, y.w, acc);
-        }
-      } else {
-        for (int g = lane8; g < len4; g += 8) {
-          const float4 x = x4[g];
-          acc += (x.x + x.y) + (x.z + x.w);
-        }
-      }
-    }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    if (valid && lane8 == 0) out(r, acc);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Network forward with jets.  Leaves the output jets in Uo [D][K][P] and the
-// saved pre-activation jets of every layer in S.
-// S layout: layer 1..L-1: [wp_k][K][P] each, then layer L: [D][K][P].
-// ---------------------------------------------------------------------------
-template <int K, int PT>
-__device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm, int P,
-                            float* __restrict__ S, int uoff) {
-  const Smem s = carve(sl);
-  float* __restrict__ Uo = s.U + uoff;
-  const int tid = threadIdx.x;
-  const int n_pg = P / PT;
-  const int L = nd.L;
-  // ---- layer 1 (2 inputs): z = W^1 x + b^1, z_i = W^1[:, i], z_ii = 0
-  {
-    const int w1 = nd.w[1], wp1 = nd.wp[1];
-    const float* W1 = prm + nd.off[1];
-    const float* b1 = W1 + 2 * w1;
-    for (int idx = tid; idx < wp1 * P; idx += blockDim.x) {
-      const int n = idx / P, p = idx - n * P;
-      float w0 = 0.f, wv = 0.f, b = 0.f;
-      if (n < w1) {
-        w0 = __ldg(W1 + 2 * n);
-        wv = __ldg(W1 + 2 * n + 1);
-        b = __ldg(b1 + n);
-      }
-      float z[K], h[K], t;
-      z[0] = fmaf(w0, s.sx[p], fmaf(wv, s.sy[p], b));
-      if (K > 1) z[1] = w0;
-      if (K > 2) z[2] = wv;
-      if (K > 3) z[3] = 0.f;
-      if (K > 4) z[4] = 0.f;
-      tanh_jet<K>(z, h, t);
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        s.A[(n * K + c) * P + p] = h[c];
-        S[(n * K + c) * P + p] = c == 0 ? t : z[c];
-      }
-    }
-  }
-  float* Sk = S + nd.wp[1] * K * P;
-  __syncthreads();
-  // ---- hidden layers 2 .. L-1
-  for (int k = 2; k <= L - 1; ++k) {
-    const int in_p = nd.wp[k - 1], out_p = nd.wp[k], in_w = nd.w[k - 1], out_w = nd.w[k];
-    const float* Wk = prm + nd.off[k];
-    const float* bk = Wk + out_w * in_w;
-    for (int idx = tid; idx < in_p * out_p; idx += blockDim.x) {
-      const int n = idx / in_p, j = idx - n * in_p;
-      s.W[j * out_p + n] = (n < out_w && j < in_w) ? __ldg(Wk + n * in_w + j) : 0.f;
-    }
-    for (int n = tid; n < out_p; n += blockDim.x) s.bias[n] = n < out_w ? __ldg(bk + n) : 0.f;
-    __syncthreads();
-    const int ng = tid / n_pg, pg = tid - ng * n_pg;
-    const bool act = ng < out_p / MT;
-    const int n0 = ng * MT, p0 = pg * PT;
-    float acc[MT][K][PT];
-    if (act) {
-      gemm_fwd<K, PT>(s.A, s.W, s.bias, in_w, out_p, P, n0, p0, acc);
-#pragma unroll
-      for (int i = 0; i < MT; ++i) {
-        float sv[K][PT];
-#pragma unroll
-        for (int pp = 0; pp < PT; ++pp) {
-          float z[K], h[K], t;
-#pragma unroll
-          for (int c = 0; c < K; ++c) z[c] = acc[i][c][pp];
-          tanh_jet<K>(z, h, t);
-#pragma unroll
-          for (int c = 0; c < K; ++c) {
-            sv[c][pp] = c == 0 ? t : z[c];
-            acc[i][c][pp] = h[c];
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < K; ++c) stp<PT>(Sk + ((n0 + i) * K + c) * P + p0, sv[c]);
-      }
-    }
-    __syncthreads();
-    if (act) {
-#pragma unroll
-      for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int c = 0; c < K; ++c) stp<PT>(s.A + ((n0 + i) * K + c) * P + p0, acc[i][c]);
-    }
-    __syncthreads();
-    Sk += out_p * K * P;
-  }
-  // ---- output layer L
-  {
-    const int in_w = nd.w[L - 1], D = nd.w[L];
-    const float* WL = prm + nd.off[L];
-    const float* bL = WL + D * in_w;
-    for (int idx = tid; idx < D * P; idx += blockDim.x) {
-      const int o = idx / P, p = idx - o * P;
-      float z[K];
-      z[0] = __ldg(bL + o);
-#pragma unroll
-      for (int c = 1; c < K; ++c) z[c] = 0.f;
-      const float* wrow = WL + o * in_w;
-      for (int j = 0; j < in_w; ++j) {
-        const float w = __ldg(wrow + j);
-#pragma unroll
-        for (int c = 0; c < K; ++c) z[c] = fmaf(w, s.A[(j * K + c) * P + p], z[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < K; ++c) Sk[(o * K + c) * P + p] = z[c];
-      float y[K];
-      if (nd.out_act == XPINN_ACT_SOFTPLUS) {
-        const float g = sigmoid_f(z[0]);
-        const float g1 = g * (1.f - g);
-        y[0] = softplus_f(z[0]);
-        if (K > 1) y[1] = g * z[1];
-        if (K > 2) y[2] = g * z[2];
-        if (K > 3) y[3] = g * z[3] + g1 * z[1] * z[1];
-        if (K > 4) y[4] = g * z[4] + g1 * z[2] * z[2];
-      } else {
-#pragma unroll
-        for (int c = 0; c < K; ++c) y[c] = z[c];
-      }
-#pragma unroll
-      for (int c = 0; c < K; ++c) Uo[(o * K + c) * P + p] = y[c];
-    }
-  }
-  __syncthreads();
-}
-
-// H^{k}[n][c][p] = act(saved S^k) into dst, for all n < wp (padded rows give 0)
-template <int K>
-__device__ __forceinline__ void act_from_saved(float* __restrict__ dst, const float* __restrict__ Sk,
-                                               int wp, int P) {
-  for (int idx = threadIdx.x; idx < wp * P; idx += blockDim.x) {
-    const int n = idx / P, p = idx - n * P;
-    float sv[K], h[K];
-#pragma unroll
-    for (int c = 0; c < K; ++c) sv[c] = Sk[(n * K + c) * P + p];
-    tanh_jet_from_saved<K>(sv, h);
-#pragma unroll
-    for (int c = 0; c < K; ++c) dst[(n * K + c) * P + p] = h[c];
-  }
-}
-
-// The same, transposed: HT[(c*P + p) * wp + n] (row stride wp), for the
-// weight-gradient contraction.  A thread takes one neuron and 4 points.
-template <int K>
-__device__ __forceinline__ void act_from_saved_T(float* __restrict__ HT, const float* __restrict__ Sk,
-                                                 int wp, int P) {
-  const int P4 = P >> 2;
-  for (int idx = threadIdx.x; idx < wp * P4; idx += blockDim.x) {
-    const int n = idx % wp, pq = idx / wp;
-    float4 sv4[K];
-#pragma unroll
-    for (int c = 0; c < K; ++c) sv4[c] = *reinterpret_cast<const float4*>(Sk + (n * K + c) * P + 4 * pq);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      float sv[K], h[K];
-#pragma unroll
-      for (int c = 0; c < K; ++c)
-        sv[c] = t == 0 ? sv4[c].x : (t == 1 ? sv4[c].y : (t == 2 ? sv4[c].z : sv4[c].w));
-      tanh_jet_from_saved<K>(sv, h);
-#pragma unroll
-      for (int c = 0; c < K; ++c) HT[(c * P + 4 * pq + t) * wp + n] = h[c];
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Network reverse pass.  Ub holds the seeds [D][K][P] (overwritten).  The
-// gradient slice gslice receives dW^k, db^k at the network's offsets.
-// ---------------------------------------------------------------------------
-template <int K, int PT>
-__device__ __noinline__ void net_backward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm, int P,
-                             const float* __restrict__ S, int uoff,
-                             float* __restrict__ gslice, bool first) {
-  const Smem s = carve(sl);
-  float* __restrict__ Ub = s.Ub + uoff;
-  const int tid = threadIdx.x;
-  const int n_pg = P / PT;
-  const int L = nd.L;
-  const int KP = K * P;
-  // saved jets of layer L (top), then walk down layer by layer
-  const float* SL = S;
-  for (int k = 1; k < L; ++k) SL += nd.wp[k] * KP;
-
-  // ---- output layer
-  const int D = nd.w[L], in_w = nd.w[L - 1], in_p = nd.wp[L - 1];
-  if (nd.out_act == XPINN_ACT_SOFTPLUS) {
-    for (int idx = tid; idx < D * P; idx += blockDim.x) {
-      const int o = idx / P, p = idx - o * P;
-      float z[K], yb[K], zb[K];
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        z[c] = SL[(o * K + c) * P + p];
-        yb[c] = Ub[(o * K + c) * P + p];
-      }
-      const float g = sigmoid_f(z[0]);
-      const float g1 = g * (1.f - g);
-      const float g2 = g1 * (1.f - 2.f * g);
-      float b0 = g * yb[0];
-      if (K > 1) { zb[1] = g * yb[1]; b0 += g1 * z[1] * yb[1]; }
-      if (K > 2) { zb[2] = g * yb[2]; b0 += g1 * z[2] * yb[2]; }
-      if (K > 3) { zb[3] = g * yb[3]; zb[1] += 2.f * g1 * z[1] * yb[3]; b0 += (g1 * z[3] + g2 * z[1] * z[1]) * yb[3]; }
-      if (K > 4) { zb[4] = g * yb[4]; zb[2] += 2.f * g1 * z[2] * yb[4]; b0 += (g1 * z[4] + g2 * z[2] * z[2]) * yb[4]; }
-      zb[0] = b0;
-#pragma unroll
-      for (int c = 0; c < K; ++c) Ub[(o * K + c) * P + p] = zb[c];
-    }
-  }
-  const float* Sk = SL - in_p * KP;   // saved jets of layer L-1
-  act_from_saved<K>(s.A, Sk, in_p, P);
-  __syncthreads();
-  {
-    float* gW = gslice + nd.off[L];
-    float* gb = gW + D * in_w;
-    // dW^L[o][j] = sum_{c,p} zb^L[o][c][p] H^{L-1}[j][c][p]
-    group_dots(D * in_w, KP / 4, Ub, s.A, [=](int r) { return r / in_w; },
-               [=](int r) { return r % in_w; }, [=](int r, float v) { accum(gW + r, v, first); });
-    // db^L[o] = sum_p zb^L[o][0][p]
-    group_dots(D, P / 4, Ub, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
-               [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
-  }
-  // h-bar^{L-1} = (W^L)^T zb^L into registers
-  float acc[MT][K][PT];
-  {
-    const float* WL = prm + nd.off[L];
-    const int ng = tid / n_pg, pg = tid - ng * n_pg;
-    const int j0 = ng * MT, p0 = pg * PT;
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-      for (int c = 0; c < K; ++c)
-#pragma unroll
-        for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = 0.f;
-    if (ng < in_p / MT) {
-      for (int o = 0; o < D; ++o) {
-        float w[MT];
-#pragma unroll
-        for (int i = 0; i < MT; ++i) w[i] = (j0 + i < in_w) ? __ldg(WL + o * in_w + j0 + i) : 0.f;
-#pragma unroll
-        for (int c = 0; c < K; ++c) {
-          float zb[PT];
-          ldp<PT>(Ub + (o * K + c) * P + p0, zb);
-#pragma unroll
-          for (int i = 0; i < MT; ++i)
-#pragma unroll
-            for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], zb[pp], acc[i][c][pp]);
-        }
-      }
-    }
-  }
-  __syncthreads();
-
-  // ---- hidden layers L-1 .. 1 (Sk points at the saved jets of layer k)
-  for (int k = L - 1; k >= 1; --k) {
-    const int out_p = nd.wp[k], out_w = nd.w[k];
-    const int ng = tid / n_pg, pg = tid - ng * n_pg;
-    const int n0 = ng * MT, p0 = pg * PT;
-    if (ng < out_p / MT) {
-#pragma unroll
-      for (int i = 0; i < MT; ++i) {
-        float sv2[K][PT];
-#pragma unroll
-        for (int c = 0; c < K; ++c) ldp<PT>(Sk + ((n0 + i) * K + c) * P + p0, sv2[c]);
-#pragma unroll
-        for (int pp = 0; pp < PT; ++pp) {
-          float sv[K], hb[K], zb[K];
-#pragma unroll
-          for (int c = 0; c < K; ++c) {
-            sv[c] = sv2[c][pp];
-            hb[c] = acc[i][c][pp];
-          }
-          tanh_jet_bwd<K>(sv, hb, zb);
-#pragma unroll
-          for (int c = 0; c < K; ++c) acc[i][c][pp] = zb[c];
-        }
-#pragma unroll
-        for (int c = 0; c < K; ++c) stp<PT>(s.B + ((n0 + i) * K + c) * P + p0, acc[i][c]);
-      }
-    }
-    float* gW = gslice + nd.off[k];
-    if (k >= 2) {
-      const int in_pk = nd.wp[k - 1], in_wk = nd.w[k - 1];
-      const float* Skm1 = Sk - in_pk * KP;
-      act_from_saved_T<K>(s.A, Skm1, in_pk, P);
-      const float* Wk = prm + nd.off[k];
-      for (int idx = tid; idx < out_p * in_pk; idx += blockDim.x) {
-        const int n = idx / in_pk, j = idx - n * in_pk;
-        s.W[idx] = (n < out_w && j < in_wk) ? __ldg(Wk + n * in_wk + j) : 0.f;
-      }
-      __syncthreads();
-      // h-bar^{k-1} = (W^k)^T zb^k into registers, then dW^k and db^k
-      if (ng < in_pk / MT) gemm_bwd<K, PT>(s.B, s.W, out_w, in_pk, P, n0, p0, acc);
-      float* gb = gW + out_w * in_wk;
-      group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
-                 [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
-      dW_tiles<8>(s.B, s.A, in_pk, out_p, in_pk, out_w, in_wk, KP, s.A, gW, first);
-      Sk = Skm1;
-    } else {
-      __syncthreads();
-      // layer 1: dW^1[n][i] = sum_p zb0[n][p] z_i[p] + sum_p zb_{1+i}[n][p]
-      float* gb = gW + 2 * out_w;
-      group_dots(out_w, P / 4, s.B, s.sx, [=](int r) { return r * K; }, [=](int r) { return 0; },
-                 [=](int r, float v) { accum(gW + 2 * r, v, first); });
-      group_dots(out_w, P / 4, s.B, s.sy, [=](int r) { return r * K; }, [=](int r) { return 0; },
-                 [=](int r, float v) { accum(gW + 2 * r + 1, v, first); });
-      __syncthreads();
-      if (K > 1)
-        group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K + 1; },
-                   [=](int r) { return 0; }, [=](int r, float v) { atomicAdd(gW + 2 * r, v); });
-      if (K > 2)
-        group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K + 2; },
-                   [=](int r) { return 0; }, [=](int r, float v) { atomicAdd(gW + 2 * r + 1, v); });
-      group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
-                 [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
-    }
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// PDE residuals, fluxes and their derivatives with respect to the jets.
-// J[net][o][c]: jets of output o of net `net` (net 1 only for diffusion).
-// ---------------------------------------------------------------------------
-struct PtJets {
-  float u[XPINN_MAX_OUT][KMAX];   // net 0
-  float k[KMAX];                  // net 1 (single output)
-};
-
-__device__ __forceinline__ int residual_fwd(int pde, const PtJets& J, float f, float nu, float re,
-                                            float r[3]) {
-  switch (pde) {
-    case XPINN_PDE_BURGERS:   // u_t + u u_x - nu u_xx - f
-      r[0] = J.u[0][2] + J.u[0][0] * J.u[0][1] - nu * J.u[0][3] - f;
-      return 1;
-    case XPINN_PDE_POISSON:   // -(u_xx + u_yy) - f
-      r[0] = -(J.u[0][3] + J.u[0][4]) - f;
-      return 1;
-    case XPINN_PDE_NS: {
-      const float* u = J.u[0];
-      const float* v = J.u[1];
-      const float* p = J.u[2];
-      const float ire = 1.f / re;
-      r[0] = u[0] * u[1] + v[0] * u[2] + p[1] - (u[3] + u[4]) * ire;
-      r[1] = u[0] * v[1] + v[0] * v[2] + p[2] - (v[3] + v[4]) * ire;
-      r[2] = u[1] + v[2];
-      return 3;
-    }
-    default: {                // K lap u + grad K . grad u - f
-      r[0] = J.k[0] * (J.u[0][3] + J.u[0][4]) + J.k[1] * J.u[0][1] + J.k[2] * J.u[0][2] - f;
-      return 1;
-    }
-  }
-}
-
-// G += sum_eq e[eq] d r_eq / d J
-__device__ __forceinline__ void residual_seed(int pde, const PtJets& J, const float e[3], float nu,
-                                              float re, PtJets& G) {
-  switch (pde) {
-    case XPINN_PDE_BURGERS:
-      G.u[0][0] += e[0] * J.u[0][1];
-      G.u[0][1] += e[0] * J.u[0][0];
-      G.u[0][2] += e[0];
-      G.u[0][3] -= nu * e[0];
-      break;
-    case XPINN_PDE_POISSON:
-      G.u[0][3] -= e[0];
-      G.u[0][4] -= e[0];
-      break;
-    case XPINN_PDE_NS: {
-      const float* u = J.u[0];
-      const float* v = J.u[1];
-      const float ire = 1.f / re;
-      G.u[0][0] += e[0] * u[1] + e[1] * v[1];
-      G.u[0][1] += e[0] * u[0] + e[2];
-      G.u[0][2] += e[0] * v[0];
-      G.u[0][3] -= e[0] * ire;
-      G.u[0][4] -= e[0] * ire;
-      G.u[1][0] += e[0] * u[2] + e[1] * v[2];
-      G.u[1][1] += e[1] * u[0];
-      G.u[1][2] += e[1] * v[0] + e[2];
-      G.u[1][3] -= e[1] * ire;
-      G.u[1][4] -= e[1] * ire;
-      G.u[2][1] += e[0];
-      G.u[2][2] += e[1];
-      break;
-    }
-    default:
-      G.u[0][1] += e[0] * J.k[1];
-      G.u[0][2] += e[0] * J.k[2];
-      G.u[0][3] += e[0] * J.k[0];
-      G.u[0][4] += e[0] * J.k[0];
-      G.k[0] += e[0] * (J.u[0][3] + J.u[0][4]);
-      G.k[1] += e[0] * J.u[0][1];
-      G.k[2] += e[0] * J.u[0][2];
-      break;
-  }
-}
-
-// normal flux f . n (cPINN)
-__device__ __forceinline__ int flux_fwd(int pde, const PtJets& J, float n0, float n1, float nu,
-                                        float re, int mode, float phi[3]) {
-  switch (pde) {
-    case XPINN_PDE_BURGERS: {
-      const float u = J.u[0][0], ux = J.u[0][1];
-      const float fx = mode == XPINN_FLUX_CONSERVATIVE ? 0.5f * u * u - nu * ux : u * ux - nu * ux;
-      phi[0] = n0 * fx + n1 * u;
-      return 1;
-    }
-    case XPINN_PDE_POISSON:
-      phi[0] = -(n0 * J.u[0][1] + n1 * J.u[0][2]);
-      return 1;
-    case XPINN_PDE_NS: {
-      const float* u = J.u[0];
-      const float* v = J.u[1];
-      const float* p = J.u[2];
-      const float ire = 1.f / re;
-      phi[0] = n0 * (u[0] * u[0] + p[0] - u[1] * ire) + n1 * (u[0] * v[0] - u[2] * ire);
-      phi[1] = n0 * (u[0] * v[0] - v[1] * ire) + n1 * (v[0] * v[0] + p[0] - v[2] * ire);
-      phi[2] = n0 * u[0] + n1 * v[0];
-      return 3;
-    }
-    default:
-      phi[0] = J.k[0] * (n0 * J.u[0][1] + n1 * J.u[0][2]);
-      return 1;
-  }
-}
-
-__device__ __forceinline__ void flux_seed(int pde, const PtJets& J, float n0, float n1, float nu,
-                                          float re, int mode, const float e[3], PtJets& G) {
-  switch (pde) {
-    case XPINN_PDE_BURGERS: {
-      const float u = J.u[0][0], ux = J.u[0][1];
-      if (mode == XPINN_FLUX_CONSERVATIVE) {
-        G.u[0][0] += e[0] * (n0 * u + n1);
-        G.u[0][1] += e[0] * (-nu * n0);
-      } else {
-        G.u[0][0] += e[0] * (n0 * ux + n1);
-        G.u[0][1] += e[0] * (n0 * (u - nu));
-      }
-      break;
-    }
-    case XPINN_PDE_POISSON:
-      G.u[0][1] -= e[0] * n0;
-      G.u[0][2] -= e[0] * n1;
-      break;
-    case XPINN_PDE_NS: {
-      const float* u = J.u[0];
-      const float* v = J.u[1];
-      const float ire = 1.f / re;
-      // x-momentum
-      G.u[0][0] += e[0] * (2.f * n0 * u[0] + n1 * v[0]);
-      G.u[1][0] += e[0] * (n1 * u[0]);
-      G.u[2][0] += e[0] * n0;
-      G.u[0][1] -= e[0] * n0 * ire;
-      G.u[0][2] -= e[0] * n1 * ire;
-      // y-momentum
-      G.u[0][0] += e[1] * (n0 * v[0]);
-      G.u[1][0] += e[1] * (n0 * u[0] + 2.f * n1 * v[0]);
-      G.u[2][0] += e[1] * n1;
-      G.u[1][1] -= e[1] * n0 * ire;
-      G.u[1][2] -= e[1] * n1 * ire;
-      // mass
-      G.u[0][0] += e[2] * n0;
-      G.u[1][0] += e[2] * n1;
-      break;
-    }
-    default: {
-      const float gn = n0 * J.u[0][1] + n1 * J.u[0][2];
-      G.k[0] += e[0] * gn;
-      G.u[0][1] += e[0] * J.k[0] * n0;
-      G.u[0][2] += e[0] * J.k[0] * n1;
-      break;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Item processing
-// ---------------------------------------------------------------------------
-template <int PT>
-__device__ void forward_any(int K, SmemLayout sl, const NetDev& nd, const float* prm, int P, float* S,
-                            int uoff) {
-  switch (K) {
-    case 1: net_forward<1, PT>(sl, nd, prm, P, S, uoff); break;
-    case 2: net_forward<2, PT>(sl, nd, prm, P, S, uoff); break;
-    case 3: net_forward<3, PT>(sl, nd, prm, P, S, uoff); break;
-    case 4: net_forward<4, PT>(sl, nd, prm, P, S, uoff); break;
-    default: net_forward<5, PT>(sl, nd, prm, P, S, uoff); break;
-  }
-}
-
-template <int PT>
-__device__ void backward_any(int K, SmemLayout sl, const NetDev& nd, const float* prm, int P,
-                             const float* S, int uoff, float* g, bool first) {
-  switch (K) {
-    case 1: net_backward<1, PT>(sl, nd, prm, P, S, uoff, g, first); break;
-    case 2: net_backward<2, PT>(sl, nd, prm, P, S, uoff, g, first); break;
-    case 3: net_backward<3, PT>(sl, nd, prm, P, S, uoff, g, first); break;
-    case 4: net_backward<4, PT>(sl, nd, prm, P, S, uoff, g, first); break;
-    default: net_backward<5, PT>(sl, nd, prm, P, S, uoff, g, first); break;
-  }
-}
-
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-  return t;
-}
-
-// Jets of point p from U into J (components beyond a net's K stay 0).
-__device__ __forceinline__ void load_point_jets(const SubDev& sd, const Item& it, const float* U,
-                                                int u1, int P, int p, PtJets& J) {
-#pragma unroll
-  for (int o = 0; o < XPINN_MAX_OUT; ++o)
-#pragma unroll
-    for (int c = 0; c < KMAX; ++c) J.u[o][c] = 0.f;
-#pragma unroll
-  for (int c = 0; c < KMAX; ++c) J.k[c] = 0.f;
-  const int K0 = it.K[0], K1 = it.K[1];
-  const int D0 = sd.net[0].w[sd.net[0].L];
-  if (K0) {
-#pragma unroll
-    for (int o = 0; o < XPINN_MAX_OUT; ++o)
-#pragma unroll
-      for (int c = 0; c < KMAX; ++c)
-        if (o < D0 && c < K0) J.u[o][c] = U[(o * K0 + c) * P + p];
-  }
-  if (K1) {
-#pragma unroll
-    for (int c = 0; c < KMAX; ++c)
-      if (c < K1) J.k[c] = U[u1 + c * P + p];
-  }
-}
-
-__device__ __forceinline__ void store_point_seeds(const SubDev& sd, const Item& it, float* Ub, int u1,
-                                                  int P, int p, const PtJets& G) {
-  const int K0 = it.K[0], K1 = it.K[1];
-  const int D0 = sd.net[0].w[sd.net[0].L];
-  if (K0) {
-#pragma unroll
-    for (int o = 0; o < XPINN_MAX_OUT; ++o)
-#pragma unroll
-      for (int c = 0; c < KMAX; ++c)
-        if (o < D0 && c < K0) Ub[(o * K0 + c) * P + p] = G.u[o][c];
-  }
-  if (K1) {
-#pragma unroll
-    for (int c = 0; c < KMAX; ++c)
-      if (c < K1) Ub[u1 + c * P + p] = G.k[c];
-  }
-}
-
-// Loss terms and seeds of one point (see the kind of item).  Returns the
-// point's contributions to the item's two loss sums in l0, l1.
-__device__ __forceinline__ void point_stage(const StepArgs& a, const SubDev& sd, const Item& it,
-                                            const IfaceDev* ifc, const PtJets& J, PtJets& G, bool valid,
-                                            int64_t gp, int64_t ip, double& l0, double& l1) {
-  const int D0 = sd.net[0].w[sd.net[0].L];
-  switch (it.kind) {
-    case IT_RES: {
-      float r[3] = {0.f, 0.f, 0.f};
-      const float f = valid ? a.res_f[gp] : 0.f;
-      const int ne = residual_fwd(a.pde, J, f, a.nu, a.re, r);
-      float sq = 0.f, e[3] = {0.f, 0.f, 0.f};
-      const float coef = 2.f * sd.w_res * sd.inv_n_res;
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-        if (q < ne) {
-          sq += r[q] * r[q];
-          e[q] = valid ? coef * r[q] : 0.f;
-        }
-      if (valid) l0 += (double)sq * sd.inv_n_res;
-      residual_seed(a.pde, J, e, a.nu, a.re, G);
-      break;
-    }
-    case IT_DATA0: {
-      const float* tg = a.tgt + sd.tgt_off[0] + (gp - sd.data_off[0]) * D0;
-      const float coef = 2.f * sd.w_data[0] * sd.inv_n_data[0];
-      float sq = 0.f;
-#pragma unroll
-      for (int o = 0; o < XPINN_MAX_OUT; ++o)
-        if (o < D0) {
-          const float d = valid ? J.u[o][0] - tg[o] : 0.f;
-          sq += d * d;
-          G.u[o][0] = coef * d;
-        }
-      if (valid) l0 += (double)sq * sd.inv_n_data[0];
-      break;
-    }
-    case IT_DATA1: {
-      const float* tg = a.tgt + sd.tgt_off[1] + (gp - sd.data_off[1]);
-      const float coef = 2.f * sd.w_data[1] * sd.inv_n_data[1];
-      const float d = valid ? J.k[0] - tg[0] : 0.f;
-      G.k[0] = coef * d;
-      if (valid) l0 += (double)(d * d) * sd.inv_n_data[1];
-      break;
-    }
-    case IT_IFACE:
-    case IT_IFACE_FWD: {
-      // solution vector (all outputs of all nets) and exchanged quantity
-      float uv[XPINN_MAX_OUT + 1] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int o = 0; o < XPINN_MAX_OUT; ++o)
-        if (o < D0) uv[o] = J.u[o][0];
-      const int nu_ = D0 + (sd.n_nets > 1 ? 1 : 0);
-      if (sd.n_nets > 1) uv[D0] = J.k[0];
-      float qv[3] = {0.f, 0.f, 0.f};
-      const int nq = ifc->method == XPINN_CPINN
-                         ? flux_fwd(a.pde, J, ifc->nx, ifc->ny, a.nu, a.re, a.flux_mode, qv)
-                         : residual_fwd(a.pde, J, 0.f, a.nu, a.re, qv);
-      if (it.kind == IT_IFACE_FWD) {
-        if (valid) {
-          float* d = a.d4 + (ip * 2 + it.side) * a.d4_nv;
-#pragma unroll
-          for (int v = 0; v < XPINN_MAX_OUT + 1; ++v)
-            if (v < nu_) d[v] = uv[v];
-#pragma unroll
-          for (int v = 0; v < 3; ++v)
-            if (v < nq) d[nu_ + v] = qv[v];
-        }
-        break;
-      }
-      const float* dsrc = a.d4 + (ip * 2 + (1 - it.side)) * a.d4_nv;
-      float d[XPINN_MAX_OUT + 1 + 3];
-#pragma unroll
-      for (int v = 0; v < XPINN_MAX_OUT + 1 + 3; ++v)
-        d[v] = v < a.d4_nv ? __ldcg(dsrc + v) : 0.f;   // written by other CTAs in this launch
-      float sa = 0.f, sf = 0.f;
-      const float ca = sd.w_avg * ifc->inv_n;          // d/du of W_I/N ((u-u')/2)^2
-      const float cf = 2.f * sd.w_iface * ifc->inv_n;
-#pragma unroll
-      for (int o = 0; o < XPINN_MAX_OUT; ++o)
-        if (o < D0) {
-          const float dd = valid ? 0.5f * (uv[o] - d[o]) : 0.f;
-          sa += dd * dd;
-          G.u[o][0] += ca * dd;
-        }
-      if (sd.n_nets > 1) {
-        const float dd = valid ? 0.5f * (uv[D0] - d[D0]) : 0.f;
-        sa += dd * dd;
-        G.k[0] += ca * dd;
-      }
-      float e[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-        if (q < nq) {
-          const float dd = valid ? qv[q] - d[nu_ + q] : 0.f;
-          sf += dd * dd;
-          e[q] = cf * dd;
-        }
-      if (ifc->method == XPINN_CPINN)
-        flux_seed(a.pde, J, ifc->nx, ifc->ny, a.nu, a.re, a.flux_mode, e, G);
-      else
-        residual_seed(a.pde, J, e, a.nu, a.re, G);
-      if (valid) {
-        l0 += (double)sa * ifc->inv_n;
-        l1 += (double)sf * ifc->inv_n;
-      }
-      break;
-    }
-    default:
-      break;
-  }
-}
-
-template <int PT>
-__device__ void process_item(const StepArgs& a, SmemLayout sl, const Item& it, int item_idx,
-                             float* __restrict__ scratch) {
-  const Smem s = carve(sl);
-  const SubDev& sd = a.subs[it.q];
-  const int P = it.P;
-  const float* prm = a.params + sd.poff;
-  const int tid = threadIdx.x;
-  const bool has_bwd = it.kind <= IT_IFACE;
-  // offsets of net 1 in U and in the scratch (net 0 starts at 0)
-  int u1 = 0;
-  int64_t s1 = 0;
-  if (it.K[0]) {
-    const NetDev& nd = sd.net[0];
-    u1 = nd.w[nd.L] * it.K[0] * P;
-    int64_t rows = 0;
-    for (int k = 1; k < nd.L; ++k) rows += nd.wp[k];
-    s1 = (rows + nd.w[nd.L]) * it.K[0] * P;
-  }
-  const IfaceDev* ifc = (it.kind == IT_IFACE || it.kind == IT_IFACE_FWD) ? &a.ifaces[it.edge] : nullptr;
-  double l0 = 0.0, l1 = 0.0;
-  for (int t0 = 0; t0 < it.n_pts; t0 += P) {
-    const int nv = min(P, it.n_pts - t0);
-    const bool first = t0 == 0;
-    const float2* src = (it.kind == IT_EVAL) ? a.eval_pts : a.pts;
-    for (int p = tid; p < P; p += blockDim.x) {
-      float2 z = make_float2(0.f, 0.f);
-      if (p < nv) z = src[it.pt_off + t0 + p];
-      s.sx[p] = z.x;
-      s.sy[p] = z.y;
-    }
-    __syncthreads();
-    if (it.K[0]) forward_any<PT>(it.K[0], sl, sd.net[0], prm, P, scratch, 0);
-    if (it.K[1]) forward_any<PT>(it.K[1], sl, sd.net[1], prm, P, scratch + s1, u1);
-    // ---- per point: loss terms and seeds (or exchange / evaluation output)
-    for (int p = tid; p < P; p += blockDim.x) {
-      const bool valid = p < nv;
-      PtJets J, G;
-      load_point_jets(sd, it, s.U, u1, P, p, J);
-      if (it.kind == IT_EVAL) {
-        if (valid) {
-          float* out = a.eval_out + it.out_off + (int64_t)(t0 + p) * a.eval_dout;
-          const float sc = a.eval_scale ? a.eval_scale[it.pt_off + t0 + p] : 1.f;
-          const int K0 = it.K[0], K1 = it.K[1];
-          const int D0 = sd.net[0].w[sd.net[0].L];
-          int col = 0;
-          if (K0) {
-#pragma unroll
-            for (int o = 0; o < XPINN_MAX_OUT; ++o)
-#pragma unroll
-              for (int c = 0; c < KMAX; ++c)
-                if (o < D0 && c < K0) out[col++] = sc * J.u[o][c];
-          }
-          if (K1) {
-#pragma unroll
-            for (int c = 0; c < KMAX; ++c)
-              if (c < K1) out[col++] = sc * J.k[c];
-          }
-        }
-        continue;
-      }
-#pragma unroll
-      for (int o = 0; o < XPINN_MAX_OUT; ++o)
-#pragma unroll
-        for (int c = 0; c < KMAX; ++c) G.u[o][c] = 0.f;
-#pragma unroll
-      for (int c = 0; c < KMAX; ++c) G.k[c] = 0.f;
-      const int64_t gp = it.pt_off + t0 + p;   // global point index
-      const int64_t ip = ifc ? ifc->d4_pt + (it.pt_off - ifc->pt_off) + t0 + p : 0;
-      point_stage(a, sd, it, ifc, J, G, valid, gp, ip, l0, l1);
-      if (has_bwd) store_point_seeds(sd, it, s.Ub, u1, P, p, G);
-    }
-    __syncthreads();
-    if (has_bwd) {
-      float* gs = a.partials + it.part_off;
-      if (it.K[0]) backward_any<PT>(it.K[0], sl, sd.net[0], prm, P, scratch, 0, gs, first);
-      if (it.K[1]) backward_any<PT>(it.K[1], sl, sd.net[1], prm, P, scratch + s1, u1, gs, first);
-      // a net that is not evaluated by this item contributes zero gradient
-      if (first)
-        for (int n = 0; n < sd.n_nets; ++n)
-          if (!it.K[n]) {
-            const NetDev& nd = sd.net[n];
-            const int beg = nd.off[1];
-            const int end = nd.off[nd.L] + nd.w[nd.L] * (nd.w[nd.L - 1] + 1);
-            for (int e = beg + tid; e < end; e += blockDim.x) gs[e] = 0.f;
-          }
-    }
-    __syncthreads();
-  }
-  if (has_bwd) {
-    const double t0s = block_sum(l0, s.red);
-    const double t1s = block_sum(l1, s.red);
-    if (tid == 0) {
-      a.loss_part[2 * item_idx] = t0s;
-      a.loss_part[2 * item_idx + 1] = t1s;
-    }
-  }
-}
-
-// PT = 1 keeps registers <= 128 so that two CTAs fit on an SM; PT = 2 uses
-// a larger register tile at one CTA per SM.
-// Wait (thread 0) until `need` exchange items have completed.  Every exchange
-// item is claimed before any item that waits, and exchange items never wait,
-// so the wait ends; it is still bounded: after about 1 s it sets the error
-// flag and returns false, and the item is skipped.
-__device__ bool wait_exchange(const StepArgs& a) {
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    unsigned ns = 32;
-    for (long it = 0; atomicAdd(a.fwd_done, 0) < a.n_fwd_wait; ++it) {
-      if (it > (1l << 20) || atomicAdd(a.err, 0) != 0) {   // gave up here or elsewhere
-        atomicCAS(a.err, 0, XPINN_ERR_TIMEOUT);
-        ok = 0;
-        break;
-      }
-      __nanosleep(ns);
-      if (ns < 1024) ns <<= 1;
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// PT = 1 keeps registers <= 128 so that two 256-thread CTAs fit on an SM;
-// PT = 2 uses a larger register tile.  NTH = 128 halves the CTA so that two
-// (or four) independent CTAs share an SM and one CTA's narrow phases (first
-// and output layers, loss, small reductions) overlap another's contractions.
-// NTH = 512 with PT = 1 keeps the sub-tile of 256 x PT=2 with twice the warps.
-template <int PT, int NTH>
-__global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : (PT == 1 ? 2 : 1) * (256 / NTH)) jet_step_kernel(StepArgs a) {
-  const SmemLayout sl{a.szA, a.szW, a.szU, a.pmax};
-  __shared__ int s_item;
-  float* scratch = a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
-    __syncthreads();
-    const int it = s_item;
-    __syncthreads();
-    if (it >= a.n_items) break;
-    if (a.n_fwd_wait > 0 && it >= a.wait_from && !wait_exchange(a)) continue;
-    const Item& item = a.items[it];
-    process_item<PT>(a, sl, item, a.item_base + it, scratch);
-    if (item.kind == IT_IFACE_FWD && a.n_fwd_wait > 0) {
-      __syncthreads();                      // every thread's exchange stores issued
-      if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(a.fwd_done, 1);
-      }
-    }
-  }
-}
+}  // namespace
 
 size_t jet_step_smem_bytes(const StepArgs& a) {
   const size_t floats = 2 * (size_t)a.szA + a.szW + 2 * (size_t)a.szU + (MAXW + 16) + 2 * (size_t)a.pmax;
@@ -1174,26 +34,20 @@ size_t jet_step_smem_bytes(const StepArgs& a) {
 
 cudaError_t jet_step_configure(size_t smem) {
   const int v = (int)smem;
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(jet_step_kernel<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, v))) return e;
-  if ((e = cudaFuncSetAttribute(jet_step_kernel<2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, v))) return e;
-  if ((e = cudaFuncSetAttribute(jet_step_kernel<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, v))) return e;
-  if ((e = cudaFuncSetAttribute(jet_step_kernel<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, v))) return e;
-  return cudaFuncSetAttribute(jet_step_kernel<1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+  const int cfg[5][2] = {{1, 256}, {2, 256}, {1, 128}, {2, 128}, {1, 512}};
+  for (const bool gen : {false, true})
+    for (const auto& c : cfg) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(kernel_for(c[0], c[1], gen), cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
 }
 
-int jet_step_blocks_per_sm(int pt, int nt, size_t smem) {
+int jet_step_blocks_per_sm(int pt, int nt, bool gen, size_t smem) {
+  const void* k = kernel_for(nt == 512 ? 1 : pt, nt, gen);
   int n = 0;
-  cudaError_t e;
-  if (nt == 512)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<1, 512>, 512, smem);
-  else if (nt == 128)
-    e = pt == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<1, 128>, 128, smem)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<2, 128>, 128, smem);
-  else
-    e = pt == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<1, 256>, 256, smem)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jet_step_kernel<2, 256>, 256, smem);
-  if (e != cudaSuccess) {
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, nt, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -1201,19 +55,11 @@ int jet_step_blocks_per_sm(int pt, int nt, size_t smem) {
 }
 
 void launch_jet_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
-  if (a.nt == 512) {
-    jet_step_kernel<1, 512><<<grid, 512, smem, s>>>(a);
-  } else if (a.nt == 128) {
-    if (a.pt == 1)
-      jet_step_kernel<1, 128><<<grid, 128, smem, s>>>(a);
-    else
-      jet_step_kernel<2, 128><<<grid, 128, smem, s>>>(a);
-  } else {
-    if (a.pt == 1)
-      jet_step_kernel<1, 256><<<grid, 256, smem, s>>>(a);
-    else
-      jet_step_kernel<2, 256><<<grid, 256, smem, s>>>(a);
-  }
+  const int nt = a.nt == 512 || a.nt == 128 ? a.nt : 256;
+  const void* k = kernel_for(nt == 512 || a.pt == 1 ? 1 : 2, nt, a.gen != 0);
+  StepArgs arg = a;
+  void* params[] = {&arg};
+  cudaLaunchKernel(k, dim3(grid), dim3(nt), params, smem, s);
 }
 
 }  // namespace xp

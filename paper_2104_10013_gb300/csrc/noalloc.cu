@@ -131,6 +131,11 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   if (net->widths[L] != (pde == XPINN_PDE_NS ? 3 : 1)) return fail(XPINN_ERR_INVALID, "wrong output count");
   if (net->out_act != XPINN_ACT_IDENTITY && net->out_act != XPINN_ACT_SOFTPLUS)
     return fail(XPINN_ERR_INVALID, "bad out_act");
+  if (net->act != XPINN_PHI_TANH && net->act != XPINN_PHI_SIN && net->act != XPINN_PHI_COS)
+    return fail(XPINN_ERR_INVALID, "bad act");
+  if ((net->adaptive != 0 && net->adaptive != 1) ||
+      (net->adaptive && !(net->slope_scale > 0.f && net->slope_scale < 3.0e38f)))
+    return fail(XPINN_ERR_INVALID, "bad adaptive slope settings");
   if (pde == XPINN_PDE_NS && !(re > 0)) return fail(XPINN_ERR_INVALID, "Reynolds number must be > 0");
   cudaStream_t s = (cudaStream_t)stream;
 
@@ -161,18 +166,9 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   SubDev& sd = d.sd;
   sd.n_nets = 1;
   NetDev& nd = sd.net[0];
-  nd.L = L;
-  nd.out_act = net->out_act;
-  int off = 0, wmax = MT;
-  for (int k = 0; k <= L; ++k) {
-    nd.w[k] = net->widths[k];
-    nd.wp[k] = (nd.w[k] + MT - 1) / MT * MT;
-    if (k >= 1 && k < L) wmax = std::max(wmax, nd.wp[k]);
-  }
-  for (int k = 1; k <= L; ++k) {
-    nd.off[k] = off;
-    off += nd.w[k] * nd.w[k - 1] + nd.w[k];
-  }
+  const int off = fill_net_dev(nd, *net, 0);
+  int wmax = MT;
+  for (int k = 1; k < L; ++k) wmax = std::max(wmax, nd.wp[k]);
   sd.n_params = off;
   sd.w_res = w_res;
   sd.n_res = (int)n;
@@ -249,6 +245,7 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   a.pmax = P;
   a.pt = 2;
   a.nt = NT;
+  a.gen = net_is_general(nd) ? 1 : 0;
   a.err = reinterpret_cast<int*>(base + lay.err);
   const size_t smem = jet_step_smem_bytes(a);
   int optin = 0;

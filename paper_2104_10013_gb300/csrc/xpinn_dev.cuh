@@ -47,7 +47,38 @@ struct NetDev {
   int wp[MAXL + 1];      // widths padded to a multiple of MT
   int off[MAXL + 1];     // offset of W^k inside the subdomain's parameters (k >= 1);
                          // b^k follows W^k
+  int act;               // hidden activation XPINN_PHI_*
+  int aoff;              // offset of the slopes a^1..a^{L-1}, or -1 (slopes fixed, n a^k = 1)
+  float scale;           // n of n a^k
+  int end;               // one past the network's last parameter
 };
+
+// A network that is not tanh with fixed slopes needs the general passes.
+__host__ __device__ inline bool net_is_general(const NetDev& nd) {
+  return !(nd.act == XPINN_PHI_TANH && nd.aoff < 0);
+}
+
+// Fills the layout fields of a NetDev from a network description whose
+// parameters start at `off` in the subdomain's block; returns the offset
+// one past them.  Layout: W^1, b^1, ..., W^L, b^L, then the slopes.
+inline int fill_net_dev(NetDev& nd, const xpinn_net_desc& n, int off) {
+  nd.L = n.n_layers;
+  nd.out_act = n.out_act;
+  nd.act = n.act;
+  for (int k = 0; k <= nd.L; ++k) {
+    nd.w[k] = n.widths[k];
+    nd.wp[k] = (nd.w[k] + MT - 1) / MT * MT;
+  }
+  for (int k = 1; k <= nd.L; ++k) {
+    nd.off[k] = off;
+    off += nd.w[k] * nd.w[k - 1] + nd.w[k];
+  }
+  nd.aoff = n.adaptive ? off : -1;
+  nd.scale = n.adaptive ? n.slope_scale : 1.f;
+  if (n.adaptive) off += nd.L - 1;
+  nd.end = off;
+  return off;
+}
 
 struct SubDev {
   int n_nets;
@@ -118,7 +149,8 @@ struct StepArgs {
   int szA, szW, szU;
   int pmax;              // largest sub-tile of any item
   int pt;                // points per thread in the register tile (1 or 2)
-  int nt;                // threads per CTA (256 or 128)
+  int nt;                // threads per CTA (256, 128 or 512)
+  int gen;               // 1: some network needs the general passes (general kernel)
   // eval
   const float2* eval_pts;
   float* eval_out;
@@ -131,7 +163,7 @@ struct StepArgs {
 void launch_jet_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
 size_t jet_step_smem_bytes(const StepArgs& a);
 cudaError_t jet_step_configure(size_t smem);
-int jet_step_blocks_per_sm(int pt, int nt, size_t smem);
+int jet_step_blocks_per_sm(int pt, int nt, bool gen, size_t smem);
 
 struct ReduceArgs {
   const int2* blocks;        // (subdomain, first param) of each CTA

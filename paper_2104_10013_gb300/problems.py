@@ -499,7 +499,8 @@ def _sample_region(rng, poly, sites, q, n, batch=200000):
 
 
 def diffusion_xpinn(n_regions=10, n_res=30000, n_obs=500, n_iface=100, n_kbc=50, n_copies=256,
-                    u_hidden=(40,) * 5, k_hidden=(20,) * 4, noise=0.01, seed=0) -> Problem:
+                    u_hidden=(40,) * 5, k_hidden=(20,) * 4, noise=0.01, seed=0,
+                    acts=(PHI_TANH, PHI_SIN, PHI_COS), adaptive=True) -> Problem:
     """Inverse diffusion div(K grad u) = f (Eq. heq) with unknown K, on a seeded
     non-convex star polygon split into the clipped Voronoi regions of
     n_regions seeded sites; two networks per region, u and K (softplus
@@ -509,7 +510,9 @@ def diffusion_xpinn(n_regions=10, n_res=30000, n_obs=500, n_iface=100, n_kbc=50,
     region, n_iface points on every common Voronoi edge (XPINN).  n_copies
     independent copies share the points and differ in initial weights,
     learning rate (log-uniform in [1e-4, 1e-2]) and the weights W_I, W_F
-    (log-uniform in [0.1, 10])."""
+    (log-uniform in [0.1, 10]).  Region q uses the hidden activation
+    acts[q % len(acts)] with trainable slopes (initially n a^k = 1): with the
+    defaults tanh, sin, cos, tanh, ... as in Table Table_USmap."""
     g = _rng(seed, 40)
     poly = star_polygon(g)
     sites = []
@@ -526,8 +529,9 @@ def diffusion_xpinn(n_regions=10, n_res=30000, n_obs=500, n_iface=100, n_kbc=50,
     cnt = _split_counts(20 * n_kbc * n_regions, lens)
     bpts = np.concatenate([_segment_points(gb, c, a, b) for (a, b), c in zip(edges, cnt)])
     bown = nearest_site(bpts, sites)
-    u_net = NetSpec([2, *u_hidden, 1])
-    k_net = NetSpec([2, *k_hidden, 1], ACT_SOFTPLUS)
+    u_nets = [NetSpec([2, *u_hidden, 1], act=acts[q % len(acts)], adaptive=adaptive) for q in range(n_regions)]
+    k_nets = [NetSpec([2, *k_hidden, 1], ACT_SOFTPLUS, act=acts[q % len(acts)], adaptive=adaptive)
+              for q in range(n_regions)]
     region_pts = []
     for q in range(n_regions):
         rng = _rng(seed, 42, q)
@@ -561,6 +565,7 @@ def diffusion_xpinn(n_regions=10, n_res=30000, n_obs=500, n_iface=100, n_kbc=50,
         w_f = float(10 ** hp.uniform(-1, 1))
         for q in range(n_regions):
             res, f, du, dk = region_pts[q]
+            u_net, k_net = u_nets[q], k_nets[q]
             sub = Subdomain(nets=[u_net, k_net], res_xy=res, res_f=f, data=[du, dk], w_data=[1.0, 1.0],
                             w_res=w_f, w_avg=w_i, w_iface=w_i, lr=lr)
             lo, hi = poly.min(0), poly.max(0)

@@ -30,7 +30,8 @@ class XpinnError(RuntimeError):
 
 
 class NetDesc(C.Structure):
-    _fields_ = [("n_layers", C.c_int32), ("widths", C.c_int32 * (MAX_LAYERS + 1)), ("out_act", C.c_int32)]
+    _fields_ = [("n_layers", C.c_int32), ("widths", C.c_int32 * (MAX_LAYERS + 1)), ("out_act", C.c_int32),
+                ("act", C.c_int32), ("adaptive", C.c_int32), ("slope_scale", C.c_float)]
 
 
 class SubDesc(C.Structure):
@@ -175,6 +176,9 @@ class Solver:
                 for k, w in enumerate(net.widths):
                     d.nets[n].widths[k] = w
                 d.nets[n].out_act = net.out_act
+                d.nets[n].act = net.act
+                d.nets[n].adaptive = int(net.adaptive)
+                d.nets[n].slope_scale = net.slope_scale
             d.n_res = s.res_xy.shape[0]
             d.res_xy = arr(s.res_xy) if d.n_res else None
             d.res_f = arr(s.res_f) if d.n_res else None

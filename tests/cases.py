@@ -45,3 +45,16 @@ def tiny_problem(pde, method, n_sub=2, widths=None, n_res=7, n_data=5, n_if=4, s
     return P.Problem("tiny", pde, subs, ifaces, nu=NU, re=7.0)
 
 
+
+
+def with_activations(pb, acts, adaptive=True, seed=0):
+    """The problem with hidden activation acts[q % len(acts)] in subdomain q
+    (as in Table Table_USmap, where tanh and sin networks sit side by side)
+    and, with `adaptive`, trainable slopes drawn in [0.08, 0.15] (n a^k in
+    [0.8, 1.5] for n = 10) so that their gradients are exercised."""
+    import dataclasses
+    rng = np.random.default_rng(500 + seed)
+    for q, s in enumerate(pb.subs):
+        s.nets = [dataclasses.replace(n, act=acts[q % len(acts)], adaptive=adaptive) for n in s.nets]
+        s.slopes = [P._f32(rng.uniform(0.08, 0.15, size=n.n_slopes)) for n in s.nets] if adaptive else []
+    return pb

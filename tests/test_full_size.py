@@ -58,5 +58,5 @@ def test_inverse_diffusion_256_copies_sampled():
     B.build()
     X.load()
     pb = P.diffusion_xpinn()
-    assert pb.n_sub == 2560 and pb.n_params == 256 * 80620
+    assert pb.n_sub == 2560 and pb.n_params == 256 * (80620 + 10 * (5 + 4))   # weights, biases; slopes
     check_sample(X, pb, [3, 1234, 2559])

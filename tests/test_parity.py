@@ -20,7 +20,7 @@ import pytest
 
 from oracle import Oracle
 from paper_2104_10013_gb300 import problems as P
-from tests.cases import CASES, tiny_problem
+from tests.cases import CASES, tiny_problem, with_activations
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +59,8 @@ def tensor_slices(pb):
                 no, ni = net.widths[k], net.widths[k - 1]
                 out.append((f"q{q}n{n}W{k}", slice(off, off + no * ni))); off += no * ni
                 out.append((f"q{q}n{n}b{k}", slice(off, off + no))); off += no
+            if net.n_slopes:
+                out.append((f"q{q}n{n}a", slice(off, off + net.n_slopes))); off += net.n_slopes
     return out
 
 

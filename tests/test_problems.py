@@ -63,3 +63,19 @@ def test_spacetime_burgers_interfaces():
             assert it.method == P.XPINN and np.allclose(it.xy[:, 1], it.xy[0, 1])
     ic = [s for s in pb.subs if s.rect[2] == 0.0]
     assert len(ic) == 4 and all(s.data[0] is not None for s in ic)
+
+
+def test_inverse_diffusion_uses_the_table_activations():
+    """Table Table_USmap: region activations tanh, sin, cos, tanh, ... with
+    trainable slopes, initialised to n a^k = 1."""
+    pb = P.diffusion_xpinn(n_res=200, n_obs=20, n_iface=10, n_kbc=5, n_copies=1)
+    want = [P.PHI_TANH, P.PHI_SIN, P.PHI_COS] * 4
+    for q, s in enumerate(pb.subs):
+        for net in s.nets:
+            assert net.act == want[q] and net.adaptive and net.slope_scale == 10.0
+    theta = pb.packed_params()
+    off = 0
+    for s in pb.subs:
+        for net in s.nets:
+            off += net.n_params
+            assert np.all(theta[off - net.n_slopes:off] * net.slope_scale == np.float32(0.1) * 10)
