@@ -154,6 +154,13 @@ struct xpinn_ctx {
   DevBuf<int> q_items_d, q_item_begin_d, counters, state_i, err_d;
   DevBuf<int64_t> q_part_off_d;
   DevBuf<int2> red_blocks_d;
+  // weight images (see NetDev): rebuilt from params at the start of every
+  // step and before an evaluation when params changed since the last build
+  DevBuf<float> wimg;
+  DevBuf<PackBlock> pack_d;
+  std::vector<PackBlock> pack_h;
+  int64_t n_img = 0;
+  bool img_stale = true;
   // eval
   DevBuf<float2> e_pts, e_epts;
   DevBuf<float> e_out, e_escale, e_eout;
@@ -282,7 +289,7 @@ void item_needs(const SubDev& sd, const Item& it, Limits& l) {
       rows += nd.wp[k];
       l.szA = std::max(l.szA, nd.wp[k] * K * it.P);
     }
-    for (int k = 2; k < nd.L; ++k) l.szW = std::max(l.szW, nd.wp[k] * nd.wp[k - 1]);
+    for (int k = 2; k < nd.L; ++k) l.szW = std::max(l.szW, layer_img_floats(nd, k));
     u += nd.w[nd.L] * K * it.P;
     sc += (int64_t)(rows + nd.w[nd.L]) * K * it.P;
   }
@@ -548,10 +555,15 @@ void mark(xpinn_ctx* h, int i, cudaStream_t s) {
   if (h->opt.profile_phases) ck(cudaEventRecordWithFlags(h->ev[i], s, cudaEventRecordExternal), "event");
 }
 
+void pack_images(xpinn_ctx* h, cudaStream_t s) {
+  launch_pack_weights(h->params.p, h->pack_d.p, (int)h->pack_h.size(), h->wimg.p, s);
+}
+
 void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads) {
   const Plan& pl = h->plan;
   mark(h, 0, s);
   launch_step_begin(h->counters.p, h->n_counters, h->step_t(), h->loss_slot(), adam ? 1 : 0, s);
+  pack_images(h, s);
   const int n_main = (int)pl.items.size() - pl.n_fwd;
   ReduceArgs r{};
   r.blocks = h->red_blocks_d.p;
@@ -655,6 +667,10 @@ void run_eval_items(xpinn_ctx* h, std::vector<Item>& items, const float2* pts, f
   h->e_items.ensure(items.size());
   ck(cudaMemcpyAsync(h->e_items.p, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice, s),
      "items");
+  if (h->img_stale) {
+    pack_images(h, s);
+    h->img_stale = false;
+  }
   StepArgs a = h->base;
   a.items = h->e_items.p;
   a.n_items = (int)items.size();
@@ -784,13 +800,22 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
     SubDev sd{};
     sd.n_nets = s.n_nets;
     sd.poff = poff;
-    int off = 0;
+    sd.img_off = h->n_img;
+    int off = 0, ioff = 0;
     for (int n = 0; n < s.n_nets; ++n) {
       validate_net(s.nets[n], d->pde, n, q);
       off = fill_net_dev(sd.net[n], s.nets[n], off);
+      NetDev& nd = sd.net[n];
+      ioff = assign_images(nd, ioff);
+      for (int k = 2; k < nd.L; ++k) {
+        const int64_t src = sd.poff + nd.off[k];
+        h->pack_h.push_back({src, sd.img_off + nd.imf[k], nd.w[k - 1], nd.w[k], nd.wp[k - 1], nd.wp[k], 1});
+        h->pack_h.push_back({src, sd.img_off + nd.imb[k], nd.w[k - 1], nd.w[k], nd.wp[k - 1], nd.wp[k], 0});
+      }
     }
     sd.n_params = off;
     poff += off;
+    h->n_img += ioff;
     if (s.n_res < 0 || (s.n_res > 0 && !s.res_xy)) fail(XPINN_ERR_INVALID, "subdomain %d: bad residual points", q);
     if (s.n_res > (1 << 30)) fail(XPINN_ERR_UNSUPPORTED, "subdomain %d: too many residual points", q);
     sd.res_off = (int64_t)pts_res.size();
@@ -890,6 +915,8 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
   h->poly.upload(poly_h.data(), poly_h.size());
   h->tgt.upload(tgt.data(), tgt.size());
   h->params.upload(d->init_params, (size_t)h->n_params);
+  h->wimg.alloc((size_t)std::max<int64_t>(4, h->n_img));
+  h->pack_d.upload(h->pack_h.data(), h->pack_h.size());
   h->m.alloc((size_t)h->n_params);
   h->v.alloc((size_t)h->n_params);
   h->grads.alloc((size_t)h->n_params);
@@ -908,6 +935,7 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
   a.subs = h->subs_d.p;
   a.ifaces = h->ifaces_d.p;
   a.params = h->params.p;
+  a.wimg = h->wimg.p;
   a.pts = h->pts.p;
   a.res_f = h->res_f.p;
   a.tgt = h->tgt.p;
@@ -953,6 +981,7 @@ int xpinn_set_params(xpinn_handle h, const float* src, int64_t n, void* stream) 
   if (!h || !src || n != h->n_params) fail(XPINN_ERR_INVALID, "bad arguments");
   DeviceGuard dg(h);
   copy_in(h->params.p, src, n * sizeof(float), (cudaStream_t)stream);
+  h->img_stale = true;
   API_END
 }
 
@@ -1020,6 +1049,7 @@ int xpinn_step(xpinn_handle h, int32_t n_steps, float* losses, void* stream) {
     }
     done += chunk;
   }
+  h->img_stale = true;
   ck(cudaGetLastError(), "step");
   if (losses && !dev_out) check_device_error(h, s);
   if (losses && !dev_out) {
@@ -1184,6 +1214,7 @@ int xpinn_set_state(xpinn_handle h, const void* blob, size_t n) {
   ck(cudaMemcpy(h->params.p, p, sizeof(float) * h->n_params, cudaMemcpyHostToDevice), "state");
   ck(cudaMemcpy(h->m.p, p + h->n_params, sizeof(float) * h->n_params, cudaMemcpyHostToDevice), "state");
   ck(cudaMemcpy(h->v.p, p + 2 * h->n_params, sizeof(float) * h->n_params, cudaMemcpyHostToDevice), "state");
+  h->img_stale = true;
   ck(cudaMemcpy(h->step_t(), &hd.step_t, sizeof(int), cudaMemcpyHostToDevice), "state");
   h->host_t = hd.step_t;
   API_END

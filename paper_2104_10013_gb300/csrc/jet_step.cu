@@ -28,8 +28,10 @@ const void* kernel_for(int pt, int nt, bool gen) {
 }  // namespace
 
 size_t jet_step_smem_bytes(const StepArgs& a) {
-  const size_t floats = 2 * (size_t)a.szA + a.szW + 2 * (size_t)a.szU + (MAXW + 16) + 2 * (size_t)a.pmax;
-  return floats * sizeof(float) + 32 * sizeof(double);
+  // A, B, two weight buffers, U, Ub, point coordinates; 32 doubles for
+  // reductions and two mbarriers (see carve in jet_step.cuh)
+  const size_t floats = 2 * (size_t)a.szA + 2 * (size_t)a.szW + 2 * (size_t)a.szU + 2 * (size_t)a.pmax;
+  return floats * sizeof(float) + 32 * sizeof(double) + 2 * sizeof(uint64_t);
 }
 
 cudaError_t jet_step_configure(size_t smem) {

@@ -58,13 +58,14 @@ __device__ __forceinline__ void stp(float* p, const float (&v)[PT]) {
 struct Smem {
   float* A;      // activations H^{k} / H^{k-1}      [wp][K][P]
   float* B;      // adjoints z-bar^k                 [wp][K][P]
-  float* W;      // one layer's weights, padded
+  float* W0;     // two weight-image buffers: one layer's image is copied
+  float* W1;     //   into one while the other layer's is in use
   float* U;      // output jets of every net         [D][K][P] per net
   float* Ub;     // seeds (adjoints of U)
-  float* bias;   // MAXW + 16
   float* sx;     // point coordinates, SoA
   float* sy;
   double* red;   // 32 doubles for block reductions
+  uint64_t* bar; // 2 mbarriers, one per weight buffer
 };
 
 // Sizes of the shared-memory regions (floats).  Functions that are not
@@ -80,14 +81,65 @@ __device__ __forceinline__ Smem carve(SmemLayout l) {
   Smem s;
   s.A = sm;
   s.B = s.A + l.szA;
-  s.W = s.B + l.szA;
-  s.U = s.W + l.szW;
+  s.W0 = s.B + l.szA;
+  s.W1 = s.W0 + l.szW;
+  s.U = s.W1 + l.szW;
   s.Ub = s.U + l.szU;
-  s.bias = s.Ub + l.szU;
-  s.sx = s.bias + (MAXW + 16);
+  s.sx = s.Ub + l.szU;
   s.sy = s.sx + l.pmax;
   s.red = reinterpret_cast<double*>(s.sy + l.pmax);
+  s.bar = reinterpret_cast<uint64_t*>(s.red + 32);
   return s;
+}
+
+// ---------------------------------------------------------------------------
+// Weight images are brought into shared memory by the bulk-copy (TMA) engine:
+// one cp.async.bulk per layer, completion counted in bytes on an mbarrier.
+// Each of the two buffers has its own mbarrier; the parity of the phase to
+// wait for is tracked in the bits of `ph` (bit b for buffer b), which every
+// thread updates identically.  Waits are bounded (about a second at 2 GHz);
+// a wait that gives up sets the error flag and returns, so the launch ends
+// and the host reports XPINN_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// One thread: copy `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global memory to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(float* dst, const float* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Every thread: wait for the phase of `bar` with parity `parity`.  Once any
+// wait of the launch has given up, the others return at once.
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  const long long t0 = clock64();
+  for (unsigned it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return;
+    if ((it & 1023u) == 1023u && *reinterpret_cast<volatile int*>(err) != 0) return;
+    if (clock64() - t0 > (1ll << 31)) {
+      atomicCAS(err, 0, XPINN_ERR_TIMEOUT);
+      return;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -478,27 +530,50 @@ __device__ __forceinline__ void group_dots(int rows, int len4, const float* __re
   }
 }
 
+// The CTA's walk over a row-major [rows][P] array: this thread's elements
+// tid, tid + blockDim.x, ... as (row r, column c), stepped without division.
+struct Walk {
+  int r, c, dr, dc, P;
+  __device__ __forceinline__ explicit Walk(int P_) : P(P_) {
+    r = (int)threadIdx.x / P;
+    c = (int)threadIdx.x - r * P;
+    dr = (int)blockDim.x / P;
+    dc = (int)blockDim.x - dr * P;
+  }
+  __device__ __forceinline__ void next() {
+    r += dr;
+    c += dc;
+    if (c >= P) {
+      c -= P;
+      ++r;
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Network forward with jets.  Leaves the output jets in Uo [D][K][P] and the
 // saved pre-activation jets of every layer in S.
 // S layout: layer 1..L-1: [wp_k][K][P] each, then layer L: [D][K][P].
 // ---------------------------------------------------------------------------
 template <int K, int PT, bool GEN>
-__device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm, int P,
-                            float* __restrict__ S, int uoff) {
+__device__ __noinline__ uint32_t net_forward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm,
+                                             const float* __restrict__ img, int P, float* __restrict__ S,
+                                             int uoff, uint32_t ph, int* err) {
   const Smem s = carve(sl);
   float* __restrict__ Uo = s.U + uoff;
   const int tid = threadIdx.x;
   const int n_pg = P / PT;
   const int L = nd.L;
+  // the first hidden-to-hidden layer's image (into buffer 0) while layer 1 runs
+  if (tid == 0 && L > 2) bulk_g2s(s.W0, img + nd.imf[2], 4u * layer_img_floats(nd, 2), s.bar);
   // ---- layer 1 (2 inputs): z = W^1 x + b^1, z_i = W^1[:, i], z_ii = 0
   {
     const Act a1 = GEN ? layer_act(nd, prm, 1) : Act{};
     const int w1 = nd.w[1], wp1 = nd.wp[1];
     const float* W1 = prm + nd.off[1];
     const float* b1 = W1 + 2 * w1;
-    for (int idx = tid; idx < wp1 * P; idx += blockDim.x) {
-      const int n = idx / P, p = idx - n * P;
+    for (Walk wk(P); wk.r < wp1; wk.next()) {
+      const int n = wk.r, p = wk.c;
       float w0 = 0.f, wv = 0.f, b = 0.f;
       if (n < w1) {
         w0 = __ldg(W1 + 2 * n);
@@ -521,24 +596,28 @@ __device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const 
   }
   float* Sk = S + nd.wp[1] * K * P;
   __syncthreads();
-  // ---- hidden layers 2 .. L-1
+  // ---- hidden layers 2 .. L-1.  Activations alternate between A and B (B
+  // holds adjoints only in the reverse pass), so one barrier per layer
+  // suffices.  Layer k uses weight buffer (k - 2) & 1, and the next layer's
+  // image goes into the other buffer, whose last readers (layer k - 1)
+  // finished before the barrier that ended that layer.
+  float* Ain = s.A;
+  float* Aout = s.B;
   for (int k = 2; k <= L - 1; ++k) {
-    const int in_p = nd.wp[k - 1], out_p = nd.wp[k], in_w = nd.w[k - 1], out_w = nd.w[k];
-    const float* Wk = prm + nd.off[k];
-    const float* bk = Wk + out_w * in_w;
+    const int in_p = nd.wp[k - 1], out_p = nd.wp[k], in_w = nd.w[k - 1];
     const Act ak = GEN ? layer_act(nd, prm, k) : Act{};
-    for (int idx = tid; idx < in_p * out_p; idx += blockDim.x) {
-      const int n = idx / in_p, j = idx - n * in_p;
-      s.W[j * out_p + n] = (n < out_w && j < in_w) ? __ldg(Wk + n * in_w + j) : 0.f;
-    }
-    for (int n = tid; n < out_p; n += blockDim.x) s.bias[n] = n < out_w ? __ldg(bk + n) : 0.f;
-    __syncthreads();
+    const int b = (k - 2) & 1;
+    const float* Wt = b ? s.W1 : s.W0;   // [in_p][out_p] = W^k transposed, then b^k
+    if (tid == 0 && k + 1 <= L - 1)
+      bulk_g2s(b ? s.W0 : s.W1, img + nd.imf[k + 1], 4u * layer_img_floats(nd, k + 1), s.bar + (b ^ 1));
+    mbar_wait(s.bar + b, (ph >> b) & 1u, err);
+    ph ^= 1u << b;
     const int ng = tid / n_pg, pg = tid - ng * n_pg;
     const bool act = ng < out_p / MT;
     const int n0 = ng * MT, p0 = pg * PT;
     float acc[MT][K][PT];
     if (act) {
-      gemm_fwd<K, PT>(s.A, s.W, s.bias, in_w, out_p, P, n0, p0, acc);
+      gemm_fwd<K, PT>(Ain, Wt, Wt + in_p * out_p, in_w, out_p, P, n0, p0, acc);
 #pragma unroll
       for (int i = 0; i < MT; ++i) {
         float sv[K][PT];
@@ -557,24 +636,24 @@ __device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const 
 #pragma unroll
         for (int c = 0; c < K; ++c) stp<PT>(Sk + ((n0 + i) * K + c) * P + p0, sv[c]);
       }
-    }
-    __syncthreads();
-    if (act) {
 #pragma unroll
       for (int i = 0; i < MT; ++i)
 #pragma unroll
-        for (int c = 0; c < K; ++c) stp<PT>(s.A + ((n0 + i) * K + c) * P + p0, acc[i][c]);
+        for (int c = 0; c < K; ++c) stp<PT>(Aout + ((n0 + i) * K + c) * P + p0, acc[i][c]);
     }
     __syncthreads();
     Sk += out_p * K * P;
+    float* t = Ain;
+    Ain = Aout;
+    Aout = t;
   }
   // ---- output layer L
   {
     const int in_w = nd.w[L - 1], D = nd.w[L];
     const float* WL = prm + nd.off[L];
     const float* bL = WL + D * in_w;
-    for (int idx = tid; idx < D * P; idx += blockDim.x) {
-      const int o = idx / P, p = idx - o * P;
+    for (Walk wk(P); wk.r < D; wk.next()) {
+      const int o = wk.r, p = wk.c;
       float z[K];
       z[0] = __ldg(bL + o);
 #pragma unroll
@@ -583,7 +662,7 @@ __device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const 
       for (int j = 0; j < in_w; ++j) {
         const float w = __ldg(wrow + j);
 #pragma unroll
-        for (int c = 0; c < K; ++c) z[c] = fmaf(w, s.A[(j * K + c) * P + p], z[c]);
+        for (int c = 0; c < K; ++c) z[c] = fmaf(w, Ain[(j * K + c) * P + p], z[c]);
       }
 #pragma unroll
       for (int c = 0; c < K; ++c) Sk[(o * K + c) * P + p] = z[c];
@@ -605,14 +684,15 @@ __device__ __noinline__ void net_forward(SmemLayout sl, const NetDev& nd, const 
     }
   }
   __syncthreads();
+  return ph;
 }
 
 // H^{k}[n][c][p] = act(saved S^k) into dst, for all n < wp (padded rows give 0)
 template <int K, bool GEN>
 __device__ __forceinline__ void act_from_saved(const Act& a, float* __restrict__ dst, const float* __restrict__ Sk,
                                                int wp, int P) {
-  for (int idx = threadIdx.x; idx < wp * P; idx += blockDim.x) {
-    const int n = idx / P, p = idx - n * P;
+  for (Walk wk(P); wk.r < wp; wk.next()) {
+    const int n = wk.r, p = wk.c;
     float sv[K], h[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) sv[c] = Sk[(n * K + c) * P + p];
@@ -628,8 +708,8 @@ template <int K, bool GEN>
 __device__ __forceinline__ void act_from_saved_T(const Act& a, float* __restrict__ HT, const float* __restrict__ Sk,
                                                  int wp, int P) {
   const int P4 = P >> 2;
-  for (int idx = threadIdx.x; idx < wp * P4; idx += blockDim.x) {
-    const int n = idx % wp, pq = idx / wp;
+  for (Walk wk(wp); wk.r < P4; wk.next()) {
+    const int n = wk.c, pq = wk.r;
     float4 sv4[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) sv4[c] = *reinterpret_cast<const float4*>(Sk + (n * K + c) * P + 4 * pq);
@@ -651,15 +731,19 @@ __device__ __forceinline__ void act_from_saved_T(const Act& a, float* __restrict
 // gradient slice gslice receives dW^k, db^k at the network's offsets.
 // ---------------------------------------------------------------------------
 template <int K, int PT, bool GEN>
-__device__ __noinline__ void net_backward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm, int P,
-                             const float* __restrict__ S, int uoff,
-                             float* __restrict__ gslice, bool first) {
+__device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm,
+                                              const float* __restrict__ img, int P, const float* __restrict__ S,
+                                              int uoff, float* __restrict__ gslice, bool first, uint32_t ph,
+                                              int* err) {
   const Smem s = carve(sl);
   float* __restrict__ Ub = s.Ub + uoff;
   const int tid = threadIdx.x;
   const int n_pg = P / PT;
   const int L = nd.L;
   const int KP = K * P;
+  // reverse image of layer L-1 (into buffer 0) while the output layer runs;
+  // layer k uses buffer (L - 1 - k) & 1
+  if (tid == 0 && L - 1 >= 2) bulk_g2s(s.W0, img + nd.imb[L - 1], 4u * nd.wp[L - 1] * nd.wp[L - 2], s.bar);
   // saved jets of layer L (top), then walk down layer by layer
   const float* SL = S;
   for (int k = 1; k < L; ++k) SL += nd.wp[k] * KP;
@@ -667,8 +751,8 @@ __device__ __noinline__ void net_backward(SmemLayout sl, const NetDev& nd, const
   // ---- output layer
   const int D = nd.w[L], in_w = nd.w[L - 1], in_p = nd.wp[L - 1];
   if (nd.out_act == XPINN_ACT_SOFTPLUS) {
-    for (int idx = tid; idx < D * P; idx += blockDim.x) {
-      const int o = idx / P, p = idx - o * P;
+    for (Walk wk(P); wk.r < D; wk.next()) {
+      const int o = wk.r, p = wk.c;
       float z[K], yb[K], zb[K];
 #pragma unroll
       for (int c = 0; c < K; ++c) {
@@ -738,6 +822,11 @@ __device__ __noinline__ void net_backward(SmemLayout sl, const NetDev& nd, const
     const int ng = tid / n_pg, pg = tid - ng * n_pg;
     const int n0 = ng * MT, p0 = pg * PT;
     const Act ak = GEN ? layer_act(nd, prm, k) : Act{};
+    const int b = (L - 1 - k) & 1;
+    // the next layer's reverse image into the other buffer, last read by the
+    // contraction of layer k + 1 (before the barrier that ended it)
+    if (tid == 0 && k - 1 >= 2)
+      bulk_g2s(b ? s.W0 : s.W1, img + nd.imb[k - 1], 4u * nd.wp[k - 1] * nd.wp[k - 2], s.bar + (b ^ 1));
     float gs = 0.f;   // dJ/ds_k, this thread's part
     if (ng < out_p / MT) {
 #pragma unroll
@@ -770,14 +859,12 @@ __device__ __noinline__ void net_backward(SmemLayout sl, const NetDev& nd, const
       const int in_pk = nd.wp[k - 1], in_wk = nd.w[k - 1];
       const float* Skm1 = Sk - in_pk * KP;
       act_from_saved_T<K, GEN>(GEN ? layer_act(nd, prm, k - 1) : Act{}, s.A, Skm1, in_pk, P);
-      const float* Wk = prm + nd.off[k];
-      for (int idx = tid; idx < out_p * in_pk; idx += blockDim.x) {
-        const int n = idx / in_pk, j = idx - n * in_pk;
-        s.W[idx] = (n < out_w && j < in_wk) ? __ldg(Wk + n * in_wk + j) : 0.f;
-      }
+      const float* Wn = b ? s.W1 : s.W0;   // [out_p][in_pk] = W^k
+      mbar_wait(s.bar + b, (ph >> b) & 1u, err);
+      ph ^= 1u << b;
       __syncthreads();
       // h-bar^{k-1} = (W^k)^T zb^k into registers, then dW^k and db^k
-      if (ng < in_pk / MT) gemm_bwd<K, PT>(s.B, s.W, out_w, in_pk, P, n0, p0, acc);
+      if (ng < in_pk / MT) gemm_bwd<K, PT>(s.B, Wn, out_w, in_pk, P, n0, p0, acc);
       float* gb = gW + out_w * in_wk;
       group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
                  [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
@@ -803,6 +890,7 @@ __device__ __noinline__ void net_backward(SmemLayout sl, const NetDev& nd, const
     }
     __syncthreads();
   }
+  return ph;
 }
 
 // ---------------------------------------------------------------------------
@@ -969,21 +1057,20 @@ __device__ __forceinline__ void flux_seed(int pde, const PtJets& J, float n0, fl
 // the fixed-slope tanh passes; the general kernel picks, per network, the
 // tanh passes or the general ones.
 template <int PT, bool GEN>
-__device__ void forward_any(int K, SmemLayout sl, const NetDev& nd, const float* prm, int P, float* S,
-                            int uoff) {
-#define XP_FWD(KK, G) net_forward<KK, PT, G>(sl, nd, prm, P, S, uoff)
-#define XP_SWITCH(G)              \
-  switch (K) {                    \
-    case 1: XP_FWD(1, G); break;  \
-    case 2: XP_FWD(2, G); break;  \
-    case 3: XP_FWD(3, G); break;  \
-    case 4: XP_FWD(4, G); break;  \
-    default: XP_FWD(5, G); break; \
+__device__ uint32_t forward_any(int K, SmemLayout sl, const NetDev& nd, const float* prm, const float* img, int P,
+                                float* S, int uoff, uint32_t ph, int* err) {
+#define XP_FWD(KK, G) return net_forward<KK, PT, G>(sl, nd, prm, img, P, S, uoff, ph, err)
+#define XP_SWITCH(G)        \
+  switch (K) {              \
+    case 1: XP_FWD(1, G);   \
+    case 2: XP_FWD(2, G);   \
+    case 3: XP_FWD(3, G);   \
+    case 4: XP_FWD(4, G);   \
+    default: XP_FWD(5, G);  \
   }
   if constexpr (GEN) {
     if (net_is_general(nd)) {
       XP_SWITCH(true)
-      return;
     }
   }
   XP_SWITCH(false)
@@ -992,21 +1079,20 @@ __device__ void forward_any(int K, SmemLayout sl, const NetDev& nd, const float*
 }
 
 template <int PT, bool GEN>
-__device__ void backward_any(int K, SmemLayout sl, const NetDev& nd, const float* prm, int P,
-                             const float* S, int uoff, float* g, bool first) {
-#define XP_BWD(KK, G) net_backward<KK, PT, G>(sl, nd, prm, P, S, uoff, g, first)
-#define XP_SWITCH(G)              \
-  switch (K) {                    \
-    case 1: XP_BWD(1, G); break;  \
-    case 2: XP_BWD(2, G); break;  \
-    case 3: XP_BWD(3, G); break;  \
-    case 4: XP_BWD(4, G); break;  \
-    default: XP_BWD(5, G); break; \
+__device__ uint32_t backward_any(int K, SmemLayout sl, const NetDev& nd, const float* prm, const float* img,
+                                 int P, const float* S, int uoff, float* g, bool first, uint32_t ph, int* err) {
+#define XP_BWD(KK, G) return net_backward<KK, PT, G>(sl, nd, prm, img, P, S, uoff, g, first, ph, err)
+#define XP_SWITCH(G)        \
+  switch (K) {              \
+    case 1: XP_BWD(1, G);   \
+    case 2: XP_BWD(2, G);   \
+    case 3: XP_BWD(3, G);   \
+    case 4: XP_BWD(4, G);   \
+    default: XP_BWD(5, G);  \
   }
   if constexpr (GEN) {
     if (net_is_general(nd)) {
       XP_SWITCH(true)
-      return;
     }
   }
   XP_SWITCH(false)
@@ -1171,12 +1257,13 @@ __device__ __forceinline__ void point_stage(const StepArgs& a, const SubDev& sd,
 }
 
 template <int PT, bool GEN>
-__device__ void process_item(const StepArgs& a, SmemLayout sl, const Item& it, int item_idx,
-                             float* __restrict__ scratch) {
+__device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& it, int item_idx,
+                                 float* __restrict__ scratch, uint32_t ph) {
   const Smem s = carve(sl);
   const SubDev& sd = a.subs[it.q];
   const int P = it.P;
   const float* prm = a.params + sd.poff;
+  const float* img = a.wimg + sd.img_off;
   const int tid = threadIdx.x;
   const bool has_bwd = it.kind <= IT_IFACE;
   // offsets of net 1 in U and in the scratch (net 0 starts at 0)
@@ -1202,8 +1289,8 @@ __device__ void process_item(const StepArgs& a, SmemLayout sl, const Item& it, i
       s.sy[p] = z.y;
     }
     __syncthreads();
-    if (it.K[0]) forward_any<PT, GEN>(it.K[0], sl, sd.net[0], prm, P, scratch, 0);
-    if (it.K[1]) forward_any<PT, GEN>(it.K[1], sl, sd.net[1], prm, P, scratch + s1, u1);
+    if (it.K[0]) ph = forward_any<PT, GEN>(it.K[0], sl, sd.net[0], prm, img, P, scratch, 0, ph, a.err);
+    if (it.K[1]) ph = forward_any<PT, GEN>(it.K[1], sl, sd.net[1], prm, img, P, scratch + s1, u1, ph, a.err);
     // ---- per point: loss terms and seeds (or exchange / evaluation output)
     for (int p = tid; p < P; p += blockDim.x) {
       const bool valid = p < nv;
@@ -1245,8 +1332,10 @@ __device__ void process_item(const StepArgs& a, SmemLayout sl, const Item& it, i
     __syncthreads();
     if (has_bwd) {
       float* gs = a.partials + it.part_off;
-      if (it.K[0]) backward_any<PT, GEN>(it.K[0], sl, sd.net[0], prm, P, scratch, 0, gs, first);
-      if (it.K[1]) backward_any<PT, GEN>(it.K[1], sl, sd.net[1], prm, P, scratch + s1, u1, gs, first);
+      if (it.K[0])
+        ph = backward_any<PT, GEN>(it.K[0], sl, sd.net[0], prm, img, P, scratch, 0, gs, first, ph, a.err);
+      if (it.K[1])
+        ph = backward_any<PT, GEN>(it.K[1], sl, sd.net[1], prm, img, P, scratch + s1, u1, gs, first, ph, a.err);
       // a net that is not evaluated by this item contributes zero gradient
       if (first)
         for (int n = 0; n < sd.n_nets; ++n)
@@ -1265,6 +1354,7 @@ __device__ void process_item(const StepArgs& a, SmemLayout sl, const Item& it, i
       a.loss_part[2 * item_idx + 1] = t1s;
     }
   }
+  return ph;
 }
 
 // PT = 1 keeps registers <= 128 so that two CTAs fit on an SM; PT = 2 uses
@@ -1306,6 +1396,14 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : (PT == 1 ? 2 : 1) * (256
   const SmemLayout sl{a.szA, a.szW, a.szU, a.pmax};
   __shared__ int s_item;
   float* scratch = a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
+  uint32_t ph = 0;   // phase parities of the two weight-buffer mbarriers
+  if (threadIdx.x == 0) {
+    const Smem s = carve(sl);
+    mbar_init(s.bar, 1);
+    mbar_init(s.bar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
     __syncthreads();
@@ -1314,7 +1412,7 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : (PT == 1 ? 2 : 1) * (256
     if (it >= a.n_items) break;
     if (a.n_fwd_wait > 0 && it >= a.wait_from && !wait_exchange(a)) continue;
     const Item& item = a.items[it];
-    process_item<PT, GEN>(a, sl, item, a.item_base + it, scratch);
+    ph = process_item<PT, GEN>(a, sl, item, a.item_base + it, scratch, ph);
     if (item.kind == IT_IFACE_FWD && a.n_fwd_wait > 0) {
       __syncthreads();                      // every thread's exchange stores issued
       if (threadIdx.x == 0) {

@@ -6,9 +6,9 @@
 // budget, or a region of a program that must not allocate because it is being
 // timed or replayed).  xpinn_residual_grad_noalloc serves them: the caller
 // passes inputs and outputs in device memory it already owns, and all working
-// memory the jet kernel needs (work descriptors, the work counter, saved jets
-// and per-item gradient slices) comes from one fixed array in this file,
-// g_noalloc_scratch, of XPINN_NOALLOC_SCRATCH_BYTES.  That array exists on
+// memory the jet kernel needs (work descriptors, the work counter, weight
+// images, saved jets and per-item gradient slices) comes from one fixed array
+// in this file, g_noalloc_scratch, of XPINN_NOALLOC_SCRATCH_BYTES.  That array exists on
 // every GPU that loads the library, for as long as the library stays loaded.
 //
 // Set-up: the first call on each device looks up the array's device address
@@ -49,16 +49,18 @@ struct NaDesc {
   SubDev sd;
   Item items[NA_MAX_ITEMS];
   int n_items;
+  PackBlock pack[2 * MAXL];   // weight images of the hidden-to-hidden layers
+  int n_pack;
 };
 
 // Layout of the scratch array (byte offsets, each 256-byte aligned).
 struct NaLayout {
-  size_t sub, items, counter, err, loss_part, partials, scratch, total;
+  size_t sub, items, counter, err, loss_part, pack, img, partials, scratch, total;
 };
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
-NaLayout layout(int n_items, int n_params, int grid, int64_t scratch_per_cta) {
+NaLayout layout(int n_items, int n_params, int grid, int64_t scratch_per_cta, int64_t img_floats) {
   NaLayout l{};
   size_t o = 0;
   l.sub = o; o = up256(o + sizeof(SubDev));
@@ -66,6 +68,8 @@ NaLayout layout(int n_items, int n_params, int grid, int64_t scratch_per_cta) {
   l.counter = o; o = up256(o + sizeof(int));
   l.err = o; o = up256(o + sizeof(int));
   l.loss_part = o; o = up256(o + sizeof(double) * 2 * NA_MAX_ITEMS);
+  l.pack = o; o = up256(o + sizeof(PackBlock) * 2 * MAXL);
+  l.img = o; o = up256(o + sizeof(float) * (size_t)img_floats);
   l.partials = o; o = up256(o + sizeof(float) * (size_t)n_items * n_params);
   l.scratch = o; o = up256(o + sizeof(float) * (size_t)grid * scratch_per_cta);
   l.total = o;
@@ -74,7 +78,7 @@ NaLayout layout(int n_items, int n_params, int grid, int64_t scratch_per_cta) {
 
 // Copies the descriptors (passed by value) into the array and clears the
 // work counter and the error flag: the only state that must start at zero.
-__global__ void na_setup_kernel(NaDesc d, SubDev* sub, Item* items, int* counter, int* err) {
+__global__ void na_setup_kernel(NaDesc d, SubDev* sub, Item* items, int* counter, int* err, PackBlock* pack) {
   const int t = threadIdx.x;
   if (t == 0) {
     *sub = d.sd;
@@ -82,6 +86,7 @@ __global__ void na_setup_kernel(NaDesc d, SubDev* sub, Item* items, int* counter
     *err = 0;
   }
   for (int i = t; i < d.n_items; i += blockDim.x) items[i] = d.items[i];
+  for (int i = t; i < d.n_pack; i += blockDim.x) pack[i] = d.pack[i];
 }
 
 // grads[e] = sum over items (in order) of the item's slice; loss = sum of the
@@ -167,6 +172,13 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   sd.n_nets = 1;
   NetDev& nd = sd.net[0];
   const int off = fill_net_dev(nd, *net, 0);
+  sd.img_off = 0;
+  const int img_floats = assign_images(nd, 0);
+  d.n_pack = 0;
+  for (int k = 2; k < L; ++k) {
+    d.pack[d.n_pack++] = {nd.off[k], nd.imf[k], nd.w[k - 1], nd.w[k], nd.wp[k - 1], nd.wp[k], 1};
+    d.pack[d.n_pack++] = {nd.off[k], nd.imb[k], nd.w[k - 1], nd.w[k], nd.wp[k - 1], nd.wp[k], 0};
+  }
   int wmax = MT;
   for (int k = 1; k < L; ++k) wmax = std::max(wmax, nd.wp[k]);
   sd.n_params = off;
@@ -191,11 +203,11 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   const int64_t tiles = (n + P - 1) / P;
   int n_items = (int)std::min<int64_t>(std::min<int64_t>(NA_MAX_ITEMS, tiles), (int64_t)n_sm);
   int grid = n_items;
-  NaLayout lay = layout(n_items, sd.n_params, grid, per_cta);
+  NaLayout lay = layout(n_items, sd.n_params, grid, per_cta, img_floats);
   while (n_items > 1 && lay.total > (size_t)XPINN_NOALLOC_SCRATCH_BYTES) {
     n_items = std::max(1, n_items * 3 / 4);
     grid = n_items;
-    lay = layout(n_items, sd.n_params, grid, per_cta);
+    lay = layout(n_items, sd.n_params, grid, per_cta, img_floats);
   }
   if (lay.total > (size_t)XPINN_NOALLOC_SCRATCH_BYTES) {
     char buf[200];
@@ -227,6 +239,7 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   a.counter = reinterpret_cast<int*>(base + lay.counter);
   a.subs = reinterpret_cast<const SubDev*>(base + lay.sub);
   a.params = params;
+  a.wimg = reinterpret_cast<const float*>(base + lay.img);
   a.pts = reinterpret_cast<const float2*>(xy);
   a.res_f = f;
   a.partials = reinterpret_cast<float*>(base + lay.partials);
@@ -240,7 +253,7 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   a.n_eq = pde == XPINN_PDE_NS ? 3 : 1;
   a.szA = (int)std::max(wmax * K * P, NT * 32);
   a.szW = 4;
-  for (int k = 2; k < L; ++k) a.szW = std::max(a.szW, nd.wp[k] * nd.wp[k - 1]);
+  for (int k = 2; k < L; ++k) a.szW = std::max(a.szW, layer_img_floats(nd, k));
   a.szU = (D * K * P + 3) / 4 * 4;
   a.pmax = P;
   a.pt = 2;
@@ -264,7 +277,10 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   na_setup_kernel<<<1, 128, 0, s>>>(d, reinterpret_cast<SubDev*>(base + lay.sub),
                                     reinterpret_cast<Item*>(base + lay.items),
                                     reinterpret_cast<int*>(base + lay.counter),
-                                    reinterpret_cast<int*>(base + lay.err));
+                                    reinterpret_cast<int*>(base + lay.err),
+                                    reinterpret_cast<PackBlock*>(base + lay.pack));
+  launch_pack_weights(params, reinterpret_cast<const PackBlock*>(base + lay.pack), d.n_pack,
+                      reinterpret_cast<float*>(base + lay.img), s);
   if (d.n_items) launch_jet_step(a, grid, smem, s);
   na_reduce_kernel<<<(sd.n_params + 255) / 256, 256, 0, s>>>(a.partials, a.loss_part, d.n_items,
                                                               sd.n_params, grads, loss);

@@ -82,4 +82,39 @@ void launch_reduce_adam(const ReduceArgs& a, cudaStream_t s) {
   if (a.n_blocks > 0) reduce_adam_kernel<<<a.n_blocks, RT, 0, s>>>(a);
 }
 
+// Weight images (layout in xpinn_dev.cuh): one CTA per image; consecutive
+// threads write consecutive image floats.
+__global__ void __launch_bounds__(RT) pack_weights_kernel(const float* __restrict__ params,
+                                                          const PackBlock* __restrict__ blocks,
+                                                          float* __restrict__ wimg) {
+  const PackBlock b = blocks[blockIdx.x];
+  const float* W = params + b.src;
+  float* dst = wimg + b.dst;
+  if (b.fwd) {
+    // [in_p][out_p] = W^T, then [out_p] = b
+    const int n_el = (b.in_p + 1) * b.out_p;
+    for (int e = threadIdx.x; e < n_el; e += RT) {
+      const int j = e / b.out_p, n = e - j * b.out_p;
+      float v = 0.f;
+      if (n < b.out_w) {
+        if (j < b.in_w) v = W[(int64_t)n * b.in_w + j];
+        else if (j == b.in_p) v = W[(int64_t)b.out_w * b.in_w + n];
+      }
+      dst[e] = v;
+    }
+  } else {
+    // [out_p][in_p] = W
+    const int n_el = b.out_p * b.in_p;
+    for (int e = threadIdx.x; e < n_el; e += RT) {
+      const int n = e / b.in_p, j = e - n * b.in_p;
+      dst[e] = (n < b.out_w && j < b.in_w) ? W[(int64_t)n * b.in_w + j] : 0.f;
+    }
+  }
+}
+
+void launch_pack_weights(const float* params, const PackBlock* blocks, int n_blocks, float* wimg,
+                         cudaStream_t s) {
+  if (n_blocks > 0) pack_weights_kernel<<<n_blocks, RT, 0, s>>>(params, blocks, wimg);
+}
+
 }  // namespace xp

@@ -51,7 +51,32 @@ struct NetDev {
   int aoff;              // offset of the slopes a^1..a^{L-1}, or -1 (slopes fixed, n a^k = 1)
   float scale;           // n of n a^k
   int end;               // one past the network's last parameter
+  // Weight images of the hidden-to-hidden layers k = 2..L-1 (offsets in
+  // floats from the subdomain's image block), copied whole into shared
+  // memory by the jet kernel:
+  //   imf[k]: forward image, W^k transposed and zero-padded [wp[k-1]][wp[k]],
+  //           then b^k zero-padded [wp[k]];
+  //   imb[k]: reverse image, W^k zero-padded [wp[k]][wp[k-1]].
+  int imf[MAXL + 1];
+  int imb[MAXL + 1];
 };
+
+// Floats of the forward image of layer k (the larger of the two).
+__host__ __device__ inline int layer_img_floats(const NetDev& nd, int k) {
+  return (nd.wp[k - 1] + 1) * nd.wp[k];
+}
+
+// Assigns the image offsets of a network starting at `ioff`; returns the end.
+inline int assign_images(NetDev& nd, int ioff) {
+  for (int k = 0; k <= MAXL; ++k) nd.imf[k] = nd.imb[k] = -1;
+  for (int k = 2; k < nd.L; ++k) {
+    nd.imf[k] = ioff;
+    ioff += layer_img_floats(nd, k);
+    nd.imb[k] = ioff;
+    ioff += nd.wp[k] * nd.wp[k - 1];
+  }
+  return ioff;
+}
 
 // A network that is not tanh with fixed slopes needs the general passes.
 __host__ __device__ inline bool net_is_general(const NetDev& nd) {
@@ -84,6 +109,7 @@ struct SubDev {
   int n_nets;
   int n_params;
   int64_t poff;          // offset of the subdomain's parameters in the packed vector
+  int64_t img_off;       // offset of the subdomain's weight images in wimg
   NetDev net[MAXNETS];
   float w_data[MAXNETS], w_res, w_avg, w_iface;
   float inv_n_res;
@@ -131,6 +157,7 @@ struct StepArgs {
   const SubDev* subs;
   const IfaceDev* ifaces;
   const float* params;
+  const float* wimg;     // weight images (see NetDev), rebuilt from params before each use
   const float2* pts;
   const float* res_f;
   const float* tgt;
@@ -189,6 +216,16 @@ struct ReduceArgs {
 };
 
 void launch_reduce_adam(const ReduceArgs& a, cudaStream_t s);
+
+// One weight image to build from the packed parameters.
+struct PackBlock {
+  int64_t src;           // W^k in params (b^k follows)
+  int64_t dst;           // image in wimg
+  int in_w, out_w, in_p, out_p;
+  int fwd;               // 1: forward image (transposed, with bias); 0: reverse image
+};
+void launch_pack_weights(const float* params, const PackBlock* blocks, int n_blocks, float* wimg,
+                         cudaStream_t s);
 void launch_step_begin(int* counters, int n_counters, int* step_t, int* loss_slot, int do_adam,
                        cudaStream_t s);
 
