@@ -283,31 +283,31 @@ __device__ __forceinline__ void act_jet_bwd(const Act& a, const float (&sv)[K], 
                                             float (&zb)[K], float& gs) {
   if constexpr (!GEN) {
     tanh_jet_bwd<K>(sv, hb, zb);
-    return;
-  }
-  float v[K], vb[K];
+  } else {
+    float v[K], vb[K];
 #pragma unroll
-  for (int c = 0; c < K; ++c) v[c] = a.s * sv[c];
-  float d0, d1, d2, d3;
-  phi_derivs(a.kind, v[0], d0, d1, d2, d3);
-  float b0 = d1 * hb[0];
-  if (K > 1) { vb[1] = d1 * hb[1]; b0 += d2 * v[1] * hb[1]; }
-  if (K > 2) { vb[2] = d1 * hb[2]; b0 += d2 * v[2] * hb[2]; }
-  if (K > 3) {
-    vb[3] = d1 * hb[3];
-    vb[1] += 2.f * d2 * v[1] * hb[3];
-    b0 += (d2 * v[3] + d3 * v[1] * v[1]) * hb[3];
-  }
-  if (K > 4) {
-    vb[4] = d1 * hb[4];
-    vb[2] += 2.f * d2 * v[2] * hb[4];
-    b0 += (d2 * v[4] + d3 * v[2] * v[2]) * hb[4];
-  }
-  vb[0] = b0;
+    for (int c = 0; c < K; ++c) v[c] = a.s * sv[c];
+    float d0, d1, d2, d3;
+    phi_derivs(a.kind, v[0], d0, d1, d2, d3);
+    float b0 = d1 * hb[0];
+    if (K > 1) { vb[1] = d1 * hb[1]; b0 += d2 * v[1] * hb[1]; }
+    if (K > 2) { vb[2] = d1 * hb[2]; b0 += d2 * v[2] * hb[2]; }
+    if (K > 3) {
+      vb[3] = d1 * hb[3];
+      vb[1] += 2.f * d2 * v[1] * hb[3];
+      b0 += (d2 * v[3] + d3 * v[1] * v[1]) * hb[3];
+    }
+    if (K > 4) {
+      vb[4] = d1 * hb[4];
+      vb[2] += 2.f * d2 * v[2] * hb[4];
+      b0 += (d2 * v[4] + d3 * v[2] * v[2]) * hb[4];
+    }
+    vb[0] = b0;
 #pragma unroll
-  for (int c = 0; c < K; ++c) {
-    gs = fmaf(vb[c], sv[c], gs);
-    zb[c] = a.s * vb[c];
+    for (int c = 0; c < K; ++c) {
+      gs = fmaf(vb[c], sv[c], gs);
+      zb[c] = a.s * vb[c];
+    }
   }
 }
 
@@ -372,9 +372,9 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const floa
   }
 }
 
-// Hb[j][c][p] = sum_n Wn[n][j] Zb[n][c][p], tile j0..j0+7 x p0..p0+PT-1
+// Hb[j][c][p] = sum_n Wn[n][j] Zb[n][c][p] (Zb row stride RSZ), tile j0..j0+7 x p0..p0+PT-1
 template <int K, int PT>
-__device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, const float* __restrict__ Wn,
+__device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, int RSZ, const float* __restrict__ Wn,
                                          int out_w, int in_p, int P, int j0, int p0,
                                          float (&acc)[MT][K][PT]) {
 #pragma unroll
@@ -392,7 +392,7 @@ __device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, const flo
     const float w[MT] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
     float zb[K][PT];
 #pragma unroll
-    for (int c = 0; c < K; ++c) ldp<PT>(zp + (n * K + c) * P, zb[c]);
+    for (int c = 0; c < K; ++c) ldp<PT>(zp + n * RSZ + c * P, zb[c]);
 #pragma unroll
     for (int i = 0; i < MT; ++i)
 #pragma unroll
@@ -414,25 +414,29 @@ __device__ __forceinline__ void accum(float* p, float v, bool first) {
 }
 
 // dW[n][j] += sum_{c,p} Zb[n][c][p] H[j][c][p] for n < out_w, j < in_w, with
-// H given transposed, HT[(c*P + p)][j] (row stride RS).  Each thread owns a
-// TA x 4 tile of dW (TA = 8: eight Zb rows share each HT load, which halves
-// the shared-memory wavefronts per FFMA against a 4 x 4 tile); narrow layers
-// split the (c, p) range over S threads per tile and reduce the S partial
-// tiles in a fixed order through shared memory (R, at least blockDim.x * TA * 4
-// floats; it may alias HT, which is dead once the contraction is done).
-// Float4 loads: Zb rows are read as 4 consecutive (c, p), broadcast to the
-// lanes of a tile row; HT rows as 4 consecutive j, contiguous across lanes.
-template <int TA>
-__device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, const float* __restrict__ HT,
+// Zb rows at stride RSZ and H given transposed, HT[(c*P + p)][j] (row stride
+// RS).  Each thread owns an 8 x TB tile of dW over the whole contraction
+// (TB = 4 measured fastest; 8, and unrolling the contraction loop, were
+// slower).  Its rows n = tn + i * (out_p / 8), i = 0..7, are interleaved so
+// that the threads of a warp, which hold consecutive tiles, read adjacent Zb
+// rows (different banks when RSZ mod 32 is not 0 or 16) and consecutive HT
+// columns.  Per 4 contraction steps a thread loads 8 Zb and TB HT float4s for
+// 32 TB FMAs.  Narrow layers split the contraction over S threads per tile
+// and reduce the S partial tiles in a fixed order through shared memory (R,
+// at least blockDim.x * 8 * TB floats; it may alias HT, which is dead once
+// the contraction is done).
+template <int TB>
+__device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, int RSZ, const float* __restrict__ HT,
                                          int RS, int out_p, int in_p, int out_w, int in_w, int KP,
                                          float* __restrict__ R, float* __restrict__ pW, bool first) {
-  constexpr int TE = TA * 4;   // tile elements
+  constexpr int TE = 8 * TB;   // tile elements
+  constexpr int NB = TB / 4;   // float4 columns per HT row
   const int tid = threadIdx.x;
-  const int tj_n = in_p >> 2, tn_n = out_p / TA;
+  const int tj_n = in_p / TB, tn_n = out_p >> 3;
   const int T = tj_n * tn_n;
   int S = (int)blockDim.x / T;
   S = S < 1 ? 1 : (S > 16 ? 16 : S);
-  const int KP4 = KP >> 2;
+  const int KP4 = KP >> 2, RSZ4 = RSZ >> 2;
   const bool split = S > 1;
   for (int base = 0; base < T * S; base += blockDim.x) {
     const int u = base + tid;
@@ -440,54 +444,63 @@ __device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, const flo
     const int tile = valid ? u % T : 0;
     const int sp = valid ? u / T : 0;
     const int tn = tile / tj_n, tj = tile - tn * tj_n;
-    const int n0 = tn * TA, j0 = tj * 4;
-    float acc[TA][4];
+    const int j0 = tj * TB;
+    float acc[8][TB];
 #pragma unroll
-    for (int i = 0; i < TA; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.f;
+      for (int jj = 0; jj < TB; ++jj) acc[i][jj] = 0.f;
     if (valid) {
-      const float4* z4 = reinterpret_cast<const float4*>(Zb + n0 * KP);
+      const float4* z4 = reinterpret_cast<const float4*>(Zb) + tn * RSZ4;
+      const int zstep = tn_n * RSZ4;
       for (int g = sp; g < KP4; g += S) {
-        float4 h[4];
+        float4 h[4][NB];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) h[t] = *reinterpret_cast<const float4*>(HT + (4 * g + t) * RS + j0);
+        for (int t = 0; t < 4; ++t) {
+          const float4* hp = reinterpret_cast<const float4*>(HT + (4 * g + t) * RS + j0);
 #pragma unroll
-        for (int i = 0; i < TA; ++i) {
-          const float4 z = z4[i * KP4 + g];
+          for (int q = 0; q < NB; ++q) h[t][q] = hp[q];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float4 z = z4[i * zstep + g];
           const float zv[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            acc[i][0] = fmaf(zv[t], h[t].x, acc[i][0]);
-            acc[i][1] = fmaf(zv[t], h[t].y, acc[i][1]);
-            acc[i][2] = fmaf(zv[t], h[t].z, acc[i][2]);
-            acc[i][3] = fmaf(zv[t], h[t].w, acc[i][3]);
-          }
+          for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+              acc[i][4 * q + 0] = fmaf(zv[t], h[t][q].x, acc[i][4 * q + 0]);
+              acc[i][4 * q + 1] = fmaf(zv[t], h[t][q].y, acc[i][4 * q + 1]);
+              acc[i][4 * q + 2] = fmaf(zv[t], h[t][q].z, acc[i][4 * q + 2]);
+              acc[i][4 * q + 3] = fmaf(zv[t], h[t][q].w, acc[i][4 * q + 3]);
+            }
         }
       }
     }
     if (!split) {
       if (valid) {
 #pragma unroll
-        for (int i = 0; i < TA; ++i)
+        for (int i = 0; i < 8; ++i) {
+          const int n = tn + i * tn_n;
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj)
-            if (n0 + i < out_w && j0 + jj < in_w) accum(pW + (n0 + i) * in_w + j0 + jj, acc[i][jj], first);
+          for (int jj = 0; jj < TB; ++jj)
+            if (n < out_w && j0 + jj < in_w) accum(pW + n * in_w + j0 + jj, acc[i][jj], first);
+        }
       }
     } else {
       __syncthreads();                       // HT / Zb reads of all threads done
       if (valid) {
 #pragma unroll
-        for (int i = 0; i < TA; ++i)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) R[(sp * T + tile) * TE + i * 4 + jj] = acc[i][jj];
+          for (int jj = 0; jj < TB; ++jj) R[(sp * T + tile) * TE + i * TB + jj] = acc[i][jj];
       }
       __syncthreads();
       for (int e = tid; e < T * TE; e += blockDim.x) {
-        const int tl = e / TE, q = e - tl * TE, i = q >> 2, jj = q & 3;
+        const int tl = e / TE, q = e - tl * TE, i = q / TB, jj = q - i * TB;
         float v = 0.f;
         for (int k = 0; k < S; ++k) v += R[(k * T + tl) * TE + q];
-        const int n = (tl / tj_n) * TA + i, j = (tl % tj_n) * 4 + jj;
+        const int n = (tl / tj_n) + i * tn_n, j = (tl % tj_n) * TB + jj;
         if (n < out_w && j < in_w) accum(pW + n * in_w + j, v, first);
       }
     }
@@ -495,7 +508,8 @@ __device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, const flo
 }
 
 // Row dot products with 8 lanes per row pair: out[r] (+)= sum_k X[r][k] Y[r'][k].
-// `rows` pairs; X row r at X + xr(r) * len, Y row at Y + yr(r) * len (Y NULL: plain sum).
+// `rows` pairs of 4 * len4 floats; X row r starts at X + xr(r), Y's at
+// Y + yr(r) (float offsets, multiples of 4; Y NULL: plain sum).
 template <typename XR, typename YR, typename OUT>
 __device__ __forceinline__ void group_dots(int rows, int len4, const float* __restrict__ X,
                                            const float* __restrict__ Y, XR xr, YR yr, OUT out) {
@@ -506,9 +520,9 @@ __device__ __forceinline__ void group_dots(int rows, int len4, const float* __re
     const bool valid = r < rows;
     float acc = 0.f;
     if (valid) {
-      const float4* x4 = reinterpret_cast<const float4*>(X) + xr(r) * len4;
+      const float4* x4 = reinterpret_cast<const float4*>(X + xr(r));
       if (Y) {
-        const float4* y4 = reinterpret_cast<const float4*>(Y) + yr(r) * len4;
+        const float4* y4 = reinterpret_cast<const float4*>(Y + yr(r));
         for (int g = lane8; g < len4; g += 8) {
           const float4 x = x4[g], y = y4[g];
           acc = fmaf(x.x, y.x, acc);
@@ -779,10 +793,10 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
     float* gW = gslice + nd.off[L];
     float* gb = gW + D * in_w;
     // dW^L[o][j] = sum_{c,p} zb^L[o][c][p] H^{L-1}[j][c][p]
-    group_dots(D * in_w, KP / 4, Ub, s.A, [=](int r) { return r / in_w; },
-               [=](int r) { return r % in_w; }, [=](int r, float v) { accum(gW + r, v, first); });
+    group_dots(D * in_w, KP / 4, Ub, s.A, [=](int r) { return (r / in_w) * KP; },
+               [=](int r) { return (r % in_w) * KP; }, [=](int r, float v) { accum(gW + r, v, first); });
     // db^L[o] = sum_p zb^L[o][0][p]
-    group_dots(D, P / 4, Ub, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
+    group_dots(D, P / 4, Ub, static_cast<const float*>(nullptr), [=](int r) { return r * KP; },
                [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
   }
   // h-bar^{L-1} = (W^L)^T zb^L into registers
@@ -816,7 +830,10 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
   }
   __syncthreads();
 
-  // ---- hidden layers L-1 .. 1 (Sk points at the saved jets of layer k)
+  // ---- hidden layers L-1 .. 1 (Sk points at the saved jets of layer k).
+  // Adjoint rows in B are RSZ floats apart (padded so that adjacent rows
+  // fall in different banks for the weight-gradient tiles).
+  const int RSZ = adj_stride(K, P);
   for (int k = L - 1; k >= 1; --k) {
     const int out_p = nd.wp[k], out_w = nd.w[k];
     const int ng = tid / n_pg, pg = tid - ng * n_pg;
@@ -847,7 +864,7 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
           for (int c = 0; c < K; ++c) acc[i][c][pp] = zb[c];
         }
 #pragma unroll
-        for (int c = 0; c < K; ++c) stp<PT>(s.B + ((n0 + i) * K + c) * P + p0, acc[i][c]);
+        for (int c = 0; c < K; ++c) stp<PT>(s.B + (n0 + i) * RSZ + c * P + p0, acc[i][c]);
       }
     }
     if (GEN && nd.aoff >= 0) {   // dJ/da^k = n dJ/ds_k
@@ -864,28 +881,29 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
       ph ^= 1u << b;
       __syncthreads();
       // h-bar^{k-1} = (W^k)^T zb^k into registers, then dW^k and db^k
-      if (ng < in_pk / MT) gemm_bwd<K, PT>(s.B, Wn, out_w, in_pk, P, n0, p0, acc);
+      if (ng < in_pk / MT) gemm_bwd<K, PT>(s.B, RSZ, Wn, out_w, in_pk, P, n0, p0, acc);
+      dW_tiles<4>(s.B, RSZ, s.A, in_pk, out_p, in_pk, out_w, in_wk, KP, s.A, gW, first);
       float* gb = gW + out_w * in_wk;
-      group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
+      group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * RSZ; },
                  [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
-      dW_tiles<8>(s.B, s.A, in_pk, out_p, in_pk, out_w, in_wk, KP, s.A, gW, first);
       Sk = Skm1;
     } else {
       __syncthreads();
       // layer 1: dW^1[n][i] = sum_p zb0[n][p] z_i[p] + sum_p zb_{1+i}[n][p]
       float* gb = gW + 2 * out_w;
-      group_dots(out_w, P / 4, s.B, s.sx, [=](int r) { return r * K; }, [=](int r) { return 0; },
+      group_dots(out_w, P / 4, s.B, s.sx, [=](int r) { return r * RSZ; }, [=](int r) { return 0; },
                  [=](int r, float v) { accum(gW + 2 * r, v, first); });
-      group_dots(out_w, P / 4, s.B, s.sy, [=](int r) { return r * K; }, [=](int r) { return 0; },
+      group_dots(out_w, P / 4, s.B, s.sy, [=](int r) { return r * RSZ; }, [=](int r) { return 0; },
                  [=](int r, float v) { accum(gW + 2 * r + 1, v, first); });
       __syncthreads();
       if (K > 1)
-        group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K + 1; },
+        group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * RSZ + P; },
                    [=](int r) { return 0; }, [=](int r, float v) { atomicAdd(gW + 2 * r, v); });
       if (K > 2)
-        group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K + 2; },
-                   [=](int r) { return 0; }, [=](int r, float v) { atomicAdd(gW + 2 * r + 1, v); });
-      group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * K; },
+        group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr),
+                   [=](int r) { return r * RSZ + 2 * P; }, [=](int r) { return 0; },
+                   [=](int r, float v) { atomicAdd(gW + 2 * r + 1, v); });
+      group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * RSZ; },
                  [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
     }
     __syncthreads();

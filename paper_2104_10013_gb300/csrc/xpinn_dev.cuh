@@ -61,6 +61,14 @@ struct NetDev {
   int imb[MAXL + 1];
 };
 
+// Row stride (floats) of the adjoint rows [c][p] of one neuron in the
+// reverse pass: K * P, padded by 4 when it is a multiple of 16, so that
+// adjacent rows start in different shared-memory banks.
+__host__ __device__ inline int adj_stride(int K, int P) {
+  const int kp = K * P;
+  return kp + ((kp & 15) == 0 ? 4 : 0);
+}
+
 // Floats of the forward image of layer k (the larger of the two).
 __host__ __device__ inline int layer_img_floats(const NetDev& nd, int k) {
   return (nd.wp[k - 1] + 1) * nd.wp[k];
