@@ -36,8 +36,8 @@ METRIC = "residual pts/s (jet fwd+bwd) grouped vs per-subdomain loop; query p50/
 # DRAM traffic of the jet kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, one launch of the default workload; see profiles/).
 # Reported only while the kernel source is the one that was measured.
-TRAFFIC = {"jet_step.cuh sha256[:16]": "d9bef43e84c634cc", "workload": "c2",
-           "bytes_per_launch": 63650432 + 944350080}
+TRAFFIC = {"jet_step.cuh sha256[:16]": "cc523a94bf2d00f0", "workload": "c2",
+           "bytes_per_launch": 12231424 + 560440576}
 FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 partitions x 32)
 
 
@@ -387,16 +387,25 @@ def main():
            "adam_steps_per_s": 1e3 / ms_step, "roofline": roof, "gpu_launches": launches_per_step * args.steps,
            "clocks": clk}
 
-    # ---- per-subdomain launch loop, same kernels, same GPU
+    # ---- per-subdomain launch loop, same kernels, same GPU.  Its items are
+    # cut at its own best granularity (more items per subdomain fill more
+    # CTAs of each per-subdomain launch), not the grouped schedule's.
     if not args.no_loop:
-        s.set_options(schedule=1)
-        for _ in range(3):
-            s.step(1, losses=None, stream=stream.cuda_stream)
-        lms, ljet = time_steps(torch, s, stream, flush, args.steps)
+        grouped_opts = s.options()
+        best = None
+        for ipc in (4, 16, 64):
+            s.set_options(schedule=1, items_per_cta=ipc)
+            for _ in range(3):
+                s.step(1, losses=None, stream=stream.cuda_stream)
+            lms, ljet = time_steps(torch, s, stream, flush, args.steps)
+            if best is None or np.sum(lms) < np.sum(best[1]):
+                best = (ipc, lms)
+        ipc, lms = best
         lval = n_res * args.steps / (np.sum(lms) / 1e3)
         out["loop"] = {"value": lval, "unit": "pts/s", "ms_per_step": float(np.mean(lms)),
+                       "items_per_cta": ipc,
                        "grouped_speedup": (n_res * args.steps / (np.sum(step_ms) / 1e3)) / lval}
-        s.set_options(schedule=0)
+        s.set_options(**grouped_opts)
 
     # ---- end to end through the public API with host buffers
     if not args.no_e2e:
