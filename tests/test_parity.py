@@ -331,3 +331,28 @@ def test_stitched_eval_on_voronoi_regions(X, order):
         assert np.isnan(got[-2:]).all() and np.isnan(ref[-2:]).all()
         assert_scaled(got[:-2], ref[:-2], RTOL_JET, f"voronoi eval model {model}", axis=(0, 1))
     s.close()
+
+
+@pytest.mark.parametrize("widths,pde,method", [
+    ([2] + [112] * 11 + [3], P.PDE_NS, P.CPINN),      # the largest width and depth the ABI accepts
+    ([2, 1, 1, 1], P.PDE_POISSON, P.XPINN),          # one neuron per hidden layer
+    ([2, 9, 17, 33, 1], P.PDE_BURGERS, P.XPINN),     # widths that are not multiples of the tile
+])
+def test_extreme_network_shapes(X, widths, pde, method):
+    pb = tiny_problem(pde, method, n_sub=2, widths=widths, n_res=37, n_data=11, n_if=9)
+    rng = np.random.default_rng(7)
+    for sd in pb.subs:   # Xavier-scaled weights keep deep wide jets in a sane range
+        sd.params = [P.xavier_params(n, rng) for n in sd.nets]
+        for layers in sd.params:
+            for k, (W, b) in enumerate(layers):
+                layers[k] = (W, P._f32(rng.normal(size=b.shape) * 0.1))
+    s = X.Solver(pb)
+    losses, g = s.grad()
+    terms, g_ref = Oracle(pb).grad(pb.packed_params())
+    assert_losses(losses, terms)
+    assert_grads(g, g_ref, pb)
+    xy = np.random.default_rng(2).uniform(0, 1, size=(300, 2)).astype(np.float32)
+    got = s.net_jets(0, 0, xy, 2)
+    ref = Oracle(pb).net_jets(pb.packed_params(), 0, 0, xy, 5)
+    assert_scaled(got, ref, RTOL_JET, "jets", axis=(0, 1))
+    s.close()
