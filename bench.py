@@ -237,6 +237,19 @@ def cpu_baseline(pb, seconds):
                       f"of the same workload, {pts} residual points in {t_tot:.1f} s"}
 
 
+def whole_job(total_ms, world, n_res, steps, dist=None, device="cpu"):
+    """Replicas only: every rank trained its own copy of the workload (n_res
+    residual points per step) for `steps` steps in total_ms.  The job's time
+    is the slowest rank's; value = all ranks' residual points / that time.
+    Returns (value in pts/s, ms per step)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * n_res * steps / (total_ms / 1e3), total_ms / steps
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -348,13 +361,7 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = float(np.sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n_res * args.steps / (total_ms / 1e3)
-    ms_step = total_ms / args.steps
+    value, ms_step = whole_job(float(np.sum(step_ms)), world, n_res, args.steps, dist, "cuda")
     launches_per_step = 4 if any(it.xy.shape[0] for it in pb.ifaces) else 3
 
     # ---- roofline of the dominant kernel (the jet kernel over all items)

@@ -1,0 +1,61 @@
+"""The N > 1 path of bench.py on CPU ranks (gloo): replicas only, so the
+only cross-rank step is the max over ranks of the timed region, and the
+reference arm runs on rank 0 alone."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        # rank r took (r + 1) * 10 ms for 5 steps of 100 residual points
+        v, ms = bench.whole_job(10.0 * (rank + 1), world, 100, 5, dist, "cpu")
+        q.put((rank, v, ms))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_whole_job_value_uses_the_slowest_rank():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, v, ms in res:
+        assert ms == pytest.approx(4.0)                    # 20 ms of the slowest rank / 5 steps
+        assert v == pytest.approx(2 * 100 * 5 / 0.020)     # both ranks' points / 20 ms
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    v, ms = bench.whole_job(50.0, 1, 1000, 10)
+    assert ms == pytest.approx(5.0) and v == pytest.approx(1000 * 10 / 0.05)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == ""
