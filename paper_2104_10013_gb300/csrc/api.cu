@@ -108,11 +108,16 @@ bool is_device_ptr(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Jet components at residual points.  Burgers needs (u, u_x, u_t, u_xx);
+// Poisson, Navier-Stokes and the diffusion u-network need only the Laplacian
+// of their second derivatives, carried as one component (Laplacian jets,
+// see jet_step.cuh); the diffusion K-network needs (K, K_x, K_y).
 int k_res(int pde, int net) {
-  if (pde == XPINN_PDE_BURGERS) return net == 0 ? 4 : 0;
-  if (pde == XPINN_PDE_DIFFUSION) return net == 0 ? 5 : 3;
-  return net == 0 ? 5 : 0;
+  if (pde == XPINN_PDE_DIFFUSION) return net == 0 ? 4 : 3;
+  return net == 0 ? 4 : 0;
 }
+// Net 0 of an item with 4 components carries the Laplacian unless the PDE is Burgers.
+int lap_of(int pde, int K0) { return K0 == 4 && pde != XPINN_PDE_BURGERS ? 1 : 0; }
 int k_iface(int pde, int method, int net) {
   if (method == XPINN_XPINN) return k_res(pde, net);
   if (pde == XPINN_PDE_BURGERS) return net == 0 ? 2 : 0;
@@ -329,6 +334,7 @@ void build_plan(xpinn_ctx* h, int p_cap) {
     it.n_pts = n;
     it.K[0] = K0;
     it.K[1] = K1;
+    it.lap = lap_of(h->pde, K0);
     it.P = choose_P(h->subs[q], it.K, p_cap, h->opt.points_per_thread, cta_threads(h));
     it.part_off = -1;
     return it;

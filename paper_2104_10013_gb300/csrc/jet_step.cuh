@@ -147,33 +147,38 @@ __device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* e
 // Components: 0 value, 1..2 first derivatives, 3..4 second derivatives
 // (component 3 pairs with 1, 4 with 2).
 //   h = t,  h_i = s z_i,  h_ii = s z_ii - 2 t s z_i^2,  t = tanh(z), s = 1 - t^2
+// Laplacian jets (LAP, K = 4): component 3 carries the Laplacian z_11 + z_22,
+// whose rule is exact because the diagonal terms add:
+//   h_lap = s z_lap - 2 t s (z_1^2 + z_2^2).
+// PDEs that only need the Laplacian (Poisson, Navier-Stokes, the diffusion
+// u-network) train with 4 components instead of 5.
 // ---------------------------------------------------------------------------
-template <int K>
+template <int K, bool LAP>
 __device__ __forceinline__ void tanh_jet(const float (&z)[K], float (&h)[K], float& t_out) {
   const float t = tanhf(z[0]);
   const float s = 1.f - t * t;
   h[0] = t;
   if (K > 1) h[1] = s * z[1];
   if (K > 2) h[2] = s * z[2];
-  if (K > 3) h[3] = s * z[3] - 2.f * t * s * z[1] * z[1];
+  if (K > 3) h[3] = s * z[3] - 2.f * t * s * (LAP ? z[1] * z[1] + z[2] * z[2] : z[1] * z[1]);
   if (K > 4) h[4] = s * z[4] - 2.f * t * s * z[2] * z[2];
   t_out = t;
 }
 
 // h from the saved (t, z_1, z_2, z_11, z_22)
-template <int K>
+template <int K, bool LAP>
 __device__ __forceinline__ void tanh_jet_from_saved(const float (&sv)[K], float (&h)[K]) {
   const float t = sv[0];
   const float s = 1.f - t * t;
   h[0] = t;
   if (K > 1) h[1] = s * sv[1];
   if (K > 2) h[2] = s * sv[2];
-  if (K > 3) h[3] = s * sv[3] - 2.f * t * s * sv[1] * sv[1];
+  if (K > 3) h[3] = s * sv[3] - 2.f * t * s * (LAP ? sv[1] * sv[1] + sv[2] * sv[2] : sv[1] * sv[1]);
   if (K > 4) h[4] = s * sv[4] - 2.f * t * s * sv[2] * sv[2];
 }
 
 // Reverse of tanh_jet: adjoints hb of (h, h_i, h_ii) to adjoints of (z, z_i, z_ii).
-template <int K>
+template <int K, bool LAP>
 __device__ __forceinline__ void tanh_jet_bwd(const float (&sv)[K], const float (&hb)[K], float (&zb)[K]) {
   const float t = sv[0];
   const float s = 1.f - t * t;
@@ -183,7 +188,9 @@ __device__ __forceinline__ void tanh_jet_bwd(const float (&sv)[K], const float (
   if (K > 3) {
     zb[3] = s * hb[3];
     zb[1] -= 4.f * t * s * sv[1] * hb[3];
-    tb += (-2.f * t * sv[3] + (6.f * t * t - 2.f) * sv[1] * sv[1]) * hb[3];
+    if (LAP) zb[2] -= 4.f * t * s * sv[2] * hb[3];
+    const float g2 = LAP ? sv[1] * sv[1] + sv[2] * sv[2] : sv[1] * sv[1];
+    tb += (-2.f * t * sv[3] + (6.f * t * t - 2.f) * g2) * hb[3];
   }
   if (K > 4) {
     zb[4] = s * hb[4];
@@ -243,7 +250,7 @@ __device__ __forceinline__ void phi_derivs(int kind, float v, float& d0, float& 
   }
 }
 
-template <int K>
+template <int K, bool LAP>
 __device__ __forceinline__ void phi_jet(const Act& a, const float (&z)[K], float (&h)[K]) {
   float v[K];
 #pragma unroll
@@ -253,36 +260,36 @@ __device__ __forceinline__ void phi_jet(const Act& a, const float (&z)[K], float
   h[0] = d0;
   if (K > 1) h[1] = d1 * v[1];
   if (K > 2) h[2] = d1 * v[2];
-  if (K > 3) h[3] = fmaf(d2 * v[1], v[1], d1 * v[3]);
+  if (K > 3) h[3] = fmaf(d2 * v[1], v[1], d1 * v[3]) + (LAP ? d2 * v[2] * v[2] : 0.f);
   if (K > 4) h[4] = fmaf(d2 * v[2], v[2], d1 * v[4]);
 }
 
 // forward: h from the pre-activation jet z; sv0 is the value to save at component 0
-template <int K, bool GEN>
+template <int K, bool LAP, bool GEN>
 __device__ __forceinline__ void act_jet(const Act& a, const float (&z)[K], float (&h)[K], float& sv0) {
   if constexpr (!GEN) {
-    tanh_jet<K>(z, h, sv0);
+    tanh_jet<K, LAP>(z, h, sv0);
   } else {
-    phi_jet<K>(a, z, h);
+    phi_jet<K, LAP>(a, z, h);
     sv0 = z[0];
   }
 }
 
-template <int K, bool GEN>
+template <int K, bool LAP, bool GEN>
 __device__ __forceinline__ void act_jet_from_saved(const Act& a, const float (&sv)[K], float (&h)[K]) {
   if constexpr (!GEN)
-    tanh_jet_from_saved<K>(sv, h);
+    tanh_jet_from_saved<K, LAP>(sv, h);
   else
-    phi_jet<K>(a, sv, h);
+    phi_jet<K, LAP>(a, sv, h);
 }
 
 // reverse: adjoints hb of h to adjoints zb of the unscaled z; gs += dJ/ds
 // (= sum over components of vb_c z_c, vb the adjoint of v = s z).
-template <int K, bool GEN>
+template <int K, bool LAP, bool GEN>
 __device__ __forceinline__ void act_jet_bwd(const Act& a, const float (&sv)[K], const float (&hb)[K],
                                             float (&zb)[K], float& gs) {
   if constexpr (!GEN) {
-    tanh_jet_bwd<K>(sv, hb, zb);
+    tanh_jet_bwd<K, LAP>(sv, hb, zb);
   } else {
     float v[K], vb[K];
 #pragma unroll
@@ -295,7 +302,9 @@ __device__ __forceinline__ void act_jet_bwd(const Act& a, const float (&sv)[K], 
     if (K > 3) {
       vb[3] = d1 * hb[3];
       vb[1] += 2.f * d2 * v[1] * hb[3];
-      b0 += (d2 * v[3] + d3 * v[1] * v[1]) * hb[3];
+      if (LAP) vb[2] += 2.f * d2 * v[2] * hb[3];
+      const float g2 = LAP ? v[1] * v[1] + v[2] * v[2] : v[1] * v[1];
+      b0 += (d2 * v[3] + d3 * g2) * hb[3];
     }
     if (K > 4) {
       vb[4] = d1 * hb[4];
@@ -569,7 +578,7 @@ struct Walk {
 // saved pre-activation jets of every layer in S.
 // S layout: layer 1..L-1: [wp_k][K][P] each, then layer L: [D][K][P].
 // ---------------------------------------------------------------------------
-template <int K, int PT, bool GEN>
+template <int K, bool LAP, int PT, bool GEN>
 __device__ __noinline__ uint32_t net_forward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm,
                                              const float* __restrict__ img, int P, float* __restrict__ S,
                                              int uoff, uint32_t ph, int* err) {
@@ -600,7 +609,7 @@ __device__ __noinline__ uint32_t net_forward(SmemLayout sl, const NetDev& nd, co
       if (K > 2) z[2] = wv;
       if (K > 3) z[3] = 0.f;
       if (K > 4) z[4] = 0.f;
-      act_jet<K, GEN>(a1, z, h, t);
+      act_jet<K, LAP, GEN>(a1, z, h, t);
 #pragma unroll
       for (int c = 0; c < K; ++c) {
         s.A[(n * K + c) * P + p] = h[c];
@@ -640,7 +649,7 @@ __device__ __noinline__ uint32_t net_forward(SmemLayout sl, const NetDev& nd, co
           float z[K], h[K], t;
 #pragma unroll
           for (int c = 0; c < K; ++c) z[c] = acc[i][c][pp];
-          act_jet<K, GEN>(ak, z, h, t);
+          act_jet<K, LAP, GEN>(ak, z, h, t);
 #pragma unroll
           for (int c = 0; c < K; ++c) {
             sv[c][pp] = c == 0 ? t : z[c];
@@ -687,7 +696,7 @@ __device__ __noinline__ uint32_t net_forward(SmemLayout sl, const NetDev& nd, co
         y[0] = softplus_f(z[0]);
         if (K > 1) y[1] = g * z[1];
         if (K > 2) y[2] = g * z[2];
-        if (K > 3) y[3] = g * z[3] + g1 * z[1] * z[1];
+        if (K > 3) y[3] = g * z[3] + g1 * (LAP ? z[1] * z[1] + z[2] * z[2] : z[1] * z[1]);
         if (K > 4) y[4] = g * z[4] + g1 * z[2] * z[2];
       } else {
 #pragma unroll
@@ -702,7 +711,7 @@ __device__ __noinline__ uint32_t net_forward(SmemLayout sl, const NetDev& nd, co
 }
 
 // H^{k}[n][c][p] = act(saved S^k) into dst, for all n < wp (padded rows give 0)
-template <int K, bool GEN>
+template <int K, bool LAP, bool GEN>
 __device__ __forceinline__ void act_from_saved(const Act& a, float* __restrict__ dst, const float* __restrict__ Sk,
                                                int wp, int P) {
   for (Walk wk(P); wk.r < wp; wk.next()) {
@@ -710,7 +719,7 @@ __device__ __forceinline__ void act_from_saved(const Act& a, float* __restrict__
     float sv[K], h[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) sv[c] = Sk[(n * K + c) * P + p];
-    act_jet_from_saved<K, GEN>(a, sv, h);
+    act_jet_from_saved<K, LAP, GEN>(a, sv, h);
 #pragma unroll
     for (int c = 0; c < K; ++c) dst[(n * K + c) * P + p] = h[c];
   }
@@ -718,7 +727,7 @@ __device__ __forceinline__ void act_from_saved(const Act& a, float* __restrict__
 
 // The same, transposed: HT[(c*P + p) * wp + n] (row stride wp), for the
 // weight-gradient contraction.  A thread takes one neuron and 4 points.
-template <int K, bool GEN>
+template <int K, bool LAP, bool GEN>
 __device__ __forceinline__ void act_from_saved_T(const Act& a, float* __restrict__ HT, const float* __restrict__ Sk,
                                                  int wp, int P) {
   const int P4 = P >> 2;
@@ -733,7 +742,7 @@ __device__ __forceinline__ void act_from_saved_T(const Act& a, float* __restrict
 #pragma unroll
       for (int c = 0; c < K; ++c)
         sv[c] = t == 0 ? sv4[c].x : (t == 1 ? sv4[c].y : (t == 2 ? sv4[c].z : sv4[c].w));
-      act_jet_from_saved<K, GEN>(a, sv, h);
+      act_jet_from_saved<K, LAP, GEN>(a, sv, h);
 #pragma unroll
       for (int c = 0; c < K; ++c) HT[(c * P + 4 * pq + t) * wp + n] = h[c];
     }
@@ -744,7 +753,7 @@ __device__ __forceinline__ void act_from_saved_T(const Act& a, float* __restrict
 // Network reverse pass.  Ub holds the seeds [D][K][P] (overwritten).  The
 // gradient slice gslice receives dW^k, db^k at the network's offsets.
 // ---------------------------------------------------------------------------
-template <int K, int PT, bool GEN>
+template <int K, bool LAP, int PT, bool GEN>
 __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm,
                                               const float* __restrict__ img, int P, const float* __restrict__ S,
                                               int uoff, float* __restrict__ gslice, bool first, uint32_t ph,
@@ -779,7 +788,12 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
       float b0 = g * yb[0];
       if (K > 1) { zb[1] = g * yb[1]; b0 += g1 * z[1] * yb[1]; }
       if (K > 2) { zb[2] = g * yb[2]; b0 += g1 * z[2] * yb[2]; }
-      if (K > 3) { zb[3] = g * yb[3]; zb[1] += 2.f * g1 * z[1] * yb[3]; b0 += (g1 * z[3] + g2 * z[1] * z[1]) * yb[3]; }
+      if (K > 3) {
+        zb[3] = g * yb[3];
+        zb[1] += 2.f * g1 * z[1] * yb[3];
+        if (LAP) zb[2] += 2.f * g1 * z[2] * yb[3];
+        b0 += (g1 * z[3] + g2 * (LAP ? z[1] * z[1] + z[2] * z[2] : z[1] * z[1])) * yb[3];
+      }
       if (K > 4) { zb[4] = g * yb[4]; zb[2] += 2.f * g1 * z[2] * yb[4]; b0 += (g1 * z[4] + g2 * z[2] * z[2]) * yb[4]; }
       zb[0] = b0;
 #pragma unroll
@@ -787,7 +801,7 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
     }
   }
   const float* Sk = SL - in_p * KP;   // saved jets of layer L-1
-  act_from_saved<K, GEN>(GEN ? layer_act(nd, prm, L - 1) : Act{}, s.A, Sk, in_p, P);
+  act_from_saved<K, LAP, GEN>(GEN ? layer_act(nd, prm, L - 1) : Act{}, s.A, Sk, in_p, P);
   __syncthreads();
   {
     float* gW = gslice + nd.off[L];
@@ -859,7 +873,7 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
             sv[c] = sv2[c][pp];
             hb[c] = acc[i][c][pp];
           }
-          act_jet_bwd<K, GEN>(ak, sv, hb, zb, gs);
+          act_jet_bwd<K, LAP, GEN>(ak, sv, hb, zb, gs);
 #pragma unroll
           for (int c = 0; c < K; ++c) acc[i][c][pp] = zb[c];
         }
@@ -875,7 +889,7 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
     if (k >= 2) {
       const int in_pk = nd.wp[k - 1], in_wk = nd.w[k - 1];
       const float* Skm1 = Sk - in_pk * KP;
-      act_from_saved_T<K, GEN>(GEN ? layer_act(nd, prm, k - 1) : Act{}, s.A, Skm1, in_pk, P);
+      act_from_saved_T<K, LAP, GEN>(GEN ? layer_act(nd, prm, k - 1) : Act{}, s.A, Skm1, in_pk, P);
       const float* Wn = b ? s.W1 : s.W0;   // [out_p][in_pk] = W^k
       mbar_wait(s.bar + b, (ph >> b) & 1u, err);
       ph ^= 1u << b;
@@ -1075,16 +1089,18 @@ __device__ __forceinline__ void flux_seed(int pde, const PtJets& J, float n0, fl
 // the fixed-slope tanh passes; the general kernel picks, per network, the
 // tanh passes or the general ones.
 template <int PT, bool GEN>
-__device__ uint32_t forward_any(int K, SmemLayout sl, const NetDev& nd, const float* prm, const float* img, int P,
-                                float* S, int uoff, uint32_t ph, int* err) {
-#define XP_FWD(KK, G) return net_forward<KK, PT, G>(sl, nd, prm, img, P, S, uoff, ph, err)
-#define XP_SWITCH(G)        \
-  switch (K) {              \
-    case 1: XP_FWD(1, G);   \
-    case 2: XP_FWD(2, G);   \
-    case 3: XP_FWD(3, G);   \
-    case 4: XP_FWD(4, G);   \
-    default: XP_FWD(5, G);  \
+__device__ uint32_t forward_any(int K, bool lap, SmemLayout sl, const NetDev& nd, const float* prm, const float* img,
+                                int P, float* S, int uoff, uint32_t ph, int* err) {
+#define XP_FWD(KK, L, G) return net_forward<KK, L, PT, G>(sl, nd, prm, img, P, S, uoff, ph, err)
+#define XP_SWITCH(G)                         \
+  switch (K) {                               \
+    case 1: XP_FWD(1, false, G);             \
+    case 2: XP_FWD(2, false, G);             \
+    case 3: XP_FWD(3, false, G);             \
+    case 4:                                  \
+      if (lap) XP_FWD(4, true, G);           \
+      XP_FWD(4, false, G);                   \
+    default: XP_FWD(5, false, G);            \
   }
   if constexpr (GEN) {
     if (net_is_general(nd)) {
@@ -1097,16 +1113,19 @@ __device__ uint32_t forward_any(int K, SmemLayout sl, const NetDev& nd, const fl
 }
 
 template <int PT, bool GEN>
-__device__ uint32_t backward_any(int K, SmemLayout sl, const NetDev& nd, const float* prm, const float* img,
-                                 int P, const float* S, int uoff, float* g, bool first, uint32_t ph, int* err) {
-#define XP_BWD(KK, G) return net_backward<KK, PT, G>(sl, nd, prm, img, P, S, uoff, g, first, ph, err)
-#define XP_SWITCH(G)        \
-  switch (K) {              \
-    case 1: XP_BWD(1, G);   \
-    case 2: XP_BWD(2, G);   \
-    case 3: XP_BWD(3, G);   \
-    case 4: XP_BWD(4, G);   \
-    default: XP_BWD(5, G);  \
+__device__ uint32_t backward_any(int K, bool lap, SmemLayout sl, const NetDev& nd, const float* prm,
+                                 const float* img, int P, const float* S, int uoff, float* g, bool first,
+                                 uint32_t ph, int* err) {
+#define XP_BWD(KK, L, G) return net_backward<KK, L, PT, G>(sl, nd, prm, img, P, S, uoff, g, first, ph, err)
+#define XP_SWITCH(G)                         \
+  switch (K) {                               \
+    case 1: XP_BWD(1, false, G);             \
+    case 2: XP_BWD(2, false, G);             \
+    case 3: XP_BWD(3, false, G);             \
+    case 4:                                  \
+      if (lap) XP_BWD(4, true, G);           \
+      XP_BWD(4, false, G);                   \
+    default: XP_BWD(5, false, G);            \
   }
   if constexpr (GEN) {
     if (net_is_general(nd)) {
@@ -1307,8 +1326,8 @@ __device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& i
       s.sy[p] = z.y;
     }
     __syncthreads();
-    if (it.K[0]) ph = forward_any<PT, GEN>(it.K[0], sl, sd.net[0], prm, img, P, scratch, 0, ph, a.err);
-    if (it.K[1]) ph = forward_any<PT, GEN>(it.K[1], sl, sd.net[1], prm, img, P, scratch + s1, u1, ph, a.err);
+    if (it.K[0]) ph = forward_any<PT, GEN>(it.K[0], it.lap != 0, sl, sd.net[0], prm, img, P, scratch, 0, ph, a.err);
+    if (it.K[1]) ph = forward_any<PT, GEN>(it.K[1], false, sl, sd.net[1], prm, img, P, scratch + s1, u1, ph, a.err);
     // ---- per point: loss terms and seeds (or exchange / evaluation output)
     for (int p = tid; p < P; p += blockDim.x) {
       const bool valid = p < nv;
@@ -1351,9 +1370,11 @@ __device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& i
     if (has_bwd) {
       float* gs = a.partials + it.part_off;
       if (it.K[0])
-        ph = backward_any<PT, GEN>(it.K[0], sl, sd.net[0], prm, img, P, scratch, 0, gs, first, ph, a.err);
+        ph = backward_any<PT, GEN>(it.K[0], it.lap != 0, sl, sd.net[0], prm, img, P, scratch, 0, gs, first, ph,
+                                   a.err);
       if (it.K[1])
-        ph = backward_any<PT, GEN>(it.K[1], sl, sd.net[1], prm, img, P, scratch + s1, u1, gs, first, ph, a.err);
+        ph = backward_any<PT, GEN>(it.K[1], false, sl, sd.net[1], prm, img, P, scratch + s1, u1, gs, first, ph,
+                                   a.err);
       // a net that is not evaluated by this item contributes zero gradient
       if (first)
         for (int n = 0; n < sd.n_nets; ++n)

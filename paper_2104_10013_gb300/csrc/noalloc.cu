@@ -185,7 +185,8 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   sd.w_res = w_res;
   sd.n_res = (int)n;
   sd.inv_n_res = n ? 1.f / (float)n : 0.f;
-  const int K = pde == XPINN_PDE_BURGERS ? 4 : 5;
+  // (u, u_x, u_t, u_xx) for Burgers, Laplacian jets (u, u_x, u_y, lap u) otherwise
+  const int K = 4;
   const int D = nd.w[L];
   int P = std::min(256, (NT / (wmax / MT)) * 2);
   P = std::min(P, std::max(4, 2048 / (D * K)));
@@ -227,6 +228,7 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
     it.n_pts = (int)std::min<int64_t>(per_item, n - s0);
     it.P = P;
     it.K[0] = K;
+    it.lap = pde == XPINN_PDE_BURGERS ? 0 : 1;
     it.part_off = (int64_t)d.n_items * sd.n_params;
     ++d.n_items;
   }

@@ -149,6 +149,7 @@ struct Item {
   int n_pts;
   int P;                 // points per sub-tile
   int K[MAXNETS];        // jet components per net, 0 if the net is not evaluated
+  int lap;               // 1: net 0 carries (u, d0 u, d1 u, d00 u + d11 u) in 4 components
   int64_t pt_off;        // first point (pts, or the eval point buffer)
   int64_t part_off;      // first float of this item's gradient slice (-1: none)
   int64_t out_off;       // eval: first output float; others unused
