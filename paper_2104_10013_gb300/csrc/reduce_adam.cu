@@ -59,11 +59,30 @@ __global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
     const int slot = (*a.loss_slot) % a.ring_cap;
     a.loss_ring[((int64_t)slot * a.n_sub + q) * XPINN_N_TERMS + term] = (float)acc;
   }
+  // the slice offsets of this subdomain's items, once per block
+  constexpr int MAXI = 256;
+  __shared__ int64_t s_off[MAXI];
+  const int n_it = ie - ib;
+  for (int k = threadIdx.x; k < n_it && k < MAXI; k += RT) s_off[k] = a.q_part_off[ib + k];
   __syncthreads();
   const int e = blk.y + threadIdx.x;
   if (e >= sd.n_params) return;
+  // fixed-order sum; four independent loads in flight per step
   float g = 0.f;
-  for (int k = ib; k < ie; ++k) g += a.partials[a.q_part_off[k] + e];
+  int k = 0;
+  if (n_it <= MAXI) {
+    for (; k + 4 <= n_it; k += 4) {
+      const float v0 = a.partials[s_off[k] + e], v1 = a.partials[s_off[k + 1] + e];
+      const float v2 = a.partials[s_off[k + 2] + e], v3 = a.partials[s_off[k + 3] + e];
+      g += v0;
+      g += v1;
+      g += v2;
+      g += v3;
+    }
+    for (; k < n_it; ++k) g += a.partials[s_off[k] + e];
+  } else {
+    for (; k < n_it; ++k) g += a.partials[a.q_part_off[ib + k] + e];
+  }
   const int64_t gi = sd.poff + e;
   if (a.grads) a.grads[gi] = g;
   if (a.do_adam) {
