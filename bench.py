@@ -362,7 +362,9 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     value, ms_step = whole_job(float(np.sum(step_ms)), world, n_res, args.steps, dist, "cuda")
-    launches_per_step = 4 if any(it.xy.shape[0] for it in pb.ifaces) else 3
+    # our kernels per step: step_begin, pack_weights (when some network has a
+    # hidden-to-hidden layer), the jet kernel, reduce_adam
+    launches_per_step = 3 + int(any(len(n.widths) > 3 for sd in pb.subs for n in sd.nets))
 
     # ---- roofline of the dominant kernel (the jet kernel over all items)
     flops = algorithmic_flops(pb)
