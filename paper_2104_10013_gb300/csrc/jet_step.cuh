@@ -347,6 +347,17 @@ __device__ __forceinline__ float sigmoid_f(float z) {
 // Register-tiled contractions
 // ---------------------------------------------------------------------------
 
+// Two fused multiply-adds in one instruction (packed FP32, sm_100 and later):
+// (a.x b.x + c.x, a.y b.y + c.y), each rounded as fmaf rounds it.
+__device__ __forceinline__ void ffma2(float& c0, float& c1, float a0, float a1, float b0, float b1) {
+  uint64_t c = (uint64_t)__float_as_uint(c0) | ((uint64_t)__float_as_uint(c1) << 32);
+  const uint64_t a = (uint64_t)__float_as_uint(a0) | ((uint64_t)__float_as_uint(a1) << 32);
+  const uint64_t b = (uint64_t)__float_as_uint(b0) | ((uint64_t)__float_as_uint(b1) << 32);
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a), "l"(b));
+  c0 = __uint_as_float((uint32_t)c);
+  c1 = __uint_as_float((uint32_t)(c >> 32));
+}
+
 // Z[n][c][p] = sum_j Wt[j][n] A[j][c][p] + (c == 0) b[n], tile n0..n0+7 x p0..p0+PT-1
 template <int K, int PT>
 __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const float* __restrict__ Wt,
@@ -375,9 +386,14 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const floa
 #pragma unroll
     for (int i = 0; i < MT; ++i)
 #pragma unroll
-      for (int c = 0; c < K; ++c)
+      for (int c = 0; c < K; ++c) {
+        if constexpr (PT == 2) {
+          ffma2(acc[i][c][0], acc[i][c][1], w[i], w[i], h[c][0], h[c][1]);
+        } else {
 #pragma unroll
-        for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], h[c][pp], acc[i][c][pp]);
+          for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], h[c][pp], acc[i][c][pp]);
+        }
+      }
   }
 }
 
@@ -405,9 +421,14 @@ __device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, int RSZ, 
 #pragma unroll
     for (int i = 0; i < MT; ++i)
 #pragma unroll
-      for (int c = 0; c < K; ++c)
+      for (int c = 0; c < K; ++c) {
+        if constexpr (PT == 2) {
+          ffma2(acc[i][c][0], acc[i][c][1], w[i], w[i], zb[c][0], zb[c][1]);
+        } else {
 #pragma unroll
-        for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], zb[c][pp], acc[i][c][pp]);
+          for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], zb[c][pp], acc[i][c][pp]);
+        }
+      }
   }
 }
 
@@ -478,10 +499,8 @@ __device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, int RSZ, 
           for (int t = 0; t < 4; ++t)
 #pragma unroll
             for (int q = 0; q < NB; ++q) {
-              acc[i][4 * q + 0] = fmaf(zv[t], h[t][q].x, acc[i][4 * q + 0]);
-              acc[i][4 * q + 1] = fmaf(zv[t], h[t][q].y, acc[i][4 * q + 1]);
-              acc[i][4 * q + 2] = fmaf(zv[t], h[t][q].z, acc[i][4 * q + 2]);
-              acc[i][4 * q + 3] = fmaf(zv[t], h[t][q].w, acc[i][4 * q + 3]);
+              ffma2(acc[i][4 * q + 0], acc[i][4 * q + 1], h[t][q].x, h[t][q].y, zv[t], zv[t]);
+              ffma2(acc[i][4 * q + 2], acc[i][4 * q + 3], h[t][q].z, h[t][q].w, zv[t], zv[t]);
             }
         }
       }
