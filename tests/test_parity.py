@@ -336,6 +336,7 @@ def test_stitched_eval_on_voronoi_regions(X, order):
 @pytest.mark.parametrize("widths,pde,method", [
     ([2] + [112] * 11 + [3], P.PDE_NS, P.CPINN),      # the largest width and depth the ABI accepts
     ([2, 1, 1, 1], P.PDE_POISSON, P.XPINN),          # one neuron per hidden layer
+    ([2, 16, 3], P.PDE_NS, P.XPINN),                 # one hidden layer: no hidden-to-hidden weights
     ([2, 9, 17, 33, 1], P.PDE_BURGERS, P.XPINN),     # widths that are not multiples of the tile
 ])
 def test_extreme_network_shapes(X, widths, pde, method):
