@@ -357,3 +357,29 @@ def test_extreme_network_shapes(X, widths, pde, method):
     ref = Oracle(pb).net_jets(pb.packed_params(), 0, 0, xy, 5)
     assert_scaled(got, ref, RTOL_JET, "jets", axis=(0, 1))
     s.close()
+
+
+def test_evaluation_follows_new_parameters(X):
+    """The weight images the jet kernel copies are rebuilt after set_params and
+    after training steps: evaluations use the parameters of the moment."""
+    pb = small_c2()
+    s = X.Solver(pb)
+    orc = Oracle(pb)
+    xy = np.random.default_rng(5).uniform(0, 1, size=(500, 2)).astype(np.float32)
+    q = 5
+    x0, x1, y0, y1 = pb.subs[q].rect
+    xy[:, 0] = x0 + (x1 - x0) * xy[:, 0]
+    xy[:, 1] = y0 + (y1 - y0) * xy[:, 1]
+    got0 = s.net_jets(q, 0, xy, 2)                    # images built from the initial parameters
+    theta = pb.packed_params() * np.float32(0.9)
+    s.set_params(theta)
+    got1 = s.net_jets(q, 0, xy, 2)
+    ref1 = orc.net_jets(theta, q, 0, xy, 5)
+    assert_scaled(got1, ref1, RTOL_JET, "after set_params", axis=(0, 1))
+    assert np.abs(got1 - got0).max() > 1e-3
+    s.step(2)
+    theta2 = s.get_params()
+    got2 = s.net_jets(q, 0, xy, 2)
+    ref2 = orc.net_jets(theta2, q, 0, xy, 5)
+    assert_scaled(got2, ref2, RTOL_JET, "after steps", axis=(0, 1))
+    s.close()
