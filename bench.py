@@ -232,9 +232,21 @@ def cpu_baseline(pb, seconds):
         pts += pb.subs[q].res_xy.shape[0]
         qs.append(q)
         q = (q + 1) % pb.n_sub
-    return {"value": pts / t_tot, "unit": "pts/s", "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle gradient of {len(qs)} whole subdomains (q = {qs[0]}..{qs[-1]} in turn) "
-                      f"of the same workload, {pts} residual points in {t_tot:.1f} s"}
+    # the same oracle on one core, for a short sample (the smallest subdomain)
+    n_thr = torch.get_num_threads()
+    q1 = int(np.argmin([sd.res_xy.shape[0] for sd in pb.subs]))
+    torch.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        orc.grad(theta, subset=[q1])
+        t1 = time.perf_counter() - t0
+    finally:
+        torch.set_num_threads(n_thr)
+    return {"value": pts / t_tot, "unit": "pts/s", "cores": n_thr, "kind": "oracle",
+            "sample": f"FP64 oracle gradients of {len(qs)} whole subdomains of the same workload, taken in "
+                      f"turn (q = 0, 1, ...), {pts} residual points in {t_tot:.1f} s",
+            "one_core": {"value": pb.subs[q1].res_xy.shape[0] / t1, "unit": "pts/s",
+                         "sample": f"subdomain {q1}, {pb.subs[q1].res_xy.shape[0]} residual points, one thread"}}
 
 
 def whole_job(total_ms, world, n_res, steps, dist=None, device="cpu"):
