@@ -60,3 +60,40 @@ def test_inverse_diffusion_256_copies_sampled():
     pb = P.diffusion_xpinn()
     assert pb.n_sub == 2560 and pb.n_params == 256 * (80620 + 10 * (5 + 4))   # weights, biases; slopes
     check_sample(X, pb, [3, 1234, 2559])
+
+
+def test_kovasznay_gradient_against_central_differences_at_step_0():
+    """The Navier-Stokes cPINN workload's weight gradients from the GPU at the
+    initial parameters, against FP64 central differences of J_q (neighbours'
+    networks unchanged) for sampled weights of every layer of two subdomains:
+    the check the Navier-Stokes configuration asks for, without the oracle's
+    own gradient in between."""
+    from paper_2104_10013_gb300 import build as B
+    from paper_2104_10013_gb300 import xpinn as X
+    import torch
+    B.build()
+    X.load()
+    pb = P.kovasznay_cpinn(nx=3, ny=3, n_res=400, n_iface=48, n_bc=40)
+    s = X.Solver(pb)
+    _, g = s.grad()
+    s.close()
+    orc = Oracle(pb)
+    W = orc.weights()
+    theta = pb.packed_params().astype(np.float64)
+    rng = np.random.default_rng(3)
+    slices = tensor_slices(pb)
+    h = 1e-6
+    for q in (0, 4):
+        gq = np.concatenate([g[sl] for name, sl in slices if name.startswith(f"q{q}n")])
+        scale = np.abs(gq).max()
+        for name, sl in slices:
+            if not name.startswith(f"q{q}n"):
+                continue
+            for i in rng.choice(np.arange(sl.start, sl.stop), 2, replace=False):
+                tp, tm = theta.copy(), theta.copy()
+                tp[i] += h
+                tm[i] -= h
+                jp = (orc.loss_terms(torch.tensor(tp), subset=[q]).detach().numpy()[0] * W[q]).sum()
+                jm = (orc.loss_terms(torch.tensor(tm), subset=[q]).detach().numpy()[0] * W[q]).sum()
+                fd = (jp - jm) / (2 * h)
+                assert abs(g[i] - fd) <= 1e-4 * scale, (name, i, g[i], fd)

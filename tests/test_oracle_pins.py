@@ -412,3 +412,55 @@ def test_gradient_with_slopes_matches_central_differences(pde, method, act):
         Jm = (orc.loss_terms(torch.tensor(tm)).detach().numpy()[q] * W[q]).sum()
         fd = (Jp - Jm) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def _taylor_forward(layers, z, out_act, act, slopes, scale):
+    """Second-order forward-mode (truncated Taylor) arithmetic written out
+    here: every quantity carries (value, d/dz0, d/dz1, d2/dz0^2, d2/dz1^2)
+    and each operation applies its chain rule.  Independent of the oracle,
+    which takes its derivatives by reverse-mode autograd."""
+    def lin(W, b, H):            # H: [n_in, 5, npts] -> [n_out, 5, npts]
+        out = np.einsum("oi,icp->ocp", W, H)
+        out[:, 0, :] += b[:, None]
+        return out
+
+    def unary(f, f1, f2, Z):     # elementwise phi with its first two derivatives
+        v, d0, d1, dd0, dd1 = Z[:, 0], Z[:, 1], Z[:, 2], Z[:, 3], Z[:, 4]
+        return np.stack([f(v), f1(v) * d0, f1(v) * d1, f1(v) * dd0 + f2(v) * d0 ** 2,
+                         f1(v) * dd1 + f2(v) * d1 ** 2], 1)
+
+    phis = {P.PHI_TANH: (np.tanh, lambda v: 1 - np.tanh(v) ** 2,
+                         lambda v: -2 * np.tanh(v) * (1 - np.tanh(v) ** 2)),
+            P.PHI_SIN: (np.sin, np.cos, lambda v: -np.sin(v)),
+            P.PHI_COS: (np.cos, lambda v: -np.sin(v), lambda v: -np.cos(v))}
+    npts = z.shape[0]
+    H = np.zeros((2, 5, npts))
+    H[:, 0, :] = z.T
+    H[0, 1, :] = 1.0
+    H[1, 2, :] = 1.0
+    for k, (W, b) in enumerate(layers):
+        if k > 0:
+            s = 1.0 if slopes is None else scale * slopes[k - 1]
+            f, f1, f2 = phis[act]
+            H = unary(lambda v: f(s * v), lambda v: s * f1(s * v), lambda v: s * s * f2(s * v), H)
+        H = lin(W, b, H)
+    if out_act == P.ACT_SOFTPLUS:
+        sig = lambda v: 1 / (1 + np.exp(-v))
+        H = unary(lambda v: np.log1p(np.exp(v)), sig, lambda v: sig(v) * (1 - sig(v)), H)
+    return np.transpose(H, (2, 0, 1))       # [npts, n_out, 5]
+
+
+@pytest.mark.parametrize("act,adaptive,out_act", [(P.PHI_TANH, False, P.ACT_IDENTITY),
+                                                  (P.PHI_SIN, True, P.ACT_IDENTITY),
+                                                  (P.PHI_COS, True, P.ACT_SOFTPLUS)])
+def test_jets_match_forward_mode_taylor_arithmetic(act, adaptive, out_act):
+    rng = np.random.default_rng(11)
+    net = P.NetSpec([2, 6, 5, 4, 2], out_act, act=act, adaptive=adaptive)
+    layers = [(rng.normal(size=(net.widths[k], net.widths[k - 1])) * 0.8, rng.normal(size=net.widths[k]) * 0.3)
+              for k in range(1, len(net.widths))]
+    slopes = rng.uniform(0.08, 0.15, size=net.n_slopes) if adaptive else None
+    z = rng.normal(size=(25, 2))
+    ref = _taylor_forward(layers, z, out_act, act, slopes, 10.0)
+    got = jets([(torch.tensor(W), torch.tensor(b)) for W, b in layers], torch.tensor(z), out_act, 5, act,
+               None if slopes is None else torch.tensor(slopes), 10.0).detach().numpy()
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-10)
