@@ -167,3 +167,24 @@ def test_noalloc_with_an_adaptive_sin_network(X):
     assert abs(float(loss.item()) - float(losses[0, 2])) <= 1e-5 * abs(float(losses[0, 2]))
     g = grads.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+
+
+def test_fixed_tanh_and_general_networks_in_one_launch(X):
+    """Subdomains alternate between fixed-slope tanh networks and trained-slope
+    sin networks: one launch of the general kernel family runs both kinds of
+    network passes, which share the weight buffers and their barriers."""
+    import dataclasses
+    pb = P.poisson_xpinn(n_res_range=(300, 1200), n_iface=64, n_bc=40)
+    rng = np.random.default_rng(8)
+    for q, s in enumerate(pb.subs):
+        if q % 2:
+            s.nets = [dataclasses.replace(n, act=P.PHI_SIN, adaptive=True) for n in s.nets]
+            s.slopes = [P._f32(rng.uniform(0.08, 0.15, size=n.n_slopes)) for n in s.nets]
+    _grad_parity(X, pb)
+    # and the diffusion pair: a fixed tanh u-network beside a trained cos K-network
+    pb2 = P.diffusion_xpinn(n_res=800, n_obs=60, n_iface=30, n_kbc=10, n_copies=1)
+    for s in pb2.subs:
+        s.nets = [dataclasses.replace(s.nets[0], act=P.PHI_TANH, adaptive=False),
+                  dataclasses.replace(s.nets[1], act=P.PHI_COS, adaptive=True)]
+        s.slopes = []
+    _grad_parity(X, pb2)
