@@ -153,3 +153,17 @@ def test_null_handles_are_errors_not_crashes(lib):
     assert lib.xpinn_step(None, 1, None, None) == -1
     assert lib.xpinn_num_params(None) == -1
     assert lib.xpinn_last_error()
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library the binding raises, and so
+    does every entry point that needs it."""
+    from paper_2104_10013_gb300 import problems as P
+    from paper_2104_10013_gb300 import xpinn as X
+    from tests.cases import tiny_problem
+    monkeypatch.setattr(X, "_LIB", None)
+    monkeypatch.setattr(X, "lib_path", lambda: str(tmp_path / "libxpinn.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        X.load()
+    with pytest.raises(RuntimeError, match="not built"):
+        X.Solver(tiny_problem(P.PDE_POISSON, P.XPINN))
