@@ -1,7 +1,9 @@
 """GPU (CUDA C-ABI) vs the FP64 oracle, element by element, on the same
 seeded inputs and the same float32 weights.
 
-Tolerances (fixed here, derived in the design doc from float32 arithmetic):
+Tolerances (fixed here; float32 rounds each layer at about 6e-8 relative to
+its activations, and the jets, losses and gradients sum tens to thousands of
+such terms):
   jets, interface values, losses:  |a - b| <= 1e-5 * max(|b|, rms(b))
       where rms is taken over the compared points and, for jets, over all
       outputs of the network for the same jet component (the float32
