@@ -51,6 +51,9 @@ def workload(name):
         return P.burgers_cpinn(), "cPINN Burgers, 4 x-slabs, 2->20x3->1, 1000 residual pts each"
     if name == "c3":
         return P.kovasznay_cpinn(), "cPINN Kovasznay NS Re=40, 8x8 grid, 2->64x6->3, 50k residual pts each"
+    if name == "c3s":
+        return P.kovasznay_cpinn(nx=4, ny=4, n_res=20000), ("the Kovasznay cPINN workload reduced for counter "
+                                                            "captures: 4x4 grid, 2->64x6->3, 20k residual pts each")
     if name == "tablevb":
         return P.burgers_spacetime(4, 2), ("XPINN space-time Burgers, 4 x 2 subdomains, 2->20x5->1, 80k residual pts "
                                            "in total, 20 pts per interface (Table TableVB)")
