@@ -1269,7 +1269,7 @@ int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* be
   try {
     for (int nt : {256, 512, 128})
     for (int pt : {2, 1})
-      for (int ipc : {4, 8, 16, 2})
+      for (int ipc : {4, 8, 16, 2, 32})
         for (int cap : {0, 64, 128, 32}) {
           if (elapsed_s() > 20.0) continue;   // time budget: keep the best so far
           if (nt == 512 && pt != 1) continue;
