@@ -120,11 +120,18 @@ __device__ __forceinline__ void bulk_g2s(float* dst, const float* src, uint32_t 
                : "memory");
 }
 
-// Every thread: wait for the phase of `bar` with parity `parity`.  Once any
-// wait of the launch has given up, the others return at once.
+// Every thread: wait for the phase of `bar` with parity `parity`, that is
+// for the bulk copy it counts.  The wait is bounded: about a second (2^31
+// clock cycles), or about a millisecond once some wait of the launch has
+// already given up, which still drains a copy in flight (a copy of one
+// layer's weights takes microseconds) but keeps a launch whose barriers are
+// out of step from waiting a second per layer.  So a copy in flight (of
+// valid memory, done in microseconds) is waited for before the CTA reuses
+// the buffer or exits.
 __device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
   const long long t0 = clock64();
-  for (unsigned it = 0;; ++it) {
+  long long limit = 0;
+  for (;;) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -134,8 +141,8 @@ __device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* e
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (ok) return;
-    if ((it & 1023u) == 1023u && *reinterpret_cast<volatile int*>(err) != 0) return;
-    if (clock64() - t0 > (1ll << 31)) {
+    if (limit == 0) limit = *reinterpret_cast<volatile int*>(err) != 0 ? (1ll << 21) : (1ll << 31);
+    if (clock64() - t0 > limit) {
       atomicCAS(err, 0, XPINN_ERR_TIMEOUT);
       return;
     }
