@@ -305,7 +305,7 @@ void item_needs(const SubDev& sd, const Item& it, Limits& l) {
 
 size_t smem_of(const Limits& l, int nt) {
   StepArgs a{};
-  a.szA = round_up(std::max(l.szA, nt * 32), 4);
+  a.szA = round_up(l.szA, 4);
   a.szW = round_up(l.szW, 4);
   a.szU = round_up(l.szU, 4);
   a.pmax = round_up(l.pmax, 4);
@@ -476,7 +476,7 @@ void size_and_upload_plan(xpinn_ctx* h) {
   const Plan& pl = h->plan;
   const Limits l = limits_of(h, h->p_cap);
   StepArgs& a = h->base;
-  a.szA = round_up(std::max(l.szA, cta_threads(h) * 32), 4);   // also the dW split-reduction buffer
+  a.szA = round_up(l.szA, 4);
   a.szW = round_up(l.szW, 4);
   a.szU = round_up(l.szU, 4);
   a.pmax = round_up(l.pmax, 4);

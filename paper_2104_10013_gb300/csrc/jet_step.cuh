@@ -452,35 +452,35 @@ __device__ __forceinline__ void accum(float* p, float v, bool first) {
 
 // dW[n][j] += sum_{c,p} Zb[n][c][p] H[j][c][p] for n < out_w, j < in_w, with
 // Zb rows at stride RSZ and H given transposed, HT[(c*P + p)][j] (row stride
-// RS).  Each thread owns an 8 x TB tile of dW over the whole contraction
-// (TB = 4 measured fastest; 8, and unrolling the contraction loop, were
-// slower).  Its rows n = tn + i * (out_p / 8), i = 0..7, are interleaved so
-// that the threads of a warp, which hold consecutive tiles, read adjacent Zb
-// rows (different banks when RSZ mod 32 is not 0 or 16) and consecutive HT
-// columns.  Per 4 contraction steps a thread loads 8 Zb and TB HT float4s for
-// 32 TB FMAs.  Narrow layers split the contraction over S threads per tile
-// and reduce the S partial tiles in a fixed order through shared memory (R,
-// at least blockDim.x * 8 * TB floats; it may alias HT, which is dead once
-// the contraction is done).
+// RS).  Each thread owns an 8 x TB tile of dW (TB = 4 measured fastest; 8,
+// and unrolling the contraction loop, were slower).  Its rows
+// n = tn + i * (out_p / 8), i = 0..7, are interleaved so that the threads of
+// a warp, which hold consecutive tiles, read adjacent Zb rows (different
+// banks when RSZ mod 32 is not 0 or 16) and consecutive HT columns.  Per 4
+// contraction steps a thread loads 8 Zb and TB HT float4s for 32 TB FMAs.
+// Narrow layers split the contraction: S threads (a power of two, up to 16)
+// share a tile as lanes l, l + 32/S, ... of one warp, and their partial
+// tiles are added with a fixed butterfly of warp shuffles (deterministic; no
+// shared-memory buffer and no block barrier; a shared-memory reduction with
+// two barriers was 0.1 ms slower on the default workload).
 template <int TB>
-__device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, int RSZ, const float* __restrict__ HT,
-                                         int RS, int out_p, int in_p, int out_w, int in_w, int KP,
-                                         float* __restrict__ R, float* __restrict__ pW, bool first) {
-  constexpr int TE = 8 * TB;   // tile elements
-  constexpr int NB = TB / 4;   // float4 columns per HT row
-  const int tid = threadIdx.x;
+__device__ __forceinline__ void dW_tiles_warp(const float* __restrict__ Zb, int RSZ, const float* __restrict__ HT,
+                                              int RS, int out_p, int in_p, int out_w, int in_w, int KP,
+                                              float* __restrict__ pW, bool first) {
+  constexpr int NB = TB / 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
   const int tj_n = in_p / TB, tn_n = out_p >> 3;
   const int T = tj_n * tn_n;
   int S = (int)blockDim.x / T;
-  S = S < 1 ? 1 : (S > 16 ? 16 : S);
+  S = S >= 16 ? 16 : (S >= 8 ? 8 : (S >= 4 ? 4 : (S >= 2 ? 2 : 1)));
+  const int TPW = 32 / S;   // tiles per warp
   const int KP4 = KP >> 2, RSZ4 = RSZ >> 2;
-  const bool split = S > 1;
-  for (int base = 0; base < T * S; base += blockDim.x) {
-    const int u = base + tid;
-    const bool valid = u < T * S;
-    const int tile = valid ? u % T : 0;
-    const int sp = valid ? u / T : 0;
-    const int tn = tile / tj_n, tj = tile - tn * tj_n;
+  const int sp = lane / TPW;
+  for (int base = 0; base < T; base += n_warps * TPW) {
+    const int tile = base + warp * TPW + (lane - sp * TPW);
+    const bool valid = tile < T;
+    const int tt = valid ? tile : 0;
+    const int tn = tt / tj_n, tj = tt - tn * tj_n;
     const int j0 = tj * TB;
     float acc[8][TB];
 #pragma unroll
@@ -512,31 +512,18 @@ __device__ __forceinline__ void dW_tiles(const float* __restrict__ Zb, int RSZ, 
         }
       }
     }
-    if (!split) {
-      if (valid) {
+    for (int o = TPW; o < 32; o <<= 1)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int n = tn + i * tn_n;
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int jj = 0; jj < TB; ++jj)
-            if (n < out_w && j0 + jj < in_w) accum(pW + n * in_w + j0 + jj, acc[i][jj], first);
-        }
-      }
-    } else {
-      __syncthreads();                       // HT / Zb reads of all threads done
-      if (valid) {
+        for (int jj = 0; jj < TB; ++jj) acc[i][jj] += __shfl_xor_sync(0xffffffffu, acc[i][jj], o);
+    if (valid && sp == 0) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 8; ++i) {
+        const int n = tn + i * tn_n;
 #pragma unroll
-          for (int jj = 0; jj < TB; ++jj) R[(sp * T + tile) * TE + i * TB + jj] = acc[i][jj];
-      }
-      __syncthreads();
-      for (int e = tid; e < T * TE; e += blockDim.x) {
-        const int tl = e / TE, q = e - tl * TE, i = q / TB, jj = q - i * TB;
-        float v = 0.f;
-        for (int k = 0; k < S; ++k) v += R[(k * T + tl) * TE + q];
-        const int n = (tl / tj_n) + i * tn_n, j = (tl % tj_n) * TB + jj;
-        if (n < out_w && j < in_w) accum(pW + n * in_w + j, v, first);
+        for (int jj = 0; jj < TB; ++jj)
+          if (n < out_w && j0 + jj < in_w) accum(pW + n * in_w + j0 + jj, acc[i][jj], first);
       }
     }
   }
@@ -922,7 +909,7 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
       __syncthreads();
       // h-bar^{k-1} = (W^k)^T zb^k into registers, then dW^k and db^k
       if (ng < in_pk / MT) gemm_bwd<K, PT>(s.B, RSZ, Wn, out_w, in_pk, P, n0, p0, acc);
-      dW_tiles<4>(s.B, RSZ, s.A, in_pk, out_p, in_pk, out_w, in_wk, KP, s.A, gW, first);
+      dW_tiles_warp<4>(s.B, RSZ, s.A, in_pk, out_p, in_pk, out_w, in_wk, KP, gW, first);
       float* gb = gW + out_w * in_wk;
       group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * RSZ; },
                  [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });

@@ -253,7 +253,7 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   a.re = re;
   a.n_out_total = D;
   a.n_eq = pde == XPINN_PDE_NS ? 3 : 1;
-  a.szA = (int)std::max(wmax * adj_stride(K, P), NT * 32);
+  a.szA = wmax * adj_stride(K, P);
   a.szW = 4;
   for (int k = 2; k < L; ++k) a.szW = std::max(a.szW, layer_img_floats(nd, k));
   a.szU = (D * K * P + 3) / 4 * 4;
