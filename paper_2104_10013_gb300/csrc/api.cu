@@ -303,8 +303,9 @@ void item_needs(const SubDev& sd, const Item& it, Limits& l) {
   l.pmax = std::max(l.pmax, it.P);
 }
 
-size_t smem_of(const Limits& l, int nt) {
+size_t smem_of(const Limits& l, int gen) {
   StepArgs a{};
+  a.gen = gen;
   a.szA = round_up(l.szA, 4);
   a.szW = round_up(l.szW, 4);
   a.szU = round_up(l.szU, 4);
@@ -525,7 +526,7 @@ void plan(xpinn_ctx* h) {
   for (;;) {
     h->grid = h->n_sm * per_sm_ctas;   // provisional, for item sizes
     build_plan(h, cap);
-    if (smem_of(limits_of(h, cap), nt) <= budget || cap <= 8) break;
+    if (smem_of(limits_of(h, cap), any_general(h)) <= budget || cap <= 8) break;
     cap -= 4;
   }
   h->p_cap = cap;

@@ -29,9 +29,11 @@ const void* kernel_for(int pt, int nt, bool gen) {
 
 size_t jet_step_smem_bytes(const StepArgs& a) {
   // A, B, two weight buffers, U, Ub, point coordinates; 32 doubles for
-  // reductions and two mbarriers (see carve in jet_step.cuh)
+  // reductions, two mbarriers and, for the general family, the per-warp
+  // slope-gradient partials [2 nets][16 warps][MAXL] (see carve in jet_step.cuh)
   const size_t floats = 2 * (size_t)a.szA + 2 * (size_t)a.szW + 2 * (size_t)a.szU + 2 * (size_t)a.pmax;
-  return floats * sizeof(float) + 32 * sizeof(double) + 2 * sizeof(uint64_t);
+  return floats * sizeof(float) + 32 * sizeof(double) + 2 * sizeof(uint64_t) +
+         (a.gen ? 2 * 16 * MAXL * sizeof(double) : 0);
 }
 
 cudaError_t jet_step_configure(size_t smem) {

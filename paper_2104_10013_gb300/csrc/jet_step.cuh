@@ -66,6 +66,7 @@ struct Smem {
   float* sy;
   double* red;   // 32 doubles for block reductions
   uint64_t* bar; // 2 mbarriers, one per weight buffer
+  double* slope; // [net][warp][layer] partial slope gradients of the current item (general family)
 };
 
 // Sizes of the shared-memory regions (floats).  Functions that are not
@@ -74,7 +75,10 @@ struct Smem {
 // memory (32-bit shared loads and stores, not generic ones).
 struct SmemLayout {
   int szA, szW, szU, pmax;
+  int slopes;   // 1: the per-warp slope-gradient partials exist (general kernel family)
 };
+
+constexpr int SLOPE_WARPS = 16;   // warps of the largest CTA (512 threads)
 
 __device__ __forceinline__ Smem carve(SmemLayout l) {
   extern __shared__ __align__(16) float sm[];
@@ -89,6 +93,7 @@ __device__ __forceinline__ Smem carve(SmemLayout l) {
   s.sy = s.sx + l.pmax;
   s.red = reinterpret_cast<double*>(s.sy + l.pmax);
   s.bar = reinterpret_cast<uint64_t*>(s.red + 32);
+  s.slope = reinterpret_cast<double*>(s.bar + 2);
   return s;
 }
 
@@ -770,7 +775,7 @@ template <int K, bool LAP, int PT, bool GEN>
 __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm,
                                               const float* __restrict__ img, int P, const float* __restrict__ S,
                                               int uoff, float* __restrict__ gslice, bool first, uint32_t ph,
-                                              int* err) {
+                                              int* err, int net) {
   const Smem s = carve(sl);
   float* __restrict__ Ub = s.Ub + uoff;
   const int tid = threadIdx.x;
@@ -894,9 +899,16 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
         for (int c = 0; c < K; ++c) stp<PT>(s.B + (n0 + i) * RSZ + c * P + p0, acc[i][c]);
       }
     }
-    if (GEN && nd.aoff >= 0) {   // dJ/da^k = n dJ/ds_k
-      const double t = block_sum((double)gs, s.red);
-      if (tid == 0) accum(gslice + nd.aoff + k - 1, nd.scale * (float)t, first);
+    if (GEN && nd.aoff >= 0) {
+      // dJ/ds_k: this warp's part, kept per warp over the item's sub-tiles
+      // (summed over the warps in order at the end of the item); no barrier
+      float w = gs;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      if ((tid & 31) == 0) {
+        double* sp = s.slope + (net * SLOPE_WARPS + (tid >> 5)) * MAXL + (k - 1);
+        *sp = first ? (double)w : *sp + (double)w;
+      }
     }
     float* gW = gslice + nd.off[k];
     if (k >= 2) {
@@ -1128,8 +1140,8 @@ __device__ uint32_t forward_any(int K, bool lap, SmemLayout sl, const NetDev& nd
 template <int PT, bool GEN>
 __device__ uint32_t backward_any(int K, bool lap, SmemLayout sl, const NetDev& nd, const float* prm,
                                  const float* img, int P, const float* S, int uoff, float* g, bool first,
-                                 uint32_t ph, int* err) {
-#define XP_BWD(KK, L, G) return net_backward<KK, L, PT, G>(sl, nd, prm, img, P, S, uoff, g, first, ph, err)
+                                 uint32_t ph, int* err, int net) {
+#define XP_BWD(KK, L, G) return net_backward<KK, L, PT, G>(sl, nd, prm, img, P, S, uoff, g, first, ph, err, net)
 #define XP_SWITCH(G)                         \
   switch (K) {                               \
     case 1: XP_BWD(1, false, G);             \
@@ -1384,10 +1396,10 @@ __device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& i
       float* gs = a.partials + it.part_off;
       if (it.K[0])
         ph = backward_any<PT, GEN>(it.K[0], it.lap != 0, sl, sd.net[0], prm, img, P, scratch, 0, gs, first, ph,
-                                   a.err);
+                                   a.err, 0);
       if (it.K[1])
         ph = backward_any<PT, GEN>(it.K[1], false, sl, sd.net[1], prm, img, P, scratch + s1, u1, gs, first, ph,
-                                   a.err);
+                                   a.err, 1);
       // a net that is not evaluated by this item contributes zero gradient
       if (first)
         for (int n = 0; n < sd.n_nets; ++n)
@@ -1397,6 +1409,21 @@ __device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& i
           }
     }
     __syncthreads();
+  }
+  if (GEN && has_bwd) {
+    // slope gradients of the item: the warps' partials in warp order, stored once
+    // (the last sub-tile ended with a barrier, so every warp's partial is visible)
+    float* gsl = a.partials + it.part_off;
+    const int n_warps = (int)(blockDim.x >> 5);
+    for (int n = 0; n < sd.n_nets; ++n) {
+      const NetDev& nd = sd.net[n];
+      if (!it.K[n] || nd.aoff < 0) continue;
+      for (int t = tid; t < nd.L - 1; t += blockDim.x) {
+        double sum = 0.0;
+        for (int w = 0; w < n_warps; ++w) sum += s.slope[(n * SLOPE_WARPS + w) * MAXL + t];
+        gsl[nd.aoff + t] = nd.scale * (float)sum;
+      }
+    }
   }
   if (has_bwd) {
     const double t0s = block_sum(l0, s.red);
@@ -1445,7 +1472,7 @@ static __device__ bool wait_exchange(const StepArgs& a) {
 // the general activations are not in this kernel, so they cost it nothing).
 template <int PT, int NTH, bool GEN>
 __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : (PT == 1 ? 2 : 1) * (256 / NTH)) jet_step_kernel(StepArgs a) {
-  const SmemLayout sl{a.szA, a.szW, a.szU, a.pmax};
+  const SmemLayout sl{a.szA, a.szW, a.szU, a.pmax, GEN ? 1 : 0};
   __shared__ int s_item;
   float* scratch = a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
   uint32_t ph = 0;   // phase parities of the two weight-buffer mbarriers
