@@ -36,8 +36,8 @@ METRIC = "residual pts/s (jet fwd+bwd) grouped vs per-subdomain loop; query p50/
 # DRAM traffic of the jet kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, one launch of the default workload; see profiles/).
 # Reported only while the kernel source is the one that was measured.
-TRAFFIC = {"jet_step.cuh sha256[:16]": "e6ad638a48cb7385", "workload": "c2",
-           "bytes_per_launch": 5127040 + 207409152}
+TRAFFIC = {"jet_step.cuh sha256[:16]": "07f1dc3282e10b69", "workload": "c2",
+           "bytes_per_launch": 4917888 + 227391744}
 FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 partitions x 32)
 
 
