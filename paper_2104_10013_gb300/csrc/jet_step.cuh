@@ -401,9 +401,8 @@ __device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const floa
       for (int c = 0; c < K; ++c) {
         if constexpr (PT == 2) {
           ffma2(acc[i][c][0], acc[i][c][1], w[i], w[i], h[c][0], h[c][1]);
-        } else {
-#pragma unroll
-          for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], h[c][pp], acc[i][c][pp]);
+        } else if ((i & 1) == 0) {   // one point: neurons i, i + 1 share a packed FMA
+          ffma2(acc[i][c][0], acc[i + 1][c][0], w[i], w[i + 1], h[c][0], h[c][0]);
         }
       }
   }
@@ -436,9 +435,8 @@ __device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, int RSZ, 
       for (int c = 0; c < K; ++c) {
         if constexpr (PT == 2) {
           ffma2(acc[i][c][0], acc[i][c][1], w[i], w[i], zb[c][0], zb[c][1]);
-        } else {
-#pragma unroll
-          for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], zb[c][pp], acc[i][c][pp]);
+        } else if ((i & 1) == 0) {
+          ffma2(acc[i][c][0], acc[i + 1][c][0], w[i], w[i + 1], zb[c][0], zb[c][0]);
         }
       }
   }
@@ -1436,8 +1434,6 @@ __device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& i
   return ph;
 }
 
-// PT = 1 keeps registers <= 128 so that two CTAs fit on an SM; PT = 2 uses
-// a larger register tile at one CTA per SM.
 // Wait (thread 0) until `need` exchange items have completed.  Every exchange
 // item is claimed before any item that waits, and exchange items never wait,
 // so the wait ends; it is still bounded: after about 1 s it sets the error

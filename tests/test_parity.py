@@ -385,3 +385,23 @@ def test_evaluation_follows_new_parameters(X):
     ref2 = orc.net_jets(theta2, q, 0, xy, 5)
     assert_scaled(got2, ref2, RTOL_JET, "after steps", axis=(0, 1))
     s.close()
+
+
+# every (points per thread, threads per CTA) instantiation the planner can
+# choose, for both kernel families: the autotuner may pick any of them
+KERNEL_CONFIGS = [(2, 256), (1, 256), (2, 128), (1, 128), (1, 512)]
+
+
+@pytest.mark.parametrize("pt,threads", KERNEL_CONFIGS)
+@pytest.mark.parametrize("family", ["tanh", "general"])
+def test_every_kernel_configuration(X, pt, threads, family):
+    pb = small_c2() if family == "tanh" else with_activations(small_c4(), [P.PHI_SIN, P.PHI_COS, P.PHI_TANH])
+    s = X.Solver(pb)
+    s.set_options(points_per_thread=pt, threads_per_cta=threads, items_per_cta=4)
+    opts = s.options()
+    assert opts["points_per_thread"] == pt and opts["threads_per_cta"] == threads
+    losses, g = s.grad()
+    terms, g_ref = Oracle(pb).grad(pb.packed_params())
+    assert_losses(losses, terms)
+    assert_grads(g, g_ref, pb)
+    s.close()
