@@ -569,6 +569,56 @@ __device__ __forceinline__ void group_dots(int rows, int len4, const float* __re
   }
 }
 
+// Gradients of the first layer (2 inputs), whose jets are z = W x + b,
+// z_i = W[:, i] and z_ii = 0: for each neuron n, in one pass over its
+// adjoint rows (8 lanes per neuron, fixed-order sums),
+//   dW[n][i] = sum_p zb0[n][p] x_i[p] + sum_p zb_{1+i}[n][p],  db[n] = sum_p zb0[n][p].
+template <int K>
+__device__ __forceinline__ void layer1_grads(int rows, int P, const float* __restrict__ Zb, int RSZ,
+                                             const float* __restrict__ sx, const float* __restrict__ sy,
+                                             float* __restrict__ gW, float* __restrict__ gb, bool first) {
+  const int lane8 = threadIdx.x & 7;
+  const int warp = threadIdx.x >> 5;
+  const int P4 = P >> 2;
+  for (int base = warp * 4; base < rows; base += (int)(blockDim.x >> 5) * 4) {
+    const int r = base + ((threadIdx.x >> 3) & 3);
+    const bool valid = r < rows;
+    float ax = 0.f, ay = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    if (valid) {
+      const float4* z0 = reinterpret_cast<const float4*>(Zb + r * RSZ);
+      const float4* x4 = reinterpret_cast<const float4*>(sx);
+      const float4* y4 = reinterpret_cast<const float4*>(sy);
+      for (int g = lane8; g < P4; g += 8) {
+        const float4 z = z0[g], x = x4[g], y = y4[g];
+        ax = fmaf(z.x, x.x, ax); ax = fmaf(z.y, x.y, ax); ax = fmaf(z.z, x.z, ax); ax = fmaf(z.w, x.w, ax);
+        ay = fmaf(z.x, y.x, ay); ay = fmaf(z.y, y.y, ay); ay = fmaf(z.z, y.z, ay); ay = fmaf(z.w, y.w, ay);
+        a0 += (z.x + z.y) + (z.z + z.w);
+        if (K > 1) {
+          const float4 u = z0[P4 + g];
+          a1 += (u.x + u.y) + (u.z + u.w);
+        }
+        if (K > 2) {
+          const float4 v = z0[2 * P4 + g];
+          a2 += (v.x + v.y) + (v.z + v.w);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (valid && lane8 == 0) {
+      accum(gW + 2 * r, ax + a1, first);
+      accum(gW + 2 * r + 1, ay + a2, first);
+      accum(gb + r, a0, first);
+    }
+  }
+}
+
 // The CTA's walk over a row-major [rows][P] array: this thread's elements
 // tid, tid + blockDim.x, ... as (row r, column c), stepped without division.
 struct Walk {
@@ -926,22 +976,8 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
       Sk = Skm1;
     } else {
       __syncthreads();
-      // layer 1: dW^1[n][i] = sum_p zb0[n][p] z_i[p] + sum_p zb_{1+i}[n][p]
-      float* gb = gW + 2 * out_w;
-      group_dots(out_w, P / 4, s.B, s.sx, [=](int r) { return r * RSZ; }, [=](int r) { return 0; },
-                 [=](int r, float v) { accum(gW + 2 * r, v, first); });
-      group_dots(out_w, P / 4, s.B, s.sy, [=](int r) { return r * RSZ; }, [=](int r) { return 0; },
-                 [=](int r, float v) { accum(gW + 2 * r + 1, v, first); });
-      __syncthreads();
-      if (K > 1)
-        group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * RSZ + P; },
-                   [=](int r) { return 0; }, [=](int r, float v) { atomicAdd(gW + 2 * r, v); });
-      if (K > 2)
-        group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr),
-                   [=](int r) { return r * RSZ + 2 * P; }, [=](int r) { return 0; },
-                   [=](int r, float v) { atomicAdd(gW + 2 * r + 1, v); });
-      group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * RSZ; },
-                 [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
+      // layer 1: dW^1[n][i] = sum_p zb0[n][p] x_i[p] + sum_p zb_{1+i}[n][p], db^1[n] = sum_p zb0[n][p]
+      layer1_grads<K>(out_w, P, s.B, RSZ, s.sx, s.sy, gW, gW + 2 * out_w, first);
     }
     __syncthreads();
   }
