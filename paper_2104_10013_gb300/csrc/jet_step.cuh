@@ -823,7 +823,7 @@ template <int K, bool LAP, int PT, bool GEN>
 __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm,
                                               const float* __restrict__ img, int P, const float* __restrict__ S,
                                               int uoff, float* __restrict__ gslice, bool first, uint32_t ph,
-                                              int* err, int net) {
+                                              int* err, int net, int hl) {
   const Smem s = carve(sl);
   float* __restrict__ Ub = s.Ub + uoff;
   const int tid = threadIdx.x;
@@ -867,13 +867,21 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
     }
   }
   const float* Sk = SL - in_p * KP;   // saved jets of layer L-1
-  act_from_saved<K, LAP, GEN>(GEN ? layer_act(nd, prm, L - 1) : Act{}, s.A, Sk, in_p, P);
-  __syncthreads();
+  // H^{L-1}: still in the activation buffer the forward pass left it in when
+  // this network's forward pass was the item's last (hl = 0: A, 1: B; the
+  // barrier after the loss stage made the seeds visible), else rebuilt into A
+  const float* HL = hl == 1 ? s.B : s.A;
+  if (hl < 0) {
+    act_from_saved<K, LAP, GEN>(GEN ? layer_act(nd, prm, L - 1) : Act{}, s.A, Sk, in_p, P);
+    __syncthreads();
+  } else if (nd.out_act == XPINN_ACT_SOFTPLUS) {
+    __syncthreads();   // the softplus seeds above
+  }
   {
     float* gW = gslice + nd.off[L];
     float* gb = gW + D * in_w;
     // dW^L[o][j] = sum_{c,p} zb^L[o][c][p] H^{L-1}[j][c][p]
-    group_dots(D * in_w, KP / 4, Ub, s.A, [=](int r) { return (r / in_w) * KP; },
+    group_dots(D * in_w, KP / 4, Ub, HL, [=](int r) { return (r / in_w) * KP; },
                [=](int r) { return (r % in_w) * KP; }, [=](int r, float v) { accum(gW + r, v, first); });
     // db^L[o] = sum_p zb^L[o][0][p]
     group_dots(D, P / 4, Ub, static_cast<const float*>(nullptr), [=](int r) { return r * KP; },
@@ -1174,8 +1182,8 @@ __device__ uint32_t forward_any(int K, bool lap, SmemLayout sl, const NetDev& nd
 template <int PT, bool GEN>
 __device__ uint32_t backward_any(int K, bool lap, SmemLayout sl, const NetDev& nd, const float* prm,
                                  const float* img, int P, const float* S, int uoff, float* g, bool first,
-                                 uint32_t ph, int* err, int net) {
-#define XP_BWD(KK, L, G) return net_backward<KK, L, PT, G>(sl, nd, prm, img, P, S, uoff, g, first, ph, err, net)
+                                 uint32_t ph, int* err, int net, int hl) {
+#define XP_BWD(KK, L, G) return net_backward<KK, L, PT, G>(sl, nd, prm, img, P, S, uoff, g, first, ph, err, net, hl)
 #define XP_SWITCH(G)                         \
   switch (K) {                               \
     case 1: XP_BWD(1, false, G);             \
@@ -1385,8 +1393,10 @@ __device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& i
       s.sy[p] = z.y;
     }
     __syncthreads();
-    if (it.K[0]) ph = forward_any<PT, GEN>(it.K[0], it.lap != 0, sl, sd.net[0], prm, img, P, scratch, 0, ph, a.err);
+    // net 1 first, so that the network whose reverse pass comes first is the
+    // one whose last hidden activations are still in shared memory
     if (it.K[1]) ph = forward_any<PT, GEN>(it.K[1], false, sl, sd.net[1], prm, img, P, scratch + s1, u1, ph, a.err);
+    if (it.K[0]) ph = forward_any<PT, GEN>(it.K[0], it.lap != 0, sl, sd.net[0], prm, img, P, scratch, 0, ph, a.err);
     // ---- per point: loss terms and seeds (or exchange / evaluation output)
     for (int p = tid; p < P; p += blockDim.x) {
       const bool valid = p < nv;
@@ -1428,12 +1438,16 @@ __device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& i
     __syncthreads();
     if (has_bwd) {
       float* gs = a.partials + it.part_off;
+      // buffer holding the last forward pass's H^{L-1}: A after an even number
+      // of hidden-to-hidden layers, B after an odd one
+      const int n_last = it.K[0] ? 0 : 1;
+      const int hl_last = (sd.net[n_last].L - 2) & 1;
       if (it.K[0])
         ph = backward_any<PT, GEN>(it.K[0], it.lap != 0, sl, sd.net[0], prm, img, P, scratch, 0, gs, first, ph,
-                                   a.err, 0);
+                                   a.err, 0, hl_last);
       if (it.K[1])
         ph = backward_any<PT, GEN>(it.K[1], false, sl, sd.net[1], prm, img, P, scratch + s1, u1, gs, first, ph,
-                                   a.err, 1);
+                                   a.err, 1, n_last == 1 ? hl_last : -1);
       // a net that is not evaluated by this item contributes zero gradient
       if (first)
         for (int n = 0; n < sd.n_nets; ++n)
@@ -1442,7 +1456,9 @@ __device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& i
             for (int e = nd.off[1] + tid; e < nd.end; e += blockDim.x) gs[e] = 0.f;
           }
     }
-    __syncthreads();
+    // no barrier here: the reverse pass ends with one (after its last reads
+    // of sx, sy and the buffers), and without it the barrier after the loss
+    // stage is the last use of shared memory in this sub-tile
   }
   if (GEN && has_bwd) {
     // slope gradients of the item: the warps' partials in warp order, stored once
