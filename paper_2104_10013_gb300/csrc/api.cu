@@ -234,12 +234,6 @@ void validate_net(const xpinn_net_desc& n, int pde, int net_idx, int q) {
     fail(XPINN_ERR_INVALID, "subdomain %d net %d: slope_scale must be finite and > 0", q, net_idx);
 }
 
-double net_macs(const NetDev& n) {
-  double t = 0;
-  for (int k = 1; k <= n.L; ++k) t += (double)n.wp[k] * n.wp[k - 1];
-  return t;
-}
-
 void check_finite(const float* a, int64_t n, const char* what) {
   for (int64_t i = 0; i < n; ++i)
     if (!std::isfinite(a[i])) fail(XPINN_ERR_INVALID, "%s[%lld] is not finite", what, (long long)i);
@@ -313,11 +307,43 @@ size_t smem_of(const Limits& l, int gen) {
   return jet_step_smem_bytes(a);
 }
 
-double item_cost(const SubDev& sd, const Item& it) {
+// Fraction of the CTA's threads the weight-gradient tiles of an out_p x in_p
+// layer keep busy: 8 x 4 tiles, the contraction split S ways (a power of two
+// up to 16, S threads of a tile in one warp), as the kernel assigns them.
+double dw_busy(int out_p, int in_p, int nt) {
+  const int T = (in_p / 4) * (out_p / MT);
+  if (T <= 0) return 1.0;
+  int S = nt / T;
+  S = S >= 16 ? 16 : (S >= 8 ? 8 : (S >= 4 ? 4 : (S >= 2 ? 2 : 1)));
+  const int per_pass = (nt / 32) * (32 / S);
+  const int passes = (T + per_pass - 1) / per_pass;
+  return (double)T * S / ((double)passes * nt);
+}
+
+// Modelled time of an item (about ns on one SM): per point, the three
+// contractions of every hidden layer with padded widths (the weight-gradient
+// one divided by its thread occupancy), scaled by the jet components, plus a
+// fixed cost per layer and sub-tile (barriers, activation passes, the first
+// and output layers) spread over the sub-tile's P points, plus a fixed cost
+// per item.  The coefficients were fitted to the measured time per point of
+// sixteen shapes (widths 25-80, depths 4-6) run alone: within 20%, where a
+// count of true-width multiply-adds was off by up to a factor of 2.3.
+double item_cost(const SubDev& sd, const Item& it, int nt) {
+  const bool fwd_only = it.kind == IT_IFACE_FWD || it.kind == IT_EVAL;
   double c = 0;
-  for (int n = 0; n < sd.n_nets; ++n)
-    if (it.K[n]) c += it.K[n] * net_macs(sd.net[n]) * (it.kind == IT_IFACE_FWD || it.kind == IT_EVAL ? 1 : 3);
-  return c * it.n_pts + 2e4;
+  for (int n = 0; n < sd.n_nets; ++n) {
+    if (!it.K[n]) continue;
+    const NetDev& nd = sd.net[n];
+    double con = 0;
+    for (int k = 2; k < nd.L; ++k) {
+      con += (double)nd.wp[k] * nd.w[k - 1];
+      if (!fwd_only)
+        con += (double)nd.w[k] * nd.wp[k - 1] + (double)nd.wp[k] * nd.wp[k - 1] / dw_busy(nd.wp[k], nd.wp[k - 1], nt);
+    }
+    con += (double)nd.w[nd.L] * nd.w[nd.L - 1] * (fwd_only ? 1 : 3);
+    c += 2.35e-4 * con * it.K[n] / 4.0 + 47.5 * nd.L / std::max(1, it.P) * (fwd_only ? 0.4 : 1.0);
+  }
+  return c * it.n_pts + 3000.0;
 }
 
 // Build items for the training step.  `schedule` 0 orders them by cost
@@ -346,13 +372,13 @@ void build_plan(xpinn_ctx* h, int p_cap) {
     const SubDev& sd = h->subs[q];
     if (sd.n_res) {
       Item it = mk(IT_RES, q, -1, 0, sd.res_off, sd.n_res, k_res(h->pde, 0), sd.n_nets > 1 ? k_res(h->pde, 1) : 0);
-      total += item_cost(sd, it);
+      total += item_cost(sd, it, cta_threads(h));
     }
   }
   const double target = std::max(1.0, total / (double)(h->grid * std::max(1, h->opt.items_per_cta)));
   auto split = [&](Item proto, std::vector<Item>& out) {
     const SubDev& sd = h->subs[proto.q];
-    const double c = item_cost(sd, proto);
+    const double c = item_cost(sd, proto, cta_threads(h));
     int chunks = std::max(1, (int)std::lround(c / target));
     int per = (proto.n_pts + chunks - 1) / chunks;
     per = std::max(proto.P, (per + proto.P - 1) / proto.P * proto.P);
@@ -392,7 +418,7 @@ void build_plan(xpinn_ctx* h, int p_cap) {
     auto key = [&](const Item& a, const Item& b) {
       const bool ia = a.kind == IT_IFACE, ib = b.kind == IT_IFACE;
       if (ia != ib) return ib;
-      return item_cost(h->subs[a.q], a) > item_cost(h->subs[b.q], b);
+      return item_cost(h->subs[a.q], a, cta_threads(h)) > item_cost(h->subs[b.q], b, cta_threads(h));
     };
     if (h->opt.schedule == 0) {
       std::stable_sort(v.begin(), v.end(), key);
