@@ -38,26 +38,38 @@ __global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
     s_bc[0] = (float)(1.0 - pow((double)a.beta1, (double)t));
     s_bc[1] = (float)(1.0 - pow((double)a.beta2, (double)t));
   }
-  // loss terms of this subdomain (first block of the subdomain only)
-  if (blk.y == 0 && threadIdx.x < XPINN_N_TERMS) {
-    const int term = threadIdx.x;
-    double acc = 0.0;
-    for (int k = ib; k < ie; ++k) {
-      const Item& it = a.items[a.q_items[k]];
-      const double* lp = a.loss_part + 2 * a.q_items[k];
-      switch (it.kind) {
-        case IT_DATA0: if (term == 0) acc += lp[0]; break;
-        case IT_DATA1: if (term == 1) acc += lp[0]; break;
-        case IT_RES: if (term == 2) acc += lp[0]; break;
+  // loss terms of this subdomain (first block of the subdomain only): one
+  // warp, lane l takes items l, l + 32, ...; the lanes' sums are combined by a
+  // fixed butterfly, so the order is the same in every step
+  if (blk.y == 0 && threadIdx.x < 32) {
+    double acc[XPINN_N_TERMS];
+#pragma unroll
+    for (int t = 0; t < XPINN_N_TERMS; ++t) acc[t] = 0.0;
+    for (int k = ib + (int)threadIdx.x; k < ie; k += 32) {
+      const int ii = a.q_items[k];
+      const int kind = a.items[ii].kind;
+      const double l0 = a.loss_part[2 * ii], l1 = a.loss_part[2 * ii + 1];
+      switch (kind) {
+        case IT_DATA0: acc[0] += l0; break;
+        case IT_DATA1: acc[1] += l0; break;
+        case IT_RES: acc[2] += l0; break;
         case IT_IFACE:
-          if (term == 3) acc += lp[0];
-          if (term == 4) acc += lp[1];
+          acc[3] += l0;
+          acc[4] += l1;
           break;
         default: break;
       }
     }
-    const int slot = (*a.loss_slot) % a.ring_cap;
-    a.loss_ring[((int64_t)slot * a.n_sub + q) * XPINN_N_TERMS + term] = (float)acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int t = 0; t < XPINN_N_TERMS; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    if (threadIdx.x == 0) {
+      const int slot = (*a.loss_slot) % a.ring_cap;
+#pragma unroll
+      for (int t = 0; t < XPINN_N_TERMS; ++t)
+        a.loss_ring[((int64_t)slot * a.n_sub + q) * XPINN_N_TERMS + t] = (float)acc[t];
+    }
   }
   // the slice offsets of this subdomain's items, once per block
   constexpr int MAXI = 256;
@@ -67,17 +79,16 @@ __global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
   __syncthreads();
   const int e = blk.y + threadIdx.x;
   if (e >= sd.n_params) return;
-  // fixed-order sum; four independent loads in flight per step
+  // fixed-order sum; eight independent loads in flight per step
   float g = 0.f;
   int k = 0;
   if (n_it <= MAXI) {
-    for (; k + 4 <= n_it; k += 4) {
-      const float v0 = a.partials[s_off[k] + e], v1 = a.partials[s_off[k + 1] + e];
-      const float v2 = a.partials[s_off[k + 2] + e], v3 = a.partials[s_off[k + 3] + e];
-      g += v0;
-      g += v1;
-      g += v2;
-      g += v3;
+    for (; k + 8 <= n_it; k += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = a.partials[s_off[k + u] + e];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) g += v[u];
     }
     for (; k < n_it; ++k) g += a.partials[s_off[k] + e];
   } else {
