@@ -35,9 +35,10 @@ METRIC = "residual pts/s (jet fwd+bwd) grouped vs per-subdomain loop; query p50/
 
 # DRAM traffic of the jet kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, one launch of the default workload; see profiles/).
-# Reported only while the kernel source is the one that was measured.
-TRAFFIC = {"jet_step.cuh sha256[:16]": "07f1dc3282e10b69", "workload": "c2",
-           "bytes_per_launch": 4917888 + 227391744}
+# Reported only while the kernel source and the launch's items per CTA (the
+# number of gradient slices it writes) are the ones that were measured.
+TRAFFIC = {"jet_step.cuh sha256[:16]": "35b2bc165dce7bfa", "workload": "c2", "items_per_cta": 8,
+           "bytes_per_launch": 6083840 + 282245248}
 FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 partitions x 32)
 
 
@@ -393,7 +394,8 @@ def main():
     src = os.path.join(ROOT, "paper_2104_10013_gb300", "csrc", "jet_step.cuh")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     traffic = (TRAFFIC["bytes_per_launch"]
-               if sha == TRAFFIC["jet_step.cuh sha256[:16]"] and args.workload == TRAFFIC["workload"] else None)
+               if sha == TRAFFIC["jet_step.cuh sha256[:16]"] and args.workload == TRAFFIC["workload"]
+               and s.options()["items_per_cta"] == TRAFFIC["items_per_cta"] else None)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "xp::jet_step_kernel (residual, data and interface items)",
             "kernel_ms": jet_avg, "kernel_share_of_step": jet_avg / ms_step,
