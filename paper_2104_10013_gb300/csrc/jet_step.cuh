@@ -27,7 +27,8 @@
 // Layer contractions are register-tiled FP32 FFMA loops: a thread owns MT=8
 // neurons x PT points x K jet components (PT = 1 or 2, a template parameter:
 // PT = 1 keeps a thread under 128 registers so that two CTAs share an SM);
-// activations live in shared memory laid out [neuron][component][point].
+// activations live in shared memory laid out [neuron][point][component], so
+// a thread's points and components are one contiguous run of a row.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -35,32 +36,97 @@
 
 namespace xp {
 
-// loads / stores of PT consecutive points
-template <int PT>
-__device__ __forceinline__ void ldp(const float* p, float (&v)[PT]) {
-  if constexpr (PT == 1) {
-    v[0] = *p;
-  } else {
+// Jet arrays (activations and adjoints in shared memory, the saved jets in
+// global scratch, the output jets) are laid out [row][point][component]: a
+// row (neuron or output) holds P x K floats with the K jet components of a
+// point adjacent.  A thread's register tile covers PT points ("slots") of K
+// components, acc[i][s * K + c].  For K = 4 and PT = 2 the threads in lanes
+// 4-7 of every 8 hold their two points in swapped slots (slot s is point
+// p0 + (s ^ 1)), so that the 16-byte accesses of 8 consecutive threads fall
+// in 8 different bank groups.
+template <int K, int PT>
+__device__ __forceinline__ int tile_swap() {
+  if constexpr (K == 4 && PT == 2)
+    return (int)(threadIdx.x >> 2) & 1;
+  else
+    return 0;
+}
+
+// the K components of one point (K = 4: 16-byte aligned; K = 2: 8-byte)
+template <int K>
+__device__ __forceinline__ void ldk(const float* __restrict__ p, float (&v)[K]) {
+  if constexpr (K == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  } else if constexpr (K == 2) {
     const float2 t = *reinterpret_cast<const float2*>(p);
     v[0] = t.x;
     v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < K; ++c) v[c] = p[c];
   }
 }
-template <int PT>
-__device__ __forceinline__ void stp(float* p, const float (&v)[PT]) {
-  if constexpr (PT == 1) {
-    *p = v[0];
-  } else {
+template <int K>
+__device__ __forceinline__ void stk(float* __restrict__ p, const float (&v)[K]) {
+  if constexpr (K == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (K == 2) {
     *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < K; ++c) p[c] = v[c];
+  }
+}
+
+// The thread's tile of one row, r = row + p0 * K (p0 even when PT = 2, so
+// r is 8-byte aligned), in slot order.
+template <int K, int PT>
+__device__ __forceinline__ void ld_tile(const float* __restrict__ r, float (&v)[PT * K], int sw) {
+  if constexpr (K == 4 && PT == 2) {
+    const float4 a = *reinterpret_cast<const float4*>(r + 4 * sw);
+    const float4 b = *reinterpret_cast<const float4*>(r + 4 - 4 * sw);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else if constexpr (PT == 2) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const float2 t = reinterpret_cast<const float2*>(r)[q];
+      v[2 * q] = t.x;
+      v[2 * q + 1] = t.y;
+    }
+  } else {
+    float t[K];
+    ldk<K>(r, t);
+#pragma unroll
+    for (int c = 0; c < K; ++c) v[c] = t[c];
+  }
+}
+template <int K, int PT>
+__device__ __forceinline__ void st_tile(float* __restrict__ r, const float (&v)[PT * K], int sw) {
+  if constexpr (K == 4 && PT == 2) {
+    *reinterpret_cast<float4*>(r + 4 * sw) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(r + 4 - 4 * sw) = make_float4(v[4], v[5], v[6], v[7]);
+  } else if constexpr (PT == 2) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) reinterpret_cast<float2*>(r)[q] = make_float2(v[2 * q], v[2 * q + 1]);
+  } else {
+    float t[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) t[c] = v[c];
+    stk<K>(r, t);
   }
 }
 
 struct Smem {
-  float* A;      // activations H^{k} / H^{k-1}      [wp][K][P]
-  float* B;      // adjoints z-bar^k                 [wp][K][P]
+  float* A;      // activations H^{k} / H^{k-1}      [wp][P][K]
+  float* B;      // adjoints z-bar^k                 [wp][P][K], rows RSZ apart
   float* W0;     // two weight-image buffers: one layer's image is copied
   float* W1;     //   into one while the other layer's is in use
-  float* U;      // output jets of every net         [D][K][P] per net
+  float* U;      // output jets of every net         [D][P][K] per net
   float* Ub;     // seeds (adjoints of U)
   float* sx;     // point coordinates, SoA
   float* sy;
@@ -370,75 +436,40 @@ __device__ __forceinline__ void ffma2(float& c0, float& c1, float a0, float a1, 
   c1 = __uint_as_float((uint32_t)(c >> 32));
 }
 
-// Z[n][c][p] = sum_j Wt[j][n] A[j][c][p] + (c == 0) b[n], tile n0..n0+7 x p0..p0+PT-1
-template <int K, int PT>
-__device__ __forceinline__ void gemm_fwd(const float* __restrict__ A, const float* __restrict__ Wt,
-                                         const float* __restrict__ bias, int in_w, int out_p, int P,
-                                         int n0, int p0, float (&acc)[MT][K][PT]) {
+// The register-tiled contraction of both passes:
+//   acc[i][m] = sum_{r < R} W[r * ws + col0 + i] X[r * xs + xo + m]  (+ bias[col0 + i] on
+//   the value component c = 0 of every slot when BIAS),
+// for the thread's MT columns col0.. of W (two float4s a row) and its tile of
+// PT x K floats at offset xo of every X row (slots as ld_tile).  Forward:
+// X = H^{k-1}, W = (W^k)^T, R = the true input width (padded inputs are zero).
+// Reverse: X = Z-bar^k, W = W^k, R = the true output width.  Pairs of
+// adjacent tile entries share one packed FMA.
+template <int K, int PT, bool BIAS>
+__device__ __forceinline__ void gemm_tile(const float* __restrict__ X, int xs, int xo, const float* __restrict__ W,
+                                          int ws, int col0, int R, const float* __restrict__ bias, int sw,
+                                          float (&acc)[MT][PT * K]) {
+  constexpr int MK = PT * K;
 #pragma unroll
   for (int i = 0; i < MT; ++i) {
-    const float b = bias[n0 + i];
+    const float b = BIAS ? bias[col0 + i] : 0.f;
 #pragma unroll
-    for (int pp = 0; pp < PT; ++pp) {
-      acc[i][0][pp] = b;
+    for (int m = 0; m < MK; ++m) acc[i][m] = (m % K == 0) ? b : 0.f;
+  }
+  const float* wp = W + col0;
+  const float* xp = X + xo;
+#pragma unroll 4
+  for (int r = 0; r < R; ++r) {
+    const float4 wa = *reinterpret_cast<const float4*>(wp + r * ws);
+    const float4 wb = *reinterpret_cast<const float4*>(wp + r * ws + 4);
+    const float w[MT] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+    float v[MK];
+    ld_tile<K, PT>(xp + r * xs, v, sw);
 #pragma unroll
-      for (int c = 1; c < K; ++c) acc[i][c][pp] = 0.f;
+    for (int i = 0; i < MT; ++i) {
+#pragma unroll
+      for (int m = 0; m + 1 < MK; m += 2) ffma2(acc[i][m], acc[i][m + 1], w[i], w[i], v[m], v[m + 1]);
+      if constexpr ((MK & 1) != 0) acc[i][MK - 1] = fmaf(w[i], v[MK - 1], acc[i][MK - 1]);
     }
-  }
-  const float* wp = Wt + n0;
-  const float* ap = A + p0;
-#pragma unroll 4
-  for (int j = 0; j < in_w; ++j) {          // padded inputs are zero: stop at the true width
-    const float4 wa = *reinterpret_cast<const float4*>(wp + j * out_p);
-    const float4 wb = *reinterpret_cast<const float4*>(wp + j * out_p + 4);
-    const float w[MT] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-    float h[K][PT];
-#pragma unroll
-    for (int c = 0; c < K; ++c) ldp<PT>(ap + (j * K + c) * P, h[c]);
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        if constexpr (PT == 2) {
-          ffma2(acc[i][c][0], acc[i][c][1], w[i], w[i], h[c][0], h[c][1]);
-        } else if ((i & 1) == 0) {   // one point: neurons i, i + 1 share a packed FMA
-          ffma2(acc[i][c][0], acc[i + 1][c][0], w[i], w[i + 1], h[c][0], h[c][0]);
-        }
-      }
-  }
-}
-
-// Hb[j][c][p] = sum_n Wn[n][j] Zb[n][c][p] (Zb row stride RSZ), tile j0..j0+7 x p0..p0+PT-1
-template <int K, int PT>
-__device__ __forceinline__ void gemm_bwd(const float* __restrict__ Zb, int RSZ, const float* __restrict__ Wn,
-                                         int out_w, int in_p, int P, int j0, int p0,
-                                         float (&acc)[MT][K][PT]) {
-#pragma unroll
-  for (int i = 0; i < MT; ++i)
-#pragma unroll
-    for (int c = 0; c < K; ++c)
-#pragma unroll
-      for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = 0.f;
-  const float* wp = Wn + j0;
-  const float* zp = Zb + p0;
-#pragma unroll 4
-  for (int n = 0; n < out_w; ++n) {         // padded neurons carry zero adjoints
-    const float4 wa = *reinterpret_cast<const float4*>(wp + n * in_p);
-    const float4 wb = *reinterpret_cast<const float4*>(wp + n * in_p + 4);
-    const float w[MT] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-    float zb[K][PT];
-#pragma unroll
-    for (int c = 0; c < K; ++c) ldp<PT>(zp + n * RSZ + c * P, zb[c]);
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        if constexpr (PT == 2) {
-          ffma2(acc[i][c][0], acc[i][c][1], w[i], w[i], zb[c][0], zb[c][1]);
-        } else if ((i & 1) == 0) {
-          ffma2(acc[i][c][0], acc[i + 1][c][0], w[i], w[i + 1], zb[c][0], zb[c][0]);
-        }
-      }
   }
 }
 
@@ -453,8 +484,8 @@ __device__ __forceinline__ void accum(float* p, float v, bool first) {
     atomicAdd(p, v);
 }
 
-// dW[n][j] += sum_{c,p} Zb[n][c][p] H[j][c][p] for n < out_w, j < in_w, with
-// Zb rows at stride RSZ and H given transposed, HT[(c*P + p)][j] (row stride
+// dW[n][j] += sum_{p,c} Zb[n][p][c] H[j][p][c] for n < out_w, j < in_w, with
+// Zb rows at stride RSZ and H given transposed, HT[(p*K + c)][j] (row stride
 // RS).  Each thread owns an 8 x TB tile of dW (TB = 4 measured fastest; 8,
 // and unrolling the contraction loop, were slower).  Its rows
 // n = tn + i * (out_p / 8), i = 0..7, are interleaved so that the threads of
@@ -571,7 +602,7 @@ __device__ __forceinline__ void group_dots(int rows, int len4, const float* __re
 
 // Gradients of the first layer (2 inputs), whose jets are z = W x + b,
 // z_i = W[:, i] and z_ii = 0: for each neuron n, in one pass over its
-// adjoint rows (8 lanes per neuron, fixed-order sums),
+// adjoint row (8 lanes per neuron, each over every 8th point; fixed-order sums),
 //   dW[n][i] = sum_p zb0[n][p] x_i[p] + sum_p zb_{1+i}[n][p],  db[n] = sum_p zb0[n][p].
 template <int K>
 __device__ __forceinline__ void layer1_grads(int rows, int P, const float* __restrict__ Zb, int RSZ,
@@ -579,28 +610,21 @@ __device__ __forceinline__ void layer1_grads(int rows, int P, const float* __res
                                              float* __restrict__ gW, float* __restrict__ gb, bool first) {
   const int lane8 = threadIdx.x & 7;
   const int warp = threadIdx.x >> 5;
-  const int P4 = P >> 2;
   for (int base = warp * 4; base < rows; base += (int)(blockDim.x >> 5) * 4) {
     const int r = base + ((threadIdx.x >> 3) & 3);
     const bool valid = r < rows;
     float ax = 0.f, ay = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f;
     if (valid) {
-      const float4* z0 = reinterpret_cast<const float4*>(Zb + r * RSZ);
-      const float4* x4 = reinterpret_cast<const float4*>(sx);
-      const float4* y4 = reinterpret_cast<const float4*>(sy);
-      for (int g = lane8; g < P4; g += 8) {
-        const float4 z = z0[g], x = x4[g], y = y4[g];
-        ax = fmaf(z.x, x.x, ax); ax = fmaf(z.y, x.y, ax); ax = fmaf(z.z, x.z, ax); ax = fmaf(z.w, x.w, ax);
-        ay = fmaf(z.x, y.x, ay); ay = fmaf(z.y, y.y, ay); ay = fmaf(z.z, y.z, ay); ay = fmaf(z.w, y.w, ay);
-        a0 += (z.x + z.y) + (z.z + z.w);
-        if (K > 1) {
-          const float4 u = z0[P4 + g];
-          a1 += (u.x + u.y) + (u.z + u.w);
-        }
-        if (K > 2) {
-          const float4 v = z0[2 * P4 + g];
-          a2 += (v.x + v.y) + (v.z + v.w);
-        }
+      const float* zr = Zb + r * RSZ;
+      for (int p = lane8; p < P; p += 8) {
+        float z[K];
+        ldk<K>(zr + p * K, z);
+        const float x = sx[p], y = sy[p];
+        ax = fmaf(z[0], x, ax);
+        ay = fmaf(z[0], y, ay);
+        a0 += z[0];
+        if (K > 1) a1 += z[1];
+        if (K > 2) a2 += z[2];
       }
     }
 #pragma unroll
@@ -616,6 +640,27 @@ __device__ __forceinline__ void layer1_grads(int rows, int P, const float* __res
       accum(gW + 2 * r + 1, ay + a2, first);
       accum(gb + r, a0, first);
     }
+  }
+}
+
+// Sums over the points of the value component (c = 0) of `rows` rows of
+// P x K floats at stride rs: out(r, sum) with 8 lanes per row, fixed order.
+template <int K, typename OUT>
+__device__ __forceinline__ void value_sums(int rows, int P, const float* __restrict__ X, int rs, OUT out) {
+  const int lane8 = threadIdx.x & 7;
+  const int warp = threadIdx.x >> 5;
+  for (int base = warp * 4; base < rows; base += (int)(blockDim.x >> 5) * 4) {
+    const int r = base + ((threadIdx.x >> 3) & 3);
+    const bool valid = r < rows;
+    float acc = 0.f;
+    if (valid) {
+      const float* xr = X + r * rs;
+      for (int p = lane8; p < P; p += 8) acc += xr[p * K];
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (valid && lane8 == 0) out(r, acc);
   }
 }
 
@@ -640,9 +685,9 @@ struct Walk {
 };
 
 // ---------------------------------------------------------------------------
-// Network forward with jets.  Leaves the output jets in Uo [D][K][P] and the
+// Network forward with jets.  Leaves the output jets in Uo [D][P][K] and the
 // saved pre-activation jets of every layer in S.
-// S layout: layer 1..L-1: [wp_k][K][P] each, then layer L: [D][K][P].
+// S layout: layer 1..L-1: [wp_k][P][K] each, then layer L: [D][P][K].
 // ---------------------------------------------------------------------------
 template <int K, bool LAP, int PT, bool GEN>
 __device__ __noinline__ uint32_t net_forward(SmemLayout sl, const NetDev& nd, const float* __restrict__ prm,
@@ -676,11 +721,9 @@ __device__ __noinline__ uint32_t net_forward(SmemLayout sl, const NetDev& nd, co
       if (K > 3) z[3] = 0.f;
       if (K > 4) z[4] = 0.f;
       act_jet<K, LAP, GEN>(a1, z, h, t);
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        s.A[(n * K + c) * P + p] = h[c];
-        S[(n * K + c) * P + p] = c == 0 ? t : z[c];
-      }
+      z[0] = t;
+      stk<K>(s.A + (n * P + p) * K, h);
+      stk<K>(S + (n * P + p) * K, z);
     }
   }
   float* Sk = S + nd.wp[1] * K * P;
@@ -704,31 +747,30 @@ __device__ __noinline__ uint32_t net_forward(SmemLayout sl, const NetDev& nd, co
     const int ng = tid / n_pg, pg = tid - ng * n_pg;
     const bool act = ng < out_p / MT;
     const int n0 = ng * MT, p0 = pg * PT;
-    float acc[MT][K][PT];
+    const int sw = tile_swap<K, PT>();
+    const int KP = K * P;
+    float acc[MT][PT * K];
     if (act) {
-      gemm_fwd<K, PT>(Ain, Wt, Wt + in_p * out_p, in_w, out_p, P, n0, p0, acc);
+      gemm_tile<K, PT, true>(Ain, KP, p0 * K, Wt, out_p, n0, in_w, Wt + in_p * out_p, sw, acc);
 #pragma unroll
       for (int i = 0; i < MT; ++i) {
-        float sv[K][PT];
+        float sv[PT * K];
 #pragma unroll
-        for (int pp = 0; pp < PT; ++pp) {
+        for (int q = 0; q < PT; ++q) {
           float z[K], h[K], t;
 #pragma unroll
-          for (int c = 0; c < K; ++c) z[c] = acc[i][c][pp];
+          for (int c = 0; c < K; ++c) z[c] = acc[i][q * K + c];
           act_jet<K, LAP, GEN>(ak, z, h, t);
 #pragma unroll
           for (int c = 0; c < K; ++c) {
-            sv[c][pp] = c == 0 ? t : z[c];
-            acc[i][c][pp] = h[c];
+            sv[q * K + c] = c == 0 ? t : z[c];
+            acc[i][q * K + c] = h[c];
           }
         }
-#pragma unroll
-        for (int c = 0; c < K; ++c) stp<PT>(Sk + ((n0 + i) * K + c) * P + p0, sv[c]);
+        st_tile<K, PT>(Sk + (n0 + i) * KP + p0 * K, sv, sw);
       }
 #pragma unroll
-      for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int c = 0; c < K; ++c) stp<PT>(Aout + ((n0 + i) * K + c) * P + p0, acc[i][c]);
+      for (int i = 0; i < MT; ++i) st_tile<K, PT>(Aout + (n0 + i) * KP + p0 * K, acc[i], sw);
     }
     __syncthreads();
     Sk += out_p * K * P;
@@ -750,11 +792,12 @@ __device__ __noinline__ uint32_t net_forward(SmemLayout sl, const NetDev& nd, co
       const float* wrow = WL + o * in_w;
       for (int j = 0; j < in_w; ++j) {
         const float w = __ldg(wrow + j);
+        float h[K];
+        ldk<K>(Ain + (j * P + p) * K, h);
 #pragma unroll
-        for (int c = 0; c < K; ++c) z[c] = fmaf(w, Ain[(j * K + c) * P + p], z[c]);
+        for (int c = 0; c < K; ++c) z[c] = fmaf(w, h[c], z[c]);
       }
-#pragma unroll
-      for (int c = 0; c < K; ++c) Sk[(o * K + c) * P + p] = z[c];
+      stk<K>(Sk + (o * P + p) * K, z);
       float y[K];
       if (nd.out_act == XPINN_ACT_SOFTPLUS) {
         const float g = sigmoid_f(z[0]);
@@ -768,55 +811,50 @@ __device__ __noinline__ uint32_t net_forward(SmemLayout sl, const NetDev& nd, co
 #pragma unroll
         for (int c = 0; c < K; ++c) y[c] = z[c];
       }
-#pragma unroll
-      for (int c = 0; c < K; ++c) Uo[(o * K + c) * P + p] = y[c];
+      stk<K>(Uo + (o * P + p) * K, y);
     }
   }
   __syncthreads();
   return ph;
 }
 
-// H^{k}[n][c][p] = act(saved S^k) into dst, for all n < wp (padded rows give 0)
+// H^{k}[n][p][c] = act(saved S^k) into dst, for all n < wp (padded rows give 0)
 template <int K, bool LAP, bool GEN>
 __device__ __forceinline__ void act_from_saved(const Act& a, float* __restrict__ dst, const float* __restrict__ Sk,
                                                int wp, int P) {
   for (Walk wk(P); wk.r < wp; wk.next()) {
-    const int n = wk.r, p = wk.c;
+    const int e = (wk.r * P + wk.c) * K;
     float sv[K], h[K];
-#pragma unroll
-    for (int c = 0; c < K; ++c) sv[c] = Sk[(n * K + c) * P + p];
+    ldk<K>(Sk + e, sv);
     act_jet_from_saved<K, LAP, GEN>(a, sv, h);
-#pragma unroll
-    for (int c = 0; c < K; ++c) dst[(n * K + c) * P + p] = h[c];
+    stk<K>(dst + e, h);
   }
 }
 
-// The same, transposed: HT[(c*P + p) * wp + n] (row stride wp), for the
-// weight-gradient contraction.  A thread takes one neuron and 4 points.
+// The same, transposed: HT[(p*K + c) * wp + n] (row stride wp), for the
+// weight-gradient contraction, whose contraction index is the position
+// p*K + c within a row.  A thread takes one neuron and 4 consecutive points.
 template <int K, bool LAP, bool GEN>
 __device__ __forceinline__ void act_from_saved_T(const Act& a, float* __restrict__ HT, const float* __restrict__ Sk,
                                                  int wp, int P) {
   const int P4 = P >> 2;
   for (Walk wk(wp); wk.r < P4; wk.next()) {
-    const int n = wk.c, pq = wk.r;
-    float4 sv4[K];
+    const int n = wk.c, p4 = 4 * wk.r;
+    float sv[4][K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) sv4[c] = *reinterpret_cast<const float4*>(Sk + (n * K + c) * P + 4 * pq);
+    for (int t = 0; t < 4; ++t) ldk<K>(Sk + (n * P + p4 + t) * K, sv[t]);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      float sv[K], h[K];
+      float h[K];
+      act_jet_from_saved<K, LAP, GEN>(a, sv[t], h);
 #pragma unroll
-      for (int c = 0; c < K; ++c)
-        sv[c] = t == 0 ? sv4[c].x : (t == 1 ? sv4[c].y : (t == 2 ? sv4[c].z : sv4[c].w));
-      act_jet_from_saved<K, LAP, GEN>(a, sv, h);
-#pragma unroll
-      for (int c = 0; c < K; ++c) HT[(c * P + 4 * pq + t) * wp + n] = h[c];
+      for (int c = 0; c < K; ++c) HT[((p4 + t) * K + c) * wp + n] = h[c];
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Network reverse pass.  Ub holds the seeds [D][K][P] (overwritten).  The
+// Network reverse pass.  Ub holds the seeds [D][P][K] (overwritten).  The
 // gradient slice gslice receives dW^k, db^k at the network's offsets.
 // ---------------------------------------------------------------------------
 template <int K, bool LAP, int PT, bool GEN>
@@ -843,11 +881,8 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
     for (Walk wk(P); wk.r < D; wk.next()) {
       const int o = wk.r, p = wk.c;
       float z[K], yb[K], zb[K];
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        z[c] = SL[(o * K + c) * P + p];
-        yb[c] = Ub[(o * K + c) * P + p];
-      }
+      ldk<K>(SL + (o * P + p) * K, z);
+      ldk<K>(Ub + (o * P + p) * K, yb);
       const float g = sigmoid_f(z[0]);
       const float g1 = g * (1.f - g);
       const float g2 = g1 * (1.f - 2.f * g);
@@ -862,8 +897,7 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
       }
       if (K > 4) { zb[4] = g * yb[4]; zb[2] += 2.f * g1 * z[2] * yb[4]; b0 += (g1 * z[4] + g2 * z[2] * z[2]) * yb[4]; }
       zb[0] = b0;
-#pragma unroll
-      for (int c = 0; c < K; ++c) Ub[(o * K + c) * P + p] = zb[c];
+      stk<K>(Ub + (o * P + p) * K, zb);
     }
   }
   const float* Sk = SL - in_p * KP;   // saved jets of layer L-1
@@ -880,15 +914,15 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
   {
     float* gW = gslice + nd.off[L];
     float* gb = gW + D * in_w;
-    // dW^L[o][j] = sum_{c,p} zb^L[o][c][p] H^{L-1}[j][c][p]
+    // dW^L[o][j] = sum_{p,c} zb^L[o][p][c] H^{L-1}[j][p][c]
     group_dots(D * in_w, KP / 4, Ub, HL, [=](int r) { return (r / in_w) * KP; },
                [=](int r) { return (r % in_w) * KP; }, [=](int r, float v) { accum(gW + r, v, first); });
-    // db^L[o] = sum_p zb^L[o][0][p]
-    group_dots(D, P / 4, Ub, static_cast<const float*>(nullptr), [=](int r) { return r * KP; },
-               [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
+    // db^L[o] = sum_p zb^L[o][p][0]
+    value_sums<K>(D, P, Ub, KP, [=](int r, float v) { accum(gb + r, v, first); });
   }
-  // h-bar^{L-1} = (W^L)^T zb^L into registers
-  float acc[MT][K][PT];
+  // h-bar^{L-1} = (W^L)^T zb^L into registers (the thread's tile, slots as ld_tile)
+  const int sw = tile_swap<K, PT>();
+  float acc[MT][PT * K];
   {
     const float* WL = prm + nd.off[L];
     const int ng = tid / n_pg, pg = tid - ng * n_pg;
@@ -896,23 +930,18 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
 #pragma unroll
     for (int i = 0; i < MT; ++i)
 #pragma unroll
-      for (int c = 0; c < K; ++c)
-#pragma unroll
-        for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = 0.f;
+      for (int m = 0; m < PT * K; ++m) acc[i][m] = 0.f;
     if (ng < in_p / MT) {
       for (int o = 0; o < D; ++o) {
         float w[MT];
 #pragma unroll
         for (int i = 0; i < MT; ++i) w[i] = (j0 + i < in_w) ? __ldg(WL + o * in_w + j0 + i) : 0.f;
+        float zb[PT * K];
+        ld_tile<K, PT>(Ub + o * KP + p0 * K, zb, sw);
 #pragma unroll
-        for (int c = 0; c < K; ++c) {
-          float zb[PT];
-          ldp<PT>(Ub + (o * K + c) * P + p0, zb);
+        for (int i = 0; i < MT; ++i)
 #pragma unroll
-          for (int i = 0; i < MT; ++i)
-#pragma unroll
-            for (int pp = 0; pp < PT; ++pp) acc[i][c][pp] = fmaf(w[i], zb[pp], acc[i][c][pp]);
-        }
+          for (int m = 0; m < PT * K; ++m) acc[i][m] = fmaf(w[i], zb[m], acc[i][m]);
       }
     }
   }
@@ -936,23 +965,21 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
     if (ng < out_p / MT) {
 #pragma unroll
       for (int i = 0; i < MT; ++i) {
-        float sv2[K][PT];
+        float sv2[PT * K];
+        ld_tile<K, PT>(Sk + (n0 + i) * KP + p0 * K, sv2, sw);
 #pragma unroll
-        for (int c = 0; c < K; ++c) ldp<PT>(Sk + ((n0 + i) * K + c) * P + p0, sv2[c]);
-#pragma unroll
-        for (int pp = 0; pp < PT; ++pp) {
+        for (int q = 0; q < PT; ++q) {
           float sv[K], hb[K], zb[K];
 #pragma unroll
           for (int c = 0; c < K; ++c) {
-            sv[c] = sv2[c][pp];
-            hb[c] = acc[i][c][pp];
+            sv[c] = sv2[q * K + c];
+            hb[c] = acc[i][q * K + c];
           }
           act_jet_bwd<K, LAP, GEN>(ak, sv, hb, zb, gs);
 #pragma unroll
-          for (int c = 0; c < K; ++c) acc[i][c][pp] = zb[c];
+          for (int c = 0; c < K; ++c) acc[i][q * K + c] = zb[c];
         }
-#pragma unroll
-        for (int c = 0; c < K; ++c) stp<PT>(s.B + (n0 + i) * RSZ + c * P + p0, acc[i][c]);
+        st_tile<K, PT>(s.B + (n0 + i) * RSZ + p0 * K, acc[i], sw);
       }
     }
     if (GEN && nd.aoff >= 0) {
@@ -976,11 +1003,10 @@ __device__ __noinline__ uint32_t net_backward(SmemLayout sl, const NetDev& nd, c
       ph ^= 1u << b;
       __syncthreads();
       // h-bar^{k-1} = (W^k)^T zb^k into registers, then dW^k and db^k
-      if (ng < in_pk / MT) gemm_bwd<K, PT>(s.B, RSZ, Wn, out_w, in_pk, P, n0, p0, acc);
+      if (ng < in_pk / MT) gemm_tile<K, PT, false>(s.B, RSZ, p0 * K, Wn, in_pk, n0, out_w, nullptr, sw, acc);
       dW_tiles_warp<4>(s.B, RSZ, s.A, in_pk, out_p, in_pk, out_w, in_wk, KP, gW, first);
       float* gb = gW + out_w * in_wk;
-      group_dots(out_w, P / 4, s.B, static_cast<const float*>(nullptr), [=](int r) { return r * RSZ; },
-                 [=](int r) { return 0; }, [=](int r, float v) { accum(gb + r, v, first); });
+      value_sums<K>(out_w, P, s.B, RSZ, [=](int r, float v) { accum(gb + r, v, first); });
       Sk = Skm1;
     } else {
       __syncthreads();
@@ -1220,12 +1246,12 @@ __device__ __forceinline__ void load_point_jets(const SubDev& sd, const Item& it
     for (int o = 0; o < XPINN_MAX_OUT; ++o)
 #pragma unroll
       for (int c = 0; c < KMAX; ++c)
-        if (o < D0 && c < K0) J.u[o][c] = U[(o * K0 + c) * P + p];
+        if (o < D0 && c < K0) J.u[o][c] = U[(o * P + p) * K0 + c];
   }
   if (K1) {
 #pragma unroll
     for (int c = 0; c < KMAX; ++c)
-      if (c < K1) J.k[c] = U[u1 + c * P + p];
+      if (c < K1) J.k[c] = U[u1 + p * K1 + c];
   }
 }
 
@@ -1238,12 +1264,12 @@ __device__ __forceinline__ void store_point_seeds(const SubDev& sd, const Item& 
     for (int o = 0; o < XPINN_MAX_OUT; ++o)
 #pragma unroll
       for (int c = 0; c < KMAX; ++c)
-        if (o < D0 && c < K0) Ub[(o * K0 + c) * P + p] = G.u[o][c];
+        if (o < D0 && c < K0) Ub[(o * P + p) * K0 + c] = G.u[o][c];
   }
   if (K1) {
 #pragma unroll
     for (int c = 0; c < KMAX; ++c)
-      if (c < K1) Ub[u1 + c * P + p] = G.k[c];
+      if (c < K1) Ub[u1 + p * K1 + c] = G.k[c];
   }
 }
 
