@@ -37,8 +37,8 @@ METRIC = "residual pts/s (jet fwd+bwd) grouped vs per-subdomain loop; query p50/
 # dram__bytes_write.sum, one launch of the default workload; see profiles/).
 # Reported only while the kernel source and the launch's items per CTA (the
 # number of gradient slices it writes) are the ones that were measured.
-TRAFFIC = {"jet_step.cuh sha256[:16]": "35b2bc165dce7bfa", "workload": "c2", "items_per_cta": 8,
-           "bytes_per_launch": 6083840 + 282245248}
+TRAFFIC = {"jet_step.cuh sha256[:16]": "c1ceacddba609484", "workload": "c2", "items_per_cta": 8,
+           "bytes_per_launch": 5888384 + 269417856}
 FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 partitions x 32)
 
 
