@@ -182,16 +182,45 @@ int xpinn_set_params(xpinn_handle h, const float* src, int64_t n, void* stream);
 /* Loss terms and gradients at the current parameters, with no update:
  * losses [n_sub][XPINN_N_TERMS] (or NULL), grads packed like the parameters
  * (or NULL), dJ(Theta_q)/dTheta_q for every q with the neighbours' interface
- * values held constant (Algorithm 1).  Host or device pointers. */
+ * values held constant (Algorithm 1).  Host or device pointers.  The call
+ * synchronises `stream` and returns XPINN_ERR_NONFINITE (outputs written) if
+ * a loss term is NaN or infinite, XPINN_ERR_TIMEOUT if a device wait gave up,
+ * in this call or an earlier asynchronous one. */
 int xpinn_grad(xpinn_handle h, float* losses, float* grads, void* stream);
+
+/* The objective of the method and its gradient at the current parameters,
+ * with no update: J (1 float, or NULL) = sum over q of J(Theta_q), where
+ * J(Theta_q) = sum_t w_t MSE_t is the weighted loss of subdomain q (Eq.
+ * cPINNLoss or Eq. XPINNLoss with the subdomain's weights, the terms as
+ * listed above); J_sub [n_sub] (or NULL) the J(Theta_q); losses and grads
+ * (or NULL) as xpinn_grad.  The gradient is that of each J(Theta_q) with
+ * respect to its own Theta_q, the neighbours' interface values held
+ * constant (Algorithm 1): the training direction of the method.  Sums are
+ * taken in a fixed order (bitwise reproducible).  Host or device pointers;
+ * synchronises `stream`; errors as xpinn_grad. */
+int xpinn_objective(xpinn_handle h, float* J, float* J_sub, float* losses, float* grads, void* stream);
 
 /* n_steps training steps of Algorithm 1, all subdomains in one grouped
  * launch per phase: interface values, jets + residual + interface terms +
  * reverse pass, then reduction and Adam (Sec. 6).  losses, if not NULL,
  * receives [n_steps][n_sub][XPINN_N_TERMS], each row measured before that
- * step's update.  Returns XPINN_ERR_NONFINITE (after completing the steps) if
- * a loss is NaN or infinite and `losses` was given. */
+ * step's update.
+ * Errors raised on the device (a bounded wait that gave up, a loss that
+ * became NaN or infinite) are kept in the handle's device status word until
+ * a synchronising call reads it.  With host `losses` this call synchronises
+ * and returns XPINN_ERR_TIMEOUT or XPINN_ERR_NONFINITE itself (after
+ * completing the steps).  With losses NULL or a device pointer it returns as
+ * soon as the steps are queued, and the error is returned by the next
+ * synchronising call on the handle: xpinn_sync, xpinn_grad, or xpinn_step
+ * with host losses.  The steps after a non-finite loss still run. */
 int xpinn_step(xpinn_handle h, int32_t n_steps, float* losses, void* stream);
+
+/* Waits for everything queued on `stream`, then reads and clears the
+ * handle's device status word: XPINN_OK, XPINN_ERR_TIMEOUT (a bounded device
+ * wait of an earlier call gave up) or XPINN_ERR_NONFINITE (a loss of an
+ * earlier step or grad was NaN or infinite).  Call it after asynchronous
+ * steps (xpinn_step with losses NULL or on the device). */
+int xpinn_sync(xpinn_handle h, void* stream);
 
 /* Jets of network `net` of subdomain q at n points xy [n][2]:
  * out [n][D_out][1 + 2*(order>0) + 2*(order>1)], order 0..2.  Host or device
@@ -352,11 +381,23 @@ int xpinn_server_destroy(xpinn_server* s);
  * any stream capture.  Every call reuses the same array and leaves its
  * contents behind; each call clears what must start at zero itself.  Calls
  * that overlap on the GPU (other streams, other threads) race on the array:
- * order them on one stream.  Errors: INVALID, UNSUPPORTED, CUDA; the message
- * is available from xpinn_last_error(). */
+ * order them on one stream.  The sub-tile of points is chosen as for a
+ * handle (lowered in steps of 4 while the shared memory does not fit), and
+ * the work is spread over at most one CTA per SM.  Errors: INVALID,
+ * UNSUPPORTED (a network whose tiles do not fit shared memory even at 8
+ * points, or a working set beyond the array), CUDA; the message is
+ * available from xpinn_last_error().  An error on the device (a bounded wait
+ * that gave up) cannot be returned by this asynchronous call: the loss and
+ * every gradient element are then written as NaN. */
 int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, const xpinn_net_desc* net,
                                 const float* params, const float* xy, const float* f, int64_t n,
                                 float w_res, float* loss, float* grads, void* stream);
+
+/* Testing only: the next xpinn_residual_grad_noalloc call of this thread
+ * starts with its device error word set to `code` (as if a wait had given up),
+ * so that the NaN outputs of a failed call can be checked without making a
+ * device wait fail.  0 (the default) leaves the word cleared. */
+int xpinn_noalloc_debug_preset_error(int32_t code);
 
 #ifdef __cplusplus
 }

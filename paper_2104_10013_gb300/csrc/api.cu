@@ -150,6 +150,7 @@ struct xpinn_ctx {
   int n_out_total = 0, n_eq = 1, d4_nv = 0;
   // device problem
   DevBuf<float> params, m, v, grads, res_f, tgt, d4, partials, scratch, loss_ring;
+  DevBuf<float> jq;              // [n_sub + 1]: J(Theta_q) of the last step or grad, then their sum
   DevBuf<float2> pts, poly;
   int n_poly = 0;
   DevBuf<SubDev> subs_d;
@@ -242,59 +243,11 @@ void check_finite(const float* a, int64_t n, const char* what) {
 // ---------------------------------------------------------------------------
 // Planning
 // ---------------------------------------------------------------------------
-struct Limits {
-  int szA = 4, szW = 4, szU = 4, pmax = 4;
-  int64_t scratch = 4;
-};
-
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 int cta_threads(const xpinn_ctx* h) {
   const int t = h->opt.threads_per_cta;
   return (t == 128 || t == 512) ? t : 256;
-}
-
-int max_hidden_wp(const NetDev& n) {
-  int w = MT;
-  for (int k = 1; k < n.L; ++k) w = std::max(w, n.wp[k]);
-  return w;
-}
-
-// Points per sub-tile for an item evaluating the nets with K[n] > 0: enough
-// (neuron group, point group) register tiles to occupy the CTA's threads.
-int choose_P(const SubDev& sd, const int K[2], int cap, int pt, int nt) {
-  int ng = 1, dk = 0;
-  for (int n = 0; n < sd.n_nets; ++n)
-    if (K[n]) {
-      ng = std::max(ng, max_hidden_wp(sd.net[n]) / MT);
-      dk += sd.net[n].w[sd.net[n].L] * K[n];
-    }
-  int P = (nt / ng) * pt;
-  P = std::min(P, 256);
-  P = std::min(P, std::max(4, 2048 / std::max(1, dk)));
-  P = std::min(P, cap);
-  return std::max(4, P / 4 * 4);
-}
-
-void item_needs(const SubDev& sd, const Item& it, Limits& l) {
-  int u = 0;
-  int64_t sc = 0;
-  for (int n = 0; n < sd.n_nets; ++n) {
-    const int K = it.K[n];
-    if (!K) continue;
-    const NetDev& nd = sd.net[n];
-    int rows = 0;
-    for (int k = 1; k < nd.L; ++k) {
-      rows += nd.wp[k];
-      l.szA = std::max(l.szA, nd.wp[k] * adj_stride(K, it.P));
-    }
-    for (int k = 2; k < nd.L; ++k) l.szW = std::max(l.szW, layer_img_floats(nd, k));
-    u += nd.w[nd.L] * K * it.P;
-    sc += (int64_t)(rows + nd.w[nd.L]) * K * it.P;
-  }
-  l.szU = std::max(l.szU, u);
-  l.scratch = std::max(l.scratch, sc);
-  l.pmax = std::max(l.pmax, it.P);
 }
 
 size_t smem_of(const Limits& l, int gen) {
@@ -621,6 +574,8 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads) {
   r.beta2 = h->beta2;
   r.eps = h->eps;
   r.n_sub = h->n_sub;
+  r.err = h->err_d.p;
+  r.jq = h->jq.p;
   if (h->opt.schedule == 0) {
     // one launch: exchange items first, interface items last (they wait)
     mark(h, 1, s);
@@ -682,13 +637,20 @@ void copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   }
 }
 
+// Reads the handle's device status word after everything queued on `s`
+// (synchronises `s`), clears it and turns a set word into an error.  Kernels
+// only ever set the word (first code wins), so an error of an asynchronous
+// call (xpinn_step without host losses) is reported by the next call that
+// comes here: xpinn_sync, xpinn_grad, xpinn_step with host losses, eval.
 void check_device_error(xpinn_ctx* h, cudaStream_t s) {
   int e = 0;
   ck(cudaMemcpyAsync(&e, h->err_d.p, sizeof(int), cudaMemcpyDeviceToHost, s), "read error flag");
   ck(cudaStreamSynchronize(s), "sync");
   if (e) {
     ck(cudaMemsetAsync(h->err_d.p, 0, sizeof(int), s), "reset error flag");
+    ck(cudaStreamSynchronize(s), "sync");
     if (e == XPINN_ERR_TIMEOUT) fail(XPINN_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (e == XPINN_ERR_NONFINITE) fail(XPINN_ERR_NONFINITE, "a loss became non-finite");
     fail(XPINN_ERR_INVALID, "device check failed (code %d)", e);
   }
 }
@@ -964,6 +926,7 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
   h->err_d.alloc(1);
   ck(cudaMemset(h->err_d.p, 0, sizeof(int)), "memset");
   h->loss_ring.alloc((size_t)h->ring_cap * h->n_sub * XPINN_N_TERMS);
+  h->jq.alloc((size_t)h->n_sub + 1);
   StepArgs& a = h->base;
   a.subs = h->subs_d.p;
   a.ifaces = h->ifaces_d.p;
@@ -1084,11 +1047,45 @@ int xpinn_step(xpinn_handle h, int32_t n_steps, float* losses, void* stream) {
   }
   h->img_stale = true;
   ck(cudaGetLastError(), "step");
+  // Host losses: the call has synchronised anyway, so the status word is
+  // read now.  NULL or device losses: the call stays asynchronous and a
+  // timeout or non-finite loss is reported by the next synchronising call
+  // (xpinn_sync).
   if (losses && !dev_out) check_device_error(h, s);
   if (losses && !dev_out) {
     for (size_t i = 0; i < (size_t)n_steps * row; ++i)
       if (!std::isfinite(losses[i])) fail(XPINN_ERR_NONFINITE, "loss became non-finite");
   }
+  API_END
+}
+
+int xpinn_objective(xpinn_handle h, float* J, float* J_sub, float* losses, float* grads, void* stream) {
+  API_BEGIN
+  if (!h) fail(XPINN_ERR_INVALID, "NULL handle");
+  DeviceGuard dg(h);
+  cudaStream_t s = (cudaStream_t)stream;
+  enqueue_step(h, s, false, h->grads.p);
+  h->host_slot += 1;
+  const int slot = h->host_slot % h->ring_cap;
+  if (J) {
+    launch_objective_sum(h->jq.p, h->n_sub, h->jq.p + h->n_sub, s);
+    ck(cudaGetLastError(), "objective launch");
+    copy_out(J, h->jq.p + h->n_sub, sizeof(float), s);
+  }
+  if (J_sub) copy_out(J_sub, h->jq.p, sizeof(float) * h->n_sub, s);
+  if (losses)
+    copy_out(losses, h->loss_ring.p + (size_t)slot * h->n_sub * XPINN_N_TERMS,
+             sizeof(float) * h->n_sub * XPINN_N_TERMS, s);
+  if (grads) copy_out(grads, h->grads.p, sizeof(float) * h->n_params, s);
+  check_device_error(h, s);
+  API_END
+}
+
+int xpinn_sync(xpinn_handle h, void* stream) {
+  API_BEGIN
+  if (!h) fail(XPINN_ERR_INVALID, "NULL handle");
+  DeviceGuard dg(h);
+  check_device_error(h, (cudaStream_t)stream);
   API_END
 }
 

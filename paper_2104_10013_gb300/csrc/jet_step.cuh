@@ -193,12 +193,13 @@ __device__ __forceinline__ void bulk_g2s(float* dst, const float* src, uint32_t 
 
 // Every thread: wait for the phase of `bar` with parity `parity`, that is
 // for the bulk copy it counts.  The wait is bounded: about a second (2^31
-// clock cycles), or about a millisecond once some wait of the launch has
-// already given up, which still drains a copy in flight (a copy of one
-// layer's weights takes microseconds) but keeps a launch whose barriers are
-// out of step from waiting a second per layer.  So a copy in flight (of
-// valid memory, done in microseconds) is waited for before the CTA reuses
-// the buffer or exits.
+// clock cycles), or about a millisecond once some wait has already given up
+// (the error word holds XPINN_ERR_TIMEOUT), which still drains a copy in
+// flight (a copy of one layer's weights takes microseconds) but keeps a
+// launch whose barriers are out of step from waiting a second per layer.
+// So a copy in flight (of valid memory, done in microseconds) is waited for
+// before the CTA reuses the buffer or exits.  Other codes in the error word
+// (a non-finite loss of an earlier step) do not shorten the wait.
 __device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
   const long long t0 = clock64();
   long long limit = 0;
@@ -212,7 +213,8 @@ __device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* e
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (ok) return;
-    if (limit == 0) limit = *reinterpret_cast<volatile int*>(err) != 0 ? (1ll << 21) : (1ll << 31);
+    if (limit == 0)
+      limit = *reinterpret_cast<volatile int*>(err) == XPINN_ERR_TIMEOUT ? (1ll << 21) : (1ll << 31);
     if (clock64() - t0 > limit) {
       atomicCAS(err, 0, XPINN_ERR_TIMEOUT);
       return;
@@ -1522,7 +1524,7 @@ static __device__ bool wait_exchange(const StepArgs& a) {
     int ok = 1;
     unsigned ns = 32;
     for (long it = 0; atomicAdd(a.fwd_done, 0) < a.n_fwd_wait; ++it) {
-      if (it > (1l << 20) || atomicAdd(a.err, 0) != 0) {   // gave up here or elsewhere
+      if (it > (1l << 20) || atomicAdd(a.err, 0) == XPINN_ERR_TIMEOUT) {   // gave up here or elsewhere
         atomicCAS(a.err, 0, XPINN_ERR_TIMEOUT);
         ok = 0;
         break;

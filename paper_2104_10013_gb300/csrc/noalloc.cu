@@ -17,10 +17,15 @@
 // first call before any stream capture.
 //
 // All calls share the one array, and each call leaves its contents behind.
-// The pieces that must start at zero (the work counter) are cleared by every
-// call on its stream.  Calls whose kernels overlap on the GPU (different
-// streams, or different threads without ordering) race on the array and give
-// wrong results: order them on one stream.
+// The pieces that must start at zero (the work counter and the error word)
+// are cleared by every call on its stream.  Calls whose kernels overlap on
+// the GPU (different streams, or different threads without ordering) race on
+// the array and give wrong results: order them on one stream.
+//
+// Errors on the device: the jet kernel's waits are bounded and set the error
+// word when they give up; the call has already returned by then, so the last
+// kernel writes NaN to the loss and to every gradient element instead of a
+// sum that may include slices an earlier call left in the array.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,13 +42,14 @@ void set_last_error(const char* msg);   // the message xpinn_last_error() return
 
 namespace {
 
-constexpr int NA_MAX_ITEMS = 128;     // work items (and gradient slices) per call
+constexpr int NA_MAX_ITEMS = 256;     // work items (and gradient slices) per call; one per CTA
 constexpr int NA_MAX_DEVICES = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[XPINN_NOALLOC_SCRATCH_BYTES];
 
 std::mutex g_mu;
 void* g_ptr[NA_MAX_DEVICES] = {};
+thread_local int g_preset_err = 0;    // testing: the next call's initial error word
 
 struct NaDesc {
   SubDev sd;
@@ -52,6 +58,8 @@ struct NaDesc {
   PackBlock pack[2 * MAXL];   // weight images of the hidden-to-hidden layers
   int n_pack;
 };
+// passed to na_setup_kernel by value: within the 32,764 bytes of kernel parameters
+static_assert(sizeof(NaDesc) <= 32000, "descriptor too large for a kernel parameter");
 
 // Layout of the scratch array (byte offsets, each 256-byte aligned).
 struct NaLayout {
@@ -77,33 +85,39 @@ NaLayout layout(int n_items, int n_params, int grid, int64_t scratch_per_cta, in
 }
 
 // Copies the descriptors (passed by value) into the array and clears the
-// work counter and the error flag: the only state that must start at zero.
-__global__ void na_setup_kernel(NaDesc d, SubDev* sub, Item* items, int* counter, int* err, PackBlock* pack) {
+// work counter and the error word: the only state that must start at zero
+// (err0 is 0 except in the testing hook xpinn_noalloc_debug_preset_error).
+__global__ void na_setup_kernel(NaDesc d, SubDev* sub, Item* items, int* counter, int* err, int err0,
+                                PackBlock* pack) {
   const int t = threadIdx.x;
   if (t == 0) {
     *sub = d.sd;
     *counter = 0;
-    *err = 0;
+    *err = err0;
   }
   for (int i = t; i < d.n_items; i += blockDim.x) items[i] = d.items[i];
   for (int i = t; i < d.n_pack; i += blockDim.x) pack[i] = d.pack[i];
 }
 
 // grads[e] = sum over items (in order) of the item's slice; loss = sum of the
-// items' residual sums (each already divided by n).
+// items' residual sums (each already divided by n).  If the jet kernel set the
+// error word (a bounded wait gave up, so some slices were never written), the
+// outputs are NaN instead: the call is asynchronous and cannot return the
+// error, and a stale sum from an earlier call must not pass for a result.
 __global__ void na_reduce_kernel(const float* __restrict__ partials, const double* __restrict__ loss_part,
-                                 int n_items, int n_params, float* __restrict__ grads,
-                                 float* __restrict__ loss) {
+                                 int n_items, int n_params, const int* __restrict__ err,
+                                 float* __restrict__ grads, float* __restrict__ loss) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool bad = *reinterpret_cast<const volatile int*>(err) != 0;
   if (e < n_params) {
     float g = 0.f;
     for (int i = 0; i < n_items; ++i) g += partials[(size_t)i * n_params + e];
-    grads[e] = g;
+    grads[e] = bad ? __int_as_float(0x7fc00000) : g;
   }
   if (e == 0) {
     double s = 0.0;
     for (int i = 0; i < n_items; ++i) s += loss_part[2 * i];
-    *loss = (float)s;
+    *loss = bad ? __int_as_float(0x7fc00000) : (float)s;
   }
 }
 
@@ -179,28 +193,55 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
     d.pack[d.n_pack++] = {nd.off[k], nd.imf[k], nd.w[k - 1], nd.w[k], nd.wp[k - 1], nd.wp[k], 1};
     d.pack[d.n_pack++] = {nd.off[k], nd.imb[k], nd.w[k - 1], nd.w[k], nd.wp[k - 1], nd.wp[k], 0};
   }
-  int wmax = MT;
-  for (int k = 1; k < L; ++k) wmax = std::max(wmax, nd.wp[k]);
   sd.n_params = off;
   sd.w_res = w_res;
   sd.n_res = (int)n;
   sd.inv_n_res = n ? 1.f / (float)n : 0.f;
   // (u, u_x, u_t, u_xx) for Burgers, Laplacian jets (u, u_x, u_y, lap u) otherwise
-  const int K = 4;
   const int D = nd.w[L];
-  int P = std::min(256, (NT / (wmax / MT)) * 2);
-  P = std::min(P, std::max(4, 2048 / (D * K)));
-  P = std::max(4, P / 4 * 4);
-  int64_t rows = 0;
-  for (int k = 1; k < L; ++k) rows += nd.wp[k];
-  const int64_t per_cta = (rows + D) * K * P;
+  Item proto;
+  memset(&proto, 0, sizeof proto);
+  proto.kind = IT_RES;
+  proto.edge = -1;
+  proto.K[0] = 4;
+  proto.lap = pde == XPINN_PDE_BURGERS ? 0 : 1;
 
-  int n_sm = 0;
-  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+  int n_sm = 0, optin = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
     cudaGetLastError();
     return fail(XPINN_ERR_CUDA, "cudaDeviceGetAttribute failed");
   }
-  // items of whole sub-tiles; as many CTAs as fit the array
+  // the dynamic limit plus the kernel's static shared memory must stay within
+  // the opt-in maximum; 1 KB is left for the static part, as handles do
+  const size_t limit = optin > 1024 ? (size_t)optin - 1024 : 0;
+  // Sub-tile size and shared memory as the handle's planner sizes them
+  // (choose_P, item_needs): the largest P the register tiles occupy, lowered
+  // in steps of 4 (down to 8) while the shared memory does not fit.
+  StepArgs a;
+  memset(&a, 0, sizeof a);
+  a.pt = 2;
+  a.nt = NT;
+  a.gen = net_is_general(nd) ? 1 : 0;
+  Limits lim;
+  size_t smem = 0;
+  for (int cap = 256;; cap -= 4) {
+    proto.P = choose_P(sd, proto.K, cap, a.pt, a.nt);
+    lim = Limits{};
+    item_needs(sd, proto, lim);
+    a.szA = round_up4(lim.szA);
+    a.szW = round_up4(lim.szW);
+    a.szU = round_up4(lim.szU);
+    a.pmax = round_up4(lim.pmax);
+    smem = jet_step_smem_bytes(a);
+    if (smem <= limit || cap <= 8) break;
+  }
+  if (smem > limit) return fail(XPINN_ERR_UNSUPPORTED, "network too wide for shared memory");
+  const int P = proto.P;
+  const int64_t per_cta = round_up4((int)lim.scratch);
+
+  // items of whole sub-tiles, one per CTA, at most one CTA per SM; fewer
+  // when the working set does not fit the array
   const int64_t tiles = (n + P - 1) / P;
   int n_items = (int)std::min<int64_t>(std::min<int64_t>(NA_MAX_ITEMS, tiles), (int64_t)n_sm);
   int grid = n_items;
@@ -221,20 +262,13 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   d.n_items = 0;
   for (int64_t s0 = 0; s0 < n; s0 += per_item) {
     Item& it = d.items[d.n_items];
-    it.kind = IT_RES;
-    it.q = 0;
-    it.edge = -1;
+    it = proto;
     it.pt_off = s0;
     it.n_pts = (int)std::min<int64_t>(per_item, n - s0);
-    it.P = P;
-    it.K[0] = K;
-    it.lap = pde == XPINN_PDE_BURGERS ? 0 : 1;
     it.part_off = (int64_t)d.n_items * sd.n_params;
     ++d.n_items;
   }
 
-  StepArgs a;
-  memset(&a, 0, sizeof a);
   a.items = reinterpret_cast<const Item*>(base + lay.items);
   a.n_items = d.n_items;
   a.item_base = 0;
@@ -253,40 +287,33 @@ extern "C" int xpinn_residual_grad_noalloc(int32_t pde, float nu, float re, cons
   a.re = re;
   a.n_out_total = D;
   a.n_eq = pde == XPINN_PDE_NS ? 3 : 1;
-  a.szA = wmax * adj_stride(K, P);
-  a.szW = 4;
-  for (int k = 2; k < L; ++k) a.szW = std::max(a.szW, layer_img_floats(nd, k));
-  a.szU = (D * K * P + 3) / 4 * 4;
-  a.pmax = P;
-  a.pt = 2;
-  a.nt = NT;
-  a.gen = net_is_general(nd) ? 1 : 0;
   a.err = reinterpret_cast<int*>(base + lay.err);
-  const size_t smem = jet_step_smem_bytes(a);
-  int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  // the dynamic limit plus the kernel's static shared memory must stay within
-  // the opt-in maximum; 1 KB is left for the static part, as handles do
-  const size_t limit = optin > 1024 ? (size_t)optin - 1024 : 0;
-  if (smem > limit) return fail(XPINN_ERR_UNSUPPORTED, "network too wide for shared memory");
-  // raise the kernel's shared-memory limit to that maximum (never lower it:
-  // handles created earlier rely on the limit they set, which is below it)
+  // raise the kernel's shared-memory limit to the opt-in maximum (never lower
+  // it: handles created earlier rely on the limit they set, which is below it)
   if (jet_step_configure(limit) != cudaSuccess) {
     cudaGetLastError();
     return fail(XPINN_ERR_CUDA, "cudaFuncSetAttribute failed");
   }
 
+  const int err0 = g_preset_err;
+  g_preset_err = 0;
   na_setup_kernel<<<1, 128, 0, s>>>(d, reinterpret_cast<SubDev*>(base + lay.sub),
                                     reinterpret_cast<Item*>(base + lay.items),
                                     reinterpret_cast<int*>(base + lay.counter),
-                                    reinterpret_cast<int*>(base + lay.err),
+                                    reinterpret_cast<int*>(base + lay.err), err0,
                                     reinterpret_cast<PackBlock*>(base + lay.pack));
   launch_pack_weights(params, reinterpret_cast<const PackBlock*>(base + lay.pack), d.n_pack,
                       reinterpret_cast<float*>(base + lay.img), s);
   if (d.n_items) launch_jet_step(a, grid, smem, s);
   na_reduce_kernel<<<(sd.n_params + 255) / 256, 256, 0, s>>>(a.partials, a.loss_part, d.n_items,
-                                                              sd.n_params, grads, loss);
+                                                              sd.n_params, a.err, grads, loss);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(XPINN_ERR_CUDA, cudaGetErrorString(e));
+  return XPINN_OK;
+}
+
+extern "C" int xpinn_noalloc_debug_preset_error(int32_t code) {
+  g_preset_err = code;
+  set_last_error("");
   return XPINN_OK;
 }

@@ -66,9 +66,24 @@ __global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
       for (int t = 0; t < XPINN_N_TERMS; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
     if (threadIdx.x == 0) {
       const int slot = (*a.loss_slot) % a.ring_cap;
+      bool finite = true;
 #pragma unroll
-      for (int t = 0; t < XPINN_N_TERMS; ++t)
-        a.loss_ring[((int64_t)slot * a.n_sub + q) * XPINN_N_TERMS + t] = (float)acc[t];
+      for (int t = 0; t < XPINN_N_TERMS; ++t) {
+        const float l = (float)acc[t];
+        a.loss_ring[((int64_t)slot * a.n_sub + q) * XPINN_N_TERMS + t] = l;
+        finite = finite && isfinite(l);
+      }
+      // sticky until the host reads it at the next synchronising call
+      if (!finite && a.err) atomicCAS(a.err, 0, XPINN_ERR_NONFINITE);
+      // J(Theta_q) = W_u MSE_u (each net) + W_F MSE_F + W_I MSE_uavg + W_flux|W_IF MSE_flux|MSE_R
+      // (Eqs. cPINNLoss, XPINNLoss), from the same float terms that are reported
+      if (a.jq) {
+        const float w[XPINN_N_TERMS] = {sd.w_data[0], sd.w_data[1], sd.w_res, sd.w_avg, sd.w_iface};
+        double j = 0.0;
+#pragma unroll
+        for (int t = 0; t < XPINN_N_TERMS; ++t) j += (double)w[t] * (double)(float)acc[t];
+        a.jq[q] = (float)j;
+      }
     }
   }
   // the slice offsets of this subdomain's items, once per block
@@ -110,6 +125,20 @@ __global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
 
 void launch_reduce_adam(const ReduceArgs& a, cudaStream_t s) {
   if (a.n_blocks > 0) reduce_adam_kernel<<<a.n_blocks, RT, 0, s>>>(a);
+}
+
+// J(Theta) = sum_q J(Theta_q): lane l sums subdomains l, l + 32, ... in
+// order, the lanes' sums are combined by a fixed butterfly.
+__global__ void objective_sum_kernel(const float* __restrict__ jq, int n_sub, float* __restrict__ out) {
+  double s = 0.0;
+  for (int q = threadIdx.x; q < n_sub; q += 32) s += (double)jq[q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) *out = (float)s;
+}
+
+void launch_objective_sum(const float* jq, int n_sub, float* out, cudaStream_t s) {
+  objective_sum_kernel<<<1, 32, 0, s>>>(jq, n_sub, out);
 }
 
 // Weight images (layout in xpinn_dev.cuh): one CTA per image; consecutive

@@ -113,6 +113,18 @@ inline int fill_net_dev(NetDev& nd, const xpinn_net_desc& n, int off) {
   return off;
 }
 
+// ---------------------------------------------------------------------------
+// Tile sizing shared by every planner of jet-kernel launches (the handle's
+// step and evaluation plans and the allocation-free entry point), so that the
+// shared memory and scratch a launch is given always match what the kernel
+// addresses.
+// ---------------------------------------------------------------------------
+inline int max_hidden_wp(const NetDev& n) {
+  int w = MT;
+  for (int k = 1; k < n.L; ++k) w = w > n.wp[k] ? w : n.wp[k];
+  return w;
+}
+
 struct SubDev {
   int n_nets;
   int n_params;
@@ -195,6 +207,60 @@ struct StepArgs {
   int* err;                  // device error flag (bounds checks)
 };
 
+// Points per sub-tile for an item evaluating the nets with K[n] > 0: enough
+// (neuron group, point group) register tiles to occupy the CTA's nt threads
+// at pt points per thread, at most 256 and `cap`, a multiple of 4 (>= 4).
+inline int choose_P(const SubDev& sd, const int K[2], int cap, int pt, int nt) {
+  int ng = 1, dk = 0;
+  for (int n = 0; n < sd.n_nets; ++n)
+    if (K[n]) {
+      const int g = max_hidden_wp(sd.net[n]) / MT;
+      ng = ng > g ? ng : g;
+      dk += sd.net[n].w[sd.net[n].L] * K[n];
+    }
+  int P = (nt / ng) * pt;
+  P = P < 256 ? P : 256;
+  const int pd = 2048 / (dk > 1 ? dk : 1);
+  P = P < (pd > 4 ? pd : 4) ? P : (pd > 4 ? pd : 4);
+  P = P < cap ? P : cap;
+  P = P / 4 * 4;
+  return P > 4 ? P : 4;
+}
+
+// Shared-memory regions (floats) and per-CTA scratch (floats) a set of items
+// needs; item_needs raises them to cover one item.
+struct Limits {
+  int szA = 4, szW = 4, szU = 4, pmax = 4;
+  int64_t scratch = 4;
+};
+
+inline void item_needs(const SubDev& sd, const Item& it, Limits& l) {
+  int u = 0;
+  int64_t sc = 0;
+  for (int n = 0; n < sd.n_nets; ++n) {
+    const int K = it.K[n];
+    if (!K) continue;
+    const NetDev& nd = sd.net[n];
+    int rows = 0;
+    for (int k = 1; k < nd.L; ++k) {
+      rows += nd.wp[k];
+      const int a = nd.wp[k] * adj_stride(K, it.P);
+      l.szA = l.szA > a ? l.szA : a;
+    }
+    for (int k = 2; k < nd.L; ++k) {
+      const int w = layer_img_floats(nd, k);
+      l.szW = l.szW > w ? l.szW : w;
+    }
+    u += nd.w[nd.L] * K * it.P;
+    sc += (int64_t)(rows + nd.w[nd.L]) * K * it.P;
+  }
+  l.szU = l.szU > u ? l.szU : u;
+  l.scratch = l.scratch > sc ? l.scratch : sc;
+  l.pmax = l.pmax > it.P ? l.pmax : it.P;
+}
+
+inline int round_up4(int x) { return (x + 3) / 4 * 4; }
+
 // Kernel entry points (defined in jet_step.cu / reduce_adam.cu / route.cu).
 void launch_jet_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
 size_t jet_step_smem_bytes(const StepArgs& a);
@@ -222,9 +288,14 @@ struct ReduceArgs {
   int do_adam;
   float beta1, beta2, eps;
   int n_sub;
+  int* err;                  // device status word: XPINN_ERR_NONFINITE is set here when a
+                             // loss term is NaN or infinite (an earlier code is kept)
+  float* jq;                 // [n_sub] J(Theta_q), the weighted loss of each subdomain, or NULL
 };
 
 void launch_reduce_adam(const ReduceArgs& a, cudaStream_t s);
+// out[0] = sum_q jq[q] in a fixed order (one warp, double accumulation)
+void launch_objective_sum(const float* jq, int n_sub, float* out, cudaStream_t s);
 
 // One weight image to build from the packed parameters.
 struct PackBlock {

@@ -119,6 +119,9 @@ def load() -> C.CDLL:
         "xpinn_server_destroy": (C.c_int, [vp]),
         "xpinn_residual_grad_noalloc": (C.c_int, [i32, C.c_float, C.c_float, C.POINTER(NetDesc), fp, fp, fp,
                                                   i64, C.c_float, fp, fp, vp]),
+        "xpinn_noalloc_debug_preset_error": (C.c_int, [i32]),
+        "xpinn_sync": (C.c_int, [vp, vp]),
+        "xpinn_objective": (C.c_int, [vp, fp, fp, fp, fp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -252,6 +255,19 @@ class Solver:
         _check(self.lib.xpinn_grad(self.h, lp, gp, _stream(grads)))
         return losses, grads
 
+    def objective(self, J=None, J_sub=None, losses=None, grads=None):
+        """The method's objective J = sum_q J(Theta_q) (Eqs. cPINNLoss /
+        XPINNLoss, weighted in the library) and its gradient: returns
+        (J [1], J_sub [n_sub], losses [n_sub, 5], grads [n_params]).  Buffers
+        may be numpy arrays or CUDA tensors (all on the same side)."""
+        J = np.empty(1, np.float32) if J is None else J
+        J_sub = np.empty(self.n_sub, np.float32) if J_sub is None else J_sub
+        losses = np.empty((self.n_sub, N_TERMS), np.float32) if losses is None else losses
+        grads = np.empty(self.n_params, np.float32) if grads is None else grads
+        ptrs = [_ptr(x)[0] for x in (J, J_sub, losses, grads)]
+        _check(self.lib.xpinn_objective(self.h, *ptrs, _stream(grads)))
+        return J, J_sub, losses, grads
+
     def step(self, n_steps=1, losses=True, stream=None):
         """Run n_steps training steps; returns losses [n_steps, n_sub, 5] (or None)."""
         if losses is True:
@@ -260,6 +276,12 @@ class Solver:
         st = stream if stream is not None else _stream(losses if hasattr(losses, "is_cuda") else None)
         _check(self.lib.xpinn_step(self.h, n_steps, lp, st))
         return losses if lp is not None else None
+
+    def sync(self, stream=None):
+        """Wait for the work queued on `stream` (a cudaStream_t handle or None)
+        and raise XpinnError if a device error (a wait that gave up, a
+        non-finite loss) was recorded by an earlier asynchronous call."""
+        _check(self.lib.xpinn_sync(self.h, stream))
 
     def set_residual_points(self, xy, f=None):
         xp_, k1 = _ptr(xy if hasattr(xy, "data_ptr") else _f32(xy))

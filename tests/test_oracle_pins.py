@@ -225,7 +225,18 @@ def test_jets_match_central_differences(out_act):
 def test_gradient_matches_central_differences(pde, method):
     """dJ(Theta_q)/dTheta_q with neighbours held constant, against central FD
     of J_q alone (the neighbours' values do not depend on Theta_q)."""
-    pb = _tiny_problem(pde, method)
+    _check_gradient_by_central_differences(_tiny_problem(pde, method))
+
+
+def test_gradient_matches_central_differences_literal_burgers_flux():
+    """The same check with the literal Burgers flux u u_x - nu u_x on the
+    cPINN interfaces (the form the Burgers cPINN configuration names)."""
+    pb = _tiny_problem(P.PDE_BURGERS, P.CPINN)
+    pb.flux_mode = P.FLUX_LITERAL
+    _check_gradient_by_central_differences(pb)
+
+
+def _check_gradient_by_central_differences(pb):
     orc = Oracle(pb)
     theta = pb.packed_params().astype(np.float64)
     W = orc.weights()
@@ -302,6 +313,44 @@ def test_constant_networks_interface_terms_closed_form():
     assert np.isclose(terms[1, 3], avg(c[1], c[0]) + avg(c[1], c[2]), rtol=1e-13)
     assert np.isclose(terms[1, 4], flux(c[1], c[0]) + flux(c[1], c[2]), rtol=1e-13)
     assert np.isclose(terms[2, 4], flux(c[2], c[1]), rtol=1e-13)
+
+
+def test_literal_burgers_flux_closed_form_on_one_neuron_networks():
+    """Literal cPINN flux of the Burgers configuration, f = (u u_x - nu u_x, u)
+    in (x, t), on one-neuron networks u = w2 tanh(a x + c t + b1) + b2 whose
+    u_x = w2 a (1 - tanh^2) is written out by hand: MSE_flux of each side is
+    the mean over the interface points of (f_q . n - f_q+ . n)^2, with a
+    normal that has both components so that both parts of f are exercised.
+    A dropped u u_x or nu u_x term, a wrong sign, or the conservative u^2/2
+    in its place fails it."""
+    pb = _tiny_problem(P.PDE_BURGERS, P.CPINN, n_sub=2, widths=[2, 1, 1])
+    pb.flux_mode = P.FLUX_LITERAL
+    normal = (0.6, 0.8)
+    pb.ifaces[0].normal = normal
+    prm = [(0.7, -0.4, 0.2, 1.3, -0.5), (-1.1, 0.9, -0.3, 0.6, 0.25)]   # a, c, b1, w2, b2
+    for s, (a, c, b1, w2, b2) in zip(pb.subs, prm):
+        s.params = [[(np.array([[a, c]], np.float32), np.array([b1], np.float32)),
+                     (np.array([[w2]], np.float32), np.array([b2], np.float32))]]
+    terms = Oracle(pb).loss_terms(torch.tensor(pb.packed_params().astype(np.float64))).detach().numpy()
+    nu = np.float64(np.float32(pb.nu))
+    n0, n1 = (np.float64(np.float32(v)) for v in normal)
+    xy = pb.ifaces[0].xy.astype(np.float64)
+
+    def f_dot_n(a, c, b1, w2, b2):
+        a, c, b1, w2, b2 = (np.float64(np.float32(v)) for v in (a, c, b1, w2, b2))
+        t = np.tanh(a * xy[:, 0] + c * xy[:, 1] + b1)
+        u = w2 * t + b2
+        ux = w2 * a * (1 - t * t)
+        return n0 * (u * ux - nu * ux) + n1 * u
+
+    f0, f1 = f_dot_n(*prm[0]), f_dot_n(*prm[1])
+    want = np.mean((f0 - f1) ** 2)
+    assert np.isclose(terms[0, 4], want, rtol=1e-12, atol=0)
+    assert np.isclose(terms[1, 4], want, rtol=1e-12, atol=0)
+    # the conservative form differs on the same networks
+    pb.flux_mode = P.FLUX_CONSERVATIVE
+    t2 = Oracle(pb).loss_terms(torch.tensor(pb.packed_params().astype(np.float64))).detach().numpy()
+    assert not np.isclose(t2[0, 4], want, rtol=1e-3)
 
 
 # ---------------------------------------------------------------- Adam

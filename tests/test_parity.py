@@ -102,9 +102,22 @@ WORKLOADS = {
     "c4_diffusion_xpinn_small": small_c4,
     "burgers_spacetime_xpinn_4x2": lambda: P.burgers_spacetime(4, 2, n_res_total=6000),
     "burgers_cpinn_x_xpinn_t_4x4": lambda: P.burgers_spacetime(4, 4, n_res_total=6000, method_x=P.CPINN),
+    # the Burgers cPINN configuration with the flux it names literally, u u_x - nu u_x
+    "c1_burgers_cpinn_literal_flux": lambda: P.burgers_cpinn(flux_mode=P.FLUX_LITERAL),
 }
 TINY = {f"tiny_pde{p}_m{m}": (lambda p=p, m=m: tiny_problem(p, m, n_sub=3, n_res=37, n_data=11, n_if=9))
         for p, m in CASES}
+
+
+def _tiny_literal():
+    pb = tiny_problem(P.PDE_BURGERS, P.CPINN, n_sub=3, n_res=37, n_data=11, n_if=9)
+    pb.flux_mode = P.FLUX_LITERAL
+    for it in pb.ifaces:                 # both components of f . n exercised
+        it.normal = (0.6, 0.8)
+    return pb
+
+
+TINY["tiny_pde0_m0_literal_flux"] = _tiny_literal
 
 
 @pytest.mark.parametrize("name", list(WORKLOADS) + list(TINY))
@@ -139,7 +152,7 @@ def test_jets_parity(X, name):
     s.close()
 
 
-@pytest.mark.parametrize("name", list(WORKLOADS) + ["tiny_pde3_m1", "tiny_pde2_m1"])
+@pytest.mark.parametrize("name", list(WORKLOADS) + ["tiny_pde3_m1", "tiny_pde2_m1", "tiny_pde0_m0_literal_flux"])
 def test_interface_exchange_parity(X, name):
     pb = {**WORKLOADS, **TINY}[name]()
     s = X.Solver(pb)
