@@ -6,13 +6,24 @@ exchange, jets (value, first and second input derivatives) through every
 subdomain's network at its residual, data and interface points, PDE residual
 and interface terms, reverse pass, fixed-order gradient reduction and Adam.
 
-Default workload: 16-subdomain XPINN Poisson on the unit square (uneven 4x4
-grid, per-subdomain depth 4-6 and width 20-80, 2k-20k residual points each,
-seed 0).  Inputs are ~2 MB, far below L2, so L2 is flushed (a 256 MB write)
-before every timed step and each step is timed alone with CUDA events on the
-launching stream.
+Headline workload (the largest single-GPU configuration): XPINN inverse
+diffusion on a seeded star polygon, 10 Voronoi regions x 256 independent
+copies (2,560 subdomains, two networks each: u 2->40x5->1 and K 2->20x4->1
+softplus, tanh/sin/cos with trained slopes), 30k residual points per region:
+76.8 M residual points and 20.7 M parameters per step.  Its inputs (0.9 GB of
+points and forcing, 0.3 GB of parameters and Adam moments) exceed L2; L2 is
+also flushed (a 256 MB write) before every timed step, and each step is timed
+alone with CUDA events on the launching stream.
+
+The same JSON line carries, as extra keys: the per-subdomain launch loop of
+the same kernels on the headline workload; the XPINN Poisson (16 uneven
+subdomains) and Kovasznay cPINN (64 x 50k points) workloads, grouped and
+looped; the Burgers cPINN configuration's Adam steps per second; the serving
+mix (query and training-step requests, p50/p99 latency); the FP64 oracle on
+the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--workload c4|c2|c3|c1|...]
 
 With N > 1 (torchrun) every rank trains its own replica (replicas only: the
 path has no cross-GPU exchange); value = all ranks' residual points / the
@@ -33,12 +44,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "residual pts/s (jet fwd+bwd) grouped vs per-subdomain loop; query p50/p99 ms"
 
-# DRAM traffic of the jet kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, one launch of the default workload; see profiles/).
-# Reported only while the kernel source and the launch's items per CTA (the
-# number of gradient slices it writes) are the ones that were measured.
-TRAFFIC = {"jet_step.cuh sha256[:16]": "c1ceacddba609484", "workload": "c2", "items_per_cta": 8,
-           "bytes_per_launch": 5888384 + 269417856}
+# DRAM traffic of the jet kernel, per workload, from one ncu capture each
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch; see profiles/).
+# A key is reported only while the kernel source and the launch options are
+# the ones that were measured.  Where the full launch is too large to capture,
+# a reduced copy of the workload was captured and its traffic is scaled to the
+# full launch by residual points ("scaled_from"): the traffic is the saved
+# jets and the gradient slices, both in proportion to the points processed.
+TRAFFIC = {}
 FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 partitions x 32)
 
 
@@ -59,9 +72,15 @@ def workload(name):
         return P.burgers_spacetime(4, 2), ("XPINN space-time Burgers, 4 x 2 subdomains, 2->20x5->1, 80k residual pts "
                                            "in total, 20 pts per interface (Table TableVB)")
     if name == "c4":
-        return P.diffusion_xpinn(), ("XPINN inverse diffusion on a star polygon, 10 Voronoi regions x 256 copies, "
-                                     "u: 2->40x5->1, K: 2->20x4->1 softplus, 30k residual pts per region, "
-                                     "adaptive tanh/sin/cos per region (Table Table_USmap)")
+        return P.diffusion_xpinn(), ("XPINN inverse diffusion div(K grad u) = f on a seeded star polygon, "
+                                     "10 Voronoi regions x 256 independent copies (2,560 subdomains), "
+                                     "u: 2->40x5->1 and K: 2->20x4->1 softplus per region, hidden activation "
+                                     "tanh/sin/cos by region with trained slopes (Table Table_USmap), "
+                                     "30k residual pts and 500 noisy u observations per region")
+    if name == "c4s":
+        return P.diffusion_xpinn(n_copies=16), ("the inverse-diffusion workload reduced for counter captures: "
+                                                "16 copies of the 10 regions (160 subdomains), same networks "
+                                                "and per-region points")
     if name == "c2a":
         import dataclasses
         pb = P.poisson_xpinn()
@@ -150,19 +169,19 @@ def time_steps(torch, s, stream, flush, steps):
     return step_ms, jet_ms
 
 
-def serving(X, solver_c2, n_req, max_query, seed=0):
+def serving(X, n_req, max_query, seed=0):
     """Continuous-batching server over three trained models (Burgers cPINN,
-    the benchmark's Poisson XPINN, Kovasznay cPINN with 2k points per
-    subdomain): Poisson arrivals at 70% of the closed-loop capacity, a mix of
-    evaluation queries (log-uniform 1..max_query points, derivative order
-    0-2) and training-step requests (one step of a whole model)."""
+    XPINN Poisson, Kovasznay cPINN with 2k points per subdomain): Poisson
+    arrivals at 70% of the closed-loop capacity, a mix of evaluation queries
+    (log-uniform 1..max_query points, derivative order 0-2) and training-step
+    requests (one step of a whole model)."""
     from paper_2104_10013_gb300 import problems as P
     rng = np.random.default_rng(seed)
-    pbs = [P.burgers_cpinn(), None, P.kovasznay_cpinn(n_res=2000)]
-    models = [X.Solver(pbs[0]), solver_c2, X.Solver(pbs[2])]
-    pbs[1] = solver_c2.pb
-    for m in (models[0], models[2]):
+    pbs = [P.burgers_cpinn(), P.poisson_xpinn(), P.kovasznay_cpinn(n_res=2000)]
+    models = [X.Solver(pb) for pb in pbs]
+    for m in models:
         m.step(20, losses=None)                       # "trained" models
+        m.sync()
     boxes = [(pb.meta["xcuts"][0], pb.meta["xcuts"][-1], pb.meta["ycuts"][0], pb.meta["ycuts"][-1])
              for pb in pbs]
 
@@ -202,8 +221,11 @@ def serving(X, solver_c2, n_req, max_query, seed=0):
     res = [(r, srv.wait(t)) for r, t in tickets]
     wall = time.perf_counter() - t_start
     srv.close()
-    for m in (models[0], models[2]):
+    for m in models:
         m.close()
+    bad = [x for _, x in res if x["status"] != 0]
+    if bad:
+        raise RuntimeError(f"serving: {len(bad)} requests failed, first: {bad[0]['error']}")
     lat = np.array([x["latency_ms"] for _, x in res])
     ev = np.array([x["latency_ms"] for r, x in res if r[0] == "eval"])
     stp = np.array([x["latency_ms"] for r, x in res if r[0] == "step"])
@@ -236,21 +258,25 @@ def cpu_baseline(pb, seconds):
         pts += pb.subs[q].res_xy.shape[0]
         qs.append(q)
         q = (q + 1) % pb.n_sub
-    # the same oracle on one core, for a short sample (the smallest subdomain)
+    # the same oracle on one core, for a short sample (the smallest subdomain,
+    # when it is small enough to finish in seconds on one core)
     n_thr = torch.get_num_threads()
     q1 = int(np.argmin([sd.res_xy.shape[0] for sd in pb.subs]))
-    torch.set_num_threads(1)
-    try:
-        t0 = time.perf_counter()
-        orc.grad(theta, subset=[q1])
-        t1 = time.perf_counter() - t0
-    finally:
-        torch.set_num_threads(n_thr)
+    one = None
+    if pb.subs[q1].res_xy.shape[0] <= 5000:
+        torch.set_num_threads(1)
+        try:
+            t0 = time.perf_counter()
+            orc.grad(theta, subset=[q1])
+            t1 = time.perf_counter() - t0
+        finally:
+            torch.set_num_threads(n_thr)
+        one = {"value": pb.subs[q1].res_xy.shape[0] / t1, "unit": "pts/s",
+               "sample": f"subdomain {q1}, {pb.subs[q1].res_xy.shape[0]} residual points, one thread"}
     return {"value": pts / t_tot, "unit": "pts/s", "cores": n_thr, "kind": "oracle",
             "sample": f"FP64 oracle gradients of {len(qs)} whole subdomains of the same workload, taken in "
                       f"turn (q = 0, 1, ...), {pts} residual points in {t_tot:.1f} s",
-            "one_core": {"value": pb.subs[q1].res_xy.shape[0] / t1, "unit": "pts/s",
-                         "sample": f"subdomain {q1}, {pb.subs[q1].res_xy.shape[0]} residual points, one thread"}}
+            "one_core": one}
 
 
 def whole_job(total_ms, world, n_res, steps, dist=None, device="cpu"):
@@ -300,17 +326,121 @@ def run_reference(args):
         "wall_s": time.perf_counter() - t_start}))
 
 
+def tuned_solver(X, pb, autotune, opts=None):
+    """A Solver with profile_phases on (the phase timer gives the jet
+    kernel's device time) and, unless disabled, autotuned tile options."""
+    s = X.Solver(pb)
+    s.set_options(profile_phases=1, **(opts or {}))
+    tune = None
+    if autotune:
+        t0 = time.perf_counter()
+        tune = s.autotune(steps=3)
+        tune["seconds"] = time.perf_counter() - t0
+        s.set_options(profile_phases=1)
+    return s, tune
+
+
+def roofline(pb, jet_ms, n_sm, name, s):
+    """Achieved algorithmic FP32 FLOP/s of the jet kernel against the derived
+    FFMA peak, with the ncu traffic of the same launch when it was captured."""
+    import hashlib
+    flops = algorithmic_flops(pb)
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (jet_ms / 1e3) / 1e12
+    src = os.path.join(ROOT, "paper_2104_10013_gb300", "csrc", "jet_step.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    t = TRAFFIC.get(name)
+    opts = s.options()
+    traffic = None
+    if t and t["sha"] == sha and all(opts.get(k) == v for k, v in t["options"].items()):
+        traffic = t["bytes_per_launch"]
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "xp::jet_step_kernel (exchange, residual, data and interface items)",
+            "kernel_ms": jet_ms, "flop_per_launch": flops,
+            "flop_per_point": "6 K M per residual point of every network (K jet components: 4 for the "
+                              "u-network (Laplacian jets) and Burgers, 3 for the K-network; M = sum over "
+                              "layers k >= 2 of N_k N_{k-1})",
+            "peak_note": f"FP32 FFMA peak derived: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x "
+                         f"{sm_max:.0f} MHz (max SM clock in MEASURED_PEAKS.json)"}
+
+
+def loop_compare(torch, s, stream, flush, steps, ipcs, n_res, grouped_ms):
+    """The per-subdomain launch loop (schedule 1) of the same kernels on the
+    same handle, at its own best items-per-CTA; the grouped options are
+    restored afterwards."""
+    grouped_opts = s.options()
+    best = None
+    for ipc in ipcs:
+        s.set_options(schedule=1, items_per_cta=ipc)
+        s.step(1, losses=None, stream=stream.cuda_stream)
+        lms, _ = time_steps(torch, s, stream, flush, steps)
+        if best is None or np.sum(lms) < np.sum(best[1]):
+            best = (ipc, lms)
+    s.sync(stream.cuda_stream)
+    ipc, lms = best
+    lval = n_res * len(lms) / (np.sum(lms) / 1e3)
+    s.set_options(**grouped_opts)
+    return {"value": lval, "unit": "pts/s", "ms_per_step": float(np.mean(lms)), "items_per_cta": ipc,
+            "steps": len(lms), "grouped_speedup": lval and (n_res / (grouped_ms / 1e3)) / lval}
+
+
+def extra_workload(torch, X, name, stream, flush, steps, loop_steps, n_sm):
+    """Grouped step (autotuned) and per-subdomain loop of one more workload."""
+    pb, desc = workload(name)
+    s, tune = tuned_solver(X, pb, True)
+    for _ in range(3):
+        s.step(1, losses=None, stream=stream.cuda_stream)
+    step_ms, jet_ms = time_steps(torch, s, stream, flush, steps)
+    s.sync(stream.cuda_stream)
+    ms = float(np.mean(step_ms))
+    out = {"workload": desc, "value": pb.n_res / (ms / 1e3), "unit": "pts/s", "ms_per_step": ms,
+           "steps": steps, "residual_pts_per_step": pb.n_res, "options": s.options(),
+           "roofline": roofline(pb, float(np.mean(jet_ms)), n_sm, name, s)}
+    if loop_steps:
+        out["loop"] = loop_compare(torch, s, stream, flush, loop_steps, (4, 16, 64), pb.n_res, ms)
+    s.close()
+    return out
+
+
+def adam_steps_per_s(torch, X, stream, n=320):
+    """Adam steps per second of the Burgers cPINN configuration (4 x 1000
+    residual points, launch-bound): n training steps back to back in one
+    call (replayed from a graph of 16 steps), timed with CUDA events; the
+    problem stays in L2 as it does in a training run."""
+    pb, desc = workload("c1")
+    s = X.Solver(pb)
+    s.set_options(profile_phases=0)
+    s.step(64, losses=None, stream=stream.cuda_stream)
+    s.sync(stream.cuda_stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(n, losses=None, stream=stream.cuda_stream)
+    e1.record(stream)
+    e1.synchronize()
+    s.sync(stream.cuda_stream)
+    ms = e0.elapsed_time(e1)
+    s.close()
+    return {"workload": desc, "value": n / (ms / 1e3), "unit": "Adam steps/s", "steps": n,
+            "ms_per_step": ms / n, "residual_pts_per_s": pb.n_res * n / (ms / 1e3),
+            "note": "steps back to back in one xpinn_step call, graphs of 16 steps; L2 not flushed"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--workload", default="c4")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-loop", action="store_true")
+    ap.add_argument("--loop-steps", type=int, default=0, help="timed loop steps (0: 2 for c4, else --steps)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads and Adam steps/s")
     ap.add_argument("--pt", type=int, default=0, help="points per thread in the register tile (0: library default)")
     ap.add_argument("--items-per-cta", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: library default)")
@@ -339,28 +469,24 @@ def main():
         dist.barrier()
     from paper_2104_10013_gb300 import xpinn as X
     X.load()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
 
     pb, desc = workload(args.workload)
     n_res = pb.n_res
-    s = X.Solver(pb)
-    opts = {"profile_phases": 1}
+    opts = {}
     if args.pt:
         opts["points_per_thread"] = args.pt
     if args.items_per_cta:
         opts["items_per_cta"] = args.items_per_cta
     if args.threads:
         opts["threads_per_cta"] = args.threads
-    s.set_options(**opts)
-    tune = None
-    if not args.no_autotune and not args.pt and not args.items_per_cta and not args.threads:
-        t0 = time.perf_counter()
-        tune = s.autotune(steps=5)
-        tune["seconds"] = time.perf_counter() - t0
-        s.set_options(profile_phases=1)
+    autotune = not args.no_autotune and not opts
+    s, tune = tuned_solver(X, pb, autotune, opts)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         s.step(1, losses=None, stream=stream.cuda_stream)
+    s.sync(stream.cuda_stream)
     torch.cuda.synchronize()
 
     # ---- timed region: K grouped steps
@@ -377,37 +503,20 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
+    s.sync(stream.cuda_stream)      # raises if a device wait gave up or a loss became non-finite
     value, ms_step = whole_job(float(np.sum(step_ms)), world, n_res, args.steps, dist, "cuda")
     # our kernels per step: step_begin, pack_weights (when some network has a
     # hidden-to-hidden layer), the jet kernel, reduce_adam
     launches_per_step = 3 + int(any(len(n.widths) > 3 for sd in pb.subs for n in sd.nets))
-
-    # ---- roofline of the dominant kernel (the jet kernel over all items)
-    flops = algorithmic_flops(pb)
-    jet_avg = float(np.mean(jet_ms))
-    peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = flops / (jet_avg / 1e3) / 1e12
-    import hashlib
-    src = os.path.join(ROOT, "paper_2104_10013_gb300", "csrc", "jet_step.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    traffic = (TRAFFIC["bytes_per_launch"]
-               if sha == TRAFFIC["jet_step.cuh sha256[:16]"] and args.workload == TRAFFIC["workload"]
-               and s.options()["items_per_cta"] == TRAFFIC["items_per_cta"] else None)
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "xp::jet_step_kernel (residual, data and interface items)",
-            "kernel_ms": jet_avg, "kernel_share_of_step": jet_avg / ms_step,
-            "flop_per_launch": flops,
-            "peak_note": f"FP32 FFMA peak derived: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x "
-                         f"{sm_max:.0f} MHz (max SM clock)"}
+    roof = roofline(pb, float(np.mean(jet_ms)), n_sm, args.workload, s)
+    roof["kernel_share_of_step"] = roof["kernel_ms"] / ms_step
 
     out = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": desc, "n_sub": pb.n_sub, "residual_pts_per_step": n_res,
-                      "params": pb.n_params, "l2": "flushed (256 MB write) before every timed step",
+                      "params": pb.n_params,
+                      "l2": "inputs larger than L2, and L2 flushed (256 MB write) before every timed step",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                       "options": s.options(), "autotune": tune},
            "adam_steps_per_s": 1e3 / ms_step, "roofline": roof, "gpu_launches": launches_per_step * args.steps,
@@ -417,47 +526,45 @@ def main():
     # cut at its own best granularity (more items per subdomain fill more
     # CTAs of each per-subdomain launch), not the grouped schedule's.
     if not args.no_loop:
-        grouped_opts = s.options()
-        best = None
-        for ipc in (4, 16, 64):
-            s.set_options(schedule=1, items_per_cta=ipc)
-            for _ in range(3):
-                s.step(1, losses=None, stream=stream.cuda_stream)
-            lms, ljet = time_steps(torch, s, stream, flush, args.steps)
-            if best is None or np.sum(lms) < np.sum(best[1]):
-                best = (ipc, lms)
-        ipc, lms = best
-        lval = n_res * args.steps / (np.sum(lms) / 1e3)
-        out["loop"] = {"value": lval, "unit": "pts/s", "ms_per_step": float(np.mean(lms)),
-                       "items_per_cta": ipc,
-                       "grouped_speedup": (n_res * args.steps / (np.sum(step_ms) / 1e3)) / lval}
-        s.set_options(**grouped_opts)
+        big = n_res > 10_000_000
+        lsteps = args.loop_steps or (2 if big else args.steps)
+        out["loop"] = loop_compare(torch, s, stream, flush, lsteps, (64,) if big else (4, 16, 64), n_res, ms_step)
 
     # ---- end to end through the public API with host buffers
     if not args.no_e2e:
         xy = torch.from_numpy(np.concatenate([sd.res_xy for sd in pb.subs])).pin_memory()
         f = torch.from_numpy(np.concatenate([sd.res_f for sd in pb.subs])).pin_memory()
         losses = torch.empty((1, pb.n_sub, 5), dtype=torch.float32).pin_memory()
-        for _ in range(3):
+        e_steps = max(3, min(args.steps, 10)) if n_res > 10_000_000 else args.steps
+        for _ in range(2):
             s.set_residual_points(xy, f)
             s.step(1, losses=losses)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e_steps):
             s.set_residual_points(xy, f)
             s.step(1, losses=losses)
         e2e_s = time.perf_counter() - t0
-        out["e2e"] = {"value": n_res * args.steps / e2e_s * world, "unit": "pts/s",
+        out["e2e"] = {"value": n_res * e_steps / e2e_s * world, "unit": "pts/s", "steps": e_steps,
                       "h2d_bytes_per_step": int(xy.numel() * 4 + f.numel() * 4),
                       "d2h_bytes_per_step": int(losses.numel() * 4),
-                      "ms_per_step": 1e3 * e2e_s / args.steps}
+                      "ms_per_step": 1e3 * e2e_s / e_steps,
+                      "path": "xpinn_set_residual_points (pinned host points and forcing) + xpinn_step with "
+                              "host losses, wall clock"}
+    s.close()
 
-    if not args.no_serving and args.workload == "c2":
-        out["serving"] = serving(X, s, args.serving_requests, args.serving_max_query)
+    if not args.no_extras and world == 1 and args.workload == "c4":
+        out["workloads"] = {
+            "c2": extra_workload(torch, X, "c2", stream, flush, args.steps, 0 if args.no_loop else args.steps, n_sm),
+            "c3": extra_workload(torch, X, "c3", stream, flush, 5, 0 if args.no_loop else 3, n_sm),
+        }
+        out["adam_steps"] = adam_steps_per_s(torch, X, stream)
+
+    if not args.no_serving:
+        out["serving"] = serving(X, args.serving_requests, args.serving_max_query)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(pb, args.cpu_seconds)
-    s.close()
     if rank == 0:
         print(json.dumps(out))
     if dist:

@@ -258,7 +258,10 @@ typedef struct {
   int32_t schedule;        /* 0 grouped (one launch per phase for all subdomains),
                               1 per-subdomain loop (the same kernels launched once
                               per subdomain per phase: the baseline) */
-  int32_t use_graph;       /* 1: replay steps from a captured CUDA graph */
+  int32_t use_graph;       /* 1: replay steps from captured CUDA graphs: one
+                              graph of 16 steps for every run of 16 steps of a
+                              call (without profile_phases), one of a single
+                              step for the rest */
   int32_t items_per_cta;   /* work items per CTA the scheduler aims for (>= 1) */
   int32_t points_per_thread; /* points in a thread's register tile: 2 (default,
                               one CTA per SM) or 1 (two CTAs per SM) */

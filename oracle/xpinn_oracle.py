@@ -199,18 +199,26 @@ def route_voronoi(sites, polygon, xy) -> list:
     """Irregular regions (Sec. 7.6): a point inside the polygon (even-odd
     rule) belongs to the Voronoi cell of its nearest site; the sites at exactly
     the same float32 distance ((dx*dx) + (dy*dy), each operation rounded to
-    float32) share it.  Points outside the polygon belong to no region."""
-    poly = np.asarray(polygon, dtype=np.float64)
+    float32) share it.  Points outside the polygon belong to no region.  The
+    even-odd test decides in float32 too, with the crossing abscissa of an
+    edge rounded as ax + ((y - ay) * (bx - ax)) / (by - ay), operation by
+    operation: points on or within rounding of an edge are an integer decision
+    taken in the precision of the data, the same on every implementation."""
+    f32 = np.float32
+    poly = np.asarray(polygon, dtype=np.float32)
     xy = np.asarray(xy)
     out = []
     s32 = np.asarray(sites, dtype=np.float32)
     for z in xy:
-        x, y = float(z[0]), float(z[1])
+        x, y = f32(z[0]), f32(z[1])
         inside = False
         for e in range(len(poly)):
             (ax, ay), (bx, by) = poly[e], poly[(e + 1) % len(poly)]
-            if (ay > y) != (by > y) and x < ax + (y - ay) * (bx - ax) / (by - ay):
-                inside = not inside
+            if (ay > y) != (by > y):
+                t = f32(f32(y - ay) * f32(bx - ax))
+                xc = f32(ax + f32(t / f32(by - ay)))
+                if x < xc:
+                    inside = not inside
         if not inside:
             out.append([])
             continue

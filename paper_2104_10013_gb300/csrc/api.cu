@@ -183,13 +183,15 @@ struct xpinn_ctx {
   int device = 0;
   cudaEvent_t ev[5] = {};
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;        // one training step
+  cudaGraphExec_t graph_multi = nullptr;  // GRAPH_STEPS training steps back to back
   int n_counters = 0;
   int p_cap = 256;
   DevBuf<int> e_counter;
 
   ~xpinn_ctx() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (graph_multi) cudaGraphExecDestroy(graph_multi);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
@@ -488,6 +490,10 @@ void size_and_upload_plan(xpinn_ctx* h) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
   }
+  if (h->graph_multi) {
+    cudaGraphExecDestroy(h->graph_multi);
+    h->graph_multi = nullptr;
+  }
 }
 
 void plan(xpinn_ctx* h) {
@@ -544,6 +550,8 @@ void mark(xpinn_ctx* h, int i, cudaStream_t s) {
 void pack_images(xpinn_ctx* h, cudaStream_t s) {
   launch_pack_weights(h->params.p, h->pack_d.p, (int)h->pack_h.size(), h->wimg.p, s);
 }
+
+constexpr int GRAPH_STEPS = 16;   // steps captured in the multi-step graph
 
 void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads) {
   const Plan& pl = h->plan;
@@ -1004,33 +1012,39 @@ int xpinn_step(xpinn_handle h, int32_t n_steps, float* losses, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const size_t row = (size_t)h->n_sub * XPINN_N_TERMS;
   const bool dev_out = losses && is_device_ptr(losses);
-  std::vector<float> host_rows;
   int done = 0;
   while (done < n_steps) {
     const int chunk = std::min(n_steps - done, h->ring_cap);
     const int first_slot = h->host_slot + 1;
-    for (int i = 0; i < chunk; ++i) {
+    for (int i = 0; i < chunk;) {
+      // runs of GRAPH_STEPS steps replay one graph that holds them all (a
+      // launch-bound problem then pays the graph launch once per run); with
+      // profile_phases the phase events must mark one step, so steps replay
+      // one at a time
+      const int g = (h->opt.use_graph && !h->opt.profile_phases && chunk - i >= GRAPH_STEPS) ? GRAPH_STEPS : 1;
       if (h->opt.use_graph) {
-        if (!h->graph) {
+        cudaGraphExec_t& ge = g > 1 ? h->graph_multi : h->graph;
+        if (!ge) {
           if (!h->cap_stream) ck(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "stream");
-          cudaGraph_t g;
+          cudaGraph_t gr;
           ck(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
           try {
-            enqueue_step(h, h->cap_stream, true, nullptr);
+            for (int k = 0; k < g; ++k) enqueue_step(h, h->cap_stream, true, nullptr);
           } catch (...) {
-            cudaStreamEndCapture(h->cap_stream, &g);
+            cudaStreamEndCapture(h->cap_stream, &gr);
             throw;
           }
-          ck(cudaStreamEndCapture(h->cap_stream, &g), "end capture");
-          ck(cudaGraphInstantiate(&h->graph, g, 0), "instantiate");
-          cudaGraphDestroy(g);
+          ck(cudaStreamEndCapture(h->cap_stream, &gr), "end capture");
+          ck(cudaGraphInstantiate(&ge, gr, 0), "instantiate");
+          cudaGraphDestroy(gr);
         }
-        ck(cudaGraphLaunch(h->graph, s), "graph launch");
+        ck(cudaGraphLaunch(ge, s), "graph launch");
       } else {
         enqueue_step(h, s, true, nullptr);
       }
-      h->host_slot += 1;
-      h->host_t += 1;
+      h->host_slot += g;
+      h->host_t += g;
+      i += g;
     }
     if (losses) {
       for (int i = 0; i < chunk; ++i) {

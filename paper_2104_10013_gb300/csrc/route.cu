@@ -11,13 +11,18 @@ namespace xp {
 constexpr int RTT = 256;
 constexpr int MAXS = 4;   // a point of a box decomposition lies in at most 4 boxes
 
-// Even-odd rule: is z inside the polygon poly[0..m)?
+// Even-odd rule: is z inside the polygon poly[0..m)?  The crossing abscissa
+// of every edge is rounded in float32 in a fixed order,
+// xc = a.x + ((z.y - a.y) * (b.x - a.x)) / (b.y - a.y), each operation
+// rounded to nearest (no fused multiply-add), so that a point on or next to
+// an edge is classified the same way by every implementation of that order.
 __device__ __forceinline__ bool in_polygon(float2 z, const float2* __restrict__ poly, int m) {
   bool in = false;
   for (int e = 0; e < m; ++e) {
     const float2 a = poly[e], b = poly[e + 1 == m ? 0 : e + 1];
     if ((a.y > z.y) != (b.y > z.y)) {
-      const float xc = a.x + (z.y - a.y) * (b.x - a.x) / (b.y - a.y);
+      const float t = __fmul_rn(__fsub_rn(z.y, a.y), __fsub_rn(b.x, a.x));
+      const float xc = __fadd_rn(a.x, __fdiv_rn(t, __fsub_rn(b.y, a.y)));
       if (z.x < xc) in = !in;
     }
   }

@@ -389,6 +389,18 @@ def test_stitched_solution_averages_on_interfaces():
     assert [len(m) for m in memb] == [1, 2, 1, 2, 4, 2, 1, 2, 1, 0]
 
 
+def test_voronoi_routing_polygon_membership_by_hand():
+    """The even-odd rule on an L-shaped (non-convex) polygon with one site:
+    points inside the L route to the site, points in the notch or outside the
+    bounding box route nowhere (membership read off the drawing)."""
+    from oracle import route_voronoi
+    L = [(0, 0), (2, 0), (2, 1), (1, 1), (1, 2), (0, 2)]
+    pts = np.array([[0.5, 0.5], [1.5, 0.5], [0.5, 1.5], [1.5, 1.5], [2.5, 0.5], [-0.1, 1.0], [0.5, 2.1]],
+                   np.float32)
+    got = route_voronoi([(0.5, 0.5)], L, pts)
+    assert got == [[0], [0], [0], [], [], [], []]
+
+
 def test_voronoi_routing_on_symmetric_sites():
     """Sites at (-1, 0), (1, 0), (0, 2) in a square: a point on the y axis
     below the third site's cell is equidistant (exactly, in float32) from the

@@ -232,6 +232,21 @@ def test_checkpoint_resume_is_bitwise(X):
     a.close(); c.close()
 
 
+def test_multi_step_graph_is_bitwise_equal_to_single_steps(X):
+    """40 steps in one call replay the 16-step graph twice and the one-step
+    graph 8 times; the same 40 steps without graphs, one launch sequence per
+    step, give the same parameters and loss rows bit for bit."""
+    pb = P.burgers_cpinn(n_res=400)
+    a = X.Solver(pb)
+    la = a.step(40)
+    b = X.Solver(pb)
+    b.set_options(use_graph=0)
+    lb = np.concatenate([b.step(1) for _ in range(40)])
+    assert np.array_equal(la, lb)
+    assert np.array_equal(a.get_params(), b.get_params())
+    a.close(); b.close()
+
+
 def test_training_trajectory_follows_the_oracle(X):
     """100 Adam steps of the full Burgers cPINN problem: the loss curve stays
     within 1e-3 relative of the FP64 trajectory (float32 drift only)."""
@@ -345,6 +360,37 @@ def test_stitched_eval_on_voronoi_regions(X, order):
         ref = Oracle(pb).eval_stitched(pb.packed_params(), model, xy, (1, 3, 5)[order])
         assert np.isnan(got[-2:]).all() and np.isnan(ref[-2:]).all()
         assert_scaled(got[:-2], ref[:-2], RTOL_JET, f"voronoi eval model {model}", axis=(0, 1))
+    s.close()
+
+
+def test_voronoi_routing_on_and_next_to_polygon_edges(X):
+    """Points exactly on the polygon's edges (rounded to float32) and one ulp
+    to either side in x and y: the GPU router and the oracle classify every one
+    the same way (inside: routed and evaluated; outside: NaN), since both take
+    the even-odd decision in float32 in the same operation order."""
+    pb = small_c4()
+    poly = np.asarray(pb.polygon, np.float32)
+    rng = np.random.default_rng(11)
+    on = []
+    for e in range(len(poly)):
+        a, b = poly[e], poly[(e + 1) % len(poly)]
+        for t in rng.random(12):
+            on.append(a + np.float32(t) * (b - a))
+    on = np.asarray(on, np.float32)
+    pts = [on]
+    for axis in (0, 1):
+        for direction in (np.inf, -np.inf):
+            q = on.copy()
+            q[:, axis] = np.nextafter(q[:, axis], np.float32(direction))
+            pts.append(q)
+    xy = np.concatenate(pts + [poly]).astype(np.float32)     # and the vertices themselves
+    s = X.Solver(pb)
+    got = s.eval(0, xy, 0)
+    ref = Oracle(pb).eval_stitched(pb.packed_params(), 0, xy, 1)
+    gn, rn = np.isnan(got[:, 0, 0]), np.isnan(ref[:, 0, 0])
+    assert np.array_equal(gn, rn), np.nonzero(gn != rn)[0][:10]
+    assert 0 < gn.sum() < len(xy)          # both outcomes occur
+    assert_scaled(got[~gn], ref[~rn], RTOL_JET, "edge points", axis=(0, 1))
     s.close()
 
 
