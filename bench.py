@@ -169,12 +169,14 @@ def time_steps(torch, s, stream, flush, steps):
     return step_ms, jet_ms
 
 
-def serving(X, n_req, max_query, seed=0):
+def serving(X, n_req, max_query, seed=0, budget=8 << 30):
     """Continuous-batching server over three trained models (Burgers cPINN,
-    XPINN Poisson, Kovasznay cPINN with 2k points per subdomain): Poisson
-    arrivals at 70% of the closed-loop capacity, a mix of evaluation queries
-    (log-uniform 1..max_query points, derivative order 0-2) and training-step
-    requests (one step of a whole model)."""
+    XPINN Poisson, Kovasznay cPINN with 2k points per subdomain) under a
+    Poisson-arrival mix: 80% evaluation queries (log-uniform 1..max_query
+    points, derivative order 0-2, routed on the device) and 20% training
+    requests on a private fork of 1-64 subdomains (at most the model's) with
+    1k-50k residual points each.  Arrivals at 70% of the closed-loop capacity;
+    latency = submit -> completion; results are drained as they complete."""
     from paper_2104_10013_gb300 import problems as P
     rng = np.random.default_rng(seed)
     pbs = [P.burgers_cpinn(), P.poisson_xpinn(), P.kovasznay_cpinn(n_res=2000)]
@@ -182,24 +184,42 @@ def serving(X, n_req, max_query, seed=0):
     for m in models:
         m.step(20, losses=None)                       # "trained" models
         m.sync()
-    boxes = [(pb.meta["xcuts"][0], pb.meta["xcuts"][-1], pb.meta["ycuts"][0], pb.meta["ycuts"][-1])
-             for pb in pbs]
+    # point pools: requests take slices (no per-request generation)
+    pool = []
+    for pb in pbs:
+        x0, x1, y0, y1 = pb.meta["xcuts"][0], pb.meta["xcuts"][-1], pb.meta["ycuts"][0], pb.meta["ycuts"][-1]
+        pool.append(np.stack([rng.uniform(x0, x1, max_query), rng.uniform(y0, y1, max_query)], 1).astype(np.float32))
+    sub_pool = []
+    for pb in pbs:
+        per = []
+        for sd in pb.subs:
+            x0, x1, y0, y1 = sd.rect
+            per.append(np.stack([rng.uniform(x0, x1, 50000), rng.uniform(y0, y1, 50000)], 1).astype(np.float32))
+        sub_pool.append(per)
 
     def make():
         m = int(rng.integers(0, 3))
         if rng.random() < 0.2:
-            return ("step", m, None, None, pbs[m].n_res)
+            k = int(rng.integers(1, min(64, pbs[m].n_sub) + 1))
+            sel = sorted(rng.choice(pbs[m].n_sub, k, replace=False).tolist())
+            xy = []
+            for q in sel:
+                n = int(rng.integers(1000, 50001))
+                o = int(rng.integers(0, 50000 - n + 1))
+                xy.append(sub_pool[m][q][o:o + n])
+            return ("fork", m, sel, xy, sum(len(a) for a in xy))
         n = int(10 ** rng.uniform(0, np.log10(max_query)))
-        x0, x1, y0, y1 = boxes[m]
-        xy = np.stack([rng.uniform(x0, x1, n), rng.uniform(y0, y1, n)], 1).astype(np.float32)
-        return ("eval", m, xy, int(rng.integers(0, 3)), n)
+        o = int(rng.integers(0, max_query - n + 1))
+        return ("eval", m, pool[m][o:o + n], int(rng.integers(0, 3)), n)
 
     def submit(srv, r):
-        return srv.submit_step(r[1], 1) if r[0] == "step" else srv.submit_eval(r[1], r[2], r[3])
+        if r[0] == "fork":
+            return srv.submit_fork(r[1], r[2], r[3], None, 1)
+        return srv.submit_eval(r[1], r[2], r[3])
 
-    srv = X.Server(models, hbm_budget=4 << 30)
+    srv = X.Server(models, hbm_budget=budget)
     # closed-loop capacity: keep 8 requests in flight
-    cap_reqs = [make() for _ in range(max(40, n_req // 5))]
+    cap_reqs = [make() for _ in range(max(40, n_req // 10))]
     t0 = time.perf_counter()
     inflight, k = [], 0
     while k < len(cap_reqs) or inflight:
@@ -208,38 +228,53 @@ def serving(X, n_req, max_query, seed=0):
         srv.wait(inflight.pop(0))
     cap = len(cap_reqs) / (time.perf_counter() - t0)
     lam = 0.7 * cap
-    reqs = [make() for _ in range(n_req)]
     gaps = rng.exponential(1.0 / lam, n_req)
-    tickets = []
+    pending = {}                  # ticket -> (kind, points)
+    res = []
+
+    def drain():
+        for t in list(pending):
+            r = srv.poll(t)
+            if r is not None:
+                kind, pts = pending.pop(t)
+                res.append((kind, pts, r["status"], r["latency_ms"], r["batch"], r["tick_requests"], r["error"]))
+
     t_start = time.perf_counter()
     t_next = t_start
-    for r, g in zip(reqs, gaps):
+    for g in gaps:
+        r = make()
         t_next += g
         while time.perf_counter() < t_next:
-            time.sleep(min(1e-4, max(0.0, t_next - time.perf_counter())))
-        tickets.append((r, submit(srv, r)))
-    res = [(r, srv.wait(t)) for r, t in tickets]
+            drain()
+            time.sleep(min(2e-4, max(0.0, t_next - time.perf_counter())))
+        pending[submit(srv, r)] = (r[0], r[4])
+    while pending:
+        drain()
+        time.sleep(1e-4)
     wall = time.perf_counter() - t_start
     srv.close()
     for m in models:
         m.close()
-    bad = [x for _, x in res if x["status"] != 0]
+    bad = [x for x in res if x[2] != 0]
     if bad:
-        raise RuntimeError(f"serving: {len(bad)} requests failed, first: {bad[0]['error']}")
-    lat = np.array([x["latency_ms"] for _, x in res])
-    ev = np.array([x["latency_ms"] for r, x in res if r[0] == "eval"])
-    stp = np.array([x["latency_ms"] for r, x in res if r[0] == "step"])
-    pts = sum(r[4] for r, _ in res)
+        raise RuntimeError(f"serving: {len(bad)} requests failed, first: {bad[0][6]}")
+    lat = np.array([x[3] for x in res])
+    ev = np.array([x[3] for x in res if x[0] == "eval"])
+    fk = np.array([x[3] for x in res if x[0] == "fork"])
+    pts = sum(x[1] for x in res)
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "eval_p50_ms": float(np.percentile(ev, 50)), "eval_p99_ms": float(np.percentile(ev, 99)),
-            "step_p50_ms": float(np.percentile(stp, 50)) if len(stp) else None,
-            "step_p99_ms": float(np.percentile(stp, 99)) if len(stp) else None,
-            "sustained_pts_per_s": pts / wall, "requests": n_req,
-            "arrival_rate_per_s": lam, "capacity_req_per_s": cap,
-            "max_batch": int(max(x["batch"] for _, x in res)),
+            "step_p50_ms": float(np.percentile(fk, 50)) if len(fk) else None,
+            "step_p99_ms": float(np.percentile(fk, 99)) if len(fk) else None,
+            "sustained_pts_per_s": pts / wall, "requests": n_req, "evals": int(len(ev)), "steps": int(len(fk)),
+            "wall_s": wall, "arrival_rate_per_s": lam, "capacity_req_per_s": cap,
+            "max_batch": int(max(x[4] for x in res)), "max_tick_requests": int(max(x[5] for x in res)),
+            "mean_tick_requests": float(np.mean([x[5] for x in res])),
+            "device_pool_bytes": budget,
             "mix": f"80% evaluation queries (log-uniform 1..{max_query} pts, order 0-2), 20% one-step "
-                   "training requests, over Burgers cPINN / Poisson XPINN / Kovasznay cPINN models; "
-                   "Poisson arrivals at 70% of closed-loop capacity"}
+                   "training requests on a private fork of 1-64 subdomains x 1k-50k residual pts, over "
+                   "Burgers cPINN / Poisson XPINN / Kovasznay cPINN models; Poisson arrivals at 70% of "
+                   "closed-loop capacity; points/s counts evaluated and trained points"}
 
 
 def cpu_baseline(pb, seconds):
@@ -446,8 +481,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: library default)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=400)
-    ap.add_argument("--serving-max-query", type=int, default=100000)
+    ap.add_argument("--serving-requests", type=int, default=10000)
+    ap.add_argument("--serving-max-query", type=int, default=1000000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

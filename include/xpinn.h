@@ -240,12 +240,60 @@ int xpinn_net_jets(xpinn_handle h, int32_t q, int32_t net, const float* xy, int6
 int xpinn_eval(xpinn_handle h, int32_t model, const float* xy, int64_t n, int32_t order,
                float* out, void* stream);
 
+/* xpinn_eval with caller-provided device workspace, for callers that keep a
+ * memory pool (the request server): the routing, its prefix sums, the work
+ * items and the stitching all run on the device from slices of `workspace`
+ * (256-byte aligned, ws_bytes >= xpinn_eval_workspace_size), so the call
+ * allocates nothing and, with device xy and out, does not synchronise (a
+ * device error is then reported by the next synchronising call on the
+ * handle, see xpinn_sync).  With host xy and out the points are staged in
+ * the workspace and the call returns after the result has been copied.
+ * xpinn_eval itself runs this path on a workspace the handle keeps.  The
+ * size covers the worst case of a point shared by four subdomains. */
+int xpinn_eval_workspace_size(xpinn_handle h, int32_t model, int64_t n, int32_t order, size_t* bytes);
+int xpinn_eval_ws(xpinn_handle h, int32_t model, const float* xy, int64_t n, int32_t order, float* out,
+                  void* workspace, size_t ws_bytes, void* stream);
+
 /* Replace the residual points (and forcing) of every subdomain, keeping the
  * per-subdomain counts: xy [n_res_total][2], f [n_res_total] or NULL (f = 0),
  * subdomain by subdomain in order.  Host or device pointers.  Used to
  * resample residual points between steps. */
 int xpinn_set_residual_points(xpinn_handle h, const float* xy, const float* f, int64_t n,
                               void* stream);
+
+/* Training on a private fork (the request server's training-step requests):
+ * n_steps steps of Algorithm 1 for the n_sel subdomains sel[] only, each with
+ * the request's own residual points (n_pts[i] points for sel[i], given
+ * subdomain by subdomain in xy [sum n_pts][2] with forcing f [sum n_pts], or
+ * f NULL for f = 0) in place of its residual set; its data points and its
+ * interfaces are the handle's.  The selected subdomains start from the
+ * handle's current parameters, Adam moments and step count, on copies in
+ * `workspace`; subdomains outside the selection that share an interface
+ * with it provide their interface values from the handle's current
+ * parameters (held constant, Algorithm 1) and are not trained.  The handle's
+ * parameters and Adam state are not changed: the fork is independent of the
+ * handle's own training and of other requests.
+ *   losses [n_steps][n_sel][XPINN_N_TERMS] (or NULL): each step's loss terms
+ *     of the selected subdomains, measured before that step's update;
+ *   params (or NULL): the fork's parameters after the steps, the selected
+ *     subdomains' blocks packed in the order of sel[].
+ * workspace: device memory of at least xpinn_fork_workspace_size bytes,
+ * 256-byte aligned; the call allocates nothing.  xy and f may be host or
+ * device pointers, losses and params too; with device outputs the call does
+ * not wait for the GPU (device errors: see xpinn_sync).  Errors: INVALID (a
+ * subdomain out of range or repeated, a negative count, a small workspace). */
+typedef struct {
+  int32_t n_sel;
+  const int32_t* sel;     /* [n_sel] distinct subdomain ids (host) */
+  const int64_t* n_pts;   /* [n_sel] residual points of each (host) */
+  const float* xy;        /* [sum n_pts][2] */
+  const float* f;         /* [sum n_pts] or NULL */
+  int32_t n_steps;
+} xpinn_fork_desc;
+
+int xpinn_fork_workspace_size(xpinn_handle h, const xpinn_fork_desc* d, size_t* bytes);
+int xpinn_fork_step(xpinn_handle h, const xpinn_fork_desc* d, void* workspace, size_t ws_bytes, float* losses,
+                    float* params, void* stream);
 
 /* Checkpoint: the parameters, Adam moments m and v and the step count as one
  * versioned blob in host memory.  get_state with blob == NULL stores the
@@ -305,54 +353,76 @@ int xpinn_phase_times(xpinn_handle h, float* ms);
 int xpinn_iface_values(xpinn_handle h, float* out, int64_t* n_floats, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Serving: continuous batching of evaluation and training-step requests over
- * several models (handles).  A dispatcher admits requests in arrival order
- * while the device memory of the admitted requests fits `hbm_budget` bytes;
- * each model has a worker thread and a CUDA stream, so the work of different
- * models overlaps on the GPU.  A worker takes every admitted request of its
- * model that is waiting: consecutive evaluation requests with the same copy
- * and derivative order are stitched (Eq. FSol) in one routed launch, step
- * requests run xpinn_step on the model in arrival order.  Each point's value
- * does not depend on the other points of a batch, so a request's result is
- * the same alone and in a mix (bitwise).  All request buffers are host
- * memory, owned by the caller until the request completes.
+ * Serving: continuous batching of evaluation and training requests over
+ * several models (handles on one device).  At creation the server allocates
+ * its two memory pools once: hbm_budget bytes of device memory and a staging
+ * pool of page-locked host memory (hbm_budget, at most 1 GiB).  A scheduler
+ * thread forms ticks: it admits submitted requests in arrival order while
+ * each one's footprint (its device workspace and device copies of its inputs
+ * and outputs; its staged host inputs and outputs) fits the free part of
+ * both pools, so no request allocates and admission is by the memory the
+ * request really holds.  In a tick:
+ *   - the evaluation queries of one model, copy and derivative order are
+ *     stitched (Eq. FSol) in one routed evaluation planned on the device
+ *     (xpinn_eval_ws): one grouped launch over all their points;
+ *   - XPINN_REQ_FORK requests train a subdomain subset on their own residual
+ *     points on a private fork of the model (xpinn_fork_step): the model is
+ *     not changed;
+ *   - XPINN_REQ_STEP requests run xpinn_step on the model in place (on its
+ *     resident buffers; only their loss rows count against the pools), in
+ *     arrival order with that model's other requests.
+ * The work of a model is queued on one CUDA stream, different models on
+ * different streams, and a tick is queued while earlier ticks still run, so
+ * work of different requests overlaps on the GPU.  A point's value does not
+ * depend on the other points of a batch, and a fork depends only on its
+ * request and the model, so a result is the same alone and in a mix
+ * (bitwise).  All request buffers are host memory, owned by the caller until
+ * the request completes.
  * ------------------------------------------------------------------------- */
-enum { XPINN_REQ_EVAL = 0, XPINN_REQ_STEP = 1 };
+enum { XPINN_REQ_EVAL = 0, XPINN_REQ_STEP = 1, XPINN_REQ_FORK = 2 };
 enum { XPINN_PENDING = 1 };   /* xpinn_server_poll: not finished yet */
 
 typedef struct {
-  int32_t kind;       /* XPINN_REQ_EVAL or XPINN_REQ_STEP */
+  int32_t kind;       /* XPINN_REQ_EVAL, XPINN_REQ_STEP or XPINN_REQ_FORK */
   int32_t model;      /* index into the server's models */
   int32_t copy;       /* EVAL: copy (model) inside the handle, as xpinn_eval */
   int32_t order;      /* EVAL: derivative order 0..2 */
   int64_t n;          /* EVAL: points */
-  const float* xy;    /* EVAL: [n][2] host */
-  float* out;         /* EVAL: [n][D_out_total][K] host, as xpinn_eval */
-  int32_t n_steps;    /* STEP: training steps */
-  float* losses;      /* STEP: [n_steps][n_sub][5] host, or NULL */
+  const float* xy;    /* EVAL: [n][2]; FORK: [sum n_pts][2] residual points */
+  float* out;         /* EVAL: [n][D_out_total][K], as xpinn_eval */
+  int32_t n_steps;    /* STEP, FORK: training steps */
+  float* losses;      /* STEP: [n_steps][n_sub][5]; FORK: [n_steps][n_sel][5]; or NULL */
+  int32_t n_sel;      /* FORK: subdomains to train (see xpinn_fork_step) */
+  const int32_t* sel; /* FORK: [n_sel] */
+  const int64_t* n_pts; /* FORK: [n_sel] residual points of each */
+  const float* f;     /* FORK: [sum n_pts] forcing, or NULL */
+  float* params;      /* FORK: the fork's parameters of sel after the steps, or NULL */
 } xpinn_request;
 
 typedef struct {
   int32_t status;     /* xpinn_status of the request */
-  double queue_ms;    /* submit -> admitted */
+  double queue_ms;    /* submit -> admitted into a tick */
   double latency_ms;  /* submit -> completed */
-  int32_t batch;      /* number of requests served in the same launch */
+  int32_t batch;      /* requests served in the same launch (stitched evaluations) */
   char error[160];    /* message when status != XPINN_OK */
+  int32_t tick_requests;  /* requests admitted in the same tick */
 } xpinn_result;
 
 typedef struct xpinn_server xpinn_server;
 
-/* models: handles that outlive the server (not owned).  hbm_budget: bytes of
- * request buffers (points, routing entries, outputs) allowed in flight. */
+/* models: handles that outlive the server (not owned), all on one device.
+ * hbm_budget: bytes of the device pool (>= 4096).  Errors: INVALID,
+ * UNSUPPORTED (models on different devices), OOM (the pools). */
 int xpinn_server_create(const xpinn_handle* models, int32_t n_models, size_t hbm_budget,
                         xpinn_server** out);
 /* Non-blocking.  *ticket identifies the request.  XPINN_ERR_OOM if the
- * request alone exceeds hbm_budget (it could never be admitted). */
+ * request alone exceeds a pool (it could never be admitted), INVALID for a
+ * malformed request. */
 int xpinn_server_submit(xpinn_server* s, const xpinn_request* req, uint64_t* ticket);
 /* XPINN_OK with *res filled once the request is finished (the ticket is then
  * released), XPINN_PENDING before, XPINN_ERR_INVALID for an unknown ticket. */
 int xpinn_server_poll(xpinn_server* s, uint64_t ticket, xpinn_result* res);
-/* Waits for every submitted request, stops the workers, frees the server. */
+/* Waits for every submitted request, stops the scheduler, frees the pools. */
 int xpinn_server_destroy(xpinn_server* s);
 
 /* Residual loss and its gradient for ONE network, allocating no device

@@ -32,6 +32,8 @@ void launch_bucket(const float2* pts, int64_t n, const int* S, const int* memb, 
                    float2* epts, float* escale, cudaStream_t st);
 void launch_gather(int64_t n, int row, const int* S, const int* pos, const float* eout, float* out,
                    cudaStream_t st);
+void launch_eval_plan(const int* counts, int nq, const EvalProto* proto, int q0, int row, int* cursor,
+                      Item* items, int* n_items, int max_items, int* err, cudaStream_t st);
 }  // namespace xp
 
 using namespace xp;
@@ -74,14 +76,22 @@ template <typename T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
+  bool owned = true;   // false: a view into memory someone else owns (a caller's workspace)
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p && owned) cudaFree(p);
     p = nullptr;
     n = 0;
+    owned = true;
+  }
+  void view(void* ptr, size_t count) {
+    release();
+    p = static_cast<T*>(ptr);
+    n = count;
+    owned = false;
   }
   void alloc(size_t count) {
     release();
@@ -146,6 +156,9 @@ struct xpinn_ctx {
   int n_sub = 0, n_iface = 0, spm = 0;
   std::vector<SubDev> subs;
   std::vector<IfaceDev> ifaces;
+  // a fork (xpinn_fork_step) trains only some of its subdomains: the others
+  // only provide their interface values; empty = every subdomain is trained
+  std::vector<char> trained;
   int64_t n_params = 0, n_res_total = 0, n_pts_total = 0, n_if_pts = 0;
   int n_out_total = 0, n_eq = 1, d4_nv = 0;
   // device problem
@@ -168,10 +181,14 @@ struct xpinn_ctx {
   int64_t n_img = 0;
   bool img_stale = true;
   // eval
-  DevBuf<float2> e_pts, e_epts;
-  DevBuf<float> e_out, e_escale, e_eout;
-  DevBuf<int> e_S, e_memb, e_pos, e_counts;
+  DevBuf<float2> e_pts;
+  DevBuf<float> e_out;
   DevBuf<Item> e_items;
+  DevBuf<char> e_ws;             // workspace of xpinn_eval (grown by that call only)
+  // routed evaluation: per subdomain, how its bucket is cut into items, for
+  // derivative orders 0, 1, 2 ([3][n_sub]); rebuilt with the plan
+  DevBuf<EvalProto> e_proto;
+  std::vector<int> e_min_chunk;  // [3][n_models]: smallest chunk of each model and order
   // plan
   Plan plan;
   StepArgs base{};
@@ -201,12 +218,14 @@ struct xpinn_ctx {
   int* loss_slot() { return state_i.p + 1; }
 };
 
-// Read-only facts of a handle for the request server.
+// Facts of a handle for the request server.
 namespace xp {
 int ctx_out_total(xpinn_handle h) { return h->n_out_total; }
 int ctx_n_sub(xpinn_handle h) { return h->n_sub; }
 int ctx_n_copies(xpinn_handle h) { return h->n_sub / h->spm; }
 int ctx_device(xpinn_handle h) { return h->device; }
+int ctx_sub_params(xpinn_handle h, int q) { return h->subs[q].n_params; }
+int* ctx_err_word(xpinn_handle h) { return h->err_d.p; }
 }  // namespace xp
 
 namespace {
@@ -354,6 +373,7 @@ void build_plan(xpinn_ctx* h, int p_cap) {
                  n == 1 ? 1 : 0),
               main_);
   }
+  auto is_trained = [&](int q) { return h->trained.empty() || h->trained[q] != 0; };
   for (int e = 0; e < h->n_iface; ++e) {
     const IfaceDev& f = h->ifaces[e];
     if (!f.n_pts) continue;
@@ -362,7 +382,7 @@ void build_plan(xpinn_ctx* h, int p_cap) {
       const int K0 = k_iface(h->pde, f.method, 0);
       const int K1 = h->subs[q].n_nets > 1 ? k_iface(h->pde, f.method, 1) : 0;
       split(mk(IT_IFACE_FWD, q, e, side, f.pt_off, f.n_pts, K0, K1), fwd);
-      split(mk(IT_IFACE, q, e, side, f.pt_off, f.n_pts, K0, K1), main_);
+      if (is_trained(q)) split(mk(IT_IFACE, q, e, side, f.pt_off, f.n_pts, K0, K1), main_);
     }
   }
   // Grouped: largest first, but items that read the exchange buffer last (in
@@ -410,7 +430,8 @@ void build_plan(xpinn_ctx* h, int p_cap) {
       pl.q_part_off.push_back(pl.items[i].part_off);
     }
     pl.q_item_begin.push_back((int)pl.q_items.size());
-    for (int e0 = 0; e0 < h->subs[q].n_params; e0 += 256) pl.red_blocks.push_back(make_int2(q, e0));
+    if (is_trained(q))
+      for (int e0 = 0; e0 < h->subs[q].n_params; e0 += 256) pl.red_blocks.push_back(make_int2(q, e0));
   }
   // per-subdomain ranges for the loop schedule
   pl.fwd_begin.assign(h->n_sub + 1, 0);
@@ -475,6 +496,27 @@ void size_and_upload_plan(xpinn_ctx* h) {
   h->partials.alloc((size_t)pl.partial_floats);
   h->loss_part.alloc(2 * pl.items.size());
   h->scratch.alloc((size_t)h->grid * a.scratch_per_cta);
+  // item prototypes of routed evaluations (all networks of a subdomain, K = 1, 3, 5)
+  {
+    const int n_models = h->n_sub / h->spm;
+    std::vector<EvalProto> pr(3 * (size_t)h->n_sub);
+    h->e_min_chunk.assign(3 * (size_t)n_models, 1 << 30);
+    for (int o = 0; o < 3; ++o)
+      for (int q = 0; q < h->n_sub; ++q) {
+        const SubDev& sd = h->subs[q];
+        const int K = o == 0 ? 1 : (o == 1 ? 3 : 5);
+        int Ks[2] = {K, sd.n_nets > 1 ? K : 0};
+        EvalProto e;
+        e.K0 = Ks[0];
+        e.K1 = Ks[1];
+        e.P = choose_P(sd, Ks, h->p_cap, h->opt.points_per_thread, cta_threads(h));
+        e.chunk = e.P * 16;
+        pr[(size_t)o * h->n_sub + q] = e;
+        int& mc = h->e_min_chunk[(size_t)o * n_models + q / h->spm];
+        mc = std::min(mc, e.chunk);
+      }
+    h->e_proto.upload(pr.data(), pr.size());
+  }
   h->n_counters = 3 + 2 * h->n_sub;   // [0] main, [1] spare, [2] exchange done, then loop counters
   h->counters.alloc(h->n_counters);
   ck(cudaMemset(h->counters.p, 0, sizeof(int) * h->n_counters), "memset");
@@ -709,6 +751,419 @@ void eval_items_for(xpinn_ctx* h, int q, int net, int K, int64_t first, int64_t 
     it.out_off = out_off + s * dout;
     items.push_back(it);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Routed evaluation (Eq. FSol) from a workspace, planned on the device:
+// route (membership of every point) -> plan (bucket starts by a prefix sum
+// of the counts, items cut from the buckets) -> bucket -> jet kernel (item
+// count read on the device) -> gather (1/S sum per point).  No host round
+// trip; every buffer is a slice of the workspace, sized for the worst case of
+// MAXS = 4 memberships per point (a point at a corner of four boxes).
+// ---------------------------------------------------------------------------
+constexpr int EVAL_MAXS = 4;
+
+struct EvalWs {
+  size_t pts, S, memb, pos, counts, epts, escale, eout, out, items, n_items, total;
+  int max_items;
+};
+
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+EvalWs eval_ws_layout(const xpinn_ctx* h, int model, int64_t n, int order) {
+  const int K = order == 0 ? 1 : (order == 1 ? 3 : 5);
+  const int row = h->n_out_total * K;
+  const int nq = h->spm;
+  const int64_t ne = EVAL_MAXS * std::max<int64_t>(n, 1);
+  const int chunk = h->e_min_chunk[(size_t)order * (h->n_sub / h->spm) + model];
+  EvalWs w{};
+  w.max_items = (int)std::min<int64_t>(nq + (ne + chunk - 1) / chunk, 1 << 30);
+  size_t o = 0;
+  auto take = [&](size_t& field, size_t bytes) { field = o; o = al256(o + bytes); };
+  take(w.pts, sizeof(float2) * std::max<int64_t>(n, 1));
+  take(w.S, sizeof(int) * std::max<int64_t>(n, 1));
+  take(w.memb, sizeof(int) * ne);
+  take(w.pos, sizeof(int) * ne);
+  take(w.counts, sizeof(int) * 2 * nq);
+  take(w.epts, sizeof(float2) * ne);
+  take(w.escale, sizeof(float) * ne);
+  take(w.eout, sizeof(float) * ne * row);
+  take(w.out, sizeof(float) * std::max<int64_t>(n, 1) * row);
+  take(w.items, sizeof(Item) * (size_t)w.max_items);
+  take(w.n_items, sizeof(int));
+  w.total = o;
+  return w;
+}
+
+// Enqueues the routed evaluation of n points (device pointer pts) into out
+// (device pointer, [n][row]); ws must hold eval_ws_layout(...).total bytes.
+void eval_enqueue(xpinn_ctx* h, int model, const float2* pts, int64_t n, int order, float* out, char* ws,
+                  const EvalWs& L, cudaStream_t s) {
+  const int K = order == 0 ? 1 : (order == 1 ? 3 : 5);
+  const int row = h->n_out_total * K;
+  const int q0 = model * h->spm, nq = h->spm;
+  int* S = reinterpret_cast<int*>(ws + L.S);
+  int* memb = reinterpret_cast<int*>(ws + L.memb);
+  int* pos = reinterpret_cast<int*>(ws + L.pos);
+  int* counts = reinterpret_cast<int*>(ws + L.counts);
+  float2* epts = reinterpret_cast<float2*>(ws + L.epts);
+  float* escale = reinterpret_cast<float*>(ws + L.escale);
+  float* eout = reinterpret_cast<float*>(ws + L.eout);
+  Item* items = reinterpret_cast<Item*>(ws + L.items);
+  int* n_items = reinterpret_cast<int*>(ws + L.n_items);
+  ck(cudaMemsetAsync(counts, 0, sizeof(int) * 2 * nq, s), "memset");
+  launch_route(pts, n, h->subs_d.p, q0, nq, S, memb, counts, h->err_d.p, h->poly.p, h->n_poly, s);
+  launch_eval_plan(counts, nq, h->e_proto.p + (size_t)order * h->n_sub + q0, q0, row, counts + nq, items,
+                   n_items, L.max_items, h->err_d.p, s);
+  launch_bucket(pts, n, S, memb, counts + nq, pos, epts, escale, s);
+  if (h->img_stale) {
+    pack_images(h, s);
+    h->img_stale = false;
+  }
+  StepArgs a = h->base;
+  a.items = items;
+  a.n_items = L.max_items;
+  a.n_items_dev = n_items;
+  a.item_base = 0;
+  h->e_counter.ensure(1);
+  a.counter = h->e_counter.p;
+  a.eval_pts = epts;
+  a.eval_out = eout;
+  a.eval_dout = row;
+  a.eval_scale = escale;
+  ck(cudaMemsetAsync(a.counter, 0, sizeof(int), s), "memset");
+  launch_jet_step(a, std::min<int>(h->grid, L.max_items), h->smem, s);
+  launch_gather(n, row, S, pos, eout, out, s);
+  ck(cudaGetLastError(), "evaluation launches");
+}
+
+// The routed evaluation with caller-provided workspace: host or device xy
+// and out (both on the same side); with device pointers nothing synchronises.
+void eval_with_ws(xpinn_handle h, int32_t model, const float* xy, int64_t n, int32_t order, float* out,
+                         char* ws, size_t ws_bytes, cudaStream_t s) {
+  const EvalWs L = eval_ws_layout(h, model, n, order);
+  if (ws_bytes < L.total) fail(XPINN_ERR_INVALID, "workspace of %zu bytes, %zu needed", ws_bytes, L.total);
+  if (reinterpret_cast<uintptr_t>(ws) % 256) fail(XPINN_ERR_INVALID, "workspace must be 256-byte aligned");
+  const int K = order == 0 ? 1 : (order == 1 ? 3 : 5);
+  const int row = h->n_out_total * K;
+  const bool dev_in = is_device_ptr(xy), dev_out = is_device_ptr(out);
+  const float2* pts = reinterpret_cast<const float2*>(xy);
+  if (!dev_in) {
+    ck(cudaMemcpyAsync(ws + L.pts, xy, n * sizeof(float2), cudaMemcpyHostToDevice, s), "copy in");
+    pts = reinterpret_cast<const float2*>(ws + L.pts);
+  }
+  float* o = dev_out ? out : reinterpret_cast<float*>(ws + L.out);
+  eval_enqueue(h, model, pts, n, order, o, ws, L, s);
+  if (!dev_out) {
+    ck(cudaMemcpyAsync(out, o, sizeof(float) * n * row, cudaMemcpyDeviceToHost, s), "copy out");
+    check_device_error(h, s);   // synchronises
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Forks (xpinn_fork_step): a training request on a subset S of a handle's
+// subdomains with its own residual points.  The fork is a second context
+// whose device buffers are views into a caller-provided workspace: the
+// parameters and Adam moments of S (copied from the handle), the parameters of
+// S's interface neighbours N (copied; they only provide interface values and
+// are not trained), S's data points and targets, the interface points, the
+// request's residual points, the plan and the per-item gradient slices.  The
+// handle's own parameters and Adam state are not touched.
+// ---------------------------------------------------------------------------
+struct ForkLayout {
+  size_t subs, ifaces, items, q_items, q_item_begin, q_part_off, red_blocks, pack, params, m, v, wimg, pts,
+      res_f, tgt, d4, partials, loss_part, counters, state, ring, total;
+};
+
+struct Fork {
+  std::unique_ptr<xpinn_ctx> f;
+  std::vector<int> T;                  // fork subdomain -> handle subdomain (S first, then N)
+  int n_sel = 0;
+  int64_t n_params_sel = 0;            // parameters of S: the first floats of the fork's vector
+  std::vector<int64_t> src_poff;       // handle parameter offset of each fork subdomain
+  struct Copy {
+    int64_t dst, src, n;
+  };
+  std::vector<Copy> pt_copies, tgt_copies;   // (data and interface points, targets) from the handle
+  int64_t n_res_req = 0, n_data_pts = 0, n_tgt = 0;
+  ForkLayout L{};
+};
+
+int img_floats_of(const SubDev& sd) {
+  int ioff = 0;
+  for (int n = 0; n < sd.n_nets; ++n) {
+    NetDev nd = sd.net[n];
+    ioff = assign_images(nd, ioff);
+  }
+  return ioff;
+}
+
+std::unique_ptr<Fork> make_fork(xpinn_ctx* h, const xpinn_fork_desc* d) {
+  if (!d || d->n_sel < 1 || d->n_sel > h->n_sub || !d->sel || !d->n_pts || d->n_steps < 0)
+    fail(XPINN_ERR_INVALID, "bad fork request");
+  auto F = std::make_unique<Fork>();
+  std::vector<int> idx(h->n_sub, -1);
+  int64_t n_req = 0;
+  for (int i = 0; i < d->n_sel; ++i) {
+    const int q = d->sel[i];
+    if (q < 0 || q >= h->n_sub || idx[q] >= 0) fail(XPINN_ERR_INVALID, "fork: bad or repeated subdomain %d", q);
+    if (d->n_pts[i] < 0 || d->n_pts[i] > (1 << 30)) fail(XPINN_ERR_INVALID, "fork: bad point count");
+    idx[q] = i;
+    F->T.push_back(q);
+    n_req += d->n_pts[i];
+  }
+  if (n_req > 0 && !d->xy) fail(XPINN_ERR_INVALID, "fork: NULL points");
+  F->n_sel = d->n_sel;
+  F->n_res_req = n_req;
+  // interface neighbours of S outside S, ascending
+  std::vector<int> nb;
+  for (const IfaceDev& e : h->ifaces) {
+    if (idx[e.q] >= 0 && idx[e.qp] < 0) nb.push_back(e.qp);
+    if (idx[e.qp] >= 0 && idx[e.q] < 0) nb.push_back(e.q);
+  }
+  std::sort(nb.begin(), nb.end());
+  nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+  for (int q : nb) {
+    idx[q] = (int)F->T.size();
+    F->T.push_back(q);
+  }
+  auto f = std::make_unique<xpinn_ctx>();
+  f->pde = h->pde;
+  f->flux_mode = h->flux_mode;
+  f->nu = h->nu;
+  f->re = h->re;
+  f->beta1 = h->beta1;
+  f->beta2 = h->beta2;
+  f->eps = h->eps;
+  f->n_sub = (int)F->T.size();
+  f->spm = f->n_sub;
+  f->n_out_total = h->n_out_total;
+  f->n_eq = h->n_eq;
+  f->d4_nv = h->d4_nv;
+  f->opt = h->opt;
+  f->opt.schedule = 0;
+  f->opt.use_graph = 0;
+  f->opt.profile_phases = 0;
+  f->opt.inject_fault = 0;
+  f->grid = h->grid;
+  f->n_sm = h->n_sm;
+  f->device = h->device;
+  f->p_cap = h->p_cap;
+  f->ring_cap = std::max(1, (int)d->n_steps);
+  f->trained.assign(f->n_sub, 0);
+  for (int i = 0; i < d->n_sel; ++i) f->trained[i] = 1;
+  // points: [request residual points][data points of S][interface points]
+  int64_t n_data = 0;
+  for (int i = 0; i < d->n_sel; ++i) {
+    const SubDev& sd = h->subs[F->T[i]];
+    for (int n = 0; n < sd.n_nets; ++n) n_data += sd.n_data[n];
+  }
+  int64_t poff = 0, img = 0, res = 0, dcur = n_req, tcur = 0;
+  for (int i = 0; i < f->n_sub; ++i) {
+    const int q = F->T[i];
+    SubDev sd = h->subs[q];
+    F->src_poff.push_back(sd.poff);
+    sd.poff = poff;
+    poff += sd.n_params;
+    if (i < d->n_sel) F->n_params_sel = poff;
+    sd.img_off = img;
+    img += img_floats_of(sd);
+    if (i < d->n_sel) {
+      sd.n_res = (int)d->n_pts[i];
+      sd.res_off = res;
+      sd.inv_n_res = sd.n_res ? 1.f / (float)sd.n_res : 0.f;
+      res += sd.n_res;
+      for (int n = 0; n < sd.n_nets; ++n) {
+        const SubDev& hs = h->subs[q];
+        const int D = sd.net[n].w[sd.net[n].L];
+        if (!hs.n_data[n]) continue;
+        F->pt_copies.push_back({dcur, hs.data_off[n], hs.n_data[n]});
+        F->tgt_copies.push_back({tcur, hs.tgt_off[n], (int64_t)hs.n_data[n] * D});
+        sd.data_off[n] = dcur;
+        sd.tgt_off[n] = tcur;
+        dcur += hs.n_data[n];
+        tcur += (int64_t)hs.n_data[n] * D;
+      }
+    } else {
+      sd.n_res = 0;
+      sd.inv_n_res = 0.f;
+      sd.res_off = 0;
+      for (int n = 0; n < sd.n_nets; ++n) {
+        sd.n_data[n] = 0;
+        sd.inv_n_data[n] = 0.f;
+      }
+    }
+    f->subs.push_back(sd);
+    for (int n = 0; n < sd.n_nets; ++n) {
+      const NetDev& nd = sd.net[n];
+      for (int k = 2; k < nd.L; ++k) {
+        const int64_t src = sd.poff + nd.off[k];
+        f->pack_h.push_back({src, sd.img_off + nd.imf[k], nd.w[k - 1], nd.w[k], nd.wp[k - 1], nd.wp[k], 1});
+        f->pack_h.push_back({src, sd.img_off + nd.imb[k], nd.w[k - 1], nd.w[k], nd.wp[k - 1], nd.wp[k], 0});
+      }
+    }
+  }
+  F->n_data_pts = n_data;
+  F->n_tgt = tcur;
+  int64_t icur = 0;
+  for (const IfaceDev& e : h->ifaces) {
+    // interfaces with a trained side; the other side is in S or N
+    const bool tq = idx[e.q] >= 0 && idx[e.q] < d->n_sel, tp = idx[e.qp] >= 0 && idx[e.qp] < d->n_sel;
+    if (!tq && !tp) continue;
+    IfaceDev fd = e;
+    fd.q = idx[e.q];
+    fd.qp = idx[e.qp];
+    F->pt_copies.push_back({n_req + n_data + icur, e.pt_off, e.n_pts});
+    fd.pt_off = n_req + n_data + icur;
+    fd.d4_pt = icur;
+    icur += e.n_pts;
+    f->ifaces.push_back(fd);
+  }
+  f->n_iface = (int)f->ifaces.size();
+  f->n_if_pts = icur;
+  f->n_params = poff;
+  f->n_img = img;
+  f->n_res_total = n_req;
+  f->n_pts_total = n_req + n_data + icur;
+  f->n_counters = 3 + 2 * f->n_sub;
+  build_plan(f.get(), h->p_cap);
+  // workspace layout
+  const Plan& pl = f->plan;
+  ForkLayout& L = F->L;
+  size_t o = 0;
+  auto take = [&](size_t& field, size_t bytes) { field = o; o = al256(o + std::max<size_t>(bytes, 4)); };
+  take(L.subs, sizeof(SubDev) * f->subs.size());
+  take(L.ifaces, sizeof(IfaceDev) * f->ifaces.size());
+  take(L.items, sizeof(Item) * pl.items.size());
+  take(L.q_items, sizeof(int) * pl.q_items.size());
+  take(L.q_item_begin, sizeof(int) * pl.q_item_begin.size());
+  take(L.q_part_off, sizeof(int64_t) * pl.q_part_off.size());
+  take(L.red_blocks, sizeof(int2) * pl.red_blocks.size());
+  take(L.pack, sizeof(PackBlock) * f->pack_h.size());
+  take(L.params, sizeof(float) * (size_t)f->n_params);
+  take(L.m, sizeof(float) * (size_t)F->n_params_sel);
+  take(L.v, sizeof(float) * (size_t)F->n_params_sel);
+  take(L.wimg, sizeof(float) * (size_t)std::max<int64_t>(4, f->n_img));
+  take(L.pts, sizeof(float2) * (size_t)f->n_pts_total);
+  take(L.res_f, sizeof(float) * (size_t)n_req);
+  take(L.tgt, sizeof(float) * (size_t)F->n_tgt);
+  take(L.d4, sizeof(float) * (size_t)std::max<int64_t>(1, f->n_if_pts * 2 * f->d4_nv));
+  take(L.partials, sizeof(float) * (size_t)pl.partial_floats);
+  take(L.loss_part, sizeof(double) * 2 * pl.items.size());
+  take(L.counters, sizeof(int) * f->n_counters);
+  take(L.state, sizeof(int) * 2);
+  take(L.ring, sizeof(float) * (size_t)f->ring_cap * f->n_sub * XPINN_N_TERMS);
+  L.total = o;
+  F->f = std::move(f);
+  return F;
+}
+
+// Binds the fork's buffers to the workspace and fills it: tables from the
+// host, parameters, moments, step count, data and interface points from the
+// handle, the request's residual points and forcing from the caller.
+// Bytes of the host tables a fork uploads (see bind_fork's `pinned`).
+size_t fork_table_bytes(const Fork& F) {
+  const xpinn_ctx* f = F.f.get();
+  const Plan& pl = f->plan;
+  size_t o = 0;
+  for (size_t b : {sizeof(SubDev) * f->subs.size(), sizeof(IfaceDev) * f->ifaces.size(),
+                   sizeof(Item) * pl.items.size(), sizeof(int) * pl.q_items.size(),
+                   sizeof(int) * pl.q_item_begin.size(), sizeof(int64_t) * pl.q_part_off.size(),
+                   sizeof(int2) * pl.red_blocks.size(), sizeof(PackBlock) * f->pack_h.size()})
+    o = al256(o + b);
+  return o;
+}
+
+// With `pinned` (host page-locked memory of fork_table_bytes), the tables are
+// staged there and uploaded asynchronously; without it they are uploaded
+// from pageable host memory, which waits for the work queued on `s`.
+void bind_fork(xpinn_ctx* h, Fork& F, char* ws, const xpinn_fork_desc* d, cudaStream_t s,
+               char* pinned = nullptr) {
+  xpinn_ctx* f = F.f.get();
+  const ForkLayout& L = F.L;
+  const Plan& pl = f->plan;
+  f->subs_d.view(ws + L.subs, f->subs.size());
+  f->ifaces_d.view(ws + L.ifaces, f->ifaces.size());
+  f->items_d.view(ws + L.items, pl.items.size());
+  f->q_items_d.view(ws + L.q_items, pl.q_items.size());
+  f->q_item_begin_d.view(ws + L.q_item_begin, pl.q_item_begin.size());
+  f->q_part_off_d.view(ws + L.q_part_off, pl.q_part_off.size());
+  f->red_blocks_d.view(ws + L.red_blocks, pl.red_blocks.size());
+  f->pack_d.view(ws + L.pack, f->pack_h.size());
+  f->params.view(ws + L.params, f->n_params);
+  f->m.view(ws + L.m, F.n_params_sel);
+  f->v.view(ws + L.v, F.n_params_sel);
+  f->wimg.view(ws + L.wimg, std::max<int64_t>(4, f->n_img));
+  f->pts.view(ws + L.pts, f->n_pts_total);
+  f->res_f.view(ws + L.res_f, F.n_res_req);
+  f->tgt.view(ws + L.tgt, F.n_tgt);
+  f->d4.view(ws + L.d4, std::max<int64_t>(1, f->n_if_pts * 2 * f->d4_nv));
+  f->partials.view(ws + L.partials, pl.partial_floats);
+  f->loss_part.view(ws + L.loss_part, 2 * pl.items.size());
+  f->counters.view(ws + L.counters, f->n_counters);
+  f->state_i.view(ws + L.state, 2);
+  f->loss_ring.view(ws + L.ring, (size_t)f->ring_cap * f->n_sub * XPINN_N_TERMS);
+  f->err_d.view(h->err_d.p, 1);              // errors are the handle's (xpinn_sync reports them)
+  f->scratch.view(h->scratch.p, h->scratch.n);
+  size_t po = 0;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (!bytes) return;
+    if (pinned) {
+      memcpy(pinned + po, src, bytes);
+      src = pinned + po;
+      po = al256(po + bytes);
+    }
+    ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s), "fork tables");
+  };
+  auto dd = [&](void* dst, const void* src, size_t bytes) {
+    if (bytes) ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s), "fork copy");
+  };
+  up(f->subs_d.p, f->subs.data(), sizeof(SubDev) * f->subs.size());
+  up(f->ifaces_d.p, f->ifaces.data(), sizeof(IfaceDev) * f->ifaces.size());
+  up(f->items_d.p, pl.items.data(), sizeof(Item) * pl.items.size());
+  up(f->q_items_d.p, pl.q_items.data(), sizeof(int) * pl.q_items.size());
+  up(f->q_item_begin_d.p, pl.q_item_begin.data(), sizeof(int) * pl.q_item_begin.size());
+  up(f->q_part_off_d.p, pl.q_part_off.data(), sizeof(int64_t) * pl.q_part_off.size());
+  up(f->red_blocks_d.p, pl.red_blocks.data(), sizeof(int2) * pl.red_blocks.size());
+  up(f->pack_d.p, f->pack_h.data(), sizeof(PackBlock) * f->pack_h.size());
+  for (int i = 0; i < f->n_sub; ++i) {
+    const SubDev& sd = f->subs[i];
+    dd(f->params.p + sd.poff, h->params.p + F.src_poff[i], sizeof(float) * sd.n_params);
+    if (i < F.n_sel) {
+      dd(f->m.p + sd.poff, h->m.p + F.src_poff[i], sizeof(float) * sd.n_params);
+      dd(f->v.p + sd.poff, h->v.p + F.src_poff[i], sizeof(float) * sd.n_params);
+    }
+  }
+  for (const Fork::Copy& c : F.pt_copies) dd(f->pts.p + c.dst, h->pts.p + c.src, sizeof(float2) * c.n);
+  for (const Fork::Copy& c : F.tgt_copies) dd(f->tgt.p + c.dst, h->tgt.p + c.src, sizeof(float) * c.n);
+  if (F.n_res_req) {
+    copy_in(f->pts.p, d->xy, sizeof(float2) * F.n_res_req, s);
+    if (d->f)
+      copy_in(f->res_f.p, d->f, sizeof(float) * F.n_res_req, s);
+    else
+      ck(cudaMemsetAsync(f->res_f.p, 0, sizeof(float) * F.n_res_req, s), "memset");
+  }
+  ck(cudaMemsetAsync(f->d4.p, 0, sizeof(float) * f->d4.n, s), "memset");
+  ck(cudaMemsetAsync(f->counters.p, 0, sizeof(int) * f->n_counters, s), "memset");
+  ck(cudaMemsetAsync(f->state_i.p, 0, sizeof(int) * 2, s), "memset");
+  dd(f->state_i.p, h->step_t(), sizeof(int));   // Adam continues from the handle's step count
+  StepArgs& a = f->base;
+  a = h->base;
+  a.subs = f->subs_d.p;
+  a.ifaces = f->ifaces_d.p;
+  a.params = f->params.p;
+  a.wimg = f->wimg.p;
+  a.pts = f->pts.p;
+  a.res_f = f->res_f.p;
+  a.tgt = f->tgt.p;
+  a.d4 = f->d4.p;
+  a.partials = f->partials.p;
+  a.loss_part = f->loss_part.p;
+  a.scratch = h->scratch.p;
+  a.err = h->err_d.p;
+  a.n_items_dev = nullptr;
+  f->smem = h->smem;
 }
 
 }  // namespace
@@ -1095,6 +1550,89 @@ int xpinn_objective(xpinn_handle h, float* J, float* J_sub, float* losses, float
   API_END
 }
 
+int xpinn_fork_workspace_size(xpinn_handle h, const xpinn_fork_desc* d, size_t* bytes) {
+  API_BEGIN
+  if (!h || !bytes) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  *bytes = make_fork(h, d)->L.total;
+  API_END
+}
+
+}  // extern "C"
+
+namespace xp {
+// The request server's fork: sizes, then the enqueue with device outputs and
+// the host tables staged in page-locked memory (nothing waits on the GPU).
+int fork_sizes(xpinn_handle h, const xpinn_fork_desc* d, size_t* ws_bytes, size_t* table_bytes) {
+  API_BEGIN
+  DeviceGuard dg(h);
+  auto F = make_fork(h, d);
+  *ws_bytes = F->L.total;
+  *table_bytes = fork_table_bytes(*F);
+  API_END
+}
+
+int fork_enqueue(xpinn_handle h, const xpinn_fork_desc* d, void* workspace, size_t ws_bytes, float* dev_losses,
+                 float* dev_params, char* pinned, cudaStream_t s) {
+  API_BEGIN
+  DeviceGuard dg(h);
+  auto F = make_fork(h, d);
+  if (ws_bytes < F->L.total) fail(XPINN_ERR_INVALID, "workspace of %zu bytes, %zu needed", ws_bytes, F->L.total);
+  bind_fork(h, *F, static_cast<char*>(workspace), d, s, pinned);
+  xpinn_ctx* f = F->f.get();
+  for (int i = 0; i < d->n_steps; ++i) enqueue_step(f, s, true, nullptr);
+  const size_t row = (size_t)F->n_sel * XPINN_N_TERMS;
+  for (int i = 0; dev_losses && i < d->n_steps; ++i)
+    ck(cudaMemcpyAsync(dev_losses + i * row, f->loss_ring.p + (size_t)((i + 1) % f->ring_cap) * f->n_sub * XPINN_N_TERMS,
+                       sizeof(float) * row, cudaMemcpyDeviceToDevice, s),
+       "fork losses");
+  if (dev_params)
+    ck(cudaMemcpyAsync(dev_params, f->params.p, sizeof(float) * F->n_params_sel, cudaMemcpyDeviceToDevice, s),
+       "fork params");
+  ck(cudaGetLastError(), "fork launches");
+  API_END
+}
+}  // namespace xp
+
+extern "C" {
+
+int xpinn_fork_step(xpinn_handle h, const xpinn_fork_desc* d, void* workspace, size_t ws_bytes, float* losses,
+                    float* params, void* stream) {
+  API_BEGIN
+  if (!h || !workspace) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  cudaStream_t s = (cudaStream_t)stream;
+  auto F = make_fork(h, d);
+  if (ws_bytes < F->L.total) fail(XPINN_ERR_INVALID, "workspace of %zu bytes, %zu needed", ws_bytes, F->L.total);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) fail(XPINN_ERR_INVALID, "workspace must be 256-byte aligned");
+  if (!is_device_ptr(workspace)) fail(XPINN_ERR_INVALID, "workspace must be device memory");
+  bind_fork(h, *F, static_cast<char*>(workspace), d, s);
+  xpinn_ctx* f = F->f.get();
+  for (int i = 0; i < d->n_steps; ++i) enqueue_step(f, s, true, nullptr);
+  bool host_out = false;
+  if (losses && d->n_steps > 0) {
+    const bool dev = is_device_ptr(losses);
+    host_out = host_out || !dev;
+    const size_t row = (size_t)F->n_sel * XPINN_N_TERMS;
+    for (int i = 0; i < d->n_steps; ++i) {
+      const int slot = (i + 1) % f->ring_cap;   // the loss slot advances once per step
+      ck(cudaMemcpyAsync(losses + i * row, f->loss_ring.p + (size_t)slot * f->n_sub * XPINN_N_TERMS,
+                         sizeof(float) * row, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+         "fork losses");
+    }
+  }
+  if (params) {
+    const bool dev = is_device_ptr(params);
+    host_out = host_out || !dev;
+    ck(cudaMemcpyAsync(params, f->params.p, sizeof(float) * F->n_params_sel,
+                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+       "fork params");
+  }
+  ck(cudaGetLastError(), "fork launches");
+  if (host_out) check_device_error(h, s);   // synchronises
+  API_END
+}
+
 int xpinn_sync(xpinn_handle h, void* stream) {
   API_BEGIN
   if (!h) fail(XPINN_ERR_INVALID, "NULL handle");
@@ -1136,6 +1674,14 @@ int xpinn_net_jets(xpinn_handle h, int32_t q, int32_t net, const float* xy, int6
   API_END
 }
 
+int xpinn_eval_workspace_size(xpinn_handle h, int32_t model, int64_t n, int32_t order, size_t* bytes) {
+  API_BEGIN
+  if (!h || !bytes || model < 0 || model >= h->n_sub / h->spm || order < 0 || order > 2 || n < 0)
+    fail(XPINN_ERR_INVALID, "bad arguments");
+  *bytes = eval_ws_layout(h, model, n, order).total;
+  API_END
+}
+
 int xpinn_eval(xpinn_handle h, int32_t model, const float* xy, int64_t n, int32_t order, float* out,
                void* stream) {
   API_BEGIN
@@ -1144,49 +1690,22 @@ int xpinn_eval(xpinn_handle h, int32_t model, const float* xy, int64_t n, int32_
     fail(XPINN_ERR_INVALID, "bad arguments");
   DeviceGuard dg(h);
   if (n == 0) { g_err.clear(); return XPINN_OK; }
-  cudaStream_t s = (cudaStream_t)stream;
-  const int K = order == 0 ? 1 : (order == 1 ? 3 : 5);
-  const int row = h->n_out_total * K;
-  const int q0 = model * h->spm, nq = h->spm;
-  const float2* pts;
-  if (is_device_ptr(xy)) {
-    pts = reinterpret_cast<const float2*>(xy);
-  } else {
-    h->e_pts.ensure(n);
-    copy_in(h->e_pts.p, xy, n * sizeof(float2), s);
-    pts = h->e_pts.p;
-  }
-  h->e_S.ensure(n);
-  h->e_memb.ensure(n * 4);
-  h->e_pos.ensure(n * 4);
-  h->e_counts.ensure(2 * nq);
-  ck(cudaMemsetAsync(h->e_counts.p, 0, sizeof(int) * 2 * nq, s), "memset");
-  launch_route(pts, n, h->subs_d.p, q0, nq, h->e_S.p, h->e_memb.p, h->e_counts.p, h->err_d.p, h->poly.p,
-               h->n_poly, s);
-  std::vector<int> counts(nq);
-  ck(cudaMemcpyAsync(counts.data(), h->e_counts.p, sizeof(int) * nq, cudaMemcpyDeviceToHost, s), "counts");
-  ck(cudaStreamSynchronize(s), "sync");
-  check_device_error(h, s);
-  std::vector<int> start(nq + 1, 0);
-  for (int l = 0; l < nq; ++l) start[l + 1] = start[l] + counts[l];
-  const int64_t n_ent = start[nq];
-  ck(cudaMemcpyAsync(h->e_counts.p + nq, start.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, s), "cursor");
-  h->e_epts.ensure(std::max<int64_t>(1, n_ent));
-  h->e_escale.ensure(std::max<int64_t>(1, n_ent));
-  h->e_eout.ensure(std::max<int64_t>(1, n_ent * row));
-  launch_bucket(pts, n, h->e_S.p, h->e_memb.p, h->e_counts.p + nq, h->e_pos.p, h->e_epts.p, h->e_escale.p, s);
-  std::vector<Item> items;
-  for (int l = 0; l < nq; ++l)
-    if (counts[l]) eval_items_for(h, q0 + l, -1, K, start[l], counts[l], (int64_t)start[l] * row, row, items);
-  run_eval_items(h, items, h->e_epts.p, h->e_eout.p, row, h->e_escale.p, s);
-  float* o = out;
-  if (!is_device_ptr(out)) {
-    h->e_out.ensure((size_t)n * row);
-    o = h->e_out.p;
-  }
-  launch_gather(n, row, h->e_S.p, h->e_pos.p, h->e_eout.p, o, s);
-  ck(cudaGetLastError(), "gather");
-  if (o != out) copy_out(out, o, sizeof(float) * n * row, s);
+  const EvalWs L = eval_ws_layout(h, model, n, order);
+  h->e_ws.ensure(L.total);
+  eval_with_ws(h, model, xy, n, order, out, h->e_ws.p, h->e_ws.n, (cudaStream_t)stream);
+  API_END
+}
+
+int xpinn_eval_ws(xpinn_handle h, int32_t model, const float* xy, int64_t n, int32_t order, float* out,
+                  void* workspace, size_t ws_bytes, void* stream) {
+  API_BEGIN
+  if (!h || model < 0 || model >= h->n_sub / h->spm || order < 0 || order > 2 || n < 0 ||
+      (n > 0 && (!xy || !out || !workspace)))
+    fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  if (n == 0) { g_err.clear(); return XPINN_OK; }
+  if (!is_device_ptr(workspace)) fail(XPINN_ERR_INVALID, "workspace must be device memory");
+  eval_with_ws(h, model, xy, n, order, out, static_cast<char*>(workspace), ws_bytes, (cudaStream_t)stream);
   API_END
 }
 

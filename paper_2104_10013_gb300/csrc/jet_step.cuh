@@ -1552,6 +1552,7 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : (PT == 1 ? 2 : 1) * (256
   __shared__ int s_item;
   float* scratch = a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
   uint32_t ph = 0;   // phase parities of the two weight-buffer mbarriers
+  const int n_items = a.n_items_dev ? min(a.n_items, *a.n_items_dev) : a.n_items;
   if (threadIdx.x == 0) {
     const Smem s = carve(sl);
     mbar_init(s.bar, 1);
@@ -1564,7 +1565,7 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : (PT == 1 ? 2 : 1) * (256
     __syncthreads();
     const int it = s_item;
     __syncthreads();
-    if (it >= a.n_items) break;
+    if (it >= n_items) break;
     if (a.n_fwd_wait > 0 && it >= a.wait_from && !wait_exchange(a)) continue;
     const Item& item = a.items[it];
     ph = process_item<PT, GEN>(a, sl, item, a.item_base + it, scratch, ph);

@@ -112,6 +112,76 @@ __global__ void gather_kernel(int64_t n, int row, const int* __restrict__ S, con
   out[idx] = acc;
 }
 
+// Device-side plan of a routed evaluation (no host round trip): one CTA
+// takes the per-subdomain entry counts, writes each bucket's start into
+// cursor[l] (exclusive prefix sum, the bucket kernel's insertion cursor) and
+// cuts every bucket into items of at most proto[l].chunk entries, written to
+// items[]; *n_items receives their number (items beyond max_items are not
+// written and raise err = XPINN_ERR_INVALID, which a correct bound excludes).
+__global__ void __launch_bounds__(256) eval_plan_kernel(const int* __restrict__ counts, int nq,
+                                                        const EvalProto* __restrict__ proto, int q0,
+                                                        int row, int* __restrict__ cursor,
+                                                        Item* __restrict__ items, int* __restrict__ n_items,
+                                                        int max_items, int* __restrict__ err) {
+  __shared__ int s_warp[2][8];
+  __shared__ int s_carry[2];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) s_carry[0] = s_carry[1] = 0;
+  __syncthreads();
+  for (int base = 0; base < nq; base += 256) {
+    const int l = base + t;
+    const int c = l < nq ? counts[l] : 0;
+    const int ch = l < nq ? proto[l].chunk : 1;
+    const int ni = (c + ch - 1) / ch;
+    // inclusive scans of (c, ni) over the 256 threads: warp shuffles, then the warps' totals
+    int a = c, b = ni;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int ua = __shfl_up_sync(0xffffffffu, a, o), ub = __shfl_up_sync(0xffffffffu, b, o);
+      if (lane >= o) { a += ua; b += ub; }
+    }
+    if (lane == 31) { s_warp[0][warp] = a; s_warp[1][warp] = b; }
+    __syncthreads();
+    int pa = s_carry[0], pb = s_carry[1];
+    for (int w = 0; w < warp; ++w) { pa += s_warp[0][w]; pb += s_warp[1][w]; }
+    const int start = pa + a - c, istart = pb + b - ni;   // exclusive
+    if (l < nq) {
+      cursor[l] = start;
+      const EvalProto pr = proto[l];
+      for (int j = 0; j < ni; ++j) {
+        const int k = istart + j;
+        if (k >= max_items) {
+          atomicCAS(err, 0, XPINN_ERR_INVALID);
+          break;
+        }
+        Item it;
+        it.kind = IT_EVAL;
+        it.q = q0 + l;
+        it.edge = -1;
+        it.side = 0;
+        it.P = pr.P;
+        it.K[0] = pr.K0;
+        it.K[1] = pr.K1;
+        it.lap = 0;
+        it.pt_off = (int64_t)start + (int64_t)j * pr.chunk;
+        it.n_pts = min(pr.chunk, c - j * pr.chunk);
+        it.part_off = -1;
+        it.out_off = it.pt_off * row;
+        items[k] = it;
+      }
+    }
+    __syncthreads();
+    if (t == 255) { s_carry[0] = pa + a; s_carry[1] = pb + b; }
+    __syncthreads();
+  }
+  if (t == 0) *n_items = min(s_carry[1], max_items);
+}
+
+void launch_eval_plan(const int* counts, int nq, const EvalProto* proto, int q0, int row, int* cursor,
+                      Item* items, int* n_items, int max_items, int* err, cudaStream_t st) {
+  eval_plan_kernel<<<1, 256, 0, st>>>(counts, nq, proto, q0, row, cursor, items, n_items, max_items, err);
+}
+
 void launch_route(const float2* pts, int64_t n, const SubDev* subs, int q0, int nq, int* S, int* memb,
                   int* counts, int* err, const float2* poly, int n_poly, cudaStream_t st) {
   if (n > 0)

@@ -205,6 +205,15 @@ struct StepArgs {
   const float* eval_scale;   // per point weight (1/S) or NULL
   int eval_dout;             // output row stride in floats per point
   int* err;                  // device error flag (bounds checks)
+  const int* n_items_dev;    // if not NULL: the number of items is min(n_items, *n_items_dev),
+                             // written on the device by an earlier kernel (device-planned evaluation)
+};
+
+// Per subdomain of a model, how a routed evaluation cuts its bucket into
+// items: the jet components of each network, the sub-tile and the entries
+// per item.
+struct EvalProto {
+  int K0, K1, P, chunk;
 };
 
 // Points per sub-tile for an item evaluating the nets with K[n] > 0: enough

@@ -65,15 +65,21 @@ class Options(C.Structure):
                 ("inject_fault", C.c_int32)]
 
 
+class ForkDesc(C.Structure):
+    _fields_ = [("n_sel", C.c_int32), ("sel", C.c_void_p), ("n_pts", C.c_void_p), ("xy", C.c_void_p),
+                ("f", C.c_void_p), ("n_steps", C.c_int32)]
+
+
 class Request(C.Structure):
     _fields_ = [("kind", C.c_int32), ("model", C.c_int32), ("copy", C.c_int32), ("order", C.c_int32),
                 ("n", C.c_int64), ("xy", C.c_void_p), ("out", C.c_void_p), ("n_steps", C.c_int32),
-                ("losses", C.c_void_p)]
+                ("losses", C.c_void_p), ("n_sel", C.c_int32), ("sel", C.c_void_p), ("n_pts", C.c_void_p),
+                ("f", C.c_void_p), ("params", C.c_void_p)]
 
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("queue_ms", C.c_double), ("latency_ms", C.c_double),
-                ("batch", C.c_int32), ("error", C.c_char * 160)]
+                ("batch", C.c_int32), ("error", C.c_char * 160), ("tick_requests", C.c_int32)]
 
 
 _LIB = None
@@ -122,6 +128,10 @@ def load() -> C.CDLL:
         "xpinn_noalloc_debug_preset_error": (C.c_int, [i32]),
         "xpinn_sync": (C.c_int, [vp, vp]),
         "xpinn_objective": (C.c_int, [vp, fp, fp, fp, fp, vp]),
+        "xpinn_eval_workspace_size": (C.c_int, [vp, i32, i64, i32, C.POINTER(C.c_size_t)]),
+        "xpinn_fork_workspace_size": (C.c_int, [vp, C.POINTER(ForkDesc), C.POINTER(C.c_size_t)]),
+        "xpinn_fork_step": (C.c_int, [vp, C.POINTER(ForkDesc), vp, C.c_size_t, fp, fp, vp]),
+        "xpinn_eval_ws": (C.c_int, [vp, i32, fp, i64, i32, fp, vp, C.c_size_t, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -319,6 +329,53 @@ class Solver:
         _check(self.lib.xpinn_eval(self.h, model, xp_, n, order, op, _stream(xy)))
         return out
 
+    def eval_workspace_size(self, n, order=0, model=0) -> int:
+        b = C.c_size_t(0)
+        _check(self.lib.xpinn_eval_workspace_size(self.h, model, n, order, C.byref(b)))
+        return b.value
+
+    def eval_ws(self, model, xy, order, out, workspace):
+        """xpinn_eval from a caller-provided device workspace (a uint8 CUDA
+        tensor of at least eval_workspace_size bytes); xy, out on the same side."""
+        xp_, _ = _ptr(xy)
+        op, _ = _ptr(out)
+        _check(self.lib.xpinn_eval_ws(self.h, model, xp_, int(xy.shape[0]), order, op, workspace.data_ptr(),
+                                      workspace.numel(), _stream(xy)))
+        return out
+
+    def _fork_desc(self, sel, xy_list, f_list, n_steps):
+        sel = np.ascontiguousarray(np.asarray(sel, dtype=np.int32))
+        counts = np.ascontiguousarray(np.array([len(x) for x in xy_list], dtype=np.int64))
+        xy = _f32(np.concatenate(xy_list)) if len(xy_list) else np.zeros((0, 2), np.float32)
+        f = None if f_list is None else _f32(np.concatenate(f_list))
+        d = ForkDesc(n_sel=len(sel), sel=sel.ctypes.data, n_pts=counts.ctypes.data,
+                     xy=xy.ctypes.data if len(xy) else None,
+                     f=f.ctypes.data if f is not None and len(f) else None, n_steps=n_steps)
+        return d, (sel, counts, xy, f)
+
+    def fork_workspace_size(self, sel, xy_list, f_list=None, n_steps=1) -> int:
+        d, keep = self._fork_desc(sel, xy_list, f_list, n_steps)
+        b = C.c_size_t(0)
+        _check(self.lib.xpinn_fork_workspace_size(self.h, C.byref(d), C.byref(b)))
+        return b.value
+
+    def fork_step(self, sel, xy_list, f_list=None, n_steps=1, workspace=None):
+        """Train the subdomains `sel` on their own residual points (xy_list[i]
+        for sel[i], forcing f_list[i] or zero) for n_steps on a private fork
+        (xpinn_fork_step); the handle is unchanged.  Returns (losses
+        [n_steps, n_sel, 5], the fork's parameters of sel, packed)."""
+        import torch
+        d, keep = self._fork_desc(sel, xy_list, f_list, n_steps)
+        if workspace is None:
+            workspace = torch.empty(self.fork_workspace_size(sel, xy_list, f_list, n_steps), dtype=torch.uint8,
+                                    device="cuda")
+        n_par = sum(self.pb.subs[q].n_params for q in keep[0])
+        losses = np.empty((n_steps, len(keep[0]), N_TERMS), np.float32)
+        params = np.empty(n_par, np.float32)
+        _check(self.lib.xpinn_fork_step(self.h, C.byref(d), workspace.data_ptr(), workspace.numel(),
+                                        losses.ctypes.data, params.ctypes.data, None))
+        return losses, params
+
     def iface_values(self):
         n = C.c_int64(0)
         _check(self.lib.xpinn_iface_values(self.h, None, C.byref(n), None))
@@ -422,6 +479,7 @@ class Server:
         return t.value
 
     def submit_step(self, model, n_steps=1):
+        """Train model `model` in place for n_steps (xpinn_step)."""
         sv = self.solvers[model]
         losses = np.empty((n_steps, sv.n_sub, N_TERMS), np.float32)
         r = Request(kind=1, model=model, copy=0, order=0, n=0, xy=None, out=None, n_steps=n_steps,
@@ -429,6 +487,25 @@ class Server:
         t = C.c_uint64()
         _check(self.lib.xpinn_server_submit(self.s, C.byref(r), C.byref(t)))
         self._keep[t.value] = (None, losses)
+        return t.value
+
+    def submit_fork(self, model, sel, xy_list, f_list=None, n_steps=1):
+        """Train subdomains `sel` of model `model` on their own residual points
+        (xy_list[i] for sel[i]) on a private fork (xpinn_fork_step); the
+        result's "out" is (losses [n_steps, n_sel, 5], fork parameters)."""
+        sv = self.solvers[model]
+        sel = np.ascontiguousarray(np.asarray(sel, np.int32))
+        counts = np.ascontiguousarray(np.array([len(x) for x in xy_list], np.int64))
+        xy = _f32(np.concatenate(xy_list))
+        f = None if f_list is None else _f32(np.concatenate(f_list))
+        losses = np.empty((n_steps, len(sel), N_TERMS), np.float32)
+        params = np.empty(sum(sv.pb.subs[q].n_params for q in sel), np.float32)
+        r = Request(kind=2, model=model, n=0, xy=xy.ctypes.data, out=None, n_steps=n_steps,
+                    losses=losses.ctypes.data, n_sel=len(sel), sel=sel.ctypes.data, n_pts=counts.ctypes.data,
+                    f=f.ctypes.data if f is not None else None, params=params.ctypes.data)
+        t = C.c_uint64()
+        _check(self.lib.xpinn_server_submit(self.s, C.byref(r), C.byref(t)))
+        self._keep[t.value] = ((sel, counts, xy, f), (losses, params))
         return t.value
 
     def poll(self, ticket):
@@ -439,7 +516,7 @@ class Server:
         _check(rc)
         _, out = self._keep.pop(ticket)
         return {"status": res.status, "queue_ms": res.queue_ms, "latency_ms": res.latency_ms,
-                "batch": res.batch, "error": res.error.decode(), "out": out}
+                "batch": res.batch, "tick_requests": res.tick_requests, "error": res.error.decode(), "out": out}
 
     def wait(self, ticket, sleep=1e-4):
         import time

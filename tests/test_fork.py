@@ -1,0 +1,105 @@
+"""Training on a private fork (xpinn_fork_step): a subset S of a model's
+subdomains trained on the request's own residual points, starting from the
+model's parameters, Adam moments and step count, with the interface
+neighbours outside S held at the model's parameters (Algorithm 1).
+
+Checked: the first step's loss terms of S against the FP64 oracle on the
+same problem with S's residual points replaced by the request's; the
+parameters after one step against a whole handle stepping that problem (the
+same first update of S, summed in another item order); the model's own
+parameters unchanged; a fork repeated is bitwise the same.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2104_10013_gb300 import problems as P
+from tests.test_parity import RTOL_JET, assert_scaled
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def X():
+    from paper_2104_10013_gb300 import build as B
+    from paper_2104_10013_gb300 import xpinn as X
+    B.build()
+    X.load()
+    return X
+
+
+def request_points(pb, sel, counts, seed=5):
+    rng = np.random.default_rng(seed)
+    xy, f = [], []
+    for q, n in zip(sel, counts):
+        x0, x1, y0, y1 = pb.subs[q].rect
+        pts = np.stack([rng.uniform(x0, x1, n), rng.uniform(y0, y1, n)], 1).astype(np.float32)
+        xy.append(pts)
+        f.append((rng.normal(size=n) if pb.pde == P.PDE_POISSON else np.zeros(n)).astype(np.float32))
+    return xy, f
+
+
+def with_points(pb, sel, xy, f):
+    pb2 = copy.deepcopy(pb)
+    for q, a, b in zip(sel, xy, f):
+        pb2.subs[q].res_xy = a
+        pb2.subs[q].res_f = b
+    return pb2
+
+
+@pytest.mark.parametrize("name,sel,counts", [
+    ("poisson_xpinn", [5, 6, 9], [1000, 2500, 777]),     # interior subdomains, neighbours outside S
+    ("burgers_cpinn", [0, 3], [1500, 640]),              # end slabs, cPINN fluxes
+    ("kovasznay_cpinn", [4], [3000]),                    # one subdomain, four neighbours
+])
+def test_fork_first_step_matches_oracle_and_full_handle(X, name, sel, counts):
+    pb = {"poisson_xpinn": lambda: P.poisson_xpinn(n_res_range=(300, 1500), n_iface=64, n_bc=40),
+          "burgers_cpinn": lambda: P.burgers_cpinn(n_res=500),
+          "kovasznay_cpinn": lambda: P.kovasznay_cpinn(nx=3, ny=3, n_res=1500, n_iface=96, n_bc=80)}[name]()
+    xy, f = request_points(pb, sel, counts)
+    s = X.Solver(pb)
+    theta0 = s.get_params()
+    losses, fparams = s.fork_step(sel, xy, f, n_steps=1)
+    assert np.array_equal(s.get_params(), theta0)             # the model is untouched
+    pb2 = with_points(pb, sel, xy, f)
+    terms, _ = Oracle(pb2).grad(pb2.packed_params(), subset=sel)
+    assert_scaled(losses[0], terms, RTOL_JET, "fork losses", axis=0)
+    # one step of the whole problem with S's points replaced: S's blocks take the same update
+    s2 = X.Solver(pb2)
+    s2.step(1)
+    th2 = s2.get_params()
+    offs = np.cumsum([0] + [sd.n_params for sd in pb.subs])
+    want = np.concatenate([th2[offs[q]:offs[q + 1]] for q in sel])
+    start = np.concatenate([theta0[offs[q]:offs[q + 1]] for q in sel])
+    d_fork, d_full = fparams - start, want - start
+    assert np.linalg.norm(d_fork - d_full) <= 1e-3 * np.linalg.norm(d_full)
+    s.close(); s2.close()
+
+
+def test_fork_is_deterministic_and_continues_adam(X):
+    pb = P.poisson_xpinn(n_res_range=(300, 1500), n_iface=64, n_bc=40)
+    s = X.Solver(pb)
+    s.step(3)                                                  # Adam moments and t > 0
+    sel = [2, 7]
+    xy, f = request_points(pb, sel, [900, 1300], seed=9)
+    l1, p1 = s.fork_step(sel, xy, f, n_steps=4)
+    l2, p2 = s.fork_step(sel, xy, f, n_steps=4)
+    assert np.array_equal(l1, l2) and np.array_equal(p1, p2)
+    assert np.all(np.isfinite(l1)) and l1.shape == (4, 2, P.N_TERMS)
+    # training the fork lowers the weighted loss of its subdomains
+    W = Oracle(pb).weights()[sel]
+    assert (l1[-1] * W).sum() < (l1[0] * W).sum()
+    s.close()
+
+
+def test_fork_rejects_bad_requests(X):
+    pb = P.burgers_cpinn(n_res=200)
+    s = X.Solver(pb)
+    xy = [np.zeros((4, 2), np.float32)] * 2
+    with pytest.raises(X.XpinnError):
+        s.fork_step([1, 1], xy)                               # repeated subdomain
+    with pytest.raises(X.XpinnError):
+        s.fork_step([9], xy[:1])                              # out of range
+    s.close()

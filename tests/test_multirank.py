@@ -66,7 +66,7 @@ def test_reference_arm_line_keeps_the_benchmark_contract():
     the oracle as the timed program, and an e2e block without copies."""
     import json
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "3"], capture_output=True, text=True, timeout=300)
+                        "--warmup", "3", "--workload", "c1"], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.strip().splitlines() if l.strip()]
     assert len(lines) == 1

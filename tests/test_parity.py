@@ -363,6 +363,35 @@ def test_stitched_eval_on_voronoi_regions(X, order):
     s.close()
 
 
+def test_eval_from_workspace_is_device_planned_and_bitwise_equal(X):
+    """xpinn_eval_ws with device points, output and workspace (no host round
+    trip) equals xpinn_eval bit for bit and the oracle within tolerance,
+    including the worst case of every point on a corner shared by four
+    subdomains (the workspace bound) and points on single cuts."""
+    import torch
+    pb = small_c2()
+    s = X.Solver(pb)
+    xc, yc = pb.meta["xcuts"], pb.meta["ycuts"]
+    rng = np.random.default_rng(8)
+    corners = np.array([[xc[i], yc[j]] for i in range(1, 4) for j in range(1, 4)], np.float32)
+    xy = np.concatenate([np.repeat(corners, 40, axis=0),                       # four boxes each
+                         np.stack([np.full(200, xc[2]), rng.random(200)], 1),  # two boxes
+                         rng.random((2000, 2))]).astype(np.float32)
+    for order in (0, 2):
+        ref_host = s.eval(0, xy, order)
+        ws = torch.empty(s.eval_workspace_size(len(xy), order), dtype=torch.uint8, device="cuda")
+        dxy = torch.from_numpy(xy).cuda()
+        dout = torch.full(ref_host.shape, float("nan"), device="cuda")
+        s.eval_ws(0, dxy, order, dout, ws)
+        torch.cuda.synchronize()
+        s.sync()
+        got = dout.cpu().numpy()
+        assert np.array_equal(got, ref_host)
+        ref = Oracle(pb).eval_stitched(pb.packed_params(), 0, xy, (1, 3, 5)[order])
+        assert_scaled(got, ref, RTOL_JET, f"workspace eval order {order}", axis=(0, 1))
+    s.close()
+
+
 def test_voronoi_routing_on_and_next_to_polygon_edges(X):
     """Points exactly on the polygon's edges (rounded to float32) and one ulp
     to either side in x and y: the GPU router and the oracle classify every one
