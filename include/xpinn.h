@@ -137,6 +137,11 @@ typedef struct {
   float normal[2];                         /* n for the cPINN flux f . n */
   int64_t n_pts;
   const float* xy;                         /* [n_pts][2] */
+  int32_t remote;                          /* 0: both sides are in this problem; 1: only
+                                              side q is (distributed training: q_plus is
+                                              another rank's, and that rank describes the
+                                              same interface with the same points; its
+                                              values come through xpinn_set_remote_values) */
 } xpinn_interface_desc;
 
 typedef struct {
@@ -214,6 +219,42 @@ int xpinn_objective(xpinn_handle h, float* J, float* J_sub, float* losses, float
  * synchronising call on the handle: xpinn_sync, xpinn_grad, or xpinn_step
  * with host losses.  The steps after a non-finite loss still run. */
 int xpinn_step(xpinn_handle h, int32_t n_steps, float* losses, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Distributed training (Algorithm 1 across ranks, one GPU each): a rank's
+ * handle holds its own subdomains (xpinn_partition picks them), and every
+ * interface it shares with another rank is described with remote = 1 and the
+ * local subdomain as q.  A training step is then
+ *   xpinn_step_begin   start of the step: this handle's side of every
+ *                      interface into the exchange buffer (one launch);
+ *   xpinn_remote_values / xpinn_set_remote_values
+ *                      the host sends its sides of the remote interfaces and
+ *                      writes the other ranks' sides (the paper's Isend /
+ *                      Irecv; NCCL send/recv or any transport);
+ *   xpinn_step_end     the residual, data and interface terms, the reverse
+ *                      pass, the reduction and Adam; losses as one row of
+ *                      xpinn_step (host or device, or NULL).
+ * The remote values are the other side's solution vector and exchanged
+ * quantity at the interface points, rows of [n_pts][nv] (nv = xpinn_iface_values'
+ * floats per point and side), interface by interface in the order of the
+ * description.  xpinn_step on such a handle uses the remote values last set.
+ * ------------------------------------------------------------------------- */
+int xpinn_step_begin(xpinn_handle h, void* stream);
+int xpinn_step_end(xpinn_handle h, float* losses, void* stream);
+/* out NULL: *n_floats receives the size.  Host or device pointer (host:
+ * returns after the copy). */
+int xpinn_remote_values(xpinn_handle h, float* out, int64_t* n_floats, void* stream);
+int xpinn_set_remote_values(xpinn_handle h, const float* in, int64_t n_floats, void* stream);
+
+/* Partition of n_sub subdomains over n_parts ranks (1 <= n_parts <= n_sub):
+ * part[q] in [0, n_parts).  weight[q] is a subdomain's work (its points),
+ * edges (eq[e], eqp[e]) its interfaces with edge_w[e] their points (the
+ * exchanged rows).  Weighted graph growing from the lowest-numbered free
+ * subdomain, then boundary refinement that moves subdomains to cut fewer
+ * interface points while every part stays within 10% of an even share.
+ * Deterministic; host only. */
+int xpinn_partition(int32_t n_sub, const double* weight, int32_t n_edge, const int32_t* eq, const int32_t* eqp,
+                    const double* edge_w, int32_t n_parts, int32_t* part);
 
 /* Waits for everything queued on `stream`, then reads and clears the
  * handle's device status word: XPINN_OK, XPINN_ERR_TIMEOUT (a bounded device
@@ -336,6 +377,22 @@ int xpinn_set_options(xpinn_handle h, const xpinn_options* opt);
  * so are the rest once about 20 s have been spent (the best so far is kept).
  * Parameters, Adam state and step count are unchanged.  Synchronises. */
 int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* best_ms);
+
+/* Per-shape tuning: subdomains whose networks have the same widths,
+ * activations, slopes and output activation form a shape class; within one
+ * grouped launch every item of a class is cut into sub-tiles of at most the
+ * class's cap of points.  xpinn_autotune_shapes picks the caps by
+ * coordinate descent over the classes (the classes with the largest modelled
+ * share of the step first; candidates 128, 96, 64, 48, 32, 160 and none),
+ * timing `steps` gradient passes of the grouped step for each and keeping a
+ * choice only when it is clearly faster; about 20 s at most, then it keeps
+ * what it has.  Parameters, Adam state and step count are unchanged;
+ * synchronises.  *best_ms: the median ms per pass of the final choice.
+ * The caps, one per subdomain (0: no cap beyond the options'), can be read
+ * and set (for a cache of tuned choices); setting re-plans the step. */
+int xpinn_autotune_shapes(xpinn_handle h, int32_t steps, float* best_ms);
+int xpinn_get_tile_caps(xpinn_handle h, int32_t* caps);         /* caps [n_sub], host */
+int xpinn_set_tile_caps(xpinn_handle h, const int32_t* caps);   /* [n_sub] (0 or >= 8), or NULL: none */
 
 /* Device time in milliseconds of the four phases of the most recent step or
  * grad call, measured by CUDA events recorded on the call's stream:

@@ -159,6 +159,9 @@ struct xpinn_ctx {
   // a fork (xpinn_fork_step) trains only some of its subdomains: the others
   // only provide their interface values; empty = every subdomain is trained
   std::vector<char> trained;
+  // per-subdomain cap on the points of a sub-tile (0: none), chosen per shape
+  // class by xpinn_autotune_shapes; empty = none
+  std::vector<int> tile_cap;
   int64_t n_params = 0, n_res_total = 0, n_pts_total = 0, n_if_pts = 0;
   int n_out_total = 0, n_eq = 1, d4_nv = 0;
   // device problem
@@ -204,6 +207,7 @@ struct xpinn_ctx {
   cudaGraphExec_t graph_multi = nullptr;  // GRAPH_STEPS training steps back to back
   int n_counters = 0;
   int p_cap = 256;
+  bool step_open = false;        // xpinn_step_begin called, xpinn_step_end pending
   DevBuf<int> e_counter;
 
   ~xpinn_ctx() {
@@ -336,7 +340,8 @@ void build_plan(xpinn_ctx* h, int p_cap) {
     it.K[0] = K0;
     it.K[1] = K1;
     it.lap = lap_of(h->pde, K0);
-    it.P = choose_P(h->subs[q], it.K, p_cap, h->opt.points_per_thread, cta_threads(h));
+    const int qcap = (h->tile_cap.empty() || h->tile_cap[q] <= 0) ? p_cap : std::min(p_cap, h->tile_cap[q]);
+    it.P = choose_P(h->subs[q], it.K, qcap, h->opt.points_per_thread, cta_threads(h));
     it.part_off = -1;
     return it;
   };
@@ -381,6 +386,7 @@ void build_plan(xpinn_ctx* h, int p_cap) {
       const int q = side ? f.qp : f.q;
       const int K0 = k_iface(h->pde, f.method, 0);
       const int K1 = h->subs[q].n_nets > 1 ? k_iface(h->pde, f.method, 1) : 0;
+      if (side == 1 && f.remote) continue;   // that side is computed by its own rank
       split(mk(IT_IFACE_FWD, q, e, side, f.pt_off, f.n_pts, K0, K1), fwd);
       if (is_trained(q)) split(mk(IT_IFACE, q, e, side, f.pt_off, f.n_pts, K0, K1), main_);
     }
@@ -585,8 +591,16 @@ StepArgs args_for(xpinn_ctx* h, int begin, int count, int counter_idx) {
   return a;
 }
 
+// Phase event i on s: an external event node while s is being captured into
+// the step graph, a plain record otherwise (calls replayed outside a graph).
 void mark(xpinn_ctx* h, int i, cudaStream_t s) {
-  if (h->opt.profile_phases) ck(cudaEventRecordWithFlags(h->ev[i], s, cudaEventRecordExternal), "event");
+  if (!h->opt.profile_phases) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ck(cudaStreamIsCapturing(s, &cs), "capture status");
+  if (cs == cudaStreamCaptureStatusActive)
+    ck(cudaEventRecordWithFlags(h->ev[i], s, cudaEventRecordExternal), "event");
+  else
+    ck(cudaEventRecord(h->ev[i], s), "event");
 }
 
 void pack_images(xpinn_ctx* h, cudaStream_t s) {
@@ -595,11 +609,24 @@ void pack_images(xpinn_ctx* h, cudaStream_t s) {
 
 constexpr int GRAPH_STEPS = 16;   // steps captured in the multi-step graph
 
-void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads) {
+// part 0: the whole step.  Part 1: its start and the exchange items only
+// (this handle's sides of every interface into the exchange buffer); part 2:
+// the rest (residual, data and interface items, reduction and Adam) once the
+// remote sides of the exchange buffer have been set (distributed training).
+void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads, int part = 0) {
   const Plan& pl = h->plan;
-  mark(h, 0, s);
-  launch_step_begin(h->counters.p, h->n_counters, h->step_t(), h->loss_slot(), adam ? 1 : 0, s);
-  pack_images(h, s);
+  if (part == 1) {
+    launch_step_begin(h->counters.p, h->n_counters, h->step_t(), h->loss_slot(), adam ? 1 : 0, s);
+    pack_images(h, s);
+    if (pl.n_fwd) launch_jet_step(args_for(h, 0, pl.n_fwd, 0), std::min(h->grid, pl.n_fwd), h->smem, s);
+    ck(cudaGetLastError(), "kernel launch");
+    return;
+  }
+  if (part == 0) {
+    mark(h, 0, s);
+    launch_step_begin(h->counters.p, h->n_counters, h->step_t(), h->loss_slot(), adam ? 1 : 0, s);
+    pack_images(h, s);
+  }
   const int n_main = (int)pl.items.size() - pl.n_fwd;
   ReduceArgs r{};
   r.blocks = h->red_blocks_d.p;
@@ -626,7 +653,10 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads) {
   r.n_sub = h->n_sub;
   r.err = h->err_d.p;
   r.jq = h->jq.p;
-  if (h->opt.schedule == 0) {
+  if (part == 2) {
+    if (n_main) launch_jet_step(args_for(h, pl.n_fwd, n_main, 1), std::min(h->grid, n_main), h->smem, s);
+    launch_reduce_adam(r, s);
+  } else if (h->opt.schedule == 0) {
     // one launch: exchange items first, interface items last (they wait)
     mark(h, 1, s);
     mark(h, 2, s);
@@ -886,6 +916,7 @@ struct Fork {
     int64_t dst, src, n;
   };
   std::vector<Copy> pt_copies, tgt_copies;   // (data and interface points, targets) from the handle
+  std::vector<Copy> d4_copies;                // interfaces with a remote side: their exchange rows
   int64_t n_res_req = 0, n_data_pts = 0, n_tgt = 0;
   ForkLayout L{};
 };
@@ -919,6 +950,7 @@ std::unique_ptr<Fork> make_fork(xpinn_ctx* h, const xpinn_fork_desc* d) {
   // interface neighbours of S outside S, ascending
   std::vector<int> nb;
   for (const IfaceDev& e : h->ifaces) {
+    if (e.remote) continue;   // the remote side's values stay what the handle holds (see bind_fork)
     if (idx[e.q] >= 0 && idx[e.qp] < 0) nb.push_back(e.qp);
     if (idx[e.qp] >= 0 && idx[e.q] < 0) nb.push_back(e.q);
   }
@@ -953,6 +985,8 @@ std::unique_ptr<Fork> make_fork(xpinn_ctx* h, const xpinn_fork_desc* d) {
   f->ring_cap = std::max(1, (int)d->n_steps);
   f->trained.assign(f->n_sub, 0);
   for (int i = 0; i < d->n_sel; ++i) f->trained[i] = 1;
+  if (!h->tile_cap.empty())
+    for (int q : F->T) f->tile_cap.push_back(h->tile_cap[q]);
   // points: [request residual points][data points of S][interface points]
   int64_t n_data = 0;
   for (int i = 0; i < d->n_sel; ++i) {
@@ -1015,6 +1049,8 @@ std::unique_ptr<Fork> make_fork(xpinn_ctx* h, const xpinn_fork_desc* d) {
     fd.q = idx[e.q];
     fd.qp = idx[e.qp];
     F->pt_copies.push_back({n_req + n_data + icur, e.pt_off, e.n_pts});
+    if (e.remote)   // the remote side's values as the handle last received them
+      F->d4_copies.push_back({icur * 2 * h->d4_nv, e.d4_pt * 2 * h->d4_nv, (int64_t)e.n_pts * 2 * h->d4_nv});
     fd.pt_off = n_req + n_data + icur;
     fd.d4_pt = icur;
     icur += e.n_pts;
@@ -1145,6 +1181,7 @@ void bind_fork(xpinn_ctx* h, Fork& F, char* ws, const xpinn_fork_desc* d, cudaSt
       ck(cudaMemsetAsync(f->res_f.p, 0, sizeof(float) * F.n_res_req, s), "memset");
   }
   ck(cudaMemsetAsync(f->d4.p, 0, sizeof(float) * f->d4.n, s), "memset");
+  for (const Fork::Copy& c : F.d4_copies) dd(f->d4.p + c.dst, h->d4.p + c.src, sizeof(float) * c.n);
   ck(cudaMemsetAsync(f->counters.p, 0, sizeof(int) * f->n_counters, s), "memset");
   ck(cudaMemsetAsync(f->state_i.p, 0, sizeof(int) * 2, s), "memset");
   dd(f->state_i.p, h->step_t(), sizeof(int));   // Adam continues from the handle's step count
@@ -1326,14 +1363,17 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
   std::vector<float2> pts_if;
   for (int e = 0; e < d->n_iface; ++e) {
     const xpinn_interface_desc& f = d->ifaces[e];
-    if (f.q < 0 || f.q >= d->n_sub || f.q_plus < 0 || f.q_plus >= d->n_sub || f.q == f.q_plus)
+    if (f.remote != 0 && f.remote != 1) fail(XPINN_ERR_INVALID, "interface %d: remote must be 0 or 1", e);
+    if (f.q < 0 || f.q >= d->n_sub ||
+        (!f.remote && (f.q_plus < 0 || f.q_plus >= d->n_sub || f.q == f.q_plus)))
       fail(XPINN_ERR_INVALID, "interface %d: bad subdomains (%d, %d)", e, f.q, f.q_plus);
     if (f.method != XPINN_CPINN && f.method != XPINN_XPINN) fail(XPINN_ERR_INVALID, "interface %d: bad method", e);
     if (f.n_pts < 0 || (f.n_pts > 0 && !f.xy)) fail(XPINN_ERR_INVALID, "interface %d: bad points", e);
     check_finite(f.xy, 2 * f.n_pts, "iface xy");
     IfaceDev fd{};
     fd.q = f.q;
-    fd.qp = f.q_plus;
+    fd.qp = f.remote ? f.q : f.q_plus;   // a remote side has no subdomain in this handle
+    fd.remote = f.remote;
     fd.method = f.method;
     fd.n_pts = (int)f.n_pts;
     fd.nx = f.normal[0];
@@ -1633,6 +1673,100 @@ int xpinn_fork_step(xpinn_handle h, const xpinn_fork_desc* d, void* workspace, s
   API_END
 }
 
+int xpinn_step_begin(xpinn_handle h, void* stream) {
+  API_BEGIN
+  if (!h) fail(XPINN_ERR_INVALID, "NULL handle");
+  if (h->step_open) fail(XPINN_ERR_INVALID, "xpinn_step_begin called twice without xpinn_step_end");
+  DeviceGuard dg(h);
+  enqueue_step(h, (cudaStream_t)stream, true, nullptr, 1);
+  h->step_open = true;
+  API_END
+}
+
+int xpinn_step_end(xpinn_handle h, float* losses, void* stream) {
+  API_BEGIN
+  if (!h) fail(XPINN_ERR_INVALID, "NULL handle");
+  if (!h->step_open) fail(XPINN_ERR_INVALID, "xpinn_step_end without xpinn_step_begin");
+  DeviceGuard dg(h);
+  cudaStream_t s = (cudaStream_t)stream;
+  h->step_open = false;
+  enqueue_step(h, s, true, nullptr, 2);
+  h->host_slot += 1;
+  h->host_t += 1;
+  h->img_stale = true;
+  if (losses) {
+    const size_t row = (size_t)h->n_sub * XPINN_N_TERMS;
+    copy_out(losses, h->loss_ring.p + (size_t)(h->host_slot % h->ring_cap) * row, sizeof(float) * row, s);
+    if (!is_device_ptr(losses)) check_device_error(h, s);
+  }
+  API_END
+}
+
+}  // extern "C"
+
+namespace {
+// Remote interfaces in interface order: (exchange-buffer row of the first
+// point, points).
+std::vector<std::pair<int64_t, int>> remote_ifaces(const xpinn_ctx* h) {
+  std::vector<std::pair<int64_t, int>> r;
+  for (const IfaceDev& f : h->ifaces)
+    if (f.remote) r.emplace_back(f.d4_pt, f.n_pts);
+  return r;
+}
+}  // namespace
+
+extern "C" {
+
+int xpinn_remote_values(xpinn_handle h, float* out, int64_t* n_floats, void* stream) {
+  API_BEGIN
+  if (!h || !n_floats) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  const auto rem = remote_ifaces(h);
+  int64_t need = 0;
+  for (const auto& e : rem) need += (int64_t)e.second * h->d4_nv;
+  if (!out) {
+    *n_floats = need;
+    g_err.clear();
+    return XPINN_OK;
+  }
+  if (*n_floats < need) fail(XPINN_ERR_INVALID, "buffer too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nv = h->d4_nv;
+  int64_t off = 0;
+  for (const auto& e : rem) {
+    if (e.second)
+      ck(cudaMemcpy2DAsync(out + off, nv * sizeof(float), h->d4.p + (size_t)e.first * 2 * nv, 2 * nv * sizeof(float),
+                           nv * sizeof(float), e.second, cudaMemcpyDefault, s),
+         "remote values out");
+    off += (int64_t)e.second * nv;
+  }
+  if (!is_device_ptr(out)) ck(cudaStreamSynchronize(s), "sync");
+  *n_floats = need;
+  API_END
+}
+
+int xpinn_set_remote_values(xpinn_handle h, const float* in, int64_t n_floats, void* stream) {
+  API_BEGIN
+  if (!h || (!in && n_floats)) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  const auto rem = remote_ifaces(h);
+  int64_t need = 0;
+  for (const auto& e : rem) need += (int64_t)e.second * h->d4_nv;
+  if (n_floats != need) fail(XPINN_ERR_INVALID, "%lld floats given, %lld expected", (long long)n_floats, (long long)need);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nv = h->d4_nv;
+  int64_t off = 0;
+  for (const auto& e : rem) {
+    if (e.second)
+      ck(cudaMemcpy2DAsync(h->d4.p + ((size_t)e.first * 2 + 1) * nv, 2 * nv * sizeof(float), in + off,
+                           nv * sizeof(float), nv * sizeof(float), e.second, cudaMemcpyDefault, s),
+         "remote values in");
+    off += (int64_t)e.second * nv;
+  }
+  if (need && !is_device_ptr(in)) ck(cudaStreamSynchronize(s), "sync");
+  API_END
+}
+
 int xpinn_sync(xpinn_handle h, void* stream) {
   API_BEGIN
   if (!h) fail(XPINN_ERR_INVALID, "NULL handle");
@@ -1806,6 +1940,147 @@ int xpinn_set_options(xpinn_handle h, const xpinn_options* opt) {
   API_END
 }
 
+}  // extern "C"
+
+namespace {
+// Median device time (ms) of `steps` gradient passes after two warm-up passes.
+float time_grads(xpinn_ctx* h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int steps) {
+  for (int w = 0; w < 2; ++w) {
+    enqueue_step(h, s, false, h->grads.p);
+    h->host_slot += 1;
+  }
+  std::vector<float> t;
+  for (int i = 0; i < steps; ++i) {
+    ck(cudaEventRecord(e0, s), "event");
+    enqueue_step(h, s, false, h->grads.p);
+    h->host_slot += 1;
+    ck(cudaEventRecord(e1, s), "event");
+    ck(cudaEventSynchronize(e1), "event sync");
+    float ms = 0;
+    ck(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+    t.push_back(ms);
+  }
+  std::sort(t.begin(), t.end());
+  return t[t.size() / 2];
+}
+
+// Shape class of a subdomain: its networks' widths, activations, slopes and
+// output activations (subdomains of one class run the same tile code).
+std::string shape_key(const SubDev& sd) {
+  std::string k;
+  for (int n = 0; n < sd.n_nets; ++n) {
+    const NetDev& nd = sd.net[n];
+    for (int l = 0; l <= nd.L; ++l) k += std::to_string(nd.w[l]) + ",";
+    k += "a" + std::to_string(nd.act) + (nd.aoff >= 0 ? "s" : "f") + "o" + std::to_string(nd.out_act) + "|";
+  }
+  return k;
+}
+}  // namespace
+
+extern "C" {
+
+int xpinn_get_tile_caps(xpinn_handle h, int32_t* caps) {
+  API_BEGIN
+  if (!h || !caps) fail(XPINN_ERR_INVALID, "bad arguments");
+  for (int q = 0; q < h->n_sub; ++q) caps[q] = h->tile_cap.empty() ? 0 : h->tile_cap[q];
+  API_END
+}
+
+int xpinn_set_tile_caps(xpinn_handle h, const int32_t* caps) {
+  API_BEGIN
+  if (!h) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  if (caps)
+    for (int q = 0; q < h->n_sub; ++q)
+      if (caps[q] < 0 || (caps[q] > 0 && caps[q] < 8)) fail(XPINN_ERR_INVALID, "tile cap must be 0 or >= 8");
+  ck(cudaDeviceSynchronize(), "sync");
+  if (caps)
+    h->tile_cap.assign(caps, caps + h->n_sub);
+  else
+    h->tile_cap.clear();
+  apply_options(h, h->opt);
+  API_END
+}
+
+int xpinn_autotune_shapes(xpinn_handle h, int32_t steps, float* best_ms) {
+  API_BEGIN
+  if (!h || steps < 1) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  ck(cudaDeviceSynchronize(), "sync");
+  // classes, largest modelled share of the step first
+  std::vector<std::string> keys;
+  std::vector<double> share;
+  std::vector<std::vector<int>> members;
+  for (int q = 0; q < h->n_sub; ++q) {
+    const std::string k = shape_key(h->subs[q]);
+    size_t c = std::find(keys.begin(), keys.end(), k) - keys.begin();
+    if (c == keys.size()) {
+      keys.push_back(k);
+      share.push_back(0);
+      members.emplace_back();
+    }
+    members[c].push_back(q);
+  }
+  for (const Item& it : h->plan.items) {
+    const size_t c = std::find(keys.begin(), keys.end(), shape_key(h->subs[it.q])) - keys.begin();
+    share[c] += item_cost(h->subs[it.q], it, cta_threads(h));
+  }
+  std::vector<size_t> order(keys.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return share[a] > share[b]; });
+  if (h->tile_cap.empty()) h->tile_cap.assign(h->n_sub, 0);
+  const std::vector<int> orig = h->tile_cap;
+  const xpinn_options orig_opt = h->opt;
+  xpinn_options topt = h->opt;
+  topt.profile_phases = 0;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ck(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
+  ck(cudaEventCreate(&e0), "event");
+  ck(cudaEventCreate(&e1), "event");
+  const auto t_start = std::chrono::steady_clock::now();
+  auto elapsed_s = [&] {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  };
+  float best = 0;
+  try {
+    apply_options(h, topt);
+    best = time_grads(h, s, e0, e1, steps);
+    for (size_t c : order) {
+      int keep = h->tile_cap[members[c][0]];
+      for (int cap : {128, 96, 64, 48, 32, 160, 0}) {
+        if (cap == keep || elapsed_s() > 20.0) continue;
+        for (int q : members[c]) h->tile_cap[q] = cap;
+        try {
+          apply_options(h, topt);
+        } catch (const Error&) {
+          for (int q : members[c]) h->tile_cap[q] = keep;
+          continue;
+        }
+        const float t = time_grads(h, s, e0, e1, steps);
+        if (t < best * 0.995f) {   // keep a choice only for a clear gain
+          best = t;
+          keep = cap;
+        }
+      }
+      for (int q : members[c]) h->tile_cap[q] = keep;
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    h->tile_cap = orig;
+    apply_options(h, orig_opt);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  apply_options(h, orig_opt);
+  if (best_ms) *best_ms = best;
+  API_END
+}
+
 int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* best_ms) {
   API_BEGIN
   if (!h || steps < 1 || !best) fail(XPINN_ERR_INVALID, "bad arguments");
@@ -1842,23 +2117,7 @@ int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* be
           } catch (const Error&) {
             continue;   // does not fit: skip
           }
-          for (int w = 0; w < 2; ++w) {
-            enqueue_step(h, s, false, h->grads.p);
-            h->host_slot += 1;
-          }
-          std::vector<float> t;
-          for (int i = 0; i < steps; ++i) {
-            ck(cudaEventRecord(e0, s), "event");
-            enqueue_step(h, s, false, h->grads.p);
-            h->host_slot += 1;
-            ck(cudaEventRecord(e1, s), "event");
-            ck(cudaEventSynchronize(e1), "event sync");
-            float ms = 0;
-            ck(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
-            t.push_back(ms);
-          }
-          std::sort(t.begin(), t.end());
-          const float med = t[t.size() / 2];
+          const float med = time_grads(h, s, e0, e1, steps);
           if (med < win_ms) {
             win_ms = med;
             win = c;

@@ -152,6 +152,7 @@ struct IfaceDev {
   float inv_n;
   int64_t pt_off;        // first point in pts
   int64_t d4_pt;         // first interface point index in d4
+  int remote;            // 1: side 1 belongs to another rank; its d4 rows are set from outside
 };
 
 struct Item {

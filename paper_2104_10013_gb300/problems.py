@@ -92,12 +92,15 @@ class Subdomain:
 
 @dataclass
 class Interface:
-    """A common interface between subdomains q and qp, with its own points."""
+    """A common interface between subdomains q and qp, with its own points.
+    remote: only side q belongs to this problem (one rank's part of a
+    distributed decomposition); side qp is another rank's."""
     q: int
     qp: int
     method: int
     normal: tuple
     xy: np.ndarray                  # float32 [n_I, 2]
+    remote: bool = False
 
 
 @dataclass

@@ -46,7 +46,7 @@ class SubDesc(C.Structure):
 
 class IfaceDesc(C.Structure):
     _fields_ = [("q", C.c_int32), ("q_plus", C.c_int32), ("method", C.c_int32),
-                ("normal", C.c_float * 2), ("n_pts", C.c_int64), ("xy", C.c_void_p)]
+                ("normal", C.c_float * 2), ("n_pts", C.c_int64), ("xy", C.c_void_p), ("remote", C.c_int32)]
 
 
 class ProblemDesc(C.Structure):
@@ -119,6 +119,14 @@ def load() -> C.CDLL:
         "xpinn_iface_values": (C.c_int, [vp, fp, C.POINTER(i64), vp]),
         "xpinn_phase_times": (C.c_int, [vp, fp]),
         "xpinn_autotune": (C.c_int, [vp, i32, C.POINTER(Options), C.POINTER(C.c_float)]),
+        "xpinn_autotune_shapes": (C.c_int, [vp, i32, C.POINTER(C.c_float)]),
+        "xpinn_step_begin": (C.c_int, [vp, vp]),
+        "xpinn_step_end": (C.c_int, [vp, fp, vp]),
+        "xpinn_remote_values": (C.c_int, [vp, fp, C.POINTER(i64), vp]),
+        "xpinn_set_remote_values": (C.c_int, [vp, fp, i64, vp]),
+        "xpinn_partition": (C.c_int, [i32, vp, i32, vp, vp, vp, i32, vp]),
+        "xpinn_get_tile_caps": (C.c_int, [vp, vp]),
+        "xpinn_set_tile_caps": (C.c_int, [vp, vp]),
         "xpinn_server_create": (C.c_int, [C.POINTER(vp), i32, C.c_size_t, C.POINTER(vp)]),
         "xpinn_server_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
         "xpinn_server_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(Result)]),
@@ -215,6 +223,7 @@ class Solver:
             f.normal[0], f.normal[1] = it.normal
             f.n_pts = it.xy.shape[0]
             f.xy = arr(it.xy) if f.n_pts else None
+            f.remote = int(getattr(it, "remote", False))
         desc = ProblemDesc()
         desc.pde, desc.nu, desc.re, desc.flux_mode = problem.pde, problem.nu, problem.re, problem.flux_mode
         desc.n_sub, desc.subs = problem.n_sub, subs
@@ -376,6 +385,29 @@ class Solver:
                                         losses.ctypes.data, params.ctypes.data, None))
         return losses, params
 
+    # ------------------------------------------------------------ distributed step
+    def step_begin(self, stream=None):
+        _check(self.lib.xpinn_step_begin(self.h, stream))
+
+    def step_end(self, losses=None, stream=None):
+        lp, _ = _ptr(losses)
+        _check(self.lib.xpinn_step_end(self.h, lp, stream))
+        return losses
+
+    def remote_values(self, out=None, stream=None):
+        """This handle's side of every remote interface, [sum n_pts * nv]."""
+        n = C.c_int64(0)
+        _check(self.lib.xpinn_remote_values(self.h, None, C.byref(n), None))
+        if out is None:
+            out = np.empty(n.value, np.float32)
+        op, _ = _ptr(out)
+        _check(self.lib.xpinn_remote_values(self.h, op, C.byref(n), stream))
+        return out
+
+    def set_remote_values(self, vals, stream=None):
+        vp_, _ = _ptr(vals if hasattr(vals, "data_ptr") else _f32(vals))
+        _check(self.lib.xpinn_set_remote_values(self.h, vp_, int(vals.shape[0]) if len(vals.shape) else 0, stream))
+
     def iface_values(self):
         n = C.c_int64(0)
         _check(self.lib.xpinn_iface_values(self.h, None, C.byref(n), None))
@@ -412,9 +444,27 @@ class Solver:
         parts.append(",".join(f"{it.method}:{it.xy.shape[0]}" for it in pb.ifaces))
         return hashlib.sha256("|".join(parts).encode()).hexdigest()[:24]
 
-    def autotune(self, steps=5, cache=None) -> dict:
-        """Pick tile shapes by timing (xpinn_autotune); with `cache` (a JSON
-        file path) reuse and record the choice for this problem shape."""
+    @staticmethod
+    def shape_class(sd) -> str:
+        """Key of a subdomain's shape class (its networks' widths, hidden and
+        output activations, fixed or trained slopes)."""
+        return "|".join(",".join(map(str, n.widths)) + f":a{n.act}{'s' if n.adaptive else 'f'}o{n.out_act}"
+                        for n in sd.nets)
+
+    def tile_caps(self):
+        caps = np.zeros(self.n_sub, np.int32)
+        _check(self.lib.xpinn_get_tile_caps(self.h, caps.ctypes.data))
+        return caps
+
+    def set_tile_caps(self, caps):
+        caps = None if caps is None else np.ascontiguousarray(np.asarray(caps, np.int32))
+        _check(self.lib.xpinn_set_tile_caps(self.h, None if caps is None else caps.ctypes.data))
+
+    def autotune(self, steps=5, cache=None, shapes=True) -> dict:
+        """Pick tile shapes by timing: the launch options (xpinn_autotune),
+        then a sub-tile cap per shape class (xpinn_autotune_shapes).  With
+        `cache` (a JSON file path) reuse and record the choice: the options
+        per problem signature, the caps per shape class."""
         import json
         key = self.signature()
         db = {}
@@ -426,11 +476,20 @@ class Solver:
                     if k in ("points_per_thread", "items_per_cta", "max_points_per_tile",
                              "threads_per_cta")}
             self.set_options(**keep)
+            cc = db[key].get("class_caps")
+            if cc:
+                self.set_tile_caps([cc.get(self.shape_class(sd), 0) for sd in self.pb.subs])
             return db[key]
         o = Options()
         ms = C.c_float(0)
         _check(self.lib.xpinn_autotune(self.h, steps, C.byref(o), C.byref(ms)))
         rec = {"options": {f: getattr(o, f) for f, _ in Options._fields_}, "ms": ms.value}
+        if shapes:
+            ms2 = C.c_float(0)
+            _check(self.lib.xpinn_autotune_shapes(self.h, steps, C.byref(ms2)))
+            caps = self.tile_caps()
+            rec["class_caps"] = {self.shape_class(sd): int(c) for sd, c in zip(self.pb.subs, caps)}
+            rec["ms_shapes"] = ms2.value
         if cache:
             db[key] = rec
             with open(cache, "w") as f:

@@ -341,7 +341,27 @@ def test_autotune_keeps_parity_and_state(X, tmp_path):
     s2 = X.Solver(pb)
     rec2 = s2.autotune(cache=cache)                         # served from the cache
     assert rec2 == rec and s2.options()["items_per_cta"] == rec["options"]["items_per_cta"]
+    assert set(rec["class_caps"]) == {X.Solver.shape_class(sd) for sd in pb.subs}
+    assert np.array_equal(s2.tile_caps(), s.tile_caps())    # per-class caps restored
     s.close(); s2.close()
+
+
+def test_per_shape_tile_caps_keep_parity(X):
+    """Different sub-tile caps for different shape classes in one grouped
+    launch (the uneven Poisson workload: every class its own cap, cycling
+    through 8..256 points): losses and gradients stay within tolerance."""
+    pb = small_c2()
+    s = X.Solver(pb)
+    keys = sorted({X.Solver.shape_class(sd) for sd in pb.subs})
+    choice = {k: (8, 32, 48, 0, 96)[i % 5] for i, k in enumerate(keys)}
+    caps = [choice[X.Solver.shape_class(sd)] for sd in pb.subs]
+    s.set_tile_caps(caps)
+    assert np.array_equal(s.tile_caps(), caps)
+    losses, g = s.grad()
+    terms, g_ref = Oracle(pb).grad(pb.packed_params())
+    assert_losses(losses, terms)
+    assert_grads(g, g_ref, pb)
+    s.close()
 
 
 @pytest.mark.parametrize("order", [0, 2])
