@@ -361,6 +361,12 @@ def run_reference(args):
         "wall_s": time.perf_counter() - t_start}))
 
 
+# Tuned options recorded on this machine's GB300 (bench.py --write-tune-cache),
+# per problem signature and shape class; problems not in it are tuned live.
+TUNE_CACHE = os.path.join(ROOT, "paper_2104_10013_gb300", "tuning_gb300.json")
+_tune_args = {"cache": TUNE_CACHE if os.path.exists(TUNE_CACHE) else None, "write": False}
+
+
 def tuned_solver(X, pb, autotune, opts=None):
     """A Solver with profile_phases on (the phase timer gives the jet
     kernel's device time) and, unless disabled, autotuned tile options."""
@@ -369,8 +375,9 @@ def tuned_solver(X, pb, autotune, opts=None):
     tune = None
     if autotune:
         t0 = time.perf_counter()
-        tune = s.autotune(steps=3)
+        tune = dict(s.autotune(steps=3, **_tune_args))
         tune["seconds"] = time.perf_counter() - t0
+        tune["cache"] = _tune_args["cache"] is not None and tune["seconds"] < 1.0
         s.set_options(profile_phases=1)
     return s, tune
 
@@ -446,6 +453,7 @@ def adam_steps_per_s(torch, X, stream, n=320):
     problem stays in L2 as it does in a training run."""
     pb, desc = workload("c1")
     s = X.Solver(pb)
+    tune = s.autotune(steps=5, **_tune_args)   # small sub-tiles spread the 4,000 points over the SMs
     s.set_options(profile_phases=0)
     s.step(64, losses=None, stream=stream.cuda_stream)
     s.sync(stream.cuda_stream)
@@ -460,6 +468,7 @@ def adam_steps_per_s(torch, X, stream, n=320):
     s.close()
     return {"workload": desc, "value": n / (ms / 1e3), "unit": "Adam steps/s", "steps": n,
             "ms_per_step": ms / n, "residual_pts_per_s": pb.n_res * n / (ms / 1e3),
+            "options": tune.get("options"), "class_caps": tune.get("class_caps"),
             "note": "steps back to back in one xpinn_step call, graphs of 16 steps; L2 not flushed"}
 
 
@@ -483,7 +492,11 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--serving-max-query", type=int, default=1000000)
+    ap.add_argument("--write-tune-cache", default=None,
+                    help="time every workload's options and record them in this JSON file")
     args = ap.parse_args()
+    if args.write_tune_cache:
+        _tune_args.update(cache=args.write_tune_cache, write=True)
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)

@@ -370,12 +370,14 @@ int xpinn_get_options(xpinn_handle h, xpinn_options* opt);
 int xpinn_set_options(xpinn_handle h, const xpinn_options* opt);
 
 /* Autotuner: times `steps` gradient passes (no parameter update) for each
- * candidate of points_per_thread {2, 1} x items_per_cta {2, 4, 8, 16} x
- * max_points_per_tile {0, 128, 64, 32} with the grouped schedule, keeps the
- * fastest, applies it and returns it in *best (and its median ms per pass
- * in *best_ms).  Candidates that do not fit shared memory are skipped, and
- * so are the rest once about 20 s have been spent (the best so far is kept).
- * Parameters, Adam state and step count are unchanged.  Synchronises. */
+ * candidate of threads_per_cta {256, 512, 128} x points_per_thread {2, 1} x
+ * items_per_cta {4, 8, 16, 2, 32} x max_points_per_tile {0, 64, 128, 32}
+ * with the grouped schedule, keeps the fastest, applies it and returns it in
+ * *best (and its median ms per pass in *best_ms).  The default comes first,
+ * then every change of one option from it, then the rest of the grid.
+ * Candidates that do not fit shared memory are skipped, and so are the rest
+ * once about 20 s have been spent (the best so far is kept).  Parameters,
+ * Adam state and step count are unchanged.  Synchronises. */
 int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* best_ms);
 
 /* Per-shape tuning: subdomains whose networks have the same widths,

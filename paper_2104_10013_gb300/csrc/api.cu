@@ -1945,9 +1945,17 @@ int xpinn_set_options(xpinn_handle h, const xpinn_options* opt) {
 namespace {
 // Median device time (ms) of `steps` gradient passes after two warm-up passes.
 float time_grads(xpinn_ctx* h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int steps) {
+  // warm-up: two passes, one when a pass takes more than 50 ms (long launches
+  // are stable after one, and the tuners' time budget buys more candidates)
   for (int w = 0; w < 2; ++w) {
+    ck(cudaEventRecord(e0, s), "event");
     enqueue_step(h, s, false, h->grads.p);
     h->host_slot += 1;
+    ck(cudaEventRecord(e1, s), "event");
+    ck(cudaEventSynchronize(e1), "event sync");
+    float ms = 0;
+    ck(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+    if (ms > 50.f) break;
   }
   std::vector<float> t;
   for (int i = 0; i < steps; ++i) {
@@ -2098,13 +2106,34 @@ int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* be
   auto elapsed_s = [&] {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   };
-  try {
-    for (int nt : {256, 512, 128})
+  // candidates: the default, then every change of one option from it, then
+  // the rest of the grid (large problems only get through the first ones)
+  struct Cand {
+    int nt, pt, ipc, cap;
+  };
+  std::vector<Cand> cands;
+  const Cand def{256, 2, 4, 0};
+  auto add = [&](Cand c) {
+    if (c.nt == 512 && c.pt != 1) return;
+    for (const Cand& o : cands)
+      if (o.nt == c.nt && o.pt == c.pt && o.ipc == c.ipc && o.cap == c.cap) return;
+    cands.push_back(c);
+  };
+  add(def);
+  for (int ipc : {8, 16, 2, 32}) add({def.nt, def.pt, ipc, def.cap});
+  add({256, 1, def.ipc, def.cap});
+  add({512, 1, def.ipc, def.cap});
+  add({128, 2, def.ipc, def.cap});
+  add({128, 1, def.ipc, def.cap});
+  for (int cap : {64, 128, 32}) add({def.nt, def.pt, def.ipc, cap});
+  for (int nt : {256, 512, 128})
     for (int pt : {2, 1})
       for (int ipc : {4, 8, 16, 2, 32})
-        for (int cap : {0, 64, 128, 32}) {
+        for (int cap : {0, 64, 128, 32}) add({nt, pt, ipc, cap});
+  try {
+    for (const Cand& cd : cands) {
+          const int nt = cd.nt, pt = cd.pt, ipc = cd.ipc, cap = cd.cap;
           if (elapsed_s() > 20.0) continue;   // time budget: keep the best so far
-          if (nt == 512 && pt != 1) continue;
           xpinn_options c = orig;
           c.schedule = 0;
           c.points_per_thread = pt;
@@ -2122,7 +2151,7 @@ int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* be
             win_ms = med;
             win = c;
           }
-        }
+    }
   } catch (...) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -460,11 +460,12 @@ class Solver:
         caps = None if caps is None else np.ascontiguousarray(np.asarray(caps, np.int32))
         _check(self.lib.xpinn_set_tile_caps(self.h, None if caps is None else caps.ctypes.data))
 
-    def autotune(self, steps=5, cache=None, shapes=True) -> dict:
+    def autotune(self, steps=5, cache=None, shapes=True, write=True) -> dict:
         """Pick tile shapes by timing: the launch options (xpinn_autotune),
         then a sub-tile cap per shape class (xpinn_autotune_shapes).  With
-        `cache` (a JSON file path) reuse and record the choice: the options
-        per problem signature, the caps per shape class."""
+        `cache` (a JSON file path) reuse a recorded choice for this problem
+        signature, else time and (with `write`) record it: the options per
+        problem signature, the caps per shape class."""
         import json
         key = self.signature()
         db = {}
@@ -490,7 +491,7 @@ class Solver:
             caps = self.tile_caps()
             rec["class_caps"] = {self.shape_class(sd): int(c) for sd, c in zip(self.pb.subs, caps)}
             rec["ms_shapes"] = ms2.value
-        if cache:
+        if cache and write:
             db[key] = rec
             with open(cache, "w") as f:
                 json.dump(db, f, indent=1)
