@@ -369,14 +369,16 @@ typedef struct {
 int xpinn_get_options(xpinn_handle h, xpinn_options* opt);
 int xpinn_set_options(xpinn_handle h, const xpinn_options* opt);
 
-/* Autotuner: times `steps` gradient passes (no parameter update) for each
- * candidate of threads_per_cta {256, 512, 128} x points_per_thread {2, 1} x
- * items_per_cta {4, 8, 16, 2, 32} x max_points_per_tile {0, 64, 128, 32}
- * with the grouped schedule, keeps the fastest, applies it and returns it in
- * *best (and its median ms per pass in *best_ms).  The default comes first,
- * then every change of one option from it, then the rest of the grid.
- * Candidates that do not fit shared memory are skipped, and so are the rest
- * once about 20 s have been spent (the best so far is kept).  Parameters,
+/* Autotuner: times gradient passes (no parameter update, grouped schedule)
+ * of candidate launch options and applies the fastest, returned in *best
+ * (its median ms per pass in *best_ms).  Candidates: the grid of CTA shapes
+ * (threads_per_cta x points_per_thread: 256x2, 256x1, 512x1, 128x2, 128x1)
+ * x items_per_cta {4, 8, 16, 2, 32} without a tile cap, the default (256x2,
+ * 4) first, then every change of one of the two, then the remaining pairs;
+ * then max_points_per_tile {64, 128, 32} on the best pair.  Each candidate
+ * takes the median of `steps` passes (one pass when a pass lasts more than
+ * 200 ms); candidates that do not fit shared memory are skipped, and the
+ * search stops after about 30 s, keeping the best so far.  Parameters,
  * Adam state and step count are unchanged.  Synchronises. */
 int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* best_ms);
 

@@ -2106,51 +2106,59 @@ int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* be
   auto elapsed_s = [&] {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   };
-  // candidates: the default, then every change of one option from it, then
-  // the rest of the grid (large problems only get through the first ones)
+  // The grid of CTA shapes (threads, points per thread) x items per CTA,
+  // without a tile cap: the default first, then every change of one of the
+  // two from it, then the remaining pairs; then the tile caps on the best
+  // pair.  Passes longer than 200 ms are timed once per candidate (their
+  // spread is small); the search stops after about 30 s, keeping the best.
   struct Cand {
     int nt, pt, ipc, cap;
   };
-  std::vector<Cand> cands;
-  const Cand def{256, 2, 4, 0};
-  auto add = [&](Cand c) {
-    if (c.nt == 512 && c.pt != 1) return;
-    for (const Cand& o : cands)
-      if (o.nt == c.nt && o.pt == c.pt && o.ipc == c.ipc && o.cap == c.cap) return;
-    cands.push_back(c);
+  const std::vector<std::pair<int, int>> shapes = {{256, 2}, {256, 1}, {512, 1}, {128, 2}, {128, 1}};
+  const std::vector<int> ipcs = {4, 8, 16, 2, 32};
+  std::vector<Cand> grid;
+  for (size_t a = 0; a < shapes.size(); ++a)
+    for (size_t b = 0; b < ipcs.size(); ++b)
+      if (a == 0 || b == 0) grid.push_back({shapes[a].first, shapes[a].second, ipcs[b], 0});
+  for (size_t a = 1; a < shapes.size(); ++a)
+    for (size_t b = 1; b < ipcs.size(); ++b) grid.push_back({shapes[a].first, shapes[a].second, ipcs[b], 0});
+  int n_steps = steps;
+  Cand best_c = grid[0];
+  float best_t = 3.4e38f;
+  auto run = [&](const Cand& cd) {
+    xpinn_options c = orig;
+    c.schedule = 0;
+    c.points_per_thread = cd.pt;
+    c.items_per_cta = cd.ipc;
+    c.max_points_per_tile = cd.cap;
+    c.threads_per_cta = cd.nt;
+    c.profile_phases = 0;
+    try {
+      apply_options(h, c);
+    } catch (const Error&) {
+      return;   // does not fit: skip
+    }
+    const float med = time_grads(h, s, e0, e1, n_steps);
+    if (med > 200.f) n_steps = 1;
+    if (med < win_ms) {
+      win_ms = med;
+      win = c;
+    }
+    if (med < best_t) {
+      best_t = med;
+      best_c = cd;
+    }
   };
-  add(def);
-  for (int ipc : {8, 16, 2, 32}) add({def.nt, def.pt, ipc, def.cap});
-  add({256, 1, def.ipc, def.cap});
-  add({512, 1, def.ipc, def.cap});
-  add({128, 2, def.ipc, def.cap});
-  add({128, 1, def.ipc, def.cap});
-  for (int cap : {64, 128, 32}) add({def.nt, def.pt, def.ipc, cap});
-  for (int nt : {256, 512, 128})
-    for (int pt : {2, 1})
-      for (int ipc : {4, 8, 16, 2, 32})
-        for (int cap : {0, 64, 128, 32}) add({nt, pt, ipc, cap});
   try {
-    for (const Cand& cd : cands) {
-          const int nt = cd.nt, pt = cd.pt, ipc = cd.ipc, cap = cd.cap;
-          if (elapsed_s() > 20.0) continue;   // time budget: keep the best so far
-          xpinn_options c = orig;
-          c.schedule = 0;
-          c.points_per_thread = pt;
-          c.items_per_cta = ipc;
-          c.max_points_per_tile = cap;
-          c.threads_per_cta = nt;
-          c.profile_phases = 0;
-          try {
-            apply_options(h, c);
-          } catch (const Error&) {
-            continue;   // does not fit: skip
-          }
-          const float med = time_grads(h, s, e0, e1, steps);
-          if (med < win_ms) {
-            win_ms = med;
-            win = c;
-          }
+    for (const Cand& cd : grid) {
+      if (elapsed_s() > 30.0) break;
+      run(cd);
+    }
+    for (int cap : {64, 128, 32}) {
+      if (elapsed_s() > 30.0) break;
+      Cand cd = best_c;
+      cd.cap = cap;
+      run(cd);
     }
   } catch (...) {
     cudaEventDestroy(e0);

@@ -559,7 +559,7 @@ class Server:
         xy = _f32(np.concatenate(xy_list))
         f = None if f_list is None else _f32(np.concatenate(f_list))
         losses = np.empty((n_steps, len(sel), N_TERMS), np.float32)
-        params = np.empty(sum(sv.pb.subs[q].n_params for q in sel), np.float32)
+        params = np.empty(sum(sv.pb.subs[q].n_params for q in sel if 0 <= q < sv.n_sub), np.float32)
         r = Request(kind=2, model=model, n=0, xy=xy.ctypes.data, out=None, n_steps=n_steps,
                     losses=losses.ctypes.data, n_sel=len(sel), sel=sel.ctypes.data, n_pts=counts.ctypes.data,
                     f=f.ctypes.data if f is not None else None, params=params.ctypes.data)

@@ -131,3 +131,24 @@ def test_fork_rejects_bad_requests(X):
     with pytest.raises(X.XpinnError):
         s.fork_step([9], xy[:1])                              # out of range
     s.close()
+
+
+def test_fork_edge_cases(X):
+    """Zero steps return the model's own parameters of the selection; a
+    selected subdomain given no residual points trains on its data and
+    interface terms only (its residual term is 0), against the oracle."""
+    pb = P.poisson_xpinn(n_res_range=(300, 1500), n_iface=64, n_bc=40)
+    s = X.Solver(pb)
+    offs = np.cumsum([0] + [sd.n_params for sd in pb.subs])
+    theta = s.get_params()
+    sel = [3, 12]
+    xy, f = request_points(pb, sel, [500, 0])
+    l0, p0 = s.fork_step(sel, xy, f, n_steps=0)
+    assert l0.shape == (0, 2, P.N_TERMS)
+    assert np.array_equal(p0, np.concatenate([theta[offs[q]:offs[q + 1]] for q in sel]))
+    l1, _ = s.fork_step(sel, xy, f, n_steps=1)
+    pb2 = with_points(pb, sel, xy, f)
+    terms, _ = Oracle(pb2).grad(pb2.packed_params(), subset=sel)
+    assert terms[1, 2] == 0 and l1[0, 1, 2] == 0
+    assert_scaled(l1[0], terms, RTOL_JET, "fork losses", axis=0)
+    s.close()

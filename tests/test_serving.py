@@ -106,6 +106,9 @@ def test_request_larger_than_budget_is_refused(X):
     assert e.value.code == -2
     t = srv.submit_eval(0, xy[:10] + 0.1, 0)
     assert srv.wait(t)["status"] == 0
+    with pytest.raises(X.XpinnError) as e:                     # a fork of a subdomain that does not exist
+        srv.submit_fork(0, [7], [np.zeros((10, 2), np.float32)])
+    assert e.value.code == -1
     srv.close()
 
 
