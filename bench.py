@@ -51,7 +51,14 @@ METRIC = "residual pts/s (jet fwd+bwd) grouped vs per-subdomain loop; query p50/
 # a reduced copy of the workload was captured and its traffic is scaled to the
 # full launch by residual points ("scaled_from"): the traffic is the saved
 # jets and the gradient slices, both in proportion to the points processed.
-TRAFFIC = {}
+TRAFFIC = {
+    # one launch of the reduced copy (160 subdomains, 4.8 M residual points):
+    # 0.976 GB read + 18.610 GB written; x16 to the full 76.8 M points
+    "c4": {"sha": "b8512c966cad9e1f", "scaled_from": "c4s", "scale": 16,
+           "options": {"points_per_thread": 1, "threads_per_cta": 256, "items_per_cta": 32,
+                       "max_points_per_tile": 0},
+           "bytes_per_launch": 16 * (976200192 + 18609841920)},
+}
 FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 partitions x 32)
 
 
@@ -396,10 +403,15 @@ def roofline(pb, jet_ms, n_sm, name, s):
     t = TRAFFIC.get(name)
     opts = s.options()
     traffic = None
+    traffic_note = None
     if t and t["sha"] == sha and all(opts.get(k) == v for k, v in t["options"].items()):
         traffic = t["bytes_per_launch"]
+        if "scaled_from" in t:
+            traffic_note = (f"DRAM bytes of one launch of the reduced workload '{t['scaled_from']}' "
+                            f"(same kernel and options) x {t['scale']}, the ratio of residual points")
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "xp::jet_step_kernel (exchange, residual, data and interface items)",
+            "traffic": traffic, "traffic_note": traffic_note,
+            "kernel": "xp::jet_step_kernel (exchange, residual, data and interface items)",
             "kernel_ms": jet_ms, "flop_per_launch": flops,
             "flop_per_point": "6 K M per residual point of every network (K jet components: 4 for the "
                               "u-network (Laplacian jets) and Burgers, 3 for the K-network; M = sum over "
