@@ -458,6 +458,71 @@ def extra_workload(torch, X, name, stream, flush, steps, loop_steps, n_sm):
     return out
 
 
+def eval_tensor_cores(torch, X, stream, flush, n_pts=1 << 20, reps=10):
+    """Routed evaluation (Eq. FSol) of the Kovasznay cPINN model (64
+    subdomains, 2->64x6->3) at n_pts uniform query points on the device,
+    derivative orders 0-2, the tensor-core kernel against the FP32 jet
+    kernel on the same handle, buffers and points.  Per order and path:
+    the whole xpinn_eval_ws call (route, plan, bucket, evaluation kernel,
+    gather) and the evaluation kernel alone, both CUDA-event medians over
+    `reps` calls with L2 flushed before each; the tensor-core kernel's
+    roofline is its algorithmic contraction FLOPs (2 K per point per weight of
+    the hidden-to-hidden layers) against the dense TF32 rate."""
+    pb, _ = workload("c3")
+    s = X.Solver(pb)
+    s.step(5, losses=None, stream=stream.cuda_stream)
+    s.set_options(profile_phases=1)
+    rng = np.random.default_rng(11)
+    xy = np.stack([rng.uniform(-0.5, 1.0, n_pts), rng.uniform(-0.5, 1.5, n_pts)], 1).astype(np.float32)
+    dxy = torch.from_numpy(xy).cuda()
+    m_h = sum(n.widths[k] * n.widths[k - 1] for n in pb.subs[0].nets for k in range(2, len(n.widths) - 1))
+    peaks = measured_peaks()
+    tf32 = peaks.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {"workload": "Kovasznay cPINN model, 64 subdomains 2->64x6->3 tanh, %d uniform query points, "
+                       "device buffers (xpinn_eval_ws)" % n_pts, "orders": {}}
+    for order in (0, 1, 2):
+        K = (1, 3, 5)[order]
+        ws = torch.empty(s.eval_workspace_size(n_pts, order), dtype=torch.uint8, device="cuda")
+        dout = torch.empty((n_pts, 3 * K), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        res = {}
+        for tc in (0, 1):
+            s.set_options(eval_tensor_cores=tc)
+            with torch.cuda.stream(stream):   # eval_ws runs on the current stream
+                for _ in range(3):
+                    s.eval_ws(0, dxy, order, dout, ws)
+            call_ms, kern_ms = [], []
+            for _ in range(reps):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                    e0.record(stream)
+                    s.eval_ws(0, dxy, order, dout, ws)
+                    e1.record(stream)
+                e1.synchronize()
+                call_ms.append(e0.elapsed_time(e1))
+                kern_ms.append(s.eval_kernel_ms())
+            s.sync(stream.cuda_stream)
+            c, k = float(np.median(call_ms)), float(np.median(kern_ms))
+            res["tensor_cores" if tc else "fp32_jet_kernel"] = {
+                "call_ms": c, "kernel_ms": k, "pts_per_s": n_pts / (c / 1e3)}
+        t = res["tensor_cores"]
+        flops = 2.0 * K * m_h * n_pts
+        t["roofline"] = {"bound": "tensor", "achieved": flops / (t["kernel_ms"] / 1e3) / 1e12, "peak": tf32,
+                         "unit": "TFLOP/s", "frac": flops / (t["kernel_ms"] / 1e3) / 1e12 / tf32,
+                         "traffic": None,
+                         "peak_note": "dense TF32: measured bf16 burst x 1.1/2.25 (nominal ratio); the "
+                                      "kernel issues three TF32 products per term (hi/lo split), so its "
+                                      "algorithmic fraction is at most 1/3"}
+        res["kernel_speedup"] = res["fp32_jet_kernel"]["kernel_ms"] / t["kernel_ms"]
+        res["call_speedup"] = res["fp32_jet_kernel"]["call_ms"] / t["call_ms"]
+        out["orders"][str(order)] = res
+    s.set_options(eval_tensor_cores=0)
+    s.close()
+    return out
+
+
 def adam_steps_per_s(torch, X, stream, n=320):
     """Adam steps per second of the Burgers cPINN configuration (4 x 1000
     residual points, launch-bound): n training steps back to back in one
@@ -619,6 +684,7 @@ def main():
             "c3": extra_workload(torch, X, "c3", stream, flush, 5, 0 if args.no_loop else 3, n_sm),
         }
         out["adam_steps"] = adam_steps_per_s(torch, X, stream)
+        out["eval_tensor_cores"] = eval_tensor_cores(torch, X, stream, flush)
 
     if not args.no_serving:
         out["serving"] = serving(X, args.serving_requests, args.serving_max_query)

@@ -364,6 +364,16 @@ typedef struct {
                                interface exchange wait for one item more than
                                exists, so it gives up after about 1 s and the
                                call returns XPINN_ERR_TIMEOUT; 0 (default) off */
+  int32_t eval_tensor_cores; /* 1: routed evaluations (xpinn_eval, xpinn_eval_ws,
+                               the server's queries) of a model whose
+                               subdomains each have one network with input
+                               (x, y), identity output, at least two hidden
+                               layers, all of one width 32, 64 or 80, run the
+                               hidden-to-hidden contractions on the tensor
+                               cores (tcgen05, three TF32 products over a hi/lo
+                               split of both operands, FP32 accumulation);
+                               other models keep the FP32 jet kernel.  0: the
+                               jet kernel for every model */
 } xpinn_options;
 
 int xpinn_get_options(xpinn_handle h, xpinn_options* opt);
@@ -405,6 +415,14 @@ int xpinn_set_tile_caps(xpinn_handle h, const int32_t* caps);   /* [n_sub] (0 or
  * exchange too), ms[2] jet kernel launch(es), ms[3] reduction and Adam.
  * Requires profile_phases = 1; waits for that step to finish. */
 int xpinn_phase_times(xpinn_handle h, float* ms);
+
+/* Device time in milliseconds of the evaluation kernel (the jet kernel, or
+ * the tensor-core kernel under eval_tensor_cores) of the most recent routed
+ * evaluation (xpinn_eval, xpinn_eval_ws) made with profile_phases = 1, from
+ * CUDA events recorded around its launch on the call's stream (none while
+ * the stream is being captured).  Waits for that kernel.  Errors: INVALID if
+ * no evaluation has been timed. */
+int xpinn_eval_kernel_time(xpinn_handle h, float* ms);
 
 /* Interface exchange buffer after the last grad/step: for every interface
  * (in order), every point, side 0 (q) then side 1 (q_plus): the solution

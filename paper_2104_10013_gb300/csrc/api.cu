@@ -23,6 +23,7 @@
 #include <string>
 #include <vector>
 
+#include "eval_tc.h"
 #include "xpinn_dev.cuh"
 
 namespace xp {
@@ -192,6 +193,19 @@ struct xpinn_ctx {
   // derivative orders 0, 1, 2 ([3][n_sub]); rebuilt with the plan
   DevBuf<EvalProto> e_proto;
   std::vector<int> e_min_chunk;  // [3][n_models]: smallest chunk of each model and order
+  // tensor-core evaluation (eval_tc.cu, option eval_tensor_cores): per model
+  // the hidden width its networks qualify with (0: the jet kernel evaluates
+  // it), and the weight images, rebuilt from params like wimg
+  std::vector<int> tc_w;         // [n_models], empty until first needed
+  DevBuf<float> tc_img;
+  DevBuf<int64_t> tc_off;        // [n_sub] first float of a subdomain's images, -1: none
+  DevBuf<TcPack> tc_pack_d;
+  int n_tc_pack = 0;
+  bool tc_stale = true;
+  // device time of the evaluation kernel of the last routed evaluation
+  // (profile_phases): events around its launch
+  cudaEvent_t eval_ev[2] = {};
+  bool eval_timed = false;
   // plan
   Plan plan;
   StepArgs base{};
@@ -199,7 +213,7 @@ struct xpinn_ctx {
   int n_sm = 0, grid = 0;
   int ring_cap = 256;
   int host_t = 0, host_slot = 0;
-  xpinn_options opt{0, 1, 4, 2, 0, 0, 256, 0};
+  xpinn_options opt{0, 1, 4, 2, 0, 0, 256, 0, 0};
   int device = 0;
   cudaEvent_t ev[5] = {};
   cudaStream_t cap_stream = nullptr;
@@ -215,6 +229,8 @@ struct xpinn_ctx {
     if (graph_multi) cudaGraphExecDestroy(graph_multi);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    for (auto& e : eval_ev)
       if (e) cudaEventDestroy(e);
   }
 
@@ -791,10 +807,65 @@ void eval_items_for(xpinn_ctx* h, int q, int net, int K, int64_t first, int64_t 
 // trip; every buffer is a slice of the workspace, sized for the worst case of
 // MAXS = 4 memberships per point (a point at a corner of four boxes).
 // ---------------------------------------------------------------------------
+// Events around the evaluation kernel of a routed evaluation (profile_phases
+// on, stream not being captured); `i` 0 before the launch, 1 after.
+void eval_mark(xpinn_ctx* h, int i, cudaStream_t s) {
+  if (!h->opt.profile_phases) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ck(cudaStreamIsCapturing(s, &cs), "capture status");
+  if (cs != cudaStreamCaptureStatusNone) return;
+  if (!h->eval_ev[i]) ck(cudaEventCreate(&h->eval_ev[i]), "cudaEventCreate");
+  ck(cudaEventRecord(h->eval_ev[i], s), "event");
+  h->eval_timed = i == 1;
+}
+
+// Hidden width W with which the networks of model `model` qualify for the
+// tensor-core evaluation (eval_tc.h), or 0; on first use also the images'
+// layout and pack list of every qualifying model.
+int tc_width(xpinn_ctx* h, int model) {
+  if (!h->opt.eval_tensor_cores) return 0;
+  if (h->tc_w.empty()) {
+    const int n_models = h->n_sub / h->spm;
+    h->tc_w.assign(n_models, 0);
+    std::vector<int64_t> off(h->n_sub, -1);
+    std::vector<TcPack> pk;
+    int64_t n_img = 0;
+    for (int m = 0; m < n_models; ++m) {
+      int W = -1;
+      for (int q = m * h->spm; q < (m + 1) * h->spm && W != 0; ++q) {
+        const SubDev& sd = h->subs[q];
+        const NetDev& nd = sd.net[0];
+        bool ok = sd.n_nets == 1 && nd.L >= 3 && nd.w[0] == 2 && nd.out_act == XPINN_ACT_IDENTITY &&
+                  nd.w[nd.L] <= XPINN_MAX_OUT && eval_tc_width_ok(nd.w[1]) && (W < 0 || nd.w[1] == W);
+        for (int k = 1; k < nd.L && ok; ++k) ok = nd.w[k] == nd.w[1];
+        W = ok ? nd.w[1] : 0;
+      }
+      if (W <= 0) continue;
+      h->tc_w[m] = W;
+      for (int q = m * h->spm; q < (m + 1) * h->spm; ++q) {
+        const SubDev& sd = h->subs[q];
+        const NetDev& nd = sd.net[0];
+        off[q] = n_img;
+        for (int k = 2; k < nd.L; ++k) {
+          pk.push_back(TcPack{sd.poff + nd.off[k], n_img, W, W});
+          n_img += 2 * (int64_t)W * W;
+        }
+      }
+    }
+    h->tc_img.alloc((size_t)std::max<int64_t>(n_img, 4));
+    h->tc_off.upload(off.data(), off.size());
+    h->tc_pack_d.upload(pk.data(), pk.size());
+    h->n_tc_pack = (int)pk.size();
+    h->tc_stale = true;
+    ck(eval_tc_configure(), "cudaFuncSetAttribute(tensor-core evaluation)");
+  }
+  return h->tc_w[model];
+}
+
 constexpr int EVAL_MAXS = 4;
 
 struct EvalWs {
-  size_t pts, S, memb, pos, counts, epts, escale, eout, out, items, n_items, total;
+  size_t pts, S, memb, pos, counts, epts, escale, eout, out, items, n_items, counter, total;
   int max_items;
 };
 
@@ -821,6 +892,7 @@ EvalWs eval_ws_layout(const xpinn_ctx* h, int model, int64_t n, int order) {
   take(w.out, sizeof(float) * std::max<int64_t>(n, 1) * row);
   take(w.items, sizeof(Item) * (size_t)w.max_items);
   take(w.n_items, sizeof(int));
+  take(w.counter, sizeof(int));
   w.total = o;
   return w;
 }
@@ -841,11 +913,41 @@ void eval_enqueue(xpinn_ctx* h, int model, const float2* pts, int64_t n, int ord
   float* eout = reinterpret_cast<float*>(ws + L.eout);
   Item* items = reinterpret_cast<Item*>(ws + L.items);
   int* n_items = reinterpret_cast<int*>(ws + L.n_items);
+  int* counter = reinterpret_cast<int*>(ws + L.counter);
   ck(cudaMemsetAsync(counts, 0, sizeof(int) * 2 * nq, s), "memset");
   launch_route(pts, n, h->subs_d.p, q0, nq, S, memb, counts, h->err_d.p, h->poly.p, h->n_poly, s);
   launch_eval_plan(counts, nq, h->e_proto.p + (size_t)order * h->n_sub + q0, q0, row, counts + nq, items,
                    n_items, L.max_items, h->err_d.p, s);
   launch_bucket(pts, n, S, memb, counts + nq, pos, epts, escale, s);
+  const int W = tc_width(h, model);
+  if (W) {
+    if (h->tc_stale) {
+      launch_pack_tc(h->params.p, h->tc_pack_d.p, h->n_tc_pack, h->tc_img.p, s);
+      h->tc_stale = false;
+    }
+    TcArgs t{};
+    t.items = items;
+    t.n_items = L.max_items;
+    t.n_items_dev = n_items;
+    t.counter = counter;
+    t.subs = h->subs_d.p;
+    t.params = h->params.p;
+    t.img = h->tc_img.p;
+    t.img_off = h->tc_off.p;
+    t.pts = epts;
+    t.scale = escale;
+    t.out = eout;
+    t.dout = row;
+    t.err = h->err_d.p;
+    const int per_sm = eval_tc_ctas_per_sm(W, K);
+    ck(cudaMemsetAsync(t.counter, 0, sizeof(int), s), "memset");
+    eval_mark(h, 0, s);
+    launch_eval_tc(W, K, t, std::min<int>(h->n_sm * per_sm, L.max_items), s);
+    eval_mark(h, 1, s);
+    launch_gather(n, row, S, pos, eout, out, s);
+    ck(cudaGetLastError(), "evaluation launches");
+    return;
+  }
   if (h->img_stale) {
     pack_images(h, s);
     h->img_stale = false;
@@ -855,14 +957,15 @@ void eval_enqueue(xpinn_ctx* h, int model, const float2* pts, int64_t n, int ord
   a.n_items = L.max_items;
   a.n_items_dev = n_items;
   a.item_base = 0;
-  h->e_counter.ensure(1);
-  a.counter = h->e_counter.p;
+  a.counter = counter;
   a.eval_pts = epts;
   a.eval_out = eout;
   a.eval_dout = row;
   a.eval_scale = escale;
   ck(cudaMemsetAsync(a.counter, 0, sizeof(int), s), "memset");
+  eval_mark(h, 0, s);
   launch_jet_step(a, std::min<int>(h->grid, L.max_items), h->smem, s);
+  eval_mark(h, 1, s);
   launch_gather(n, row, S, pos, eout, out, s);
   ck(cudaGetLastError(), "evaluation launches");
 }
@@ -1480,7 +1583,7 @@ int xpinn_set_params(xpinn_handle h, const float* src, int64_t n, void* stream) 
   if (!h || !src || n != h->n_params) fail(XPINN_ERR_INVALID, "bad arguments");
   DeviceGuard dg(h);
   copy_in(h->params.p, src, n * sizeof(float), (cudaStream_t)stream);
-  h->img_stale = true;
+  h->img_stale = h->tc_stale = true;
   API_END
 }
 
@@ -1554,7 +1657,7 @@ int xpinn_step(xpinn_handle h, int32_t n_steps, float* losses, void* stream) {
     }
     done += chunk;
   }
-  h->img_stale = true;
+  h->img_stale = h->tc_stale = true;
   ck(cudaGetLastError(), "step");
   // Host losses: the call has synchronised anyway, so the status word is
   // read now.  NULL or device losses: the call stays asynchronous and a
@@ -1693,7 +1796,7 @@ int xpinn_step_end(xpinn_handle h, float* losses, void* stream) {
   enqueue_step(h, s, true, nullptr, 2);
   h->host_slot += 1;
   h->host_t += 1;
-  h->img_stale = true;
+  h->img_stale = h->tc_stale = true;
   if (losses) {
     const size_t row = (size_t)h->n_sub * XPINN_N_TERMS;
     copy_out(losses, h->loss_ring.p + (size_t)(h->host_slot % h->ring_cap) * row, sizeof(float) * row, s);
@@ -1911,7 +2014,7 @@ int xpinn_set_state(xpinn_handle h, const void* blob, size_t n) {
   ck(cudaMemcpy(h->params.p, p, sizeof(float) * h->n_params, cudaMemcpyHostToDevice), "state");
   ck(cudaMemcpy(h->m.p, p + h->n_params, sizeof(float) * h->n_params, cudaMemcpyHostToDevice), "state");
   ck(cudaMemcpy(h->v.p, p + 2 * h->n_params, sizeof(float) * h->n_params, cudaMemcpyHostToDevice), "state");
-  h->img_stale = true;
+  h->img_stale = h->tc_stale = true;
   ck(cudaMemcpy(h->step_t(), &hd.step_t, sizeof(int), cudaMemcpyHostToDevice), "state");
   h->host_t = hd.step_t;
   API_END
@@ -1933,7 +2036,8 @@ int xpinn_set_options(xpinn_handle h, const xpinn_options* opt) {
       opt->profile_phases > 1 || opt->max_points_per_tile < 0 ||
       (opt->threads_per_cta != 0 && opt->threads_per_cta != 128 && opt->threads_per_cta != 256 &&
        opt->threads_per_cta != 512) || opt->inject_fault < 0 || opt->inject_fault > 1 ||
-      (opt->threads_per_cta == 512 && opt->points_per_thread != 1))
+      (opt->threads_per_cta == 512 && opt->points_per_thread != 1) || opt->eval_tensor_cores < 0 ||
+      opt->eval_tensor_cores > 1)
     fail(XPINN_ERR_INVALID, "bad options");
   ck(cudaDeviceSynchronize(), "sync");
   apply_options(h, *opt);
@@ -2186,6 +2290,16 @@ int xpinn_phase_times(xpinn_handle h, float* ms) {
   if (!h->opt.profile_phases || !h->ev[0]) fail(XPINN_ERR_INVALID, "profile_phases is off");
   ck(cudaEventSynchronize(h->ev[4]), "event sync");
   for (int i = 0; i < 4; ++i) ck(cudaEventElapsedTime(ms + i, h->ev[i], h->ev[i + 1]), "elapsed");
+  API_END
+}
+
+int xpinn_eval_kernel_time(xpinn_handle h, float* ms) {
+  API_BEGIN
+  if (!h || !ms) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  if (!h->eval_timed) fail(XPINN_ERR_INVALID, "no routed evaluation timed (profile_phases off)");
+  ck(cudaEventSynchronize(h->eval_ev[1]), "event sync");
+  ck(cudaEventElapsedTime(ms, h->eval_ev[0], h->eval_ev[1]), "elapsed");
   API_END
 }
 

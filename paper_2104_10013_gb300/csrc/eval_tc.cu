@@ -1,0 +1,426 @@
+// Evaluation jets on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Forward jets of a network (Sec. 3) at query points for the networks
+// eval_tc.h describes: the point-by-width contraction of every
+// hidden-to-hidden layer runs as tcgen05.mma kind::tf32 in three passes over a
+// hi/lo split of both operands (A_hi B_hi + A_hi B_lo + A_lo B_hi), hi and lo
+// both rounded to nearest tf32 (the tensor cores would truncate fp32 inputs),
+// so each operand is represented to 2^-22 and the dropped lo x lo term is
+// below 2^-22 of a product.  The tf32 products are exact; hi x hi accumulates
+// in one fp32 accumulator in tensor memory and the two cross terms in a second
+// one, summed in the epilogue, so that the accumulation rounding of the cross
+// terms stays at their own scale (about 2^-11 of the main term): with one
+// accumulator the 3-pass sum erred up to 1.3e-5 of the jet scale on a width-80
+// sin network with trained slopes, in emulation and on the GPU alike.  The first layer (two
+// inputs) and the output layer (identity, at most three outputs) stay on the
+// FP32 pipes.
+//
+// Tile: 128 rows = the MMA's M, one thread and one tensor-memory lane per row,
+// a row per (point, jet component): KR = 1, 4 or 8 rows per point for 1, 3 or
+// 5 components (u; u, u_x, u_y; u, u_x, u_y, u_xx, u_yy), padding rows held at
+// zero, so 128, 32 or 16 points per tile.  Per hidden layer: A = the
+// activation rows H [128][W] and B = W^k [W][W], both K-major in shared memory
+// in the no-swizzle canonical layout (core matrices of 8 rows x 16 bytes),
+// D = Z [128 lanes][W columns] in tensor memory.  The epilogue reads a row of
+// D per thread (tcgen05.ld); the value rows publish their pre-activations, all
+// 128 threads evaluate Phi, Phi', Phi'' once per (point, neuron), and every
+// row applies the jet rule
+//   h_0 = Phi(v_0), h_i = Phi'(v_0) v_i, h_ii = Phi'(v_0) v_ii + Phi''(v_0) v_i^2
+// (v = s z, s the layer's slope), taking v_i of its own point by a warp
+// shuffle (a point's rows share a warp).  The rows of h are the next A.
+// Weight images (hi and lo, built by pack_tc_kernel) come by one bulk copy
+// per layer into one of two buffers, the copy of layer k + 2 in flight while
+// layer k's epilogue runs.  Every wait is bounded; a wait that gives up sets
+// the error word, the launch stops taking items, frees its tensor memory and
+// ends.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "eval_tc.h"
+#include "jet_step.cuh"
+
+namespace xp {
+
+namespace {
+
+constexpr int TC_ROWS = 128;
+constexpr int TC_A_LBO = TC_ROWS * 16;   // bytes between K-adjacent core matrices of A
+
+template <int W, int KR>
+struct TcSmem {
+  static constexpr int TP = TC_ROWS / KR;          // points per tile
+  static constexpr int A = TC_ROWS * W;            // floats of one A image (hi or lo)
+  static constexpr int B = 2 * W * W;              // floats of one weight buffer (hi, lo)
+  static constexpr int Z = KR > 1 ? W * TP : 0;    // floats of the shared activation table
+  static constexpr int floats = 2 * A + 2 * B + 3 * Z + 2 * TP;
+  // tensor-memory columns: the main accumulator (hi x hi) at column 0, the
+  // cross terms (hi x lo + lo x hi) at column COLS / 2
+  static constexpr int COLS = W <= 32 ? 64 : (W <= 64 ? 128 : 256);
+};
+
+constexpr int kr_of(int K) { return K == 1 ? 1 : (K == 3 ? 4 : 8); }
+
+// kind::tf32, D f32, A and B tf32, both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t tc_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+}
+
+// no-swizzle K-major shared-memory descriptor: lbo = bytes between core
+// matrices adjacent in K, sbo = bytes between 8-row groups
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// x rounded to the nearest tf32 value (10 explicit mantissa bits; halfway
+// cases away from zero) by integer arithmetic on the fp32 bit pattern; the
+// tensor cores then read it exactly.
+__device__ __forceinline__ float tf32_rna(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// hi/lo split: x = hi + lo + e with hi = rna(x), lo = rna(x - hi) and
+// |e| <= 2^-22 |x| (x - hi is exact in fp32 and |x - hi| <= 2^-11 |x|)
+__device__ __forceinline__ float2 tf32_split(float x) {
+  const float hi = tf32_rna(x);
+  return make_float2(hi, tf32_rna(x - hi));
+}
+
+// A element (row r, column j): 8-row groups 128 bytes apart, K-adjacent core
+// matrices TC_A_LBO bytes apart, so the 16-byte chunks of a column group sit
+// row after row (conflict-free across a warp).
+__device__ __forceinline__ int a_off(int r, int j) { return (j >> 2) * (TC_A_LBO / 4) + r * 4 + (j & 3); }
+
+// Loads 16 columns of this thread's tensor-memory lane (no wait).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// Ties registers loaded from tensor memory to the wait before it: no use of
+// them moves above the wait.
+__device__ __forceinline__ void tmem_fence_regs8(uint32_t* v) {
+  asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]));
+}
+
+// This thread's row of Z = the main accumulator (columns of `main`) plus the
+// cross-term accumulator (columns of `cross`), columns 0..W-1, into z.  The
+// cross terms (about 2^-11 of the main term) accumulate apart, so that their
+// accumulation rounding stays at that scale.
+template <int W>
+__device__ __forceinline__ void tmem_row(uint32_t main, uint32_t cross, float (&z)[W]) {
+  uint32_t v[W], u[W];
+#pragma unroll
+  for (int c0 = 0; c0 < W; c0 += 16) {
+    tmem_ld16(main + (uint32_t)c0, v + c0);
+    tmem_ld16(cross + (uint32_t)c0, u + c0);
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c0 = 0; c0 < W; c0 += 8) {
+    tmem_fence_regs8(v + c0);
+    tmem_fence_regs8(u + c0);
+  }
+#pragma unroll
+  for (int i = 0; i < W; ++i) z[i] = __uint_as_float(v[i]) + __uint_as_float(u[i]);
+}
+
+// The jet rule of the layer's activation on this thread's row (component c
+// of point p): z (without the bias) in, h out in z and in the A images.
+template <int W, int KR>
+__device__ __forceinline__ void jet_rows(const Act& act, const float* __restrict__ bias, float (&z)[W], int r,
+                                         int p, int c, int lane, bool valid, float* Ahi, float* Alo, float* Zs,
+                                         float2* Ds) {
+  constexpr int TP = TC_ROWS / KR;
+  if constexpr (KR == 1) {
+#pragma unroll
+    for (int n = 0; n < W; ++n) {
+      float d0, d1, d2, d3;
+      phi_derivs(act.kind, act.s * (z[n] + __ldg(bias + n)), d0, d1, d2, d3);
+      z[n] = valid ? d0 : 0.f;
+    }
+  } else {
+    if (c == 0) {
+#pragma unroll
+      for (int n = 0; n < W; ++n) Zs[n * TP + p] = z[n] + __ldg(bias + n);
+    }
+    __syncthreads();
+    for (int e = r; e < W * TP; e += TC_ROWS) {
+      float d0, d1, d2, d3;
+      phi_derivs(act.kind, act.s * Zs[e], d0, d1, d2, d3);
+      Zs[e] = d0;
+      Ds[e] = make_float2(d1, d2);
+    }
+    __syncthreads();
+    // second-derivative rows pair with the first-derivative row of their
+    // direction (component 3 with 1, 4 with 2)
+    const int src = lane - c + (c >= 3 ? c - 2 : 0);
+#pragma unroll
+    for (int n = 0; n < W; ++n) {
+      const float vc = act.s * z[n];
+      const float vi = act.s * __shfl_sync(0xffffffffu, z[n], src);
+      const float2 d = Ds[n * TP + p];
+      float h = c == 0 ? Zs[n * TP + p] : d.x * vc;
+      if (c >= 3) h = fmaf(d.y * vi, vi, h);
+      z[n] = valid ? h : 0.f;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < W; j += 4) {
+    const float2 s0 = tf32_split(z[j]), s1 = tf32_split(z[j + 1]), s2 = tf32_split(z[j + 2]),
+                 s3 = tf32_split(z[j + 3]);
+    *reinterpret_cast<float4*>(Ahi + a_off(r, j)) = make_float4(s0.x, s1.x, s2.x, s3.x);
+    *reinterpret_cast<float4*>(Alo + a_off(r, j)) = make_float4(s0.y, s1.y, s2.y, s3.y);
+  }
+}
+
+template <int W, int KR>
+__global__ void __launch_bounds__(TC_ROWS, 1) eval_tc_kernel(TcArgs a) {
+  using S = TcSmem<W, KR>;
+  constexpr int TP = S::TP;
+  constexpr int K = KR == 1 ? 1 : (KR == 4 ? 3 : 5);
+  constexpr uint32_t IMG_BYTES = 4u * S::B;
+  extern __shared__ __align__(1024) float tsm[];
+  float* Ahi = tsm;
+  float* Alo = tsm + S::A;
+  float* Bbuf = tsm + 2 * S::A;   // buffer b at Bbuf + b * S::B
+  float* Zs = tsm + 2 * S::A + 2 * S::B;
+  float2* Ds = reinterpret_cast<float2*>(Zs + S::Z);
+  float2* sp = reinterpret_cast<float2*>(Zs + 3 * S::Z);
+  __shared__ __align__(8) uint64_t bars[3];   // weight buffers 0 and 1, MMA completion
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_item, s_stop;
+  const int r = threadIdx.x, lane = r & 31, warp = r >> 5;
+  const int p = r / KR, c = r % KR;
+  if (r == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(bars + i, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "n"(S::COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  const uint32_t t_warp = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's lanes
+  const uint32_t idesc = tc_idesc(W);
+  const uint32_t sa_hi = smem_u32(Ahi), sa_lo = smem_u32(Alo);
+  uint32_t wph = 0, mph = 0;
+  const int n_items = a.n_items_dev ? min(a.n_items, *a.n_items_dev) : a.n_items;
+  for (;;) {
+    // one thread decides, so that every thread leaves the loop together
+    if (r == 0) {
+      s_item = atomicAdd(a.counter, 1);
+      s_stop = *reinterpret_cast<volatile int*>(a.err) == XPINN_ERR_TIMEOUT;
+    }
+    __syncthreads();
+    const int ii = s_item;
+    const bool stop = s_stop != 0;
+    __syncthreads();
+    if (ii >= n_items || stop) break;
+    const Item it = a.items[ii];
+    const SubDev& sd = a.subs[it.q];
+    const NetDev& nd = sd.net[0];
+    const int L = nd.L;
+    const int64_t io = a.img_off[it.q];
+    bool ok = it.K[0] == K && it.K[1] == 0 && io >= 0 && L >= 3 && L <= MAXL && nd.w[0] == 2 &&
+              nd.w[L] >= 1 && nd.w[L] <= XPINN_MAX_OUT && nd.out_act == XPINN_ACT_IDENTITY;
+    for (int k = 1; k < L && ok; ++k) ok = nd.w[k] == W;
+    if (!ok) {
+      if (r == 0) atomicCAS(a.err, 0, XPINN_ERR_INVALID);
+      continue;
+    }
+    const float* prm = a.params + sd.poff;
+    const float* img = a.img + io;
+    const int D = nd.w[L];
+    for (int t0 = 0; t0 < it.n_pts; t0 += TP) {
+      const int nv = min(TP, it.n_pts - t0);
+      const bool valid = p < nv && c < K;
+      // the first two hidden-to-hidden layers' images (every earlier MMA has completed)
+      if (r == 0) {
+        bulk_g2s(Bbuf, img, IMG_BYTES, bars);
+        if (L - 1 >= 3) bulk_g2s(Bbuf + S::B, img + S::B, IMG_BYTES, bars + 1);
+      }
+      if (r < TP) sp[r] = r < nv ? a.pts[it.pt_off + t0 + r] : make_float2(0.f, 0.f);
+      __syncthreads();
+      float z[W];
+      // layer 1: z = W^1 x (b^1 is added on the value rows), z_i = W^1[:, i], z_ii = 0
+      {
+        const float* W1 = prm + nd.off[1];
+        const float2 x = sp[p];
+#pragma unroll
+        for (int n = 0; n < W; ++n) {
+          const float w0 = __ldg(W1 + 2 * n), w1 = __ldg(W1 + 2 * n + 1);
+          z[n] = c == 0 ? fmaf(w0, x.x, w1 * x.y) : (c == 1 ? w0 : (c == 2 ? w1 : 0.f));
+        }
+        jet_rows<W, KR>(layer_act(nd, prm, 1), W1 + 2 * W, z, r, p, c, lane, valid, Ahi, Alo, Zs, Ds);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      // hidden-to-hidden layers: Z = H W^T on the tensor cores, then the jet rule
+      for (int k = 2; k <= L - 1; ++k) {
+        const int b = (k - 2) & 1;
+        float* B = Bbuf + b * S::B;
+        if (r == 0) {
+          mbar_wait(bars + b, (wph >> b) & 1u, a.err);
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sb_hi = smem_u32(B), sb_lo = smem_u32(B + W * W);
+          constexpr uint32_t B_SBO = (uint32_t)(W / 4) * 128;
+#pragma unroll
+          for (int ks = 0; ks < W / 8; ++ks) {
+            const uint64_t ahi = tc_sdesc(sa_hi + ks * 2 * TC_A_LBO, TC_A_LBO, 128);
+            const uint64_t alo = tc_sdesc(sa_lo + ks * 2 * TC_A_LBO, TC_A_LBO, 128);
+            const uint64_t bhi = tc_sdesc(sb_hi + ks * 256, 128, B_SBO);
+            const uint64_t blo = tc_sdesc(sb_lo + ks * 256, 128, B_SBO);
+            tc_mma(tmem, ahi, bhi, idesc, ks > 0 ? 1u : 0u);
+            tc_mma(tmem + S::COLS / 2, ahi, blo, idesc, ks > 0 ? 1u : 0u);
+            tc_mma(tmem + S::COLS / 2, alo, bhi, idesc, 1u);
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(bars + 2))
+                       : "memory");
+        }
+        wph ^= 1u << b;
+        mbar_wait(bars + 2, mph, a.err);
+        mph ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // this layer's buffer is free again: the image two layers on
+        if (r == 0 && k + 2 <= L - 1) bulk_g2s(B, img + (int64_t)k * S::B, IMG_BYTES, bars + b);
+        tmem_row<W>(t_warp, t_warp + S::COLS / 2, z);
+        jet_rows<W, KR>(layer_act(nd, prm, k), prm + nd.off[k] + W * W, z, r, p, c, lane, valid, Ahi, Alo, Zs,
+                        Ds);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+      }
+      // output layer (identity): y = W^L h + b^L on the value rows, W^L h on the others
+      {
+        const float* WL = prm + nd.off[L];
+        const float* bL = WL + D * W;
+        const float sc = (a.scale && p < nv) ? a.scale[it.pt_off + t0 + p] : 1.f;
+#pragma unroll
+        for (int o = 0; o < XPINN_MAX_OUT; ++o) {
+          if (o >= D) break;
+          float y = c == 0 ? __ldg(bL + o) : 0.f;
+#pragma unroll
+          for (int n = 0; n < W; ++n) y = fmaf(__ldg(WL + o * W + n), z[n], y);
+          if (valid) a.out[it.out_off + (int64_t)(t0 + p) * a.dout + o * K + c] = sc * y;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(S::COLS) : "memory");
+}
+
+// Weight images for the tensor cores: W^k [n_out][n_in] in the no-swizzle
+// K-major canonical layout (8-row groups n_in/4 x 128 bytes apart, K-adjacent
+// core matrices 128 bytes apart), the hi parts then the lo parts of
+// tf32_split.  One CTA per layer.
+__global__ void __launch_bounds__(256) pack_tc_kernel(const float* __restrict__ params,
+                                                      const TcPack* __restrict__ blocks, float* __restrict__ img) {
+  const TcPack b = blocks[blockIdx.x];
+  const float* W = params + b.src;
+  float* hi = img + b.dst;
+  float* lo = hi + b.n_out * b.n_in;
+  for (int e = threadIdx.x; e < b.n_out * b.n_in; e += blockDim.x) {
+    const int n = e / b.n_in, j = e - n * b.n_in;
+    const float2 w = tf32_split(W[e]);
+    const int off = (n >> 3) * (b.n_in / 4) * 32 + (j >> 2) * 32 + (n & 7) * 4 + (j & 3);
+    hi[off] = w.x;
+    lo[off] = w.y;
+  }
+}
+
+template <int W, int KR>
+constexpr size_t smem_of() {
+  return sizeof(float) * (size_t)TcSmem<W, KR>::floats;
+}
+
+template <int W>
+cudaError_t configure_w() {
+  cudaError_t e = cudaFuncSetAttribute(eval_tc_kernel<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_of<W, 1>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(eval_tc_kernel<W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_of<W, 4>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(eval_tc_kernel<W, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_of<W, 8>());
+  return e;
+}
+
+template <int W>
+void launch_w(int K, const TcArgs& a, int grid, cudaStream_t s) {
+  switch (kr_of(K)) {
+    case 1: eval_tc_kernel<W, 1><<<grid, TC_ROWS, smem_of<W, 1>(), s>>>(a); break;
+    case 4: eval_tc_kernel<W, 4><<<grid, TC_ROWS, smem_of<W, 4>(), s>>>(a); break;
+    default: eval_tc_kernel<W, 8><<<grid, TC_ROWS, smem_of<W, 8>(), s>>>(a); break;
+  }
+}
+
+static_assert(smem_of<80, 4>() + 64 <= 227 * 1024, "tensor-core evaluation tile exceeds shared memory");
+
+}  // namespace
+
+bool eval_tc_width_ok(int W) { return W == 32 || W == 64 || W == 80; }
+
+size_t eval_tc_smem_bytes(int W, int K) {
+  const int kr = kr_of(K);
+  switch (W) {
+    case 32: return kr == 1 ? smem_of<32, 1>() : (kr == 4 ? smem_of<32, 4>() : smem_of<32, 8>());
+    case 64: return kr == 1 ? smem_of<64, 1>() : (kr == 4 ? smem_of<64, 4>() : smem_of<64, 8>());
+    default: return kr == 1 ? smem_of<80, 1>() : (kr == 4 ? smem_of<80, 4>() : smem_of<80, 8>());
+  }
+}
+
+int eval_tc_ctas_per_sm(int W, int K) {
+  const int by_smem = (int)((227u << 10) / (eval_tc_smem_bytes(W, K) + 1024));
+  const int cols = W <= 32 ? 64 : (W <= 64 ? 128 : 256);
+  const int by_tmem = 512 / cols;
+  return std::max(1, std::min(by_smem, by_tmem));
+}
+
+cudaError_t eval_tc_configure() {
+  cudaError_t e = configure_w<32>();
+  if (e == cudaSuccess) e = configure_w<64>();
+  if (e == cudaSuccess) e = configure_w<80>();
+  return e;
+}
+
+void launch_eval_tc(int W, int K, const TcArgs& a, int grid, cudaStream_t s) {
+  switch (W) {
+    case 32: launch_w<32>(K, a, grid, s); break;
+    case 64: launch_w<64>(K, a, grid, s); break;
+    default: launch_w<80>(K, a, grid, s); break;
+  }
+}
+
+void launch_pack_tc(const float* params, const TcPack* blocks, int n_blocks, float* img, cudaStream_t s) {
+  if (n_blocks > 0) pack_tc_kernel<<<n_blocks, 256, 0, s>>>(params, blocks, img);
+}
+
+}  // namespace xp
