@@ -16,23 +16,27 @@
 // FP32 pipes.
 //
 // Tile: 128 rows = the MMA's M, one thread and one tensor-memory lane per row,
-// a row per (point, jet component): KR = 1, 4 or 8 rows per point for 1, 3 or
-// 5 components (u; u, u_x, u_y; u, u_x, u_y, u_xx, u_yy), padding rows held at
-// zero, so 128, 32 or 16 points per tile.  Per hidden layer: A = the
-// activation rows H [128][W] and B = W^k [W][W], both K-major in shared memory
-// in the no-swizzle canonical layout (core matrices of 8 rows x 16 bytes),
-// D = Z [128 lanes][W columns] in tensor memory.  The epilogue reads a row of
-// D per thread (tcgen05.ld); the value rows publish their pre-activations, all
-// 128 threads evaluate Phi, Phi', Phi'' once per (point, neuron), and every
-// row applies the jet rule
+// a row per (point, jet component) for K = 1, 3 or 5 components (u; u, u_x,
+// u_y; u, u_x, u_y, u_xx, u_yy).  A warp holds 32 / K whole points (its last
+// 32 mod K rows are padding, held at zero), so that a point's rows share a
+// warp: 128, 40 or 24 points per tile.  Per hidden layer: A = the activation
+// rows H [128][W] and B = W^k [W][W], both K-major in shared memory in the
+// no-swizzle canonical layout (core matrices of 8 rows x 16 bytes), D = Z
+// [128 lanes][W columns] in tensor memory.  The epilogue reads a row of D per
+// thread (tcgen05.ld); the value rows publish their pre-activations, all 128
+// threads evaluate Phi, Phi', Phi'' once per (point, neuron) into tables that
+// live in the A lo image (free between the layer's MMAs and the writing of the
+// next A), and every row applies the jet rule
 //   h_0 = Phi(v_0), h_i = Phi'(v_0) v_i, h_ii = Phi'(v_0) v_ii + Phi''(v_0) v_i^2
-// (v = s z, s the layer's slope), taking v_i of its own point by a warp
-// shuffle (a point's rows share a warp).  The rows of h are the next A.
+// (v = s z, s the layer's slope), the second-derivative rows taking v_i of
+// their point from a third table.  The rows of h are the next A.
 // Weight images (hi and lo, built by pack_tc_kernel) come by one bulk copy
-// per layer into one of two buffers, the copy of layer k + 2 in flight while
-// layer k's epilogue runs.  Every wait is bounded; a wait that gives up sets
-// the error word, the launch stops taking items, frees its tensor memory and
-// ends.
+// per layer into a single buffer, free again once a layer's MMAs complete: the
+// copy of layer k + 1 is in flight while layer k's epilogue runs.  At width 64
+// a tile then needs 98 KB of shared memory, so two CTAs (8 warps) share an SM
+// to hide the epilogue's latencies.  Every wait is bounded; a wait that gives
+// up sets the error word, the launch stops taking items, frees its tensor
+// memory and ends.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,19 +51,21 @@ namespace {
 constexpr int TC_ROWS = 128;
 constexpr int TC_A_LBO = TC_ROWS * 16;   // bytes between K-adjacent core matrices of A
 
-template <int W, int KR>
+template <int W, int K>
 struct TcSmem {
-  static constexpr int TP = TC_ROWS / KR;          // points per tile
+  static constexpr int PW = 32 / K;                // points per warp
+  static constexpr int TP = 4 * PW;                // points per tile
   static constexpr int A = TC_ROWS * W;            // floats of one A image (hi or lo)
-  static constexpr int B = 2 * W * W;              // floats of one weight buffer (hi, lo)
-  static constexpr int Z = KR > 1 ? W * TP : 0;    // floats of the shared activation table
-  static constexpr int floats = 2 * A + 2 * B + 3 * Z + 2 * TP;
+  static constexpr int B = 2 * W * W;              // floats of the weight buffer (hi, lo)
+  static constexpr int Z = K > 1 ? W * TP : 0;     // (point, neuron) pairs of the activation tables
+  static constexpr int DS = K == 5 ? 2 : 1;        // Phi' (3 components) or Phi', Phi'' (5) per pair
+  static constexpr int VS = K == 5 ? 2 : 0;        // v_x, v_y per pair (second-derivative rows read them)
+  static_assert((1 + DS + VS) * Z <= A, "the activation tables live in the A lo image");
+  static constexpr int floats = 2 * A + B + 2 * TP;
   // tensor-memory columns: the main accumulator (hi x hi) at column 0, the
   // cross terms (hi x lo + lo x hi) at column COLS / 2
   static constexpr int COLS = W <= 32 ? 64 : (W <= 64 ? 128 : 256);
 };
-
-constexpr int kr_of(int K) { return K == 1 ? 1 : (K == 3 ? 4 : 8); }
 
 // kind::tf32, D f32, A and B tf32, both K-major, M = 128, N = n
 __device__ __forceinline__ uint32_t tc_idesc(int n) {
@@ -143,13 +149,16 @@ __device__ __forceinline__ void tmem_row(uint32_t main, uint32_t cross, float (&
 }
 
 // The jet rule of the layer's activation on this thread's row (component c
-// of point p): z (without the bias) in, h out in z and in the A images.
-template <int W, int KR>
+// of point p; c = K on padding rows): z (without the bias) in, h out in z and
+// in the A images.  With K > 1 the activation tables Zs (Phi) and Ds (Phi',
+// and Phi'' for K = 5) and, for K = 5, Vs (v_x, v_y) occupy the A lo image
+// until the last barrier.
+template <int W, int K>
 __device__ __forceinline__ void jet_rows(const Act& act, const float* __restrict__ bias, float (&z)[W], int r,
-                                         int p, int c, int lane, bool valid, float* Ahi, float* Alo, float* Zs,
-                                         float2* Ds) {
-  constexpr int TP = TC_ROWS / KR;
-  if constexpr (KR == 1) {
+                                         int p, int c, bool valid, float* Ahi, float* Alo) {
+  using S = TcSmem<W, K>;
+  constexpr int TP = S::TP;
+  if constexpr (K == 1) {
 #pragma unroll
     for (int n = 0; n < W; ++n) {
       float d0, d1, d2, d3;
@@ -157,30 +166,53 @@ __device__ __forceinline__ void jet_rows(const Act& act, const float* __restrict
       z[n] = valid ? d0 : 0.f;
     }
   } else {
+    float* Zs = Alo;
+    float* Ds = Alo + S::Z;
+    float* Vs = Ds + S::DS * S::Z;   // K = 5: v_x, v_y of every pair
     if (c == 0) {
 #pragma unroll
       for (int n = 0; n < W; ++n) Zs[n * TP + p] = z[n] + __ldg(bias + n);
+    }
+    if constexpr (K == 5) {
+      if (c == 1 || c == 2) {
+#pragma unroll
+        for (int n = 0; n < W; ++n) Vs[(n * TP + p) * 2 + c - 1] = act.s * z[n];
+      }
     }
     __syncthreads();
     for (int e = r; e < W * TP; e += TC_ROWS) {
       float d0, d1, d2, d3;
       phi_derivs(act.kind, act.s * Zs[e], d0, d1, d2, d3);
       Zs[e] = d0;
-      Ds[e] = make_float2(d1, d2);
+      if constexpr (K == 5)
+        reinterpret_cast<float2*>(Ds)[e] = make_float2(d1, d2);
+      else
+        Ds[e] = d1;
     }
     __syncthreads();
     // second-derivative rows pair with the first-derivative row of their
-    // direction (component 3 with 1, 4 with 2)
-    const int src = lane - c + (c >= 3 ? c - 2 : 0);
+    // direction (component 3 with 1, 4 with 2), whose v they read from Vs;
+    // every lane loads and computes every candidate and selects (no branch)
+    const int vsel = c >= 3 && c < K ? c - 3 : 0;
 #pragma unroll
     for (int n = 0; n < W; ++n) {
+      const int e = n * TP + p;
       const float vc = act.s * z[n];
-      const float vi = act.s * __shfl_sync(0xffffffffu, z[n], src);
-      const float2 d = Ds[n * TP + p];
-      float h = c == 0 ? Zs[n * TP + p] : d.x * vc;
-      if (c >= 3) h = fmaf(d.y * vi, vi, h);
+      const float d0 = Zs[e];
+      float h;
+      if constexpr (K == 5) {
+        const float2 d = reinterpret_cast<const float2*>(Ds)[e];
+        const float vi = Vs[2 * e + vsel];
+        const float h1 = d.x * vc;
+        const float h2 = fmaf(d.y * vi, vi, h1);
+        h = c == 0 ? d0 : (c >= 3 ? h2 : h1);
+      } else {
+        const float h1 = Ds[e] * vc;
+        h = c == 0 ? d0 : h1;
+      }
       z[n] = valid ? h : 0.f;
     }
+    __syncthreads();   // the tables are read; A lo is written next
   }
 #pragma unroll
   for (int j = 0; j < W; j += 4) {
@@ -191,26 +223,26 @@ __device__ __forceinline__ void jet_rows(const Act& act, const float* __restrict
   }
 }
 
-template <int W, int KR>
+template <int W, int K>
 __global__ void __launch_bounds__(TC_ROWS, 1) eval_tc_kernel(TcArgs a) {
-  using S = TcSmem<W, KR>;
+  using S = TcSmem<W, K>;
   constexpr int TP = S::TP;
-  constexpr int K = KR == 1 ? 1 : (KR == 4 ? 3 : 5);
   constexpr uint32_t IMG_BYTES = 4u * S::B;
   extern __shared__ __align__(1024) float tsm[];
   float* Ahi = tsm;
   float* Alo = tsm + S::A;
-  float* Bbuf = tsm + 2 * S::A;   // buffer b at Bbuf + b * S::B
-  float* Zs = tsm + 2 * S::A + 2 * S::B;
-  float2* Ds = reinterpret_cast<float2*>(Zs + S::Z);
-  float2* sp = reinterpret_cast<float2*>(Zs + 3 * S::Z);
-  __shared__ __align__(8) uint64_t bars[3];   // weight buffers 0 and 1, MMA completion
+  float* B = tsm + 2 * S::A;
+  float2* sp = reinterpret_cast<float2*>(tsm + 2 * S::A + S::B);
+  __shared__ __align__(8) uint64_t bars[2];   // weight buffer, MMA completion
   __shared__ uint32_t s_tmem;
   __shared__ int s_item, s_stop;
   const int r = threadIdx.x, lane = r & 31, warp = r >> 5;
-  const int p = r / KR, c = r % KR;
+  // row -> (point, component): whole points per warp, padding rows last (c = K)
+  const bool pad = lane >= S::PW * K;
+  const int p = pad ? 0 : warp * S::PW + lane / K;
+  const int c = pad ? K : lane % K;
   if (r == 0) {
-    for (int i = 0; i < 3; ++i) mbar_init(bars + i, 1);
+    for (int i = 0; i < 2; ++i) mbar_init(bars + i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -257,11 +289,8 @@ __global__ void __launch_bounds__(TC_ROWS, 1) eval_tc_kernel(TcArgs a) {
     for (int t0 = 0; t0 < it.n_pts; t0 += TP) {
       const int nv = min(TP, it.n_pts - t0);
       const bool valid = p < nv && c < K;
-      // the first two hidden-to-hidden layers' images (every earlier MMA has completed)
-      if (r == 0) {
-        bulk_g2s(Bbuf, img, IMG_BYTES, bars);
-        if (L - 1 >= 3) bulk_g2s(Bbuf + S::B, img + S::B, IMG_BYTES, bars + 1);
-      }
+      // the first hidden-to-hidden layer's image (every earlier MMA has completed)
+      if (r == 0) bulk_g2s(B, img, IMG_BYTES, bars);
       if (r < TP) sp[r] = r < nv ? a.pts[it.pt_off + t0 + r] : make_float2(0.f, 0.f);
       __syncthreads();
       float z[W];
@@ -274,16 +303,14 @@ __global__ void __launch_bounds__(TC_ROWS, 1) eval_tc_kernel(TcArgs a) {
           const float w0 = __ldg(W1 + 2 * n), w1 = __ldg(W1 + 2 * n + 1);
           z[n] = c == 0 ? fmaf(w0, x.x, w1 * x.y) : (c == 1 ? w0 : (c == 2 ? w1 : 0.f));
         }
-        jet_rows<W, KR>(layer_act(nd, prm, 1), W1 + 2 * W, z, r, p, c, lane, valid, Ahi, Alo, Zs, Ds);
+        jet_rows<W, K>(layer_act(nd, prm, 1), W1 + 2 * W, z, r, p, c, valid, Ahi, Alo);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       // hidden-to-hidden layers: Z = H W^T on the tensor cores, then the jet rule
       for (int k = 2; k <= L - 1; ++k) {
-        const int b = (k - 2) & 1;
-        float* B = Bbuf + b * S::B;
         if (r == 0) {
-          mbar_wait(bars + b, (wph >> b) & 1u, a.err);
+          mbar_wait(bars, wph, a.err);
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sb_hi = smem_u32(B), sb_lo = smem_u32(B + W * W);
           constexpr uint32_t B_SBO = (uint32_t)(W / 4) * 128;
@@ -298,18 +325,18 @@ __global__ void __launch_bounds__(TC_ROWS, 1) eval_tc_kernel(TcArgs a) {
             tc_mma(tmem + S::COLS / 2, alo, bhi, idesc, 1u);
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           smem_u32(bars + 2))
+                           smem_u32(bars + 1))
                        : "memory");
         }
-        wph ^= 1u << b;
-        mbar_wait(bars + 2, mph, a.err);
+        wph ^= 1u;
+        mbar_wait(bars + 1, mph, a.err);
         mph ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // this layer's buffer is free again: the image two layers on
-        if (r == 0 && k + 2 <= L - 1) bulk_g2s(B, img + (int64_t)k * S::B, IMG_BYTES, bars + b);
+        // the weight buffer is free again: the next layer's image, in flight
+        // while this layer's epilogue runs
+        if (r == 0 && k + 1 <= L - 1) bulk_g2s(B, img + (int64_t)(k - 1) * S::B, IMG_BYTES, bars);
         tmem_row<W>(t_warp, t_warp + S::COLS / 2, z);
-        jet_rows<W, KR>(layer_act(nd, prm, k), prm + nd.off[k] + W * W, z, r, p, c, lane, valid, Ahi, Alo, Zs,
-                        Ds);
+        jet_rows<W, K>(layer_act(nd, prm, k), prm + nd.off[k] + W * W, z, r, p, c, valid, Ahi, Alo);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -355,9 +382,9 @@ __global__ void __launch_bounds__(256) pack_tc_kernel(const float* __restrict__ 
   }
 }
 
-template <int W, int KR>
+template <int W, int K>
 constexpr size_t smem_of() {
-  return sizeof(float) * (size_t)TcSmem<W, KR>::floats;
+  return sizeof(float) * (size_t)TcSmem<W, K>::floats;
 }
 
 template <int W>
@@ -365,35 +392,34 @@ cudaError_t configure_w() {
   cudaError_t e = cudaFuncSetAttribute(eval_tc_kernel<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_of<W, 1>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(eval_tc_kernel<W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_of<W, 4>());
+    e = cudaFuncSetAttribute(eval_tc_kernel<W, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_of<W, 3>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(eval_tc_kernel<W, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_of<W, 8>());
+    e = cudaFuncSetAttribute(eval_tc_kernel<W, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_of<W, 5>());
   return e;
 }
 
 template <int W>
 void launch_w(int K, const TcArgs& a, int grid, cudaStream_t s) {
-  switch (kr_of(K)) {
+  switch (K) {
     case 1: eval_tc_kernel<W, 1><<<grid, TC_ROWS, smem_of<W, 1>(), s>>>(a); break;
-    case 4: eval_tc_kernel<W, 4><<<grid, TC_ROWS, smem_of<W, 4>(), s>>>(a); break;
-    default: eval_tc_kernel<W, 8><<<grid, TC_ROWS, smem_of<W, 8>(), s>>>(a); break;
+    case 3: eval_tc_kernel<W, 3><<<grid, TC_ROWS, smem_of<W, 3>(), s>>>(a); break;
+    default: eval_tc_kernel<W, 5><<<grid, TC_ROWS, smem_of<W, 5>(), s>>>(a); break;
   }
 }
 
-static_assert(smem_of<80, 4>() + 64 <= 227 * 1024, "tensor-core evaluation tile exceeds shared memory");
+static_assert(smem_of<80, 5>() + 64 <= 227 * 1024, "tensor-core evaluation tile exceeds shared memory");
 
 }  // namespace
 
 bool eval_tc_width_ok(int W) { return W == 32 || W == 64 || W == 80; }
 
 size_t eval_tc_smem_bytes(int W, int K) {
-  const int kr = kr_of(K);
   switch (W) {
-    case 32: return kr == 1 ? smem_of<32, 1>() : (kr == 4 ? smem_of<32, 4>() : smem_of<32, 8>());
-    case 64: return kr == 1 ? smem_of<64, 1>() : (kr == 4 ? smem_of<64, 4>() : smem_of<64, 8>());
-    default: return kr == 1 ? smem_of<80, 1>() : (kr == 4 ? smem_of<80, 4>() : smem_of<80, 8>());
+    case 32: return K == 1 ? smem_of<32, 1>() : (K == 3 ? smem_of<32, 3>() : smem_of<32, 5>());
+    case 64: return K == 1 ? smem_of<64, 1>() : (K == 3 ? smem_of<64, 3>() : smem_of<64, 5>());
+    default: return K == 1 ? smem_of<80, 1>() : (K == 3 ? smem_of<80, 3>() : smem_of<80, 5>());
   }
 }
 
@@ -401,7 +427,8 @@ int eval_tc_ctas_per_sm(int W, int K) {
   const int by_smem = (int)((227u << 10) / (eval_tc_smem_bytes(W, K) + 1024));
   const int cols = W <= 32 ? 64 : (W <= 64 ? 128 : 256);
   const int by_tmem = 512 / cols;
-  return std::max(1, std::min(by_smem, by_tmem));
+  // and at most four: registers (up to 255 a thread) allow no more
+  return std::max(1, std::min(std::min(by_smem, by_tmem), 4));
 }
 
 cudaError_t eval_tc_configure() {
