@@ -364,16 +364,16 @@ typedef struct {
                                interface exchange wait for one item more than
                                exists, so it gives up after about 1 s and the
                                call returns XPINN_ERR_TIMEOUT; 0 (default) off */
-  int32_t eval_tensor_cores; /* 1: routed evaluations (xpinn_eval, xpinn_eval_ws,
-                               the server's queries) of a model whose
-                               subdomains each have one network with input
-                               (x, y), identity output, at least two hidden
-                               layers, all of one width 32, 64 or 80, run the
-                               hidden-to-hidden contractions on the tensor
-                               cores (tcgen05, three TF32 products over a hi/lo
-                               split of both operands, FP32 accumulation);
-                               other models keep the FP32 jet kernel.  0: the
-                               jet kernel for every model */
+  int32_t eval_tensor_cores; /* 1 (default): routed evaluations (xpinn_eval,
+                               xpinn_eval_ws, the server's queries) of a model
+                               whose subdomains each have one network with
+                               input (x, y), identity output, at least two
+                               hidden layers, all of one width 32, 64 or 80,
+                               run the hidden-to-hidden contractions on the
+                               tensor cores (tcgen05, three TF32 products over
+                               a hi/lo split of both operands, FP32
+                               accumulation); other models keep the FP32 jet
+                               kernel.  0: the jet kernel for every model */
 } xpinn_options;
 
 int xpinn_get_options(xpinn_handle h, xpinn_options* opt);

@@ -213,7 +213,7 @@ struct xpinn_ctx {
   int n_sm = 0, grid = 0;
   int ring_cap = 256;
   int host_t = 0, host_slot = 0;
-  xpinn_options opt{0, 1, 4, 2, 0, 0, 256, 0, 0};
+  xpinn_options opt{0, 1, 4, 2, 0, 0, 256, 0, 1};
   int device = 0;
   cudaEvent_t ev[5] = {};
   cudaStream_t cap_stream = nullptr;

@@ -11,9 +11,9 @@
 // one, summed in the epilogue, so that the accumulation rounding of the cross
 // terms stays at their own scale (about 2^-11 of the main term): with one
 // accumulator the 3-pass sum erred up to 1.3e-5 of the jet scale on a width-80
-// sin network with trained slopes, in emulation and on the GPU alike.  The first layer (two
-// inputs) and the output layer (identity, at most three outputs) stay on the
-// FP32 pipes.
+// sin network with trained slopes, in emulation and on the GPU alike.  The
+// first layer (two inputs) and the output layer (identity, at most three
+// outputs) stay on the FP32 pipes.
 //
 // Tile: 128 rows = the MMA's M, one thread and one tensor-memory lane per row,
 // a row per (point, jet component) for K = 1, 3 or 5 components (u; u, u_x,
