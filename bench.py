@@ -458,7 +458,7 @@ def extra_workload(torch, X, name, stream, flush, steps, loop_steps, n_sm):
     return out
 
 
-def eval_tensor_cores(torch, X, stream, flush, n_pts=1 << 20, reps=10):
+def eval_tensor_cores(torch, X, stream, flush, n_pts=1 << 20, reps=10, orders=(0, 1, 2)):
     """Routed evaluation (Eq. FSol) of the Kovasznay cPINN model (64
     subdomains, 2->64x6->3) at n_pts uniform query points on the device,
     derivative orders 0-2, the tensor-core kernel against the FP32 jet
@@ -482,7 +482,7 @@ def eval_tensor_cores(torch, X, stream, flush, n_pts=1 << 20, reps=10):
     e1 = torch.cuda.Event(enable_timing=True)
     out = {"workload": "Kovasznay cPINN model, 64 subdomains 2->64x6->3 tanh, %d uniform query points, "
                        "device buffers (xpinn_eval_ws)" % n_pts, "orders": {}}
-    for order in (0, 1, 2):
+    for order in orders:
         K = (1, 3, 5)[order]
         ws = torch.empty(s.eval_workspace_size(n_pts, order), dtype=torch.uint8, device="cuda")
         dout = torch.empty((n_pts, 3 * K), dtype=torch.float32, device="cuda")
@@ -562,6 +562,10 @@ def main():
     ap.add_argument("--loop-steps", type=int, default=0, help="timed loop steps (0: 2 for c4, else --steps)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads and Adam steps/s")
+    ap.add_argument("--only-eval", action="store_true",
+                    help="run only the tensor-core vs FP32 evaluation comparison and print its JSON")
+    ap.add_argument("--eval-points", type=int, default=1 << 20, help="query points of that comparison")
+    ap.add_argument("--eval-orders", default="0,1,2", help="derivative orders of that comparison")
     ap.add_argument("--pt", type=int, default=0, help="points per thread in the register tile (0: library default)")
     ap.add_argument("--items-per-cta", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: library default)")
@@ -595,6 +599,12 @@ def main():
     from paper_2104_10013_gb300 import xpinn as X
     X.load()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    eval_orders = tuple(int(o) for o in args.eval_orders.split(","))
+    if args.only_eval:
+        stream = torch.cuda.Stream()
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        print(json.dumps(eval_tensor_cores(torch, X, stream, flush, n_pts=args.eval_points, orders=eval_orders)))
+        return
 
     pb, desc = workload(args.workload)
     n_res = pb.n_res
@@ -684,7 +694,8 @@ def main():
             "c3": extra_workload(torch, X, "c3", stream, flush, 5, 0 if args.no_loop else 3, n_sm),
         }
         out["adam_steps"] = adam_steps_per_s(torch, X, stream)
-        out["eval_tensor_cores"] = eval_tensor_cores(torch, X, stream, flush)
+        out["eval_tensor_cores"] = eval_tensor_cores(torch, X, stream, flush, n_pts=args.eval_points,
+                                                     orders=eval_orders)
 
     if not args.no_serving:
         out["serving"] = serving(X, args.serving_requests, args.serving_max_query)

@@ -236,6 +236,7 @@ struct xpinn_ctx {
 
   int* step_t() { return state_i.p; }
   int* loss_slot() { return state_i.p + 1; }
+  float* step_bc() { return reinterpret_cast<float*>(state_i.p + 2); }   // [2] bias corrections
 };
 
 // Facts of a handle for the request server.
@@ -623,6 +624,24 @@ void pack_images(xpinn_ctx* h, cudaStream_t s) {
   launch_pack_weights(h->params.p, h->pack_d.p, (int)h->pack_h.size(), h->wimg.p, s);
 }
 
+// Start of a step and the weight images, one launch.
+void step_start(xpinn_ctx* h, bool adam, cudaStream_t s) {
+  StepStart a{};
+  a.counters = h->counters.p;
+  a.n_counters = h->n_counters;
+  a.step_t = h->step_t();
+  a.loss_slot = h->loss_slot();
+  a.bc = h->step_bc();
+  a.do_adam = adam ? 1 : 0;
+  a.beta1 = h->beta1;
+  a.beta2 = h->beta2;
+  a.params = h->params.p;
+  a.blocks = h->pack_d.p;
+  a.n_blocks = (int)h->pack_h.size();
+  a.wimg = h->wimg.p;
+  launch_step_start(a, s);
+}
+
 constexpr int GRAPH_STEPS = 16;   // steps captured in the multi-step graph
 
 // part 0: the whole step.  Part 1: its start and the exchange items only
@@ -632,16 +651,14 @@ constexpr int GRAPH_STEPS = 16;   // steps captured in the multi-step graph
 void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads, int part = 0) {
   const Plan& pl = h->plan;
   if (part == 1) {
-    launch_step_begin(h->counters.p, h->n_counters, h->step_t(), h->loss_slot(), adam ? 1 : 0, s);
-    pack_images(h, s);
+    step_start(h, adam, s);
     if (pl.n_fwd) launch_jet_step(args_for(h, 0, pl.n_fwd, 0), std::min(h->grid, pl.n_fwd), h->smem, s);
     ck(cudaGetLastError(), "kernel launch");
     return;
   }
   if (part == 0) {
     mark(h, 0, s);
-    launch_step_begin(h->counters.p, h->n_counters, h->step_t(), h->loss_slot(), adam ? 1 : 0, s);
-    pack_images(h, s);
+    step_start(h, adam, s);
   }
   const int n_main = (int)pl.items.size() - pl.n_fwd;
   ReduceArgs r{};
@@ -662,6 +679,7 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads, int par
   r.ring_cap = h->ring_cap;
   r.loss_slot = h->loss_slot();
   r.step_t = h->step_t();
+  r.bc = h->step_bc();
   r.do_adam = adam ? 1 : 0;
   r.beta1 = h->beta1;
   r.beta2 = h->beta2;
@@ -1191,7 +1209,7 @@ std::unique_ptr<Fork> make_fork(xpinn_ctx* h, const xpinn_fork_desc* d) {
   take(L.partials, sizeof(float) * (size_t)pl.partial_floats);
   take(L.loss_part, sizeof(double) * 2 * pl.items.size());
   take(L.counters, sizeof(int) * f->n_counters);
-  take(L.state, sizeof(int) * 2);
+  take(L.state, sizeof(int) * 4);
   take(L.ring, sizeof(float) * (size_t)f->ring_cap * f->n_sub * XPINN_N_TERMS);
   L.total = o;
   F->f = std::move(f);
@@ -1241,7 +1259,7 @@ void bind_fork(xpinn_ctx* h, Fork& F, char* ws, const xpinn_fork_desc* d, cudaSt
   f->partials.view(ws + L.partials, pl.partial_floats);
   f->loss_part.view(ws + L.loss_part, 2 * pl.items.size());
   f->counters.view(ws + L.counters, f->n_counters);
-  f->state_i.view(ws + L.state, 2);
+  f->state_i.view(ws + L.state, 4);
   f->loss_ring.view(ws + L.ring, (size_t)f->ring_cap * f->n_sub * XPINN_N_TERMS);
   f->err_d.view(h->err_d.p, 1);              // errors are the handle's (xpinn_sync reports them)
   f->scratch.view(h->scratch.p, h->scratch.n);
@@ -1286,7 +1304,7 @@ void bind_fork(xpinn_ctx* h, Fork& F, char* ws, const xpinn_fork_desc* d, cudaSt
   ck(cudaMemsetAsync(f->d4.p, 0, sizeof(float) * f->d4.n, s), "memset");
   for (const Fork::Copy& c : F.d4_copies) dd(f->d4.p + c.dst, h->d4.p + c.src, sizeof(float) * c.n);
   ck(cudaMemsetAsync(f->counters.p, 0, sizeof(int) * f->n_counters, s), "memset");
-  ck(cudaMemsetAsync(f->state_i.p, 0, sizeof(int) * 2, s), "memset");
+  ck(cudaMemsetAsync(f->state_i.p, 0, sizeof(int) * 4, s), "memset");
   dd(f->state_i.p, h->step_t(), sizeof(int));   // Adam continues from the handle's step count
   StepArgs& a = f->base;
   a = h->base;
@@ -1527,8 +1545,8 @@ int xpinn_create(const xpinn_problem_desc* d, xpinn_handle* out) {
   h->ifaces_d.upload(h->ifaces.data(), h->ifaces.size());
   h->d4.alloc((size_t)std::max<int64_t>(1, h->n_if_pts * 2 * h->d4_nv));
   ck(cudaMemset(h->d4.p, 0, h->d4.n * sizeof(float)), "memset");
-  h->state_i.alloc(2);
-  ck(cudaMemset(h->state_i.p, 0, 2 * sizeof(int)), "memset");
+  h->state_i.alloc(4);   // step count, loss slot, two float bias corrections
+  ck(cudaMemset(h->state_i.p, 0, 4 * sizeof(int)), "memset");
   h->err_d.alloc(1);
   ck(cudaMemset(h->err_d.p, 0, sizeof(int)), "memset");
   h->loss_ring.alloc((size_t)h->ring_cap * h->n_sub * XPINN_N_TERMS);

@@ -13,18 +13,56 @@ namespace xp {
 
 constexpr int RT = 256;
 
-// Start of a step: reset the work counters of both jet launches, advance the
-// Adam step count and the loss-ring slot.  One thread.
-__global__ void step_begin_kernel(int* counters, int n_counters, int* step_t, int* loss_slot,
-                                  int do_adam) {
-  for (int i = 0; i < n_counters; ++i) counters[i] = 0;
-  if (do_adam) *step_t += 1;
-  *loss_slot += 1;
+// One weight image from the packed parameters (see NetDev), by a CTA.
+__device__ __forceinline__ void pack_block(const float* __restrict__ params, const PackBlock& b,
+                                           float* __restrict__ wimg) {
+  const float* W = params + b.src;
+  float* dst = wimg + b.dst;
+  if (b.fwd) {
+    // [in_p][out_p] = W^T, then [out_p] = b
+    const int n_el = (b.in_p + 1) * b.out_p;
+    for (int e = threadIdx.x; e < n_el; e += RT) {
+      const int j = e / b.out_p, n = e - j * b.out_p;
+      float v = 0.f;
+      if (n < b.out_w) {
+        if (j < b.in_w) v = W[(int64_t)n * b.in_w + j];
+        else if (j == b.in_p) v = W[(int64_t)b.out_w * b.in_w + n];
+      }
+      dst[e] = v;
+    }
+  } else {
+    // [out_p][in_p] = W
+    const int n_el = b.out_p * b.in_p;
+    for (int e = threadIdx.x; e < n_el; e += RT) {
+      const int n = e / b.in_p, j = e - n * b.in_p;
+      dst[e] = (n < b.out_w && j < b.in_w) ? W[(int64_t)n * b.in_w + j] : 0.f;
+    }
+  }
 }
 
-void launch_step_begin(int* counters, int n_counters, int* step_t, int* loss_slot, int do_adam,
-                       cudaStream_t s) {
-  step_begin_kernel<<<1, 1, 0, s>>>(counters, n_counters, step_t, loss_slot, do_adam);
+// Start of a step, one launch: CTA 0 resets the work counters of the jet
+// launches, advances the Adam step count t and the loss-ring slot, and
+// stores the bias corrections 1 - beta1^t and 1 - beta2^t (in double, once
+// per step, for every CTA of the reduction); CTA b < n_blocks builds weight
+// image b.
+__global__ void __launch_bounds__(RT) step_start_kernel(StepStart a) {
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < a.n_counters; i += RT) a.counters[i] = 0;
+    if (threadIdx.x == 0) {
+      if (a.do_adam) {
+        const int t = *a.step_t + 1;
+        *a.step_t = t;
+        a.bc[0] = (float)(1.0 - pow((double)a.beta1, (double)t));
+        a.bc[1] = (float)(1.0 - pow((double)a.beta2, (double)t));
+      }
+      *a.loss_slot += 1;
+    }
+  }
+  if ((int)blockIdx.x < a.n_blocks) pack_block(a.params, a.blocks[blockIdx.x], a.wimg);
+}
+
+void launch_step_start(const StepStart& a, cudaStream_t s) {
+  step_start_kernel<<<a.n_blocks > 1 ? a.n_blocks : 1, RT, 0, s>>>(a);
 }
 
 __global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
@@ -32,12 +70,6 @@ __global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
   const int q = blk.x;
   const SubDev& sd = a.subs[q];
   const int ib = a.q_item_begin[q], ie = a.q_item_begin[q + 1];
-  __shared__ float s_bc[2];
-  if (threadIdx.x == 0 && a.do_adam) {
-    const int t = *a.step_t;
-    s_bc[0] = (float)(1.0 - pow((double)a.beta1, (double)t));
-    s_bc[1] = (float)(1.0 - pow((double)a.beta2, (double)t));
-  }
   // loss terms of this subdomain (first block of the subdomain only): one
   // warp, lane l takes items l, l + 32, ...; the lanes' sums are combined by a
   // fixed butterfly, so the order is the same in every step
@@ -117,8 +149,8 @@ __global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
     const float v = b2 * a.v[gi] + (1.f - b2) * g * g;
     a.m[gi] = m;
     a.v[gi] = v;
-    const float mhat = m / s_bc[0];
-    const float vhat = v / s_bc[1];
+    const float mhat = m / a.bc[0];
+    const float vhat = v / a.bc[1];
     a.params[gi] -= sd.lr * mhat / (sqrtf(vhat) + a.eps);
   }
 }
@@ -146,29 +178,7 @@ void launch_objective_sum(const float* jq, int n_sub, float* out, cudaStream_t s
 __global__ void __launch_bounds__(RT) pack_weights_kernel(const float* __restrict__ params,
                                                           const PackBlock* __restrict__ blocks,
                                                           float* __restrict__ wimg) {
-  const PackBlock b = blocks[blockIdx.x];
-  const float* W = params + b.src;
-  float* dst = wimg + b.dst;
-  if (b.fwd) {
-    // [in_p][out_p] = W^T, then [out_p] = b
-    const int n_el = (b.in_p + 1) * b.out_p;
-    for (int e = threadIdx.x; e < n_el; e += RT) {
-      const int j = e / b.out_p, n = e - j * b.out_p;
-      float v = 0.f;
-      if (n < b.out_w) {
-        if (j < b.in_w) v = W[(int64_t)n * b.in_w + j];
-        else if (j == b.in_p) v = W[(int64_t)b.out_w * b.in_w + n];
-      }
-      dst[e] = v;
-    }
-  } else {
-    // [out_p][in_p] = W
-    const int n_el = b.out_p * b.in_p;
-    for (int e = threadIdx.x; e < n_el; e += RT) {
-      const int n = e / b.in_p, j = e - n * b.in_p;
-      dst[e] = (n < b.out_w && j < b.in_w) ? W[(int64_t)n * b.in_w + j] : 0.f;
-    }
-  }
+  pack_block(params, blocks[blockIdx.x], wimg);
 }
 
 void launch_pack_weights(const float* params, const PackBlock* blocks, int n_blocks, float* wimg,

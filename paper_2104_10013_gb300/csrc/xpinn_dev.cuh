@@ -295,6 +295,7 @@ struct ReduceArgs {
   const int* loss_slot;      // device slot counter (already incremented)
   const int64_t* q_part_off; // CSR (like q_items): gradient slice offset of each item
   const int* step_t;         // device Adam step count (already incremented)
+  const float* bc;           // [2] bias corrections 1 - beta1^t, 1 - beta2^t of this step
   int do_adam;
   float beta1, beta2, eps;
   int n_sub;
@@ -316,7 +317,21 @@ struct PackBlock {
 };
 void launch_pack_weights(const float* params, const PackBlock* blocks, int n_blocks, float* wimg,
                          cudaStream_t s);
-void launch_step_begin(int* counters, int n_counters, int* step_t, int* loss_slot, int do_adam,
-                       cudaStream_t s);
+// Start of a step (step_start_kernel): counters, step count, bias
+// corrections, loss slot, weight images.
+struct StepStart {
+  int* counters;
+  int n_counters;
+  int* step_t;
+  int* loss_slot;
+  float* bc;                 // [2] out: 1 - beta1^t, 1 - beta2^t
+  int do_adam;
+  float beta1, beta2;
+  const float* params;
+  const PackBlock* blocks;
+  int n_blocks;
+  float* wimg;
+};
+void launch_step_start(const StepStart& a, cudaStream_t s);
 
 }  // namespace xp
