@@ -58,12 +58,25 @@ int jet_step_blocks_per_sm(int pt, int nt, bool gen, size_t smem) {
   return n;
 }
 
+// Launched as a programmatic dependent of the kernel before it on the
+// stream: its launch overlaps that kernel's end, and the kernel waits for the
+// previous grid's completion (griddepcontrol.wait) before it reads anything.
 void launch_jet_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
   const int nt = a.nt == 512 || a.nt == 128 ? a.nt : 256;
   const void* k = kernel_for(nt == 512 || a.pt == 1 ? 1 : 2, nt, a.gen != 0);
   StepArgs arg = a;
   void* params[] = {&arg};
-  cudaLaunchKernel(k, dim3(grid), dim3(nt), params, smem, s);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(nt);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelExC(&cfg, k, params);
 }
 
 }  // namespace xp

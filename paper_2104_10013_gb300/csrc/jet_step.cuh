@@ -1548,6 +1548,9 @@ static __device__ bool wait_exchange(const StepArgs& a) {
 // the general activations are not in this kernel, so they cost it nothing).
 template <int PT, int NTH, bool GEN>
 __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : (PT == 1 ? 2 : 1) * (256 / NTH)) jet_step_kernel(StepArgs a) {
+  // launched as a programmatic dependent: nothing is read or written before
+  // the previous kernel on the stream has completed
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const SmemLayout sl{a.szA, a.szW, a.szU, a.pmax, GEN ? 1 : 0};
   __shared__ int s_item;
   float* scratch = a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;

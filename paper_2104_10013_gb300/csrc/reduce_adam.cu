@@ -46,6 +46,7 @@ __device__ __forceinline__ void pack_block(const float* __restrict__ params, con
 // per step, for every CTA of the reduction); CTA b < n_blocks builds weight
 // image b.
 __global__ void __launch_bounds__(RT) step_start_kernel(StepStart a) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // see launch_pdl
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i < a.n_counters; i += RT) a.counters[i] = 0;
     if (threadIdx.x == 0) {
@@ -61,11 +62,30 @@ __global__ void __launch_bounds__(RT) step_start_kernel(StepStart a) {
   if ((int)blockIdx.x < a.n_blocks) pack_block(a.params, a.blocks[blockIdx.x], a.wimg);
 }
 
+// Launch as a programmatic dependent of the kernel before it on the stream:
+// the launch overlaps that kernel's end; the kernel waits for the previous
+// grid's completion (griddepcontrol.wait) before it reads or writes anything.
+template <typename Arg>
+void launch_pdl(void (*kernel)(Arg), int grid, const Arg& arg, cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(RT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, arg);
+}
+
 void launch_step_start(const StepStart& a, cudaStream_t s) {
-  step_start_kernel<<<a.n_blocks > 1 ? a.n_blocks : 1, RT, 0, s>>>(a);
+  launch_pdl(step_start_kernel, a.n_blocks > 1 ? a.n_blocks : 1, a, s);
 }
 
 __global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // see launch_pdl
   const int2 blk = a.blocks[blockIdx.x];
   const int q = blk.x;
   const SubDev& sd = a.subs[q];
@@ -156,7 +176,7 @@ __global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
 }
 
 void launch_reduce_adam(const ReduceArgs& a, cudaStream_t s) {
-  if (a.n_blocks > 0) reduce_adam_kernel<<<a.n_blocks, RT, 0, s>>>(a);
+  if (a.n_blocks > 0) launch_pdl(reduce_adam_kernel, a.n_blocks, a, s);
 }
 
 // J(Theta) = sum_q J(Theta_q): lane l sums subdomains l, l + 32, ... in
