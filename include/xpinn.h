@@ -374,6 +374,22 @@ typedef struct {
                                a hi/lo split of both operands, FP32
                                accumulation); other models keep the FP32 jet
                                kernel.  0: the jet kernel for every model */
+  int32_t train_tensor_cores; /* 0 (default): the FP32 jet kernel trains every
+                               subdomain.  N in [1, 64]: the residual points
+                               of every subdomain with one fixed-slope tanh
+                               network of input (x, y), identity output of at
+                               most 3 components, 3 to 7 weight layers and
+                               every hidden width within [N, 64], under a PDE
+                               trained with Laplacian jets (Poisson,
+                               Navier-Stokes), are trained by the tensor-core
+                               kernel: the forward, reverse and weight-gradient
+                               contractions of the hidden-to-hidden layers as
+                               tcgen05 MMAs (three TF32 products over hi/lo
+                               splits of both operands, FP32 accumulation),
+                               layers narrower than 64 zero-padded.  Their
+                               data and interface points stay on the jet
+                               kernel; forks (xpinn_fork_step) use the jet
+                               kernel throughout */
 } xpinn_options;
 
 int xpinn_get_options(xpinn_handle h, xpinn_options* opt);
@@ -415,6 +431,13 @@ int xpinn_set_tile_caps(xpinn_handle h, const int32_t* caps);   /* [n_sub] (0 or
  * exchange too), ms[2] jet kernel launch(es), ms[3] reduction and Adam.
  * Requires profile_phases = 1; waits for that step to finish. */
 int xpinn_phase_times(xpinn_handle h, float* ms);
+
+/* Work items of the current step plan (host tables, no device work):
+ * *n_items all of them (exchange, residual, data and interface items),
+ * *n_tc the residual items the tensor-core kernel runs (option
+ * train_tensor_cores), *n_tc_sub the subdomains those belong to.  Any
+ * output pointer may be NULL. */
+int xpinn_plan_counts(xpinn_handle h, int32_t* n_items, int32_t* n_tc, int32_t* n_tc_sub);
 
 /* Device time in milliseconds of the evaluation kernel (the jet kernel, or
  * the tensor-core kernel under eval_tensor_cores) of the most recent routed

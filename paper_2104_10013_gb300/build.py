@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libxpinn.so")
 SOURCES = ["jet_step_tanh_pt2.cu", "jet_step_tanh_pt1.cu", "jet_step_gen_pt2.cu", "jet_step_gen_pt1.cu",
-           "jet_step.cu", "eval_tc.cu", "reduce_adam.cu", "route.cu", "api.cu", "noalloc.cu", "serve.cu",
-           "partition.cu"]
+           "jet_step.cu", "eval_tc.cu", "step_tc.cu", "reduce_adam.cu", "route.cu", "api.cu", "noalloc.cu",
+           "serve.cu", "partition.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

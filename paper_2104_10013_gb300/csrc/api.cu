@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "eval_tc.h"
+#include "step_tc.h"
 #include "xpinn_dev.cuh"
 
 namespace xp {
@@ -148,6 +149,12 @@ struct Plan {
   // per-subdomain ranges (loop schedule)
   std::vector<int> fwd_begin, main_begin;   // [n_sub + 1], relative to n_fwd for main
   int64_t partial_floats = 0;
+  // residual items of the tensor-core kernel (step_tc.cu): the last n_tc
+  // items; tc_begin [n_sub + 1] ranges per subdomain (loop schedule),
+  // relative to the first of them
+  int n_tc = 0;
+  std::vector<int> tc_begin;
+  int n_simt() const { return (int)items.size() - n_tc; }
 };
 
 struct xpinn_ctx {
@@ -202,6 +209,15 @@ struct xpinn_ctx {
   DevBuf<TcPack> tc_pack_d;
   int n_tc_pack = 0;
   bool tc_stale = true;
+  // tensor-core training (step_tc.cu, option train_tensor_cores): weight
+  // images of the qualifying subdomains (forward and reverse of every
+  // hidden-to-hidden layer), rebuilt at the start of every step, and the
+  // kernel's per-CTA scratch
+  DevBuf<float> tct_img, tct_scratch;
+  DevBuf<int64_t> tct_off;       // [n_sub] first float of a subdomain's images, -1: none
+  DevBuf<TcTrainPack> tct_pack_d;
+  int n_tct_pack = 0;
+  int tct_grid = 0;
   // device time of the evaluation kernel of the last routed evaluation
   // (profile_phases): events around its launch
   cudaEvent_t eval_ev[2] = {};
@@ -213,7 +229,7 @@ struct xpinn_ctx {
   int n_sm = 0, grid = 0;
   int ring_cap = 256;
   int host_t = 0, host_slot = 0;
-  xpinn_options opt{0, 1, 4, 2, 0, 0, 256, 0, 1};
+  xpinn_options opt{0, 1, 4, 2, 0, 0, 256, 0, 1, 0};
   int device = 0;
   cudaEvent_t ev[5] = {};
   cudaStream_t cap_stream = nullptr;
@@ -362,15 +378,45 @@ void build_plan(xpinn_ctx* h, int p_cap) {
     it.part_off = -1;
     return it;
   };
-  // first pass: one item per point set, to estimate the total cost
+  // subdomains whose residual items run on the tensor-core kernel
+  std::vector<char> tcq(h->n_sub, 0);
+  double tc_total = 0;
+  bool any_tc = false;
+  for (int q = 0; q < h->n_sub; ++q) {
+    const SubDev& sd = h->subs[q];
+    if (sd.n_res && step_tc_net_ok(sd.net[0], sd.n_nets, h->pde, h->opt.train_tensor_cores)) {
+      tcq[q] = 1;
+      any_tc = true;
+      tc_total += (double)sd.n_res * (sd.net[0].L - 1);
+    }
+  }
+  // first pass: one item per point set, to estimate the total cost (with
+  // tensor-core residual items, of everything the jet kernel still runs)
   double total = 0;
   for (int q = 0; q < h->n_sub; ++q) {
     const SubDev& sd = h->subs[q];
-    if (sd.n_res) {
+    if (sd.n_res && !tcq[q]) {
       Item it = mk(IT_RES, q, -1, 0, sd.res_off, sd.n_res, k_res(h->pde, 0), sd.n_nets > 1 ? k_res(h->pde, 1) : 0);
       total += item_cost(sd, it, cta_threads(h));
     }
+    if (any_tc)
+      for (int n = 0; n < sd.n_nets; ++n)
+        if (sd.n_data[n])
+          total += item_cost(sd, mk(n == 0 ? IT_DATA0 : IT_DATA1, q, -1, 0, sd.data_off[n], sd.n_data[n],
+                                    n == 0 ? 1 : 0, n == 1 ? 1 : 0),
+                             cta_threads(h));
   }
+  if (any_tc)
+    for (int e = 0; e < h->n_iface; ++e) {
+      const IfaceDev& f = h->ifaces[e];
+      for (int side = 0; side < 2 && f.n_pts; ++side) {
+        const int q = side ? f.qp : f.q;
+        total += 2 * item_cost(h->subs[q],
+                               mk(IT_IFACE, q, e, side, f.pt_off, f.n_pts, k_iface(h->pde, f.method, 0),
+                                  h->subs[q].n_nets > 1 ? k_iface(h->pde, f.method, 1) : 0),
+                               cta_threads(h));
+      }
+    }
   const double target = std::max(1.0, total / (double)(h->grid * std::max(1, h->opt.items_per_cta)));
   auto split = [&](Item proto, std::vector<Item>& out) {
     const SubDev& sd = h->subs[proto.q];
@@ -385,10 +431,30 @@ void build_plan(xpinn_ctx* h, int p_cap) {
       out.push_back(it);
     }
   };
+  // tensor-core items: whole tiles of STC_PTS points, about tc_ipc items per
+  // CTA of its launch (one CTA per SM), cost ~ points x layers
+  std::vector<Item> tcv;
+  constexpr int tc_ipc = 8;
+  const double tc_target = tc_total / (double)(std::max(1, h->n_sm) * tc_ipc);
   for (int q = 0; q < h->n_sub; ++q) {
     const SubDev& sd = h->subs[q];
     const int K1 = sd.n_nets > 1 ? k_res(h->pde, 1) : 0;
-    if (sd.n_res) split(mk(IT_RES, q, -1, 0, sd.res_off, sd.n_res, k_res(h->pde, 0), K1), main_);
+    if (sd.n_res && tcq[q]) {
+      Item proto = mk(IT_RES, q, -1, 0, sd.res_off, sd.n_res, 4, 0);
+      proto.P = STC_PTS;
+      int per = (int)std::ceil(tc_target / (sd.net[0].L - 1));
+      per = std::max(4 * STC_PTS, (per + STC_PTS - 1) / STC_PTS * STC_PTS);
+      const int chunks = (sd.n_res + per - 1) / per;
+      per = ((sd.n_res + chunks - 1) / chunks + STC_PTS - 1) / STC_PTS * STC_PTS;
+      for (int s0 = 0; s0 < sd.n_res; s0 += per) {
+        Item it = proto;
+        it.pt_off = proto.pt_off + s0;
+        it.n_pts = std::min(per, sd.n_res - s0);
+        tcv.push_back(it);
+      }
+    } else if (sd.n_res) {
+      split(mk(IT_RES, q, -1, 0, sd.res_off, sd.n_res, k_res(h->pde, 0), K1), main_);
+    }
     for (int n = 0; n < sd.n_nets; ++n)
       if (sd.n_data[n])
         split(mk(n == 0 ? IT_DATA0 : IT_DATA1, q, -1, 0, sd.data_off[n], sd.n_data[n], n == 0 ? 1 : 0,
@@ -429,6 +495,13 @@ void build_plan(xpinn_ctx* h, int p_cap) {
   };
   order(fwd);
   order(main_);
+  {
+    auto tc_cost = [&](const Item& a) { return (double)a.n_pts * (h->subs[a.q].net[0].L - 1); };
+    std::stable_sort(tcv.begin(), tcv.end(), [&](const Item& a, const Item& b) {
+      if (h->opt.schedule == 1 && a.q != b.q) return a.q < b.q;
+      return tc_cost(a) > tc_cost(b);
+    });
+  }
   pl.n_fwd = (int)fwd.size();
   pl.first_iface = pl.n_fwd + (int)main_.size();
   for (size_t i = 0; i < main_.size(); ++i)
@@ -438,6 +511,8 @@ void build_plan(xpinn_ctx* h, int p_cap) {
     }
   pl.items = fwd;
   pl.items.insert(pl.items.end(), main_.begin(), main_.end());
+  pl.items.insert(pl.items.end(), tcv.begin(), tcv.end());
+  pl.n_tc = (int)tcv.size();
   // gradient slices and per-subdomain item lists (in item order: deterministic)
   std::vector<std::vector<int>> per_q(h->n_sub);
   for (size_t i = pl.n_fwd; i < pl.items.size(); ++i) {
@@ -459,12 +534,15 @@ void build_plan(xpinn_ctx* h, int p_cap) {
   // per-subdomain ranges for the loop schedule
   pl.fwd_begin.assign(h->n_sub + 1, 0);
   pl.main_begin.assign(h->n_sub + 1, 0);
+  pl.tc_begin.assign(h->n_sub + 1, 0);
   if (h->opt.schedule == 1) {
     for (int i = 0; i < pl.n_fwd; ++i) pl.fwd_begin[pl.items[i].q + 1]++;
-    for (size_t i = pl.n_fwd; i < pl.items.size(); ++i) pl.main_begin[pl.items[i].q + 1]++;
+    for (int i = pl.n_fwd; i < pl.n_simt(); ++i) pl.main_begin[pl.items[i].q + 1]++;
+    for (int i = pl.n_simt(); i < (int)pl.items.size(); ++i) pl.tc_begin[pl.items[i].q + 1]++;
     for (int q = 0; q < h->n_sub; ++q) {
       pl.fwd_begin[q + 1] += pl.fwd_begin[q];
       pl.main_begin[q + 1] += pl.main_begin[q];
+      pl.tc_begin[q + 1] += pl.tc_begin[q];
     }
   }
   h->plan = std::move(pl);
@@ -496,6 +574,42 @@ int any_general(const xpinn_ctx* h) {
     for (int n = 0; n < sd.n_nets; ++n)
       if (net_is_general(sd.net[n])) return 1;
   return 0;
+}
+
+// Weight images, pack list and scratch of the tensor-core residual items:
+// per qualifying subdomain the forward images of layers 2..L-1, then their
+// reverse images, STC_IMG floats each.
+void plan_tc(xpinn_ctx* h) {
+  const Plan& pl = h->plan;
+  std::vector<int64_t> off(h->n_sub, -1);
+  std::vector<TcTrainPack> pk;
+  int64_t n = 0;
+  for (int i = pl.n_simt(); i < (int)pl.items.size(); ++i) {
+    const int q = pl.items[i].q;
+    if (off[q] >= 0) continue;
+    const SubDev& sd = h->subs[q];
+    const NetDev& nd = sd.net[0];
+    off[q] = n;
+    for (int k = 2; k < nd.L; ++k) {
+      const int64_t src = sd.poff + nd.off[k];
+      pk.push_back({src, n + (int64_t)(k - 2) * STC_IMG, nd.w[k], nd.w[k - 1], 0});
+      pk.push_back({src, n + (int64_t)(nd.L - 2 + k - 2) * STC_IMG, nd.w[k], nd.w[k - 1], 1});
+    }
+    n += (int64_t)2 * (nd.L - 2) * STC_IMG;
+  }
+  h->n_tct_pack = pl.n_tc ? (int)pk.size() : 0;
+  h->tct_grid = 0;
+  if (!pl.n_tc) {
+    h->tct_img.release();
+    h->tct_scratch.release();
+    return;
+  }
+  h->tct_img.alloc((size_t)n);
+  h->tct_off.upload(off.data(), off.size());
+  h->tct_pack_d.upload(pk.data(), pk.size());
+  h->tct_grid = std::min(h->n_sm, pl.n_tc);
+  h->tct_scratch.alloc((size_t)h->tct_grid * STC_SCRATCH);
+  ck(step_tc_configure(), "cudaFuncSetAttribute(step_tc smem)");
 }
 
 void size_and_upload_plan(xpinn_ctx* h) {
@@ -540,7 +654,10 @@ void size_and_upload_plan(xpinn_ctx* h) {
       }
     h->e_proto.upload(pr.data(), pr.size());
   }
-  h->n_counters = 3 + 2 * h->n_sub;   // [0] main, [1] spare, [2] exchange done, then loop counters
+  // [0] main, [1] spare, [2] exchange done, [3, 3 + 2 n_sub) loop counters,
+  // then the tensor-core launch's: grouped, and one per subdomain (loop)
+  h->n_counters = 4 + 3 * h->n_sub;
+  plan_tc(h);
   h->counters.alloc(h->n_counters);
   ck(cudaMemset(h->counters.p, 0, sizeof(int) * h->n_counters), "memset");
   // The limit is a property of the kernel, shared by every handle: raise it to
@@ -644,6 +761,35 @@ void step_start(xpinn_ctx* h, bool adam, cudaStream_t s) {
 
 constexpr int GRAPH_STEPS = 16;   // steps captured in the multi-step graph
 
+// The tensor-core kernel over `count` of its items from plan item `begin`.
+void launch_tc(xpinn_ctx* h, int begin, int count, int counter_idx, cudaStream_t s) {
+  if (count <= 0) return;
+  StepTcArgs a{};
+  a.items = h->items_d.p + begin;
+  a.n_items = count;
+  a.item_base = begin;
+  a.counter = h->counters.p + counter_idx;
+  a.subs = h->subs_d.p;
+  a.params = h->params.p;
+  a.img = h->tct_img.p;
+  a.img_off = h->tct_off.p;
+  a.pts = h->pts.p;
+  a.res_f = h->res_f.p;
+  a.partials = h->partials.p;
+  a.loss_part = h->loss_part.p;
+  a.scratch = h->tct_scratch.p;
+  a.pde = h->pde;
+  a.nu = h->nu;
+  a.re = h->re;
+  a.err = h->err_d.p;
+  launch_step_tc(a, std::min(h->tct_grid, count), s);
+}
+
+// The weight images of the tensor-core kernel, from the current parameters.
+void pack_tc_train(xpinn_ctx* h, cudaStream_t s) {
+  launch_pack_tc_train(h->params.p, h->tct_pack_d.p, h->n_tct_pack, h->tct_img.p, s);
+}
+
 // part 0: the whole step.  Part 1: its start and the exchange items only
 // (this handle's sides of every interface into the exchange buffer); part 2:
 // the rest (residual, data and interface items, reduction and Adam) once the
@@ -660,7 +806,6 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads, int par
     mark(h, 0, s);
     step_start(h, adam, s);
   }
-  const int n_main = (int)pl.items.size() - pl.n_fwd;
   ReduceArgs r{};
   r.blocks = h->red_blocks_d.p;
   r.n_blocks = (int)pl.red_blocks.size();
@@ -687,14 +832,23 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads, int par
   r.n_sub = h->n_sub;
   r.err = h->err_d.p;
   r.jq = h->jq.p;
+  const int tc0 = pl.n_simt(), tc_ctr = 3 + 2 * h->n_sub;
   if (part == 2) {
-    if (n_main) launch_jet_step(args_for(h, pl.n_fwd, n_main, 1), std::min(h->grid, n_main), h->smem, s);
+    if (pl.n_tc) {
+      pack_tc_train(h, s);
+      launch_tc(h, tc0, pl.n_tc, tc_ctr, s);
+    }
+    const int n_rest = pl.n_simt() - pl.n_fwd;
+    if (n_rest) launch_jet_step(args_for(h, pl.n_fwd, n_rest, 1), std::min(h->grid, n_rest), h->smem, s);
     launch_reduce_adam(r, s);
   } else if (h->opt.schedule == 0) {
     // one launch: exchange items first, interface items last (they wait)
+    if (pl.n_tc) pack_tc_train(h, s);
     mark(h, 1, s);
     mark(h, 2, s);
-    const int n_all = (int)pl.items.size();
+    // residual items of the tensor-core kernel first, then the jet kernel's
+    launch_tc(h, tc0, pl.n_tc, tc_ctr, s);
+    const int n_all = pl.n_simt();
     if (n_all) {
       StepArgs a = args_for(h, 0, n_all, 0);
       a.wait_from = pl.first_iface;
@@ -704,6 +858,7 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads, int par
     mark(h, 3, s);
     launch_reduce_adam(r, s);
   } else {
+    if (pl.n_tc) pack_tc_train(h, s);
     mark(h, 1, s);
     for (int q = 0; q < h->n_sub; ++q) {
       const int b = pl.fwd_begin[q], c = pl.fwd_begin[q + 1] - b;
@@ -711,6 +866,7 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads, int par
     }
     mark(h, 2, s);
     for (int q = 0; q < h->n_sub; ++q) {
+      launch_tc(h, tc0 + pl.tc_begin[q], pl.tc_begin[q + 1] - pl.tc_begin[q], tc_ctr + 1 + q, s);
       const int b = pl.n_fwd + pl.main_begin[q], c = pl.main_begin[q + 1] - pl.main_begin[q];
       if (c) launch_jet_step(args_for(h, b, c, 2 + h->n_sub + q), std::min(h->grid, c), h->smem, s);
     }
@@ -1099,6 +1255,7 @@ std::unique_ptr<Fork> make_fork(xpinn_ctx* h, const xpinn_fork_desc* d) {
   f->opt.use_graph = 0;
   f->opt.profile_phases = 0;
   f->opt.inject_fault = 0;
+  f->opt.train_tensor_cores = 0;   // forks train on the jet kernel
   f->grid = h->grid;
   f->n_sm = h->n_sm;
   f->device = h->device;
@@ -2055,7 +2212,7 @@ int xpinn_set_options(xpinn_handle h, const xpinn_options* opt) {
       (opt->threads_per_cta != 0 && opt->threads_per_cta != 128 && opt->threads_per_cta != 256 &&
        opt->threads_per_cta != 512) || opt->inject_fault < 0 || opt->inject_fault > 1 ||
       (opt->threads_per_cta == 512 && opt->points_per_thread != 1) || opt->eval_tensor_cores < 0 ||
-      opt->eval_tensor_cores > 1)
+      opt->eval_tensor_cores > 1 || opt->train_tensor_cores < 0 || opt->train_tensor_cores > STC_W)
     fail(XPINN_ERR_INVALID, "bad options");
   ck(cudaDeviceSynchronize(), "sync");
   apply_options(h, *opt);
@@ -2308,6 +2465,25 @@ int xpinn_phase_times(xpinn_handle h, float* ms) {
   if (!h->opt.profile_phases || !h->ev[0]) fail(XPINN_ERR_INVALID, "profile_phases is off");
   ck(cudaEventSynchronize(h->ev[4]), "event sync");
   for (int i = 0; i < 4; ++i) ck(cudaEventElapsedTime(ms + i, h->ev[i], h->ev[i + 1]), "elapsed");
+  API_END
+}
+
+int xpinn_plan_counts(xpinn_handle h, int32_t* n_items, int32_t* n_tc, int32_t* n_tc_sub) {
+  API_BEGIN
+  if (!h) fail(XPINN_ERR_INVALID, "bad arguments");
+  const Plan& pl = h->plan;
+  if (n_items) *n_items = (int32_t)pl.items.size();
+  if (n_tc) *n_tc = pl.n_tc;
+  if (n_tc_sub) {
+    std::vector<char> seen(h->n_sub, 0);
+    int c = 0;
+    for (int i = pl.n_simt(); i < (int)pl.items.size(); ++i)
+      if (!seen[pl.items[i].q]) {
+        seen[pl.items[i].q] = 1;
+        ++c;
+      }
+    *n_tc_sub = c;
+  }
   API_END
 }
 

@@ -62,7 +62,8 @@ class Options(C.Structure):
     _fields_ = [("schedule", C.c_int32), ("use_graph", C.c_int32), ("items_per_cta", C.c_int32),
                 ("points_per_thread", C.c_int32), ("profile_phases", C.c_int32),
                 ("max_points_per_tile", C.c_int32), ("threads_per_cta", C.c_int32),
-                ("inject_fault", C.c_int32), ("eval_tensor_cores", C.c_int32)]
+                ("inject_fault", C.c_int32), ("eval_tensor_cores", C.c_int32),
+                ("train_tensor_cores", C.c_int32)]
 
 
 class ForkDesc(C.Structure):
@@ -118,6 +119,7 @@ def load() -> C.CDLL:
         "xpinn_set_options": (C.c_int, [vp, C.POINTER(Options)]),
         "xpinn_iface_values": (C.c_int, [vp, fp, C.POINTER(i64), vp]),
         "xpinn_phase_times": (C.c_int, [vp, fp]),
+        "xpinn_plan_counts": (C.c_int, [vp, vp, vp, vp]),
         "xpinn_eval_kernel_time": (C.c_int, [vp, C.POINTER(C.c_float)]),
         "xpinn_autotune": (C.c_int, [vp, i32, C.POINTER(Options), C.POINTER(C.c_float)]),
         "xpinn_autotune_shapes": (C.c_int, [vp, i32, C.POINTER(C.c_float)]),
@@ -503,6 +505,13 @@ class Solver:
         ms = np.zeros(4, np.float32)
         _check(self.lib.xpinn_phase_times(self.h, ms.ctypes.data))
         return ms
+
+    def plan_counts(self):
+        """(work items of the step plan, residual items on the tensor-core
+        kernel, subdomains those belong to)."""
+        v = (C.c_int32 * 3)()
+        _check(self.lib.xpinn_plan_counts(self.h, C.byref(v, 0), C.byref(v, 4), C.byref(v, 8)))
+        return int(v[0]), int(v[1]), int(v[2])
 
     def eval_kernel_ms(self) -> float:
         """Device ms of the evaluation kernel of the last routed evaluation

@@ -1,0 +1,101 @@
+"""Residual items of the training step on the tensor cores (option
+train_tensor_cores): the forward jets, the reverse pass and the weight
+gradients of hidden layers up to 64 wide as tcgen05 TF32 MMAs over hi/lo
+splits of both operands, for fixed-slope tanh networks under Laplacian-jet
+PDEs (Poisson, Navier-Stokes).
+
+* losses (1e-5) and every gradient tensor (1e-4) match the FP64 oracle on a
+  Navier-Stokes cPINN (width 64, six hidden layers, three outputs) and on a
+  Poisson XPINN whose subdomains mix qualifying networks (widths 40-64,
+  zero-padded to 64, two to five hidden layers) with one-hidden-layer
+  networks that stay on the jet kernel in the same step; point counts leave
+  ragged tiles (32 points) and ragged items;
+* Adam steps follow the oracle given the gradient, repeated gradients agree
+  bit for bit, and so do the grouped and per-subdomain loop schedules;
+* the result lies within the tolerances of the FP32 jet kernel's.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, adam_update
+from paper_2104_10013_gb300 import problems as P
+from tests.test_parity import RTOL_GRAD, X, assert_grads, assert_losses  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def ns_small(n_res=300):
+    return P.kovasznay_cpinn(nx=2, ny=2, n_res=n_res, n_iface=32, n_bc=40)
+
+
+def poisson_mixed():
+    return P.poisson_xpinn(nx=3, ny=2, n_res_range=(150, 700), width_range=(40, 64), depth_range=(1, 5),
+                           n_iface=40, n_bc=30, seed=12)
+
+
+def solver(X, pb, tc):
+    s = X.Solver(pb)
+    s.set_options(train_tensor_cores=tc)
+    return s
+
+
+@pytest.mark.parametrize("name", ["ns_w64_d6", "poisson_w40_64_mixed"])
+def test_tensor_core_grad_matches_the_oracle(X, name):
+    pb = ns_small() if name == "ns_w64_d6" else poisson_mixed()
+    s = solver(X, pb, 64 if name == "ns_w64_d6" else 40)
+    n_items, n_tc, n_tc_sub = s.plan_counts()
+    depths = [len(sd.nets[0].widths) - 2 for sd in pb.subs]
+    assert n_tc > 0 and n_tc_sub == sum(d >= 2 for d in depths), (n_tc, n_tc_sub, depths)
+    if name != "ns_w64_d6":
+        assert n_tc_sub < pb.n_sub   # some subdomains stay on the jet kernel
+    losses, g = s.grad()
+    terms, g_ref = Oracle(pb).grad(pb.packed_params())
+    assert_losses(losses, terms)
+    assert_grads(g, g_ref, pb)
+    s.close()
+
+
+def test_tensor_core_items_are_deterministic_and_schedule_independent(X):
+    pb = poisson_mixed()
+    s = solver(X, pb, 40)
+    l1, g1 = s.grad()
+    l2, g2 = s.grad()
+    assert np.array_equal(g1, g2) and np.array_equal(l1, l2)
+    s.set_options(schedule=1)
+    assert s.plan_counts()[1] > 0
+    l3, g3 = s.grad()
+    assert np.array_equal(g1, g3) and np.array_equal(l1, l3)
+    s.close()
+
+
+def test_tensor_core_grad_is_near_the_jet_kernel(X):
+    pb = ns_small(n_res=700)
+    a = solver(X, pb, 64)
+    b = solver(X, pb, 0)
+    assert a.plan_counts()[1] > 0 and b.plan_counts()[1] == 0
+    la, ga = a.grad()
+    lb, gb = b.grad()
+    assert_losses(la, lb)
+    assert_grads(ga, gb.astype(np.float64), pb, rtol=2 * RTOL_GRAD)
+    a.close(); b.close()
+
+
+def test_tensor_core_adam_steps_follow_the_oracle(X):
+    pb = ns_small()
+    s = solver(X, pb, 64)
+    orc = Oracle(pb)
+    th = s.get_params().astype(np.float64)
+    _, g = s.grad()
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    lr = orc.lr_vector()
+    for t in (1, 2, 3):
+        s.step(1)
+        th, m, v = adam_update(th, g.astype(np.float64), m, v, t, lr, orc.beta1, orc.beta2, orc.eps)
+        got = s.get_params().astype(np.float64)
+        assert np.all(np.abs(got - th) <= 1e-6 * lr + 1e-7 * np.abs(th)), (t, np.abs(got - th).max())
+        th = got
+        _, g = s.grad()
+        terms, g_ref = orc.grad(th)
+        assert_grads(g, g_ref, pb)
+    s.close()
