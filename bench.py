@@ -570,6 +570,8 @@ def main():
     ap.add_argument("--items-per-cta", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: library default)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--train-tensor-cores", type=int, default=-1,
+                    help="option train_tensor_cores of the timed workload (-1: library default)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--serving-max-query", type=int, default=1000000)
@@ -617,6 +619,8 @@ def main():
         opts["threads_per_cta"] = args.threads
     autotune = not args.no_autotune and not opts
     s, tune = tuned_solver(X, pb, autotune, opts)
+    if args.train_tensor_cores >= 0:
+        s.set_options(train_tensor_cores=args.train_tensor_cores)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):

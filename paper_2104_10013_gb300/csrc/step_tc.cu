@@ -15,9 +15,9 @@
 // the jet rules and the residual stay on the FP32 pipes.
 //
 // Tile: 128 rows = the MMA's M, 32 points x 4 jet components (u, u_x, u_y,
-// lap u) with the components of a point in 4 adjacent lanes; two threads per
-// row (warps w and w + 4 share tensor-memory lanes), each owning 32 of the 64
-// neurons.  The jet rule of tanh (h = t, h_i = s z_i, h_lap = s z_lap -
+// lap u) with the components of a point in 4 adjacent lanes; four threads per
+// row (warps w, w + 4, w + 8 and w + 12 share tensor-memory lanes), each
+// owning 16 of the 64 neurons.  The jet rule of tanh (h = t, h_i = s z_i, h_lap = s z_lap -
 // 2 t s (z_x^2 + z_y^2), t = tanh z, s = 1 - t^2) and its reverse exchange
 // t, hbar_lap and the sums over a point's rows by warp shuffles; tanh itself
 // is evaluated once per (point, neuron), spread over the point's 4 lanes.
@@ -52,10 +52,13 @@ namespace xp {
 
 namespace {
 
-constexpr int NTH = 256;
+constexpr int NPT = 16;                  // neurons of a thread (of the 64)
+constexpr int NTH = 128 * (STC_W / NPT); // four threads per row
 constexpr int ROWS = 128;
 constexpr unsigned FULL = 0xffffffffu;
-// floats between K-adjacent core matrices of the images whose K is the rows
+// K-major images whose K is the tile's rows: floats between K-adjacent core
+// matrices, padded by 16 bytes so that a warp's 32 rows of one column store
+// into 32 different banks
 constexpr int LB_B = 8 * 32 + 4;    // B' = H^T [N = 64][K = rows]: 1040 bytes
 constexpr int LB_T = 16 * 32 + 4;   // At = stacked Zb^T [M = 128][K = rows]: 2064 bytes
 constexpr int LB_S = 2 * 32 + 4;    // [N = 16][K = rows] (input jets, output seeds): 272 bytes
@@ -63,27 +66,38 @@ constexpr int SZ_B = 32 * LB_B;     // one B' image (hi or lo)
 constexpr int SZ_T = 32 * LB_T;
 constexpr int SZ_S = 32 * LB_S;
 constexpr int SZ_AF = ROWS * STC_W;  // one row-major A image (hi or lo)
-constexpr int SZ_RA = 2 * SZ_B;      // region A: A (hi | lo), or B' (hi | lo), or two [N = 16] images
-static_assert(2 * SZ_AF <= SZ_RA && 2 * SZ_S <= SZ_RA && 2 * 64 * 65 <= SZ_RA, "region A");
-// shared-memory map (floats)
+constexpr int SZ_RA = 2 * SZ_B;      // region A: A (hi | lo), or B' (hi | lo)
+// region A also holds, between the forward and the reverse pass, the partial
+// outputs [4 parts][128 rows][4] and the output jets and seeds [32 points][3][4]
+constexpr int RA_X = 0, RA_J = RA_X + 4 * ROWS * 4, RA_G = RA_J + 384;
+static_assert(2 * SZ_AF <= SZ_RA && RA_G + 384 <= SZ_RA && 2 * 64 * 65 <= SZ_RA, "region A");
+// the item's FP32-pipe weights, zero-padded to 64 neurons: W^1 [64][2], b^1,
+// b^k (k = 2..L-1) [STC_MAXL - 2][64], W^L [3][64], b^L [4]
+constexpr int PW_W1 = 0, PW_B1 = 128, PW_BK = 192, PW_WL = PW_BK + 64 * (STC_MAXL - 2), PW_BL = PW_WL + 192;
+constexpr int SZ_PW = PW_BL + 4;
+// shared-memory map (floats): region A, At, two weight buffers, the [16][rows]
+// images, the points, the bias-gradient partials [STC_MAXL - 2][4 lane
+// quadrants][64] and [32 points][4], the FP32-pipe weights
 constexpr int O_A = 0;
 constexpr int O_T = O_A + SZ_RA;
-constexpr int O_W = O_T + SZ_T;                     // two weight buffers
-constexpr int O_J = O_W + 2 * STC_IMG;              // output jets [32 points][3 outputs][4]
-constexpr int O_G = O_J + 384;                      // their seeds, same layout
-constexpr int O_X = O_G + 384;                      // second-half partial outputs [128 rows][4]
-constexpr int O_P = O_X + 512;                      // points, float2 [32]
-constexpr int O_DB = O_P + 64;                      // hidden bias-gradient partials [STC_MAXL - 2][256]
-constexpr int O_DL = O_DB + (STC_MAXL - 2) * 256;   // output bias-gradient partials [32 points][4]
-constexpr int SMEM_FLOATS = O_DL + 128;
+constexpr int O_W = O_T + SZ_T;
+constexpr int O_S = O_W + 2 * STC_IMG;
+constexpr int O_P = O_S + 2 * SZ_S;
+constexpr int O_DB = O_P + 64;
+constexpr int O_DL = O_DB + (STC_MAXL - 2) * 4 * 64;
+constexpr int O_PW = O_DL + 128;
+constexpr int SMEM_FLOATS = O_PW + SZ_PW;
 // tensor-memory columns: Z main [0, 64), Z cross [64, 128), dW^k (k = 2..L-1)
 // at 128 + 64 (k - 2), then dW^1 and dW^L (16 columns each)
 constexpr int TMEM_COLS = 512;
 static_assert(128 + 64 * (STC_MAXL - 2) + 32 <= TMEM_COLS, "tensor memory");
 
+// element offsets in the images whose K is the rows (column n, row r); for
+// column nb + i with nb a multiple of 8: base + col_step(i)
 __device__ __forceinline__ int t_off(int m, int r) { return (m >> 3) * 32 + (r >> 2) * LB_T + (m & 7) * 4 + (r & 3); }
 __device__ __forceinline__ int b_off(int j, int r) { return (j >> 3) * 32 + (r >> 2) * LB_B + (j & 7) * 4 + (r & 3); }
 __device__ __forceinline__ int s_off(int j, int r) { return (j >> 3) * 32 + (r >> 2) * LB_S + (j & 7) * 4 + (r & 3); }
+__device__ __forceinline__ constexpr int col_step(int i) { return (i >> 3) * 32 + (i & 7) * 4; }
 
 __device__ __forceinline__ void fence_to_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -96,8 +110,9 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// Z (+)= A . B over K = 64: A the row-major image at a (hi, then lo), B a
-// weight image at b (hi, then lo); hi x hi into tm, the cross terms into tm + 64.
+// Z (+)= A . B over K = 64: A the row-major image at a (hi, then lo), read
+// K-major; B a weight image at b (hi, then lo); hi x hi into tm, the cross
+// terms into tm + 64.
 __device__ __forceinline__ void mma_rows(uint32_t tm, uint32_t a, uint32_t b) {
   const uint32_t id = tc_idesc(STC_W);
 #pragma unroll
@@ -128,24 +143,25 @@ __device__ __forceinline__ void mma_grad(uint32_t tm, uint32_t t, uint32_t b, ui
   }
 }
 
-// 32 columns of this thread's lane: main + cross accumulators
-__device__ __forceinline__ void tmem_row32(uint32_t main, uint32_t cross, float (&z)[32]) {
-  uint32_t v[32], u[32];
-  tmem_ld16(main, v);
-  tmem_ld16(main + 16, v + 16);
-  tmem_ld16(cross, u);
-  tmem_ld16(cross + 16, u + 16);
+// NPT columns of this thread's lane: main + cross accumulators
+__device__ __forceinline__ void tmem_rowz(uint32_t main, uint32_t cross, float (&z)[NPT]) {
+  uint32_t v[NPT], u[NPT];
+#pragma unroll
+  for (int c0 = 0; c0 < NPT; c0 += 16) {
+    tmem_ld16(main + c0, v + c0);
+    tmem_ld16(cross + c0, u + c0);
+  }
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int c0 = 0; c0 < 32; c0 += 8) {
+  for (int c0 = 0; c0 < NPT; c0 += 8) {
     tmem_fence_regs8(v + c0);
     tmem_fence_regs8(u + c0);
   }
 #pragma unroll
-  for (int i = 0; i < 32; ++i) z[i] = __uint_as_float(v[i]) + __uint_as_float(u[i]);
+  for (int i = 0; i < NPT; ++i) z[i] = __uint_as_float(v[i]) + __uint_as_float(u[i]);
 }
 
-// n columns (16 or 32) of this thread's lane of one accumulator
+// N columns (a multiple of 16) of this thread's lane of one accumulator
 template <int N>
 __device__ __forceinline__ void tmem_cols(uint32_t taddr, float (&z)[N]) {
   uint32_t v[N];
@@ -158,14 +174,15 @@ __device__ __forceinline__ void tmem_cols(uint32_t taddr, float (&z)[N]) {
   for (int i = 0; i < N; ++i) z[i] = __uint_as_float(v[i]);
 }
 
-// Forward jet rule of tanh on this thread's row (component c) for its 32
+// Forward jet rule of tanh on this thread's row (component c) for its NPT
 // neurons: z in (the value row's includes the bias), h out in z.  The saved
-// value (t on the value row, z_c on the others) goes to Sk[n][row].
-__device__ __forceinline__ void jet_fwd(float (&z)[32], int c, int gb, float* __restrict__ Sk, int r, int nb) {
-  float t[32];
+// value (t on the value row, z_c on the others) goes to Sk[n][row] (Sk
+// points at this thread's first neuron and row).
+__device__ __forceinline__ void jet_fwd(float (&z)[NPT], int c, int gb, float* __restrict__ Sk) {
+  float t[NPT];
   // tanh of the value row's z, neuron 4g + c evaluated by lane c of the point
 #pragma unroll
-  for (int g = 0; g < 8; ++g) {
+  for (int g = 0; g < NPT / 4; ++g) {
     const float a0 = __shfl_sync(FULL, z[4 * g], gb), a1 = __shfl_sync(FULL, z[4 * g + 1], gb);
     const float a2 = __shfl_sync(FULL, z[4 * g + 2], gb), a3 = __shfl_sync(FULL, z[4 * g + 3], gb);
     const float tm = tanhf(c == 0 ? a0 : (c == 1 ? a1 : (c == 2 ? a2 : a3)));
@@ -173,25 +190,13 @@ __device__ __forceinline__ void jet_fwd(float (&z)[32], int c, int gb, float* __
     for (int j = 0; j < 4; ++j) t[4 * g + j] = __shfl_sync(FULL, tm, gb + j);
   }
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
+  for (int i = 0; i < NPT; ++i) {
     const float zi = z[i], ti = t[i], s = 1.f - ti * ti;
     float q = (c == 1 || c == 2) ? zi * zi : 0.f;
     q += __shfl_xor_sync(FULL, q, 1);
     q += __shfl_xor_sync(FULL, q, 2);
-    Sk[(nb + i) * ROWS + r] = c == 0 ? ti : zi;
+    Sk[i * ROWS] = c == 0 ? ti : zi;
     z[i] = c == 0 ? ti : (c == 3 ? s * zi - 2.f * ti * s * q : s * zi);
-  }
-}
-
-// H from saved jets: sv (this row's saved value), tv (t of the point)
-__device__ __forceinline__ void jet_from_saved(const float (&sv)[32], const float (&tv)[32], int c, float (&h)[32]) {
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const float zi = sv[i], ti = tv[i], s = 1.f - ti * ti;
-    float q = (c == 1 || c == 2) ? zi * zi : 0.f;
-    q += __shfl_xor_sync(FULL, q, 1);
-    q += __shfl_xor_sync(FULL, q, 2);
-    h[i] = c == 0 ? ti : (c == 3 ? s * zi - 2.f * ti * s * q : s * zi);
   }
 }
 
@@ -200,10 +205,10 @@ __device__ __forceinline__ void jet_from_saved(const float (&sv)[32], const floa
 //   zb_lap = s hb_lap,  zb_i = s hb_i - 4 t s z_i hb_lap,
 //   zb = s [hb - 2 t (z_x hb_x + z_y hb_y) + (-2 t z_lap + (6 t^2 - 2)(z_x^2 + z_y^2)) hb_lap]
 // the bracket summed over the point's 4 rows.
-__device__ __forceinline__ void jet_bwd(const float (&sv)[32], const float (&tv)[32], const float (&hb)[32], int c,
-                                        int gb, float (&zb)[32]) {
+__device__ __forceinline__ void jet_bwd(const float (&sv)[NPT], const float (&tv)[NPT], const float (&hb)[NPT],
+                                        int c, int gb, float (&zb)[NPT]) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
+  for (int i = 0; i < NPT; ++i) {
     const float zi = sv[i], ti = tv[i], s = 1.f - ti * ti, hbi = hb[i];
     const float h3 = __shfl_sync(FULL, hbi, gb + 3);
     float e = c == 0 ? hbi
@@ -215,44 +220,90 @@ __device__ __forceinline__ void jet_bwd(const float (&sv)[32], const float (&tv)
   }
 }
 
-// This row's 32 values into the row-major A image (hi at A, lo at A + SZ_AF)
-__device__ __forceinline__ void put_rows(float* __restrict__ A, const float (&v)[32], int r, int nb) {
+__device__ __forceinline__ void split_all(const float (&v)[NPT], float (&hi)[NPT], float (&lo)[NPT]) {
 #pragma unroll
-  for (int g = 0; g < 8; ++g) {
-    const float2 s0 = tf32_split(v[4 * g]), s1 = tf32_split(v[4 * g + 1]), s2 = tf32_split(v[4 * g + 2]),
-                 s3 = tf32_split(v[4 * g + 3]);
-    const int o = a_off(r, nb + 4 * g);
-    *reinterpret_cast<float4*>(A + o) = make_float4(s0.x, s1.x, s2.x, s3.x);
-    *reinterpret_cast<float4*>(A + SZ_AF + o) = make_float4(s0.y, s1.y, s2.y, s3.y);
+  for (int i = 0; i < NPT; ++i) {
+    const float2 s = tf32_split(v[i]);
+    hi[i] = s.x;
+    lo[i] = s.y;
   }
 }
 
-// ... into the stacked transposed image (M-row n: hi, 64 + n: lo; K = row)
-__device__ __forceinline__ void put_stacked(float* __restrict__ T, const float (&v)[32], int r, int nb) {
+// Row-major A image (hi at A, lo at A + SZ_AF); A points at a_off(r, nb)
+__device__ __forceinline__ void put_rows(float* __restrict__ A, const float (&hi)[NPT], const float (&lo)[NPT]) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const float2 sp = tf32_split(v[i]);
-    T[t_off(nb + i, r)] = sp.x;
-    T[t_off(64 + nb + i, r)] = sp.y;
+  for (int g = 0; g < NPT / 4; ++g) {
+    *reinterpret_cast<float4*>(A + g * (TC_A_LBO / 4)) =
+        make_float4(hi[4 * g], hi[4 * g + 1], hi[4 * g + 2], hi[4 * g + 3]);
+    *reinterpret_cast<float4*>(A + SZ_AF + g * (TC_A_LBO / 4)) =
+        make_float4(lo[4 * g], lo[4 * g + 1], lo[4 * g + 2], lo[4 * g + 3]);
   }
 }
 
-// ... into the transposed B' image (N = neuron, K = row; hi, then lo)
-__device__ __forceinline__ void put_bt(float* __restrict__ B, const float (&v)[32], int r, int nb) {
+// Stacked transposed image (M-row n: hi, 64 + n: lo; K = row); T points at t_off(nb, r)
+__device__ __forceinline__ void put_stacked(float* __restrict__ T, const float (&hi)[NPT], const float (&lo)[NPT]) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const float2 sp = tf32_split(v[i]);
-    B[b_off(nb + i, r)] = sp.x;
-    B[SZ_B + b_off(nb + i, r)] = sp.y;
+  for (int i = 0; i < NPT; ++i) {
+    T[col_step(i)] = hi[i];
+    T[8 * 32 + col_step(i)] = lo[i];   // M-row 64 + n: eight 8-row groups further
   }
 }
 
-__device__ __forceinline__ void load_saved(const float* __restrict__ Sk, int r, int nb, int gb, float (&sv)[32],
-                                           float (&tv)[32]) {
+// Transposed B' image (N = neuron, K = row; hi, then lo); B points at b_off(nb, r)
+__device__ __forceinline__ void put_bt(float* __restrict__ B, const float (&hi)[NPT], const float (&lo)[NPT]) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) sv[i] = __ldcg(Sk + (nb + i) * ROWS + r);
+  for (int i = 0; i < NPT; ++i) {
+    B[col_step(i)] = hi[i];
+    B[SZ_B + col_step(i)] = lo[i];
+  }
+}
+
+// H from saved jets: sv (this row's saved value), tv (t of the point)
+__device__ __forceinline__ void jet_from_saved(const float (&sv)[NPT], const float (&tv)[NPT], int c,
+                                               float (&h)[NPT]) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) tv[i] = __shfl_sync(FULL, sv[i], gb);
+  for (int i = 0; i < NPT; ++i) {
+    const float zi = sv[i], ti = tv[i], s = 1.f - ti * ti;
+    float q = (c == 1 || c == 2) ? zi * zi : 0.f;
+    q += __shfl_xor_sync(FULL, q, 1);
+    q += __shfl_xor_sync(FULL, q, 2);
+    h[i] = c == 0 ? ti : (c == 3 ? s * zi - 2.f * ti * s * q : s * zi);
+  }
+}
+
+// Saved jets of one layer (Sk at this thread's first neuron and row) and t
+// of the point on every row
+__device__ __forceinline__ void load_saved(const float* __restrict__ Sk, int gb, float (&sv)[NPT],
+                                           float (&tv)[NPT]) {
+#pragma unroll
+  for (int i = 0; i < NPT; ++i) sv[i] = __ldcg(Sk + i * ROWS);
+#pragma unroll
+  for (int i = 0; i < NPT; ++i) tv[i] = __shfl_sync(FULL, sv[i], gb);
+}
+
+// Sum of the value rows' zb over the warp's 8 points, scattered: the value
+// lane of point v (lane 4 v) ends with the sums of neurons 2 v and 2 v + 1
+// (of the thread's NPT) in out[0], out[1].  Halving exchanges: xor 16
+// (neurons 0-7 / 8-15), xor 8, xor 4.
+__device__ __forceinline__ void value_row_sums(const float (&zb)[NPT], int lane, float (&out)[2]) {
+  static_assert(NPT == 16, "three halving steps");
+  float a[8], b[4];
+  const bool h16 = (lane >> 4) & 1, h8 = (lane >> 3) & 1, h4 = (lane >> 2) & 1;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float keep = h16 ? zb[8 + j] : zb[j], send = h16 ? zb[j] : zb[8 + j];
+    a[j] = keep + __shfl_xor_sync(FULL, send, 16);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float keep = h8 ? a[4 + j] : a[j], send = h8 ? a[j] : a[4 + j];
+    b[j] = keep + __shfl_xor_sync(FULL, send, 8);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float keep = h4 ? b[2 + j] : b[j], send = h4 ? b[j] : b[2 + j];
+    out[j] = keep + __shfl_xor_sync(FULL, send, 4);
+  }
 }
 
 __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
@@ -260,19 +311,25 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   float* RA = sm + O_A;
   float* RT = sm + O_T;
   float* RW = sm + O_W;
-  float* Js = sm + O_J;
-  float* Gs = sm + O_G;
-  float* Xs = sm + O_X;
+  float* RS = sm + O_S;
+  float* Xs = RA + RA_X;
+  float* Js = RA + RA_J;
+  float* Gs = RA + RA_G;
   float2* sp = reinterpret_cast<float2*>(sm + O_P);
   float* dbs = sm + O_DB;
   float* dls = sm + O_DL;
+  float* pw = sm + O_PW;
   __shared__ __align__(8) uint64_t bars[4];   // weight buffers 0 and 1, row MMAs, gradient MMAs
   __shared__ uint32_t s_tmem;
   __shared__ int s_item, s_stop;
   __shared__ double red[NTH / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, nb = (warp >> 2) * 32;
+  const int quad = warp & 3, part = warp >> 2, nb = part * NPT;
   const int r = quad * 32 + lane, p = r >> 2, c = r & 3, gb = lane & ~3;
+  // this thread's bases in the images
+  float* const A_r = RA + a_off(r, nb);
+  float* const T_r = RT + t_off(nb, r);
+  float* const B_r = RA + b_off(nb, r);
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) mbar_init(bars + i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -288,8 +345,8 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   after_sync();
   const uint32_t tmem = s_tmem;
   const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16);   // this warp's lanes
-  const uint32_t sa = smem_u32(RA), st = smem_u32(RT), sw = smem_u32(RW);
-  float* S = a.scratch + (int64_t)blockIdx.x * STC_SCRATCH;
+  const uint32_t sa = smem_u32(RA), st = smem_u32(RT), sw = smem_u32(RW), ss = smem_u32(RS);
+  float* const S_r = a.scratch + (int64_t)blockIdx.x * STC_SCRATCH + nb * ROWS + r;
   uint32_t wph = 0, mph = 0, dph = 0;   // phase parities (wph: bit per weight buffer)
   bool d_pending = false;               // a gradient-MMA commit not yet waited for
   for (;;) {
@@ -322,17 +379,36 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
       const int k = i < L - 2 ? i + 2 : 2 * L - 3 - i;
       return img + (int64_t)((i < L - 2 ? 0 : L - 2) + k - 2) * STC_IMG;
     };
-    const float* WL = prm + nd.off[L];
     const float coef = 2.f * sd.w_res * sd.inv_n_res;
-    for (int k = 0; k < L - 2; ++k) dbs[k * NTH + tid] = 0.f;
+    // the item's FP32-pipe weights, zero-padded (visible after the first tile's barrier)
+    for (int e = tid; e < SZ_PW; e += NTH) {
+      float v = 0.f;
+      if (e < PW_B1) {
+        const int n = e >> 1;
+        if (n < nd.w[1]) v = prm[nd.off[1] + e];
+      } else if (e < PW_BK) {
+        const int n = e - PW_B1;
+        if (n < nd.w[1]) v = prm[nd.off[1] + 2 * nd.w[1] + n];
+      } else if (e < PW_WL) {
+        const int k = 2 + (e - PW_BK) / 64, n = (e - PW_BK) % 64;
+        if (k < L && n < nd.w[k]) v = prm[nd.off[k] + nd.w[k] * nd.w[k - 1] + n];
+      } else if (e < PW_BL) {
+        const int o = (e - PW_WL) / 64, n = (e - PW_WL) % 64;
+        if (o < D && n < wl) v = prm[nd.off[L] + o * wl + n];
+      } else if (e - PW_BL < D) {
+        v = prm[nd.off[L] + D * wl + e - PW_BL];
+      }
+      pw[e] = v;
+    }
+    for (int e = tid; e < (STC_MAXL - 2) * 4 * 64; e += NTH) dbs[e] = 0.f;
     if (tid < 128) dls[tid] = 0.f;
     double l0 = 0.0;
     const int n_tiles = (it.n_pts + STC_PTS - 1) / STC_PTS;
     for (int tile = 0; tile < n_tiles; ++tile) {
       const int t0 = tile * STC_PTS;
       const int nv = min(STC_PTS, it.n_pts - t0);
-      // every MMA of the previous tile has completed: both weight buffers,
-      // region A and At are free
+      // every MMA of the previous tile has completed: both weight buffers and
+      // regions A, At and S are free
       if (d_pending) {
         mbar_wait(bars + 3, dph, a.err);
         dph ^= 1u;
@@ -344,25 +420,19 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
       }
       if (tid < STC_PTS) sp[tid] = tid < nv ? a.pts[it.pt_off + t0 + tid] : make_float2(0.f, 0.f);
       __syncthreads();
-      float z[32];
+      float z[NPT], zh[NPT], zl[NPT];
       // ---- layer 1: z = W^1 x + b^1, z_x = W^1[:, 0], z_y = W^1[:, 1], z_lap = 0
       {
-        const float* W1 = prm + nd.off[1];
-        const float* b1 = W1 + 2 * nd.w[1];
         const float2 x = sp[p];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int n = nb + i;
-          float w0 = 0.f, w1 = 0.f, b = 0.f;
-          if (n < nd.w[1]) {
-            w0 = __ldg(W1 + 2 * n);
-            w1 = __ldg(W1 + 2 * n + 1);
-            b = __ldg(b1 + n);
-          }
-          z[i] = c == 0 ? fmaf(w0, x.x, fmaf(w1, x.y, b)) : (c == 1 ? w0 : (c == 2 ? w1 : 0.f));
+        for (int i = 0; i < NPT; ++i) {
+          const float2 w = reinterpret_cast<const float2*>(pw + PW_W1)[nb + i];
+          const float b = pw[PW_B1 + nb + i];
+          z[i] = c == 0 ? fmaf(w.x, x.x, fmaf(w.y, x.y, b)) : (c == 1 ? w.x : (c == 2 ? w.y : 0.f));
         }
-        jet_fwd(z, c, gb, S, r, nb);
-        put_rows(RA, z, r, nb);   // L >= 3: a hidden-to-hidden layer reads it
+        jet_fwd(z, c, gb, S_r);
+        split_all(z, zh, zl);
+        put_rows(A_r, zh, zl);   // L >= 3: a hidden-to-hidden layer reads it
       }
       // ---- hidden-to-hidden layers on the tensor cores
       for (int k = 2; k <= L - 1; ++k) {
@@ -380,39 +450,37 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         mph ^= 1u;
         after_sync();
         if (tid == 0 && i + 2 < nimg) bulk_g2s(RW + STC_IMG * buf, img_src(i + 2), 4u * STC_IMG, bars + buf);
-        tmem_row32(tq + nb, tq + 64 + nb, z);
-        if (c == 0) {
-          const float* bk = prm + nd.off[k] + nd.w[k] * nd.w[k - 1];
+        tmem_rowz(tq + nb, tq + 64 + nb, z);
+        const float* bk = pw + PW_BK + (k - 2) * 64 + nb;
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (nb + j < nd.w[k]) z[j] += __ldg(bk + nb + j);
-        }
-        jet_fwd(z, c, gb, S + (k - 1) * STC_W * ROWS, r, nb);
+        for (int j = 0; j < NPT; ++j) z[j] += c == 0 ? bk[j] : 0.f;
+        jet_fwd(z, c, gb, S_r + (k - 1) * STC_W * ROWS);
+        split_all(z, zh, zl);
         if (k < L - 1)
-          put_rows(RA, z, r, nb);
+          put_rows(A_r, zh, zl);
         else
-          put_stacked(RT, z, r, nb);   // H^{L-1} for the output layer's weight gradient
+          put_stacked(T_r, zh, zl);   // H^{L-1} for the output layer's weight gradient
       }
       // ---- output layer (FP32): y = W^L h + b^L on the value row, W^L h on the others
       {
+        const float* WL = pw + PW_WL;
         float y[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int o = 0; o < 3; ++o)
-          if (o < D) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (nb + j < wl) y[o] = fmaf(__ldg(WL + o * wl + nb + j), z[j], y[o]);
-          }
-        if (nb) {
+          for (int j = 0; j < NPT; ++j) y[o] = fmaf(WL[o * 64 + nb + j], z[j], y[o]);
 #pragma unroll
-          for (int o = 0; o < 3; ++o) Xs[r * 4 + o] = y[o];
-        }
+        for (int o = 0; o < 3; ++o) Xs[(part * ROWS + r) * 4 + o] = y[o];
         __syncthreads();
-        if (!nb) {
-          const float* bL = WL + D * wl;
+        if (part == 0) {
 #pragma unroll
           for (int o = 0; o < 3; ++o)
-            if (o < D) Js[(p * 3 + o) * 4 + c] = y[o] + Xs[r * 4 + o] + (c == 0 ? __ldg(bL + o) : 0.f);
+            if (o < D) {
+              float v = y[o];
+#pragma unroll
+              for (int q = 1; q < STC_W / NPT; ++q) v += Xs[(q * ROWS + r) * 4 + o];
+              Js[(p * 3 + o) * 4 + c] = v + (c == 0 ? pw[PW_BL + o] : 0.f);
+            }
         }
         __syncthreads();
       }
@@ -444,31 +512,26 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
 #pragma unroll
         for (int o = 0; o < 3; ++o)
 #pragma unroll
-          for (int cc = 0; cc < 4; ++cc)
-            if (o < D) Gs[(tid * 3 + o) * 4 + cc] = G.u[o][cc];
+          for (int cc = 0; cc < 4; ++cc) Gs[(tid * 3 + o) * 4 + cc] = o < D ? G.u[o][cc] : 0.f;
       }
       __syncthreads();
       // ---- output layer, reverse: Hb^{L-1} = (W^L)^T yb (FP32); dW^L on the
       // tensor cores (At = stacked H^{L-1} transposed, B = yb transposed)
-      float hb[32];
+      float hb[NPT];
       {
+        const float* WL = pw + PW_WL;
         float yb[3];
 #pragma unroll
-        for (int o = 0; o < 3; ++o) yb[o] = o < D ? Gs[(p * 3 + o) * 4 + c] : 0.f;
+        for (int o = 0; o < 3; ++o) yb[o] = Gs[(p * 3 + o) * 4 + c];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float acc = 0.f;
-#pragma unroll
-          for (int o = 0; o < 3; ++o)
-            if (o < D && nb + j < wl) acc = fmaf(yb[o], __ldg(WL + o * wl + nb + j), acc);
-          hb[j] = acc;
-        }
-        if (!nb) {
+        for (int j = 0; j < NPT; ++j)
+          hb[j] = fmaf(yb[0], WL[nb + j], fmaf(yb[1], WL[64 + nb + j], yb[2] * WL[128 + nb + j]));
+        if (part == 0) {
 #pragma unroll
           for (int o = 0; o < 16; ++o) {
             const float2 s2 = tf32_split(o < 3 ? yb[o] : 0.f);
-            RA[s_off(o, r)] = s2.x;
-            RA[SZ_S + s_off(o, r)] = s2.y;
+            RS[s_off(o, r)] = s2.x;
+            RS[SZ_S + s_off(o, r)] = s2.y;
           }
           if (c == 0) {
 #pragma unroll
@@ -479,28 +542,29 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         __syncthreads();
         if (tid == 0) {
           after_sync();
-          mma_grad(tmem + 144 + 64 * (L - 2), st, sa, 4u * SZ_S, 4u * LB_S, 16, tile == 0);
+          mma_grad(tmem + 144 + 64 * (L - 2), st, ss, 4u * SZ_S, 4u * LB_S, 16, tile == 0);
           mma_commit(bars + 3);
         }
         d_pending = true;
       }
-      // ---- hidden layers, reverse
-      float sv[32], tv[32];
-      load_saved(S + (L - 2) * STC_W * ROWS, r, nb, gb, sv, tv);
+      // ---- hidden layers, reverse.  Hb^k of k < L - 1 is in tensor memory
+      // (the row MMA of the step before, already waited for).
+      float sv[NPT], tv[NPT];
+      load_saved(S_r + (L - 2) * STC_W * ROWS, gb, sv, tv);
       for (int k = L - 1; k >= 1; --k) {
-        if (k < L - 1) tmem_row32(tq + nb, tq + 64 + nb, hb);
-        float zb[32];
-        jet_bwd(sv, tv, hb, c, gb, zb);
-        if (d_pending) {   // the last gradient MMAs read region A and At
+        if (k < L - 1) tmem_rowz(tq + nb, tq + 64 + nb, hb);
+        jet_bwd(sv, tv, hb, c, gb, z);
+        split_all(z, zh, zl);
+        if (d_pending) {   // the last gradient MMAs read regions A, At and S
           mbar_wait(bars + 3, dph, a.err);
           dph ^= 1u;
           d_pending = false;
           after_sync();
         }
-        put_stacked(RT, zb, r, nb);
+        put_stacked(T_r, zh, zl);
         if (k >= 2) {
-          put_rows(RA, zb, r, nb);
-        } else if (!nb) {
+          put_rows(A_r, zh, zl);
+        } else if (part == 0) {
           // layer 1's input jets, transposed: value row (x, y, 1), x row
           // (1, 0, 0), y row (0, 1, 0), Laplacian row 0; column 2 gives db^1
           const float2 x = sp[p];
@@ -509,8 +573,8 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
             const float vj = j == 0 ? (c == 0 ? x.x : (c == 1 ? 1.f : 0.f))
                                     : (j == 1 ? (c == 0 ? x.y : (c == 2 ? 1.f : 0.f)) : (j == 2 && c == 0 ? 1.f : 0.f));
             const float2 s2 = tf32_split(vj);
-            RA[s_off(j, r)] = s2.x;
-            RA[SZ_S + s_off(j, r)] = s2.y;
+            RS[s_off(j, r)] = s2.x;
+            RS[SZ_S + s_off(j, r)] = s2.y;
           }
         }
         fence_to_async();
@@ -518,7 +582,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         if (k == 1) {
           if (tid == 0) {
             after_sync();
-            mma_grad(tmem + 128 + 64 * (L - 2), st, sa, 4u * SZ_S, 4u * LB_S, 16, tile == 0);
+            mma_grad(tmem + 128 + 64 * (L - 2), st, ss, 4u * SZ_S, 4u * LB_S, 16, tile == 0);
             mma_commit(bars + 3);
           }
           d_pending = true;
@@ -532,24 +596,26 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           mma_rows(tmem, sa, sw + 4u * STC_IMG * buf);
           mma_commit(bars + 2);
         }
-        // bias gradient: value rows of Zb^k from At (this thread: neuron
-        // tid & 63, points 8 (tid >> 6) .. + 7), while the MMAs run
+        // bias gradient: sums of the value rows of Zb^k over the warp's points
         {
-          const int n = tid & 63, p0 = (tid >> 6) * 8;
-          float sb = 0.f;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) sb += RT[t_off(n, 4 * (p0 + q))] + RT[t_off(64 + n, 4 * (p0 + q))];
-          dbs[(k - 2) * NTH + tid] += sb;
+          float sb[2];
+          value_row_sums(z, lane, sb);
+          if (c == 0) {
+            float* d = dbs + ((k - 2) * 4 + quad) * 64 + nb + 2 * (lane >> 2);
+            d[0] += sb[0];
+            d[1] += sb[1];
+          }
         }
-        // H^{k-1} from the saved jets of layer k - 1
-        load_saved(S + (k - 2) * STC_W * ROWS, r, nb, gb, sv, tv);
-        float hp[32];
-        jet_from_saved(sv, tv, c, hp);
-        mbar_wait(bars + 2, mph, a.err);
+        // H^{k-1} from the saved jets of layer k - 1 (which the next step's
+        // reverse rule uses too)
+        load_saved(S_r + (k - 2) * STC_W * ROWS, gb, sv, tv);
+        jet_from_saved(sv, tv, c, z);
+        split_all(z, zh, zl);
+        mbar_wait(bars + 2, mph, a.err);   // region A and the weight buffer are free
         mph ^= 1u;
         after_sync();
         if (tid == 0 && i + 2 < nimg) bulk_g2s(RW + STC_IMG * buf, img_src(i + 2), 4u * STC_IMG, bars + buf);
-        put_bt(RA, hp, r, nb);
+        put_bt(B_r, zh, zl);
         fence_to_async();
         __syncthreads();
         if (tid == 0) {
@@ -573,10 +639,10 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
     float* stg = quad < 2 ? st_hi : st_lo;
     const int m = r & 63;
     for (int k = 2; k <= L - 1; ++k) {
-      float v[32];
-      tmem_cols<32>(tq + 128 + 64 * (k - 2) + nb, v);
+      float v[NPT];
+      tmem_cols<NPT>(tq + 128 + 64 * (k - 2) + nb, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) stg[m * 65 + nb + j] = v[j];
+      for (int j = 0; j < NPT; ++j) stg[m * 65 + nb + j] = v[j];
       __syncthreads();
       const int wo = nd.w[k], wi = nd.w[k - 1];
       float* g = gs + nd.off[k];
@@ -586,7 +652,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
       }
       if (tid < wo) {
         float sb = 0.f;
-        for (int q = 0; q < 4; ++q) sb += dbs[(k - 2) * NTH + q * 64 + tid];
+        for (int q = 0; q < 4; ++q) sb += dbs[((k - 2) * 4 + q) * 64 + tid];
         g[wo * wi + tid] = sb;
       }
       __syncthreads();
@@ -596,7 +662,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
       float v1[16], vl[16];
       tmem_cols<16>(tq + 128 + 64 * (L - 2), v1);
       tmem_cols<16>(tq + 144 + 64 * (L - 2), vl);
-      if (!nb) {
+      if (part == 0) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           stg[m * 65 + j] = v1[j];
