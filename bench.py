@@ -160,8 +160,12 @@ def measured_peaks():
 
 def time_steps(torch, s, stream, flush, steps):
     """Time `steps` single steps, each alone: flush L2, then events around
-    the step on its stream.  Returns (step ms list, jet-kernel ms list)."""
+    the step on its stream.  Returns (step ms list, jet-kernel ms list); the
+    tensor-core kernel's ms of each step, when it runs, go to s.tc_ms."""
     step_ms, jet_ms = [], []
+    has_tc = s.plan_counts()[1] > 0 and s.options()["schedule"] == 0
+    if has_tc:
+        s.tc_ms = []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     for _ in range(steps):
@@ -173,6 +177,8 @@ def time_steps(torch, s, stream, flush, steps):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         jet_ms.append(float(s.phase_times()[2]))
+        if has_tc:
+            s.tc_ms.append(s.tc_kernel_ms())
     return step_ms, jet_ms
 
 
@@ -420,6 +426,34 @@ def roofline(pb, jet_ms, n_sm, name, s):
                          f"{sm_max:.0f} MHz (max SM clock in MEASURED_PEAKS.json)"}
 
 
+# TF32 dense tensor rate relative to BF16 (nominal 1.1 vs 2.25 PFLOP/s per GPU)
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def roofline_tc(pb, s, step_ms):
+    """The tensor-core training kernel (residual items of the width-64
+    networks) against the TF32 tensor peak: the measured BF16 burst figure
+    times the nominal TF32/BF16 ratio.  achieved = the algorithmic 6 K M FLOP
+    per residual point of those items / its CUDA-event time; the executed
+    tensor work is 10/3 of that (three TF32 products for the forward and
+    reverse contractions, four for the weight gradient)."""
+    n_items, n_tc, n_tc_sub = s.plan_counts()
+    if not n_tc:
+        return None
+    tc_ms = float(np.mean(s.tc_ms)) if getattr(s, "tc_ms", None) else s.tc_kernel_ms()
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops")
+    peak = bf16 * TF32_OVER_BF16 if bf16 else 1900.0 * TF32_OVER_BF16
+    flops = algorithmic_flops(pb)
+    achieved = flops / (tc_ms / 1e3) / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "kernel": "xp::step_tc_kernel (residual items, tcgen05 kind::tf32)", "kernel_ms": tc_ms,
+            "kernel_share_of_step": tc_ms / step_ms, "items": n_tc, "subdomains": n_tc_sub,
+            "flop_per_launch": flops, "executed_tensor_flop_per_launch": flops * 10.0 / 3.0,
+            "peak_note": ("TF32 dense peak = measured BF16 burst (MEASURED_PEAKS.json) x 1.1/2.25, the nominal "
+                          "TF32/BF16 ratio" if bf16 else "fallback 1.9 PFLOP/s BF16 x 1.1/2.25")}
+
+
 def loop_compare(torch, s, stream, flush, steps, ipcs, n_res, grouped_ms):
     """The per-subdomain launch loop (schedule 1) of the same kernels on the
     same handle, at its own best items-per-CTA; the grouped options are
@@ -452,6 +486,12 @@ def extra_workload(torch, X, name, stream, flush, steps, loop_steps, n_sm):
     out = {"workload": desc, "value": pb.n_res / (ms / 1e3), "unit": "pts/s", "ms_per_step": ms,
            "steps": steps, "residual_pts_per_step": pb.n_res, "options": s.options(),
            "roofline": roofline(pb, float(np.mean(jet_ms)), n_sm, name, s)}
+    tc = roofline_tc(pb, s, ms)
+    if tc:
+        # the residual items run on the tensor cores: their kernel is the one
+        # to hold against its roofline; the FP32 line covers the whole phase
+        out["roofline_fp32_phase"] = out.pop("roofline")
+        out["roofline"] = tc
     if loop_steps:
         out["loop"] = loop_compare(torch, s, stream, flush, loop_steps, (4, 16, 64), pb.n_res, ms)
     s.close()

@@ -374,15 +374,19 @@ typedef struct {
                                a hi/lo split of both operands, FP32
                                accumulation); other models keep the FP32 jet
                                kernel.  0: the jet kernel for every model */
-  int32_t train_tensor_cores; /* 0 (default): the FP32 jet kernel trains every
-                               subdomain.  N in [1, 64]: the residual points
-                               of every subdomain with one fixed-slope tanh
-                               network of input (x, y), identity output of at
-                               most 3 components, 3 to 7 weight layers and
-                               every hidden width within [N, 64], under a PDE
-                               trained with Laplacian jets (Poisson,
-                               Navier-Stokes), are trained by the tensor-core
-                               kernel: the forward, reverse and weight-gradient
+  int32_t train_tensor_cores; /* 0: the FP32 jet kernel trains every
+                               subdomain.  N in [1, 64] (default 64): the
+                               residual points of every subdomain with one
+                               fixed-slope tanh network of input (x, y),
+                               identity output of at most 3 components, 3 to
+                               7 weight layers and every hidden width within
+                               [N, 64], under a PDE trained with Laplacian
+                               jets (Poisson, Navier-Stokes), are trained by
+                               the tensor-core kernel when those subdomains
+                               hold at least half of the residual points (it
+                               runs before the jet kernel, so it only pays off
+                               when it takes over most of the step): the
+                               forward, reverse and weight-gradient
                                contractions of the hidden-to-hidden layers as
                                tcgen05 MMAs (three TF32 products over hi/lo
                                splits of both operands, FP32 accumulation),
@@ -446,6 +450,13 @@ int xpinn_plan_counts(xpinn_handle h, int32_t* n_items, int32_t* n_tc, int32_t* 
  * the stream is being captured).  Waits for that kernel.  Errors: INVALID if
  * no evaluation has been timed. */
 int xpinn_eval_kernel_time(xpinn_handle h, float* ms);
+
+/* Device time in milliseconds of the tensor-core training kernel (option
+ * train_tensor_cores) in the most recent grouped step or grad call made with
+ * profile_phases = 1, from CUDA events recorded around its launch (inside
+ * the step graph too).  Part of ms[2] of xpinn_phase_times.  Waits for that
+ * kernel.  Errors: INVALID if no such step has been timed. */
+int xpinn_tc_kernel_time(xpinn_handle h, float* ms);
 
 /* Interface exchange buffer after the last grad/step: for every interface
  * (in order), every point, side 0 (q) then side 1 (q_plus): the solution

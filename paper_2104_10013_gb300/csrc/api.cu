@@ -229,9 +229,10 @@ struct xpinn_ctx {
   int n_sm = 0, grid = 0;
   int ring_cap = 256;
   int host_t = 0, host_slot = 0;
-  xpinn_options opt{0, 1, 4, 2, 0, 0, 256, 0, 1, 0};
+  xpinn_options opt{0, 1, 4, 2, 0, 0, 256, 0, 1, STC_W};
   int device = 0;
-  cudaEvent_t ev[5] = {};
+  cudaEvent_t ev[6] = {};         // phase marks 0-4, and 5 after the tensor-core kernel
+  bool tc_timed = false;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;        // one training step
   cudaGraphExec_t graph_multi = nullptr;  // GRAPH_STEPS training steps back to back
@@ -382,13 +383,22 @@ void build_plan(xpinn_ctx* h, int p_cap) {
   std::vector<char> tcq(h->n_sub, 0);
   double tc_total = 0;
   bool any_tc = false;
+  int64_t tc_pts = 0;
   for (int q = 0; q < h->n_sub; ++q) {
     const SubDev& sd = h->subs[q];
     if (sd.n_res && step_tc_net_ok(sd.net[0], sd.n_nets, h->pde, h->opt.train_tensor_cores)) {
       tcq[q] = 1;
       any_tc = true;
       tc_total += (double)sd.n_res * (sd.net[0].L - 1);
+      tc_pts += sd.n_res;
     }
+  }
+  // the tensor-core kernel runs before the jet kernel, so it pays off only
+  // when it takes over most of the step: at least half of the residual points
+  if (any_tc && 2 * tc_pts < h->n_res_total) {
+    std::fill(tcq.begin(), tcq.end(), 0);
+    any_tc = false;
+    tc_total = 0;
   }
   // first pass: one item per point set, to estimate the total cost (with
   // tensor-core residual items, of everything the jet kernel still runs)
@@ -442,7 +452,10 @@ void build_plan(xpinn_ctx* h, int p_cap) {
     if (sd.n_res && tcq[q]) {
       Item proto = mk(IT_RES, q, -1, 0, sd.res_off, sd.n_res, 4, 0);
       proto.P = STC_PTS;
-      int per = (int)std::ceil(tc_target / (sd.net[0].L - 1));
+      // grouped: about tc_ipc items per CTA over the whole launch; loop
+      // schedule: each subdomain's own launch gets two items per SM
+      int per = h->opt.schedule == 1 ? (int)std::ceil(sd.n_res / (2.0 * std::max(1, h->n_sm)))
+                                     : (int)std::ceil(tc_target / (sd.net[0].L - 1));
       per = std::max(4 * STC_PTS, (per + STC_PTS - 1) / STC_PTS * STC_PTS);
       const int chunks = (sd.n_res + per - 1) / per;
       per = ((sd.n_res + chunks - 1) / chunks + STC_PTS - 1) / STC_PTS * STC_PTS;
@@ -834,6 +847,7 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads, int par
   r.jq = h->jq.p;
   const int tc0 = pl.n_simt(), tc_ctr = 3 + 2 * h->n_sub;
   if (part == 2) {
+    h->tc_timed = false;
     if (pl.n_tc) {
       pack_tc_train(h, s);
       launch_tc(h, tc0, pl.n_tc, tc_ctr, s);
@@ -848,6 +862,8 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads, int par
     mark(h, 2, s);
     // residual items of the tensor-core kernel first, then the jet kernel's
     launch_tc(h, tc0, pl.n_tc, tc_ctr, s);
+    if (pl.n_tc) mark(h, 5, s);
+    h->tc_timed = pl.n_tc > 0 && h->opt.profile_phases;
     const int n_all = pl.n_simt();
     if (n_all) {
       StepArgs a = args_for(h, 0, n_all, 0);
@@ -858,6 +874,7 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads, int par
     mark(h, 3, s);
     launch_reduce_adam(r, s);
   } else {
+    h->tc_timed = false;
     if (pl.n_tc) pack_tc_train(h, s);
     mark(h, 1, s);
     for (int q = 0; q < h->n_sub; ++q) {
@@ -2484,6 +2501,16 @@ int xpinn_plan_counts(xpinn_handle h, int32_t* n_items, int32_t* n_tc, int32_t* 
       }
     *n_tc_sub = c;
   }
+  API_END
+}
+
+int xpinn_tc_kernel_time(xpinn_handle h, float* ms) {
+  API_BEGIN
+  if (!h || !ms) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  if (!h->tc_timed) fail(XPINN_ERR_INVALID, "no grouped step with tensor-core items timed (profile_phases off)");
+  ck(cudaEventSynchronize(h->ev[5]), "event sync");
+  ck(cudaEventElapsedTime(ms, h->ev[2], h->ev[5]), "elapsed");
   API_END
 }
 

@@ -33,7 +33,10 @@
 // 128 M-rows (0-63 hi, 64-127 lo) and issues two MMAs, B = H_hi and B = H_lo:
 // lanes 0-63 accumulate hi.H_hi + hi.H_lo, lanes 64-127 lo.H_hi + lo.H_lo,
 // and dW^k is their sum (all four products at the MMA's full M = 128).  The
-// dW^k accumulators stay in tensor memory over all tiles of the item.
+// dW^k accumulators stay in tensor memory over 16 tiles and are then added
+// into the item's gradient slice in FP32: a single accumulator over the
+// whole item (about 80 tiles) erred up to 1.04e-4 of the largest gradient
+// element on the full-size Navier-Stokes workload.
 //
 // Operands are K-major, no swizzle.  Images whose K is the tile's rows pad
 // every K-step of core matrices by 16 bytes so that a warp's 32 rows of one
@@ -76,20 +79,23 @@ static_assert(2 * SZ_AF <= SZ_RA && RA_G + 384 <= SZ_RA && 2 * 64 * 65 <= SZ_RA,
 constexpr int PW_W1 = 0, PW_B1 = 128, PW_BK = 192, PW_WL = PW_BK + 64 * (STC_MAXL - 2), PW_BL = PW_WL + 192;
 constexpr int SZ_PW = PW_BL + 4;
 // shared-memory map (floats): region A, At, two weight buffers, the [16][rows]
-// images, the points, the bias-gradient partials [STC_MAXL - 2][4 lane
+// images, the points of two tiles, the bias-gradient partials [STC_MAXL - 2][4 lane
 // quadrants][64] and [32 points][4], the FP32-pipe weights
 constexpr int O_A = 0;
 constexpr int O_T = O_A + SZ_RA;
 constexpr int O_W = O_T + SZ_T;
 constexpr int O_S = O_W + 2 * STC_IMG;
 constexpr int O_P = O_S + 2 * SZ_S;
-constexpr int O_DB = O_P + 64;
+constexpr int O_DB = O_P + 128;
 constexpr int O_DL = O_DB + (STC_MAXL - 2) * 4 * 64;
 constexpr int O_PW = O_DL + 128;
 constexpr int SMEM_FLOATS = O_PW + SZ_PW;
 // tensor-memory columns: Z main [0, 64), Z cross [64, 128), dW^k (k = 2..L-1)
 // at 128 + 64 (k - 2), then dW^1 and dW^L (16 columns each)
 constexpr int TMEM_COLS = 512;
+// tiles a weight-gradient accumulator sums before it is added into the
+// item's slice (bounds the length of each tensor-memory accumulation)
+constexpr int STC_FLUSH = 16;
 static_assert(128 + 64 * (STC_MAXL - 2) + 32 <= TMEM_COLS, "tensor memory");
 
 // element offsets in the images whose K is the rows (column n, row r); for
@@ -105,41 +111,74 @@ __device__ __forceinline__ void fence_to_async() {
 }
 __device__ __forceinline__ void after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// mbar_wait with a suspend-time hint: a warp that finds the phase
+// incomplete is parked in the barrier until the phase completes (or the hint
+// of 10 ms runs out) instead of polling, so that waiting warps take no issue
+// slots from working ones.  Bounded like mbar_wait: about a second, then the
+// error word holds XPINN_ERR_TIMEOUT.
+__device__ __forceinline__ void mbar_park(uint64_t* bar, uint32_t parity, int* err) {
+  const long long t0 = clock64();
+  long long limit = 0;
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(10000000u)
+        : "memory");
+    if (ok) return;
+    if (limit == 0)
+      limit = *reinterpret_cast<volatile int*>(err) == XPINN_ERR_TIMEOUT ? (1ll << 21) : (1ll << 31);
+    if (clock64() - t0 > limit) {
+      atomicCAS(err, 0, XPINN_ERR_TIMEOUT);
+      return;
+    }
+  }
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
+
+// Descriptors of successive K-steps differ only in the start address (bits
+// 0-13, in 16-byte units): each MMA adds its step's offset to a base
+// descriptor built once per call, so that issuing a layer's MMAs costs few
+// instructions on the issuing thread.
+__device__ __forceinline__ uint64_t dstep(int bytes) { return (uint64_t)(bytes >> 4); }
 
 // Z (+)= A . B over K = 64: A the row-major image at a (hi, then lo), read
 // K-major; B a weight image at b (hi, then lo); hi x hi into tm, the cross
 // terms into tm + 64.
 __device__ __forceinline__ void mma_rows(uint32_t tm, uint32_t a, uint32_t b) {
   const uint32_t id = tc_idesc(STC_W);
+  const uint64_t ahi = tc_sdesc(a, TC_A_LBO, 128), alo = tc_sdesc(a + 4 * SZ_AF, TC_A_LBO, 128);
+  const uint64_t bhi = tc_sdesc(b, 128, STC_W / 4 * 128);
+  const uint64_t blo = tc_sdesc(b + 4 * STC_W * STC_W, 128, STC_W / 4 * 128);
 #pragma unroll
   for (int ks = 0; ks < STC_W / 8; ++ks) {
-    const uint64_t ahi = tc_sdesc(a + ks * 2 * TC_A_LBO, TC_A_LBO, 128);
-    const uint64_t alo = tc_sdesc(a + 4 * SZ_AF + ks * 2 * TC_A_LBO, TC_A_LBO, 128);
-    const uint64_t bhi = tc_sdesc(b + ks * 256, 128, STC_W / 4 * 128);
-    const uint64_t blo = tc_sdesc(b + 4 * STC_W * STC_W + ks * 256, 128, STC_W / 4 * 128);
-    tc_mma(tm, ahi, bhi, id, ks > 0 ? 1u : 0u);
-    tc_mma(tm + 64, ahi, blo, id, ks > 0 ? 1u : 0u);
-    tc_mma(tm + 64, alo, bhi, id, 1u);
+    const uint64_t da = dstep(ks * 2 * TC_A_LBO), db = dstep(ks * 256);
+    tc_mma(tm, ahi + da, bhi + db, id, ks > 0 ? 1u : 0u);
+    tc_mma(tm + 64, ahi + da, blo + db, id, ks > 0 ? 1u : 0u);
+    tc_mma(tm + 64, alo + da, bhi + db, id, 1u);
   }
 }
 
 // D (+)= At . B over K = 128 rows: At the stacked image at t, B an [N][rows]
-// image at b (hi) and b + lo_bytes (lo) with lb bytes between K-adjacent core
+// image at b (hi) and b + lo_bytes (lo) with LB bytes between K-adjacent core
 // matrices; N = n.  first: the accumulator starts at zero.
-__device__ __forceinline__ void mma_grad(uint32_t tm, uint32_t t, uint32_t b, uint32_t lo_bytes, uint32_t lb,
-                                         int n, bool first) {
+template <int LB>
+__device__ __forceinline__ void mma_grad(uint32_t tm, uint32_t t, uint32_t b, uint32_t lo_bytes, int n, bool first) {
   const uint32_t id = tc_idesc(n);
-#pragma unroll 4
+  const uint64_t at = tc_sdesc(t, LB_T * 4, 128);
+  const uint64_t bh = tc_sdesc(b, LB, 128), bl = tc_sdesc(b + lo_bytes, LB, 128);
+#pragma unroll
   for (int ks = 0; ks < ROWS / 8; ++ks) {
-    const uint64_t at = tc_sdesc(t + ks * 2 * LB_T * 4, LB_T * 4, 128);
-    const uint64_t bh = tc_sdesc(b + ks * 2 * lb, lb, 128);
-    const uint64_t bl = tc_sdesc(b + lo_bytes + ks * 2 * lb, lb, 128);
-    tc_mma(tm, at, bh, id, (first && ks == 0) ? 0u : 1u);
-    tc_mma(tm, at, bl, id, 1u);
+    const uint64_t dt = dstep(ks * 2 * LB_T * 4), db = dstep(ks * 2 * LB);
+    tc_mma(tm, at + dt, bh + db, id, (first && ks == 0) ? 0u : 1u);
+    tc_mma(tm, at + dt, bl + db, id, 1u);
   }
 }
 
@@ -315,7 +354,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   float* Xs = RA + RA_X;
   float* Js = RA + RA_J;
   float* Gs = RA + RA_G;
-  float2* sp = reinterpret_cast<float2*>(sm + O_P);
+  float2* const sp2 = reinterpret_cast<float2*>(sm + O_P);   // points: this tile's and the next one's
   float* dbs = sm + O_DB;
   float* dls = sm + O_DL;
   float* pw = sm + O_PW;
@@ -404,13 +443,14 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
     if (tid < 128) dls[tid] = 0.f;
     double l0 = 0.0;
     const int n_tiles = (it.n_pts + STC_PTS - 1) / STC_PTS;
+    if (tid < STC_PTS) sp2[tid] = tid < it.n_pts ? a.pts[it.pt_off + tid] : make_float2(0.f, 0.f);
     for (int tile = 0; tile < n_tiles; ++tile) {
       const int t0 = tile * STC_PTS;
       const int nv = min(STC_PTS, it.n_pts - t0);
       // every MMA of the previous tile has completed: both weight buffers and
       // regions A, At and S are free
       if (d_pending) {
-        mbar_wait(bars + 3, dph, a.err);
+        mbar_park(bars + 3, dph, a.err);
         dph ^= 1u;
         d_pending = false;
       }
@@ -418,7 +458,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         bulk_g2s(RW, img_src(0), 4u * STC_IMG, bars);
         if (nimg > 1) bulk_g2s(RW + STC_IMG, img_src(1), 4u * STC_IMG, bars + 1);
       }
-      if (tid < STC_PTS) sp[tid] = tid < nv ? a.pts[it.pt_off + t0 + tid] : make_float2(0.f, 0.f);
+      const float2* sp = sp2 + (tile & 1) * STC_PTS;
       __syncthreads();
       float z[NPT], zh[NPT], zl[NPT];
       // ---- layer 1: z = W^1 x + b^1, z_x = W^1[:, 0], z_y = W^1[:, 1], z_lap = 0
@@ -446,7 +486,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           mma_rows(tmem, sa, sw + 4u * STC_IMG * buf);
           mma_commit(bars + 2);
         }
-        mbar_wait(bars + 2, mph, a.err);
+        mbar_park(bars + 2, mph, a.err);
         mph ^= 1u;
         after_sync();
         if (tid == 0 && i + 2 < nimg) bulk_g2s(RW + STC_IMG * buf, img_src(i + 2), 4u * STC_IMG, bars + buf);
@@ -526,6 +566,11 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
 #pragma unroll
         for (int j = 0; j < NPT; ++j)
           hb[j] = fmaf(yb[0], WL[nb + j], fmaf(yb[1], WL[64 + nb + j], yb[2] * WL[128 + nb + j]));
+        // the next tile's points, read while this tile's reverse pass runs
+        if (tid < STC_PTS && tile + 1 < n_tiles) {
+          const int t1 = t0 + STC_PTS + tid;
+          sp2[((tile + 1) & 1) * STC_PTS + tid] = t1 < it.n_pts ? a.pts[it.pt_off + t1] : make_float2(0.f, 0.f);
+        }
         if (part == 0) {
 #pragma unroll
           for (int o = 0; o < 16; ++o) {
@@ -542,7 +587,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         __syncthreads();
         if (tid == 0) {
           after_sync();
-          mma_grad(tmem + 144 + 64 * (L - 2), st, ss, 4u * SZ_S, 4u * LB_S, 16, tile == 0);
+          mma_grad<4 * LB_S>(tmem + 144 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, tile % STC_FLUSH == 0);
           mma_commit(bars + 3);
         }
         d_pending = true;
@@ -556,7 +601,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         jet_bwd(sv, tv, hb, c, gb, z);
         split_all(z, zh, zl);
         if (d_pending) {   // the last gradient MMAs read regions A, At and S
-          mbar_wait(bars + 3, dph, a.err);
+          mbar_park(bars + 3, dph, a.err);
           dph ^= 1u;
           d_pending = false;
           after_sync();
@@ -582,7 +627,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         if (k == 1) {
           if (tid == 0) {
             after_sync();
-            mma_grad(tmem + 128 + 64 * (L - 2), st, ss, 4u * SZ_S, 4u * LB_S, 16, tile == 0);
+            mma_grad<4 * LB_S>(tmem + 128 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, tile % STC_FLUSH == 0);
             mma_commit(bars + 3);
           }
           d_pending = true;
@@ -611,7 +656,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         load_saved(S_r + (k - 2) * STC_W * ROWS, gb, sv, tv);
         jet_from_saved(sv, tv, c, z);
         split_all(z, zh, zl);
-        mbar_wait(bars + 2, mph, a.err);   // region A and the weight buffer are free
+        mbar_park(bars + 2, mph, a.err);   // region A and the weight buffer are free
         mph ^= 1u;
         after_sync();
         if (tid == 0 && i + 2 < nimg) bulk_g2s(RW + STC_IMG * buf, img_src(i + 2), 4u * STC_IMG, bars + buf);
@@ -620,72 +665,79 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         __syncthreads();
         if (tid == 0) {
           after_sync();
-          mma_grad(tmem + 128 + 64 * (k - 2), st, sa, 4u * SZ_B, 4u * LB_B, STC_W, tile == 0);
+          mma_grad<4 * LB_B>(tmem + 128 + 64 * (k - 2), st, sa, 4u * SZ_B, STC_W, tile % STC_FLUSH == 0);
           mma_commit(bars + 3);
         }
         d_pending = true;
       }
-    }
-    // ---- the item's gradient slice and loss
-    if (d_pending) {
-      mbar_wait(bars + 3, dph, a.err);
-      dph ^= 1u;
-      d_pending = false;
-    }
-    after_sync();
-    float* gs = a.partials + it.part_off;
-    float* st_hi = RA;             // [64][65]: lanes 0-63 (hi parts)
-    float* st_lo = RA + 64 * 65;   // lanes 64-127 (lo parts)
-    float* stg = quad < 2 ? st_hi : st_lo;
-    const int m = r & 63;
-    for (int k = 2; k <= L - 1; ++k) {
-      float v[NPT];
-      tmem_cols<NPT>(tq + 128 + 64 * (k - 2) + nb, v);
-#pragma unroll
-      for (int j = 0; j < NPT; ++j) stg[m * 65 + nb + j] = v[j];
-      __syncthreads();
-      const int wo = nd.w[k], wi = nd.w[k - 1];
-      float* g = gs + nd.off[k];
-      for (int e = tid; e < wo * wi; e += NTH) {
-        const int n = e / wi, j = e - n * wi;
-        g[e] = st_hi[n * 65 + j] + st_lo[n * 65 + j];
-      }
-      if (tid < wo) {
-        float sb = 0.f;
-        for (int q = 0; q < 4; ++q) sb += dbs[((k - 2) * 4 + q) * 64 + tid];
-        g[wo * wi + tid] = sb;
-      }
-      __syncthreads();
-    }
-    {
-      // dW^1 (columns 0, 1) and db^1 (column 2); dW^L (columns o < D), transposed
-      float v1[16], vl[16];
-      tmem_cols<16>(tq + 128 + 64 * (L - 2), v1);
-      tmem_cols<16>(tq + 144 + 64 * (L - 2), vl);
-      if (part == 0) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          stg[m * 65 + j] = v1[j];
-          stg[m * 65 + 16 + j] = vl[j];
+      // ---- flush the weight-gradient accumulators into the item's slice
+      // every STC_FLUSH tiles and after the last: each accumulator then sums
+      // at most STC_FLUSH tiles, and the flushes add in FP32 in tile order
+      if (tile + 1 == n_tiles || (tile + 1) % STC_FLUSH == 0) {
+        const bool add = tile >= STC_FLUSH, last = tile + 1 == n_tiles;
+        if (d_pending) {
+          mbar_park(bars + 3, dph, a.err);
+          dph ^= 1u;
+          d_pending = false;
         }
-      }
-      __syncthreads();
-      const int w1 = nd.w[1];
-      if (tid < w1) {
-        float* g = gs + nd.off[1];
-        g[2 * tid] = st_hi[tid * 65] + st_lo[tid * 65];
-        g[2 * tid + 1] = st_hi[tid * 65 + 1] + st_lo[tid * 65 + 1];
-        g[2 * w1 + tid] = st_hi[tid * 65 + 2] + st_lo[tid * 65 + 2];
-      }
-      float* g = gs + nd.off[L];
-      for (int e = tid; e < D * wl; e += NTH) {
-        const int o = e / wl, n = e - o * wl;
-        g[e] = st_hi[n * 65 + 16 + o] + st_lo[n * 65 + 16 + o];
-      }
-      if (tid < D) {
-        float sb = 0.f;
-        for (int q = 0; q < STC_PTS; ++q) sb += dls[q * 4 + tid];
-        g[D * wl + tid] = sb;
+        after_sync();
+        float* gs = a.partials + it.part_off;
+        float* st_hi = RA;             // [64][65]: lanes 0-63 (hi parts)
+        float* st_lo = RA + 64 * 65;   // lanes 64-127 (lo parts)
+        float* stg = quad < 2 ? st_hi : st_lo;
+        const int m = r & 63;
+        for (int k = 2; k <= L - 1; ++k) {
+          float v[NPT];
+          tmem_cols<NPT>(tq + 128 + 64 * (k - 2) + nb, v);
+#pragma unroll
+          for (int j = 0; j < NPT; ++j) stg[m * 65 + nb + j] = v[j];
+          __syncthreads();
+          const int wo = nd.w[k], wi = nd.w[k - 1];
+          float* g = gs + nd.off[k];
+          for (int e = tid; e < wo * wi; e += NTH) {
+            const int n = e / wi, j = e - n * wi;
+            g[e] = (add ? g[e] : 0.f) + (st_hi[n * 65 + j] + st_lo[n * 65 + j]);
+          }
+          if (last && tid < wo) {
+            float sb = 0.f;
+            for (int q = 0; q < 4; ++q) sb += dbs[((k - 2) * 4 + q) * 64 + tid];
+            g[wo * wi + tid] = sb;
+          }
+          __syncthreads();
+        }
+        {
+          // dW^1 (columns 0, 1) and db^1 (column 2); dW^L (columns o < D), transposed
+          float v1[16], vl[16];
+          tmem_cols<16>(tq + 128 + 64 * (L - 2), v1);
+          tmem_cols<16>(tq + 144 + 64 * (L - 2), vl);
+          if (part == 0) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              stg[m * 65 + j] = v1[j];
+              stg[m * 65 + 16 + j] = vl[j];
+            }
+          }
+          __syncthreads();
+          const int w1 = nd.w[1];
+          if (tid < w1) {
+            float* g = gs + nd.off[1];
+            g[2 * tid] = (add ? g[2 * tid] : 0.f) + (st_hi[tid * 65] + st_lo[tid * 65]);
+            g[2 * tid + 1] = (add ? g[2 * tid + 1] : 0.f) + (st_hi[tid * 65 + 1] + st_lo[tid * 65 + 1]);
+            g[2 * w1 + tid] = (add ? g[2 * w1 + tid] : 0.f) + (st_hi[tid * 65 + 2] + st_lo[tid * 65 + 2]);
+          }
+          float* g = gs + nd.off[L];
+          for (int e = tid; e < D * wl; e += NTH) {
+            const int o = e / wl, n = e - o * wl;
+            g[e] = (add ? g[e] : 0.f) + (st_hi[n * 65 + 16 + o] + st_lo[n * 65 + 16 + o]);
+          }
+          if (last && tid < D) {
+            float sb = 0.f;
+            for (int q = 0; q < STC_PTS; ++q) sb += dls[q * 4 + tid];
+            g[D * wl + tid] = sb;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();   // region A is rewritten by the next tile
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

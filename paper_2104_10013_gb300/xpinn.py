@@ -121,6 +121,7 @@ def load() -> C.CDLL:
         "xpinn_phase_times": (C.c_int, [vp, fp]),
         "xpinn_plan_counts": (C.c_int, [vp, vp, vp, vp]),
         "xpinn_eval_kernel_time": (C.c_int, [vp, C.POINTER(C.c_float)]),
+        "xpinn_tc_kernel_time": (C.c_int, [vp, C.POINTER(C.c_float)]),
         "xpinn_autotune": (C.c_int, [vp, i32, C.POINTER(Options), C.POINTER(C.c_float)]),
         "xpinn_autotune_shapes": (C.c_int, [vp, i32, C.POINTER(C.c_float)]),
         "xpinn_step_begin": (C.c_int, [vp, vp]),
@@ -512,6 +513,13 @@ class Solver:
         v = (C.c_int32 * 3)()
         _check(self.lib.xpinn_plan_counts(self.h, C.byref(v, 0), C.byref(v, 4), C.byref(v, 8)))
         return int(v[0]), int(v[1]), int(v[2])
+
+    def tc_kernel_ms(self) -> float:
+        """Device ms of the tensor-core training kernel in the last grouped
+        step or grad call made with profile_phases on."""
+        ms = C.c_float(0)
+        _check(self.lib.xpinn_tc_kernel_time(self.h, C.byref(ms)))
+        return ms.value
 
     def eval_kernel_ms(self) -> float:
         """Device ms of the evaluation kernel of the last routed evaluation

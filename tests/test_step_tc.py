@@ -56,6 +56,9 @@ def test_tensor_core_grad_matches_the_oracle(X, name):
 
 
 def test_tensor_core_items_are_deterministic_and_schedule_independent(X):
+    """Repeated gradients agree bit for bit; the per-subdomain loop schedule
+    (which cuts each subdomain's residual points into two items per SM so
+    that its own launch fills the GPU) agrees within the tolerances."""
     pb = poisson_mixed()
     s = solver(X, pb, 40)
     l1, g1 = s.grad()
@@ -64,7 +67,8 @@ def test_tensor_core_items_are_deterministic_and_schedule_independent(X):
     s.set_options(schedule=1)
     assert s.plan_counts()[1] > 0
     l3, g3 = s.grad()
-    assert np.array_equal(g1, g3) and np.array_equal(l1, l3)
+    assert_losses(l3, l1)
+    assert_grads(g3, g1.astype(np.float64), pb)
     s.close()
 
 
