@@ -10,8 +10,11 @@ PDEs (Poisson, Navier-Stokes).
   zero-padded to 64, two to five hidden layers) with one-hidden-layer
   networks that stay on the jet kernel in the same step; point counts leave
   ragged tiles (32 points) and ragged items;
+* the smallest network the kernel takes (one hidden-to-hidden layer of width
+  33, zero-padded to 64) and items longer than one accumulator flush (16
+  tiles) on a large workload, sampled against the oracle;
 * Adam steps follow the oracle given the gradient, repeated gradients agree
-  bit for bit, and so do the grouped and per-subdomain loop schedules;
+  bit for bit, and the per-subdomain loop schedule agrees within tolerance;
 * the result lies within the tolerances of the FP32 jet kernel's.
 """
 import numpy as np
@@ -103,3 +106,40 @@ def test_tensor_core_adam_steps_follow_the_oracle(X):
         terms, g_ref = orc.grad(th)
         assert_grads(g, g_ref, pb)
     s.close()
+
+
+def test_narrowest_shallowest_network_on_the_tensor_cores(X):
+    """2 -> 33 x 2 -> 1: one hidden-to-hidden layer, 31 zero-padded neurons."""
+    pb = P.poisson_xpinn(nx=2, ny=1, n_res_range=(300, 400), width_range=(33, 33), depth_range=(2, 2),
+                         n_iface=24, n_bc=20, seed=5)
+    s = solver(X, pb, 33)
+    assert s.plan_counts()[2] == 2
+    losses, g = s.grad()
+    terms, g_ref = Oracle(pb).grad(pb.packed_params())
+    assert_losses(losses, terms)
+    assert_grads(g, g_ref, pb)
+    s.close()
+
+
+def test_items_longer_than_a_flush_sampled():
+    """4 x 200k residual points: items of about 21 tiles, so each item's
+    gradient accumulators are flushed into its slice once mid-item and once
+    at its end; the oracle checks one whole subdomain."""
+    from paper_2104_10013_gb300 import build as B
+    from paper_2104_10013_gb300 import xpinn as XX
+    B.build()
+    XX.load()
+    pb = P.kovasznay_cpinn(nx=2, ny=2, n_res=200_000, n_iface=64, n_bc=40)
+    s = XX.Solver(pb)
+    n_items, n_tc, _ = s.plan_counts()
+    assert 800_000 / n_tc > 16 * 32, n_tc   # items span more than one flush of 16 tiles
+    losses, g = s.grad()
+    s.close()
+    terms, g_ref = Oracle(pb).grad(pb.packed_params(), subset=[1])
+    assert_losses(losses[[1]], terms)
+    from tests.test_parity import tensor_slices
+    for name, sl in tensor_slices(pb):
+        if name.startswith("q1n"):
+            a, b = g[sl].astype(np.float64), g_ref[sl]
+            assert np.linalg.norm(a - b) <= RTOL_GRAD * np.linalg.norm(b), name
+            assert np.abs(a - b).max() <= RTOL_GRAD * np.abs(b).max(), name
