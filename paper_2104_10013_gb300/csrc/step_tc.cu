@@ -5,7 +5,7 @@
 // step_tc.h admits) the kernel computes what the FP32 jet kernel computes for
 // it: the Taylor jets of the network (Sec. 3) at the points, the PDE
 // residual term of Eq. cPINNLoss / Eq. XPINNLoss (Sec. 4.2) and its gradient
-// with respect to every weight and bias, written once to the item's gradient
+// with respect to every weight and bias, written to the item's gradient
 // slice, and the item's loss sum.  The three point-by-width contractions of
 // every hidden-to-hidden layer k run on the tensor cores:
 //   forward    Z^k  = H^{k-1} (W^k)^T           [128 rows x 64] . [64 x 64]
@@ -15,15 +15,18 @@
 // the jet rules and the residual stay on the FP32 pipes.
 //
 // Tile: 128 rows = the MMA's M, 32 points x 4 jet components (u, u_x, u_y,
-// lap u) with the components of a point in 4 adjacent lanes; four threads per
-// row (warps w, w + 4, w + 8 and w + 12 share tensor-memory lanes), each
-// owning 16 of the 64 neurons.  The jet rule of tanh (h = t, h_i = s z_i, h_lap = s z_lap -
-// 2 t s (z_x^2 + z_y^2), t = tanh z, s = 1 - t^2) and its reverse exchange
-// t, hbar_lap and the sums over a point's rows by warp shuffles; tanh itself
-// is evaluated once per (point, neuron), spread over the point's 4 lanes.
-// Pre-activation jets (t on the value row, z_c on the others) go to per-CTA
-// scratch in global memory (L2-resident) for the reverse pass, which
-// rebuilds H^{k-1} from them.
+// lap u), row 4 p + c.  512 threads take two roles.  As row threads (four per
+// row: warps w, w + 4, w + 8, w + 12 read the same tensor-memory lanes, 16 of
+// the 64 neurons each) they move accumulator rows out of tensor memory into a
+// staging array [point][component][neuron].  As point threads (lane = point,
+// warp = a group of 4 neurons) they apply the jet rule of tanh to all four
+// components of a point at once, in registers:
+//   h = t,  h_i = s z_i,  h_lap = s z_lap - 2 t s (z_x^2 + z_y^2),  t = tanh z,
+// s = 1 - t^2, and its reverse, and write the MMA operand images: 4 rows of one
+// neuron are one 16-byte run in every image, transposed or not.  tanh is
+// evaluated once per (point, neuron).  The pre-activation jets (t, z_x, z_y,
+// z_lap) go to per-CTA scratch in global memory (L2-resident) for the reverse
+// pass, which rebuilds H^{k-1} from them.
 //
 // Precision: every contraction takes three TF32 products over hi/lo splits
 // of both operands (hi = rna(x), lo = rna(x - hi); the dropped lo x lo term
@@ -39,12 +42,11 @@
 // element on the full-size Navier-Stokes workload.
 //
 // Operands are K-major, no swizzle.  Images whose K is the tile's rows pad
-// every K-step of core matrices by 16 bytes so that a warp's 32 rows of one
-// column store into 32 different banks.  Weight images (forward and reverse,
-// built by pack_tc_train_kernel) arrive by bulk copy into two buffers, the
-// copy of the image after next issued as soon as an MMA has released its
-// buffer.  Every wait is bounded; a wait that gives up sets the error word,
-// the launch stops taking items, frees its tensor memory and ends.
+// every K-step of core matrices by 16 bytes.  Weight images (forward and
+// reverse, built by pack_tc_train_kernel) arrive by bulk copy into one buffer,
+// the next image's copy issued as soon as an MMA has released it (it lands
+// during the epilogue).  Every wait is bounded; a wait that gives up sets the
+// error word, the launch stops taking items, frees its tensor memory and ends.
 #include <cuda_runtime.h>
 
 #include "jet_step.cuh"
@@ -55,39 +57,51 @@ namespace xp {
 
 namespace {
 
-constexpr int NPT = 16;                  // neurons of a thread (of the 64)
-constexpr int NTH = 128 * (STC_W / NPT); // four threads per row
+constexpr int NPT = 16;                  // neurons of a row thread (of the 64)
+constexpr int NTH = 128 * (STC_W / NPT); // four row threads per row; 16 warps of point threads
+constexpr int NPG = 4;                   // neurons of a point thread
 constexpr int ROWS = 128;
 constexpr unsigned FULL = 0xffffffffu;
 // K-major images whose K is the tile's rows: floats between K-adjacent core
-// matrices, padded by 16 bytes so that a warp's 32 rows of one column store
-// into 32 different banks
+// matrices, padded by 16 bytes (conflict-free 16-byte stores across points)
 constexpr int LB_B = 8 * 32 + 4;    // B' = H^T [N = 64][K = rows]: 1040 bytes
 constexpr int LB_T = 16 * 32 + 4;   // At = stacked Zb^T [M = 128][K = rows]: 2064 bytes
 constexpr int LB_S = 2 * 32 + 4;    // [N = 16][K = rows] (input jets, output seeds): 272 bytes
 constexpr int SZ_B = 32 * LB_B;     // one B' image (hi or lo)
 constexpr int SZ_T = 32 * LB_T;
 constexpr int SZ_S = 32 * LB_S;
-constexpr int SZ_AF = ROWS * STC_W;  // one row-major A image (hi or lo)
-constexpr int SZ_RA = 2 * SZ_B;      // region A: A (hi | lo), or B' (hi | lo)
+// the row-major A image [128 rows][64 neurons] (K = neuron): core matrices of
+// 8 rows x 4 neurons, 8-row groups 144 bytes apart (padded by 16 bytes, so
+// that the 16-byte runs of 8 points' rows fall in distinct bank groups),
+// 4-neuron groups 16 x 144 bytes apart
+constexpr int A_SBO = 144, A_LBO = 16 * A_SBO;
+constexpr int SZ_AF = 16 * A_LBO / 4;   // one A image (hi or lo), floats
+constexpr int SZ_RA = 2 * SZ_AF;        // region A: A (hi | lo), or B' (hi | lo)
+static_assert(2 * SZ_B <= SZ_RA, "region A holds B'");
 // region A also holds, between the forward and the reverse pass, the partial
 // outputs [4 parts][128 rows][4] and the output jets and seeds [32 points][3][4]
 constexpr int RA_X = 0, RA_J = RA_X + 4 * ROWS * 4, RA_G = RA_J + 384;
-static_assert(2 * SZ_AF <= SZ_RA && RA_G + 384 <= SZ_RA && 2 * 64 * 65 <= SZ_RA, "region A");
+static_assert(RA_G + 384 <= SZ_RA && 2 * 64 * 65 <= SZ_RA, "region A");
+// staging [point][component][neuron]: component stride 68, point stride 276
+// floats: a point thread's 16-byte loads (8 points) fall in distinct bank
+// groups, a row thread's 16-byte stores (8 rows) at most two to a group
+constexpr int ZS_C = 68, ZS_P = 4 * ZS_C + 4;
+constexpr int SZ_ZS = 32 * ZS_P;
 // the item's FP32-pipe weights, zero-padded to 64 neurons: W^1 [64][2], b^1,
 // b^k (k = 2..L-1) [STC_MAXL - 2][64], W^L [3][64], b^L [4]
 constexpr int PW_W1 = 0, PW_B1 = 128, PW_BK = 192, PW_WL = PW_BK + 64 * (STC_MAXL - 2), PW_BL = PW_WL + 192;
 constexpr int SZ_PW = PW_BL + 4;
-// shared-memory map (floats): region A, At, two weight buffers, the [16][rows]
-// images, the points of two tiles, the bias-gradient partials [STC_MAXL - 2][4 lane
-// quadrants][64] and [32 points][4], the FP32-pipe weights
+// shared-memory map (floats): region A, At, the weight buffer, the [16][rows]
+// images, the staging array, the points of two tiles, the bias-gradient
+// sums [STC_MAXL - 2][64] and [32 points][4], the FP32-pipe weights
 constexpr int O_A = 0;
 constexpr int O_T = O_A + SZ_RA;
 constexpr int O_W = O_T + SZ_T;
-constexpr int O_S = O_W + 2 * STC_IMG;
-constexpr int O_P = O_S + 2 * SZ_S;
+constexpr int O_S = O_W + STC_IMG;
+constexpr int O_Z = O_S + 2 * SZ_S;
+constexpr int O_P = O_Z + SZ_ZS;
 constexpr int O_DB = O_P + 128;
-constexpr int O_DL = O_DB + (STC_MAXL - 2) * 4 * 64;
+constexpr int O_DL = O_DB + (STC_MAXL - 2) * 64;
 constexpr int O_PW = O_DL + 128;
 constexpr int SMEM_FLOATS = O_PW + SZ_PW;
 // tensor-memory columns: Z main [0, 64), Z cross [64, 128), dW^k (k = 2..L-1)
@@ -98,12 +112,12 @@ constexpr int TMEM_COLS = 512;
 constexpr int STC_FLUSH = 16;
 static_assert(128 + 64 * (STC_MAXL - 2) + 32 <= TMEM_COLS, "tensor memory");
 
-// element offsets in the images whose K is the rows (column n, row r); for
-// column nb + i with nb a multiple of 8: base + col_step(i)
+// element offsets in the images whose K is the rows (column n, row r); the 4
+// rows of a point (r = 4 p + c) are one 16-byte run
+__device__ __forceinline__ int a_off5(int r, int g) { return g * (A_LBO / 4) + (r >> 3) * (A_SBO / 4) + (r & 7) * 4; }
 __device__ __forceinline__ int t_off(int m, int r) { return (m >> 3) * 32 + (r >> 2) * LB_T + (m & 7) * 4 + (r & 3); }
 __device__ __forceinline__ int b_off(int j, int r) { return (j >> 3) * 32 + (r >> 2) * LB_B + (j & 7) * 4 + (r & 3); }
 __device__ __forceinline__ int s_off(int j, int r) { return (j >> 3) * 32 + (r >> 2) * LB_S + (j & 7) * 4 + (r & 3); }
-__device__ __forceinline__ constexpr int col_step(int i) { return (i >> 3) * 32 + (i & 7) * 4; }
 
 __device__ __forceinline__ void fence_to_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -154,12 +168,12 @@ __device__ __forceinline__ uint64_t dstep(int bytes) { return (uint64_t)(bytes >
 // terms into tm + 64.
 __device__ __forceinline__ void mma_rows(uint32_t tm, uint32_t a, uint32_t b) {
   const uint32_t id = tc_idesc(STC_W);
-  const uint64_t ahi = tc_sdesc(a, TC_A_LBO, 128), alo = tc_sdesc(a + 4 * SZ_AF, TC_A_LBO, 128);
+  const uint64_t ahi = tc_sdesc(a, A_LBO, A_SBO), alo = tc_sdesc(a + 4 * SZ_AF, A_LBO, A_SBO);
   const uint64_t bhi = tc_sdesc(b, 128, STC_W / 4 * 128);
   const uint64_t blo = tc_sdesc(b + 4 * STC_W * STC_W, 128, STC_W / 4 * 128);
 #pragma unroll
   for (int ks = 0; ks < STC_W / 8; ++ks) {
-    const uint64_t da = dstep(ks * 2 * TC_A_LBO), db = dstep(ks * 256);
+    const uint64_t da = dstep(ks * 2 * A_LBO), db = dstep(ks * 256);
     tc_mma(tm, ahi + da, bhi + db, id, ks > 0 ? 1u : 0u);
     tc_mma(tm + 64, ahi + da, blo + db, id, ks > 0 ? 1u : 0u);
     tc_mma(tm + 64, alo + da, bhi + db, id, 1u);
@@ -213,135 +227,174 @@ __device__ __forceinline__ void tmem_cols(uint32_t taddr, float (&z)[N]) {
   for (int i = 0; i < N; ++i) z[i] = __uint_as_float(v[i]);
 }
 
-// Forward jet rule of tanh on this thread's row (component c) for its NPT
-// neurons: z in (the value row's includes the bias), h out in z.  The saved
-// value (t on the value row, z_c on the others) goes to Sk[n][row] (Sk
-// points at this thread's first neuron and row).
-__device__ __forceinline__ void jet_fwd(float (&z)[NPT], int c, int gb, float* __restrict__ Sk) {
-  float t[NPT];
-  // tanh of the value row's z, neuron 4g + c evaluated by lane c of the point
+// ---------------------------------------------------------------------------
+// Point threads: lane p = point, warp g = neurons 4 g .. 4 g + 3.  v[c][i] is
+// component c (0 value, 1 x, 2 y, 3 Laplacian) of neuron 4 g + i; row 4 p + c.
+// ---------------------------------------------------------------------------
+
+// Forward rule from the pre-activation jets z (the value's includes the
+// bias): h, and the saved jets sv = (t, z_x, z_y, z_lap) of every neuron.
+__device__ __forceinline__ void jet4_fwd(const float (&z)[4][NPG], float (&h)[4][NPG], float (&sv)[4][NPG]) {
 #pragma unroll
-  for (int g = 0; g < NPT / 4; ++g) {
-    const float a0 = __shfl_sync(FULL, z[4 * g], gb), a1 = __shfl_sync(FULL, z[4 * g + 1], gb);
-    const float a2 = __shfl_sync(FULL, z[4 * g + 2], gb), a3 = __shfl_sync(FULL, z[4 * g + 3], gb);
-    const float tm = tanhf(c == 0 ? a0 : (c == 1 ? a1 : (c == 2 ? a2 : a3)));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) t[4 * g + j] = __shfl_sync(FULL, tm, gb + j);
-  }
-#pragma unroll
-  for (int i = 0; i < NPT; ++i) {
-    const float zi = z[i], ti = t[i], s = 1.f - ti * ti;
-    float q = (c == 1 || c == 2) ? zi * zi : 0.f;
-    q += __shfl_xor_sync(FULL, q, 1);
-    q += __shfl_xor_sync(FULL, q, 2);
-    Sk[i * ROWS] = c == 0 ? ti : zi;
-    z[i] = c == 0 ? ti : (c == 3 ? s * zi - 2.f * ti * s * q : s * zi);
+  for (int i = 0; i < NPG; ++i) {
+    const float t = tanhf(z[0][i]), s = 1.f - t * t;
+    const float q = z[1][i] * z[1][i] + z[2][i] * z[2][i];
+    h[0][i] = t;
+    h[1][i] = s * z[1][i];
+    h[2][i] = s * z[2][i];
+    h[3][i] = s * z[3][i] - 2.f * t * s * q;
+    sv[0][i] = t;
+    sv[1][i] = z[1][i];
+    sv[2][i] = z[2][i];
+    sv[3][i] = z[3][i];
   }
 }
 
-// Reverse jet rule: adjoints hb of (h, h_x, h_y, h_lap) on this row to
-// adjoints zb of (z, z_x, z_y, z_lap):
+// The same from saved jets (no tanh)
+__device__ __forceinline__ void jet4_saved(const float (&sv)[4][NPG], float (&h)[4][NPG]) {
+#pragma unroll
+  for (int i = 0; i < NPG; ++i) {
+    const float t = sv[0][i], s = 1.f - t * t;
+    const float q = sv[1][i] * sv[1][i] + sv[2][i] * sv[2][i];
+    h[0][i] = t;
+    h[1][i] = s * sv[1][i];
+    h[2][i] = s * sv[2][i];
+    h[3][i] = s * sv[3][i] - 2.f * t * s * q;
+  }
+}
+
+// Reverse rule: adjoints hb of (h, h_x, h_y, h_lap) to adjoints zb of
+// (z, z_x, z_y, z_lap):
 //   zb_lap = s hb_lap,  zb_i = s hb_i - 4 t s z_i hb_lap,
 //   zb = s [hb - 2 t (z_x hb_x + z_y hb_y) + (-2 t z_lap + (6 t^2 - 2)(z_x^2 + z_y^2)) hb_lap]
-// the bracket summed over the point's 4 rows.
-__device__ __forceinline__ void jet_bwd(const float (&sv)[NPT], const float (&tv)[NPT], const float (&hb)[NPT],
-                                        int c, int gb, float (&zb)[NPT]) {
+__device__ __forceinline__ void jet4_bwd(const float (&sv)[4][NPG], const float (&hb)[4][NPG],
+                                         float (&zb)[4][NPG]) {
 #pragma unroll
-  for (int i = 0; i < NPT; ++i) {
-    const float zi = sv[i], ti = tv[i], s = 1.f - ti * ti, hbi = hb[i];
-    const float h3 = __shfl_sync(FULL, hbi, gb + 3);
-    float e = c == 0 ? hbi
-                     : (c == 3 ? -2.f * ti * zi * h3
-                               : -2.f * ti * zi * hbi + (6.f * ti * ti - 2.f) * zi * zi * h3);
-    e += __shfl_xor_sync(FULL, e, 1);
-    e += __shfl_xor_sync(FULL, e, 2);
-    zb[i] = c == 0 ? s * e : (c == 3 ? s * hbi : s * hbi - 4.f * ti * s * zi * h3);
+  for (int i = 0; i < NPG; ++i) {
+    const float t = sv[0][i], z1 = sv[1][i], z2 = sv[2][i], z3 = sv[3][i], s = 1.f - t * t;
+    const float h3 = hb[3][i];
+    zb[3][i] = s * h3;
+    zb[1][i] = s * hb[1][i] - 4.f * t * s * z1 * h3;
+    zb[2][i] = s * hb[2][i] - 4.f * t * s * z2 * h3;
+    float tb = hb[0][i] - 2.f * t * (z1 * hb[1][i] + z2 * hb[2][i]);
+    tb += (-2.f * t * z3 + (6.f * t * t - 2.f) * (z1 * z1 + z2 * z2)) * h3;
+    zb[0][i] = s * tb;
   }
 }
 
-__device__ __forceinline__ void split_all(const float (&v)[NPT], float (&hi)[NPT], float (&lo)[NPT]) {
+__device__ __forceinline__ void split4(const float (&v)[4][NPG], float (&hi)[4][NPG], float (&lo)[4][NPG]) {
 #pragma unroll
-  for (int i = 0; i < NPT; ++i) {
-    const float2 s = tf32_split(v[i]);
-    hi[i] = s.x;
-    lo[i] = s.y;
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int i = 0; i < NPG; ++i) {
+      const float2 s = tf32_split(v[c][i]);
+      hi[c][i] = s.x;
+      lo[c][i] = s.y;
+    }
+}
+
+// Row-major A image (hi at A, lo at A + SZ_AF): per row, the 4 neurons
+__device__ __forceinline__ void put_a(float* __restrict__ A, int p, int g, const float (&hi)[4][NPG],
+                                      const float (&lo)[4][NPG]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int o = a_off5(4 * p + c, g);
+    *reinterpret_cast<float4*>(A + o) = make_float4(hi[c][0], hi[c][1], hi[c][2], hi[c][3]);
+    *reinterpret_cast<float4*>(A + SZ_AF + o) = make_float4(lo[c][0], lo[c][1], lo[c][2], lo[c][3]);
   }
 }
 
-// Row-major A image (hi at A, lo at A + SZ_AF); A points at a_off(r, nb)
-__device__ __forceinline__ void put_rows(float* __restrict__ A, const float (&hi)[NPT], const float (&lo)[NPT]) {
+// Stacked transposed image (M-row n: hi, 64 + n: lo): per neuron, the 4 rows
+__device__ __forceinline__ void put_t(float* __restrict__ T, int p, int g, const float (&hi)[4][NPG],
+                                      const float (&lo)[4][NPG]) {
 #pragma unroll
-  for (int g = 0; g < NPT / 4; ++g) {
-    *reinterpret_cast<float4*>(A + g * (TC_A_LBO / 4)) =
-        make_float4(hi[4 * g], hi[4 * g + 1], hi[4 * g + 2], hi[4 * g + 3]);
-    *reinterpret_cast<float4*>(A + SZ_AF + g * (TC_A_LBO / 4)) =
-        make_float4(lo[4 * g], lo[4 * g + 1], lo[4 * g + 2], lo[4 * g + 3]);
+  for (int i = 0; i < NPG; ++i) {
+    const int n = 4 * g + i;
+    *reinterpret_cast<float4*>(T + t_off(n, 4 * p)) = make_float4(hi[0][i], hi[1][i], hi[2][i], hi[3][i]);
+    *reinterpret_cast<float4*>(T + t_off(64 + n, 4 * p)) = make_float4(lo[0][i], lo[1][i], lo[2][i], lo[3][i]);
   }
 }
 
-// Stacked transposed image (M-row n: hi, 64 + n: lo; K = row); T points at t_off(nb, r)
-__device__ __forceinline__ void put_stacked(float* __restrict__ T, const float (&hi)[NPT], const float (&lo)[NPT]) {
+// Transposed B' image (hi at B, lo at B + SZ_B): per neuron, the 4 rows
+__device__ __forceinline__ void put_b(float* __restrict__ B, int p, int g, const float (&hi)[4][NPG],
+                                      const float (&lo)[4][NPG]) {
 #pragma unroll
-  for (int i = 0; i < NPT; ++i) {
-    T[col_step(i)] = hi[i];
-    T[8 * 32 + col_step(i)] = lo[i];   // M-row 64 + n: eight 8-row groups further
+  for (int i = 0; i < NPG; ++i) {
+    const int o = b_off(4 * g + i, 4 * p);
+    *reinterpret_cast<float4*>(B + o) = make_float4(hi[0][i], hi[1][i], hi[2][i], hi[3][i]);
+    *reinterpret_cast<float4*>(B + SZ_B + o) = make_float4(lo[0][i], lo[1][i], lo[2][i], lo[3][i]);
   }
 }
 
-// Transposed B' image (N = neuron, K = row; hi, then lo); B points at b_off(nb, r)
-__device__ __forceinline__ void put_bt(float* __restrict__ B, const float (&hi)[NPT], const float (&lo)[NPT]) {
+// Saved jets of one layer, [neuron][row] (Sk at the layer's first float):
+// the 4 rows of a point are (t, z_x, z_y, z_lap), one 16-byte run
+__device__ __forceinline__ void save4(float* __restrict__ Sk, int p, int g, const float (&sv)[4][NPG]) {
 #pragma unroll
-  for (int i = 0; i < NPT; ++i) {
-    B[col_step(i)] = hi[i];
-    B[SZ_B + col_step(i)] = lo[i];
+  for (int i = 0; i < NPG; ++i)
+    *reinterpret_cast<float4*>(Sk + (4 * g + i) * ROWS + 4 * p) = make_float4(sv[0][i], sv[1][i], sv[2][i], sv[3][i]);
+}
+
+__device__ __forceinline__ void load4(const float* __restrict__ Sk, int p, int g, float (&sv)[4][NPG]) {
+#pragma unroll
+  for (int i = 0; i < NPG; ++i) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(Sk + (4 * g + i) * ROWS + 4 * p));
+    sv[0][i] = v.x;
+    sv[1][i] = v.y;
+    sv[2][i] = v.z;
+    sv[3][i] = v.w;
   }
 }
 
-// H from saved jets: sv (this row's saved value), tv (t of the point)
-__device__ __forceinline__ void jet_from_saved(const float (&sv)[NPT], const float (&tv)[NPT], int c,
-                                               float (&h)[NPT]) {
+// Staging [point][component][neuron]: a point thread's 4 rows x 4 neurons
+__device__ __forceinline__ void zs_read4(const float* __restrict__ ZS, int p, int g, float (&v)[4][NPG]) {
 #pragma unroll
-  for (int i = 0; i < NPT; ++i) {
-    const float zi = sv[i], ti = tv[i], s = 1.f - ti * ti;
-    float q = (c == 1 || c == 2) ? zi * zi : 0.f;
-    q += __shfl_xor_sync(FULL, q, 1);
-    q += __shfl_xor_sync(FULL, q, 2);
-    h[i] = c == 0 ? ti : (c == 3 ? s * zi - 2.f * ti * s * q : s * zi);
+  for (int c = 0; c < 4; ++c) {
+    const float4 x = *reinterpret_cast<const float4*>(ZS + p * ZS_P + c * ZS_C + 4 * g);
+    v[c][0] = x.x;
+    v[c][1] = x.y;
+    v[c][2] = x.z;
+    v[c][3] = x.w;
   }
 }
 
-// Saved jets of one layer (Sk at this thread's first neuron and row) and t
-// of the point on every row
-__device__ __forceinline__ void load_saved(const float* __restrict__ Sk, int gb, float (&sv)[NPT],
-                                           float (&tv)[NPT]) {
+__device__ __forceinline__ void zs_write4(float* __restrict__ ZS, int p, int g, const float (&v)[4][NPG]) {
 #pragma unroll
-  for (int i = 0; i < NPT; ++i) sv[i] = __ldcg(Sk + i * ROWS);
-#pragma unroll
-  for (int i = 0; i < NPT; ++i) tv[i] = __shfl_sync(FULL, sv[i], gb);
+  for (int c = 0; c < 4; ++c)
+    *reinterpret_cast<float4*>(ZS + p * ZS_P + c * ZS_C + 4 * g) = make_float4(v[c][0], v[c][1], v[c][2], v[c][3]);
 }
 
-// Sum of the value rows' zb over the warp's 8 points, scattered: the value
-// lane of point v (lane 4 v) ends with the sums of neurons 2 v and 2 v + 1
-// (of the thread's NPT) in out[0], out[1].  Halving exchanges: xor 16
-// (neurons 0-7 / 8-15), xor 8, xor 4.
-__device__ __forceinline__ void value_row_sums(const float (&zb)[NPT], int lane, float (&out)[2]) {
-  static_assert(NPT == 16, "three halving steps");
-  float a[8], b[4];
-  const bool h16 = (lane >> 4) & 1, h8 = (lane >> 3) & 1, h4 = (lane >> 2) & 1;
+// ... and a row thread's row (r = 4 p + c), neurons nb .. nb + NPT - 1
+__device__ __forceinline__ void zs_row_write(float* __restrict__ ZS, int r, int nb, const float (&z)[NPT]) {
+  float* d = ZS + (r >> 2) * ZS_P + (r & 3) * ZS_C + nb;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const float keep = h16 ? zb[8 + j] : zb[j], send = h16 ? zb[j] : zb[8 + j];
-    a[j] = keep + __shfl_xor_sync(FULL, send, 16);
+  for (int j = 0; j < NPT; j += 4) *reinterpret_cast<float4*>(d + j) = make_float4(z[j], z[j + 1], z[j + 2], z[j + 3]);
+}
+
+__device__ __forceinline__ void zs_row_read(const float* __restrict__ ZS, int r, int nb, float (&z)[NPT]) {
+  const float* d = ZS + (r >> 2) * ZS_P + (r & 3) * ZS_C + nb;
+#pragma unroll
+  for (int j = 0; j < NPT; j += 4) {
+    const float4 x = *reinterpret_cast<const float4*>(d + j);
+    z[j] = x.x;
+    z[j + 1] = x.y;
+    z[j + 2] = x.z;
+    z[j + 3] = x.w;
   }
+}
+
+// Sums over the warp's 32 points of the value-row adjoints of the thread's 4
+// neurons (fixed butterfly); lane 0 adds them to d[0..3]
+__device__ __forceinline__ void value_sums(const float (&zb)[4][NPG], int lane, float* __restrict__ d) {
+  float v[NPG];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float keep = h8 ? a[4 + j] : a[j], send = h8 ? a[j] : a[4 + j];
-    b[j] = keep + __shfl_xor_sync(FULL, send, 8);
-  }
+  for (int i = 0; i < NPG; ++i) v[i] = zb[0][i];
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const float keep = h4 ? b[2 + j] : b[j], send = h4 ? b[j] : b[2 + j];
-    out[j] = keep + __shfl_xor_sync(FULL, send, 4);
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < NPG; ++i) v[i] += __shfl_xor_sync(FULL, v[i], o);
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NPG; ++i) d[i] += v[i];
   }
 }
 
@@ -351,6 +404,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   float* RT = sm + O_T;
   float* RW = sm + O_W;
   float* RS = sm + O_S;
+  float* ZS = sm + O_Z;
   float* Xs = RA + RA_X;
   float* Js = RA + RA_J;
   float* Gs = RA + RA_G;
@@ -358,19 +412,18 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   float* dbs = sm + O_DB;
   float* dls = sm + O_DL;
   float* pw = sm + O_PW;
-  __shared__ __align__(8) uint64_t bars[4];   // weight buffers 0 and 1, row MMAs, gradient MMAs
+  __shared__ __align__(8) uint64_t bars[3];   // weight buffer, row MMAs, gradient MMAs
   __shared__ uint32_t s_tmem;
   __shared__ int s_item, s_stop;
   __shared__ double red[NTH / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // row-thread view (tensor memory, the output layer)
   const int quad = warp & 3, part = warp >> 2, nb = part * NPT;
-  const int r = quad * 32 + lane, p = r >> 2, c = r & 3, gb = lane & ~3;
-  // this thread's bases in the images
-  float* const A_r = RA + a_off(r, nb);
-  float* const T_r = RT + t_off(nb, r);
-  float* const B_r = RA + b_off(nb, r);
+  const int r = quad * 32 + lane, pr = r >> 2, cr = r & 3;
+  // point-thread view (jet rules, operand images)
+  const int p = lane, g = warp;
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(bars + i, 1);
+    for (int i = 0; i < 3; ++i) mbar_init(bars + i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -385,8 +438,8 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   const uint32_t tmem = s_tmem;
   const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16);   // this warp's lanes
   const uint32_t sa = smem_u32(RA), st = smem_u32(RT), sw = smem_u32(RW), ss = smem_u32(RS);
-  float* const S_r = a.scratch + (int64_t)blockIdx.x * STC_SCRATCH + nb * ROWS + r;
-  uint32_t wph = 0, mph = 0, dph = 0;   // phase parities (wph: bit per weight buffer)
+  float* const scr = a.scratch + (int64_t)blockIdx.x * STC_SCRATCH;
+  uint32_t wph = 0, mph = 0, dph = 0;   // phase parities
   bool d_pending = false;               // a gradient-MMA commit not yet waited for
   for (;;) {
     if (tid == 0) {
@@ -439,7 +492,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
       }
       pw[e] = v;
     }
-    for (int e = tid; e < (STC_MAXL - 2) * 4 * 64; e += NTH) dbs[e] = 0.f;
+    for (int e = tid; e < (STC_MAXL - 2) * 64; e += NTH) dbs[e] = 0.f;
     if (tid < 128) dls[tid] = 0.f;
     double l0 = 0.0;
     const int n_tiles = (it.n_pts + STC_PTS - 1) / STC_PTS;
@@ -447,63 +500,81 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
     for (int tile = 0; tile < n_tiles; ++tile) {
       const int t0 = tile * STC_PTS;
       const int nv = min(STC_PTS, it.n_pts - t0);
-      // every MMA of the previous tile has completed: both weight buffers and
+      const bool first = tile % STC_FLUSH == 0;   // the gradient accumulators start from zero
+      // every MMA of the previous tile has completed: the weight buffer and
       // regions A, At and S are free
       if (d_pending) {
-        mbar_park(bars + 3, dph, a.err);
+        mbar_park(bars + 2, dph, a.err);
         dph ^= 1u;
         d_pending = false;
       }
-      if (tid == 0) {
-        bulk_g2s(RW, img_src(0), 4u * STC_IMG, bars);
-        if (nimg > 1) bulk_g2s(RW + STC_IMG, img_src(1), 4u * STC_IMG, bars + 1);
-      }
+      if (tid == 0) bulk_g2s(RW, img_src(0), 4u * STC_IMG, bars);
       const float2* sp = sp2 + (tile & 1) * STC_PTS;
       __syncthreads();
-      float z[NPT], zh[NPT], zl[NPT];
+      float v[4][NPG], h[4][NPG], sv[4][NPG], hh[4][NPG], hl[4][NPG];
       // ---- layer 1: z = W^1 x + b^1, z_x = W^1[:, 0], z_y = W^1[:, 1], z_lap = 0
       {
         const float2 x = sp[p];
 #pragma unroll
-        for (int i = 0; i < NPT; ++i) {
-          const float2 w = reinterpret_cast<const float2*>(pw + PW_W1)[nb + i];
-          const float b = pw[PW_B1 + nb + i];
-          z[i] = c == 0 ? fmaf(w.x, x.x, fmaf(w.y, x.y, b)) : (c == 1 ? w.x : (c == 2 ? w.y : 0.f));
+        for (int i = 0; i < NPG; ++i) {
+          const float2 w = reinterpret_cast<const float2*>(pw + PW_W1)[4 * g + i];
+          v[0][i] = fmaf(w.x, x.x, fmaf(w.y, x.y, pw[PW_B1 + 4 * g + i]));
+          v[1][i] = w.x;
+          v[2][i] = w.y;
+          v[3][i] = 0.f;
         }
-        jet_fwd(z, c, gb, S_r);
-        split_all(z, zh, zl);
-        put_rows(A_r, zh, zl);   // L >= 3: a hidden-to-hidden layer reads it
+        jet4_fwd(v, h, sv);
+        save4(scr, p, g, sv);
+        split4(h, hh, hl);
+        put_a(RA, p, g, hh, hl);   // L >= 3: a hidden-to-hidden layer reads it
       }
       // ---- hidden-to-hidden layers on the tensor cores
       for (int k = 2; k <= L - 1; ++k) {
-        const int i = k - 2, buf = i & 1;
+        const int i = k - 2;
         fence_to_async();
         __syncthreads();
         if (tid == 0) {
-          mbar_wait(bars + buf, (wph >> buf) & 1u, a.err);
-          wph ^= 1u << buf;
+          mbar_wait(bars, wph, a.err);
+          wph ^= 1u;
           after_sync();
-          mma_rows(tmem, sa, sw + 4u * STC_IMG * buf);
-          mma_commit(bars + 2);
+          mma_rows(tmem, sa, sw);
+          mma_commit(bars + 1);
         }
-        mbar_park(bars + 2, mph, a.err);
+        mbar_park(bars + 1, mph, a.err);
         mph ^= 1u;
         after_sync();
-        if (tid == 0 && i + 2 < nimg) bulk_g2s(RW + STC_IMG * buf, img_src(i + 2), 4u * STC_IMG, bars + buf);
-        tmem_rowz(tq + nb, tq + 64 + nb, z);
-        const float* bk = pw + PW_BK + (k - 2) * 64 + nb;
-#pragma unroll
-        for (int j = 0; j < NPT; ++j) z[j] += c == 0 ? bk[j] : 0.f;
-        jet_fwd(z, c, gb, S_r + (k - 1) * STC_W * ROWS);
-        split_all(z, zh, zl);
-        if (k < L - 1)
-          put_rows(A_r, zh, zl);
-        else
-          put_stacked(T_r, zh, zl);   // H^{L-1} for the output layer's weight gradient
+        // the weight buffer is free: the next image lands during the epilogue
+        if (tid == 0) bulk_g2s(RW, img_src(i + 1), 4u * STC_IMG, bars);
+        {
+          float z[NPT];
+          tmem_rowz(tq + nb, tq + 64 + nb, z);
+          zs_row_write(ZS, r, nb, z);
+        }
+        __syncthreads();
+        zs_read4(ZS, p, g, v);
+        {
+          const float4 b = *reinterpret_cast<const float4*>(pw + PW_BK + (k - 2) * 64 + 4 * g);
+          v[0][0] += b.x;
+          v[0][1] += b.y;
+          v[0][2] += b.z;
+          v[0][3] += b.w;
+        }
+        jet4_fwd(v, h, sv);
+        save4(scr + (k - 1) * STC_W * ROWS, p, g, sv);
+        split4(h, hh, hl);
+        if (k < L - 1) {
+          put_a(RA, p, g, hh, hl);
+        } else {
+          put_t(RT, p, g, hh, hl);   // H^{L-1} for the output layer's weight gradient
+          zs_write4(ZS, p, g, h);    // and, exact, for the output layer
+        }
       }
-      // ---- output layer (FP32): y = W^L h + b^L on the value row, W^L h on the others
+      // ---- output layer (FP32, row threads): y = W^L h + b^L on the value row, W^L h on the others
+      __syncthreads();   // H^{L-1} in the staging array
       {
         const float* WL = pw + PW_WL;
+        float z[NPT];
+        zs_row_read(ZS, r, nb, z);
         float y[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int o = 0; o < 3; ++o)
@@ -516,17 +587,17 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
 #pragma unroll
           for (int o = 0; o < 3; ++o)
             if (o < D) {
-              float v = y[o];
+              float yy = y[o];
 #pragma unroll
-              for (int q = 1; q < STC_W / NPT; ++q) v += Xs[(q * ROWS + r) * 4 + o];
-              Js[(p * 3 + o) * 4 + c] = v + (c == 0 ? pw[PW_BL + o] : 0.f);
+              for (int q = 1; q < STC_W / NPT; ++q) yy += Xs[(q * ROWS + r) * 4 + o];
+              Js[(pr * 3 + o) * 4 + cr] = yy + (cr == 0 ? pw[PW_BL + o] : 0.f);
             }
         }
         __syncthreads();
       }
       // ---- residual and its seeds, one thread per point
       if (tid < STC_PTS) {
-        const bool v = tid < nv;
+        const bool vv = tid < nv;
         PtJets J, G;
 #pragma unroll
         for (int o = 0; o < XPINN_MAX_OUT; ++o)
@@ -538,16 +609,16 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
 #pragma unroll
         for (int cc = 0; cc < KMAX; ++cc) J.k[cc] = G.k[cc] = 0.f;
         float rr[3] = {0.f, 0.f, 0.f};
-        const float f = v ? a.res_f[it.pt_off + t0 + tid] : 0.f;
+        const float f = vv ? a.res_f[it.pt_off + t0 + tid] : 0.f;
         const int ne = residual_fwd(a.pde, J, f, a.nu, a.re, rr);
         float sq = 0.f, e[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 3; ++q)
           if (q < ne) {
             sq += rr[q] * rr[q];
-            e[q] = v ? coef * rr[q] : 0.f;
+            e[q] = vv ? coef * rr[q] : 0.f;
           }
-        if (v) l0 += (double)sq * sd.inv_n_res;
+        if (vv) l0 += (double)sq * sd.inv_n_res;
         residual_seed(a.pde, J, e, a.nu, a.re, G);
 #pragma unroll
         for (int o = 0; o < 3; ++o)
@@ -555,17 +626,18 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           for (int cc = 0; cc < 4; ++cc) Gs[(tid * 3 + o) * 4 + cc] = o < D ? G.u[o][cc] : 0.f;
       }
       __syncthreads();
-      // ---- output layer, reverse: Hb^{L-1} = (W^L)^T yb (FP32); dW^L on the
-      // tensor cores (At = stacked H^{L-1} transposed, B = yb transposed)
-      float hb[NPT];
+      // ---- output layer, reverse (row threads): Hb^{L-1} = (W^L)^T yb into the
+      // staging array (FP32); dW^L on the tensor cores (At = stacked H^{L-1}
+      // transposed, B = yb transposed)
       {
         const float* WL = pw + PW_WL;
-        float yb[3];
+        float yb[3], hb[NPT];
 #pragma unroll
-        for (int o = 0; o < 3; ++o) yb[o] = Gs[(p * 3 + o) * 4 + c];
+        for (int o = 0; o < 3; ++o) yb[o] = Gs[(pr * 3 + o) * 4 + cr];
 #pragma unroll
         for (int j = 0; j < NPT; ++j)
           hb[j] = fmaf(yb[0], WL[nb + j], fmaf(yb[1], WL[64 + nb + j], yb[2] * WL[128 + nb + j]));
+        zs_row_write(ZS, r, nb, hb);
         // the next tile's points, read while this tile's reverse pass runs
         if (tid < STC_PTS && tile + 1 < n_tiles) {
           const int t1 = t0 + STC_PTS + tid;
@@ -578,48 +650,63 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
             RS[s_off(o, r)] = s2.x;
             RS[SZ_S + s_off(o, r)] = s2.y;
           }
-          if (c == 0) {
+          if (cr == 0) {
 #pragma unroll
-            for (int o = 0; o < 3; ++o) dls[p * 4 + o] += yb[o];
+            for (int o = 0; o < 3; ++o) dls[pr * 4 + o] += yb[o];
           }
         }
         fence_to_async();
         __syncthreads();
         if (tid == 0) {
           after_sync();
-          mma_grad<4 * LB_S>(tmem + 144 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, tile % STC_FLUSH == 0);
-          mma_commit(bars + 3);
+          mma_grad<4 * LB_S>(tmem + 144 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, first);
+          mma_commit(bars + 2);
         }
         d_pending = true;
       }
-      // ---- hidden layers, reverse.  Hb^k of k < L - 1 is in tensor memory
-      // (the row MMA of the step before, already waited for).
-      float sv[NPT], tv[NPT];
-      load_saved(S_r + (L - 2) * STC_W * ROWS, gb, sv, tv);
+      // ---- hidden layers, reverse (point threads).  Hb^k is in the staging
+      // array: written above for k = L - 1, moved there from tensor memory
+      // (the row MMA of the step before, already waited for) for k < L - 1.
+      load4(scr + (L - 2) * STC_W * ROWS, p, g, sv);
       for (int k = L - 1; k >= 1; --k) {
-        if (k < L - 1) tmem_rowz(tq + nb, tq + 64 + nb, hb);
-        jet_bwd(sv, tv, hb, c, gb, z);
-        split_all(z, zh, zl);
+        if (k < L - 1) {
+          float z[NPT];
+          tmem_rowz(tq + nb, tq + 64 + nb, z);
+          zs_row_write(ZS, r, nb, z);
+          __syncthreads();
+        }
+        zs_read4(ZS, p, g, h);        // Hb^k
+        jet4_bwd(sv, h, v);           // Zb^k
+        split4(v, hh, hl);
+        if (k >= 2) value_sums(v, lane, dbs + (k - 2) * 64 + 4 * g);   // db^k
         if (d_pending) {   // the last gradient MMAs read regions A, At and S
-          mbar_park(bars + 3, dph, a.err);
+          mbar_park(bars + 2, dph, a.err);
           dph ^= 1u;
           d_pending = false;
           after_sync();
         }
-        put_stacked(T_r, zh, zl);
+        put_t(RT, p, g, hh, hl);
         if (k >= 2) {
-          put_rows(A_r, zh, zl);
-        } else if (part == 0) {
+          put_a(RA, p, g, hh, hl);
+        } else if (g == 0) {
           // layer 1's input jets, transposed: value row (x, y, 1), x row
           // (1, 0, 0), y row (0, 1, 0), Laplacian row 0; column 2 gives db^1
           const float2 x = sp[p];
+          const float2 sx = tf32_split(x.x), sy = tf32_split(x.y);
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const float vj = j == 0 ? (c == 0 ? x.x : (c == 1 ? 1.f : 0.f))
-                                    : (j == 1 ? (c == 0 ? x.y : (c == 2 ? 1.f : 0.f)) : (j == 2 && c == 0 ? 1.f : 0.f));
-            const float2 s2 = tf32_split(vj);
-            RS[s_off(j, r)] = s2.x;
-            RS[SZ_S + s_off(j, r)] = s2.y;
+            float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
+            if (j == 0) {
+              hi = make_float4(sx.x, 1.f, 0.f, 0.f);
+              lo.x = sx.y;
+            } else if (j == 1) {
+              hi = make_float4(sy.x, 0.f, 1.f, 0.f);
+              lo.x = sy.y;
+            } else if (j == 2) {
+              hi.x = 1.f;
+            }
+            *reinterpret_cast<float4*>(RS + s_off(j, 4 * p)) = hi;
+            *reinterpret_cast<float4*>(RS + SZ_S + s_off(j, 4 * p)) = lo;
           }
         }
         fence_to_async();
@@ -627,46 +714,36 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         if (k == 1) {
           if (tid == 0) {
             after_sync();
-            mma_grad<4 * LB_S>(tmem + 128 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, tile % STC_FLUSH == 0);
-            mma_commit(bars + 3);
+            mma_grad<4 * LB_S>(tmem + 128 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, first);
+            mma_commit(bars + 2);
           }
           d_pending = true;
           break;
         }
-        const int i = (L - 2) + (L - 1 - k), buf = i & 1;
+        const int i = (L - 2) + (L - 1 - k);
         if (tid == 0) {
-          mbar_wait(bars + buf, (wph >> buf) & 1u, a.err);
-          wph ^= 1u << buf;
+          mbar_wait(bars, wph, a.err);
+          wph ^= 1u;
           after_sync();
-          mma_rows(tmem, sa, sw + 4u * STC_IMG * buf);
-          mma_commit(bars + 2);
-        }
-        // bias gradient: sums of the value rows of Zb^k over the warp's points
-        {
-          float sb[2];
-          value_row_sums(z, lane, sb);
-          if (c == 0) {
-            float* d = dbs + ((k - 2) * 4 + quad) * 64 + nb + 2 * (lane >> 2);
-            d[0] += sb[0];
-            d[1] += sb[1];
-          }
+          mma_rows(tmem, sa, sw);
+          mma_commit(bars + 1);
         }
         // H^{k-1} from the saved jets of layer k - 1 (which the next step's
         // reverse rule uses too)
-        load_saved(S_r + (k - 2) * STC_W * ROWS, gb, sv, tv);
-        jet_from_saved(sv, tv, c, z);
-        split_all(z, zh, zl);
-        mbar_park(bars + 2, mph, a.err);   // region A and the weight buffer are free
+        load4(scr + (k - 2) * STC_W * ROWS, p, g, sv);
+        jet4_saved(sv, h);
+        split4(h, hh, hl);
+        mbar_park(bars + 1, mph, a.err);   // region A and the weight buffer are free
         mph ^= 1u;
         after_sync();
-        if (tid == 0 && i + 2 < nimg) bulk_g2s(RW + STC_IMG * buf, img_src(i + 2), 4u * STC_IMG, bars + buf);
-        put_bt(B_r, zh, zl);
+        if (tid == 0 && i + 1 < nimg) bulk_g2s(RW, img_src(i + 1), 4u * STC_IMG, bars);
+        put_b(RA, p, g, hh, hl);
         fence_to_async();
         __syncthreads();
         if (tid == 0) {
           after_sync();
-          mma_grad<4 * LB_B>(tmem + 128 + 64 * (k - 2), st, sa, 4u * SZ_B, STC_W, tile % STC_FLUSH == 0);
-          mma_commit(bars + 3);
+          mma_grad<4 * LB_B>(tmem + 128 + 64 * (k - 2), st, sa, 4u * SZ_B, STC_W, first);
+          mma_commit(bars + 2);
         }
         d_pending = true;
       }
@@ -676,7 +753,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
       if (tile + 1 == n_tiles || (tile + 1) % STC_FLUSH == 0) {
         const bool add = tile >= STC_FLUSH, last = tile + 1 == n_tiles;
         if (d_pending) {
-          mbar_park(bars + 3, dph, a.err);
+          mbar_park(bars + 2, dph, a.err);
           dph ^= 1u;
           d_pending = false;
         }
@@ -693,16 +770,12 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           for (int j = 0; j < NPT; ++j) stg[m * 65 + nb + j] = v[j];
           __syncthreads();
           const int wo = nd.w[k], wi = nd.w[k - 1];
-          float* g = gs + nd.off[k];
+          float* gw = gs + nd.off[k];
           for (int e = tid; e < wo * wi; e += NTH) {
             const int n = e / wi, j = e - n * wi;
-            g[e] = (add ? g[e] : 0.f) + (st_hi[n * 65 + j] + st_lo[n * 65 + j]);
+            gw[e] = (add ? gw[e] : 0.f) + (st_hi[n * 65 + j] + st_lo[n * 65 + j]);
           }
-          if (last && tid < wo) {
-            float sb = 0.f;
-            for (int q = 0; q < 4; ++q) sb += dbs[((k - 2) * 4 + q) * 64 + tid];
-            g[wo * wi + tid] = sb;
-          }
+          if (last && tid < wo) gw[wo * wi + tid] = dbs[(k - 2) * 64 + tid];
           __syncthreads();
         }
         {
@@ -720,20 +793,20 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           __syncthreads();
           const int w1 = nd.w[1];
           if (tid < w1) {
-            float* g = gs + nd.off[1];
-            g[2 * tid] = (add ? g[2 * tid] : 0.f) + (st_hi[tid * 65] + st_lo[tid * 65]);
-            g[2 * tid + 1] = (add ? g[2 * tid + 1] : 0.f) + (st_hi[tid * 65 + 1] + st_lo[tid * 65 + 1]);
-            g[2 * w1 + tid] = (add ? g[2 * w1 + tid] : 0.f) + (st_hi[tid * 65 + 2] + st_lo[tid * 65 + 2]);
+            float* gw = gs + nd.off[1];
+            gw[2 * tid] = (add ? gw[2 * tid] : 0.f) + (st_hi[tid * 65] + st_lo[tid * 65]);
+            gw[2 * tid + 1] = (add ? gw[2 * tid + 1] : 0.f) + (st_hi[tid * 65 + 1] + st_lo[tid * 65 + 1]);
+            gw[2 * w1 + tid] = (add ? gw[2 * w1 + tid] : 0.f) + (st_hi[tid * 65 + 2] + st_lo[tid * 65 + 2]);
           }
-          float* g = gs + nd.off[L];
+          float* gw = gs + nd.off[L];
           for (int e = tid; e < D * wl; e += NTH) {
             const int o = e / wl, n = e - o * wl;
-            g[e] = (add ? g[e] : 0.f) + (st_hi[n * 65 + 16 + o] + st_lo[n * 65 + 16 + o]);
+            gw[e] = (add ? gw[e] : 0.f) + (st_hi[n * 65 + 16 + o] + st_lo[n * 65 + 16 + o]);
           }
           if (last && tid < D) {
             float sb = 0.f;
             for (int q = 0; q < STC_PTS; ++q) sb += dls[q * 4 + tid];
-            g[D * wl + tid] = sb;
+            gw[D * wl + tid] = sb;
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
