@@ -79,26 +79,27 @@ constexpr int SZ_AF = 16 * A_LBO / 4;   // one A image (hi or lo), floats
 constexpr int SZ_RA = 2 * SZ_AF;        // region A: A (hi | lo), or B' (hi | lo)
 static_assert(2 * SZ_B <= SZ_RA, "region A holds B'");
 // region A also holds, between the forward and the reverse pass, the partial
-// outputs [4 parts][128 rows][4] and the output jets and seeds [32 points][3][4]
-constexpr int RA_X = 0, RA_J = RA_X + 4 * ROWS * 4, RA_G = RA_J + 384;
-static_assert(RA_G + 384 <= SZ_RA && 2 * 64 * 65 <= SZ_RA, "region A");
-// staging [point][component][neuron]: component stride 68, point stride 276
-// floats: a point thread's 16-byte loads (8 points) fall in distinct bank
-// groups, a row thread's 16-byte stores (8 rows) at most two to a group
-constexpr int ZS_C = 68, ZS_P = 4 * ZS_C + 4;
+// outputs [4 parts][128 rows][4], the output jets and seeds [32 points][3][4],
+// and the [16][rows] images (hi | lo) of the output layer's and the first
+// layer's weight gradients, whose MMAs complete before region A is rewritten
+constexpr int RA_X = 0, RA_J = RA_X + 4 * ROWS * 4, RA_G = RA_J + 384, RA_S = 12288;
+static_assert(RA_G + 384 <= RA_S && RA_S + 2 * SZ_S <= SZ_RA && 2 * 64 * 65 <= SZ_RA, "region A");
+// staging [point][component][neuron]: component stride 72, point stride 292
+// floats, so that a point thread's 16-byte loads (8 points) and a row
+// thread's 16-byte stores (8 rows) each fall in distinct bank groups
+constexpr int ZS_C = 72, ZS_P = 4 * ZS_C + 4;
 constexpr int SZ_ZS = 32 * ZS_P;
 // the item's FP32-pipe weights, zero-padded to 64 neurons: W^1 [64][2], b^1,
 // b^k (k = 2..L-1) [STC_MAXL - 2][64], W^L [3][64], b^L [4]
 constexpr int PW_W1 = 0, PW_B1 = 128, PW_BK = 192, PW_WL = PW_BK + 64 * (STC_MAXL - 2), PW_BL = PW_WL + 192;
 constexpr int SZ_PW = PW_BL + 4;
-// shared-memory map (floats): region A, At, the weight buffer, the [16][rows]
-// images, the staging array, the points of two tiles, the bias-gradient
-// sums [STC_MAXL - 2][64] and [32 points][4], the FP32-pipe weights
+// shared-memory map (floats): region A, At, the weight buffer, the staging
+// array, the points of two tiles, the bias-gradient sums [STC_MAXL - 2][64]
+// and [32 points][4], the FP32-pipe weights
 constexpr int O_A = 0;
 constexpr int O_T = O_A + SZ_RA;
 constexpr int O_W = O_T + SZ_T;
-constexpr int O_S = O_W + STC_IMG;
-constexpr int O_Z = O_S + 2 * SZ_S;
+constexpr int O_Z = O_W + STC_IMG;
 constexpr int O_P = O_Z + SZ_ZS;
 constexpr int O_DB = O_P + 128;
 constexpr int O_DL = O_DB + (STC_MAXL - 2) * 64;
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   float* RA = sm + O_A;
   float* RT = sm + O_T;
   float* RW = sm + O_W;
-  float* RS = sm + O_S;
+  float* RS = RA + RA_S;
   float* ZS = sm + O_Z;
   float* Xs = RA + RA_X;
   float* Js = RA + RA_J;
@@ -569,6 +570,9 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           zs_write4(ZS, p, g, h);    // and, exact, for the output layer
         }
       }
+      // saved jets of layer L - 1 for the first reverse step, in flight
+      // during the output layer and the residual
+      load4(scr + (L - 2) * STC_W * ROWS, p, g, sv);
       // ---- output layer (FP32, row threads): y = W^L h + b^L on the value row, W^L h on the others
       __syncthreads();   // H^{L-1} in the staging array
       {
@@ -667,7 +671,6 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
       // ---- hidden layers, reverse (point threads).  Hb^k is in the staging
       // array: written above for k = L - 1, moved there from tensor memory
       // (the row MMA of the step before, already waited for) for k < L - 1.
-      load4(scr + (L - 2) * STC_W * ROWS, p, g, sv);
       for (int k = L - 1; k >= 1; --k) {
         if (k < L - 1) {
           float z[NPT];
@@ -678,7 +681,12 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         zs_read4(ZS, p, g, h);        // Hb^k
         jet4_bwd(sv, h, v);           // Zb^k
         split4(v, hh, hl);
-        if (k >= 2) value_sums(v, lane, dbs + (k - 2) * 64 + 4 * g);   // db^k
+        if (k >= 2) {
+          value_sums(v, lane, dbs + (k - 2) * 64 + 4 * g);   // db^k
+          // saved jets of layer k - 1 (for H^{k-1} below and the next step's
+          // reverse rule), in flight while the images are written
+          load4(scr + (k - 2) * STC_W * ROWS, p, g, sv);
+        }
         if (d_pending) {   // the last gradient MMAs read regions A, At and S
           mbar_park(bars + 2, dph, a.err);
           dph ^= 1u;
@@ -728,9 +736,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           mma_rows(tmem, sa, sw);
           mma_commit(bars + 1);
         }
-        // H^{k-1} from the saved jets of layer k - 1 (which the next step's
-        // reverse rule uses too)
-        load4(scr + (k - 2) * STC_W * ROWS, p, g, sv);
+        // H^{k-1} from the saved jets of layer k - 1
         jet4_saved(sv, h);
         split4(h, hh, hl);
         mbar_park(bars + 1, mph, a.err);   // region A and the weight buffer are free
