@@ -1,11 +1,11 @@
-"""Why the contractions run in FP32 and not on the TF32 tensor cores: a CPU
+"""Why the tensor-core kernels take three TF32 products per term: a CPU
 emulation of the forward jet contraction of the Navier-Stokes workload's
 network (2 -> 64 x 6 -> 3, Laplacian jets; the widest uniform layers of the
 five workloads) with float32 accumulation in the kernel's order, against the
 FP64 oracle in the jet parity metric (1e-5 of max(|b|, RMS over the points
 and outputs)).  One TF32 product per term misses the tolerance by two orders
-of magnitude; three products over a hi/lo split of both operands meet it, as
-plain FP32 does."""
+of magnitude; three products over a hi/lo split of both operands (the form
+the evaluation and training kernels use) meet it, as plain FP32 does."""
 import numpy as np
 import pytest
 
