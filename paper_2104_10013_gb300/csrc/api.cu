@@ -155,6 +155,9 @@ struct Plan {
   int n_tc = 0;
   std::vector<int> tc_begin;
   int n_simt() const { return (int)items.size() - n_tc; }
+  // threads that share one parameter's slice sum in the reduction (1-8): each
+  // takes a contiguous run of at most about 8 of the subdomain's items
+  int red_split = 1;
 };
 
 struct xpinn_ctx {
@@ -535,6 +538,13 @@ void build_plan(xpinn_ctx* h, int p_cap) {
     per_q[it.q].push_back((int)i);
   }
   pl.q_item_begin.push_back(0);
+  {
+    size_t most = 1;
+    for (const auto& v : per_q) most = std::max(most, v.size());
+    int S = 1;
+    while (S < 8 && (most + S - 1) / S > 8) S *= 2;
+    pl.red_split = S;
+  }
   for (int q = 0; q < h->n_sub; ++q) {
     for (int i : per_q[q]) {
       pl.q_items.push_back(i);
@@ -542,7 +552,7 @@ void build_plan(xpinn_ctx* h, int p_cap) {
     }
     pl.q_item_begin.push_back((int)pl.q_items.size());
     if (is_trained(q))
-      for (int e0 = 0; e0 < h->subs[q].n_params; e0 += 256) pl.red_blocks.push_back(make_int2(q, e0));
+      for (int e0 = 0; e0 < h->subs[q].n_params; e0 += 256 / pl.red_split) pl.red_blocks.push_back(make_int2(q, e0));
   }
   // per-subdomain ranges for the loop schedule
   pl.fwd_begin.assign(h->n_sub + 1, 0);
@@ -822,6 +832,7 @@ void enqueue_step(xpinn_ctx* h, cudaStream_t s, bool adam, float* grads, int par
   ReduceArgs r{};
   r.blocks = h->red_blocks_d.p;
   r.n_blocks = (int)pl.red_blocks.size();
+  r.split = pl.red_split;
   r.subs = h->subs_d.p;
   r.q_items = h->q_items_d.p;
   r.q_item_begin = h->q_item_begin_d.p;

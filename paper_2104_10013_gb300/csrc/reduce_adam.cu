@@ -141,26 +141,41 @@ __global__ void __launch_bounds__(RT) reduce_adam_kernel(ReduceArgs a) {
   // the slice offsets of this subdomain's items, once per block
   constexpr int MAXI = 256;
   __shared__ int64_t s_off[MAXI];
+  __shared__ float s_part[RT];
   const int n_it = ie - ib;
   for (int k = threadIdx.x; k < n_it && k < MAXI; k += RT) s_off[k] = a.q_part_off[ib + k];
   __syncthreads();
-  const int e = blk.y + threadIdx.x;
-  if (e >= sd.n_params) return;
-  // fixed-order sum; eight independent loads in flight per step
+  // split threads per parameter: thread (s, j) sums items [s * chunk, (s + 1)
+  // * chunk) of parameter blk.y + j in their order; the partial sums are
+  // then added in s order, so the result is the same in every step
+  const int S = a.split > 0 ? a.split : 1, PB = RT / S;
+  const int sidx = threadIdx.x / PB, j = threadIdx.x - sidx * PB;
+  const int e = blk.y + j;
+  const int chunk = (n_it + S - 1) / S;
+  const int k0 = min(n_it, sidx * chunk), k1 = min(n_it, k0 + chunk);
   float g = 0.f;
-  int k = 0;
-  if (n_it <= MAXI) {
-    for (; k + 8 <= n_it; k += 8) {
-      float v[8];
+  if (e < sd.n_params) {
+    int k = k0;
+    if (n_it <= MAXI) {
+      for (; k + 8 <= k1; k += 8) {
+        float v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = a.partials[s_off[k + u] + e];
+        for (int u = 0; u < 8; ++u) v[u] = a.partials[s_off[k + u] + e];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) g += v[u];
+        for (int u = 0; u < 8; ++u) g += v[u];
+      }
+      for (; k < k1; ++k) g += a.partials[s_off[k] + e];
+    } else {
+      for (; k < k1; ++k) g += a.partials[a.q_part_off[ib + k] + e];
     }
-    for (; k < n_it; ++k) g += a.partials[s_off[k] + e];
-  } else {
-    for (; k < n_it; ++k) g += a.partials[a.q_part_off[ib + k] + e];
   }
+  if (S > 1) {
+    s_part[threadIdx.x] = g;
+    __syncthreads();
+    if (sidx != 0) return;
+    for (int q = 1; q < S; ++q) g += s_part[q * PB + j];
+  }
+  if (e >= sd.n_params) return;
   const int64_t gi = sd.poff + e;
   if (a.grads) a.grads[gi] = g;
   if (a.do_adam) {

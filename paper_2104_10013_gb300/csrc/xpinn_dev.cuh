@@ -278,8 +278,9 @@ cudaError_t jet_step_configure(size_t smem);
 int jet_step_blocks_per_sm(int pt, int nt, bool gen, size_t smem);
 
 struct ReduceArgs {
-  const int2* blocks;        // (subdomain, first param) of each CTA
+  const int2* blocks;        // (subdomain, first param) of each CTA: 256 / split params
   int n_blocks;
+  int split;                 // threads per parameter (1, 2, 4 or 8), each summing a contiguous run of items
   const SubDev* subs;
   const int* q_items;        // CSR: items contributing to each subdomain
   const int* q_item_begin;   // [n_sub + 1]
