@@ -53,11 +53,11 @@ METRIC = "residual pts/s (jet fwd+bwd) grouped vs per-subdomain loop; query p50/
 # jets and the gradient slices, both in proportion to the points processed.
 TRAFFIC = {
     # one launch of the reduced copy (160 subdomains, 4.8 M residual points):
-    # 0.974 GB read + 18.597 GB written; x16 to the full 76.8 M points
-    "c4": {"sha": "0ef8386454f6c656", "scaled_from": "c4s", "scale": 16,
+    # 0.921 GB read + 17.893 GB written; x16 to the full 76.8 M points
+    "c4": {"sha": "e80959e32d830038", "scaled_from": "c4s", "scale": 16,
            "options": {"points_per_thread": 1, "threads_per_cta": 256, "items_per_cta": 32,
                        "max_points_per_tile": 0},
-           "bytes_per_launch": 16 * (973804288 + 18597096192)},
+           "bytes_per_launch": 16 * (920784640 + 17893173248)},
 }
 FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 partitions x 32)
 

@@ -1388,9 +1388,35 @@ __device__ __forceinline__ void point_stage(const StepArgs& a, const SubDev& sd,
   }
 }
 
+// Wait (thread 0) until `need` exchange items have completed.  Every exchange
+// item is claimed before any item that waits, and exchange items never wait,
+// so the wait ends; it is still bounded: after about 1 s it sets the error
+// flag and returns false; the item then completes on whatever the exchange
+// buffer holds, and the call reports XPINN_ERR_TIMEOUT.
+static __device__ bool wait_exchange(const StepArgs& a) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned ns = 32;
+    for (long it = 0; atomicAdd(a.fwd_done, 0) < a.n_fwd_wait; ++it) {
+      if (it > (1l << 20) || atomicAdd(a.err, 0) == XPINN_ERR_TIMEOUT) {   // gave up here or elsewhere
+        atomicCAS(a.err, 0, XPINN_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 1024) ns <<= 1;
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 template <int PT, bool GEN>
 __device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& it, int item_idx,
-                                 float* __restrict__ scratch, uint32_t ph) {
+                                 float* __restrict__ scratch, uint32_t ph, bool wait_x) {
   const Smem s = carve(sl);
   const SubDev& sd = a.subs[it.q];
   const int P = it.P;
@@ -1425,6 +1451,10 @@ __device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& i
     // one whose last hidden activations are still in shared memory
     if (it.K[1]) ph = forward_any<PT, GEN>(it.K[1], false, sl, sd.net[1], prm, img, P, scratch + s1, u1, ph, a.err);
     if (it.K[0]) ph = forward_any<PT, GEN>(it.K[0], it.lap != 0, sl, sd.net[0], prm, img, P, scratch, 0, ph, a.err);
+    // interface items read the neighbours' values from the exchange buffer:
+    // wait for the exchange items only now, after the first forward pass,
+    // which does not need them
+    if (wait_x && first) wait_exchange(a);
     // ---- per point: loss terms and seeds (or exchange / evaluation output)
     for (int p = tid; p < P; p += blockDim.x) {
       const bool valid = p < nv;
@@ -1514,31 +1544,6 @@ __device__ uint32_t process_item(const StepArgs& a, SmemLayout sl, const Item& i
   return ph;
 }
 
-// Wait (thread 0) until `need` exchange items have completed.  Every exchange
-// item is claimed before any item that waits, and exchange items never wait,
-// so the wait ends; it is still bounded: after about 1 s it sets the error
-// flag and returns false, and the item is skipped.
-static __device__ bool wait_exchange(const StepArgs& a) {
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    unsigned ns = 32;
-    for (long it = 0; atomicAdd(a.fwd_done, 0) < a.n_fwd_wait; ++it) {
-      if (it > (1l << 20) || atomicAdd(a.err, 0) == XPINN_ERR_TIMEOUT) {   // gave up here or elsewhere
-        atomicCAS(a.err, 0, XPINN_ERR_TIMEOUT);
-        ok = 0;
-        break;
-      }
-      __nanosleep(ns);
-      if (ns < 1024) ns <<= 1;
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 // PT = 1 keeps registers <= 128 so that two 256-thread CTAs fit on an SM;
 // PT = 2 uses a larger register tile.  NTH = 128 halves the CTA so that two
 // (or four) independent CTAs share an SM and one CTA's narrow phases (first
@@ -1569,9 +1574,9 @@ __global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : (PT == 1 ? 2 : 1) * (256
     const int it = s_item;
     __syncthreads();
     if (it >= n_items) break;
-    if (a.n_fwd_wait > 0 && it >= a.wait_from && !wait_exchange(a)) continue;
+    const bool wait_x = a.n_fwd_wait > 0 && it >= a.wait_from;
     const Item& item = a.items[it];
-    ph = process_item<PT, GEN>(a, sl, item, a.item_base + it, scratch, ph);
+    ph = process_item<PT, GEN>(a, sl, item, a.item_base + it, scratch, ph, wait_x);
     if (item.kind == IT_IFACE_FWD && a.n_fwd_wait > 0) {
       __syncthreads();                      // every thread's exchange stores issued
       if (threadIdx.x == 0) {
