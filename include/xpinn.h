@@ -419,14 +419,22 @@ int xpinn_autotune(xpinn_handle h, int32_t steps, xpinn_options* best, float* be
  * coordinate descent over the classes (the classes with the largest modelled
  * share of the step first; candidates 128, 96, 64, 48, 32, 160 and none),
  * timing `steps` gradient passes of the grouped step for each and keeping a
- * choice only when it is clearly faster; about 20 s at most, then it keeps
- * what it has.  Parameters, Adam state and step count are unchanged;
- * synchronises.  *best_ms: the median ms per pass of the final choice.
- * The caps, one per subdomain (0: no cap beyond the options'), can be read
- * and set (for a cache of tuned choices); setting re-plans the step. */
+ * choice only when it is clearly faster; about 20 s at most.  Then, for every
+ * class whose networks the tensor-core kernel takes (see train_tensor_cores),
+ * it times that kernel on and off for the class's residual items, keeping
+ * the faster (about 30 s in all).  Parameters, Adam state and step count are
+ * unchanged; synchronises.  *best_ms: the median ms per pass of the final
+ * choice.  The caps and the tensor-core choices, one per subdomain, can be
+ * read and set (for a cache of tuned choices); setting re-plans the step. */
 int xpinn_autotune_shapes(xpinn_handle h, int32_t steps, float* best_ms);
 int xpinn_get_tile_caps(xpinn_handle h, int32_t* caps);         /* caps [n_sub], host */
 int xpinn_set_tile_caps(xpinn_handle h, const int32_t* caps);   /* [n_sub] (0 or >= 8), or NULL: none */
+/* Tensor-core choice per subdomain, sel[n_sub] (host): 1 its residual items
+ * run on the tensor-core kernel whenever its network qualifies (overriding
+ * the rule that the qualifying subdomains must hold half of the residual
+ * points), 0 never, -1 (the default; also sel = NULL) by that rule. */
+int xpinn_get_tc_select(xpinn_handle h, int32_t* sel);
+int xpinn_set_tc_select(xpinn_handle h, const int32_t* sel);
 
 /* Device time in milliseconds of the four phases of the most recent step or
  * grad call, measured by CUDA events recorded on the call's stream:

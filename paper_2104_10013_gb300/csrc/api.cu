@@ -173,6 +173,10 @@ struct xpinn_ctx {
   // per-subdomain cap on the points of a sub-tile (0: none), chosen per shape
   // class by xpinn_autotune_shapes; empty = none
   std::vector<int> tile_cap;
+  // per-subdomain choice of the tensor-core kernel for its residual items
+  // (1 on, 0 off, -1 the default rule), chosen per shape class by
+  // xpinn_autotune_shapes; empty = the default rule everywhere
+  std::vector<int> tc_sel;
   int64_t n_params = 0, n_res_total = 0, n_pts_total = 0, n_if_pts = 0;
   int n_out_total = 0, n_eq = 1, d4_nv = 0;
   // device problem
@@ -389,20 +393,23 @@ void build_plan(xpinn_ctx* h, int p_cap) {
   int64_t tc_pts = 0;
   for (int q = 0; q < h->n_sub; ++q) {
     const SubDev& sd = h->subs[q];
-    if (sd.n_res && step_tc_net_ok(sd.net[0], sd.n_nets, h->pde, h->opt.train_tensor_cores)) {
-      tcq[q] = 1;
-      any_tc = true;
-      tc_total += (double)sd.n_res * (sd.net[0].L - 1);
+    const int sel = h->tc_sel.empty() ? -1 : h->tc_sel[q];
+    if (sel != 0 && sd.n_res && step_tc_net_ok(sd.net[0], sd.n_nets, h->pde, h->opt.train_tensor_cores)) {
+      tcq[q] = sel == 1 ? 2 : 1;   // 2: chosen for this subdomain, 1: by the default rule
       tc_pts += sd.n_res;
     }
   }
-  // the tensor-core kernel runs before the jet kernel, so it pays off only
-  // when it takes over most of the step: at least half of the residual points
-  if (any_tc && 2 * tc_pts < h->n_res_total) {
-    std::fill(tcq.begin(), tcq.end(), 0);
-    any_tc = false;
-    tc_total = 0;
-  }
+  // default rule: the tensor-core kernel runs before the jet kernel, so it
+  // pays off only when it takes over most of the step, at least half of the
+  // residual points; subdomains chosen explicitly keep it regardless
+  if (2 * tc_pts < h->n_res_total)
+    for (auto& t : tcq)
+      if (t == 1) t = 0;
+  for (int q = 0; q < h->n_sub; ++q)
+    if (tcq[q]) {
+      any_tc = true;
+      tc_total += (double)h->subs[q].n_res * (h->subs[q].net[0].L - 1);
+    }
   // first pass: one item per point set, to estimate the total cost (with
   // tensor-core residual items, of everything the jet kernel still runs)
   double total = 0;
@@ -2317,6 +2324,29 @@ int xpinn_set_tile_caps(xpinn_handle h, const int32_t* caps) {
   API_END
 }
 
+int xpinn_get_tc_select(xpinn_handle h, int32_t* sel) {
+  API_BEGIN
+  if (!h || !sel) fail(XPINN_ERR_INVALID, "bad arguments");
+  for (int q = 0; q < h->n_sub; ++q) sel[q] = h->tc_sel.empty() ? -1 : h->tc_sel[q];
+  API_END
+}
+
+int xpinn_set_tc_select(xpinn_handle h, const int32_t* sel) {
+  API_BEGIN
+  if (!h) fail(XPINN_ERR_INVALID, "bad arguments");
+  DeviceGuard dg(h);
+  if (sel)
+    for (int q = 0; q < h->n_sub; ++q)
+      if (sel[q] < -1 || sel[q] > 1) fail(XPINN_ERR_INVALID, "tensor-core selection must be -1, 0 or 1");
+  ck(cudaDeviceSynchronize(), "sync");
+  if (sel)
+    h->tc_sel.assign(sel, sel + h->n_sub);
+  else
+    h->tc_sel.clear();
+  apply_options(h, h->opt);
+  API_END
+}
+
 int xpinn_autotune_shapes(xpinn_handle h, int32_t steps, float* best_ms) {
   API_BEGIN
   if (!h || steps < 1) fail(XPINN_ERR_INVALID, "bad arguments");
@@ -2345,6 +2375,7 @@ int xpinn_autotune_shapes(xpinn_handle h, int32_t steps, float* best_ms) {
   std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return share[a] > share[b]; });
   if (h->tile_cap.empty()) h->tile_cap.assign(h->n_sub, 0);
   const std::vector<int> orig = h->tile_cap;
+  const std::vector<int> orig_sel = h->tc_sel;
   const xpinn_options orig_opt = h->opt;
   xpinn_options topt = h->opt;
   topt.profile_phases = 0;
@@ -2380,11 +2411,31 @@ int xpinn_autotune_shapes(xpinn_handle h, int32_t steps, float* best_ms) {
       }
       for (int q : members[c]) h->tile_cap[q] = keep;
     }
+    // then, for classes whose networks the tensor-core kernel takes, that
+    // kernel on and off for their residual items
+    if (h->tc_sel.empty()) h->tc_sel.assign(h->n_sub, -1);
+    for (size_t c : order) {
+      const SubDev& sd = h->subs[members[c][0]];
+      if (!step_tc_net_ok(sd.net[0], sd.n_nets, h->pde, h->opt.train_tensor_cores)) continue;
+      int keep = h->tc_sel[members[c][0]];
+      for (int sel : {1, 0}) {
+        if (sel == keep || elapsed_s() > 30.0) continue;
+        for (int q : members[c]) h->tc_sel[q] = sel;
+        apply_options(h, topt);
+        const float t = time_grads(h, s, e0, e1, steps);
+        if (t < best * 0.995f) {
+          best = t;
+          keep = sel;
+        }
+      }
+      for (int q : members[c]) h->tc_sel[q] = keep;
+    }
   } catch (...) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
     h->tile_cap = orig;
+    h->tc_sel = orig_sel;
     apply_options(h, orig_opt);
     throw;
   }

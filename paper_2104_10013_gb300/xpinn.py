@@ -130,6 +130,8 @@ def load() -> C.CDLL:
         "xpinn_set_remote_values": (C.c_int, [vp, fp, i64, vp]),
         "xpinn_partition": (C.c_int, [i32, vp, i32, vp, vp, vp, i32, vp]),
         "xpinn_get_tile_caps": (C.c_int, [vp, vp]),
+        "xpinn_get_tc_select": (C.c_int, [vp, vp]),
+        "xpinn_set_tc_select": (C.c_int, [vp, vp]),
         "xpinn_set_tile_caps": (C.c_int, [vp, vp]),
         "xpinn_server_create": (C.c_int, [C.POINTER(vp), i32, C.c_size_t, C.POINTER(vp)]),
         "xpinn_server_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
@@ -464,9 +466,20 @@ class Solver:
         caps = None if caps is None else np.ascontiguousarray(np.asarray(caps, np.int32))
         _check(self.lib.xpinn_set_tile_caps(self.h, None if caps is None else caps.ctypes.data))
 
+    def tc_select(self):
+        """Per subdomain: 1 tensor-core kernel, 0 jet kernel, -1 default rule."""
+        sel = np.zeros(self.n_sub, np.int32)
+        _check(self.lib.xpinn_get_tc_select(self.h, sel.ctypes.data))
+        return sel
+
+    def set_tc_select(self, sel):
+        sel = None if sel is None else np.ascontiguousarray(np.asarray(sel, np.int32))
+        _check(self.lib.xpinn_set_tc_select(self.h, None if sel is None else sel.ctypes.data))
+
     def autotune(self, steps=5, cache=None, shapes=True, write=True) -> dict:
         """Pick tile shapes by timing: the launch options (xpinn_autotune),
-        then a sub-tile cap per shape class (xpinn_autotune_shapes).  With
+        then a sub-tile cap and the tensor-core choice per shape class
+        (xpinn_autotune_shapes).  With
         `cache` (a JSON file path) reuse a recorded choice for this problem
         signature, else time and (with `write`) record it: the options per
         problem signature, the caps per shape class."""
@@ -484,6 +497,9 @@ class Solver:
             cc = db[key].get("class_caps")
             if cc:
                 self.set_tile_caps([cc.get(self.shape_class(sd), 0) for sd in self.pb.subs])
+            ct = db[key].get("class_tc")
+            if ct:
+                self.set_tc_select([ct.get(self.shape_class(sd), -1) for sd in self.pb.subs])
             return db[key]
         o = Options()
         ms = C.c_float(0)
@@ -494,6 +510,7 @@ class Solver:
             _check(self.lib.xpinn_autotune_shapes(self.h, steps, C.byref(ms2)))
             caps = self.tile_caps()
             rec["class_caps"] = {self.shape_class(sd): int(c) for sd, c in zip(self.pb.subs, caps)}
+            rec["class_tc"] = {self.shape_class(sd): int(c) for sd, c in zip(self.pb.subs, self.tc_select())}
             rec["ms_shapes"] = ms2.value
         if cache and write:
             db[key] = rec

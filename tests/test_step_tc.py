@@ -143,3 +143,31 @@ def test_items_longer_than_a_flush_sampled():
             a, b = g[sl].astype(np.float64), g_ref[sl]
             assert np.linalg.norm(a - b) <= RTOL_GRAD * np.linalg.norm(b), name
             assert np.abs(a - b).max() <= RTOL_GRAD * np.abs(b).max(), name
+
+
+def test_tensor_core_choice_per_subdomain(X):
+    """The one 64-wide subdomain of the uneven Poisson workload lies below
+    the default share rule; choosing the tensor-core kernel for it alone puts
+    its residual items there, and the gradient still matches the oracle.
+    Choosing the jet kernel everywhere empties the tensor-core items of the
+    Navier-Stokes case."""
+    pb = P.poisson_xpinn(n_res_range=(300, 1500), n_iface=64, n_bc=40)
+    s = X.Solver(pb)
+    assert s.plan_counts()[1] == 0
+    wide = [q for q, sd in enumerate(pb.subs) if max(sd.nets[0].widths[1:-1]) == 64 and len(sd.nets[0].widths) >= 4]
+    assert wide
+    sel = np.full(pb.n_sub, -1, np.int32)
+    sel[wide] = 1
+    s.set_tc_select(sel)
+    assert s.plan_counts()[2] == len(wide)
+    assert list(s.tc_select()) == list(sel)
+    losses, g = s.grad()
+    terms, g_ref = Oracle(pb).grad(pb.packed_params())
+    assert_losses(losses, terms)
+    assert_grads(g, g_ref, pb)
+    s.close()
+    t = solver(X, ns_small(), 64)
+    assert t.plan_counts()[1] > 0
+    t.set_tc_select(np.zeros(4, np.int32))
+    assert t.plan_counts()[1] == 0
+    t.close()
