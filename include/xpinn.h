@@ -377,7 +377,8 @@ typedef struct {
   int32_t train_tensor_cores; /* 0: the FP32 jet kernel trains every
                                subdomain.  N in [1, 64] (default 64): the
                                residual points of every subdomain with one
-                               fixed-slope tanh network of input (x, y),
+                               network of input (x, y), tanh, sin or cos
+                               hidden layers (fixed or trained slopes),
                                identity output of at most 3 components, 3 to
                                7 weight layers and every hidden width within
                                [N, 64], under a PDE trained with Laplacian

@@ -225,6 +225,7 @@ struct xpinn_ctx {
   DevBuf<TcTrainPack> tct_pack_d;
   int n_tct_pack = 0;
   int tct_grid = 0;
+  int tct_gen = 0;               // 1: some of those networks need the general activation rules
   // device time of the evaluation kernel of the last routed evaluation
   // (profile_phases): events around its launch
   cudaEvent_t eval_ev[2] = {};
@@ -614,12 +615,14 @@ void plan_tc(xpinn_ctx* h) {
   std::vector<int64_t> off(h->n_sub, -1);
   std::vector<TcTrainPack> pk;
   int64_t n = 0;
+  int gen = 0;
   for (int i = pl.n_simt(); i < (int)pl.items.size(); ++i) {
     const int q = pl.items[i].q;
     if (off[q] >= 0) continue;
     const SubDev& sd = h->subs[q];
     const NetDev& nd = sd.net[0];
     off[q] = n;
+    if (net_is_general(nd)) gen = 1;
     for (int k = 2; k < nd.L; ++k) {
       const int64_t src = sd.poff + nd.off[k];
       pk.push_back({src, n + (int64_t)(k - 2) * STC_IMG, nd.w[k], nd.w[k - 1], 0});
@@ -628,6 +631,7 @@ void plan_tc(xpinn_ctx* h) {
     n += (int64_t)2 * (nd.L - 2) * STC_IMG;
   }
   h->n_tct_pack = pl.n_tc ? (int)pk.size() : 0;
+  h->tct_gen = gen;
   h->tct_grid = 0;
   if (!pl.n_tc) {
     h->tct_img.release();
@@ -811,6 +815,7 @@ void launch_tc(xpinn_ctx* h, int begin, int count, int counter_idx, cudaStream_t
   a.pde = h->pde;
   a.nu = h->nu;
   a.re = h->re;
+  a.gen = h->tct_gen;
   a.err = h->err_d.p;
   launch_step_tc(a, std::min(h->tct_grid, count), s);
 }

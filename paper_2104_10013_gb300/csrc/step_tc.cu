@@ -104,7 +104,8 @@ constexpr int O_P = O_Z + SZ_ZS;
 constexpr int O_DB = O_P + 128;
 constexpr int O_DL = O_DB + (STC_MAXL - 2) * 64;
 constexpr int O_PW = O_DL + 128;
-constexpr int SMEM_FLOATS = O_PW + SZ_PW;
+constexpr int O_SL = O_PW + SZ_PW;                   // slope-gradient sums [STC_MAXL - 1][16 warps]
+constexpr int SMEM_FLOATS = O_SL + (STC_MAXL - 1) * 16;
 // tensor-memory columns: Z main [0, 64), Z cross [64, 128), dW^k (k = 2..L-1)
 // at 128 + 64 (k - 2), then dW^1 and dW^L (16 columns each)
 constexpr int TMEM_COLS = 512;
@@ -383,6 +384,49 @@ __device__ __forceinline__ void zs_row_read(const float* __restrict__ ZS, int r,
   }
 }
 
+// The same for a general hidden activation h = Phi(s z) (tanh, sin or cos,
+// slope s = n a^k), per neuron by the shared jet rules of the jet kernel;
+// the saved jets are then the unscaled z, and the reverse rule adds
+// dJ/ds = sum over components of vb_c z_c to gs.
+__device__ __forceinline__ void jet4_fwd_gen(const Act& act, const float (&z)[4][NPG], float (&h)[4][NPG],
+                                             float (&sv)[4][NPG]) {
+#pragma unroll
+  for (int i = 0; i < NPG; ++i) {
+    const float zz[4] = {z[0][i], z[1][i], z[2][i], z[3][i]};
+    float hh[4];
+    phi_jet<4, true>(act, zz, hh);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      h[c][i] = hh[c];
+      sv[c][i] = zz[c];
+    }
+  }
+}
+
+__device__ __forceinline__ void jet4_saved_gen(const Act& act, const float (&sv)[4][NPG], float (&h)[4][NPG]) {
+#pragma unroll
+  for (int i = 0; i < NPG; ++i) {
+    const float zz[4] = {sv[0][i], sv[1][i], sv[2][i], sv[3][i]};
+    float hh[4];
+    phi_jet<4, true>(act, zz, hh);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) h[c][i] = hh[c];
+  }
+}
+
+__device__ __forceinline__ void jet4_bwd_gen(const Act& act, const float (&sv)[4][NPG], const float (&hb)[4][NPG],
+                                             float (&zb)[4][NPG], float& gs) {
+#pragma unroll
+  for (int i = 0; i < NPG; ++i) {
+    const float zz[4] = {sv[0][i], sv[1][i], sv[2][i], sv[3][i]};
+    const float hh[4] = {hb[0][i], hb[1][i], hb[2][i], hb[3][i]};
+    float zr[4];
+    act_jet_bwd<4, true, true>(act, zz, hh, zr, gs);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) zb[c][i] = zr[c];
+  }
+}
+
 // Sums over the warp's 32 points of the value-row adjoints of the thread's 4
 // neurons (fixed butterfly); lane 0 adds them to d[0..3]
 __device__ __forceinline__ void value_sums(const float (&zb)[4][NPG], int lane, float* __restrict__ d) {
@@ -399,6 +443,10 @@ __device__ __forceinline__ void value_sums(const float (&zb)[4][NPG], int lane, 
   }
 }
 
+// GEN = false: every network is tanh with fixed slopes (saved t); true: any
+// hidden activation and trained slopes (saved z, Phi evaluated again in the
+// reverse pass, slope gradients summed per layer).
+template <bool GEN>
 __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   extern __shared__ __align__(1024) float sm[];
   float* RA = sm + O_A;
@@ -413,6 +461,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   float* dbs = sm + O_DB;
   float* dls = sm + O_DL;
   float* pw = sm + O_PW;
+  float* sls = sm + O_SL;
   __shared__ __align__(8) uint64_t bars[3];   // weight buffer, row MMAs, gradient MMAs
   __shared__ uint32_t s_tmem;
   __shared__ int s_item, s_stop;
@@ -495,6 +544,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
     }
     for (int e = tid; e < (STC_MAXL - 2) * 64; e += NTH) dbs[e] = 0.f;
     if (tid < 128) dls[tid] = 0.f;
+    if (tid < (STC_MAXL - 1) * 16) sls[tid] = 0.f;
     double l0 = 0.0;
     const int n_tiles = (it.n_pts + STC_PTS - 1) / STC_PTS;
     if (tid < STC_PTS) sp2[tid] = tid < it.n_pts ? a.pts[it.pt_off + tid] : make_float2(0.f, 0.f);
@@ -524,7 +574,10 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           v[2][i] = w.y;
           v[3][i] = 0.f;
         }
-        jet4_fwd(v, h, sv);
+        if constexpr (GEN)
+          jet4_fwd_gen(layer_act(nd, prm, 1), v, h, sv);
+        else
+          jet4_fwd(v, h, sv);
         save4(scr, p, g, sv);
         split4(h, hh, hl);
         put_a(RA, p, g, hh, hl);   // L >= 3: a hidden-to-hidden layer reads it
@@ -560,7 +613,10 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           v[0][2] += b.z;
           v[0][3] += b.w;
         }
-        jet4_fwd(v, h, sv);
+        if constexpr (GEN)
+          jet4_fwd_gen(layer_act(nd, prm, k), v, h, sv);
+        else
+          jet4_fwd(v, h, sv);
         save4(scr + (k - 1) * STC_W * ROWS, p, g, sv);
         split4(h, hh, hl);
         if (k < L - 1) {
@@ -679,7 +735,16 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           __syncthreads();
         }
         zs_read4(ZS, p, g, h);        // Hb^k
-        jet4_bwd(sv, h, v);           // Zb^k
+        if constexpr (GEN) {
+          float gsl = 0.f;
+          jet4_bwd_gen(layer_act(nd, prm, k), sv, h, v, gsl);
+          // dJ/ds of layer k over the warp's points and neurons, added per warp
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) gsl += __shfl_xor_sync(FULL, gsl, o);
+          if (lane == 0 && nd.aoff >= 0) sls[(k - 1) * 16 + warp] += gsl;
+        } else {
+          jet4_bwd(sv, h, v);         // Zb^k
+        }
         split4(v, hh, hl);
         if (k >= 2) {
           value_sums(v, lane, dbs + (k - 2) * 64 + 4 * g);   // db^k
@@ -737,7 +802,10 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           mma_commit(bars + 1);
         }
         // H^{k-1} from the saved jets of layer k - 1
-        jet4_saved(sv, h);
+        if constexpr (GEN)
+          jet4_saved_gen(layer_act(nd, prm, k - 1), sv, h);
+        else
+          jet4_saved(sv, h);
         split4(h, hh, hl);
         mbar_park(bars + 1, mph, a.err);   // region A and the weight buffer are free
         mph ^= 1u;
@@ -814,6 +882,12 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
             for (int q = 0; q < STC_PTS; ++q) sb += dls[q * 4 + tid];
             gw[D * wl + tid] = sb;
           }
+          // trained slopes: dJ/da^k = n dJ/ds, the warps' sums in warp order
+          if (GEN && last && nd.aoff >= 0 && tid < L - 1) {
+            float sb = 0.f;
+            for (int q = 0; q < 16; ++q) sb += sls[tid * 16 + q];
+            gs[nd.aoff + tid] = nd.scale * sb;
+          }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();   // region A is rewritten by the next tile
@@ -858,7 +932,7 @@ __global__ void __launch_bounds__(256) pack_tc_train_kernel(const float* __restr
 bool step_tc_net_ok(const NetDev& nd, int n_nets, int pde, int min_width) {
   if (min_width <= 0 || n_nets != 1 || (pde != XPINN_PDE_POISSON && pde != XPINN_PDE_NS)) return false;
   if (nd.L < 3 || nd.L > STC_MAXL || nd.w[0] != 2 || nd.w[nd.L] < 1 || nd.w[nd.L] > 3) return false;
-  if (nd.out_act != XPINN_ACT_IDENTITY || net_is_general(nd)) return false;
+  if (nd.out_act != XPINN_ACT_IDENTITY) return false;
   for (int k = 1; k < nd.L; ++k)
     if (nd.w[k] < min_width || nd.w[k] > STC_W) return false;
   return true;
@@ -867,12 +941,20 @@ bool step_tc_net_ok(const NetDev& nd, int n_nets, int pde, int min_width) {
 size_t step_tc_smem_bytes() { return sizeof(float) * (size_t)SMEM_FLOATS; }
 
 cudaError_t step_tc_configure() {
-  return cudaFuncSetAttribute(step_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)step_tc_smem_bytes());
+  cudaError_t e = cudaFuncSetAttribute(step_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)step_tc_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)step_tc_smem_bytes());
+  return e;
 }
 
 void launch_step_tc(const StepTcArgs& a, int grid, cudaStream_t s) {
-  if (grid > 0 && a.n_items > 0) step_tc_kernel<<<grid, NTH, step_tc_smem_bytes(), s>>>(a);
+  if (grid <= 0 || a.n_items <= 0) return;
+  if (a.gen)
+    step_tc_kernel<true><<<grid, NTH, step_tc_smem_bytes(), s>>>(a);
+  else
+    step_tc_kernel<false><<<grid, NTH, step_tc_smem_bytes(), s>>>(a);
 }
 
 void launch_pack_tc_train(const float* params, const TcTrainPack* blocks, int n_blocks, float* img,

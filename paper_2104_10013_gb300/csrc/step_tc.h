@@ -1,10 +1,10 @@
 // Training-step kernel on the tensor cores (step_tc.cu): launch interface for
 // the host planner.  A subdomain qualifies when it has one network with
-// input (x, y), identity output of at most three components, fixed-slope
-// tanh hidden layers, 3 to 7 weight layers and every hidden width within
-// [min_width, 64], and its PDE trains with Laplacian jets (Poisson,
-// Navier-Stokes).  Its residual items then run on this kernel; its data and
-// interface items stay on the FP32 jet kernel.
+// input (x, y), identity output of at most three components, tanh, sin or
+// cos hidden layers with fixed or trained slopes, 3 to 7 weight layers and
+// every hidden width within [min_width, 64], and its PDE trains with
+// Laplacian jets (Poisson, Navier-Stokes).  Its residual items then run on
+// this kernel; its data and interface items stay on the FP32 jet kernel.
 #pragma once
 #include <cstdint>
 
@@ -37,6 +37,7 @@ struct StepTcArgs {
   float* scratch;            // STC_SCRATCH floats per CTA
   int pde;
   float nu, re;
+  int gen;                   // 1: some network has a general activation or trained slopes
   int* err;                  // device status word
 };
 

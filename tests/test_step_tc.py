@@ -1,7 +1,7 @@
 """Residual items of the training step on the tensor cores (option
 train_tensor_cores): the forward jets, the reverse pass and the weight
 gradients of hidden layers up to 64 wide as tcgen05 TF32 MMAs over hi/lo
-splits of both operands, for fixed-slope tanh networks under Laplacian-jet
+splits of both operands, for tanh, sin and cos networks under Laplacian-jet
 PDEs (Poisson, Navier-Stokes).
 
 * losses (1e-5) and every gradient tensor (1e-4) match the FP64 oracle on a
@@ -10,6 +10,8 @@ PDEs (Poisson, Navier-Stokes).
   zero-padded to 64, two to five hidden layers) with one-hidden-layer
   networks that stay on the jet kernel in the same step; point counts leave
   ragged tiles (32 points) and ragged items;
+* tanh, sin and cos hidden layers with trained or fixed slopes (the slope
+  gradients included);
 * the smallest network the kernel takes (one hidden-to-hidden layer of width
   33, zero-padded to 64) and items longer than one accumulator flush (16
   tiles) on a large workload, sampled against the oracle;
@@ -171,3 +173,20 @@ def test_tensor_core_choice_per_subdomain(X):
     t.set_tc_select(np.zeros(4, np.int32))
     assert t.plan_counts()[1] == 0
     t.close()
+
+
+@pytest.mark.parametrize("acts,adaptive", [((P.PHI_SIN, P.PHI_COS, P.PHI_TANH), True),
+                                           ((P.PHI_COS, P.PHI_SIN), False),
+                                           ((P.PHI_TANH,), True)])
+def test_general_activations_on_the_tensor_cores(X, acts, adaptive):
+    """tanh, sin and cos hidden layers with trained slopes n a^k (Sec. 3) or
+    fixed ones: the kernel's general rules, including every slope gradient."""
+    from tests.cases import with_activations
+    pb = with_activations(ns_small(), list(acts), adaptive=adaptive)
+    s = solver(X, pb, 64)
+    assert s.plan_counts()[2] == pb.n_sub
+    losses, g = s.grad()
+    terms, g_ref = Oracle(pb).grad(pb.packed_params())
+    assert_losses(losses, terms)
+    assert_grads(g, g_ref, pb)
+    s.close()
