@@ -19,14 +19,16 @@
 // row: warps w, w + 4, w + 8, w + 12 read the same tensor-memory lanes, 16 of
 // the 64 neurons each) they move accumulator rows out of tensor memory into a
 // staging array [point][component][neuron].  As point threads (lane = point,
-// warp = a group of 4 neurons) they apply the jet rule of tanh to all four
-// components of a point at once, in registers:
+// warp = a group of 4 neurons) they apply the jet rule to all four components
+// of a point at once, in registers -- for fixed-slope tanh
 //   h = t,  h_i = s z_i,  h_lap = s z_lap - 2 t s (z_x^2 + z_y^2),  t = tanh z,
-// s = 1 - t^2, and its reverse, and write the MMA operand images: 4 rows of one
-// neuron are one 16-byte run in every image, transposed or not.  tanh is
-// evaluated once per (point, neuron).  The pre-activation jets (t, z_x, z_y,
-// z_lap) go to per-CTA scratch in global memory (L2-resident) for the reverse
-// pass, which rebuilds H^{k-1} from them.
+// s = 1 - t^2, for tanh, sin or cos with a slope the jet kernel's general rule
+// -- and its reverse, and write the MMA operand images: 4 rows of one neuron
+// are one 16-byte run in every image, transposed or not.  The activation is
+// evaluated once per (point, neuron) and pass.  The pre-activation jets (t,
+// z_x, z_y, z_lap for tanh; z for the general rule) go to per-CTA scratch in
+// global memory (L2-resident) for the reverse pass, which rebuilds H^{k-1}
+// from them.
 //
 // Precision: every contraction takes three TF32 products over hi/lo splits
 // of both operands (hi = rna(x), lo = rna(x - hi); the dropped lo x lo term
