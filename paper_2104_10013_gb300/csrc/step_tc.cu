@@ -15,7 +15,7 @@
 // the jet rules and the residual stay on the FP32 pipes.
 //
 // Tile: 128 rows = the MMA's M, 32 points x 4 jet components (u, u_x, u_y,
-// lap u), row 4 p + c.  512 threads take two roles.  As row threads (four per
+// lap u), row 4 p + c.  16 compute warps take two roles.  As row threads (four per
 // row: warps w, w + 4, w + 8, w + 12 read the same tensor-memory lanes, 16 of
 // the 64 neurons each) they move accumulator rows out of tensor memory into a
 // staging array [point][component][neuron].  As point threads (lane = point,
@@ -43,11 +43,23 @@
 // whole item (about 80 tiles) erred up to 1.04e-4 of the largest gradient
 // element on the full-size Navier-Stokes workload.
 //
+// A 17th warp issues the MMAs (one thread) and the weight copies.  Issuing
+// an MMA stalls the issuing thread for about as long as the tensor core
+// takes to run the one before it, so a compute warp that issued the 32 MMAs
+// of a weight gradient would hold every later barrier of the tile for their
+// whole duration; from the MMA warp they run while the compute warps move on
+// to the next layer's reverse rule.  The compute warps hand over each
+// operand set with one arrival per warp on an mbarrier (after a proxy fence)
+// and synchronise among themselves on a named barrier that the MMA warp
+// does not join; the MMA warp follows the same fixed sequence of MMA groups
+// per tile, so their order, and the gradient, do not depend on timing.
+//
 // Operands are K-major, no swizzle.  Images whose K is the tile's rows pad
 // every K-step of core matrices by 16 bytes.  Weight images (forward and
 // reverse, built by pack_tc_train_kernel) arrive by bulk copy into one buffer,
 // the next image's copy issued as soon as an MMA has released it (it lands
-// during the epilogue).  Every wait is bounded; a wait that gives up sets the
+// during the epilogue; the first image of the next tile during the reverse
+// pass's last layers).  Every wait is bounded; a wait that gives up sets the
 // error word, the launch stops taking items, frees its tensor memory and ends.
 #include <cuda_runtime.h>
 
@@ -60,7 +72,10 @@ namespace xp {
 namespace {
 
 constexpr int NPT = 16;                  // neurons of a row thread (of the 64)
-constexpr int NTH = 128 * (STC_W / NPT); // four row threads per row; 16 warps of point threads
+constexpr int NCW = 16;                  // compute warps: row threads and point threads
+constexpr int NTC = 32 * NCW;            // compute threads (four row threads per row)
+constexpr int NTH = NTC + 32;            // and one warp that issues the MMAs and the weight copies
+static_assert(NTC == 128 * (STC_W / NPT), "four row threads per row");
 constexpr int NPG = 4;                   // neurons of a point thread
 constexpr int ROWS = 128;
 constexpr unsigned FULL = 0xffffffffu;
@@ -129,6 +144,35 @@ __device__ __forceinline__ void fence_to_async() {
 }
 __device__ __forceinline__ void after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// barrier of the compute warps (the MMA warp does not take part)
+__device__ __forceinline__ void csync() { asm volatile("bar.sync 1, %0;" ::"n"(NTC) : "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// A compute warp has written its part of the next MMA's operands: its
+// writes are made visible to the tensor core, then the warp arrives (once)
+// on the operand barrier, which completes when all NCW warps have.
+__device__ __forceinline__ void operands_ready(uint64_t* bar, int lane) {
+  fence_to_async();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar);
+}
+
+// sum over the compute threads (thread 0 gets it)
+__device__ __forceinline__ double compute_sum(double v, double* red, int warp, int lane) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  csync();
+  if (lane == 0) red[warp] = v;
+  csync();
+  double t = 0.0;
+  if (warp == 0 && lane == 0)
+    for (int w = 0; w < NCW; ++w) t += red[w];
+  return t;
+}
+
 // mbar_wait with a suspend-time hint: a warp that finds the phase
 // incomplete is parked in the barrier until the phase completes (or the hint
 // of 10 ms runs out) instead of polling, so that waiting warps take no issue
@@ -169,18 +213,20 @@ __device__ __forceinline__ uint64_t dstep(int bytes) { return (uint64_t)(bytes >
 
 // Z (+)= A . B over K = 64: A the row-major image at a (hi, then lo), read
 // K-major; B a weight image at b (hi, then lo); hi x hi into tm, the cross
-// terms into tm + 64.
+// terms into tm + 64.  The hi and lo halves of a weight image are one
+// operand of N = 128 (their 8-row groups continue at the same stride), so a
+// single MMA takes A_hi against both: the A tile is read from shared memory
+// twice per K-step instead of three times (the MMAs of this kernel are
+// bound by shared-memory reads: 6 KB of operands per N = 64 MMA).
 __device__ __forceinline__ void mma_rows(uint32_t tm, uint32_t a, uint32_t b) {
-  const uint32_t id = tc_idesc(STC_W);
+  const uint32_t id2 = tc_idesc(2 * STC_W), id = tc_idesc(STC_W);
   const uint64_t ahi = tc_sdesc(a, A_LBO, A_SBO), alo = tc_sdesc(a + 4 * SZ_AF, A_LBO, A_SBO);
-  const uint64_t bhi = tc_sdesc(b, 128, STC_W / 4 * 128);
-  const uint64_t blo = tc_sdesc(b + 4 * STC_W * STC_W, 128, STC_W / 4 * 128);
+  const uint64_t bhl = tc_sdesc(b, 128, STC_W / 4 * 128);   // hi rows 0-63, lo rows 64-127
 #pragma unroll
   for (int ks = 0; ks < STC_W / 8; ++ks) {
     const uint64_t da = dstep(ks * 2 * A_LBO), db = dstep(ks * 256);
-    tc_mma(tm, ahi + da, bhi + db, id, ks > 0 ? 1u : 0u);
-    tc_mma(tm + 64, ahi + da, blo + db, id, ks > 0 ? 1u : 0u);
-    tc_mma(tm + 64, alo + da, bhi + db, id, 1u);
+    tc_mma(tm, ahi + da, bhl + db, id2, ks > 0 ? 1u : 0u);
+    tc_mma(tm + 64, alo + da, bhl + db, id, 1u);
   }
 }
 
@@ -286,47 +332,39 @@ __device__ __forceinline__ void jet4_bwd(const float (&sv)[4][NPG], const float 
   }
 }
 
-__device__ __forceinline__ void split4(const float (&v)[4][NPG], float (&hi)[4][NPG], float (&lo)[4][NPG]) {
-#pragma unroll
-  for (int c = 0; c < 4; ++c)
-#pragma unroll
-    for (int i = 0; i < NPG; ++i) {
-      const float2 s = tf32_split(v[c][i]);
-      hi[c][i] = s.x;
-      lo[c][i] = s.y;
-    }
+// The operand images take the hi/lo split of a thread's 16 values, formed
+// as they are stored (no split copy stays live in registers).
+__device__ __forceinline__ void split_store(float* __restrict__ hi_at, float* __restrict__ lo_at, float a, float b,
+                                            float c, float d) {
+  const float2 sa = tf32_split(a), sb = tf32_split(b), sc = tf32_split(c), sd = tf32_split(d);
+  *reinterpret_cast<float4*>(hi_at) = make_float4(sa.x, sb.x, sc.x, sd.x);
+  *reinterpret_cast<float4*>(lo_at) = make_float4(sa.y, sb.y, sc.y, sd.y);
 }
 
 // Row-major A image (hi at A, lo at A + SZ_AF): per row, the 4 neurons
-__device__ __forceinline__ void put_a(float* __restrict__ A, int p, int g, const float (&hi)[4][NPG],
-                                      const float (&lo)[4][NPG]) {
+__device__ __forceinline__ void put_a(float* __restrict__ A, int p, int g, const float (&x)[4][NPG]) {
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const int o = a_off5(4 * p + c, g);
-    *reinterpret_cast<float4*>(A + o) = make_float4(hi[c][0], hi[c][1], hi[c][2], hi[c][3]);
-    *reinterpret_cast<float4*>(A + SZ_AF + o) = make_float4(lo[c][0], lo[c][1], lo[c][2], lo[c][3]);
+    split_store(A + o, A + SZ_AF + o, x[c][0], x[c][1], x[c][2], x[c][3]);
   }
 }
 
 // Stacked transposed image (M-row n: hi, 64 + n: lo): per neuron, the 4 rows
-__device__ __forceinline__ void put_t(float* __restrict__ T, int p, int g, const float (&hi)[4][NPG],
-                                      const float (&lo)[4][NPG]) {
+__device__ __forceinline__ void put_t(float* __restrict__ T, int p, int g, const float (&x)[4][NPG]) {
 #pragma unroll
   for (int i = 0; i < NPG; ++i) {
     const int n = 4 * g + i;
-    *reinterpret_cast<float4*>(T + t_off(n, 4 * p)) = make_float4(hi[0][i], hi[1][i], hi[2][i], hi[3][i]);
-    *reinterpret_cast<float4*>(T + t_off(64 + n, 4 * p)) = make_float4(lo[0][i], lo[1][i], lo[2][i], lo[3][i]);
+    split_store(T + t_off(n, 4 * p), T + t_off(64 + n, 4 * p), x[0][i], x[1][i], x[2][i], x[3][i]);
   }
 }
 
 // Transposed B' image (hi at B, lo at B + SZ_B): per neuron, the 4 rows
-__device__ __forceinline__ void put_b(float* __restrict__ B, int p, int g, const float (&hi)[4][NPG],
-                                      const float (&lo)[4][NPG]) {
+__device__ __forceinline__ void put_b(float* __restrict__ B, int p, int g, const float (&x)[4][NPG]) {
 #pragma unroll
   for (int i = 0; i < NPG; ++i) {
     const int o = b_off(4 * g + i, 4 * p);
-    *reinterpret_cast<float4*>(B + o) = make_float4(hi[0][i], hi[1][i], hi[2][i], hi[3][i]);
-    *reinterpret_cast<float4*>(B + SZ_B + o) = make_float4(lo[0][i], lo[1][i], lo[2][i], lo[3][i]);
+    split_store(B + o, B + SZ_B + o, x[0][i], x[1][i], x[2][i], x[3][i]);
   }
 }
 
@@ -445,6 +483,39 @@ __device__ __forceinline__ void value_sums(const float (&zb)[4][NPG], int lane, 
   }
 }
 
+// The residual of one point from its output jets J[o][c] (o < D, c < 4:
+// value, x, y, Laplacian), and the seeds G[o][c] = coef dr^2/dJ; returns the
+// squared residual.  Not inlined: the 40 jet values it holds would raise the
+// register peak of the whole kernel, and one warp runs it once per tile.
+__device__ __noinline__ float point_residual(int pde, int D, const float* __restrict__ Jo, float* __restrict__ Go,
+                                             float f, float coef, float nu, float re) {
+  PtJets J, G;
+#pragma unroll
+  for (int o = 0; o < XPINN_MAX_OUT; ++o)
+#pragma unroll
+    for (int cc = 0; cc < KMAX; ++cc) {
+      J.u[o][cc] = (o < D && cc < 4) ? Jo[o * 4 + cc] : 0.f;
+      G.u[o][cc] = 0.f;
+    }
+#pragma unroll
+  for (int cc = 0; cc < KMAX; ++cc) J.k[cc] = G.k[cc] = 0.f;
+  float rr[3] = {0.f, 0.f, 0.f};
+  const int ne = residual_fwd(pde, J, f, nu, re, rr);
+  float sq = 0.f, e[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    if (q < ne) {
+      sq += rr[q] * rr[q];
+      e[q] = coef * rr[q];
+    }
+  residual_seed(pde, J, e, nu, re, G);
+#pragma unroll
+  for (int o = 0; o < 3; ++o)
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) Go[o * 4 + cc] = o < D ? G.u[o][cc] : 0.f;
+  return sq;
+}
+
 // GEN = false: every network is tanh with fixed slopes (saved t); true: any
 // hidden activation and trained slopes (saved z, Phi evaluated again in the
 // reverse pass, slope gradients summed per layer).
@@ -464,10 +535,10 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   float* dls = sm + O_DL;
   float* pw = sm + O_PW;
   float* sls = sm + O_SL;
-  __shared__ __align__(8) uint64_t bars[3];   // weight buffer, row MMAs, gradient MMAs
+  __shared__ __align__(8) uint64_t bars[4];   // weight buffer, row MMAs, gradient MMAs, operands
   __shared__ uint32_t s_tmem;
   __shared__ int s_item, s_stop;
-  __shared__ double red[NTH / 32];
+  __shared__ double red[NCW];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // row-thread view (tensor memory, the output layer)
   const int quad = warp & 3, part = warp >> 2, nb = part * NPT;
@@ -476,6 +547,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   const int p = lane, g = warp;
   if (tid == 0) {
     for (int i = 0; i < 3; ++i) mbar_init(bars + i, 1);
+    mbar_init(bars + 3, NCW);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -491,7 +563,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16);   // this warp's lanes
   const uint32_t sa = smem_u32(RA), st = smem_u32(RT), sw = smem_u32(RW), ss = smem_u32(RS);
   float* const scr = a.scratch + (int64_t)blockIdx.x * STC_SCRATCH;
-  uint32_t wph = 0, mph = 0, dph = 0;   // phase parities
+  uint32_t wph = 0, mph = 0, dph = 0, oph = 0;   // phase parities
   bool d_pending = false;               // a gradient-MMA commit not yet waited for
   for (;;) {
     if (tid == 0) {
@@ -524,8 +596,65 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
       return img + (int64_t)((i < L - 2 ? 0 : L - 2) + k - 2) * STC_IMG;
     };
     const float coef = 2.f * sd.w_res * sd.inv_n_res;
+    const int n_tiles = (it.n_pts + STC_PTS - 1) / STC_PTS;
+    if (warp == NCW) {
+      // The MMA warp: one thread issues the item's MMAs in the order in
+      // which the compute warps complete their operands, and the weight
+      // copies, each as soon as the buffer is free.
+      if (lane == 0 && n_tiles > 0) {
+        bulk_g2s(RW, img_src(0), 4u * STC_IMG, bars);
+        for (int tile = 0; tile < n_tiles; ++tile) {
+          const bool first = tile % STC_FLUSH == 0;   // the gradient accumulators start from zero
+          for (int k = 2; k <= L - 1; ++k) {            // Z^k = H^{k-1} (W^k)^T
+            mbar_park(bars + 3, oph, a.err);
+            oph ^= 1u;
+            mbar_park(bars, wph, a.err);
+            wph ^= 1u;
+            after_sync();
+            mma_rows(tmem, sa, sw);
+            mma_commit(bars + 1);
+            mbar_park(bars + 1, mph, a.err);
+            mph ^= 1u;
+            bulk_g2s(RW, img_src(k - 1), 4u * STC_IMG, bars);
+          }
+          mbar_park(bars + 3, oph, a.err);              // dW^L: H^{L-1} and the output seeds
+          oph ^= 1u;
+          after_sync();
+          mma_grad<4 * LB_S>(tmem + 144 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, first);
+          mma_commit(bars + 2);
+          for (int k = L - 1; k >= 2; --k) {
+            mbar_park(bars + 3, oph, a.err);            // Hb^{k-1} = Zb^k W^k
+            oph ^= 1u;
+            mbar_park(bars, wph, a.err);
+            wph ^= 1u;
+            after_sync();
+            mma_rows(tmem, sa, sw);
+            mma_commit(bars + 1);
+            mbar_park(bars + 1, mph, a.err);
+            mph ^= 1u;
+            const int i = (L - 2) + (L - 1 - k);
+            if (i + 1 < nimg)
+              bulk_g2s(RW, img_src(i + 1), 4u * STC_IMG, bars);
+            else if (tile + 1 < n_tiles)
+              bulk_g2s(RW, img_src(0), 4u * STC_IMG, bars);
+            mbar_park(bars + 3, oph, a.err);            // dW^k: Zb^k and H^{k-1}
+            oph ^= 1u;
+            after_sync();
+            mma_grad<4 * LB_B>(tmem + 128 + 64 * (k - 2), st, sa, 4u * SZ_B, STC_W, first);
+            mma_commit(bars + 2);
+          }
+          mbar_park(bars + 3, oph, a.err);              // dW^1, db^1: Zb^1 and the input jets
+          oph ^= 1u;
+          after_sync();
+          mma_grad<4 * LB_S>(tmem + 128 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, first);
+          mma_commit(bars + 2);
+        }
+      }
+      __syncwarp();
+      continue;
+    }
     // the item's FP32-pipe weights, zero-padded (visible after the first tile's barrier)
-    for (int e = tid; e < SZ_PW; e += NTH) {
+    for (int e = tid; e < SZ_PW; e += NTC) {
       float v = 0.f;
       if (e < PW_B1) {
         const int n = e >> 1;
@@ -544,27 +673,23 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
       }
       pw[e] = v;
     }
-    for (int e = tid; e < (STC_MAXL - 2) * 64; e += NTH) dbs[e] = 0.f;
+    for (int e = tid; e < (STC_MAXL - 2) * 64; e += NTC) dbs[e] = 0.f;
     if (tid < 128) dls[tid] = 0.f;
     if (tid < (STC_MAXL - 1) * 16) sls[tid] = 0.f;
     double l0 = 0.0;
-    const int n_tiles = (it.n_pts + STC_PTS - 1) / STC_PTS;
     if (tid < STC_PTS) sp2[tid] = tid < it.n_pts ? a.pts[it.pt_off + tid] : make_float2(0.f, 0.f);
     for (int tile = 0; tile < n_tiles; ++tile) {
       const int t0 = tile * STC_PTS;
       const int nv = min(STC_PTS, it.n_pts - t0);
-      const bool first = tile % STC_FLUSH == 0;   // the gradient accumulators start from zero
-      // every MMA of the previous tile has completed: the weight buffer and
-      // regions A, At and S are free
+      // every MMA of the previous tile has completed: regions A, At and S are free
       if (d_pending) {
         mbar_park(bars + 2, dph, a.err);
         dph ^= 1u;
         d_pending = false;
       }
-      if (tid == 0) bulk_g2s(RW, img_src(0), 4u * STC_IMG, bars);
       const float2* sp = sp2 + (tile & 1) * STC_PTS;
-      __syncthreads();
-      float v[4][NPG], h[4][NPG], sv[4][NPG], hh[4][NPG], hl[4][NPG];
+      csync();
+      float v[4][NPG], h[4][NPG], sv[4][NPG];
       // ---- layer 1: z = W^1 x + b^1, z_x = W^1[:, 0], z_y = W^1[:, 1], z_lap = 0
       {
         const float2 x = sp[p];
@@ -581,32 +706,20 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         else
           jet4_fwd(v, h, sv);
         save4(scr, p, g, sv);
-        split4(h, hh, hl);
-        put_a(RA, p, g, hh, hl);   // L >= 3: a hidden-to-hidden layer reads it
+        put_a(RA, p, g, h);   // L >= 3: a hidden-to-hidden layer reads it
       }
       // ---- hidden-to-hidden layers on the tensor cores
       for (int k = 2; k <= L - 1; ++k) {
-        const int i = k - 2;
-        fence_to_async();
-        __syncthreads();
-        if (tid == 0) {
-          mbar_wait(bars, wph, a.err);
-          wph ^= 1u;
-          after_sync();
-          mma_rows(tmem, sa, sw);
-          mma_commit(bars + 1);
-        }
+        operands_ready(bars + 3, lane);
         mbar_park(bars + 1, mph, a.err);
         mph ^= 1u;
         after_sync();
-        // the weight buffer is free: the next image lands during the epilogue
-        if (tid == 0) bulk_g2s(RW, img_src(i + 1), 4u * STC_IMG, bars);
         {
           float z[NPT];
           tmem_rowz(tq + nb, tq + 64 + nb, z);
           zs_row_write(ZS, r, nb, z);
         }
-        __syncthreads();
+        csync();
         zs_read4(ZS, p, g, v);
         {
           const float4 b = *reinterpret_cast<const float4*>(pw + PW_BK + (k - 2) * 64 + 4 * g);
@@ -620,19 +733,15 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         else
           jet4_fwd(v, h, sv);
         save4(scr + (k - 1) * STC_W * ROWS, p, g, sv);
-        split4(h, hh, hl);
         if (k < L - 1) {
-          put_a(RA, p, g, hh, hl);
+          put_a(RA, p, g, h);
         } else {
-          put_t(RT, p, g, hh, hl);   // H^{L-1} for the output layer's weight gradient
+          put_t(RT, p, g, h);   // H^{L-1} for the output layer's weight gradient
           zs_write4(ZS, p, g, h);    // and, exact, for the output layer
         }
       }
-      // saved jets of layer L - 1 for the first reverse step, in flight
-      // during the output layer and the residual
-      load4(scr + (L - 2) * STC_W * ROWS, p, g, sv);
       // ---- output layer (FP32, row threads): y = W^L h + b^L on the value row, W^L h on the others
-      __syncthreads();   // H^{L-1} in the staging array
+      csync();   // H^{L-1} in the staging array
       {
         const float* WL = pw + PW_WL;
         float z[NPT];
@@ -644,7 +753,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           for (int j = 0; j < NPT; ++j) y[o] = fmaf(WL[o * 64 + nb + j], z[j], y[o]);
 #pragma unroll
         for (int o = 0; o < 3; ++o) Xs[(part * ROWS + r) * 4 + o] = y[o];
-        __syncthreads();
+        csync();
         if (part == 0) {
 #pragma unroll
           for (int o = 0; o < 3; ++o)
@@ -655,39 +764,19 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
               Js[(pr * 3 + o) * 4 + cr] = yy + (cr == 0 ? pw[PW_BL + o] : 0.f);
             }
         }
-        __syncthreads();
+        csync();
       }
       // ---- residual and its seeds, one thread per point
       if (tid < STC_PTS) {
         const bool vv = tid < nv;
-        PtJets J, G;
-#pragma unroll
-        for (int o = 0; o < XPINN_MAX_OUT; ++o)
-#pragma unroll
-          for (int cc = 0; cc < KMAX; ++cc) {
-            J.u[o][cc] = (o < D && cc < 4) ? Js[(tid * 3 + o) * 4 + cc] : 0.f;
-            G.u[o][cc] = 0.f;
-          }
-#pragma unroll
-        for (int cc = 0; cc < KMAX; ++cc) J.k[cc] = G.k[cc] = 0.f;
-        float rr[3] = {0.f, 0.f, 0.f};
         const float f = vv ? a.res_f[it.pt_off + t0 + tid] : 0.f;
-        const int ne = residual_fwd(a.pde, J, f, a.nu, a.re, rr);
-        float sq = 0.f, e[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          if (q < ne) {
-            sq += rr[q] * rr[q];
-            e[q] = vv ? coef * rr[q] : 0.f;
-          }
+        const float sq = point_residual(a.pde, D, Js + tid * 12, Gs + tid * 12, f, vv ? coef : 0.f, a.nu, a.re);
         if (vv) l0 += (double)sq * sd.inv_n_res;
-        residual_seed(a.pde, J, e, a.nu, a.re, G);
-#pragma unroll
-        for (int o = 0; o < 3; ++o)
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) Gs[(tid * 3 + o) * 4 + cc] = o < D ? G.u[o][cc] : 0.f;
       }
-      __syncthreads();
+      csync();
+      // saved jets of layer L - 1 for the first reverse step, in flight
+      // during the output layer's reverse pass
+      load4(scr + (L - 2) * STC_W * ROWS, p, g, sv);
       // ---- output layer, reverse (row threads): Hb^{L-1} = (W^L)^T yb into the
       // staging array (FP32); dW^L on the tensor cores (At = stacked H^{L-1}
       // transposed, B = yb transposed)
@@ -718,12 +807,8 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           }
         }
         fence_to_async();
-        __syncthreads();
-        if (tid == 0) {
-          after_sync();
-          mma_grad<4 * LB_S>(tmem + 144 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, first);
-          mma_commit(bars + 2);
-        }
+        csync();   // and Hb^{L-1} in the staging array for the point threads
+        if (lane == 0) mbar_arrive(bars + 3);
         d_pending = true;
       }
       // ---- hidden layers, reverse (point threads).  Hb^k is in the staging
@@ -734,7 +819,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           float z[NPT];
           tmem_rowz(tq + nb, tq + 64 + nb, z);
           zs_row_write(ZS, r, nb, z);
-          __syncthreads();
+          csync();
         }
         zs_read4(ZS, p, g, h);        // Hb^k
         if constexpr (GEN) {
@@ -747,7 +832,6 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         } else {
           jet4_bwd(sv, h, v);         // Zb^k
         }
-        split4(v, hh, hl);
         if (k >= 2) {
           value_sums(v, lane, dbs + (k - 2) * 64 + 4 * g);   // db^k
           // saved jets of layer k - 1 (for H^{k-1} below and the next step's
@@ -760,9 +844,9 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           d_pending = false;
           after_sync();
         }
-        put_t(RT, p, g, hh, hl);
+        put_t(RT, p, g, v);
         if (k >= 2) {
-          put_a(RA, p, g, hh, hl);
+          put_a(RA, p, g, v);
         } else if (g == 0) {
           // layer 1's input jets, transposed: value row (x, y, 1), x row
           // (1, 0, 0), y row (0, 1, 0), Laplacian row 0; column 2 gives db^1
@@ -784,43 +868,21 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
             *reinterpret_cast<float4*>(RS + SZ_S + s_off(j, 4 * p)) = lo;
           }
         }
-        fence_to_async();
-        __syncthreads();
+        operands_ready(bars + 3, lane);
         if (k == 1) {
-          if (tid == 0) {
-            after_sync();
-            mma_grad<4 * LB_S>(tmem + 128 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, first);
-            mma_commit(bars + 2);
-          }
           d_pending = true;
           break;
-        }
-        const int i = (L - 2) + (L - 1 - k);
-        if (tid == 0) {
-          mbar_wait(bars, wph, a.err);
-          wph ^= 1u;
-          after_sync();
-          mma_rows(tmem, sa, sw);
-          mma_commit(bars + 1);
         }
         // H^{k-1} from the saved jets of layer k - 1
         if constexpr (GEN)
           jet4_saved_gen(layer_act(nd, prm, k - 1), sv, h);
         else
           jet4_saved(sv, h);
-        split4(h, hh, hl);
-        mbar_park(bars + 1, mph, a.err);   // region A and the weight buffer are free
+        mbar_park(bars + 1, mph, a.err);   // region A is free
         mph ^= 1u;
         after_sync();
-        if (tid == 0 && i + 1 < nimg) bulk_g2s(RW, img_src(i + 1), 4u * STC_IMG, bars);
-        put_b(RA, p, g, hh, hl);
-        fence_to_async();
-        __syncthreads();
-        if (tid == 0) {
-          after_sync();
-          mma_grad<4 * LB_B>(tmem + 128 + 64 * (k - 2), st, sa, 4u * SZ_B, STC_W, first);
-          mma_commit(bars + 2);
-        }
+        put_b(RA, p, g, h);
+        operands_ready(bars + 3, lane);
         d_pending = true;
       }
       // ---- flush the weight-gradient accumulators into the item's slice
@@ -844,15 +906,15 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           tmem_cols<NPT>(tq + 128 + 64 * (k - 2) + nb, v);
 #pragma unroll
           for (int j = 0; j < NPT; ++j) stg[m * 65 + nb + j] = v[j];
-          __syncthreads();
+          csync();
           const int wo = nd.w[k], wi = nd.w[k - 1];
           float* gw = gs + nd.off[k];
-          for (int e = tid; e < wo * wi; e += NTH) {
+          for (int e = tid; e < wo * wi; e += NTC) {
             const int n = e / wi, j = e - n * wi;
             gw[e] = (add ? gw[e] : 0.f) + (st_hi[n * 65 + j] + st_lo[n * 65 + j]);
           }
           if (last && tid < wo) gw[wo * wi + tid] = dbs[(k - 2) * 64 + tid];
-          __syncthreads();
+          csync();
         }
         {
           // dW^1 (columns 0, 1) and db^1 (column 2); dW^L (columns o < D), transposed
@@ -866,7 +928,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
               stg[m * 65 + 16 + j] = vl[j];
             }
           }
-          __syncthreads();
+          csync();
           const int w1 = nd.w[1];
           if (tid < w1) {
             float* gw = gs + nd.off[1];
@@ -875,7 +937,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
             gw[2 * w1 + tid] = (add ? gw[2 * w1 + tid] : 0.f) + (st_hi[tid * 65 + 2] + st_lo[tid * 65 + 2]);
           }
           float* gw = gs + nd.off[L];
-          for (int e = tid; e < D * wl; e += NTH) {
+          for (int e = tid; e < D * wl; e += NTC) {
             const int o = e / wl, n = e - o * wl;
             gw[e] = (add ? gw[e] : 0.f) + (st_hi[n * 65 + 16 + o] + st_lo[n * 65 + 16 + o]);
           }
@@ -892,16 +954,15 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();   // region A is rewritten by the next tile
+        csync();   // region A is rewritten by the next tile
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    const double ls = block_sum(l0, red);
+    const double ls = compute_sum(l0, red, warp, lane);
     if (tid == 0) {
       a.loss_part[2 * (int64_t)(a.item_base + ii)] = ls;
       a.loss_part[2 * (int64_t)(a.item_base + ii) + 1] = 0.0;
     }
-    __syncthreads();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
