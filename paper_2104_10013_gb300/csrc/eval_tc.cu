@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(TC_ROWS, 1) eval_tc_kernel(TcArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
   const uint32_t t_warp = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's lanes
-  const uint32_t idesc = tc_idesc(W);
+  const uint32_t idesc = tc_idesc(W), idesc2 = tc_idesc(2 * W);
   const uint32_t sa_hi = smem_u32(Ahi), sa_lo = smem_u32(Alo);
   uint32_t wph = 0, mph = 0;
   const int n_items = a.n_items_dev ? min(a.n_items, *a.n_items_dev) : a.n_items;
@@ -258,9 +258,16 @@ __global__ void __launch_bounds__(TC_ROWS, 1) eval_tc_kernel(TcArgs a) {
             const uint64_t ahi = tc_sdesc(sa_hi + ks * 2 * TC_A_LBO, TC_A_LBO, 128);
             const uint64_t alo = tc_sdesc(sa_lo + ks * 2 * TC_A_LBO, TC_A_LBO, 128);
             const uint64_t bhi = tc_sdesc(sb_hi + ks * 256, 128, B_SBO);
-            const uint64_t blo = tc_sdesc(sb_lo + ks * 256, 128, B_SBO);
-            tc_mma(tmem, ahi, bhi, idesc, ks > 0 ? 1u : 0u);
-            tc_mma(tmem + S::COLS / 2, ahi, blo, idesc, ks > 0 ? 1u : 0u);
+            if constexpr (S::COLS / 2 == W) {
+              // the image's hi and lo halves as one operand of N = 2 W (their
+              // 8-row groups continue at the same stride): A_hi is read once
+              // for hi x hi (columns 0..W-1) and hi x lo (the cross columns)
+              tc_mma(tmem, ahi, bhi, idesc2, ks > 0 ? 1u : 0u);
+            } else {
+              const uint64_t blo = tc_sdesc(sb_lo + ks * 256, 128, B_SBO);
+              tc_mma(tmem, ahi, bhi, idesc, ks > 0 ? 1u : 0u);
+              tc_mma(tmem + S::COLS / 2, ahi, blo, idesc, ks > 0 ? 1u : 0u);
+            }
             tc_mma(tmem + S::COLS / 2, alo, bhi, idesc, 1u);
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
