@@ -104,11 +104,14 @@ def workload(name):
 K_RES = {0: (4,), 1: (4,), 2: (4,), 3: (4, 3)}
 
 
-def algorithmic_flops(pb):
+def algorithmic_flops(pb, subset=None):
     """6 K M FLOP per residual point (forward W h, reverse W^T z-bar and
-    z-bar h^T, FMA = 2 FLOP), M = sum over layers k >= 2 of N_k N_{k-1}."""
+    z-bar h^T, FMA = 2 FLOP), M = sum over layers k >= 2 of N_k N_{k-1};
+    over the subdomains in `subset` (indices), else all."""
     tot = 0.0
-    for s in pb.subs:
+    for q, s in enumerate(pb.subs):
+        if subset is not None and q not in subset:
+            continue
         for net, K in zip(s.nets, K_RES[pb.pde]):
             w = net.widths
             M = sum(w[k] * w[k - 1] for k in range(2, len(w)))
@@ -431,12 +434,13 @@ TF32_OVER_BF16 = 1.1 / 2.25
 
 
 def roofline_tc(pb, s, step_ms):
-    """The tensor-core training kernel (residual items of the width-64
-    networks) against the TF32 tensor peak: the measured BF16 burst figure
-    times the nominal TF32/BF16 ratio.  achieved = the algorithmic 6 K M FLOP
-    per residual point of those items / its CUDA-event time; the executed
-    tensor work is 10/3 of that (three TF32 products for the forward and
-    reverse contractions, four for the weight gradient)."""
+    """The tensor-core training kernel (residual items of the networks of
+    hidden widths train_tensor_cores..64) against the TF32 tensor peak: the
+    measured BF16 burst figure times the nominal TF32/BF16 ratio.  achieved =
+    the algorithmic 6 K M FLOP per residual point of the subdomains it trains
+    (unpadded widths) / its CUDA-event time; the executed tensor work counts
+    the hidden-to-hidden layers at the padded width, three TF32 products for
+    the forward and reverse contractions and four for the weight gradient."""
     n_items, n_tc, n_tc_sub = s.plan_counts()
     if not n_tc:
         return None
@@ -444,12 +448,17 @@ def roofline_tc(pb, s, step_ms):
     peaks = measured_peaks()
     bf16 = peaks.get("bf16_tflops")
     peak = bf16 * TF32_OVER_BF16 if bf16 else 1900.0 * TF32_OVER_BF16
-    flops = algorithmic_flops(pb)
+    on = s.tc_subdomains()
+    flops = algorithmic_flops(pb, {q for q in range(pb.n_sub) if on[q]})
+    # on the tensor pipe: the hidden-to-hidden layers at the padded width 64,
+    # three products forward and reverse and four for the weight gradient
+    executed = sum(10.0 / 3.0 * 6 * 4 * (len(sd.nets[0].widths) - 3) * 64 * 64 * sd.res_xy.shape[0]
+                   for q, sd in enumerate(pb.subs) if on[q])
     achieved = flops / (tc_ms / 1e3) / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "kernel": "xp::step_tc_kernel (residual items, tcgen05 kind::tf32)", "kernel_ms": tc_ms,
             "kernel_share_of_step": tc_ms / step_ms, "items": n_tc, "subdomains": n_tc_sub,
-            "flop_per_launch": flops, "executed_tensor_flop_per_launch": flops * 10.0 / 3.0,
+            "flop_per_launch": flops, "executed_tensor_flop_per_launch": executed,
             "peak_note": ("TF32 dense peak = measured BF16 burst (MEASURED_PEAKS.json) x 1.1/2.25, the nominal "
                           "TF32/BF16 ratio" if bf16 else "fallback 1.9 PFLOP/s BF16 x 1.1/2.25")}
 

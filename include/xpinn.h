@@ -375,7 +375,7 @@ typedef struct {
                                accumulation); other models keep the FP32 jet
                                kernel.  0: the jet kernel for every model */
   int32_t train_tensor_cores; /* 0: the FP32 jet kernel trains every
-                               subdomain.  N in [1, 64] (default 64): the
+                               subdomain.  N in [1, 64] (default 33): the
                                residual points of every subdomain with one
                                network of input (x, y), tanh, sin or cos
                                hidden layers (fixed or trained slopes),
@@ -391,7 +391,9 @@ typedef struct {
                                contractions of the hidden-to-hidden layers as
                                tcgen05 MMAs (three TF32 products over hi/lo
                                splits of both operands, FP32 accumulation),
-                               layers narrower than 64 zero-padded.  Their
+                               layers narrower than 64 zero-padded (the
+                               default 33 admits the widths that fill more
+                               than half of the 64-wide tile).  Their
                                data and interface points stay on the jet
                                kernel; forks (xpinn_fork_step) use the jet
                                kernel throughout */
@@ -451,6 +453,11 @@ int xpinn_phase_times(xpinn_handle h, float* ms);
  * train_tensor_cores), *n_tc_sub the subdomains those belong to.  Any
  * output pointer may be NULL. */
 int xpinn_plan_counts(xpinn_handle h, int32_t* n_items, int32_t* n_tc, int32_t* n_tc_sub);
+
+/* on[n_sub] (host): 1 where the subdomain's residual items run on the
+ * tensor-core kernel in the current plan (option train_tensor_cores, the
+ * half-the-points rule, xpinn_set_tc_select), else 0.  No device work. */
+int xpinn_tc_subdomains(xpinn_handle h, int32_t* on);
 
 /* Device time in milliseconds of the evaluation kernel (the jet kernel, or
  * the tensor-core kernel under eval_tensor_cores) of the most recent routed

@@ -237,7 +237,9 @@ struct xpinn_ctx {
   int n_sm = 0, grid = 0;
   int ring_cap = 256;
   int host_t = 0, host_slot = 0;
-  xpinn_options opt{0, 1, 4, 2, 0, 0, 256, 0, 1, STC_W};
+  // train_tensor_cores 33: hidden widths 33..64 qualify (below 33 the zero-padding to 64 more than
+  // quadruples the tensor work; the shape tuner decides per class above that)
+  xpinn_options opt{0, 1, 4, 2, 0, 0, 256, 0, 1, 33};
   int device = 0;
   cudaEvent_t ev[6] = {};         // phase marks 0-4, and 5 after the tensor-core kernel
   bool tc_timed = false;
@@ -2568,6 +2570,15 @@ int xpinn_plan_counts(xpinn_handle h, int32_t* n_items, int32_t* n_tc, int32_t* 
       }
     *n_tc_sub = c;
   }
+  API_END
+}
+
+int xpinn_tc_subdomains(xpinn_handle h, int32_t* on) {
+  API_BEGIN
+  if (!h || !on) fail(XPINN_ERR_INVALID, "bad arguments");
+  const Plan& pl = h->plan;
+  for (int q = 0; q < h->n_sub; ++q) on[q] = 0;
+  for (int i = pl.n_simt(); i < (int)pl.items.size(); ++i) on[pl.items[i].q] = 1;
   API_END
 }
 

@@ -120,6 +120,7 @@ def load() -> C.CDLL:
         "xpinn_iface_values": (C.c_int, [vp, fp, C.POINTER(i64), vp]),
         "xpinn_phase_times": (C.c_int, [vp, fp]),
         "xpinn_plan_counts": (C.c_int, [vp, vp, vp, vp]),
+        "xpinn_tc_subdomains": (C.c_int, [vp, vp]),
         "xpinn_eval_kernel_time": (C.c_int, [vp, C.POINTER(C.c_float)]),
         "xpinn_tc_kernel_time": (C.c_int, [vp, C.POINTER(C.c_float)]),
         "xpinn_autotune": (C.c_int, [vp, i32, C.POINTER(Options), C.POINTER(C.c_float)]),
@@ -530,6 +531,13 @@ class Solver:
         v = (C.c_int32 * 3)()
         _check(self.lib.xpinn_plan_counts(self.h, C.byref(v, 0), C.byref(v, 4), C.byref(v, 8)))
         return int(v[0]), int(v[1]), int(v[2])
+
+    def tc_subdomains(self):
+        """Per subdomain, 1 where its residual items run on the tensor-core
+        kernel in the current plan."""
+        on = np.zeros(self.pb.n_sub, np.int32)
+        _check(self.lib.xpinn_tc_subdomains(self.h, on.ctypes.data))
+        return on
 
     def tc_kernel_ms(self) -> float:
         """Device ms of the tensor-core training kernel in the last grouped

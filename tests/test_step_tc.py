@@ -148,20 +148,22 @@ def test_items_longer_than_a_flush_sampled():
 
 
 def test_tensor_core_choice_per_subdomain(X):
-    """The one 64-wide subdomain of the uneven Poisson workload lies below
-    the default share rule; choosing the tensor-core kernel for it alone puts
-    its residual items there, and the gradient still matches the oracle.
+    """With train_tensor_cores = 64, the one 64-wide subdomain of the uneven
+    Poisson workload lies below the share rule; choosing the tensor-core
+    kernel for it alone puts its residual items there, and the gradient still
+    matches the oracle.
     Choosing the jet kernel everywhere empties the tensor-core items of the
     Navier-Stokes case."""
     pb = P.poisson_xpinn(n_res_range=(300, 1500), n_iface=64, n_bc=40)
-    s = X.Solver(pb)
-    assert s.plan_counts()[1] == 0
+    s = solver(X, pb, 64)
+    assert s.plan_counts()[1] == 0 and not s.tc_subdomains().any()
     wide = [q for q, sd in enumerate(pb.subs) if max(sd.nets[0].widths[1:-1]) == 64 and len(sd.nets[0].widths) >= 4]
     assert wide
     sel = np.full(pb.n_sub, -1, np.int32)
     sel[wide] = 1
     s.set_tc_select(sel)
     assert s.plan_counts()[2] == len(wide)
+    assert list(np.flatnonzero(s.tc_subdomains())) == wide
     assert list(s.tc_select()) == list(sel)
     losses, g = s.grad()
     terms, g_ref = Oracle(pb).grad(pb.packed_params())
@@ -185,6 +187,26 @@ def test_general_activations_on_the_tensor_cores(X, acts, adaptive):
     pb = with_activations(ns_small(), list(acts), adaptive=adaptive)
     s = solver(X, pb, 64)
     assert s.plan_counts()[2] == pb.n_sub
+    losses, g = s.grad()
+    terms, g_ref = Oracle(pb).grad(pb.packed_params())
+    assert_losses(losses, terms)
+    assert_grads(g, g_ref, pb)
+    s.close()
+
+
+def test_default_minimum_width_takes_the_uneven_poisson_workload(X):
+    """At the default train_tensor_cores (33) the subdomains of the uneven
+    Poisson XPINN with hidden widths 33-64 and at least two hidden layers
+    hold more than half of its residual points, so the share rule sends
+    their residual items to the tensor-core kernel; the gradient matches the
+    oracle."""
+    pb = P.poisson_xpinn(n_res_range=(300, 1500), n_iface=64, n_bc=40)
+    s = X.Solver(pb)
+    assert s.options()["train_tensor_cores"] == 33
+    want = [q for q, sd in enumerate(pb.subs)
+            if all(33 <= w <= 64 for w in sd.nets[0].widths[1:-1]) and len(sd.nets[0].widths) >= 4]
+    assert 2 * sum(pb.subs[q].res_xy.shape[0] for q in want) >= pb.n_res
+    assert list(np.flatnonzero(s.tc_subdomains())) == want
     losses, g = s.grad()
     terms, g_ref = Oracle(pb).grad(pb.packed_params())
     assert_losses(losses, terms)
