@@ -11,8 +11,10 @@
 //   forward    Z^k  = H^{k-1} (W^k)^T           [128 rows x 64] . [64 x 64]
 //   reverse    Hb^{k-1} = Zb^k W^k              [128 rows x 64] . [64 x 64]
 //   gradient   dW^k += (Zb^k)^T H^{k-1}         [64 x 128 rows] . [128 rows x 64]
-// The first layer (two inputs), the output layer (at most three outputs),
-// the jet rules and the residual stay on the FP32 pipes.
+// The first layer (two inputs) and the output layer (at most three outputs),
+// their weight gradients included (sums over a warp's points by shuffles,
+// accumulated over the item in shared memory), the jet rules and the
+// residual stay on the FP32 pipes.
 //
 // Tile: 128 rows = the MMA's M, 32 points x 4 jet components (u, u_x, u_y,
 // lap u), row 4 p + c.  16 compute warps take two roles.  As row threads (four per
@@ -83,10 +85,8 @@ constexpr unsigned FULL = 0xffffffffu;
 // matrices, padded by 16 bytes (conflict-free 16-byte stores across points)
 constexpr int LB_B = 8 * 32 + 4;    // B' = H^T [N = 64][K = rows]: 1040 bytes
 constexpr int LB_T = 16 * 32 + 4;   // At = stacked Zb^T [M = 128][K = rows]: 2064 bytes
-constexpr int LB_S = 2 * 32 + 4;    // [N = 16][K = rows] (input jets, output seeds): 272 bytes
 constexpr int SZ_B = 32 * LB_B;     // one B' image (hi or lo)
 constexpr int SZ_T = 32 * LB_T;
-constexpr int SZ_S = 32 * LB_S;
 // the row-major A image [128 rows][64 neurons] (K = neuron): core matrices of
 // 8 rows x 4 neurons, 8-row groups 144 bytes apart (padded by 16 bytes, so
 // that the 16-byte runs of 8 points' rows fall in distinct bank groups),
@@ -96,11 +96,9 @@ constexpr int SZ_AF = 16 * A_LBO / 4;   // one A image (hi or lo), floats
 constexpr int SZ_RA = 2 * SZ_AF;        // region A: A (hi | lo), or B' (hi | lo)
 static_assert(2 * SZ_B <= SZ_RA, "region A holds B'");
 // region A also holds, between the forward and the reverse pass, the partial
-// outputs [4 parts][128 rows][4], the output jets and seeds [32 points][3][4],
-// and the [16][rows] images (hi | lo) of the output layer's and the first
-// layer's weight gradients, whose MMAs complete before region A is rewritten
-constexpr int RA_X = 0, RA_J = RA_X + 4 * ROWS * 4, RA_G = RA_J + 384, RA_S = 12288;
-static_assert(RA_G + 384 <= RA_S && RA_S + 2 * SZ_S <= SZ_RA && 2 * 64 * 65 <= SZ_RA, "region A");
+// outputs [4 parts][128 rows][4] and the output jets [32 points][3][4]
+constexpr int RA_X = 0, RA_J = RA_X + 4 * ROWS * 4;
+static_assert(RA_J + 384 <= SZ_RA && 2 * 64 * 65 <= SZ_RA, "region A");
 // staging [point][component][neuron]: component stride 72, point stride 292
 // floats, so that a point thread's 16-byte loads (8 points) and a row
 // thread's 16-byte stores (8 rows) each fall in distinct bank groups
@@ -112,7 +110,8 @@ constexpr int PW_W1 = 0, PW_B1 = 128, PW_BK = 192, PW_WL = PW_BK + 64 * (STC_MAX
 constexpr int SZ_PW = PW_BL + 4;
 // shared-memory map (floats): region A, At, the weight buffer, the staging
 // array, the points of two tiles, the bias-gradient sums [STC_MAXL - 2][64]
-// and [32 points][4], the FP32-pipe weights
+// and [32 points][4], the FP32-pipe weights, the slope-gradient sums, the
+// output seeds, the first and output layers' weight-gradient sums
 constexpr int O_A = 0;
 constexpr int O_T = O_A + SZ_RA;
 constexpr int O_W = O_T + SZ_T;
@@ -122,21 +121,23 @@ constexpr int O_DB = O_P + 128;
 constexpr int O_DL = O_DB + (STC_MAXL - 2) * 64;
 constexpr int O_PW = O_DL + 128;
 constexpr int O_SL = O_PW + SZ_PW;                   // slope-gradient sums [STC_MAXL - 1][16 warps]
-constexpr int SMEM_FLOATS = O_SL + (STC_MAXL - 1) * 16;
+constexpr int O_G = O_SL + (STC_MAXL - 1) * 16;      // output seeds [32 points][3][4]
+constexpr int O_D1 = O_G + 384;                      // dW^1 | db^1 sums [64][3]
+constexpr int O_DLW = O_D1 + 192;                    // dW^L sums [3][64]
+constexpr int SMEM_FLOATS = O_DLW + 192;
 // tensor-memory columns: Z main [0, 64), Z cross [64, 128), dW^k (k = 2..L-1)
-// at 128 + 64 (k - 2), then dW^1 and dW^L (16 columns each)
+// at 128 + 64 (k - 2)
 constexpr int TMEM_COLS = 512;
 // tiles a weight-gradient accumulator sums before it is added into the
 // item's slice (bounds the length of each tensor-memory accumulation)
 constexpr int STC_FLUSH = 16;
-static_assert(128 + 64 * (STC_MAXL - 2) + 32 <= TMEM_COLS, "tensor memory");
+static_assert(128 + 64 * (STC_MAXL - 2) <= TMEM_COLS, "tensor memory");
 
 // element offsets in the images whose K is the rows (column n, row r); the 4
 // rows of a point (r = 4 p + c) are one 16-byte run
 __device__ __forceinline__ int a_off5(int r, int g) { return g * (A_LBO / 4) + (r >> 3) * (A_SBO / 4) + (r & 7) * 4; }
 __device__ __forceinline__ int t_off(int m, int r) { return (m >> 3) * 32 + (r >> 2) * LB_T + (m & 7) * 4 + (r & 3); }
 __device__ __forceinline__ int b_off(int j, int r) { return (j >> 3) * 32 + (r >> 2) * LB_B + (j & 7) * 4 + (r & 3); }
-__device__ __forceinline__ int s_off(int j, int r) { return (j >> 3) * 32 + (r >> 2) * LB_S + (j & 7) * 4 + (r & 3); }
 
 __device__ __forceinline__ void fence_to_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -516,6 +517,59 @@ __device__ __noinline__ float point_residual(int pde, int D, const float* __rest
   return sq;
 }
 
+// The output layer's weight gradient over the warp's 32 points: for the
+// thread's 4 neurons m, sum over components c of yb[o][c] h[c][m] (yb the
+// point's output seeds [3][4], h = H^{L-1}); fixed butterfly, lane 0 adds
+// them to d[o * 64 + m]
+__device__ __forceinline__ void out_grad_sums(const float (&h)[4][NPG], const float* __restrict__ yb, int lane,
+                                              float* __restrict__ d) {
+  float g[3][NPG];
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    const float4 y = *reinterpret_cast<const float4*>(yb + 4 * o);
+#pragma unroll
+    for (int m = 0; m < NPG; ++m) g[o][m] = fmaf(y.x, h[0][m], fmaf(y.y, h[1][m], fmaf(y.z, h[2][m], y.w * h[3][m])));
+  }
+#pragma unroll
+  for (int sh = 16; sh > 0; sh >>= 1)
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+      for (int m = 0; m < NPG; ++m) g[o][m] += __shfl_xor_sync(FULL, g[o][m], sh);
+  if (lane == 0) {
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+      for (int m = 0; m < NPG; ++m) d[o * 64 + m] += g[o][m];
+  }
+}
+
+// The first layer's weight and bias gradients over the warp's 32 points from
+// the adjoints zb of z^1 = W^1 x + b^1 (value, x, y rows; the Laplacian row
+// of z^1 is constant): dW^1[m] += (zb x + zb_x, zb y + zb_y), db^1[m] += zb;
+// fixed butterfly, lane 0 adds them to d[3 m + 0..2]
+__device__ __forceinline__ void in_grad_sums(const float (&zb)[4][NPG], float2 x, int lane, float* __restrict__ d) {
+  float g[NPG][3];
+#pragma unroll
+  for (int m = 0; m < NPG; ++m) {
+    g[m][0] = fmaf(zb[0][m], x.x, zb[1][m]);
+    g[m][1] = fmaf(zb[0][m], x.y, zb[2][m]);
+    g[m][2] = zb[0][m];
+  }
+#pragma unroll
+  for (int sh = 16; sh > 0; sh >>= 1)
+#pragma unroll
+    for (int m = 0; m < NPG; ++m)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g[m][c] += __shfl_xor_sync(FULL, g[m][c], sh);
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < NPG; ++m)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) d[3 * m + c] += g[m][c];
+  }
+}
+
 // GEN = false: every network is tanh with fixed slopes (saved t); true: any
 // hidden activation and trained slopes (saved z, Phi evaluated again in the
 // reverse pass, slope gradients summed per layer).
@@ -525,11 +579,12 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   float* RA = sm + O_A;
   float* RT = sm + O_T;
   float* RW = sm + O_W;
-  float* RS = RA + RA_S;
   float* ZS = sm + O_Z;
   float* Xs = RA + RA_X;
   float* Js = RA + RA_J;
-  float* Gs = RA + RA_G;
+  float* Gs = sm + O_G;
+  float* d1s = sm + O_D1;
+  float* dlw = sm + O_DLW;
   float2* const sp2 = reinterpret_cast<float2*>(sm + O_P);   // points: this tile's and the next one's
   float* dbs = sm + O_DB;
   float* dls = sm + O_DL;
@@ -561,7 +616,7 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
   after_sync();
   const uint32_t tmem = s_tmem;
   const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16);   // this warp's lanes
-  const uint32_t sa = smem_u32(RA), st = smem_u32(RT), sw = smem_u32(RW), ss = smem_u32(RS);
+  const uint32_t sa = smem_u32(RA), st = smem_u32(RT), sw = smem_u32(RW);
   float* const scr = a.scratch + (int64_t)blockIdx.x * STC_SCRATCH;
   uint32_t wph = 0, mph = 0, dph = 0, oph = 0;   // phase parities
   bool d_pending = false;               // a gradient-MMA commit not yet waited for
@@ -617,11 +672,6 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
             mph ^= 1u;
             bulk_g2s(RW, img_src(k - 1), 4u * STC_IMG, bars);
           }
-          mbar_park(bars + 3, oph, a.err);              // dW^L: H^{L-1} and the output seeds
-          oph ^= 1u;
-          after_sync();
-          mma_grad<4 * LB_S>(tmem + 144 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, first);
-          mma_commit(bars + 2);
           for (int k = L - 1; k >= 2; --k) {
             mbar_park(bars + 3, oph, a.err);            // Hb^{k-1} = Zb^k W^k
             oph ^= 1u;
@@ -643,11 +693,6 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
             mma_grad<4 * LB_B>(tmem + 128 + 64 * (k - 2), st, sa, 4u * SZ_B, STC_W, first);
             mma_commit(bars + 2);
           }
-          mbar_park(bars + 3, oph, a.err);              // dW^1, db^1: Zb^1 and the input jets
-          oph ^= 1u;
-          after_sync();
-          mma_grad<4 * LB_S>(tmem + 128 + 64 * (L - 2), st, ss, 4u * SZ_S, 16, first);
-          mma_commit(bars + 2);
         }
       }
       __syncwarp();
@@ -676,12 +721,16 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
     for (int e = tid; e < (STC_MAXL - 2) * 64; e += NTC) dbs[e] = 0.f;
     if (tid < 128) dls[tid] = 0.f;
     if (tid < (STC_MAXL - 1) * 16) sls[tid] = 0.f;
+    if (tid < 192) {
+      d1s[tid] = 0.f;
+      dlw[tid] = 0.f;
+    }
     double l0 = 0.0;
     if (tid < STC_PTS) sp2[tid] = tid < it.n_pts ? a.pts[it.pt_off + tid] : make_float2(0.f, 0.f);
     for (int tile = 0; tile < n_tiles; ++tile) {
       const int t0 = tile * STC_PTS;
       const int nv = min(STC_PTS, it.n_pts - t0);
-      // every MMA of the previous tile has completed: regions A, At and S are free
+      // every MMA of the previous tile has completed: regions A and At are free
       if (d_pending) {
         mbar_park(bars + 2, dph, a.err);
         dph ^= 1u;
@@ -733,12 +782,10 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         else
           jet4_fwd(v, h, sv);
         save4(scr + (k - 1) * STC_W * ROWS, p, g, sv);
-        if (k < L - 1) {
+        if (k < L - 1)
           put_a(RA, p, g, h);
-        } else {
-          put_t(RT, p, g, h);   // H^{L-1} for the output layer's weight gradient
-          zs_write4(ZS, p, g, h);    // and, exact, for the output layer
-        }
+        else
+          zs_write4(ZS, p, g, h);    // H^{L-1}, exact, for the output layer
       }
       // ---- output layer (FP32, row threads): y = W^L h + b^L on the value row, W^L h on the others
       csync();   // H^{L-1} in the staging array
@@ -778,8 +825,8 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
       // during the output layer's reverse pass
       load4(scr + (L - 2) * STC_W * ROWS, p, g, sv);
       // ---- output layer, reverse (row threads): Hb^{L-1} = (W^L)^T yb into the
-      // staging array (FP32); dW^L on the tensor cores (At = stacked H^{L-1}
-      // transposed, B = yb transposed)
+      // staging array (FP32); its weight gradient follows in the reverse step
+      // of layer L - 1 (point threads)
       {
         const float* WL = pw + PW_WL;
         float yb[3], hb[NPT];
@@ -794,22 +841,11 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           const int t1 = t0 + STC_PTS + tid;
           sp2[((tile + 1) & 1) * STC_PTS + tid] = t1 < it.n_pts ? a.pts[it.pt_off + t1] : make_float2(0.f, 0.f);
         }
-        if (part == 0) {
+        if (part == 0 && cr == 0) {
 #pragma unroll
-          for (int o = 0; o < 16; ++o) {
-            const float2 s2 = tf32_split(o < 3 ? yb[o] : 0.f);
-            RS[s_off(o, r)] = s2.x;
-            RS[SZ_S + s_off(o, r)] = s2.y;
-          }
-          if (cr == 0) {
-#pragma unroll
-            for (int o = 0; o < 3; ++o) dls[pr * 4 + o] += yb[o];
-          }
+          for (int o = 0; o < 3; ++o) dls[pr * 4 + o] += yb[o];
         }
-        fence_to_async();
-        csync();   // and Hb^{L-1} in the staging array for the point threads
-        if (lane == 0) mbar_arrive(bars + 3);
-        d_pending = true;
+        csync();   // Hb^{L-1} in the staging array for the point threads
       }
       // ---- hidden layers, reverse (point threads).  Hb^k is in the staging
       // array: written above for k = L - 1, moved there from tensor memory
@@ -832,47 +868,34 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
         } else {
           jet4_bwd(sv, h, v);         // Zb^k
         }
+        if (k == L - 1) {
+          // dW^L[o][n] = sum over points and components of yb_o H^{L-1}_n
+          // (FP32; H^{L-1} rebuilt from the saved jets still in sv)
+          if constexpr (GEN)
+            jet4_saved_gen(layer_act(nd, prm, k), sv, h);
+          else
+            jet4_saved(sv, h);
+          out_grad_sums(h, Gs + p * 12, lane, dlw + 4 * g);
+        }
         if (k >= 2) {
           value_sums(v, lane, dbs + (k - 2) * 64 + 4 * g);   // db^k
           // saved jets of layer k - 1 (for H^{k-1} below and the next step's
           // reverse rule), in flight while the images are written
           load4(scr + (k - 2) * STC_W * ROWS, p, g, sv);
+        } else {
+          // dW^1 = sum of Zb x^T + Zb_x e_x^T + Zb_y e_y^T, db^1 = sum of Zb (FP32)
+          in_grad_sums(v, sp[p], lane, d1s + 12 * g);
+          break;
         }
-        if (d_pending) {   // the last gradient MMAs read regions A, At and S
+        if (d_pending) {   // the last gradient MMAs read regions A and At
           mbar_park(bars + 2, dph, a.err);
           dph ^= 1u;
           d_pending = false;
           after_sync();
         }
         put_t(RT, p, g, v);
-        if (k >= 2) {
-          put_a(RA, p, g, v);
-        } else if (g == 0) {
-          // layer 1's input jets, transposed: value row (x, y, 1), x row
-          // (1, 0, 0), y row (0, 1, 0), Laplacian row 0; column 2 gives db^1
-          const float2 x = sp[p];
-          const float2 sx = tf32_split(x.x), sy = tf32_split(x.y);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
-            if (j == 0) {
-              hi = make_float4(sx.x, 1.f, 0.f, 0.f);
-              lo.x = sx.y;
-            } else if (j == 1) {
-              hi = make_float4(sy.x, 0.f, 1.f, 0.f);
-              lo.x = sy.y;
-            } else if (j == 2) {
-              hi.x = 1.f;
-            }
-            *reinterpret_cast<float4*>(RS + s_off(j, 4 * p)) = hi;
-            *reinterpret_cast<float4*>(RS + SZ_S + s_off(j, 4 * p)) = lo;
-          }
-        }
+        put_a(RA, p, g, v);
         operands_ready(bars + 3, lane);
-        if (k == 1) {
-          d_pending = true;
-          break;
-        }
         // H^{k-1} from the saved jets of layer k - 1
         if constexpr (GEN)
           jet4_saved_gen(layer_act(nd, prm, k - 1), sv, h);
@@ -916,38 +939,27 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
           if (last && tid < wo) gw[wo * wi + tid] = dbs[(k - 2) * 64 + tid];
           csync();
         }
-        {
-          // dW^1 (columns 0, 1) and db^1 (column 2); dW^L (columns o < D), transposed
-          float v1[16], vl[16];
-          tmem_cols<16>(tq + 128 + 64 * (L - 2), v1);
-          tmem_cols<16>(tq + 144 + 64 * (L - 2), vl);
-          if (part == 0) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              stg[m * 65 + j] = v1[j];
-              stg[m * 65 + 16 + j] = vl[j];
-            }
-          }
-          csync();
+        if (last) {
+          // dW^1, db^1 and dW^L: FP32 sums over the whole item (shared memory)
           const int w1 = nd.w[1];
           if (tid < w1) {
             float* gw = gs + nd.off[1];
-            gw[2 * tid] = (add ? gw[2 * tid] : 0.f) + (st_hi[tid * 65] + st_lo[tid * 65]);
-            gw[2 * tid + 1] = (add ? gw[2 * tid + 1] : 0.f) + (st_hi[tid * 65 + 1] + st_lo[tid * 65 + 1]);
-            gw[2 * w1 + tid] = (add ? gw[2 * w1 + tid] : 0.f) + (st_hi[tid * 65 + 2] + st_lo[tid * 65 + 2]);
+            gw[2 * tid] = d1s[3 * tid];
+            gw[2 * tid + 1] = d1s[3 * tid + 1];
+            gw[2 * w1 + tid] = d1s[3 * tid + 2];
           }
           float* gw = gs + nd.off[L];
           for (int e = tid; e < D * wl; e += NTC) {
             const int o = e / wl, n = e - o * wl;
-            gw[e] = (add ? gw[e] : 0.f) + (st_hi[n * 65 + 16 + o] + st_lo[n * 65 + 16 + o]);
+            gw[e] = dlw[o * 64 + n];
           }
-          if (last && tid < D) {
+          if (tid < D) {
             float sb = 0.f;
             for (int q = 0; q < STC_PTS; ++q) sb += dls[q * 4 + tid];
             gw[D * wl + tid] = sb;
           }
           // trained slopes: dJ/da^k = n dJ/ds, the warps' sums in warp order
-          if (GEN && last && nd.aoff >= 0 && tid < L - 1) {
+          if (GEN && nd.aoff >= 0 && tid < L - 1) {
             float sb = 0.f;
             for (int q = 0; q < 16; ++q) sb += sls[tid * 16 + q];
             gs[nd.aoff + tid] = nd.scale * sb;
