@@ -377,10 +377,12 @@ __device__ __forceinline__ void save4(float* __restrict__ Sk, int p, int g, cons
     *reinterpret_cast<float4*>(Sk + (4 * g + i) * ROWS + 4 * p) = make_float4(sv[0][i], sv[1][i], sv[2][i], sv[3][i]);
 }
 
+// (through L1: the reverse pass prefetches a layer's lines there an epilogue
+// ahead of this load)
 __device__ __forceinline__ void load4(const float* __restrict__ Sk, int p, int g, float (&sv)[4][NPG]) {
 #pragma unroll
   for (int i = 0; i < NPG; ++i) {
-    const float4 v = __ldcg(reinterpret_cast<const float4*>(Sk + (4 * g + i) * ROWS + 4 * p));
+    const float4 v = __ldca(reinterpret_cast<const float4*>(Sk + (4 * g + i) * ROWS + 4 * p));
     sv[0][i] = v.x;
     sv[1][i] = v.y;
     sv[2][i] = v.z;
@@ -851,6 +853,13 @@ __global__ void __launch_bounds__(NTH, 1) step_tc_kernel(StepTcArgs a) {
       // array: written above for k = L - 1, moved there from tensor memory
       // (the row MMA of the step before, already waited for) for k < L - 1.
       for (int k = L - 1; k >= 1; --k) {
+        if (k >= 2) {
+          // the saved jets of layer k - 1, loaded after this step's rule:
+          // into L1 now, so that the load waits for L1 rather than L2
+#pragma unroll
+          for (int i = 0; i < NPG; ++i)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(scr + (k - 2) * STC_W * ROWS + (4 * g + i) * ROWS + 4 * p));
+        }
         if (k < L - 1) {
           float z[NPT];
           tmem_rowz(tq + nb, tq + 64 + nb, z);
