@@ -380,7 +380,7 @@ typedef struct {
                                network of input (x, y), tanh, sin or cos
                                hidden layers (fixed or trained slopes),
                                identity output of at most 3 components, 3 to
-                               7 weight layers and every hidden width within
+                               8 weight layers and every hidden width within
                                [N, 64], under a PDE trained with Laplacian
                                jets (Poisson, Navier-Stokes), are trained by
                                the tensor-core kernel when those subdomains

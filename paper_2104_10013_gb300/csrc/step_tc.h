@@ -1,7 +1,7 @@
 // Training-step kernel on the tensor cores (step_tc.cu): launch interface for
 // the host planner.  A subdomain qualifies when it has one network with
 // input (x, y), identity output of at most three components, tanh, sin or
-// cos hidden layers with fixed or trained slopes, 3 to 7 weight layers and
+// cos hidden layers with fixed or trained slopes, 3 to 8 weight layers and
 // every hidden width within [min_width, 64], and its PDE trains with
 // Laplacian jets (Poisson, Navier-Stokes).  Its residual items then run on
 // this kernel; its data and interface items stay on the FP32 jet kernel.
@@ -14,7 +14,7 @@
 
 namespace xp {
 
-constexpr int STC_MAXL = 7;                  // weight layers (the tensor-memory budget)
+constexpr int STC_MAXL = 8;                  // weight layers (the tensor-memory budget: 128 + 64 (L - 2) columns)
 constexpr int STC_W = 64;                    // hidden width of the tiles (narrower layers are zero-padded)
 constexpr int STC_PTS = 32;                  // points per tile (128 rows of 4 jet components)
 constexpr int STC_IMG = 2 * STC_W * STC_W;   // floats of one weight image (hi, then lo)

@@ -13,8 +13,9 @@ PDEs (Poisson, Navier-Stokes).
 * tanh, sin and cos hidden layers with trained or fixed slopes (the slope
   gradients included);
 * the smallest network the kernel takes (one hidden-to-hidden layer of width
-  33, zero-padded to 64) and items longer than one accumulator flush (16
-  tiles) on a large workload, sampled against the oracle;
+  33, zero-padded to 64), the deepest (seven hidden layers, every tensor-memory
+  column in use) and items longer than one accumulator flush (16 tiles) on a
+  large workload, sampled against the oracle;
 * Adam steps follow the oracle given the gradient, repeated gradients agree
   bit for bit, and the per-subdomain loop schedule agrees within tolerance;
 * the result lies within the tolerances of the FP32 jet kernel's.
@@ -207,6 +208,19 @@ def test_default_minimum_width_takes_the_uneven_poisson_workload(X):
             if all(33 <= w <= 64 for w in sd.nets[0].widths[1:-1]) and len(sd.nets[0].widths) >= 4]
     assert 2 * sum(pb.subs[q].res_xy.shape[0] for q in want) >= pb.n_res
     assert list(np.flatnonzero(s.tc_subdomains())) == want
+    losses, g = s.grad()
+    terms, g_ref = Oracle(pb).grad(pb.packed_params())
+    assert_losses(losses, terms)
+    assert_grads(g, g_ref, pb)
+    s.close()
+
+
+def test_deepest_network_on_the_tensor_cores(X):
+    """2 -> 64 x 7 -> 3: eight weight layers, every tensor-memory column in use
+    (six hidden-to-hidden weight-gradient accumulators)."""
+    pb = P.kovasznay_cpinn(nx=2, ny=1, n_res=300, n_iface=24, n_bc=30, depth=7)
+    s = solver(X, pb, 64)
+    assert s.plan_counts()[2] == pb.n_sub
     losses, g = s.grad()
     terms, g_ref = Oracle(pb).grad(pb.packed_params())
     assert_losses(losses, terms)
